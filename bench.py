@@ -1,0 +1,373 @@
+"""Benchmark of the CSFMM evaluation pass on GB300.
+
+Default workload (one step = one csfmm_evaluate of the whole hot path on a
+resident plan): Newtonian kernel 1/sqrt(2(1 - x.y)) on the equiangular
+cubed sphere with 6 x 1024^2 = 6,291,456 points, land-masked random weights,
+degree n = 12, MAC 0.7, leaf size N0 = 576, FP32-bulk form, one right-hand
+side.  Reported metric: FMM targets per second (N / time per evaluation),
+with the relative l2 error against an FP64 direct sum on sampled targets.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (launched by torch.distributed.run) every rank evaluates its own
+replica of the workload on its GPU (the path has no data-path exchange:
+replicas only); the time is the maximum over ranks and the value is the sum
+of targets over ranks divided by it.  --impl reference times the CPU oracle
+FMM (plain FP64 C) on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "newton-6m": dict(m=1024, kernel=2, n=12, theta=0.7, N0=576,
+                      desc="Newtonian 1/sqrt(2(1-x.y)), cubed sphere 6x1024^2 = 6,291,456 "
+                           "points, land-masked U[0,1] weights x cell area, n=12, MAC 0.7, "
+                           "N0=576, 1 RHS"),
+    "poisson-multirhs-1.5m": dict(m=512, kernel=0, n=10, theta=0.7, N0=400, nrhs=16,
+                                  desc="Poisson log kernel, cubed sphere 6x512^2 = 1,572,864 "
+                                       "points, 16 RHS of random Y_nm combinations, n=10, "
+                                       "MAC 0.7, N0=400"),
+}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload(name):
+    from paper_2508_13550_gb300 import inputs as I
+    wl = WORKLOADS[name]
+    if name == "newton-6m":
+        pts, A, w = I.workload_newton_land(wl["m"])
+    else:
+        pts, A, w, _ = I.workload_multi_rhs(wl["m"], wl["nrhs"], with_exact=False)
+    return wl, pts, A, np.ascontiguousarray(w)
+
+
+def cpu_oracle_sample(pts, w, wl, n_leaves, seed, repeats=1):
+    """Times the CPU oracle FMM evaluation restricted to every target of
+    n_leaves seeded random leaves (tree built beforehand, like a resident
+    plan).  Returns (targets/s, seconds, targets, threads)."""
+    import oracle as O
+    f = O.FMM(pts, wl["n"], wl["theta"], wl["N0"])
+    C = f.cells()
+    leaf = np.where(C["child"].max(axis=1) < 0)[0]
+    rng = np.random.default_rng(seed)
+    pick = rng.choice(leaf, min(n_leaves, len(leaf)), replace=False)
+    order = f.order()
+    tg = np.concatenate([order[C["begin"][c]:C["end"][c]] for c in pick])
+    t0 = time.perf_counter()
+    for _ in range(repeats):
+        f.evaluate(wl["kernel"], w, tg)
+    dt = (time.perf_counter() - t0) / repeats
+    return len(tg) / dt, dt, len(tg), O.num_threads()
+
+
+def run_reference(args):
+    """CPU oracle arm: each step evaluates a bounded sample of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle as O
+    wl, pts, A, w = make_workload(args.workload)
+    f = O.FMM(pts, wl["n"], wl["theta"], wl["N0"])
+    C = f.cells()
+    leaf = np.where(C["child"].max(axis=1) < 0)[0]
+    order = f.order()
+    rng = np.random.default_rng(7)
+    per_step = args.ref_leaves
+
+    def step():
+        pick = rng.choice(leaf, per_step, replace=False)
+        tg = np.concatenate([order[C["begin"][c]:C["end"][c]] for c in pick])
+        f.evaluate(wl["kernel"], w[:1], tg)
+        return len(tg)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    nt = 0
+    for _ in range(args.steps):
+        nt += step()
+    dt = time.perf_counter() - t0
+    val = nt / dt
+    sample = (f"per step: all targets of {per_step} seeded random leaves "
+              f"({nt // max(args.steps, 1)} targets) of the {wl['desc']} workload; "
+              f"tree built once before timing")
+    line = {"impl": "reference", "metric": "FMM targets/s at N=6.3M", "value": val,
+            "unit": "targets/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "N": len(pts),
+                                            "kernel": wl["kernel"], "degree": wl["n"],
+                                            "theta": wl["theta"], "max_leaf": wl["N0"]},
+            "cpu_baseline": {"value": val, "unit": "targets/s", "cores": O.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": "targets/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    from paper_2508_13550_gb300 import csfmm as Cs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    wl, pts, A, w = make_workload(args.workload)
+    N = len(pts)
+    nrhs = w.shape[0]
+    prec = Cs.FP32_BULK if args.precision == "fp32" else Cs.FP64
+    dpts = torch.from_numpy(pts).to(dev)
+    dw = torch.from_numpy(w).to(dev)
+    plan = Cs.plan_create(dpts, wl["kernel"], wl["n"], wl["theta"], wl["N0"], precision=prec,
+                          max_nrhs=max(nrhs, 1))
+    st = Cs.plan_stats(plan)
+    dim = Cs.kernel_dim(wl["kernel"])
+    out = torch.empty((nrhs, N, dim), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        Cs.evaluate(plan, dw, out=out)
+    torch.cuda.synchronize(dev)
+    Cs.plan_sync(plan)
+
+    # timed region (inputs resident; working set >> 129 MB L2)
+    Cs.plan_enable_timing(plan, True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        time.sleep(0.3)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            Cs.evaluate(plan, dw, out=out)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+    Cs.plan_enable_timing(plan, False)
+    ms = ev0.elapsed_time(ev1)
+    phases, calls = Cs.plan_phase_times(plan)
+    Cs.plan_sync(plan)
+    launches = Cs.plan_stats(plan)["launches_per_evaluate"] * args.steps
+    if dist:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = world * N * nrhs / (ms_step / 1e3)
+
+    # end to end through the host-buffer entry point: H2D weights, evaluate, D2H result
+    hw = torch.from_numpy(w).pin_memory()
+    hout = torch.empty((nrhs, N, dim), dtype=torch.float64).pin_memory()
+    lib = Cs.load()
+    import ctypes
+    for _ in range(2):
+        Cs._check(lib.csfmm_evaluate_host(plan.handle, ctypes.c_void_p(hw.data_ptr()), nrhs,
+                                          ctypes.c_void_p(hout.data_ptr()),
+                                          ctypes.c_void_p(stream.cuda_stream)))
+    e2e_steps = max(3, min(args.steps, 10))
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        Cs._check(lib.csfmm_evaluate_host(plan.handle, ctypes.c_void_p(hw.data_ptr()), nrhs,
+                                          ctypes.c_void_p(hout.data_ptr()),
+                                          ctypes.c_void_p(stream.cuda_stream)))
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if dist:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_val = world * N * nrhs / e2e_s
+
+    # accuracy against the FP64 direct sum on sampled targets (GPU direct sum)
+    rng = np.random.default_rng(20250813)
+    tg = np.sort(rng.choice(N, args.err_samples, replace=False)).astype(np.int64)
+    dtg = torch.from_numpy(tg).to(dev)
+    ds = Cs.direct(dpts, wl["kernel"], dw[:1], precision=Cs.FP64, targets=dtg)
+    got = out[:1, dtg]
+    err = float(torch.linalg.norm(got - ds) / torch.linalg.norm(ds))
+
+    # the plain single-RHS FP64 GPU FMM on the same workload, for the speedup
+    fp64 = None
+    if args.fp64_compare and prec == Cs.FP32_BULK:
+        p64 = Cs.plan_create(dpts, wl["kernel"], wl["n"], wl["theta"], wl["N0"],
+                             precision=Cs.FP64, max_nrhs=1)
+        o64 = torch.empty((1, N, dim), dtype=torch.float64, device=dev)
+        Cs.evaluate(p64, dw[:1], out=o64)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        Cs.evaluate(p64, dw[:1], out=o64)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms64 = e0.elapsed_time(e1)
+        err64 = float(torch.linalg.norm(o64[:1, dtg] - ds) / torch.linalg.norm(ds))
+        fp64 = {"ms_per_eval_1rhs": ms64, "rel_err_vs_fp64_ds": err64,
+                "speedup_of_fp32_bulk_per_rhs": ms64 / (ms_step / nrhs)}
+        Cs.plan_destroy(p64)
+        del o64
+
+    peaks, peak_kind = load_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    near_ms = phases["near"] / max(calls, 1)
+    near_evals = st["evals"][0] + st["evals"][1]
+    # ALU roofline of the near-field kernel: per evaluation 7 FP32-pipe
+    # operations and one MUFU operation; GB300 SM: 128 FP32 lanes and 16 MUFU
+    # lanes per clock, so the MUFU pipe bounds at 16 evaluations/clock/SM.
+    per_sm_clk = {2: 16.0, 0: 16.0, 1: 128.0 / 11.0, 100: 128.0 / 4.0}[wl["kernel"]]
+    peak_evals = 152 * per_sm_clk * sm_max * 1e6 * nrhs
+    achieved = near_evals * nrhs / (near_ms / 1e3)
+    traffic = None
+    line = {
+        "metric": "FMM targets/s at N=6.3M", "value": value, "unit": "targets/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if prec == Cs.FP32_BULK else "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": wl["desc"], "N": N, "nrhs": nrhs,
+                   "kernel": wl["kernel"], "degree": wl["n"], "theta": wl["theta"],
+                   "max_leaf": wl["N0"], "precision": args.precision,
+                   "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (plan + workspace "
+                         f"{st['device_bytes'] / 1e9:.2f} GB resident)"},
+        "rel_err_vs_fp64_ds": err, "err_samples": args.err_samples,
+        "kernel_evals_per_s": world * sum(st["evals"]) * nrhs / (ms_step / 1e3),
+        "phase_ms": {k: v / max(calls, 1) for k, v in phases.items()},
+        "plan_build_ms": st["build_ms"],
+        "fp64_gpu_fmm": fp64,
+        "gpu_launches": launches,
+        "e2e": {"value": e2e_val, "unit": "targets/s",
+                "h2d_bytes_per_step": int(w.nbytes), "d2h_bytes_per_step": int(8 * nrhs * N * dim)},
+        "roofline": {"kernel": "near_kernel (PP + PC)", "bound": "alu",
+                     "achieved": achieved / 1e9, "peak": peak_evals / 1e9, "unit": "Geval/s",
+                     "frac": achieved / peak_evals, "traffic": traffic,
+                     "peak_source": f"{peak_kind} sm_max_mhz x 152 SMs x {per_sm_clk:.1f} "
+                                    "evals/clk/SM"},
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, dt, ntg, cores = cpu_oracle_sample(pts, w[:1], wl, args.cpu_leaves, 3)
+        line["cpu_baseline"] = {"value": v, "unit": "targets/s", "cores": cores, "kind": "oracle",
+                                "sample": f"all {ntg} targets of {args.cpu_leaves} seeded random "
+                                          f"leaves, FP64 oracle FMM, {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    Cs.plan_destroy(plan)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="newton-6m", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--err-samples", type=int, default=2048)
+    ap.add_argument("--cpu-leaves", type=int, default=64)
+    ap.add_argument("--ref-leaves", type=int, default=16)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-compare", dest="fp64_compare", action="store_false")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        log("warning: fewer than 3 warm-up steps")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,214 @@
+/*
+ * csfmm.h -- C ABI of the GB300 cubed-sphere fast multipole method (CSFMM).
+ *
+ * The library evaluates the spherical N-body sum of the midpoint rule
+ *     phi(x_i) = sum_{j != i} K(x_i, x_j) w_j ,    i = 1..N          (Sec. 1, Eq. nbodysum)
+ * for points x_j on the unit sphere, either directly (csfmm_direct) or with
+ * the CSFMM of Chen & Krasny (arXiv 2508.13550): a quadtree of equiangular
+ * gnomonic cubed-sphere cells (Sec. 3), barycentric Lagrange interpolation on
+ * (n+1)^2 Chebyshev proxy points per cell (Sec. 4), PP/PC/CP/CC interactions
+ * chosen by a dual tree traversal with the MAC (r_t + r_s)/R < theta (Sec. 5,
+ * Sec. 8, Algorithm "CSFMM"), an upward pass (Sec. 6) and a downward pass
+ * (Sec. 8.1).  All work runs in CUDA kernels on one GPU.
+ *
+ * Conventions for every entry point
+ *   - Status: every function returns a csfmm_status and never throws.  The
+ *     text of the last error of the calling thread is csfmm_last_error().
+ *     Argument errors are detected on the host before any launch.
+ *   - Memory: "device" pointers are CUDA global memory of the current
+ *     device, owned by the caller; "host" pointers are host memory owned by
+ *     the caller.  A plan owns every device buffer it allocates and frees it
+ *     in csfmm_plan_destroy.
+ *   - Streams: a stream argument is a cudaStream_t passed as void* (NULL =
+ *     the legacy default stream).  Calls marked "asynchronous" only enqueue
+ *     work; their inputs and outputs must stay valid until the stream reaches
+ *     the end of the call.
+ *   - Layout: points are [N][3] row-major FP64 unit vectors.  Weights are
+ *     [nrhs][N] FP64 (weight vector r starts at weights + r*N).  Outputs are
+ *     [nrhs][N][dim] FP64 in the input order of the points, dim = 3 for the
+ *     Biot-Savart kernel, 1 otherwise.
+ */
+#ifndef CSFMM_H
+#define CSFMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CSFMM_OK = 0,
+  CSFMM_ERR_INVALID_ARG = 1,   /* bad pointer, size, kernel id, degree, theta or leaf size */
+  CSFMM_ERR_NOT_ON_SPHERE = 2, /* a point with | |x|^2 - 1 | > 1e-12 (the method assumes x on S^2, Sec. 1) */
+  CSFMM_ERR_OUT_OF_MEMORY = 3, /* a device allocation failed; nothing was leaked */
+  CSFMM_ERR_CUDA = 4,          /* a CUDA runtime call failed (message in csfmm_last_error) */
+  CSFMM_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up */
+  CSFMM_ERR_UNSUPPORTED = 6,   /* valid request outside what this build implements */
+  CSFMM_ERR_BUSY = 7,          /* serving: no slot or memory free right now */
+  CSFMM_ERR_DEVICE = 8         /* a kernel reported an internal error in the plan's status word */
+} csfmm_status;
+
+/* Kernels K(x, y) on the unit sphere (Sec. 2); 1 - x.y is evaluated as
+ * |x - y|^2 / 2. */
+enum {
+  CSFMM_KERNEL_LAPLACE = 0,     /* G_L = -(1/4pi) ln(1 - x.y), Eq. G_L; dim 1 */
+  CSFMM_KERNEL_BIOT_SAVART = 1, /* K_BS = -(1/4pi) (x cross y)/(1 - x.y), Eq. K_BS; dim 3 */
+  CSFMM_KERNEL_NEWTON = 2,      /* 1/sqrt(2(1 - x.y)) = 1/|x - y|, leading term of Eq. G_SAL_approx; dim 1 */
+  CSFMM_KERNEL_ONE = 100        /* K = 1, a test kernel (every interpolation is exact) */
+};
+
+/* Precision forms. */
+enum {
+  CSFMM_FP64 = 0,      /* every step in FP64 */
+  CSFMM_FP32_BULK = 1  /* kernel evaluations and per-tile sums in FP32 on pair-relative
+                          coordinates; geometry, interpolation weights and the final
+                          per-target accumulation in FP64 */
+};
+
+/* Interaction list types (Sec. 5). */
+enum { CSFMM_LIST_PP = 0, CSFMM_LIST_PC = 1, CSFMM_LIST_CP = 2, CSFMM_LIST_CC = 3 };
+
+typedef struct {
+  int precision;  /* CSFMM_FP64 (default) or CSFMM_FP32_BULK */
+  int max_nrhs;   /* right-hand sides processed per pass; larger nrhs is split (default 16) */
+  int use_graphs; /* 1: replay evaluate passes from a captured CUDA graph (default 0) */
+  int reserved[5];
+} csfmm_options;
+
+typedef struct csfmm_plan_s *csfmm_plan;
+
+typedef struct {
+  int64_t N;
+  int kernel_id, degree, max_leaf, precision;
+  double theta;
+  int32_t nlevels, ncells, nleaves;
+  int64_t n_list[4];       /* entries of the PP, PC, CP, CC lists */
+  int64_t evals[4];        /* kernel evaluations per evaluate and RHS: PP (self excluded), PC, CP, CC */
+  int64_t pairs_covered;   /* sum over list entries of |C_t| |C_s|; equals N^2 */
+  double mac_margin;       /* min |(r_t + r_s) - theta R| / (theta R) over MAC tests with R > 0 */
+  int64_t device_bytes;    /* device memory held by the plan (including its workspace) */
+  double build_ms;         /* wall time of csfmm_plan_create */
+  int64_t launches_per_evaluate; /* kernels launched by the last evaluation */
+} csfmm_stats;
+
+/* Evaluation phases timed by csfmm_plan_phase_times. */
+enum {
+  CSFMM_PHASE_GATHER = 0, CSFMM_PHASE_P2M = 1, CSFMM_PHASE_M2M = 2, CSFMM_PHASE_FAR = 3,
+  CSFMM_PHASE_NEAR = 4, CSFMM_PHASE_L2L = 5, CSFMM_PHASE_L2P = 6, CSFMM_NUM_PHASES = 7
+};
+
+/* Builds a plan on the current device: sorts the points into cubed-sphere
+ * quadtree order (Sec. 3; a cell with more than max_leaf points splits into
+ * its non-empty quadrants), computes cell centres, radii and Chebyshev proxy
+ * points (Sec. 4), and the PP/PC/CP/CC lists of the dual tree traversal
+ * (Sec. 8, Algorithm "CSFMM").
+ *   points    device, [N][3] FP64 unit vectors; copied, may be freed after return
+ *   N         >= 1 (< 2^31)
+ *   kernel_id a CSFMM_KERNEL_* value
+ *   degree    n, 1..16: (n+1)^2 proxies per cell
+ *   theta     MAC parameter, 0 < theta < 1 (the paper uses 0.5..0.9)
+ *   max_leaf  N0 >= 1
+ *   opt       NULL for defaults
+ *   stream    work is enqueued on it; the call synchronises it before returning
+ *   out       receives the plan handle (NULL on error)
+ * Errors: INVALID_ARG, NOT_ON_SPHERE, OUT_OF_MEMORY, CUDA. */
+csfmm_status csfmm_plan_create(const double *points, int64_t N, int kernel_id, int degree,
+                               double theta, int max_leaf, const csfmm_options *opt,
+                               void *stream, csfmm_plan *out);
+
+/* Evaluates phi for nrhs weight vectors with the plan's tree (Algorithm
+ * "CSFMM": upward pass, PP/PC/CP/CC interactions, downward pass).
+ * Asynchronous on stream.
+ *   weights device, [nrhs][N] FP64 in input order
+ *   out     device, [nrhs][N][dim] FP64 in input order (fully overwritten)
+ * Calls on one plan must not overlap in time (they share its workspace):
+ * serialise them on one stream or use csfmm_workspace + csfmm_evaluate_ws.
+ * Errors: INVALID_ARG, CUDA, DEVICE (a deferred device status). */
+csfmm_status csfmm_evaluate(csfmm_plan plan, const double *weights, int nrhs, double *out,
+                            void *stream);
+
+/* Same as csfmm_evaluate with HOST weights and output: copies the weights
+ * to the device, evaluates, copies phi back and synchronises the stream.
+ * Pinned host memory makes the copies asynchronous DMA.
+ *   weights host, [nrhs][N]; out host, [nrhs][N][dim]. */
+csfmm_status csfmm_evaluate_host(csfmm_plan plan, const double *weights, int nrhs, double *out,
+                                 void *stream);
+
+/* A workspace holds the per-evaluation buffers (sorted weights, proxy
+ * weights, proxy potentials, near-field potentials) for up to max_nrhs
+ * right-hand sides, so that evaluations of one plan can run concurrently on
+ * different streams.  It must be used with the plan it was made for. */
+typedef struct csfmm_workspace_s *csfmm_workspace;
+csfmm_status csfmm_workspace_create(csfmm_plan plan, int max_nrhs, csfmm_workspace *out);
+csfmm_status csfmm_workspace_destroy(csfmm_workspace ws);
+csfmm_status csfmm_evaluate_ws(csfmm_plan plan, csfmm_workspace ws, const double *weights,
+                               int nrhs, double *out, void *stream);
+
+/* Direct sum of Eq. (nbodysum) with the i = j term omitted.  Asynchronous.
+ *   points  device [N][3]; weights device [nrhs][N]; out device [nrhs][N][dim]
+ *   precision CSFMM_FP64 (per-target compensated FP64 sums) or CSFMM_FP32_BULK
+ *             (FP32 kernel values on FP64-differenced coordinates, FP64
+ *             accumulation across 256-source tiles)
+ * Errors: INVALID_ARG, CUDA. */
+csfmm_status csfmm_direct(const double *points, int64_t N, int kernel_id, const double *weights,
+                          int nrhs, double *out, int precision, void *stream);
+
+/* Direct sum at a subset of targets: out[r][t][dim] = phi(points[targets[t]]).
+ *   targets device int64 [ntargets], each in [0, N). */
+csfmm_status csfmm_direct_targets(const double *points, int64_t N, int kernel_id,
+                                  const double *weights, int nrhs, const int64_t *targets,
+                                  int64_t ntargets, double *out, int precision, void *stream);
+
+/* Plan statistics (host struct). */
+csfmm_status csfmm_plan_stats(csfmm_plan plan, csfmm_stats *stats);
+
+/* Copies plan structures to HOST arrays sized from csfmm_plan_stats, for
+ * tests and tools.  Cells are exported in the plan's order:
+ *   face, level (int32 [ncells]); ia, ib (int64, integer (xi, eta) cell
+ *   coordinates at its level); begin, end (int64, range in tree order);
+ *   parent (int32, -1 for roots); child (int32 [ncells][4] by quadrant
+ *   2*bit_eta + bit_xi, -1 if empty); centre (FP64 [ncells][3]); radius.
+ * Any pointer may be NULL to skip that array. */
+csfmm_status csfmm_plan_export_cells(csfmm_plan plan, int32_t *face, int32_t *level, int64_t *ia,
+                                     int64_t *ib, int64_t *begin, int64_t *end, int32_t *parent,
+                                     int32_t *child, double *centre, double *radius);
+/* List entries of one type, grouped by target cell: t[e], s[e] (int32). */
+csfmm_status csfmm_plan_export_list(csfmm_plan plan, int list_type, int32_t *t, int32_t *s);
+/* Tree order: order[i] = input index of the i-th point in tree order. */
+csfmm_status csfmm_plan_export_order(csfmm_plan plan, int64_t *order);
+/* Proxy points FP64 [ncells][(n+1)^2][3], proxy index k1*(n+1) + k2. */
+csfmm_status csfmm_plan_export_proxies(csfmm_plan plan, double *proxies);
+/* Proxy weights after the upward pass of the last evaluation, HOST FP64
+ * [ncells][nrhs][(n+1)^2] (first nrhs vectors of that call, nrhs <= its count). */
+csfmm_status csfmm_plan_export_proxy_weights(csfmm_plan plan, int nrhs, double *wbar);
+
+/* Phase timing.  While enabled, every evaluation of the plan records CUDA
+ * events on its stream between its phases (no synchronisation).
+ * csfmm_plan_phase_times synchronises those events, writes the summed
+ * milliseconds per phase into ms[CSFMM_NUM_PHASES] (host), the number of
+ * timed evaluations into *calls, and clears the record.  For the FAR and NEAR
+ * phases the sum covers every launch of the phase in the evaluation. */
+csfmm_status csfmm_plan_enable_timing(csfmm_plan plan, int on);
+csfmm_status csfmm_plan_phase_times(csfmm_plan plan, double *ms, int64_t *calls);
+
+/* Waits for the plan's work on stream and returns a deferred device status
+ * (CSFMM_ERR_DEVICE / CSFMM_ERR_TIMEOUT) if a kernel reported one. */
+csfmm_status csfmm_plan_sync(csfmm_plan plan, void *stream);
+
+/* Frees every device buffer of the plan.  The caller must make sure no work
+ * of the plan is still running. */
+csfmm_status csfmm_plan_destroy(csfmm_plan plan);
+
+/* Thread-local text of the last error (never NULL). */
+const char *csfmm_last_error(void);
+
+/* Library version string. */
+const char *csfmm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CSFMM_H */

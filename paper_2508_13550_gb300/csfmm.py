@@ -1,0 +1,326 @@
+"""Thin Python binding of the C ABI in include/csfmm.h.
+
+Argument marshalling only: every step of the evaluation runs in the CUDA
+library libcsfmm.so.  Tensors are torch CUDA tensors (float64, contiguous);
+streams default to torch's current stream.  There is no CPU fallback: if the
+library cannot be loaded, every call raises.
+
+    plan = plan_create(points, kernel_id, degree, theta, max_leaf, precision=FP64)
+    out  = evaluate(plan, weights)            # weights [nrhs, N] -> [nrhs, N, dim]
+    out  = evaluate_host(plan, weights_np)    # host numpy in/out (copies inside)
+    out  = direct(points, kernel_id, weights, precision=FP64)
+    plan_stats(plan), plan_export_cells(plan), plan_export_list(plan, type), ...
+    plan_destroy(plan)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+KERNEL_LAPLACE = 0
+KERNEL_BIOT_SAVART = 1
+KERNEL_NEWTON = 2
+KERNEL_ONE = 100
+FP64 = 0
+FP32_BULK = 1
+LIST_PP, LIST_PC, LIST_CP, LIST_CC = 0, 1, 2, 3
+
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "NOT_ON_SPHERE", 3: "OUT_OF_MEMORY", 4: "CUDA",
+          5: "TIMEOUT", 6: "UNSUPPORTED", 7: "BUSY", 8: "DEVICE"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libcsfmm.so")
+_lock = threading.Lock()
+_lib = None
+
+
+class CsfmmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"csfmm {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("max_nrhs", ctypes.c_int),
+                ("use_graphs", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("kernel_id", ctypes.c_int), ("degree", ctypes.c_int),
+                ("max_leaf", ctypes.c_int), ("precision", ctypes.c_int),
+                ("theta", ctypes.c_double), ("nlevels", ctypes.c_int32),
+                ("ncells", ctypes.c_int32), ("nleaves", ctypes.c_int32),
+                ("n_list", ctypes.c_int64 * 4), ("evals", ctypes.c_int64 * 4),
+                ("pairs_covered", ctypes.c_int64), ("mac_margin", ctypes.c_double),
+                ("device_bytes", ctypes.c_int64), ("build_ms", ctypes.c_double),
+                ("launches_per_evaluate", ctypes.c_int64)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["n_list"] = list(self.n_list)
+        d["evals"] = list(self.evals)
+        return d
+
+
+_VP, _I64, _I32, _D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+_SIGS = {
+    "csfmm_plan_create": [_VP, _I64, ctypes.c_int, ctypes.c_int, _D, ctypes.c_int,
+                          ctypes.POINTER(Options), _VP, ctypes.POINTER(_VP)],
+    "csfmm_evaluate": [_VP, _VP, ctypes.c_int, _VP, _VP],
+    "csfmm_evaluate_host": [_VP, _VP, ctypes.c_int, _VP, _VP],
+    "csfmm_workspace_create": [_VP, ctypes.c_int, ctypes.POINTER(_VP)],
+    "csfmm_workspace_destroy": [_VP],
+    "csfmm_evaluate_ws": [_VP, _VP, _VP, ctypes.c_int, _VP, _VP],
+    "csfmm_direct": [_VP, _I64, ctypes.c_int, _VP, ctypes.c_int, _VP, ctypes.c_int, _VP],
+    "csfmm_direct_targets": [_VP, _I64, ctypes.c_int, _VP, ctypes.c_int, _VP, _I64, _VP,
+                             ctypes.c_int, _VP],
+    "csfmm_plan_stats": [_VP, ctypes.POINTER(Stats)],
+    "csfmm_plan_export_cells": [_VP] + [_VP] * 10,
+    "csfmm_plan_export_list": [_VP, ctypes.c_int, _VP, _VP],
+    "csfmm_plan_export_order": [_VP, _VP],
+    "csfmm_plan_export_proxies": [_VP, _VP],
+    "csfmm_plan_export_proxy_weights": [_VP, ctypes.c_int, _VP],
+    "csfmm_plan_enable_timing": [_VP, ctypes.c_int],
+    "csfmm_plan_phase_times": [_VP, _VP, _VP],
+    "csfmm_plan_sync": [_VP, _VP],
+    "csfmm_plan_destroy": [_VP],
+    "csfmm_last_error": [],
+    "csfmm_version": [],
+}
+
+
+def load(path: str | None = None):
+    """Loads libcsfmm.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"CUDA library {p} is missing: run __graft_entry__.build()")
+        lib = ctypes.CDLL(p)
+        for name, args in _SIGS.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = ctypes.c_char_p if name in ("csfmm_last_error", "csfmm_version") else ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(rc):
+    if rc != 0:
+        raise CsfmmError(rc, load().csfmm_last_error().decode())
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev(t, dtype=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def kernel_dim(kernel_id: int) -> int:
+    return 3 if kernel_id == KERNEL_BIOT_SAVART else 1
+
+
+class Plan:
+    """Owns a csfmm_plan handle (destroyed with the object)."""
+
+    def __init__(self, handle, N, kernel_id, points):
+        self.handle = handle
+        self.N = N
+        self.kernel_id = kernel_id
+        self.dim = kernel_dim(kernel_id)
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            try:
+                load().csfmm_plan_destroy(self.handle)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def plan_create(points, kernel_id: int, degree: int, theta: float, max_leaf: int,
+                precision: int = FP64, max_nrhs: int = 16, use_graphs: int = 0, stream=None):
+    import torch
+    lib = load()
+    opt = Options(precision, max_nrhs, use_graphs)
+    h = ctypes.c_void_p()
+    N = points.shape[0]
+    rc = lib.csfmm_plan_create(_dev(points, torch.float64), N, kernel_id, degree, theta,
+                               max_leaf, ctypes.byref(opt), _stream(stream), ctypes.byref(h))
+    _check(rc)
+    return Plan(h, N, kernel_id, points)
+
+
+def plan_destroy(plan: Plan):
+    if plan.handle:
+        _check(load().csfmm_plan_destroy(plan.handle))
+        plan.handle = None
+
+
+def evaluate(plan: Plan, weights, out=None, stream=None):
+    import torch
+    w = weights if weights.dim() == 2 else weights.unsqueeze(0)
+    nrhs = w.shape[0]
+    if out is None:
+        out = torch.empty((nrhs, plan.N, plan.dim), dtype=torch.float64, device=w.device)
+    _check(load().csfmm_evaluate(plan.handle, _dev(w, torch.float64), nrhs,
+                                 _dev(out, torch.float64), _stream(stream)))
+    return out
+
+
+def evaluate_host(plan: Plan, weights, out=None, stream=None):
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    if w.ndim == 1:
+        w = w[None]
+    nrhs = w.shape[0]
+    if out is None:
+        out = np.empty((nrhs, plan.N, plan.dim))
+    _check(load().csfmm_evaluate_host(plan.handle, ctypes.c_void_p(w.ctypes.data), nrhs,
+                                      ctypes.c_void_p(out.ctypes.data), _stream(stream)))
+    return out
+
+
+def workspace_create(plan: Plan, max_nrhs: int):
+    h = ctypes.c_void_p()
+    _check(load().csfmm_workspace_create(plan.handle, max_nrhs, ctypes.byref(h)))
+    return h
+
+
+def workspace_destroy(ws):
+    _check(load().csfmm_workspace_destroy(ws))
+
+
+def evaluate_ws(plan: Plan, ws, weights, out=None, stream=None):
+    import torch
+    w = weights if weights.dim() == 2 else weights.unsqueeze(0)
+    nrhs = w.shape[0]
+    if out is None:
+        out = torch.empty((nrhs, plan.N, plan.dim), dtype=torch.float64, device=w.device)
+    _check(load().csfmm_evaluate_ws(plan.handle, ws, _dev(w, torch.float64), nrhs,
+                                    _dev(out, torch.float64), _stream(stream)))
+    return out
+
+
+def direct(points, kernel_id: int, weights, precision: int = FP64, targets=None, out=None,
+           stream=None):
+    import torch
+    w = weights if weights.dim() == 2 else weights.unsqueeze(0)
+    nrhs = w.shape[0]
+    N = points.shape[0]
+    dim = kernel_dim(kernel_id)
+    lib = load()
+    if targets is None:
+        if out is None:
+            out = torch.empty((nrhs, N, dim), dtype=torch.float64, device=w.device)
+        _check(lib.csfmm_direct(_dev(points, torch.float64), N, kernel_id,
+                                _dev(w, torch.float64), nrhs, _dev(out, torch.float64),
+                                precision, _stream(stream)))
+    else:
+        nt = targets.shape[0]
+        if out is None:
+            out = torch.empty((nrhs, nt, dim), dtype=torch.float64, device=w.device)
+        _check(lib.csfmm_direct_targets(_dev(points, torch.float64), N, kernel_id,
+                                        _dev(w, torch.float64), nrhs,
+                                        _dev(targets, torch.int64), nt,
+                                        _dev(out, torch.float64), precision, _stream(stream)))
+    return out
+
+
+def plan_stats(plan: Plan) -> dict:
+    s = Stats()
+    _check(load().csfmm_plan_stats(plan.handle, ctypes.byref(s)))
+    return s.as_dict()
+
+
+def _np_ptr(a):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def plan_export_cells(plan: Plan) -> dict:
+    nc = plan_stats(plan)["ncells"]
+    out = dict(face=np.zeros(nc, np.int32), level=np.zeros(nc, np.int32),
+               ia=np.zeros(nc, np.int64), ib=np.zeros(nc, np.int64),
+               begin=np.zeros(nc, np.int64), end=np.zeros(nc, np.int64),
+               parent=np.zeros(nc, np.int32), child=np.zeros((nc, 4), np.int32),
+               centre=np.zeros((nc, 3)), radius=np.zeros(nc))
+    keys = ("face", "level", "ia", "ib", "begin", "end", "parent", "child", "centre", "radius")
+    _check(load().csfmm_plan_export_cells(plan.handle, *[_np_ptr(out[k]) for k in keys]))
+    return out
+
+
+def plan_export_list(plan: Plan, list_type: int):
+    n = plan_stats(plan)["n_list"][list_type]
+    t = np.zeros(max(n, 1), np.int32)
+    s = np.zeros(max(n, 1), np.int32)
+    _check(load().csfmm_plan_export_list(plan.handle, list_type, _np_ptr(t), _np_ptr(s)))
+    return t[:n], s[:n]
+
+
+def plan_export_order(plan: Plan):
+    o = np.zeros(plan.N, np.int64)
+    _check(load().csfmm_plan_export_order(plan.handle, _np_ptr(o)))
+    return o
+
+
+def plan_export_proxies(plan: Plan):
+    st = plan_stats(plan)
+    P = (st["degree"] + 1) ** 2
+    px = np.zeros((st["ncells"], P, 3))
+    _check(load().csfmm_plan_export_proxies(plan.handle, _np_ptr(px)))
+    return px
+
+
+def plan_export_proxy_weights(plan: Plan, nrhs: int = 1):
+    st = plan_stats(plan)
+    P = (st["degree"] + 1) ** 2
+    wb = np.zeros((st["ncells"], nrhs, P))
+    _check(load().csfmm_plan_export_proxy_weights(plan.handle, nrhs, _np_ptr(wb)))
+    return wb
+
+
+PHASES = ("gather", "p2m", "m2m", "far", "near", "l2l", "l2p")
+
+
+def plan_enable_timing(plan: Plan, on: bool = True):
+    _check(load().csfmm_plan_enable_timing(plan.handle, 1 if on else 0))
+
+
+def plan_phase_times(plan: Plan):
+    """({phase: summed ms}, number of timed evaluations); clears the record."""
+    ms = np.zeros(len(PHASES))
+    calls = np.zeros(1, np.int64)
+    _check(load().csfmm_plan_phase_times(plan.handle, _np_ptr(ms), _np_ptr(calls)))
+    return dict(zip(PHASES, ms.tolist())), int(calls[0])
+
+
+def plan_sync(plan: Plan, stream=None):
+    _check(load().csfmm_plan_sync(plan.handle, _stream(stream)))
+
+
+def last_error() -> str:
+    return load().csfmm_last_error().decode()
+
+
+def version() -> str:
+    return load().csfmm_version().decode()

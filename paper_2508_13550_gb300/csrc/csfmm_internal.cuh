@@ -1,0 +1,233 @@
+// csfmm_internal.cuh -- shared definitions of the CUDA library behind csfmm.h.
+//
+// Layout of a plan in HBM (tree order = points sorted by face and Morton key
+// of their (xi, eta) cell coordinates, Sec. 3):
+//   x[3][N]            FP64 sorted points (SoA)
+//   perm[N]            tree position -> input index
+//   La[N][p], Lb[N][p] barycentric Lagrange values L_k(u_i), L_k(v_i) of every
+//                      point in its leaf (Sec. 4, Eq. barycentric); FP64 for
+//                      the FP64 form, FP32 for the FP32-bulk form
+//   off32[N]           float4 offset of each point from its leaf centre
+//   cells (SoA)        face, level, ia, ib, begin, end, parent, child[4],
+//                      centre[3], radius, xi_mid, eta_mid, half
+//   proxy[nc][3][P]    FP64 proxy points; proxy32[nc][3][P] FP32 offsets from
+//                      the cell centre
+//   lists              CSR by target cell for PP, PC, CP, CC
+//   m2m[2][p][p]       the two 1-D child-to-parent interpolation matrices
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/csfmm.h"
+
+namespace csfmm {
+
+constexpr int kD = 18;          // tangent table resolution: 2^kD intervals per face
+constexpr int kLMax = 17;       // deepest cell level
+constexpr int kMaxDegree = 16;  // n <= 16, p <= 17, P <= 289
+constexpr int kMaxP = kMaxDegree + 1;
+
+// Bits of the plan's device status word.
+constexpr int kStatusNotOnSphere = 1;
+constexpr int kStatusOverflow = 2;
+constexpr int kStatusInternal = 4;
+constexpr int kStatusTimeout = 8;
+
+void set_error(const char *fmt, ...);
+csfmm_status cuda_status(cudaError_t e, const char *what);
+
+#define CSFMM_CUDA(call)                                               \
+  do {                                                                 \
+    cudaError_t e__ = (call);                                          \
+    if (e__ != cudaSuccess) return csfmm::cuda_status(e__, #call);     \
+  } while (0)
+
+struct Workspace;
+
+// Device buffers are tracked so that a failed build frees everything.
+struct DeviceArena {
+  std::vector<void *> ptrs;
+  int64_t bytes = 0;
+  template <class T>
+  csfmm_status alloc(T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      set_error("cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+      return CSFMM_ERR_OUT_OF_MEMORY;
+    }
+    ptrs.push_back(q);
+    bytes += (int64_t)(count * sizeof(T));
+    *p = (T *)q;
+    return CSFMM_OK;
+  }
+  void release() {
+    for (void *p : ptrs) cudaFree(p);
+    ptrs.clear();
+    bytes = 0;
+  }
+};
+
+// Read-only view of a plan passed to kernels by value.
+struct PlanView {
+  int N, n, p, P, N0, ncells, dim, kernel_id;
+  const double *x;       // [3][N]
+  const int32_t *perm;   // [N]
+  const double *La64, *Lb64;  // [N][p]
+  const float *La32, *Lb32;   // [N][p]
+  const float4 *off32;   // [N]
+  const int32_t *cbegin, *cend, *clevel, *cface, *cparent, *cchild;
+  const double *ccentre; // [nc][3]
+  const double *cradius;
+  const double *cxmid, *cymid, *chalf;
+  const double *proxy;   // [nc][3][P]
+  const float *proxy32;  // [nc][3][P]
+  const int32_t *loff[4], *lsrc[4];
+  const double *m2m64;   // [2][p][p]: M[q][k][m] = L_k((s_m + 2q - 1)/2)
+  const float *m2m32;
+  const double *cheb;    // [p]
+  int *status;
+};
+
+struct Plan {
+  int device = 0;
+  int64_t N = 0;
+  int kernel_id = 0, n = 0, p = 0, P = 0, N0 = 0, precision = 0, dim = 1, max_nrhs = 16;
+  int use_graphs = 0;
+  double theta = 0.7;
+  int ncells = 0, nleaves = 0, nlevels = 0;
+  std::vector<int> level_begin;  // cells of level l: [level_begin[l], level_begin[l+1])
+  DeviceArena arena;
+  double *x = nullptr;
+  int32_t *perm = nullptr;
+  double *La64 = nullptr, *Lb64 = nullptr;
+  float *La32 = nullptr, *Lb32 = nullptr;
+  float4 *off32 = nullptr;
+  int32_t *leaf_of = nullptr;
+  int32_t *cface = nullptr, *clevel = nullptr, *cbegin = nullptr, *cend = nullptr,
+          *cparent = nullptr, *cchild = nullptr;
+  int64_t *cia = nullptr, *cib = nullptr;
+  double *ccentre = nullptr, *cradius = nullptr, *cxmid = nullptr, *cymid = nullptr,
+         *chalf = nullptr;
+  double *proxy = nullptr;
+  float *proxy32 = nullptr;
+  int32_t *loff[4] = {nullptr, nullptr, nullptr, nullptr};
+  int32_t *lsrc[4] = {nullptr, nullptr, nullptr, nullptr};
+  int64_t nlist[4] = {0, 0, 0, 0};
+  // target cells that own at least one entry of a list group, for launches
+  int32_t *near_targets = nullptr;  // leaves with PP or PC entries
+  int n_near_targets = 0;
+  int32_t *far_targets = nullptr;   // cells with CP or CC entries
+  int n_far_targets = 0;
+  int32_t *leaves = nullptr;        // all leaf cells
+  double *m2m64 = nullptr;
+  float *m2m32 = nullptr;
+  double *cheb = nullptr;
+  int *status = nullptr;
+  Workspace *ws = nullptr;          // default workspace
+  csfmm_stats stats{};
+  // phase timing: one set of CSFMM_NUM_PHASES + 1 events per timed evaluation
+  bool timing = false;
+  std::vector<cudaEvent_t> events;
+  int timed_calls = 0;
+  int launches = 0;                 // kernels launched by the current evaluation
+  csfmm_status mark(int phase, cudaStream_t st);  // records the event opening a phase
+
+  PlanView view() const;
+};
+
+struct Workspace {
+  Plan *plan = nullptr;
+  int max_nrhs = 0;
+  DeviceArena arena;
+  double *ws = nullptr;     // [max_nrhs][N] weights in tree order
+  double *wbar = nullptr;   // [nc][max_nrhs][P] proxy weights (FP64 form)
+  float *wbar32 = nullptr;  // [nc][max_nrhs][P] proxy weights (FP32 form)
+  double *psi = nullptr;    // [nc][max_nrhs][dim][P] proxy potentials
+  double *phi = nullptr;    // [max_nrhs][N][dim] near-field potentials, tree order
+  double *stage_w = nullptr;    // device staging for host-buffer evaluations [max_nrhs][N]
+  double *stage_out = nullptr;  // [max_nrhs][N][dim]
+  int last_nrhs = 0;
+};
+
+// Tree and list construction (tree.cu).
+csfmm_status build_tree(Plan &pl, const double *points, cudaStream_t st);
+// Evaluation passes (evaluate.cu).
+csfmm_status evaluate_impl(Plan &pl, Workspace &ws, const double *w, int nrhs, double *out,
+                           cudaStream_t st);
+csfmm_status workspace_alloc(Plan &pl, Workspace &ws, int max_nrhs);
+// Direct sum (direct.cu).
+csfmm_status direct_impl(const double *points, int64_t N, int kernel_id, const double *w,
+                         int nrhs, const int64_t *targets, int64_t ntargets, double *out,
+                         int precision, cudaStream_t st);
+
+// Host helpers shared by the library's own files.
+const double *host_tan_table();  // T[k] = tan(k (pi/2)/2^kD - pi/4), k = 0..2^kD
+int grid_for(int64_t n, int block, int max_blocks = 1 << 30);
+csfmm_status exclusive_scan_i32(const int32_t *in, int32_t *out, int n, int32_t *total_host,
+                                int32_t *tmp, cudaStream_t st);
+size_t scan_tmp_elems(int n);
+csfmm_status radix_sort_u64(uint64_t *keys, int32_t *vals, uint64_t *keys_alt, int32_t *vals_alt,
+                            int n, int begin_bit, int end_bit, int32_t *tmp, size_t tmp_elems,
+                            cudaStream_t st, bool *result_in_alt);
+size_t radix_tmp_elems(int n);
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+
+// Sphere point of face-plane coordinates (a, b) on face f: q = sqrt((1 + a*a) + b*b),
+// x_axis = +-1/q, x_u = a/q, x_v = b/q with u = (axis+1) mod 3, v = (axis+2) mod 3.
+// Evaluated with explicit round-to-nearest operations (no fused multiply-add), so the
+// result is the same as a host evaluation of the same expression.
+__device__ __forceinline__ void face_point_rn(int f, double a, double b, double *x) {
+  int ax = f >> 1;
+  double sg = (f & 1) ? -1.0 : 1.0;
+  int u = ax + 1 == 3 ? 0 : ax + 1;
+  int v = u + 1 == 3 ? 0 : u + 1;
+  double q = __dsqrt_rn(__dadd_rn(__dadd_rn(1.0, __dmul_rn(a, a)), __dmul_rn(b, b)));
+  x[ax] = __ddiv_rn(sg, q);
+  x[u] = __ddiv_rn(a, q);
+  x[v] = __ddiv_rn(b, q);
+}
+
+__device__ __forceinline__ double chord_rn(const double *x, const double *y) {
+  double dx = __dsub_rn(x[0], y[0]), dy = __dsub_rn(x[1], y[1]), dz = __dsub_rn(x[2], y[2]);
+  return __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+}
+
+// Barycentric weights of the Chebyshev points s_k = cos(k pi/n) (Sec. 4).
+__device__ __forceinline__ double bary_w(int k, int n) {
+  double w = (k & 1) ? -1.0 : 1.0;
+  return (k == 0 || k == n) ? 0.5 * w : w;
+}
+
+// L_k(u), k = 0..n, at nodes s (Eq. barycentric); L = delta if u is a node.
+__device__ __forceinline__ void lagrange_dev(int n, const double *s, double u, double *L) {
+  int hit = -1;
+  for (int k = 0; k <= n; ++k)
+    if (u == s[k]) hit = k;
+  if (hit >= 0) {
+    for (int k = 0; k <= n; ++k) L[k] = (k == hit) ? 1.0 : 0.0;
+    return;
+  }
+  double den = 0.0;
+  for (int k = 0; k <= n; ++k) {
+    L[k] = bary_w(k, n) / (u - s[k]);
+    den += L[k];
+  }
+  double inv = 1.0 / den;
+  for (int k = 0; k <= n; ++k) L[k] *= inv;
+}
+
+constexpr double kInv4Pi = 0.079577471545947667884;  // 1/(4 pi)
+constexpr double kInv2Pi = 0.15915494309189533577;   // 1/(2 pi)
+
+}  // namespace csfmm

@@ -1,0 +1,647 @@
+// evaluate.cu -- one CSFMM evaluation (Algorithm "CSFMM") on a built plan:
+//   gather     weights into tree order
+//   P2M        leaf proxy weights, Eq. (PC) right-hand side          (Sec. 6)
+//   M2M        parent proxy weights from children, Eq. (upwardpass2) (Sec. 6)
+//   far        CP and CC proxy potentials of every target cell,
+//              Eqs. (CP), (CC), accumulated as Eq. (CP_CC_accumulated) (Sec. 8)
+//   near       PP and PC potentials at the target particles, Eqs. (PP), (PC)
+//   L2L        parent proxy potentials interpolated to child proxies,
+//              Eq. (downward_2), top-down                             (Sec. 8.1)
+//   L2P        leaf proxy potentials interpolated to the particles, added to
+//              the near-field potentials, written in input order
+//
+// Two precision forms share the structure (template parameter Real):
+//   double  everything in FP64;
+//   float   kernel evaluations on pair-relative FP32 coordinates: the centre
+//           difference c_T - c_S of a (target, source) cell pair is formed in
+//           FP64 and rounded once, particles and proxies carry FP32 offsets
+//           from their cell centre; sums over one source cell in FP32, sums
+//           across source cells and the final per-target value in FP64.
+// Every target cell or leaf is owned by one thread block, so no atomics are
+// used and results are deterministic.
+#include <math.h>
+
+#include "csfmm_internal.cuh"
+
+namespace csfmm {
+
+namespace {
+
+constexpr int kRB = 4;  // right-hand sides per kernel pass
+
+template <typename Real>
+__device__ __forceinline__ const Real *La_of(const PlanView &v);
+template <>
+__device__ __forceinline__ const double *La_of<double>(const PlanView &v) { return v.La64; }
+template <>
+__device__ __forceinline__ const float *La_of<float>(const PlanView &v) { return v.La32; }
+template <typename Real>
+__device__ __forceinline__ const Real *Lb_of(const PlanView &v);
+template <>
+__device__ __forceinline__ const double *Lb_of<double>(const PlanView &v) { return v.Lb64; }
+template <>
+__device__ __forceinline__ const float *Lb_of<float>(const PlanView &v) { return v.Lb32; }
+template <typename Real>
+__device__ __forceinline__ const Real *M_of(const PlanView &v);
+template <>
+__device__ __forceinline__ const double *M_of<double>(const PlanView &v) { return v.m2m64; }
+template <>
+__device__ __forceinline__ const float *M_of<float>(const PlanView &v) { return v.m2m32; }
+
+__device__ __forceinline__ float fast_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double fast_rsqrt(double x) { return rsqrt(x); }
+__device__ __forceinline__ float fast_log2(float x) { return __log2f(x); }
+__device__ __forceinline__ double fast_log2(double x) { return log2(x); }
+__device__ __forceinline__ float fast_rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double fast_rcp(double x) { return 1.0 / x; }
+
+// ---------------------------------------------------------------------------
+// Kernel sums.  For a fixed target x and a tile of sources y_j with weights
+// w_j and r_j = x - y_j (d2 = |r_j|^2), the kernel factor f_j is computed once
+// per source and shared by all right-hand sides:
+//   Laplace      f = log2(d2);  a += w f, sw += w;  value = -(ln 2/(4 pi)) (a - sw)
+//                (since -(1/4pi) ln(d2/2) = -(ln2/4pi)(log2 d2 - 1))
+//   Newtonian    f = 1/sqrt(d2);  a += w f
+//   Biot-Savart  f = 1/d2;  a += w f r (3 components);  value = (1/(2 pi)) x cross a
+//                (since x cross y = -x cross r and 1 - x.y = d2/2)
+//   K = 1        a += w
+// ---------------------------------------------------------------------------
+template <int KID, typename Real>
+struct KFac {
+  Real f, rx, ry, rz;
+  __device__ __forceinline__ KFac(Real x, Real y, Real z) : rx(x), ry(y), rz(z) {
+    Real d2 = x * x + y * y + z * z;
+    if constexpr (KID == CSFMM_KERNEL_LAPLACE) f = fast_log2(d2);
+    else if constexpr (KID == CSFMM_KERNEL_NEWTON) f = fast_rsqrt(d2);
+    else if constexpr (KID == CSFMM_KERNEL_BIOT_SAVART) f = fast_rcp(d2);
+    else f = 1;
+  }
+};
+
+template <int KID, typename Real>
+struct Acc {
+  Real a0 = 0, a1 = 0, a2 = 0, sw = 0;
+  __device__ __forceinline__ void add(const KFac<KID, Real> &k, Real w) {
+    if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
+      a0 += w * k.f;
+      sw += w;
+    } else if constexpr (KID == CSFMM_KERNEL_BIOT_SAVART) {
+      Real q = w * k.f;
+      a0 += q * k.rx;
+      a1 += q * k.ry;
+      a2 += q * k.rz;
+    } else if constexpr (KID == CSFMM_KERNEL_NEWTON) {
+      a0 += w * k.f;
+    } else {
+      a0 += w;
+    }
+  }
+  // Adds the tile's kernel sum into out[0..dim) (FP64); x = target position.
+  __device__ __forceinline__ void flush(double *out, double x0, double x1, double x2) const {
+    if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
+      out[0] += -(0.69314718055994530942 * kInv4Pi) * ((double)a0 - (double)sw);
+    } else if constexpr (KID == CSFMM_KERNEL_BIOT_SAVART) {
+      double b0 = a0, b1 = a1, b2 = a2;
+      out[0] += kInv2Pi * (x1 * b2 - x2 * b1);
+      out[1] += kInv2Pi * (x2 * b0 - x0 * b2);
+      out[2] += kInv2Pi * (x0 * b1 - x1 * b0);
+    } else {
+      out[0] += (double)a0;
+    }
+  }
+};
+
+template <int KID>
+constexpr int kdim() {
+  return KID == CSFMM_KERNEL_BIOT_SAVART ? 3 : 1;
+}
+
+// ---------------------------------------------------------------------------
+// gather: ws[r][i] = w[r][perm[i]]
+// ---------------------------------------------------------------------------
+__global__ void gather_kernel(const int32_t *perm, const double *w, double *ws, int N, int nrhs,
+                              int ld_ws) {
+  int64_t total = (int64_t)N * nrhs;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    int r = (int)(q / N);
+    int i = (int)(q - (int64_t)r * N);
+    ws[(int64_t)r * ld_ws + i] = w[(int64_t)r * N + perm[i]];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// P2M: for leaf c, wbar[c][r][k1 p + k2] = sum_j La[j][k1] Lb[j][k2] w_r[j].
+// One block per leaf, threads over proxies.
+// ---------------------------------------------------------------------------
+template <typename Real>
+__global__ void p2m_kernel(PlanView v, const int32_t *leaves, const double *ws, int ldw,
+                           int r0, int nr, Real *wbar, int ldr) {
+  constexpr int CH = 32;
+  __shared__ Real sLa[CH * kMaxP], sLb[CH * kMaxP], sw[kRB * CH];
+  const int c = leaves[blockIdx.x];
+  const int b = v.cbegin[c], e = v.cend[c], p = v.p, P = v.P;
+  const Real *La = La_of<Real>(v), *Lb = Lb_of<Real>(v);
+  for (int k0 = 0; k0 < P; k0 += blockDim.x) {
+    int k = k0 + threadIdx.x;
+    int k1 = k / p, k2 = k - k1 * p;
+    Real acc[kRB];
+#pragma unroll
+    for (int q = 0; q < kRB; ++q) acc[q] = 0;
+    for (int j0 = b; j0 < e; j0 += CH) {
+      int nj = min(CH, e - j0);
+      __syncthreads();
+      for (int t = threadIdx.x; t < nj * p; t += blockDim.x) {
+        sLa[t] = La[(int64_t)j0 * p + t];
+        sLb[t] = Lb[(int64_t)j0 * p + t];
+      }
+      for (int t = threadIdx.x; t < kRB * CH; t += blockDim.x) {
+        int q = t / CH, j = t - q * CH;
+        sw[t] = (q < nr && j < nj) ? (Real)ws[(int64_t)(r0 + q) * ldw + j0 + j] : (Real)0;
+      }
+      __syncthreads();
+      if (k < P) {
+        for (int j = 0; j < nj; ++j) {
+          Real l = sLa[j * p + k1] * sLb[j * p + k2];
+#pragma unroll
+          for (int q = 0; q < kRB; ++q) acc[q] += l * sw[q * CH + j];
+        }
+      }
+    }
+    if (k < P) {
+      for (int q = 0; q < nr; ++q) wbar[((int64_t)c * ldr + r0 + q) * P + k] = acc[q];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// M2M at one level: parent wbar = sum_c (M_qa (x) M_qb) child wbar.
+// One block per cell of the level (leaves exit), threads over proxies.
+// ---------------------------------------------------------------------------
+template <typename Real>
+__global__ void m2m_kernel(PlanView v, int cell0, int r0, int nr, Real *wbar, int ldr) {
+  __shared__ Real sM[2 * kMaxP * kMaxP];
+  __shared__ Real sw[kMaxP * kMaxP], st[kMaxP * kMaxP];
+  const int c = cell0 + blockIdx.x;
+  const int p = v.p, P = v.P;
+  const int32_t *ch = v.cchild + 4 * c;
+  if (ch[0] < 0 && ch[1] < 0 && ch[2] < 0 && ch[3] < 0) return;
+  const Real *M = M_of<Real>(v);
+  for (int t = threadIdx.x; t < 2 * p * p; t += blockDim.x) sM[t] = M[t];
+  for (int r = r0; r < r0 + nr; ++r) {
+    Real acc[(kMaxP * kMaxP + 127) / 128];
+    const int nper = (P + blockDim.x - 1) / blockDim.x;
+    for (int u = 0; u < nper; ++u) acc[u] = 0;
+    for (int q = 0; q < 4; ++q) {
+      int cc = ch[q];
+      if (cc < 0) continue;
+      int qa = q & 1, qb = q >> 1;
+      __syncthreads();
+      for (int t = threadIdx.x; t < P; t += blockDim.x) sw[t] = wbar[((int64_t)cc * ldr + r) * P + t];
+      __syncthreads();
+      // st[m1][k2] = sum_m2 M[qb][k2][m2] w[m1][m2]
+      for (int t = threadIdx.x; t < P; t += blockDim.x) {
+        int m1 = t / p, k2 = t - m1 * p;
+        const Real *Mr = sM + (qb * p + k2) * p;
+        Real s = 0;
+        for (int m2 = 0; m2 < p; ++m2) s += Mr[m2] * sw[m1 * p + m2];
+        st[t] = s;
+      }
+      __syncthreads();
+      // acc[k1][k2] += sum_m1 M[qa][k1][m1] st[m1][k2]
+      for (int u = 0, t = threadIdx.x; t < P; ++u, t += blockDim.x) {
+        int k1 = t / p, k2 = t - k1 * p;
+        const Real *Mr = sM + (qa * p + k1) * p;
+        Real s = 0;
+        for (int m1 = 0; m1 < p; ++m1) s += Mr[m1] * st[m1 * p + k2];
+        acc[u] += s;
+      }
+    }
+    for (int u = 0, t = threadIdx.x; t < P; ++u, t += blockDim.x)
+      wbar[((int64_t)c * ldr + r) * P + t] = acc[u];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// L2L at one level: child psi += (M_qa (x) M_qb)^T parent psi.
+// ---------------------------------------------------------------------------
+template <typename Real>
+__global__ void l2l_kernel(PlanView v, int cell0, int r0, int nr, int dim, Real *psi, int ldr) {
+  __shared__ Real sM[2 * kMaxP * kMaxP];
+  __shared__ Real sp[kMaxP * kMaxP], st[kMaxP * kMaxP];
+  const int c = cell0 + blockIdx.x;
+  const int p = v.p, P = v.P;
+  const int32_t *ch = v.cchild + 4 * c;
+  if (ch[0] < 0 && ch[1] < 0 && ch[2] < 0 && ch[3] < 0) return;
+  const Real *M = M_of<Real>(v);
+  for (int t = threadIdx.x; t < 2 * p * p; t += blockDim.x) sM[t] = M[t];
+  for (int r = r0; r < r0 + nr; ++r)
+    for (int d = 0; d < dim; ++d) {
+      __syncthreads();
+      for (int t = threadIdx.x; t < P; t += blockDim.x)
+        sp[t] = psi[(((int64_t)c * ldr + r) * dim + d) * P + t];
+      for (int q = 0; q < 4; ++q) {
+        int cc = ch[q];
+        if (cc < 0) continue;
+        int qa = q & 1, qb = q >> 1;
+        __syncthreads();
+        // st[m1][n2] = sum_m2 psi[m1][m2] M[qb][m2][n2]
+        for (int t = threadIdx.x; t < P; t += blockDim.x) {
+          int m1 = t / p, n2 = t - m1 * p;
+          Real s = 0;
+          for (int m2 = 0; m2 < p; ++m2) s += sp[m1 * p + m2] * sM[(qb * p + m2) * p + n2];
+          st[t] = s;
+        }
+        __syncthreads();
+        Real *dst = psi + (((int64_t)cc * ldr + r) * dim + d) * P;
+        for (int t = threadIdx.x; t < P; t += blockDim.x) {
+          int n1 = t / p, n2 = t - n1 * p;
+          Real s = 0;
+          for (int m1 = 0; m1 < p; ++m1) s += sM[(qa * p + m1) * p + n1] * st[m1 * p + n2];
+          dst[t] += s;
+        }
+      }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// far: psi[c][r][d][m] = sum over CP sources (particles) and CC sources
+// (proxies) of K(t_m, y) w.  One block per cell (all cells; cells without
+// CP/CC entries write zeros), one thread per target proxy m.
+// ---------------------------------------------------------------------------
+constexpr int kFarTile = 128;
+
+template <int KID, typename Real, int NR>
+__global__ void far_kernel(PlanView v, const double *ws, int ldw, const Real *wbar, int ldr,
+                           int r0, Real *psi) {
+  constexpr int nr = NR;
+  // psi[c][r][d][m] with rhs stride ldr
+  constexpr int DIM = kdim<KID>();
+  __shared__ Real sx[kFarTile], sy[kFarTile], sz[kFarTile], sw[kRB * kFarTile];
+  const int c = blockIdx.x;
+  const int P = v.P;
+  const int m = threadIdx.x;
+  const bool active = m < P;
+  double out[NR][DIM];
+#pragma unroll
+  for (int q = 0; q < NR; ++q)
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) out[q][d] = 0.0;
+  // target proxy: absolute (FP64 form) or offset from the cell centre (FP32 form)
+  const int64_t po = (int64_t)c * 3 * P;
+  double tx = 0, ty = 0, tz = 0;  // absolute target position (for Biot-Savart)
+  Real ox = 0, oy = 0, oz = 0;    // offset from centre
+  if (active) {
+    tx = v.proxy[po + m];
+    ty = v.proxy[po + P + m];
+    tz = v.proxy[po + 2 * P + m];
+    ox = (Real)v.proxy32[po + m];
+    oy = (Real)v.proxy32[po + P + m];
+    oz = (Real)v.proxy32[po + 2 * P + m];
+  }
+  const double cTx = v.ccentre[3 * c], cTy = v.ccentre[3 * c + 1], cTz = v.ccentre[3 * c + 2];
+  for (int pass = 0; pass < 2; ++pass) {
+    const int type = pass == 0 ? CSFMM_LIST_CP : CSFMM_LIST_CC;
+    const int e0 = v.loff[type][c], e1 = v.loff[type][c + 1];
+    for (int e = e0; e < e1; ++e) {
+      const int s = v.lsrc[type][e];
+      // pair-relative target coordinates (FP32 form): t = offset + (c_T - c_S)
+      Real rx0, ry0, rz0;
+      if constexpr (sizeof(Real) == 4) {
+        rx0 = ox + (Real)(cTx - v.ccentre[3 * s]);
+        ry0 = oy + (Real)(cTy - v.ccentre[3 * s + 1]);
+        rz0 = oz + (Real)(cTz - v.ccentre[3 * s + 2]);
+      } else {
+        rx0 = tx;
+        ry0 = ty;
+        rz0 = tz;
+      }
+      const int nsrc = (type == CSFMM_LIST_CP) ? v.cend[s] - v.cbegin[s] : P;
+      for (int j0 = 0; j0 < nsrc; j0 += kFarTile) {
+        const int nj = min(kFarTile, nsrc - j0);
+        __syncthreads();
+        for (int t = threadIdx.x; t < nj; t += blockDim.x) {
+          if (type == CSFMM_LIST_CP) {
+            const int j = v.cbegin[s] + j0 + t;
+            if constexpr (sizeof(Real) == 4) {
+              float4 o = v.off32[j];
+              sx[t] = o.x; sy[t] = o.y; sz[t] = o.z;
+            } else {
+              sx[t] = v.x[j]; sy[t] = v.x[v.N + j]; sz[t] = v.x[2 * (int64_t)v.N + j];
+            }
+#pragma unroll
+            for (int q = 0; q < NR; ++q) sw[q * kFarTile + t] = (Real)ws[(int64_t)(r0 + q) * ldw + j];
+          } else {
+            const int64_t so = (int64_t)s * 3 * P;
+            const int k = j0 + t;
+            if constexpr (sizeof(Real) == 4) {
+              sx[t] = v.proxy32[so + k]; sy[t] = v.proxy32[so + P + k]; sz[t] = v.proxy32[so + 2 * P + k];
+            } else {
+              sx[t] = v.proxy[so + k]; sy[t] = v.proxy[so + P + k]; sz[t] = v.proxy[so + 2 * P + k];
+            }
+#pragma unroll
+            for (int q = 0; q < NR; ++q) sw[q * kFarTile + t] = wbar[((int64_t)s * ldr + r0 + q) * P + k];
+          }
+        }
+        __syncthreads();
+        if (active) {
+          Acc<KID, Real> acc[NR];
+          for (int j = 0; j < nj; ++j) {
+            KFac<KID, Real> kf(rx0 - sx[j], ry0 - sy[j], rz0 - sz[j]);
+#pragma unroll
+            for (int q = 0; q < NR; ++q) acc[q].add(kf, sw[q * kFarTile + j]);
+          }
+#pragma unroll
+          for (int q = 0; q < NR; ++q) acc[q].flush(out[q], tx, ty, tz);
+        }
+      }
+    }
+  }
+  if (active) {
+    for (int q = 0; q < nr; ++q)
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) psi[(((int64_t)c * ldr + r0 + q) * DIM + d) * P + m] = (Real)out[q][d];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// near: phi[r][i][d] = sum over PP sources (particles, i = j omitted) and PC
+// sources (proxies) of K(x_i, y) w.  One block per leaf, one thread per
+// target particle (looping over chunks of the block size).
+// ---------------------------------------------------------------------------
+constexpr int kNearTile = 128;
+
+template <int KID, typename Real, int NR>
+__global__ void near_kernel(PlanView v, const int32_t *leaves, const double *ws, int ldw,
+                            const Real *wbar, int ldr, int r0, double *phi) {
+  constexpr int nr = NR;
+  constexpr int DIM = kdim<KID>();
+  __shared__ Real sx[kNearTile], sy[kNearTile], sz[kNearTile], sw[kRB * kNearTile];
+  const int c = leaves[blockIdx.x];
+  const int b = v.cbegin[c], e = v.cend[c];
+  const int P = v.P;
+  const double cTx = v.ccentre[3 * c], cTy = v.ccentre[3 * c + 1], cTz = v.ccentre[3 * c + 2];
+  for (int i0 = b; i0 < e; i0 += blockDim.x) {
+    const int i = i0 + threadIdx.x;
+    const bool active = i < e;
+    double out[NR][DIM];
+#pragma unroll
+    for (int q = 0; q < NR; ++q)
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) out[q][d] = 0.0;
+    double tx = 0, ty = 0, tz = 0;
+    Real ox = 0, oy = 0, oz = 0;
+    if (active) {
+      tx = v.x[i];
+      ty = v.x[v.N + i];
+      tz = v.x[2 * (int64_t)v.N + i];
+      float4 o = v.off32[i];
+      ox = o.x; oy = o.y; oz = o.z;
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+      const int type = pass == 0 ? CSFMM_LIST_PP : CSFMM_LIST_PC;
+      const int e0 = v.loff[type][c], e1 = v.loff[type][c + 1];
+      for (int ee = e0; ee < e1; ++ee) {
+        const int s = v.lsrc[type][ee];
+        Real rx0, ry0, rz0;
+        if constexpr (sizeof(Real) == 4) {
+          rx0 = ox + (Real)(cTx - v.ccentre[3 * s]);
+          ry0 = oy + (Real)(cTy - v.ccentre[3 * s + 1]);
+          rz0 = oz + (Real)(cTz - v.ccentre[3 * s + 2]);
+        } else {
+          rx0 = tx;
+          ry0 = ty;
+          rz0 = tz;
+        }
+        const bool pp = type == CSFMM_LIST_PP;
+        const int sb = pp ? v.cbegin[s] : 0;
+        const int nsrc = pp ? v.cend[s] - v.cbegin[s] : P;
+        const int self = (pp && s == c) ? i - sb : -1;  // index of x_i among the sources
+        for (int j0 = 0; j0 < nsrc; j0 += kNearTile) {
+          const int nj = min(kNearTile, nsrc - j0);
+          __syncthreads();
+          for (int t = threadIdx.x; t < nj; t += blockDim.x) {
+            if (pp) {
+              const int j = sb + j0 + t;
+              if constexpr (sizeof(Real) == 4) {
+                float4 o = v.off32[j];
+                sx[t] = o.x; sy[t] = o.y; sz[t] = o.z;
+              } else {
+                sx[t] = v.x[j]; sy[t] = v.x[v.N + j]; sz[t] = v.x[2 * (int64_t)v.N + j];
+              }
+#pragma unroll
+              for (int q = 0; q < NR; ++q) sw[q * kNearTile + t] = (Real)ws[(int64_t)(r0 + q) * ldw + j];
+            } else {
+              const int64_t so = (int64_t)s * 3 * P;
+              const int k = j0 + t;
+              if constexpr (sizeof(Real) == 4) {
+                sx[t] = v.proxy32[so + k]; sy[t] = v.proxy32[so + P + k]; sz[t] = v.proxy32[so + 2 * P + k];
+              } else {
+                sx[t] = v.proxy[so + k]; sy[t] = v.proxy[so + P + k]; sz[t] = v.proxy[so + 2 * P + k];
+              }
+#pragma unroll
+              for (int q = 0; q < NR; ++q) sw[q * kNearTile + t] = wbar[((int64_t)s * ldr + r0 + q) * P + k];
+            }
+          }
+          __syncthreads();
+          if (active) {
+            Acc<KID, Real> acc[NR];
+            const int skip = self - j0;  // in [0, nj) only on the tile holding x_i
+            for (int j = 0; j < nj; ++j) {
+              if (j == skip) continue;
+              KFac<KID, Real> kf(rx0 - sx[j], ry0 - sy[j], rz0 - sz[j]);
+#pragma unroll
+              for (int q = 0; q < NR; ++q) acc[q].add(kf, sw[q * kNearTile + j]);
+            }
+#pragma unroll
+            for (int q = 0; q < NR; ++q) acc[q].flush(out[q], tx, ty, tz);
+          }
+        }
+      }
+    }
+    if (active) {
+      for (int q = 0; q < nr; ++q)
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) phi[((int64_t)(r0 + q) * v.N + i) * DIM + d] = out[q][d];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// L2P + finalize: out[r][perm[i]][d] = phi[r][i][d] + sum_m psi_leaf[m] La[i][m1] Lb[i][m2].
+// ---------------------------------------------------------------------------
+template <typename Real>
+__global__ void l2p_kernel(PlanView v, const int32_t *leaves, const Real *psi, int ldr, int r0,
+                           int nr, int dim, const double *phi, double *out) {
+  __shared__ Real sp[kMaxP * kMaxP];
+  const int c = leaves[blockIdx.x];
+  const int b = v.cbegin[c], e = v.cend[c], p = v.p, P = v.P;
+  const Real *La = La_of<Real>(v), *Lb = Lb_of<Real>(v);
+  for (int r = r0; r < r0 + nr; ++r)
+    for (int d = 0; d < dim; ++d) {
+      __syncthreads();
+      for (int t = threadIdx.x; t < P; t += blockDim.x)
+        sp[t] = psi[(((int64_t)c * ldr + r) * dim + d) * P + t];
+      __syncthreads();
+      for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
+        const Real *la = La + (int64_t)i * p, *lb = Lb + (int64_t)i * p;
+        Real lbv[kMaxP];
+        for (int m2 = 0; m2 < p; ++m2) lbv[m2] = lb[m2];
+        Real acc = 0;
+        for (int m1 = 0; m1 < p; ++m1) {
+          Real s = 0;
+          for (int m2 = 0; m2 < p; ++m2) s += sp[m1 * p + m2] * lbv[m2];
+          acc += la[m1] * s;
+        }
+        const int64_t oi = ((int64_t)r * v.N + i) * dim + d;
+        out[((int64_t)r * v.N + v.perm[i]) * dim + d] = phi[oi] + (double)acc;
+      }
+    }
+}
+
+template <int KID, typename Real>
+void launch_far(const PlanView &v, Plan &pl, Workspace &W, int nr, int r0, int tb_prox,
+                Real *wbar, Real *psi, cudaStream_t st) {
+  const int N = (int)pl.N, ldr = W.max_nrhs;
+  switch (nr) {
+    case 1: far_kernel<KID, Real, 1><<<pl.ncells, tb_prox, 0, st>>>(v, W.ws, N, wbar, ldr, r0, psi); break;
+    case 2: far_kernel<KID, Real, 2><<<pl.ncells, tb_prox, 0, st>>>(v, W.ws, N, wbar, ldr, r0, psi); break;
+    case 3: far_kernel<KID, Real, 3><<<pl.ncells, tb_prox, 0, st>>>(v, W.ws, N, wbar, ldr, r0, psi); break;
+    default: far_kernel<KID, Real, 4><<<pl.ncells, tb_prox, 0, st>>>(v, W.ws, N, wbar, ldr, r0, psi); break;
+  }
+}
+
+template <int KID, typename Real>
+void launch_near(const PlanView &v, Plan &pl, Workspace &W, int nr, int r0, const Real *wbar,
+                 cudaStream_t st) {
+  const int N = (int)pl.N, ldr = W.max_nrhs;
+  switch (nr) {
+    case 1: near_kernel<KID, Real, 1><<<pl.nleaves, kNearTile, 0, st>>>(v, pl.leaves, W.ws, N, wbar, ldr, r0, W.phi); break;
+    case 2: near_kernel<KID, Real, 2><<<pl.nleaves, kNearTile, 0, st>>>(v, pl.leaves, W.ws, N, wbar, ldr, r0, W.phi); break;
+    case 3: near_kernel<KID, Real, 3><<<pl.nleaves, kNearTile, 0, st>>>(v, pl.leaves, W.ws, N, wbar, ldr, r0, W.phi); break;
+    default: near_kernel<KID, Real, 4><<<pl.nleaves, kNearTile, 0, st>>>(v, pl.leaves, W.ws, N, wbar, ldr, r0, W.phi); break;
+  }
+}
+
+template <int KID, typename Real>
+csfmm_status run_passes(Plan &pl, Workspace &W, const double *w, int nrhs, double *out,
+                        cudaStream_t st) {
+  PlanView v = pl.view();
+  const int N = (int)pl.N, P = pl.P, dim = pl.dim;
+  const int ldr = W.max_nrhs;  // rhs stride of wbar / psi
+  Real *wbar;
+  if constexpr (sizeof(Real) == 4) wbar = W.wbar32; else wbar = W.wbar;
+  Real *psi = reinterpret_cast<Real *>(W.psi);
+  pl.launches = 0;
+#define CSFMM_MARK(ph)                              \
+  do {                                              \
+    csfmm_status s__ = pl.mark(ph, st);             \
+    if (s__ != CSFMM_OK) return s__;                \
+  } while (0)
+  CSFMM_MARK(CSFMM_PHASE_GATHER);
+  gather_kernel<<<grid_for((int64_t)N * nrhs, 256, 152 * 32), 256, 0, st>>>(pl.perm, w, W.ws, N,
+                                                                             nrhs, N);
+  ++pl.launches;
+  const int tb_prox = ((P + 31) / 32) * 32;
+  CSFMM_MARK(CSFMM_PHASE_P2M);
+  for (int r0 = 0; r0 < nrhs; r0 += kRB) {
+    int nr = min(kRB, nrhs - r0);
+    p2m_kernel<Real><<<pl.nleaves, 128, 0, st>>>(v, pl.leaves, W.ws, N, r0, nr, wbar, ldr);
+    ++pl.launches;
+  }
+  CSFMM_MARK(CSFMM_PHASE_M2M);
+  for (int l = pl.nlevels - 2; l >= 0; --l) {
+    int c0 = pl.level_begin[l], nlev = pl.level_begin[l + 1] - c0;
+    m2m_kernel<Real><<<nlev, 128, 0, st>>>(v, c0, 0, nrhs, wbar, ldr);
+    ++pl.launches;
+  }
+  CSFMM_MARK(CSFMM_PHASE_FAR);
+  for (int r0 = 0; r0 < nrhs; r0 += kRB) {
+    int nr = min(kRB, nrhs - r0);
+    launch_far<KID, Real>(v, pl, W, nr, r0, tb_prox, wbar, psi, st);
+    ++pl.launches;
+  }
+  CSFMM_MARK(CSFMM_PHASE_NEAR);
+  for (int r0 = 0; r0 < nrhs; r0 += kRB) {
+    int nr = min(kRB, nrhs - r0);
+    launch_near<KID, Real>(v, pl, W, nr, r0, wbar, st);
+    ++pl.launches;
+  }
+  CSFMM_MARK(CSFMM_PHASE_L2L);
+  for (int l = 0; l + 1 < pl.nlevels; ++l) {
+    int c0 = pl.level_begin[l], nlev = pl.level_begin[l + 1] - c0;
+    l2l_kernel<Real><<<nlev, 128, 0, st>>>(v, c0, 0, nrhs, dim, psi, ldr);
+    ++pl.launches;
+  }
+  CSFMM_MARK(CSFMM_PHASE_L2P);
+  l2p_kernel<Real><<<pl.nleaves, 128, 0, st>>>(v, pl.leaves, psi, ldr, 0, nrhs, dim, W.phi, out);
+  ++pl.launches;
+  CSFMM_MARK(CSFMM_NUM_PHASES);
+#undef CSFMM_MARK
+  CSFMM_CUDA(cudaGetLastError());
+  pl.stats.launches_per_evaluate = pl.launches;
+  return CSFMM_OK;
+}
+
+template <typename Real>
+csfmm_status dispatch_kernel(Plan &pl, Workspace &W, const double *w, int nrhs, double *out,
+                             cudaStream_t st) {
+  switch (pl.kernel_id) {
+    case CSFMM_KERNEL_LAPLACE: return run_passes<CSFMM_KERNEL_LAPLACE, Real>(pl, W, w, nrhs, out, st);
+    case CSFMM_KERNEL_BIOT_SAVART: return run_passes<CSFMM_KERNEL_BIOT_SAVART, Real>(pl, W, w, nrhs, out, st);
+    case CSFMM_KERNEL_NEWTON: return run_passes<CSFMM_KERNEL_NEWTON, Real>(pl, W, w, nrhs, out, st);
+    case CSFMM_KERNEL_ONE: return run_passes<CSFMM_KERNEL_ONE, Real>(pl, W, w, nrhs, out, st);
+  }
+  set_error("unknown kernel id %d", pl.kernel_id);
+  return CSFMM_ERR_INVALID_ARG;
+}
+
+}  // namespace
+
+csfmm_status Plan::mark(int phase, cudaStream_t st) {
+  if (!timing) return CSFMM_OK;
+  if (phase == 0) {
+    // a new timed evaluation: CSFMM_NUM_PHASES + 1 fresh events
+    for (int k = 0; k <= CSFMM_NUM_PHASES; ++k) {
+      cudaEvent_t e;
+      CSFMM_CUDA(cudaEventCreate(&e));
+      events.push_back(e);
+    }
+    ++timed_calls;
+  }
+  cudaEvent_t e = events[events.size() - (CSFMM_NUM_PHASES + 1) + phase];
+  CSFMM_CUDA(cudaEventRecord(e, st));
+  return CSFMM_OK;
+}
+
+csfmm_status workspace_alloc(Plan &pl, Workspace &W, int max_nrhs) {
+  W.plan = &pl;
+  W.max_nrhs = max_nrhs;
+  const size_t N = (size_t)pl.N, nc = (size_t)pl.ncells, P = (size_t)pl.P, R = (size_t)max_nrhs;
+  csfmm_status s;
+  if ((s = W.arena.alloc(&W.ws, R * N)) != CSFMM_OK) return s;
+  if (pl.precision == CSFMM_FP64) {
+    if ((s = W.arena.alloc(&W.wbar, nc * R * P)) != CSFMM_OK) return s;
+    if ((s = W.arena.alloc(&W.psi, nc * R * pl.dim * P)) != CSFMM_OK) return s;
+  } else {
+    if ((s = W.arena.alloc(&W.wbar32, nc * R * P)) != CSFMM_OK) return s;
+    // FP32 proxy potentials live in the psi buffer (half of its FP64 size is used)
+    if ((s = W.arena.alloc(&W.psi, (nc * R * pl.dim * P + 1) / 2)) != CSFMM_OK) return s;
+  }
+  if ((s = W.arena.alloc(&W.phi, R * N * pl.dim)) != CSFMM_OK) return s;
+  return CSFMM_OK;
+}
+
+// Evaluates nrhs <= W.max_nrhs right-hand sides.
+csfmm_status evaluate_impl(Plan &pl, Workspace &W, const double *w, int nrhs, double *out,
+                           cudaStream_t st) {
+  if (nrhs > W.max_nrhs) {
+    set_error("nrhs %d exceeds the workspace capacity %d", nrhs, W.max_nrhs);
+    return CSFMM_ERR_INVALID_ARG;
+  }
+  W.last_nrhs = nrhs;
+  if (pl.precision == CSFMM_FP64) return dispatch_kernel<double>(pl, W, w, nrhs, out, st);
+  return dispatch_kernel<float>(pl, W, w, nrhs, out, st);
+}
+
+}  // namespace csfmm
