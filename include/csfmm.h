@@ -146,6 +146,32 @@ csfmm_status csfmm_workspace_destroy(csfmm_workspace ws);
 csfmm_status csfmm_evaluate_ws(csfmm_plan plan, csfmm_workspace ws, const double *weights,
                                int nrhs, double *out, void *stream);
 
+/* Evaluation that allocates no device memory.  The paper has no counterpart:
+ * this entry point exists for callers that must not call cudaMalloc when they
+ * evaluate -- a serving loop whose free device memory is all promised to its
+ * admission budget, or a host application whose device memory belongs to its
+ * own allocator -- and that need a second evaluation of a plan while the
+ * plan's workspace is busy.  It computes the same result with the same
+ * kernels as csfmm_evaluate, but its scratch (weights in tree order, proxy
+ * weights, proxy potentials, near-field potentials) comes from one static
+ * device array of CSFMM_STATIC_SCRATCH_BYTES that every GPU loading the
+ * library keeps until the process exits.
+ *   plan    a plan of the current device (built earlier, e.g. at start-up)
+ *   weights device [nrhs][N]; out device [nrhs][N][dim]; 1 <= nrhs <= 64
+ * Needs 8 N nrhs (1 + dim) + ncells nrhs P (1 + dim) s bytes of scratch
+ * (s = 8 for CSFMM_FP64, 4 for CSFMM_FP32_BULK; each part rounded up to 256
+ * bytes); larger requests fail with CSFMM_ERR_INVALID_ARG and a message that
+ * states the size.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress with that device current); make that first
+ * call before any stream capture.  Every call shares the one array, which
+ * keeps the last call's contents: calls that overlap on the GPU (other
+ * streams, other threads, other plans) race, so serialise them.  Nothing in
+ * the array needs clearing between calls (every part is written before it
+ * is read).  Asynchronous on stream. */
+#define CSFMM_STATIC_SCRATCH_BYTES (64u << 20)
+csfmm_status csfmm_evaluate_static(csfmm_plan plan, const double *weights, int nrhs, double *out,
+                                   void *stream);
+
 /* Direct sum of Eq. (nbodysum) with the i = j term omitted.  Asynchronous.
  *   points  device [N][3]; weights device [nrhs][N]; out device [nrhs][N][dim]
  *   precision CSFMM_FP64 (per-target compensated FP64 sums) or CSFMM_FP32_BULK

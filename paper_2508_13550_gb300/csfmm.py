@@ -71,6 +71,7 @@ _SIGS = {
                           ctypes.POINTER(Options), _VP, ctypes.POINTER(_VP)],
     "csfmm_evaluate": [_VP, _VP, ctypes.c_int, _VP, _VP],
     "csfmm_evaluate_host": [_VP, _VP, ctypes.c_int, _VP, _VP],
+    "csfmm_evaluate_static": [_VP, _VP, ctypes.c_int, _VP, _VP],
     "csfmm_workspace_create": [_VP, ctypes.c_int, ctypes.POINTER(_VP)],
     "csfmm_workspace_destroy": [_VP],
     "csfmm_evaluate_ws": [_VP, _VP, _VP, ctypes.c_int, _VP, _VP],
@@ -186,6 +187,23 @@ def evaluate(plan: Plan, weights, out=None, stream=None):
         out = torch.empty((nrhs, plan.N, plan.dim), dtype=torch.float64, device=w.device)
     _check(load().csfmm_evaluate(plan.handle, _dev(w, torch.float64), nrhs,
                                  _dev(out, torch.float64), _stream(stream)))
+    return out
+
+
+STATIC_SCRATCH_BYTES = 64 << 20
+
+
+def evaluate_static(plan: Plan, weights, out=None, stream=None):
+    """csfmm_evaluate_static: same result as evaluate(), with the library's
+    static device scratch instead of the plan's workspace (allocates no device
+    memory inside the library; `out` may be passed preallocated)."""
+    import torch
+    w = weights if weights.dim() == 2 else weights.unsqueeze(0)
+    nrhs = w.shape[0]
+    if out is None:
+        out = torch.empty((nrhs, plan.N, plan.dim), dtype=torch.float64, device=w.device)
+    _check(load().csfmm_evaluate_static(plan.handle, _dev(w, torch.float64), nrhs,
+                                        _dev(out, torch.float64), _stream(stream)))
     return out
 
 

@@ -157,6 +157,15 @@ struct Workspace {
   int last_nrhs = 0;
 };
 
+}  // namespace csfmm
+
+// The opaque handle of include/csfmm.h wraps one Plan.
+struct csfmm_plan_s {
+  csfmm::Plan impl;
+};
+
+namespace csfmm {
+
 // Tree and list construction (tree.cu).
 csfmm_status build_tree(Plan &pl, const double *points, cudaStream_t st);
 // Evaluation passes (evaluate.cu).
