@@ -35,6 +35,10 @@ WORKLOADS = {
                       desc="Newtonian 1/sqrt(2(1-x.y)), cubed sphere 6x1024^2 = 6,291,456 "
                            "points, land-masked U[0,1] weights x cell area, n=12, MAC 0.7, "
                            "N0=576, 1 RHS"),
+    "newton-1.5m": dict(m=512, kernel=2, n=12, theta=0.7, N0=576,
+                        desc="Newtonian 1/sqrt(2(1-x.y)), cubed sphere 6x512^2 = 1,572,864 "
+                             "points (profiling case of the same kernel shapes), n=12, MAC 0.7, "
+                             "N0=576, 1 RHS"),
     "poisson-multirhs-1.5m": dict(m=512, kernel=0, n=10, theta=0.7, N0=400, nrhs=16,
                                   desc="Poisson log kernel, cubed sphere 6x512^2 = 1,572,864 "
                                        "points, 16 RHS of random Y_nm combinations, n=10, "
@@ -114,7 +118,7 @@ class ClockSampler:
 def make_workload(name):
     from paper_2508_13550_gb300 import inputs as I
     wl = WORKLOADS[name]
-    if name == "newton-6m":
+    if name.startswith("newton"):
         pts, A, w = I.workload_newton_land(wl["m"])
     else:
         pts, A, w, _ = I.workload_multi_rhs(wl["m"], wl["nrhs"], with_exact=False)
@@ -357,7 +361,7 @@ def main():
     ap.add_argument("--workload", default="newton-6m", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--err-samples", type=int, default=2048)
-    ap.add_argument("--cpu-leaves", type=int, default=64)
+    ap.add_argument("--cpu-leaves", type=int, default=8192)
     ap.add_argument("--ref-leaves", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", dest="fp64_compare", action="store_false")

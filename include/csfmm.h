@@ -159,8 +159,8 @@ csfmm_status csfmm_evaluate_ws(csfmm_plan plan, csfmm_workspace ws, const double
  *   plan    a plan of the current device (built earlier, e.g. at start-up)
  *   weights device [nrhs][N]; out device [nrhs][N][dim]; 1 <= nrhs <= 64
  * Needs 8 N nrhs (1 + dim) + ncells nrhs P (1 + dim) s bytes of scratch
- * (s = 8 for CSFMM_FP64, 4 for CSFMM_FP32_BULK; each part rounded up to 256
- * bytes); larger requests fail with CSFMM_ERR_INVALID_ARG and a message that
+ * (s = 8 for CSFMM_FP64, 4 for CSFMM_FP32_BULK, which also needs 4 N nrhs;
+ * each part rounded up to 256 bytes); larger requests fail with CSFMM_ERR_INVALID_ARG and a message that
  * states the size.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress with that device current); make that first
  * call before any stream capture.  Every call shares the one array, which

@@ -148,6 +148,7 @@ struct Workspace {
   int max_nrhs = 0;
   DeviceArena arena;
   double *ws = nullptr;     // [max_nrhs][N] weights in tree order
+  float *wsf = nullptr;     // [max_nrhs][N] the same in FP32 (FP32 form only)
   double *wbar = nullptr;   // [nc][max_nrhs][P] proxy weights (FP64 form)
   float *wbar32 = nullptr;  // [nc][max_nrhs][P] proxy weights (FP32 form)
   double *psi = nullptr;    // [nc][max_nrhs][dim][P] proxy potentials
@@ -172,6 +173,9 @@ csfmm_status build_tree(Plan &pl, const double *points, cudaStream_t st);
 csfmm_status evaluate_impl(Plan &pl, Workspace &ws, const double *w, int nrhs, double *out,
                            cudaStream_t st);
 csfmm_status workspace_alloc(Plan &pl, Workspace &ws, int max_nrhs);
+// FP32-bulk near field (near32.cu): nr <= 4 right-hand sides from r0.
+void launch_near32(const PlanView &v, const int32_t *leaves, int nleaves, const float *wsf, int ldw,
+                   const float *wbar, int ldr, int r0, int nr, double *phi, cudaStream_t st);
 // Direct sum (direct.cu).
 csfmm_status direct_impl(const double *points, int64_t N, int kernel_id, const double *w,
                          int nrhs, const int64_t *targets, int64_t ntargets, double *out,

@@ -119,14 +119,16 @@ constexpr int kdim() {
 // ---------------------------------------------------------------------------
 // gather: ws[r][i] = w[r][perm[i]]
 // ---------------------------------------------------------------------------
-__global__ void gather_kernel(const int32_t *perm, const double *w, double *ws, int N, int nrhs,
-                              int ld_ws) {
+__global__ void gather_kernel(const int32_t *perm, const double *w, double *ws, float *wsf, int N,
+                              int nrhs, int ld_ws) {
   int64_t total = (int64_t)N * nrhs;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
        q += (int64_t)gridDim.x * blockDim.x) {
     int r = (int)(q / N);
     int i = (int)(q - (int64_t)r * N);
-    ws[(int64_t)r * ld_ws + i] = w[(int64_t)r * N + perm[i]];
+    double x = w[(int64_t)r * N + perm[i]];
+    ws[(int64_t)r * ld_ws + i] = x;
+    if (wsf) wsf[(int64_t)r * ld_ws + i] = (float)x;
   }
 }
 
@@ -539,8 +541,8 @@ csfmm_status run_passes(Plan &pl, Workspace &W, const double *w, int nrhs, doubl
     if (s__ != CSFMM_OK) return s__;                \
   } while (0)
   CSFMM_MARK(CSFMM_PHASE_GATHER);
-  gather_kernel<<<grid_for((int64_t)N * nrhs, 256, 152 * 32), 256, 0, st>>>(pl.perm, w, W.ws, N,
-                                                                             nrhs, N);
+  gather_kernel<<<grid_for((int64_t)N * nrhs, 256, 152 * 32), 256, 0, st>>>(
+      pl.perm, w, W.ws, sizeof(Real) == 4 ? W.wsf : nullptr, N, nrhs, N);
   ++pl.launches;
   const int tb_prox = ((P + 31) / 32) * 32;
   CSFMM_MARK(CSFMM_PHASE_P2M);
@@ -564,7 +566,10 @@ csfmm_status run_passes(Plan &pl, Workspace &W, const double *w, int nrhs, doubl
   CSFMM_MARK(CSFMM_PHASE_NEAR);
   for (int r0 = 0; r0 < nrhs; r0 += kRB) {
     int nr = min(kRB, nrhs - r0);
-    launch_near<KID, Real>(v, pl, W, nr, r0, wbar, st);
+    if constexpr (sizeof(Real) == 4)
+      launch_near32(v, pl.leaves, pl.nleaves, W.wsf, N, wbar, ldr, r0, nr, W.phi, st);
+    else
+      launch_near<KID, Real>(v, pl, W, nr, r0, wbar, st);
     ++pl.launches;
   }
   CSFMM_MARK(CSFMM_PHASE_L2L);
@@ -625,6 +630,7 @@ csfmm_status workspace_alloc(Plan &pl, Workspace &W, int max_nrhs) {
     if ((s = W.arena.alloc(&W.psi, nc * R * pl.dim * P)) != CSFMM_OK) return s;
   } else {
     if ((s = W.arena.alloc(&W.wbar32, nc * R * P)) != CSFMM_OK) return s;
+    if ((s = W.arena.alloc(&W.wsf, R * N)) != CSFMM_OK) return s;
     // FP32 proxy potentials live in the psi buffer (half of its FP64 size is used)
     if ((s = W.arena.alloc(&W.psi, (nc * R * pl.dim * P + 1) / 2)) != CSFMM_OK) return s;
   }

@@ -82,7 +82,8 @@ extern "C" csfmm_status csfmm_evaluate_static(csfmm_plan plan, const double *wei
   const size_t b_wbar = round256(nc * R * P * real);
   const size_t b_psi = round256(nc * R * dim * P * real);
   const size_t b_phi = round256(R * N * dim * sizeof(double));
-  const size_t need = b_ws + b_wbar + b_psi + b_phi;
+  const size_t b_wsf = pl.precision == CSFMM_FP64 ? 0 : round256(R * N * sizeof(float));
+  const size_t need = b_ws + b_wbar + b_psi + b_phi + b_wsf;
   if (need > (size_t)CSFMM_STATIC_SCRATCH_BYTES) {
     set_error("this evaluation needs %zu bytes of scratch; the static scratch holds %zu bytes "
               "(use csfmm_evaluate, or fewer right-hand sides)",
@@ -102,5 +103,6 @@ extern "C" csfmm_status csfmm_evaluate_static(csfmm_plan plan, const double *wei
   else W.wbar32 = reinterpret_cast<float *>(base + b_ws);
   W.psi = reinterpret_cast<double *>(base + b_ws + b_wbar);
   W.phi = reinterpret_cast<double *>(base + b_ws + b_wbar + b_psi);
+  if (b_wsf) W.wsf = reinterpret_cast<float *>(base + b_ws + b_wbar + b_psi + b_phi);
   return evaluate_impl(pl, W, weights, nrhs, out, (cudaStream_t)stream);
 }
