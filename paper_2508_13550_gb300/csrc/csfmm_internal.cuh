@@ -173,7 +173,10 @@ csfmm_status build_tree(Plan &pl, const double *points, cudaStream_t st);
 csfmm_status evaluate_impl(Plan &pl, Workspace &ws, const double *w, int nrhs, double *out,
                            cudaStream_t st);
 csfmm_status workspace_alloc(Plan &pl, Workspace &ws, int max_nrhs);
-// FP32-bulk near field (near32.cu): nr <= 4 right-hand sides from r0.
+// FP32-bulk far field (interact32.cu): nr <= 4 right-hand sides from r0.
+void launch_far32(const PlanView &v, int ncells, const float *wsf, const float *wbar, int ldr,
+                  int r0, int nr, float *psi, cudaStream_t st);
+// FP32-bulk near field (interact32.cu): nr <= 4 right-hand sides from r0.
 void launch_near32(const PlanView &v, const int32_t *leaves, int nleaves, const float *wsf, int ldw,
                    const float *wbar, int ldr, int r0, int nr, double *phi, cudaStream_t st);
 // Direct sum (direct.cu).

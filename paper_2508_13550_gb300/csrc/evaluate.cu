@@ -48,11 +48,10 @@ __device__ __forceinline__ const double *M_of<double>(const PlanView &v) { retur
 template <>
 __device__ __forceinline__ const float *M_of<float>(const PlanView &v) { return v.m2m32; }
 
-__device__ __forceinline__ float fast_rsqrt(float x) { return rsqrtf(x); }
+// FP64 kernel factors of the reference form (the FP32-bulk kernels live in
+// interact32.cu).
 __device__ __forceinline__ double fast_rsqrt(double x) { return rsqrt(x); }
-__device__ __forceinline__ float fast_log2(float x) { return __log2f(x); }
 __device__ __forceinline__ double fast_log2(double x) { return log2(x); }
-__device__ __forceinline__ float fast_rcp(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double fast_rcp(double x) { return 1.0 / x; }
 
 // ---------------------------------------------------------------------------
@@ -134,45 +133,45 @@ __global__ void gather_kernel(const int32_t *perm, const double *w, double *ws, 
 
 // ---------------------------------------------------------------------------
 // P2M: for leaf c, wbar[c][r][k1 p + k2] = sum_j La[j][k1] Lb[j][k2] w_r[j].
-// One block per leaf, threads over proxies.
+// One block per leaf (blockDim >= P), one thread per proxy; the Lagrange
+// rows of CH points at a time are staged through shared memory (coalesced).
 // ---------------------------------------------------------------------------
-template <typename Real>
-__global__ void p2m_kernel(PlanView v, const int32_t *leaves, const double *ws, int ldw,
-                           int r0, int nr, Real *wbar, int ldr) {
-  constexpr int CH = 32;
-  __shared__ Real sLa[CH * kMaxP], sLb[CH * kMaxP], sw[kRB * CH];
+template <typename Real, int NR>
+__global__ void p2m_kernel(PlanView v, const int32_t *leaves, const double *ws, int ldw, int r0,
+                           Real *wbar, int ldr) {
+  constexpr int CH = 64;
+  __shared__ Real sLa[CH * kMaxP], sLb[CH * kMaxP], sw[NR * CH];
   const int c = leaves[blockIdx.x];
   const int b = v.cbegin[c], e = v.cend[c], p = v.p, P = v.P;
   const Real *La = La_of<Real>(v), *Lb = Lb_of<Real>(v);
-  for (int k0 = 0; k0 < P; k0 += blockDim.x) {
-    int k = k0 + threadIdx.x;
-    int k1 = k / p, k2 = k - k1 * p;
-    Real acc[kRB];
+  const int k = threadIdx.x;
+  const int k1 = k / p, k2 = k - (k / p) * p;
+  Real acc[NR];
 #pragma unroll
-    for (int q = 0; q < kRB; ++q) acc[q] = 0;
-    for (int j0 = b; j0 < e; j0 += CH) {
-      int nj = min(CH, e - j0);
-      __syncthreads();
-      for (int t = threadIdx.x; t < nj * p; t += blockDim.x) {
-        sLa[t] = La[(int64_t)j0 * p + t];
-        sLb[t] = Lb[(int64_t)j0 * p + t];
-      }
-      for (int t = threadIdx.x; t < kRB * CH; t += blockDim.x) {
-        int q = t / CH, j = t - q * CH;
-        sw[t] = (q < nr && j < nj) ? (Real)ws[(int64_t)(r0 + q) * ldw + j0 + j] : (Real)0;
-      }
-      __syncthreads();
-      if (k < P) {
-        for (int j = 0; j < nj; ++j) {
-          Real l = sLa[j * p + k1] * sLb[j * p + k2];
-#pragma unroll
-          for (int q = 0; q < kRB; ++q) acc[q] += l * sw[q * CH + j];
-        }
-      }
+  for (int q = 0; q < NR; ++q) acc[q] = 0;
+  for (int j0 = b; j0 < e; j0 += CH) {
+    const int nj = min(CH, e - j0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < nj * p; t += blockDim.x) {
+      sLa[t] = La[(int64_t)j0 * p + t];
+      sLb[t] = Lb[(int64_t)j0 * p + t];
     }
+    for (int t = threadIdx.x; t < NR * CH; t += blockDim.x) {
+      const int q = t / CH, j = t - q * CH;
+      sw[t] = j < nj ? (Real)ws[(int64_t)(r0 + q) * ldw + j0 + j] : (Real)0;
+    }
+    __syncthreads();
     if (k < P) {
-      for (int q = 0; q < nr; ++q) wbar[((int64_t)c * ldr + r0 + q) * P + k] = acc[q];
+      for (int j = 0; j < nj; ++j) {
+        const Real l = sLa[j * p + k1] * sLb[j * p + k2];
+#pragma unroll
+        for (int q = 0; q < NR; ++q) acc[q] += l * sw[q * CH + j];
+      }
     }
+  }
+  if (k < P) {
+#pragma unroll
+    for (int q = 0; q < NR; ++q) wbar[((int64_t)c * ldr + r0 + q) * P + k] = acc[q];
   }
 }
 
@@ -471,34 +470,48 @@ __global__ void near_kernel(PlanView v, const int32_t *leaves, const double *ws,
 
 // ---------------------------------------------------------------------------
 // L2P + finalize: out[r][perm[i]][d] = phi[r][i][d] + sum_m psi_leaf[m] La[i][m1] Lb[i][m2].
+// One block per leaf, one thread per point of a chunk; the chunk's Lagrange
+// rows are staged through shared memory once for every (r, d).
 // ---------------------------------------------------------------------------
+constexpr int kL2PThreads = 128;
+
 template <typename Real>
-__global__ void l2p_kernel(PlanView v, const int32_t *leaves, const Real *psi, int ldr, int r0,
-                           int nr, int dim, const double *phi, double *out) {
+__global__ void __launch_bounds__(kL2PThreads) l2p_kernel(PlanView v, const int32_t *leaves,
+                                                          const Real *psi, int ldr, int nrhs,
+                                                          int dim, const double *phi, double *out) {
   __shared__ Real sp[kMaxP * kMaxP];
+  __shared__ Real sLa[kL2PThreads * kMaxP], sLb[kL2PThreads * kMaxP];
   const int c = leaves[blockIdx.x];
   const int b = v.cbegin[c], e = v.cend[c], p = v.p, P = v.P;
   const Real *La = La_of<Real>(v), *Lb = Lb_of<Real>(v);
-  for (int r = r0; r < r0 + nr; ++r)
-    for (int d = 0; d < dim; ++d) {
-      __syncthreads();
-      for (int t = threadIdx.x; t < P; t += blockDim.x)
-        sp[t] = psi[(((int64_t)c * ldr + r) * dim + d) * P + t];
-      __syncthreads();
-      for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
-        const Real *la = La + (int64_t)i * p, *lb = Lb + (int64_t)i * p;
-        Real lbv[kMaxP];
-        for (int m2 = 0; m2 < p; ++m2) lbv[m2] = lb[m2];
-        Real acc = 0;
-        for (int m1 = 0; m1 < p; ++m1) {
-          Real s = 0;
-          for (int m2 = 0; m2 < p; ++m2) s += sp[m1 * p + m2] * lbv[m2];
-          acc += la[m1] * s;
-        }
-        const int64_t oi = ((int64_t)r * v.N + i) * dim + d;
-        out[((int64_t)r * v.N + v.perm[i]) * dim + d] = phi[oi] + (double)acc;
-      }
+  for (int i0 = b; i0 < e; i0 += kL2PThreads) {
+    const int nj = min(kL2PThreads, e - i0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < nj * p; t += kL2PThreads) {
+      sLa[t] = La[(int64_t)i0 * p + t];
+      sLb[t] = Lb[(int64_t)i0 * p + t];
     }
+    const int t = threadIdx.x;
+    const int i = i0 + t;
+    for (int r = 0; r < nrhs; ++r)
+      for (int d = 0; d < dim; ++d) {
+        __syncthreads();
+        for (int u = threadIdx.x; u < P; u += kL2PThreads)
+          sp[u] = psi[(((int64_t)c * ldr + r) * dim + d) * P + u];
+        __syncthreads();
+        if (t < nj) {
+          const Real *la = sLa + t * p, *lb = sLb + t * p;
+          Real acc = 0;
+          for (int m1 = 0; m1 < p; ++m1) {
+            Real s = 0;
+            for (int m2 = 0; m2 < p; ++m2) s += sp[m1 * p + m2] * lb[m2];
+            acc += la[m1] * s;
+          }
+          const int64_t oi = ((int64_t)r * v.N + i) * dim + d;
+          out[((int64_t)r * v.N + v.perm[i]) * dim + d] = phi[oi] + (double)acc;
+        }
+      }
+  }
 }
 
 template <int KID, typename Real>
@@ -546,9 +559,15 @@ csfmm_status run_passes(Plan &pl, Workspace &W, const double *w, int nrhs, doubl
   ++pl.launches;
   const int tb_prox = ((P + 31) / 32) * 32;
   CSFMM_MARK(CSFMM_PHASE_P2M);
+  const int tb_p2m = tb_prox < 64 ? 64 : tb_prox;
   for (int r0 = 0; r0 < nrhs; r0 += kRB) {
     int nr = min(kRB, nrhs - r0);
-    p2m_kernel<Real><<<pl.nleaves, 128, 0, st>>>(v, pl.leaves, W.ws, N, r0, nr, wbar, ldr);
+    switch (nr) {
+      case 1: p2m_kernel<Real, 1><<<pl.nleaves, tb_p2m, 0, st>>>(v, pl.leaves, W.ws, N, r0, wbar, ldr); break;
+      case 2: p2m_kernel<Real, 2><<<pl.nleaves, tb_p2m, 0, st>>>(v, pl.leaves, W.ws, N, r0, wbar, ldr); break;
+      case 3: p2m_kernel<Real, 3><<<pl.nleaves, tb_p2m, 0, st>>>(v, pl.leaves, W.ws, N, r0, wbar, ldr); break;
+      default: p2m_kernel<Real, 4><<<pl.nleaves, tb_p2m, 0, st>>>(v, pl.leaves, W.ws, N, r0, wbar, ldr); break;
+    }
     ++pl.launches;
   }
   CSFMM_MARK(CSFMM_PHASE_M2M);
@@ -560,7 +579,10 @@ csfmm_status run_passes(Plan &pl, Workspace &W, const double *w, int nrhs, doubl
   CSFMM_MARK(CSFMM_PHASE_FAR);
   for (int r0 = 0; r0 < nrhs; r0 += kRB) {
     int nr = min(kRB, nrhs - r0);
-    launch_far<KID, Real>(v, pl, W, nr, r0, tb_prox, wbar, psi, st);
+    if constexpr (sizeof(Real) == 4)
+      launch_far32(v, pl.ncells, W.wsf, wbar, ldr, r0, nr, psi, st);
+    else
+      launch_far<KID, Real>(v, pl, W, nr, r0, tb_prox, wbar, psi, st);
     ++pl.launches;
   }
   CSFMM_MARK(CSFMM_PHASE_NEAR);
@@ -579,7 +601,7 @@ csfmm_status run_passes(Plan &pl, Workspace &W, const double *w, int nrhs, doubl
     ++pl.launches;
   }
   CSFMM_MARK(CSFMM_PHASE_L2P);
-  l2p_kernel<Real><<<pl.nleaves, 128, 0, st>>>(v, pl.leaves, psi, ldr, 0, nrhs, dim, W.phi, out);
+  l2p_kernel<Real><<<pl.nleaves, kL2PThreads, 0, st>>>(v, pl.leaves, psi, ldr, nrhs, dim, W.phi, out);
   ++pl.launches;
   CSFMM_MARK(CSFMM_NUM_PHASES);
 #undef CSFMM_MARK

@@ -1,0 +1,704 @@
+// interact32.cu -- the FP32-bulk interactions.
+//
+// Near field: PP and PC potentials at the target
+// particles of every leaf (Sec. 5, Eqs. PP and PC):
+//     phi(x_i) = sum_{S in PP(T)} sum_{y_j in S, j != i} K(x_i, y_j) w_j
+//              + sum_{S in PC(T)} sum_k K(x_i, s_k) wbar_k(S)
+//
+// This is the hot loop of the evaluation (82% of the kernel evaluations of
+// the N = 6.3M workload).  It is bound by the arithmetic pipes, not by memory:
+// per evaluation 7 FP32 operations (3 for the pair-relative difference, 3 for
+// |r|^2, 1 to accumulate) and one MUFU operation (rsqrt, lg2 or rcp).
+//
+// Layout: one thread block (kThreads threads) per target leaf; each thread
+// owns NT targets (strided by kThreads, coalesced loads) and reuses every
+// source it reads from shared memory NT times.  Sources of one list entry (a
+// leaf's particles or a cell's proxies) are staged through shared memory as
+// float4 (offset from the source cell centre, weight) tiles of kTile.
+// Coordinates are pair-relative: t_i = (x_i - c_T) + (c_T - c_S) with the
+// centre difference formed in FP64 and rounded once, so that r = t_i - s_j is
+// accurate to FP32 rounding of |x_i - c_T| + |c_T - c_S| without cancellation
+// against |x|=1.  Sums over one tile are FP32; the per-target total is FP64.
+// The i = j term only exists when S = T; that tile runs a variant that masks
+// r = 0, every other tile runs unmasked.
+#include <math.h>
+
+#include "csfmm_internal.cuh"
+
+namespace csfmm {
+
+namespace {
+
+constexpr int kThreads = 64;
+constexpr int kTile = 256;
+// Resident blocks per SM requested from the register allocator for the
+// packed near-field kernel (16 caps it at 64 registers per thread; measured
+// fastest of 8, 10, 12 and 16 on the N = 6.3M Newtonian workload).
+#ifndef CSFMM_NEAR_MINB
+#define CSFMM_NEAR_MINB 16
+#endif
+
+template <int KID>
+__host__ __device__ constexpr int kdim32() {
+  return KID == CSFMM_KERNEL_BIOT_SAVART ? 3 : 1;
+}
+
+// Kernel factor f(d2) (Laplace: log2 d2, Newton: 1/sqrt d2, Biot-Savart: 1/d2),
+// one MUFU instruction each.  Flush-to-zero is safe: d2 of two distinct
+// points on the unit sphere is far above the FP32 denormal range.
+__device__ __forceinline__ float mufu_rsqrt(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float mufu_lg2(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float mufu_rcp(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+template <int KID>
+__device__ __forceinline__ float kfactor(float d2) {
+  if constexpr (KID == CSFMM_KERNEL_LAPLACE) return mufu_lg2(d2);
+  else if constexpr (KID == CSFMM_KERNEL_NEWTON) return mufu_rsqrt(d2);
+  else if constexpr (KID == CSFMM_KERNEL_BIOT_SAVART) return mufu_rcp(d2);
+  else return 1.0f;
+}
+
+// Packed pairs of FP32 values in one 64-bit register (Blackwell f32x2 math).
+typedef unsigned long long f2x;
+__device__ __forceinline__ f2x f2_sub(f2x a, f2x b) {
+  f2x d;
+  asm("sub.rn.ftz.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2x f2_mul(f2x a, f2x b) {
+  f2x d;
+  asm("mul.rn.ftz.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2x f2_fma(f2x a, f2x b, f2x c) {
+  f2x d;
+  asm("fma.rn.ftz.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ f2x f2_pack(float lo, float hi) {
+  f2x d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+  return d;
+}
+__device__ __forceinline__ void f2_unpack(f2x a, float &lo, float &hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a));
+}
+
+// One tile for NP pairs of targets (2 NP targets) and one right-hand side:
+// sA[j] = (x, x, y, y), sB[j] = (z, z, w, w) of source j.
+template <int KID, int NP, bool SELF>
+__device__ __forceinline__ void tile_sum_x2(const ulonglong2 *__restrict__ sA,
+                                            const ulonglong2 *__restrict__ sB, int nj,
+                                            const f2x (&tx)[NP], const f2x (&ty)[NP],
+                                            const f2x (&tz)[NP], const int (&self)[2 * NP],
+                                            f2x (&acc)[NP]) {
+#pragma unroll 4
+  for (int j = 0; j < nj; ++j) {
+    const ulonglong2 A = sA[j], B = sB[j];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      const f2x rx = f2_sub(tx[q], A.x), ry = f2_sub(ty[q], A.y), rz = f2_sub(tz[q], B.x);
+      f2x d2 = f2_mul(rx, rx);
+      d2 = f2_fma(ry, ry, d2);
+      d2 = f2_fma(rz, rz, d2);
+      float d0, d1;
+      f2_unpack(d2, d0, d1);
+      float f0 = kfactor<KID>(d0), f1 = kfactor<KID>(d1);
+      if constexpr (SELF) {
+        f0 = (j == self[2 * q]) ? 0.0f : f0;
+        f1 = (j == self[2 * q + 1]) ? 0.0f : f1;
+      }
+      acc[q] = f2_fma(B.y, f2_pack(f0, f1), acc[q]);
+    }
+  }
+}
+
+template <int KID, int NT, int NR, bool SELF>
+__device__ __forceinline__ void tile_sum(const float4 *__restrict__ sp, const float *__restrict__ sw,
+                                         int nj, const float (&tx)[NT], const float (&ty)[NT],
+                                         const float (&tz)[NT], const int (&self)[NT],
+                                         float (&a)[NT][NR][3]) {
+#pragma unroll 4
+  for (int j = 0; j < nj; ++j) {
+    const float4 s = sp[j];
+    float wq[NR];
+    wq[0] = s.w;
+#pragma unroll
+    for (int q = 1; q < NR; ++q) wq[q] = sw[q * kTile + j];
+#pragma unroll
+    for (int k = 0; k < NT; ++k) {
+      const float rx = tx[k] - s.x, ry = ty[k] - s.y, rz = tz[k] - s.z;
+      const float d2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+      float f = kfactor<KID>(d2);
+      if constexpr (SELF) f = (j == self[k]) ? 0.0f : f;
+#pragma unroll
+      for (int q = 0; q < NR; ++q) {
+        if constexpr (KID == CSFMM_KERNEL_BIOT_SAVART) {
+          const float g = wq[q] * f;
+          a[k][q][0] = fmaf(g, rx, a[k][q][0]);
+          a[k][q][1] = fmaf(g, ry, a[k][q][1]);
+          a[k][q][2] = fmaf(g, rz, a[k][q][2]);
+        } else {
+          a[k][q][0] = fmaf(wq[q], f, a[k][q][0]);
+        }
+      }
+    }
+  }
+}
+
+template <int KID, int NT, int NR>
+__global__ void __launch_bounds__(kThreads) near32_kernel(PlanView v, const int32_t *leaves,
+                                                          const float *wsf, int ldw,
+                                                          const float *wbar, int ldr, int r0,
+                                                          double *phi) {
+  constexpr int DIM = kdim32<KID>();
+  __shared__ float4 sp[kTile];
+  __shared__ float sw[NR * kTile];
+  __shared__ float wsum[NR][kThreads / 32];
+  const int c = leaves[blockIdx.x];
+  const int b = v.cbegin[c], e = v.cend[c], P = v.P;
+  const double cTx = v.ccentre[3 * c], cTy = v.ccentre[3 * c + 1], cTz = v.ccentre[3 * c + 2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i0 = b; i0 < e; i0 += kThreads * NT) {
+    float ox[NT], oy[NT], oz[NT];
+    double xa[NT][3];   // absolute target position (Biot-Savart cross product)
+    bool act[NT];
+    double out[NT][NR][DIM];
+#pragma unroll
+    for (int k = 0; k < NT; ++k) {
+      const int i = i0 + threadIdx.x + k * kThreads;
+      act[k] = i < e;
+      const int ii = act[k] ? i : b;
+      const float4 o = v.off32[ii];
+      ox[k] = o.x; oy[k] = o.y; oz[k] = o.z;
+      if constexpr (KID == CSFMM_KERNEL_BIOT_SAVART) {
+        xa[k][0] = v.x[ii]; xa[k][1] = v.x[v.N + ii]; xa[k][2] = v.x[2 * (int64_t)v.N + ii];
+      }
+#pragma unroll
+      for (int q = 0; q < NR; ++q)
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) out[k][q][d] = 0.0;
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+      const int type = pass == 0 ? CSFMM_LIST_PP : CSFMM_LIST_PC;
+      const int e0 = v.loff[type][c], e1 = v.loff[type][c + 1];
+      for (int ee = e0; ee < e1; ++ee) {
+        const int s = v.lsrc[type][ee];
+        const float dcx = (float)(cTx - v.ccentre[3 * s]);
+        const float dcy = (float)(cTy - v.ccentre[3 * s + 1]);
+        const float dcz = (float)(cTz - v.ccentre[3 * s + 2]);
+        float tx[NT], ty[NT], tz[NT];
+#pragma unroll
+        for (int k = 0; k < NT; ++k) {
+          tx[k] = ox[k] + dcx;
+          ty[k] = oy[k] + dcy;
+          tz[k] = oz[k] + dcz;
+        }
+        const bool pp = type == CSFMM_LIST_PP;
+        const int sb = pp ? v.cbegin[s] : 0;
+        const int nsrc = pp ? v.cend[s] - sb : P;
+        const bool self_tile = pp && s == c;
+        for (int j0 = 0; j0 < nsrc; j0 += kTile) {
+          const int nj = min(kTile, nsrc - j0);
+          __syncthreads();
+          float part[NR];
+#pragma unroll
+          for (int q = 0; q < NR; ++q) part[q] = 0.f;
+          for (int t = threadIdx.x; t < nj; t += kThreads) {
+            float4 val;
+            float wv[NR];
+            if (pp) {
+              const int j = sb + j0 + t;
+              val = v.off32[j];
+#pragma unroll
+              for (int q = 0; q < NR; ++q) wv[q] = wsf[(int64_t)(r0 + q) * ldw + j];
+            } else {
+              const int64_t so = (int64_t)s * 3 * P;
+              const int k = j0 + t;
+              val = make_float4(v.proxy32[so + k], v.proxy32[so + P + k], v.proxy32[so + 2 * P + k], 0.f);
+#pragma unroll
+              for (int q = 0; q < NR; ++q) wv[q] = wbar[((int64_t)s * ldr + r0 + q) * P + k];
+            }
+            val.w = wv[0];
+            sp[t] = val;
+#pragma unroll
+            for (int q = 1; q < NR; ++q) sw[q * kTile + t] = wv[q];
+#pragma unroll
+            for (int q = 0; q < NR; ++q) part[q] += wv[q];
+          }
+          if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
+#pragma unroll
+            for (int q = 0; q < NR; ++q) {
+              float x = part[q];
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+              if (lane == 0) wsum[q][warp] = x;
+            }
+          }
+          __syncthreads();
+          float a[NT][NR][3];
+#pragma unroll
+          for (int k = 0; k < NT; ++k)
+#pragma unroll
+            for (int q = 0; q < NR; ++q) a[k][q][0] = a[k][q][1] = a[k][q][2] = 0.f;
+          int self[NT];
+#pragma unroll
+          for (int k = 0; k < NT; ++k) self[k] = (i0 + (int)threadIdx.x + k * kThreads) - (sb + j0);
+          if (self_tile)
+            tile_sum<KID, NT, NR, true>(sp, sw, nj, tx, ty, tz, self, a);
+          else
+            tile_sum<KID, NT, NR, false>(sp, sw, nj, tx, ty, tz, self, a);
+#pragma unroll
+          for (int k = 0; k < NT; ++k) {
+#pragma unroll
+            for (int q = 0; q < NR; ++q) {
+              if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
+                // -(1/4pi) sum w ln(d2/2) = -(ln2/4pi) (sum w log2 d2 - sum w)
+                float tot = 0.f;
+#pragma unroll
+                for (int u = 0; u < kThreads / 32; ++u) tot += wsum[q][u];
+                if (self_tile && self[k] >= 0 && self[k] < nj)
+                  tot -= (q == 0) ? sp[self[k]].w : sw[q * kTile + self[k]];
+                out[k][q][0] += -(0.69314718055994530942 * kInv4Pi) * ((double)a[k][q][0] - (double)tot);
+              } else if constexpr (KID == CSFMM_KERNEL_BIOT_SAVART) {
+                const double b0 = a[k][q][0], b1 = a[k][q][1], b2 = a[k][q][2];
+                out[k][q][0] += kInv2Pi * (xa[k][1] * b2 - xa[k][2] * b1);
+                out[k][q][1] += kInv2Pi * (xa[k][2] * b0 - xa[k][0] * b2);
+                out[k][q][2] += kInv2Pi * (xa[k][0] * b1 - xa[k][1] * b0);
+              } else {
+                out[k][q][0] += (double)a[k][q][0];
+              }
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < NT; ++k) {
+      if (!act[k]) continue;
+      const int i = i0 + threadIdx.x + k * kThreads;
+#pragma unroll
+      for (int q = 0; q < NR; ++q)
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) phi[((int64_t)(r0 + q) * v.N + i) * DIM + d] = out[k][q][d];
+    }
+  }
+}
+
+// Packed variant for one right-hand side and a scalar kernel (Laplace,
+// Newtonian, K = 1): same arithmetic per pair, two targets per instruction.
+template <int KID, int NP>
+__global__ void __launch_bounds__(kThreads, CSFMM_NEAR_MINB) near32x2_kernel(PlanView v, const int32_t *leaves,
+                                                            const float *wsf, const float *wbar,
+                                                            int ldr, int r0, double *phi) {
+  constexpr int NT = 2 * NP;
+  __shared__ ulonglong2 sA[kTile], sB[kTile];
+  __shared__ float wsum[kThreads / 32];
+  const int c = leaves[blockIdx.x];
+  const int b = v.cbegin[c], e = v.cend[c], P = v.P;
+  const double cTx = v.ccentre[3 * c], cTy = v.ccentre[3 * c + 1], cTz = v.ccentre[3 * c + 2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float *wr = wsf + (int64_t)r0 * v.N;
+  for (int i0 = b; i0 < e; i0 += kThreads * NT) {
+    float ox[NT], oy[NT], oz[NT];
+    double out[NT];
+#pragma unroll
+    for (int k = 0; k < NT; ++k) {
+      const int i = i0 + threadIdx.x + k * kThreads;
+      const float4 o = v.off32[i < e ? i : b];
+      ox[k] = o.x; oy[k] = o.y; oz[k] = o.z;
+      out[k] = 0.0;
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+      const int type = pass == 0 ? CSFMM_LIST_PP : CSFMM_LIST_PC;
+      const int e0 = v.loff[type][c], e1 = v.loff[type][c + 1];
+      for (int ee = e0; ee < e1; ++ee) {
+        const int s = v.lsrc[type][ee];
+        const float dcx = (float)(cTx - v.ccentre[3 * s]);
+        const float dcy = (float)(cTy - v.ccentre[3 * s + 1]);
+        const float dcz = (float)(cTz - v.ccentre[3 * s + 2]);
+        f2x tx[NP], ty[NP], tz[NP];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+          tx[q] = f2_pack(ox[2 * q] + dcx, ox[2 * q + 1] + dcx);
+          ty[q] = f2_pack(oy[2 * q] + dcy, oy[2 * q + 1] + dcy);
+          tz[q] = f2_pack(oz[2 * q] + dcz, oz[2 * q + 1] + dcz);
+        }
+        const bool pp = type == CSFMM_LIST_PP;
+        const int sb = pp ? v.cbegin[s] : 0;
+        const int nsrc = pp ? v.cend[s] - sb : P;
+        const bool self_tile = pp && s == c;
+        for (int j0 = 0; j0 < nsrc; j0 += kTile) {
+          const int nj = min(kTile, nsrc - j0);
+          __syncthreads();
+          float part = 0.f;
+          for (int t = threadIdx.x; t < nj; t += kThreads) {
+            float x, y, z, w;
+            if (pp) {
+              const int j = sb + j0 + t;
+              const float4 o = v.off32[j];
+              x = o.x; y = o.y; z = o.z;
+              w = wr[j];
+            } else {
+              const int64_t so = (int64_t)s * 3 * P;
+              const int k = j0 + t;
+              x = v.proxy32[so + k]; y = v.proxy32[so + P + k]; z = v.proxy32[so + 2 * P + k];
+              w = wbar[((int64_t)s * ldr + r0) * P + k];
+            }
+            sA[t] = make_ulonglong2(f2_pack(x, x), f2_pack(y, y));
+            sB[t] = make_ulonglong2(f2_pack(z, z), f2_pack(w, w));
+            part += w;
+          }
+          if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+            if (lane == 0) wsum[warp] = part;
+          }
+          __syncthreads();
+          f2x acc[NP];
+#pragma unroll
+          for (int q = 0; q < NP; ++q) acc[q] = 0ull;
+          int self[NT];
+#pragma unroll
+          for (int k = 0; k < NT; ++k) self[k] = (i0 + (int)threadIdx.x + k * kThreads) - (sb + j0);
+          if (self_tile)
+            tile_sum_x2<KID, NP, true>(sA, sB, nj, tx, ty, tz, self, acc);
+          else
+            tile_sum_x2<KID, NP, false>(sA, sB, nj, tx, ty, tz, self, acc);
+          float tot = 0.f;
+          if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
+#pragma unroll
+            for (int u = 0; u < kThreads / 32; ++u) tot += wsum[u];
+          }
+#pragma unroll
+          for (int q = 0; q < NP; ++q) {
+            float a0, a1;
+            f2_unpack(acc[q], a0, a1);
+            float aa[2] = {a0, a1};
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int k = 2 * q + h;
+              if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
+                float t = tot;
+                if (self_tile && self[k] >= 0 && self[k] < nj) {
+                  float wself, dummy;
+                  f2_unpack(sB[self[k]].y, wself, dummy);
+                  t -= wself;
+                }
+                // -(1/4pi) sum w ln(d2/2) = -(ln2/4pi) (sum w log2 d2 - sum w)
+                out[k] += -(0.69314718055994530942 * kInv4Pi) * ((double)aa[h] - (double)t);
+              } else {
+                out[k] += (double)aa[h];
+              }
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < NT; ++k) {
+      const int i = i0 + threadIdx.x + k * kThreads;
+      if (i < e) phi[((int64_t)r0 * v.N + i)] = out[k];
+    }
+  }
+}
+
+
+// ---------------------------------------------------------------------------
+// Far field: CP and CC proxy potentials of every cell (Sec. 5, Eqs. CP and
+// CC, accumulated as Eq. CP_CC_accumulated):
+//     psi_T(t_m) = sum_{S in CP(T)} sum_{y_j in S} K(t_m, y_j) w_j
+//                + sum_{S in CC(T)} sum_k K(t_m, s_k) wbar_k(S)
+// One block per cell (cells without CP/CC entries write zeros), blockDim a
+// multiple of 32 covering P/2, two target proxies m and m + blockDim per
+// thread.  Same pair-relative FP32 arithmetic as the near field; a target
+// proxy never coincides with a source (the pair is well separated).
+// ---------------------------------------------------------------------------
+template <int KID>
+__global__ void __launch_bounds__(160) far32x2_kernel(PlanView v, const float *wsf,
+                                                      const float *wbar, int ldr, int r0,
+                                                      float *psi) {
+  __shared__ ulonglong2 sA[kTile], sB[kTile];
+  __shared__ float wsum[8];
+  const int c = blockIdx.x, P = v.P, nth = blockDim.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = nth >> 5;
+  const int64_t po = (int64_t)c * 3 * P;
+  float ox[2], oy[2], oz[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int m = threadIdx.x + h * nth;
+    const int mm = m < P ? m : 0;
+    ox[h] = v.proxy32[po + mm];
+    oy[h] = v.proxy32[po + P + mm];
+    oz[h] = v.proxy32[po + 2 * P + mm];
+  }
+  double out[2] = {0.0, 0.0};
+  const double cTx = v.ccentre[3 * c], cTy = v.ccentre[3 * c + 1], cTz = v.ccentre[3 * c + 2];
+  const float *wr = wsf + (int64_t)r0 * v.N;
+  const int self_none[2] = {-1, -1};
+  for (int pass = 0; pass < 2; ++pass) {
+    const int type = pass == 0 ? CSFMM_LIST_CP : CSFMM_LIST_CC;
+    const int e0 = v.loff[type][c], e1 = v.loff[type][c + 1];
+    for (int ee = e0; ee < e1; ++ee) {
+      const int s = v.lsrc[type][ee];
+      const float dcx = (float)(cTx - v.ccentre[3 * s]);
+      const float dcy = (float)(cTy - v.ccentre[3 * s + 1]);
+      const float dcz = (float)(cTz - v.ccentre[3 * s + 2]);
+      const f2x tx[1] = {f2_pack(ox[0] + dcx, ox[1] + dcx)};
+      const f2x ty[1] = {f2_pack(oy[0] + dcy, oy[1] + dcy)};
+      const f2x tz[1] = {f2_pack(oz[0] + dcz, oz[1] + dcz)};
+      const bool cp = type == CSFMM_LIST_CP;
+      const int sb = cp ? v.cbegin[s] : 0;
+      const int nsrc = cp ? v.cend[s] - sb : P;
+      for (int j0 = 0; j0 < nsrc; j0 += kTile) {
+        const int nj = min(kTile, nsrc - j0);
+        __syncthreads();
+        float part = 0.f;
+        for (int t = threadIdx.x; t < nj; t += nth) {
+          float x, y, z, w;
+          if (cp) {
+            const int j = sb + j0 + t;
+            const float4 o = v.off32[j];
+            x = o.x; y = o.y; z = o.z;
+            w = wr[j];
+          } else {
+            const int64_t so = (int64_t)s * 3 * P;
+            const int k = j0 + t;
+            x = v.proxy32[so + k]; y = v.proxy32[so + P + k]; z = v.proxy32[so + 2 * P + k];
+            w = wbar[((int64_t)s * ldr + r0) * P + k];
+          }
+          sA[t] = make_ulonglong2(f2_pack(x, x), f2_pack(y, y));
+          sB[t] = make_ulonglong2(f2_pack(z, z), f2_pack(w, w));
+          part += w;
+        }
+        if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+          if (lane == 0) wsum[warp] = part;
+        }
+        __syncthreads();
+        f2x acc[1] = {0ull};
+        tile_sum_x2<KID, 1, false>(sA, sB, nj, tx, ty, tz, self_none, acc);
+        float a0, a1;
+        f2_unpack(acc[0], a0, a1);
+        if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
+          float tot = 0.f;
+          for (int u = 0; u < nwarp; ++u) tot += wsum[u];
+          out[0] += -(0.69314718055994530942 * kInv4Pi) * ((double)a0 - (double)tot);
+          out[1] += -(0.69314718055994530942 * kInv4Pi) * ((double)a1 - (double)tot);
+        } else {
+          out[0] += (double)a0;
+          out[1] += (double)a1;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int m = threadIdx.x + h * nth;
+    if (m < P) psi[((int64_t)c * ldr + r0) * P + m] = (float)out[h];
+  }
+}
+
+// Scalar far field for Biot-Savart and for several right-hand sides.
+template <int KID, int NR>
+__global__ void __launch_bounds__(160) far32_kernel(PlanView v, const float *wsf, const float *wbar,
+                                                    int ldr, int r0, float *psi) {
+  constexpr int DIM = kdim32<KID>();
+  constexpr int NT = 2;
+  __shared__ float4 sp[kTile];
+  __shared__ float sw[NR * kTile];
+  __shared__ float wsum[NR][8];
+  const int c = blockIdx.x, P = v.P, nth = blockDim.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = nth >> 5;
+  const int64_t po = (int64_t)c * 3 * P;
+  float ox[NT], oy[NT], oz[NT];
+  double xa[NT][3];
+  double out[NT][NR][DIM];
+#pragma unroll
+  for (int h = 0; h < NT; ++h) {
+    const int m = threadIdx.x + h * nth;
+    const int mm = m < P ? m : 0;
+    ox[h] = v.proxy32[po + mm];
+    oy[h] = v.proxy32[po + P + mm];
+    oz[h] = v.proxy32[po + 2 * P + mm];
+    xa[h][0] = v.proxy[po + mm];
+    xa[h][1] = v.proxy[po + P + mm];
+    xa[h][2] = v.proxy[po + 2 * P + mm];
+#pragma unroll
+    for (int q = 0; q < NR; ++q)
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) out[h][q][d] = 0.0;
+  }
+  const double cTx = v.ccentre[3 * c], cTy = v.ccentre[3 * c + 1], cTz = v.ccentre[3 * c + 2];
+  const int self_none[NT] = {-1, -1};
+  for (int pass = 0; pass < 2; ++pass) {
+    const int type = pass == 0 ? CSFMM_LIST_CP : CSFMM_LIST_CC;
+    const int e0 = v.loff[type][c], e1 = v.loff[type][c + 1];
+    for (int ee = e0; ee < e1; ++ee) {
+      const int s = v.lsrc[type][ee];
+      const float dcx = (float)(cTx - v.ccentre[3 * s]);
+      const float dcy = (float)(cTy - v.ccentre[3 * s + 1]);
+      const float dcz = (float)(cTz - v.ccentre[3 * s + 2]);
+      float tx[NT], ty[NT], tz[NT];
+#pragma unroll
+      for (int h = 0; h < NT; ++h) {
+        tx[h] = ox[h] + dcx;
+        ty[h] = oy[h] + dcy;
+        tz[h] = oz[h] + dcz;
+      }
+      const bool cp = type == CSFMM_LIST_CP;
+      const int sb = cp ? v.cbegin[s] : 0;
+      const int nsrc = cp ? v.cend[s] - sb : P;
+      for (int j0 = 0; j0 < nsrc; j0 += kTile) {
+        const int nj = min(kTile, nsrc - j0);
+        __syncthreads();
+        float part[NR];
+#pragma unroll
+        for (int q = 0; q < NR; ++q) part[q] = 0.f;
+        for (int t = threadIdx.x; t < nj; t += nth) {
+          float4 val;
+          float wv[NR];
+          if (cp) {
+            const int j = sb + j0 + t;
+            val = v.off32[j];
+#pragma unroll
+            for (int q = 0; q < NR; ++q) wv[q] = wsf[(int64_t)(r0 + q) * v.N + j];
+          } else {
+            const int64_t so = (int64_t)s * 3 * P;
+            const int k = j0 + t;
+            val = make_float4(v.proxy32[so + k], v.proxy32[so + P + k], v.proxy32[so + 2 * P + k], 0.f);
+#pragma unroll
+            for (int q = 0; q < NR; ++q) wv[q] = wbar[((int64_t)s * ldr + r0 + q) * P + k];
+          }
+          val.w = wv[0];
+          sp[t] = val;
+#pragma unroll
+          for (int q = 1; q < NR; ++q) sw[q * kTile + t] = wv[q];
+#pragma unroll
+          for (int q = 0; q < NR; ++q) part[q] += wv[q];
+        }
+        if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
+#pragma unroll
+          for (int q = 0; q < NR; ++q) {
+            float x = part[q];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+            if (lane == 0) wsum[q][warp] = x;
+          }
+        }
+        __syncthreads();
+        float a[NT][NR][3];
+#pragma unroll
+        for (int h = 0; h < NT; ++h)
+#pragma unroll
+          for (int q = 0; q < NR; ++q) a[h][q][0] = a[h][q][1] = a[h][q][2] = 0.f;
+        tile_sum<KID, NT, NR, false>(sp, sw, nj, tx, ty, tz, self_none, a);
+#pragma unroll
+        for (int h = 0; h < NT; ++h)
+#pragma unroll
+          for (int q = 0; q < NR; ++q) {
+            if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
+              float tot = 0.f;
+              for (int u = 0; u < nwarp; ++u) tot += wsum[q][u];
+              out[h][q][0] += -(0.69314718055994530942 * kInv4Pi) * ((double)a[h][q][0] - (double)tot);
+            } else if constexpr (KID == CSFMM_KERNEL_BIOT_SAVART) {
+              const double b0 = a[h][q][0], b1 = a[h][q][1], b2 = a[h][q][2];
+              out[h][q][0] += kInv2Pi * (xa[h][1] * b2 - xa[h][2] * b1);
+              out[h][q][1] += kInv2Pi * (xa[h][2] * b0 - xa[h][0] * b2);
+              out[h][q][2] += kInv2Pi * (xa[h][0] * b1 - xa[h][1] * b0);
+            } else {
+              out[h][q][0] += (double)a[h][q][0];
+            }
+          }
+      }
+    }
+  }
+#pragma unroll
+  for (int h = 0; h < NT; ++h) {
+    const int m = threadIdx.x + h * nth;
+    if (m >= P) continue;
+#pragma unroll
+    for (int q = 0; q < NR; ++q)
+#pragma unroll
+      for (int d = 0; d < DIM; ++d)
+        psi[(((int64_t)c * ldr + r0 + q) * DIM + d) * P + m] = (float)out[h][q][d];
+  }
+}
+
+template <int KID>
+void launch_far_kid(const PlanView &v, int ncells, const float *wsf, const float *wbar, int ldr,
+                    int r0, int nr, float *psi, cudaStream_t st) {
+  const int nth = ((v.P + 63) / 64) * 32;  // 2 targets per thread
+  if constexpr (KID != CSFMM_KERNEL_BIOT_SAVART) {
+    if (nr == 1) {
+      far32x2_kernel<KID><<<ncells, nth, 0, st>>>(v, wsf, wbar, ldr, r0, psi);
+      return;
+    }
+  }
+  switch (nr) {
+    case 1: far32_kernel<KID, 1><<<ncells, nth, 0, st>>>(v, wsf, wbar, ldr, r0, psi); break;
+    case 2: far32_kernel<KID, 2><<<ncells, nth, 0, st>>>(v, wsf, wbar, ldr, r0, psi); break;
+    case 3: far32_kernel<KID, 3><<<ncells, nth, 0, st>>>(v, wsf, wbar, ldr, r0, psi); break;
+    default: far32_kernel<KID, 4><<<ncells, nth, 0, st>>>(v, wsf, wbar, ldr, r0, psi); break;
+  }
+}
+
+template <int KID, int NR>
+void launch_nr(const PlanView &v, const int32_t *leaves, int nleaves, const float *wsf, int ldw,
+               const float *wbar, int ldr, int r0, double *phi, cudaStream_t st) {
+  if constexpr (NR == 1 && KID != CSFMM_KERNEL_BIOT_SAVART) {
+    near32x2_kernel<KID, 2><<<nleaves, kThreads, 0, st>>>(v, leaves, wsf, wbar, ldr, r0, phi);
+  } else {
+    near32_kernel<KID, 2, NR><<<nleaves, kThreads, 0, st>>>(v, leaves, wsf, ldw, wbar, ldr, r0, phi);
+  }
+}
+
+template <int KID>
+void launch_kid(const PlanView &v, const int32_t *leaves, int nleaves, const float *wsf, int ldw,
+                const float *wbar, int ldr, int r0, int nr, double *phi, cudaStream_t st) {
+  switch (nr) {
+    case 1: launch_nr<KID, 1>(v, leaves, nleaves, wsf, ldw, wbar, ldr, r0, phi, st); break;
+    case 2: launch_nr<KID, 2>(v, leaves, nleaves, wsf, ldw, wbar, ldr, r0, phi, st); break;
+    case 3: launch_nr<KID, 3>(v, leaves, nleaves, wsf, ldw, wbar, ldr, r0, phi, st); break;
+    default: launch_nr<KID, 4>(v, leaves, nleaves, wsf, ldw, wbar, ldr, r0, phi, st); break;
+  }
+}
+
+}  // namespace
+
+// nr right-hand sides r0 .. r0+nr-1 (nr <= 4); psi [nc][ldr][dim][P] FP32.
+void launch_far32(const PlanView &v, int ncells, const float *wsf, const float *wbar, int ldr,
+                  int r0, int nr, float *psi, cudaStream_t st) {
+  switch (v.kernel_id) {
+    case CSFMM_KERNEL_LAPLACE: launch_far_kid<CSFMM_KERNEL_LAPLACE>(v, ncells, wsf, wbar, ldr, r0, nr, psi, st); break;
+    case CSFMM_KERNEL_BIOT_SAVART: launch_far_kid<CSFMM_KERNEL_BIOT_SAVART>(v, ncells, wsf, wbar, ldr, r0, nr, psi, st); break;
+    case CSFMM_KERNEL_NEWTON: launch_far_kid<CSFMM_KERNEL_NEWTON>(v, ncells, wsf, wbar, ldr, r0, nr, psi, st); break;
+    default: launch_far_kid<CSFMM_KERNEL_ONE>(v, ncells, wsf, wbar, ldr, r0, nr, psi, st); break;
+  }
+}
+
+// nr right-hand sides r0 .. r0+nr-1 (nr <= 4).
+void launch_near32(const PlanView &v, const int32_t *leaves, int nleaves, const float *wsf, int ldw,
+                   const float *wbar, int ldr, int r0, int nr, double *phi, cudaStream_t st) {
+  switch (v.kernel_id) {
+    case CSFMM_KERNEL_LAPLACE: launch_kid<CSFMM_KERNEL_LAPLACE>(v, leaves, nleaves, wsf, ldw, wbar, ldr, r0, nr, phi, st); break;
+    case CSFMM_KERNEL_BIOT_SAVART: launch_kid<CSFMM_KERNEL_BIOT_SAVART>(v, leaves, nleaves, wsf, ldw, wbar, ldr, r0, nr, phi, st); break;
+    case CSFMM_KERNEL_NEWTON: launch_kid<CSFMM_KERNEL_NEWTON>(v, leaves, nleaves, wsf, ldw, wbar, ldr, r0, nr, phi, st); break;
+    default: launch_kid<CSFMM_KERNEL_ONE>(v, leaves, nleaves, wsf, ldw, wbar, ldr, r0, nr, phi, st); break;
+  }
+}
+
+}  // namespace csfmm
