@@ -173,6 +173,11 @@ csfmm_status build_tree(Plan &pl, const double *points, cudaStream_t st);
 csfmm_status evaluate_impl(Plan &pl, Workspace &ws, const double *w, int nrhs, double *out,
                            cudaStream_t st);
 csfmm_status workspace_alloc(Plan &pl, Workspace &ws, int max_nrhs);
+// FP32-bulk near (far = false) or far (far = true) field for nr = 8 or 16
+// right-hand sides from r0, scalar kernels only (interact32.cu).
+void launch_multi32(const PlanView &v, bool far, int ngrid, const int32_t *leaves,
+                    const float *wsf, const float *wbar, int ldr, int r0, int nr, double *phi,
+                    float *psi, cudaStream_t st);
 // FP32-bulk far field (interact32.cu): nr <= 4 right-hand sides from r0.
 void launch_far32(const PlanView &v, int ncells, const float *wsf, const float *wbar, int ldr,
                   int r0, int nr, float *psi, cudaStream_t st);

@@ -577,21 +577,38 @@ csfmm_status run_passes(Plan &pl, Workspace &W, const double *w, int nrhs, doubl
     ++pl.launches;
   }
   CSFMM_MARK(CSFMM_PHASE_FAR);
-  for (int r0 = 0; r0 < nrhs; r0 += kRB) {
-    int nr = min(kRB, nrhs - r0);
-    if constexpr (sizeof(Real) == 4)
-      launch_far32(v, pl.ncells, W.wsf, wbar, ldr, r0, nr, psi, st);
-    else
+  // FP32 form, scalar kernels: chunks of 16 or 8 right-hand sides share every
+  // kernel value; the rest goes in chunks of up to kRB
+  const bool multi = sizeof(Real) == 4 && KID != CSFMM_KERNEL_BIOT_SAVART;
+  auto chunk = [&](int r0) {
+    const int left = nrhs - r0;
+    if (multi && left >= 16) return 16;
+    if (multi && left >= 8) return 8;
+    return min(kRB, left);
+  };
+  for (int r0 = 0; r0 < nrhs; r0 += chunk(r0)) {
+    const int nr = chunk(r0);
+    if constexpr (sizeof(Real) == 4) {
+      if (nr > kRB)
+        launch_multi32(v, true, pl.ncells, pl.leaves, W.wsf, wbar, ldr, r0, nr, W.phi, psi, st);
+      else
+        launch_far32(v, pl.ncells, W.wsf, wbar, ldr, r0, nr, psi, st);
+    } else {
       launch_far<KID, Real>(v, pl, W, nr, r0, tb_prox, wbar, psi, st);
+    }
     ++pl.launches;
   }
   CSFMM_MARK(CSFMM_PHASE_NEAR);
-  for (int r0 = 0; r0 < nrhs; r0 += kRB) {
-    int nr = min(kRB, nrhs - r0);
-    if constexpr (sizeof(Real) == 4)
-      launch_near32(v, pl.leaves, pl.nleaves, W.wsf, N, wbar, ldr, r0, nr, W.phi, st);
-    else
+  for (int r0 = 0; r0 < nrhs; r0 += chunk(r0)) {
+    const int nr = chunk(r0);
+    if constexpr (sizeof(Real) == 4) {
+      if (nr > kRB)
+        launch_multi32(v, false, pl.nleaves, pl.leaves, W.wsf, wbar, ldr, r0, nr, W.phi, psi, st);
+      else
+        launch_near32(v, pl.leaves, pl.nleaves, W.wsf, N, wbar, ldr, r0, nr, W.phi, st);
+    } else {
       launch_near<KID, Real>(v, pl, W, nr, r0, wbar, st);
+    }
     ++pl.launches;
   }
   CSFMM_MARK(CSFMM_PHASE_L2L);

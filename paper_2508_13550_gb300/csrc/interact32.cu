@@ -23,6 +23,8 @@
 // r = 0, every other tile runs unmasked.
 #include <math.h>
 
+#include <algorithm>
+
 #include "csfmm_internal.cuh"
 
 namespace csfmm {
@@ -656,6 +658,214 @@ void launch_far_kid(const PlanView &v, int ncells, const float *wsf, const float
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Several right-hand sides (NR = 8 or 16, scalar kernels): the kernel factor
+// of a (target, source) pair is computed once and applied to every
+// right-hand side with packed FMAs over pairs of right-hand sides.  Used for
+// both the near field (targets = particles of a leaf, PP and PC sources) and
+// the far field (targets = proxies of a cell, CP and CC sources).
+// ---------------------------------------------------------------------------
+template <int KID, int NT, int NR, bool SELF>
+__device__ __forceinline__ void tile_sum_multi(const float4 *__restrict__ sp,
+                                               const ulonglong2 *__restrict__ sw4, int nj,
+                                               const float (&tx)[NT], const float (&ty)[NT],
+                                               const float (&tz)[NT], const int (&self)[NT],
+                                               f2x (&acc)[NT][NR / 2]) {
+#pragma unroll 2
+  for (int j = 0; j < nj; ++j) {
+    const float4 s = sp[j];
+    f2x w2[NR / 2];
+#pragma unroll
+    for (int q = 0; q < NR / 4; ++q) {
+      const ulonglong2 u = sw4[j * (NR / 4) + q];
+      w2[2 * q] = u.x;
+      w2[2 * q + 1] = u.y;
+    }
+#pragma unroll
+    for (int k = 0; k < NT; ++k) {
+      const float rx = tx[k] - s.x, ry = ty[k] - s.y, rz = tz[k] - s.z;
+      const float d2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+      float f = kfactor<KID>(d2);
+      if constexpr (SELF) f = (j == self[k]) ? 0.0f : f;
+      const f2x ff = f2_pack(f, f);
+#pragma unroll
+      for (int q = 0; q < NR / 2; ++q) acc[k][q] = f2_fma(w2[q], ff, acc[k][q]);
+    }
+  }
+}
+
+// FAR = false: near field of leaf leaves[blockIdx.x] into phi (FP64);
+// FAR = true: far field of cell blockIdx.x into psi (FP32).  NT targets per
+// thread, strided by blockDim; each tile's FP32 sums are added to the
+// block-owned output rows, which hold the running per-target totals.
+// Targets per thread and threads per block of the near-field launch of the
+// multi-right-hand-side kernel.
+#ifndef CSFMM_MULTI_NT
+#define CSFMM_MULTI_NT 1
+#endif
+#ifndef CSFMM_MULTI_THREADS
+#define CSFMM_MULTI_THREADS 128
+#endif
+
+template <int KID, int NR, bool FAR>
+__global__ void __launch_bounds__(CSFMM_MULTI_THREADS) multi32_kernel(
+    PlanView v, const int32_t *leaves, const float *wsf, const float *wbar, int ldr, int r0,
+    double *phi, float *psi) {
+  constexpr int NT = CSFMM_MULTI_NT;
+  // one partial weight sum per warp; every launch uses at most
+  // CSFMM_MULTI_THREADS threads
+  static_assert(CSFMM_MULTI_THREADS % 32 == 0 && CSFMM_MULTI_THREADS <= 1024, "block size");
+  __shared__ float4 sp[kTile];
+  __shared__ ulonglong2 sw4[(NR / 4) * kTile];
+  __shared__ float wsum[NR][CSFMM_MULTI_THREADS / 32];
+  const int c = FAR ? (int)blockIdx.x : leaves[blockIdx.x];
+  const int P = v.P, nth = blockDim.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = nth >> 5;
+  const int tb = FAR ? 0 : v.cbegin[c];
+  const int te = FAR ? P : v.cend[c];
+  const double cTx = v.ccentre[3 * c], cTy = v.ccentre[3 * c + 1], cTz = v.ccentre[3 * c + 2];
+  const int64_t po = (int64_t)c * 3 * P;
+  float *swf = reinterpret_cast<float *>(sw4);
+  for (int i0 = tb; i0 < te; i0 += nth * NT) {
+    float ox[NT], oy[NT], oz[NT];
+#pragma unroll
+    for (int k = 0; k < NT; ++k) {
+      const int i = i0 + threadIdx.x + k * nth;
+      const int ii = i < te ? i : tb;
+      if (FAR) {
+        ox[k] = v.proxy32[po + ii]; oy[k] = v.proxy32[po + P + ii]; oz[k] = v.proxy32[po + 2 * P + ii];
+      } else {
+        const float4 o = v.off32[ii];
+        ox[k] = o.x; oy[k] = o.y; oz[k] = o.z;
+      }
+      if (i < te) {
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+          if (FAR) psi[((int64_t)c * ldr + r0 + q) * P + i] = 0.f;
+          else phi[(int64_t)(r0 + q) * v.N + i] = 0.0;
+        }
+      }
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+      const int type = FAR ? (pass == 0 ? CSFMM_LIST_CP : CSFMM_LIST_CC)
+                           : (pass == 0 ? CSFMM_LIST_PP : CSFMM_LIST_PC);
+      const bool particles = type == CSFMM_LIST_PP || type == CSFMM_LIST_CP;
+      const int e0 = v.loff[type][c], e1 = v.loff[type][c + 1];
+      for (int ee = e0; ee < e1; ++ee) {
+        const int s = v.lsrc[type][ee];
+        const float dcx = (float)(cTx - v.ccentre[3 * s]);
+        const float dcy = (float)(cTy - v.ccentre[3 * s + 1]);
+        const float dcz = (float)(cTz - v.ccentre[3 * s + 2]);
+        float tx[NT], ty[NT], tz[NT];
+#pragma unroll
+        for (int k = 0; k < NT; ++k) {
+          tx[k] = ox[k] + dcx;
+          ty[k] = oy[k] + dcy;
+          tz[k] = oz[k] + dcz;
+        }
+        const int sb = particles ? v.cbegin[s] : 0;
+        const int nsrc = particles ? v.cend[s] - sb : P;
+        const bool self_tile = !FAR && type == CSFMM_LIST_PP && s == c;
+        for (int j0 = 0; j0 < nsrc; j0 += kTile) {
+          const int nj = min(kTile, nsrc - j0);
+          __syncthreads();
+          float part[NR];
+#pragma unroll
+          for (int q = 0; q < NR; ++q) part[q] = 0.f;
+          for (int t = threadIdx.x; t < nj; t += nth) {
+            float wv[NR];
+            if (particles) {
+              const int j = sb + j0 + t;
+              sp[t] = v.off32[j];
+#pragma unroll
+              for (int q = 0; q < NR; ++q) wv[q] = wsf[(int64_t)(r0 + q) * v.N + j];
+            } else {
+              const int64_t so = (int64_t)s * 3 * P;
+              const int k = j0 + t;
+              sp[t] = make_float4(v.proxy32[so + k], v.proxy32[so + P + k], v.proxy32[so + 2 * P + k], 0.f);
+#pragma unroll
+              for (int q = 0; q < NR; ++q) wv[q] = wbar[((int64_t)s * ldr + r0 + q) * P + k];
+            }
+#pragma unroll
+            for (int q = 0; q < NR / 4; ++q)
+              reinterpret_cast<float4 *>(swf)[t * (NR / 4) + q] =
+                  make_float4(wv[4 * q], wv[4 * q + 1], wv[4 * q + 2], wv[4 * q + 3]);
+#pragma unroll
+            for (int q = 0; q < NR; ++q) part[q] += wv[q];
+          }
+          if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
+#pragma unroll
+            for (int q = 0; q < NR; ++q) {
+              float x = part[q];
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+              if (lane == 0) wsum[q][warp] = x;
+            }
+          }
+          __syncthreads();
+          f2x acc[NT][NR / 2];
+#pragma unroll
+          for (int k = 0; k < NT; ++k)
+#pragma unroll
+            for (int q = 0; q < NR / 2; ++q) acc[k][q] = 0ull;
+          int self[NT];
+#pragma unroll
+          for (int k = 0; k < NT; ++k) self[k] = (i0 + (int)threadIdx.x + k * nth) - (sb + j0);
+          if (self_tile)
+            tile_sum_multi<KID, NT, NR, true>(sp, sw4, nj, tx, ty, tz, self, acc);
+          else
+            tile_sum_multi<KID, NT, NR, false>(sp, sw4, nj, tx, ty, tz, self, acc);
+#pragma unroll
+          for (int k = 0; k < NT; ++k) {
+            const int i = i0 + threadIdx.x + k * nth;
+            if (i >= te) continue;
+#pragma unroll
+            for (int q = 0; q < NR / 2; ++q) {
+              float a2[2];
+              f2_unpack(acc[k][q], a2[0], a2[1]);
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                const int qq = 2 * q + h;
+                double val = (double)a2[h];
+                if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
+                  float tot = 0.f;
+                  for (int u = 0; u < nwarp; ++u) tot += wsum[qq][u];
+                  if (self_tile && self[k] >= 0 && self[k] < nj) tot -= swf[self[k] * NR + qq];
+                  val = -(0.69314718055994530942 * kInv4Pi) * (val - (double)tot);
+                }
+                if (FAR) psi[((int64_t)c * ldr + r0 + qq) * P + i] += (float)val;
+                else phi[(int64_t)(r0 + qq) * v.N + i] += val;
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
+template <int KID, int NR>
+void launch_multi(const PlanView &v, bool far, int ngrid, const int32_t *leaves, const float *wsf,
+                  const float *wbar, int ldr, int r0, double *phi, float *psi, cudaStream_t st) {
+  if (far) {
+    const int per = 32 * CSFMM_MULTI_NT;  // targets covered by one warp
+    const int nth = std::min(CSFMM_MULTI_THREADS, std::max(32, ((v.P + per - 1) / per) * 32));
+    multi32_kernel<KID, NR, true><<<ngrid, nth, 0, st>>>(v, leaves, wsf, wbar, ldr, r0, phi, psi);
+  } else {
+    multi32_kernel<KID, NR, false><<<ngrid, CSFMM_MULTI_THREADS, 0, st>>>(v, leaves, wsf, wbar,
+                                                                          ldr, r0, phi, psi);
+  }
+}
+
+template <int KID>
+void launch_multi_kid(const PlanView &v, bool far, int ngrid, const int32_t *leaves,
+                      const float *wsf, const float *wbar, int ldr, int r0, int nr, double *phi,
+                      float *psi, cudaStream_t st) {
+  if (nr == 16) launch_multi<KID, 16>(v, far, ngrid, leaves, wsf, wbar, ldr, r0, phi, psi, st);
+  else launch_multi<KID, 8>(v, far, ngrid, leaves, wsf, wbar, ldr, r0, phi, psi, st);
+}
+
 template <int KID, int NR>
 void launch_nr(const PlanView &v, const int32_t *leaves, int nleaves, const float *wsf, int ldw,
                const float *wbar, int ldr, int r0, double *phi, cudaStream_t st) {
@@ -678,6 +888,18 @@ void launch_kid(const PlanView &v, const int32_t *leaves, int nleaves, const flo
 }
 
 }  // namespace
+
+// Right-hand sides r0 .. r0+nr-1 with nr = 8 or 16 for the scalar kernels:
+// near field (far = false, one block per leaf) or far field (far = true).
+void launch_multi32(const PlanView &v, bool far, int ngrid, const int32_t *leaves,
+                    const float *wsf, const float *wbar, int ldr, int r0, int nr, double *phi,
+                    float *psi, cudaStream_t st) {
+  switch (v.kernel_id) {
+    case CSFMM_KERNEL_LAPLACE: launch_multi_kid<CSFMM_KERNEL_LAPLACE>(v, far, ngrid, leaves, wsf, wbar, ldr, r0, nr, phi, psi, st); break;
+    case CSFMM_KERNEL_NEWTON: launch_multi_kid<CSFMM_KERNEL_NEWTON>(v, far, ngrid, leaves, wsf, wbar, ldr, r0, nr, phi, psi, st); break;
+    default: launch_multi_kid<CSFMM_KERNEL_ONE>(v, far, ngrid, leaves, wsf, wbar, ldr, r0, nr, phi, psi, st); break;
+  }
+}
 
 // nr right-hand sides r0 .. r0+nr-1 (nr <= 4); psi [nc][ldr][dim][P] FP32.
 void launch_far32(const PlanView &v, int ncells, const float *wsf, const float *wbar, int ldr,

@@ -279,3 +279,25 @@ def test_argument_errors(torch, C):
     out = C.evaluate(P, torch.ones((1, 100), dtype=torch.float64, device="cuda"))
     torch.cuda.synchronize()
     assert np.isfinite(out.cpu().numpy()).all()
+
+
+@pytest.mark.parametrize("kernel,nrhs", [(O.KERNEL_LAPLACE, 16), (O.KERNEL_NEWTON, 9),
+                                         (O.KERNEL_ONE, 8), (O.KERNEL_BIOT_SAVART, 6)])
+def test_fp32_multi_rhs_matches_single_and_fp64(torch, C, kernel, nrhs):
+    """FP32-bulk with many right-hand sides (chunks of 16 / 8 share each kernel
+    value) against one-at-a-time FP32 evaluations and the FP64 FMM."""
+    pts, A = I.cubed_sphere_grid(48)
+    coeffs = I.random_sh_coeffs(6, nrhs, seed=kernel + 1)
+    W = I.sph_harm_combination(pts, coeffs, nrhs=nrhs) * A[None, :]
+    if kernel == O.KERNEL_ONE:
+        # K = 1 sums all weights: keep that sum away from zero (no cancellation)
+        W = W + A[None, :]
+    P32 = C.plan_create(dev(torch, pts), kernel, 8, 0.7, 64, precision=C.FP32_BULK, max_nrhs=nrhs)
+    P64 = C.plan_create(dev(torch, pts), kernel, 8, 0.7, 64, precision=C.FP64, max_nrhs=nrhs)
+    dW = dev(torch, W)
+    allr = C.evaluate(P32, dW).cpu().numpy()
+    ref = C.evaluate(P64, dW).cpu().numpy()
+    for r in range(nrhs):
+        one = C.evaluate(P32, dW[r:r + 1].contiguous()).cpu().numpy()[0]
+        assert rel(allr[r], one) <= 1e-5, (r, rel(allr[r], one))
+        assert rel(allr[r], ref[r]) <= 1e-5, (r, rel(allr[r], ref[r]))
