@@ -681,14 +681,14 @@ static int fmm_evaluate(oplan *pl, int kid, const double *w, int nrhs,
   for (int r = 0; r < nrhs; ++r)
     for (int64_t i = 0; i < N; ++i) ws[(int64_t)r * N + i] = w[(int64_t)r * N + pl->order[i]];
 
-  /* Line 5: upward pass */
+  /* Algorithm "CSFMM": upward pass */
   double *wbar = (double *)malloc(sizeof(double) * (size_t)nc * (size_t)nrhs * (size_t)P);
   upward_pass(pl, ws, nrhs, wbar);
 
   int64_t *off[4]; int *src[4];
   for (int ty = 0; ty < 4; ++ty) group_by_target(pl, ty, &off[ty], &src[ty]);
 
-  /* Lines 11-15: CP and CC proxy potentials, accumulated per target cell
+  /* CP and CC proxy potentials, accumulated per target cell
    * (Eq. CP_CC_accumulated).  psi[c][r][m][d]. */
   size_t psz = (size_t)nc * (size_t)nrhs * (size_t)P * (size_t)dim;
   double *psi = (double *)calloc(psz, sizeof(double));
@@ -724,7 +724,7 @@ static int fmm_evaluate(oplan *pl, int kid, const double *w, int nrhs,
     }
   }
 
-  /* Lines 10 and 19: PC and PP potentials at the target particles. */
+  /* PC and PP potentials at the target particles. */
   double *phi = (double *)calloc((size_t)N * (size_t)nrhs * (size_t)dim, sizeof(double));
 #pragma omp parallel for schedule(dynamic, 1)
   for (int t = 0; t < nc; ++t) {
@@ -766,7 +766,7 @@ static int fmm_evaluate(oplan *pl, int kid, const double *w, int nrhs,
     free(a);
   }
 
-  /* Line 20: downward pass.  L2L through all levels (Eq. downward_2) ... */
+  /* Downward pass.  L2L through all levels (Eq. downward_2) ... */
   for (int l = 0; l + 1 < pl->nlevels; ++l) {
     if (g_mutation == 9 && l == pl->nlevels - 2) continue;
 #pragma omp parallel for schedule(dynamic, 4)
@@ -819,7 +819,7 @@ static int fmm_evaluate(oplan *pl, int kid, const double *w, int nrhs,
     }
   }
 
-  /* Line 21: output */
+  /* Output */
   if (tgt) {
     for (int r = 0; r < nrhs; ++r)
       for (int64_t t = 0; t < ntgt; ++t)
