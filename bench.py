@@ -361,7 +361,7 @@ def main():
     ap.add_argument("--workload", default="newton-6m", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--err-samples", type=int, default=2048)
-    ap.add_argument("--cpu-leaves", type=int, default=8192)
+    ap.add_argument("--cpu-leaves", type=int, default=16384)
     ap.add_argument("--ref-leaves", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", dest="fp64_compare", action="store_false")

@@ -73,7 +73,10 @@ enum { CSFMM_LIST_PP = 0, CSFMM_LIST_PC = 1, CSFMM_LIST_CP = 2, CSFMM_LIST_CC = 
 typedef struct {
   int precision;  /* CSFMM_FP64 (default) or CSFMM_FP32_BULK */
   int max_nrhs;   /* right-hand sides processed per pass; larger nrhs is split (default 16) */
-  int use_graphs; /* 1: replay evaluate passes from a captured CUDA graph (default 0) */
+  int use_graphs; /* 1: the first evaluation of each right-hand-side count on a stream other
+                     than the legacy default stream is captured into a CUDA graph that later
+                     evaluations replay (only the weight and output pointers are updated);
+                     evaluations with phase timing enabled are launched directly (default 0) */
   int reserved[5];
 } csfmm_options;
 
@@ -176,8 +179,12 @@ csfmm_status csfmm_evaluate_static(csfmm_plan plan, const double *weights, int n
  *   points  device [N][3]; weights device [nrhs][N]; out device [nrhs][N][dim]
  *   precision CSFMM_FP64 (per-target compensated FP64 sums) or CSFMM_FP32_BULK
  *             (FP32 kernel values on FP64-differenced coordinates, FP64
- *             accumulation across 256-source tiles)
- * Errors: INVALID_ARG, CUDA. */
+ *             accumulation across 128-source tiles)
+ * When there are few targets the sources are split across thread blocks; the
+ * partial sums then live in temporary device memory allocated and freed in
+ * stream order (cudaMallocAsync / cudaFreeAsync) and are reduced in a fixed
+ * order, so results are deterministic.
+ * Errors: INVALID_ARG, CUDA, OUT_OF_MEMORY. */
 csfmm_status csfmm_direct(const double *points, int64_t N, int kernel_id, const double *weights,
                           int nrhs, double *out, int precision, void *stream);
 

@@ -260,6 +260,7 @@ csfmm_status csfmm_workspace_create(csfmm_plan plan, int max_nrhs, csfmm_workspa
 
 csfmm_status csfmm_workspace_destroy(csfmm_workspace ws) {
   if (!ws) return CSFMM_OK;
+  ws->impl.release_graphs();
   ws->impl.arena.release();
   delete ws;
   return CSFMM_OK;
@@ -470,6 +471,7 @@ csfmm_status csfmm_plan_destroy(csfmm_plan plan) {
   for (cudaEvent_t e : pl.events) cudaEventDestroy(e);
   pl.events.clear();
   if (pl.ws) {
+    pl.ws->release_graphs();
     pl.ws->arena.release();
     delete pl.ws;
     pl.ws = nullptr;

@@ -143,9 +143,32 @@ struct Plan {
   PlanView view() const;
 };
 
+// A captured evaluation of one right-hand-side count, replayed with
+// cudaGraphLaunch; only the gather node (reads the caller's weights) and the
+// L2P node (writes the caller's output) change between calls.
+struct GraphEntry {
+  int nrhs = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t gather = nullptr, l2p = nullptr;
+  cudaKernelNodeParams gather_params{}, l2p_params{};
+  const double *w = nullptr;
+  double *out = nullptr;
+  int launches = 0;
+};
+
 struct Workspace {
   Plan *plan = nullptr;
   int max_nrhs = 0;
+  bool graphs_ok = true;            // false for short-lived workspaces
+  std::vector<GraphEntry> graphs;   // captured evaluations (use_graphs)
+  void release_graphs() {
+    for (GraphEntry &g : graphs) {
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+      if (g.graph) cudaGraphDestroy(g.graph);
+    }
+    graphs.clear();
+  }
   DeviceArena arena;
   double *ws = nullptr;     // [max_nrhs][N] weights in tree order
   float *wsf = nullptr;     // [max_nrhs][N] the same in FP32 (FP32 form only)

@@ -1,6 +1,6 @@
 // direct.cu -- direct summation of Eq. (nbodysum), phi_i = sum_{j != i} K(x_i, x_j) w_j
 // (Sec. 1), tiled: one thread per target, sources staged through shared memory
-// in tiles of kTile points.  FP64 form: FP64 kernel values, plain sums within a
+// in tiles of kTile points (split across grid rows when there are few targets).  FP64 form: FP64 kernel values, plain sums within a
 // tile and Neumaier-compensated sums across tiles.  FP32 form: the difference
 // x_i - y_j is formed in FP64 and rounded once, kernel values and tile sums in
 // FP32, FP64 sums across tiles.
@@ -22,9 +22,13 @@ __device__ __forceinline__ void neumaier(double &s, double &c, double v) {
   s = t;
 }
 
+// Sources [j_lo, j_hi) of split blockIdx.y, j_lo = blockIdx.y * chunk.  With one
+// split the result goes to out[r][t][d]; with several, each split writes its
+// (sum, compensation) pair to part[split][r][t][d][2] for a fixed-order reduction.
 template <int KID, typename Real>
 __global__ void direct_kernel(const double *pts, int N, const double *w, int r0, int nr,
-                              const int64_t *targets, int nt, double *out) {
+                              const int64_t *targets, int nt, double *out, int chunk,
+                              double *part, int64_t n_out) {
   constexpr int DIM = KID == CSFMM_KERNEL_BIOT_SAVART ? 3 : 1;
   __shared__ double sx[kTile], sy[kTile], sz[kTile];
   __shared__ Real sw[kRBd * kTile];
@@ -43,8 +47,10 @@ __global__ void direct_kernel(const double *pts, int N, const double *w, int r0,
   for (int q = 0; q < kRBd; ++q)
 #pragma unroll
     for (int d = 0; d < DIM; ++d) s[q][d] = c[q][d] = 0.0;
-  for (int j0 = 0; j0 < N; j0 += kTile) {
-    const int nj = min(kTile, N - j0);
+  const int j_lo = (int)min((int64_t)blockIdx.y * chunk, (int64_t)N);
+  const int j_hi = (int)min((int64_t)j_lo + chunk, (int64_t)N);
+  for (int j0 = j_lo; j0 < j_hi; j0 += kTile) {
+    const int nj = min(kTile, j_hi - j0);
     __syncthreads();
     for (int u = threadIdx.x; u < nj; u += blockDim.x) {
       const int64_t j = j0 + u;
@@ -101,33 +107,85 @@ __global__ void direct_kernel(const double *pts, int N, const double *w, int r0,
   if (active) {
     for (int q = 0; q < nr; ++q)
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) out[((int64_t)(r0 + q) * nt + t) * DIM + d] = s[q][d] + c[q][d];
+      for (int d = 0; d < DIM; ++d) {
+        const int64_t o = ((int64_t)(r0 + q) * nt + t) * DIM + d;
+        if (part) {
+          double *pp = part + 2 * ((int64_t)blockIdx.y * n_out + o);
+          pp[0] = s[q][d];
+          pp[1] = c[q][d];
+        } else {
+          out[o] = s[q][d] + c[q][d];
+        }
+      }
   }
 }
 
+// out[o] = Neumaier sum over splits of part[split][o] (o over nrhs * nt * dim).
+__global__ void direct_reduce_kernel(const double *part, int nsplit, int64_t n_out, double *out) {
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n_out;
+       o += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0, c = 0.0;
+    for (int k = 0; k < nsplit; ++k) {
+      neumaier(s, c, part[2 * (k * n_out + o)]);
+      c += part[2 * (k * n_out + o) + 1];
+    }
+    out[o] = s + c;
+  }
+}
+
+// Few target tiles cannot fill the GPU; then the sources are split into
+// nsplit chunks (one grid row each) whose partial sums are reduced in a fixed
+// order, so results do not depend on scheduling.
 template <typename Real>
 csfmm_status launch_direct(const double *pts, int N, int kid, const double *w, int nrhs,
                            const int64_t *targets, int nt, double *out, cudaStream_t st) {
-  int grid = grid_for(nt, kTile);
-  for (int r0 = 0; r0 < nrhs; r0 += kRBd) {
+  const int tiles = grid_for(nt, kTile);
+  const int dim = kid == CSFMM_KERNEL_BIOT_SAVART ? 3 : 1;
+  int nsplit = 1;
+  if (tiles < 4 * 152) {
+    nsplit = (4 * 152 + tiles - 1) / tiles;
+    const int max_split = (N + 4 * kTile - 1) / (4 * kTile);  // at least 4 tiles per split
+    if (nsplit > max_split) nsplit = max_split;
+    if (nsplit > 2048) nsplit = 2048;
+    if (nsplit < 1) nsplit = 1;
+  }
+  const int chunk = (N + nsplit - 1) / nsplit;
+  const int64_t n_out = (int64_t)nrhs * nt * dim;
+  double *part = nullptr;
+  if (nsplit > 1) {
+    CSFMM_CUDA(cudaMallocAsync((void **)&part, sizeof(double) * 2 * (size_t)nsplit * n_out, st));
+  }
+  dim3 grid(tiles, nsplit);
+  csfmm_status result = CSFMM_OK;
+  for (int r0 = 0; r0 < nrhs && result == CSFMM_OK; r0 += kRBd) {
     int nr = min(kRBd, nrhs - r0);
     switch (kid) {
       case CSFMM_KERNEL_LAPLACE:
-        direct_kernel<CSFMM_KERNEL_LAPLACE, Real><<<grid, kTile, 0, st>>>(pts, N, w, r0, nr, targets, nt, out);
+        direct_kernel<CSFMM_KERNEL_LAPLACE, Real><<<grid, kTile, 0, st>>>(pts, N, w, r0, nr, targets, nt, out, chunk, part, n_out);
         break;
       case CSFMM_KERNEL_BIOT_SAVART:
-        direct_kernel<CSFMM_KERNEL_BIOT_SAVART, Real><<<grid, kTile, 0, st>>>(pts, N, w, r0, nr, targets, nt, out);
+        direct_kernel<CSFMM_KERNEL_BIOT_SAVART, Real><<<grid, kTile, 0, st>>>(pts, N, w, r0, nr, targets, nt, out, chunk, part, n_out);
         break;
       case CSFMM_KERNEL_NEWTON:
-        direct_kernel<CSFMM_KERNEL_NEWTON, Real><<<grid, kTile, 0, st>>>(pts, N, w, r0, nr, targets, nt, out);
+        direct_kernel<CSFMM_KERNEL_NEWTON, Real><<<grid, kTile, 0, st>>>(pts, N, w, r0, nr, targets, nt, out, chunk, part, n_out);
         break;
       default:
-        direct_kernel<CSFMM_KERNEL_ONE, Real><<<grid, kTile, 0, st>>>(pts, N, w, r0, nr, targets, nt, out);
+        direct_kernel<CSFMM_KERNEL_ONE, Real><<<grid, kTile, 0, st>>>(pts, N, w, r0, nr, targets, nt, out, chunk, part, n_out);
         break;
     }
-    CSFMM_CUDA(cudaGetLastError());
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) result = cuda_status(e, "direct_kernel launch");
   }
-  return CSFMM_OK;
+  if (part) {
+    if (result == CSFMM_OK) {
+      direct_reduce_kernel<<<grid_for(n_out, 256, 152 * 8), 256, 0, st>>>(part, nsplit, n_out, out);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) result = cuda_status(e, "direct_reduce_kernel launch");
+    }
+    cudaError_t e = cudaFreeAsync(part, st);
+    if (e != cudaSuccess && result == CSFMM_OK) result = cuda_status(e, "cudaFreeAsync");
+  }
+  return result;
 }
 
 }  // namespace

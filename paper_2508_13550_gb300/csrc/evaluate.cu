@@ -677,7 +677,99 @@ csfmm_status workspace_alloc(Plan &pl, Workspace &W, int max_nrhs) {
   return CSFMM_OK;
 }
 
-// Evaluates nrhs <= W.max_nrhs right-hand sides.
+namespace {
+
+csfmm_status enqueue(Plan &pl, Workspace &W, const double *w, int nrhs, double *out,
+                     cudaStream_t st) {
+  if (pl.precision == CSFMM_FP64) return dispatch_kernel<double>(pl, W, w, nrhs, out, st);
+  return dispatch_kernel<float>(pl, W, w, nrhs, out, st);
+}
+
+// Captures one evaluation into a graph and records its gather and L2P nodes.
+csfmm_status capture(Plan &pl, Workspace &W, const double *w, int nrhs, double *out,
+                     cudaStream_t st, GraphEntry &g) {
+  CSFMM_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  csfmm_status s = enqueue(pl, W, w, nrhs, out, st);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(st, &graph);
+  if (s != CSFMM_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return s;
+  }
+  if (e != cudaSuccess) return cuda_status(e, "cudaStreamEndCapture");
+  g.graph = graph;
+  size_t n = 0;
+  CSFMM_CUDA(cudaGraphGetNodes(graph, nullptr, &n));
+  std::vector<cudaGraphNode_t> nodes(n);
+  CSFMM_CUDA(cudaGraphGetNodes(graph, nodes.data(), &n));
+  const void *f_gather = (const void *)gather_kernel;
+  const void *f_l2p = pl.precision == CSFMM_FP64 ? (const void *)l2p_kernel<double>
+                                                 : (const void *)l2p_kernel<float>;
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType ty;
+    CSFMM_CUDA(cudaGraphNodeGetType(nd, &ty));
+    if (ty != cudaGraphNodeTypeKernel) continue;
+    cudaKernelNodeParams kp{};
+    CSFMM_CUDA(cudaGraphKernelNodeGetParams(nd, &kp));
+    if (kp.func == f_gather) {
+      g.gather = nd;
+      g.gather_params = kp;
+    } else if (kp.func == f_l2p) {
+      g.l2p = nd;
+      g.l2p_params = kp;
+    }
+  }
+  if (!g.gather || !g.l2p) {
+    set_error("graph capture: gather or L2P node not found");
+    return CSFMM_ERR_CUDA;
+  }
+  CSFMM_CUDA(cudaGraphInstantiate(&g.exec, graph, 0));
+  g.nrhs = nrhs;
+  g.w = w;
+  g.out = out;
+  g.launches = pl.launches;
+  return CSFMM_OK;
+}
+
+// Points the captured gather and L2P nodes at new caller buffers; the other
+// arguments are rebuilt from the plan and workspace exactly as at capture.
+csfmm_status retarget(Plan &pl, Workspace &W, GraphEntry &g, const double *w, double *out) {
+  const int N = (int)pl.N;
+  {
+    const int32_t *perm = pl.perm;
+    double *ws = W.ws;
+    float *wsf = pl.precision == CSFMM_FP64 ? nullptr : W.wsf;
+    int nrhs = g.nrhs, ld = N, n = N;
+    void *args[] = {(void *)&perm, (void *)&w, (void *)&ws, (void *)&wsf, (void *)&n,
+                    (void *)&nrhs, (void *)&ld};
+    cudaKernelNodeParams kp = g.gather_params;
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    CSFMM_CUDA(cudaGraphExecKernelNodeSetParams(g.exec, g.gather, &kp));
+  }
+  {
+    PlanView v = pl.view();
+    const int32_t *leaves = pl.leaves;
+    const void *psi = W.psi;
+    int ldr = W.max_nrhs, nrhs = g.nrhs, dim = pl.dim;
+    const double *phi = W.phi;
+    void *args[] = {(void *)&v, (void *)&leaves, (void *)&psi, (void *)&ldr, (void *)&nrhs,
+                    (void *)&dim, (void *)&phi, (void *)&out};
+    cudaKernelNodeParams kp = g.l2p_params;
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    CSFMM_CUDA(cudaGraphExecKernelNodeSetParams(g.exec, g.l2p, &kp));
+  }
+  g.w = w;
+  g.out = out;
+  return CSFMM_OK;
+}
+
+}  // namespace
+
+// Evaluates nrhs <= W.max_nrhs right-hand sides.  With use_graphs (and no
+// phase timing, on a stream other than the legacy default stream) the launch
+// sequence is captured once per right-hand-side count and replayed.
 csfmm_status evaluate_impl(Plan &pl, Workspace &W, const double *w, int nrhs, double *out,
                            cudaStream_t st) {
   if (nrhs > W.max_nrhs) {
@@ -685,8 +777,29 @@ csfmm_status evaluate_impl(Plan &pl, Workspace &W, const double *w, int nrhs, do
     return CSFMM_ERR_INVALID_ARG;
   }
   W.last_nrhs = nrhs;
-  if (pl.precision == CSFMM_FP64) return dispatch_kernel<double>(pl, W, w, nrhs, out, st);
-  return dispatch_kernel<float>(pl, W, w, nrhs, out, st);
+  const bool graphs = pl.use_graphs && W.graphs_ok && !pl.timing && st != nullptr &&
+                      st != cudaStreamLegacy && st != cudaStreamPerThread;
+  if (!graphs) return enqueue(pl, W, w, nrhs, out, st);
+  GraphEntry *g = nullptr;
+  for (GraphEntry &e : W.graphs)
+    if (e.nrhs == nrhs) g = &e;
+  if (!g) {
+    GraphEntry ne;
+    csfmm_status s = capture(pl, W, w, nrhs, out, st, ne);
+    if (s != CSFMM_OK) {
+      if (ne.exec) cudaGraphExecDestroy(ne.exec);
+      if (ne.graph) cudaGraphDestroy(ne.graph);
+      return s;
+    }
+    W.graphs.push_back(ne);
+    g = &W.graphs.back();
+  } else if (g->w != w || g->out != out) {
+    csfmm_status s = retarget(pl, W, *g, w, out);
+    if (s != CSFMM_OK) return s;
+  }
+  pl.stats.launches_per_evaluate = g->launches;
+  CSFMM_CUDA(cudaGraphLaunch(g->exec, st));
+  return CSFMM_OK;
 }
 
 }  // namespace csfmm

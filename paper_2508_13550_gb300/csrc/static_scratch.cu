@@ -96,6 +96,7 @@ extern "C" csfmm_status csfmm_evaluate_static(csfmm_plan plan, const double *wei
   // Every scratch buffer is fully written before it is read (gather, P2M/M2M,
   // far, near), so nothing needs clearing between calls.
   Workspace W;
+  W.graphs_ok = false;  // W lives only for this call
   W.plan = &pl;
   W.max_nrhs = nrhs;
   W.ws = reinterpret_cast<double *>(base);
