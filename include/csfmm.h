@@ -226,6 +226,69 @@ csfmm_status csfmm_plan_export_proxy_weights(csfmm_plan plan, int nrhs, double *
 csfmm_status csfmm_plan_enable_timing(csfmm_plan plan, int on);
 csfmm_status csfmm_plan_phase_times(csfmm_plan plan, double *ms, int64_t *calls);
 
+/* ------------------------------------------------------------------------
+ * Serving (continuous batching).  No counterpart in the paper: a request
+ * loop that keeps plans resident on the device, admits requests as slots and
+ * device memory free up, and runs admitted evaluations concurrently on
+ * separate streams.
+ *
+ * A request names a point set by the caller's key (plan_key, e.g. the grid
+ * size) plus its method parameters; plans are cached by (plan_key, kernel_id,
+ * degree, theta, max_leaf, precision) and built from `points` the first time.
+ * Admission is first-come first-served: the head request starts when a slot
+ * is free and the memory it needs (its plan if not cached, plus a workspace
+ * for up to CSFMM_SERVER_MAX_NRHS right-hand sides if none is idle) fits in
+ * hbm_budget_bytes next to what is held; idle cached plans are evicted (least
+ * recently used) to make room.  Plans are built with use_graphs = 1.
+ * ------------------------------------------------------------------------ */
+#define CSFMM_SERVER_MAX_NRHS 8
+typedef struct csfmm_server_s *csfmm_server;
+
+typedef struct {
+  const double *points;  /* device [N][3]; read only when the plan is built */
+  int64_t N;
+  uint64_t plan_key;     /* caller's identity of the point set */
+  int kernel_id, degree, max_leaf, precision;
+  double theta;
+  const double *weights; /* device [nrhs][N], valid until the request completes */
+  int nrhs;              /* 1 .. CSFMM_SERVER_MAX_NRHS */
+  double *out;           /* device [nrhs][N][dim], written by the request */
+} csfmm_request;
+
+typedef struct {
+  int status;            /* csfmm_status of the request */
+  double submit_ms;      /* host clock (ms since the server was created) at submit */
+  double admit_ms;       /* ... when its evaluation was enqueued */
+  double done_ms;        /* ... when the scheduler saw its completion event */
+  double gpu_ms;         /* CUDA-event time of the evaluation on its slot stream */
+  int slot;              /* slot (stream) that ran it */
+  int built_plan;        /* 1 if the request built its plan */
+} csfmm_request_timing;
+
+typedef struct {
+  int64_t submitted, completed, failed, plans_built, plans_evicted;
+  int64_t bytes_held, peak_bytes_held, budget_bytes;
+  int slots, max_in_flight;
+} csfmm_server_stats;
+
+/* Creates a server on the current device with `slots` concurrent evaluation
+ * slots (1..64) and a device-memory budget for plans and workspaces.
+ * Errors: INVALID_ARG, CUDA. */
+csfmm_status csfmm_server_create(int64_t hbm_budget_bytes, int slots, csfmm_server *out);
+/* Queues a request (copied; the buffers it points to must stay valid until
+ * it completes) and returns its id.  Never blocks.  Errors: INVALID_ARG;
+ * OUT_OF_MEMORY if the request alone can never fit the budget. */
+csfmm_status csfmm_server_submit(csfmm_server s, const csfmm_request *req, int64_t *id);
+/* *done = 1 and *timing filled when request id has completed (or failed). */
+csfmm_status csfmm_server_poll(csfmm_server s, int64_t id, int *done, csfmm_request_timing *timing);
+/* Blocks until request id completes; returns its status. */
+csfmm_status csfmm_server_wait(csfmm_server s, int64_t id, csfmm_request_timing *timing);
+/* Blocks until every submitted request has completed. */
+csfmm_status csfmm_server_drain(csfmm_server s);
+csfmm_status csfmm_server_stats_get(csfmm_server s, csfmm_server_stats *stats);
+/* Drains, then frees every plan, workspace and stream of the server. */
+csfmm_status csfmm_server_destroy(csfmm_server s);
+
 /* Waits for the plan's work on stream and returns a deferred device status
  * (CSFMM_ERR_DEVICE / CSFMM_ERR_TIMEOUT) if a kernel reported one. */
 csfmm_status csfmm_plan_sync(csfmm_plan plan, void *stream);

@@ -65,6 +65,34 @@ class Stats(ctypes.Structure):
         return d
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("points", ctypes.c_void_p), ("N", ctypes.c_int64), ("plan_key", ctypes.c_uint64),
+                ("kernel_id", ctypes.c_int), ("degree", ctypes.c_int), ("max_leaf", ctypes.c_int),
+                ("precision", ctypes.c_int), ("theta", ctypes.c_double),
+                ("weights", ctypes.c_void_p), ("nrhs", ctypes.c_int), ("out", ctypes.c_void_p)]
+
+
+class RequestTiming(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("submit_ms", ctypes.c_double),
+                ("admit_ms", ctypes.c_double), ("done_ms", ctypes.c_double),
+                ("gpu_ms", ctypes.c_double), ("slot", ctypes.c_int), ("built_plan", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("submitted", "completed", "failed", "plans_built",
+                                              "plans_evicted", "bytes_held", "peak_bytes_held",
+                                              "budget_bytes")] + \
+               [("slots", ctypes.c_int), ("max_in_flight", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+SERVER_MAX_NRHS = 8
+
 _VP, _I64, _I32, _D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
 _SIGS = {
     "csfmm_plan_create": [_VP, _I64, ctypes.c_int, ctypes.c_int, _D, ctypes.c_int,
@@ -88,6 +116,13 @@ _SIGS = {
     "csfmm_plan_phase_times": [_VP, _VP, _VP],
     "csfmm_plan_sync": [_VP, _VP],
     "csfmm_plan_destroy": [_VP],
+    "csfmm_server_create": [_I64, ctypes.c_int, ctypes.POINTER(_VP)],
+    "csfmm_server_submit": [_VP, ctypes.POINTER(Request), ctypes.POINTER(_I64)],
+    "csfmm_server_poll": [_VP, _I64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(RequestTiming)],
+    "csfmm_server_wait": [_VP, _I64, ctypes.POINTER(RequestTiming)],
+    "csfmm_server_drain": [_VP],
+    "csfmm_server_stats_get": [_VP, ctypes.POINTER(ServerStats)],
+    "csfmm_server_destroy": [_VP],
     "csfmm_last_error": [],
     "csfmm_version": [],
 }
@@ -334,6 +369,58 @@ def plan_phase_times(plan: Plan):
 
 def plan_sync(plan: Plan, stream=None):
     _check(load().csfmm_plan_sync(plan.handle, _stream(stream)))
+
+
+class Server:
+    """csfmm_server: continuous batching over resident plans (one scheduler
+    thread in the library; this class only marshals arguments)."""
+
+    def __init__(self, budget_bytes: int, slots: int):
+        self.handle = ctypes.c_void_p()
+        _check(load().csfmm_server_create(int(budget_bytes), int(slots), ctypes.byref(self.handle)))
+
+    def submit(self, points, plan_key, kernel_id, degree, theta, max_leaf, precision, weights,
+               out):
+        """Queues a request; points, weights and out are CUDA tensors that must
+        stay alive until the request completes.  Returns the request id."""
+        import torch
+        req = Request(_dev(points, torch.float64).value, points.shape[0], int(plan_key),
+                      int(kernel_id), int(degree), int(max_leaf), int(precision), float(theta),
+                      _dev(weights, torch.float64).value, weights.shape[0],
+                      _dev(out, torch.float64).value)
+        rid = ctypes.c_int64()
+        _check(load().csfmm_server_submit(self.handle, ctypes.byref(req), ctypes.byref(rid)))
+        return rid.value
+
+    def poll(self, rid):
+        done = ctypes.c_int()
+        t = RequestTiming()
+        _check(load().csfmm_server_poll(self.handle, rid, ctypes.byref(done), ctypes.byref(t)))
+        return bool(done.value), t.as_dict()
+
+    def wait(self, rid):
+        t = RequestTiming()
+        rc = load().csfmm_server_wait(self.handle, rid, ctypes.byref(t))
+        return rc, t.as_dict()
+
+    def drain(self):
+        _check(load().csfmm_server_drain(self.handle))
+
+    def stats(self):
+        s = ServerStats()
+        _check(load().csfmm_server_stats_get(self.handle, ctypes.byref(s)))
+        return s.as_dict()
+
+    def close(self):
+        if self.handle:
+            _check(load().csfmm_server_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def last_error() -> str:

@@ -10,9 +10,6 @@
 
 #include "csfmm_internal.cuh"
 
-struct csfmm_workspace_s {
-  csfmm::Workspace impl;
-};
 
 namespace csfmm {
 

@@ -183,9 +183,12 @@ struct Workspace {
 
 }  // namespace csfmm
 
-// The opaque handle of include/csfmm.h wraps one Plan.
+// The opaque handles of include/csfmm.h wrap one Plan / one Workspace.
 struct csfmm_plan_s {
   csfmm::Plan impl;
+};
+struct csfmm_workspace_s {
+  csfmm::Workspace impl;
 };
 
 namespace csfmm {
