@@ -339,6 +339,8 @@ def run_ours(args):
                                     "evals/clk/SM"},
         "clocks": clk.summary(),
     }
+    if rank == 0 and world == 1 and args.serve_sample > 0:
+        line["serving"] = run_serving(args, sample=args.serve_sample)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, dt, ntg, cores = cpu_oracle_sample(pts, w[:1], wl, args.cpu_leaves, 3)
         line["cpu_baseline"] = {"value": v, "unit": "targets/s", "cores": cores, "kind": "oracle",
@@ -352,24 +354,72 @@ def run_ours(args):
     return 0
 
 
+def run_serving(args, sample=None):
+    """Serving stream (seeded requests: m ~ U{64..1024}, kernel ~ U{Laplace,
+    Biot-Savart, Newtonian}, 1-8 RHS, degree 8-12, FP32 bulk, N0 = 4 n^2):
+    warm-up requests fill the plan cache, a burst measures the saturation
+    request rate, then the stream runs with Poisson arrivals at 70% of it.
+    Returns the summary dict."""
+    import torch
+    from paper_2508_13550_gb300 import csfmm as Cs
+    from paper_2508_13550_gb300 import inputs as I
+    from paper_2508_13550_gb300 import serving as S
+    n_req = sample or args.serve_requests
+    ms = (64, 128, 256, 512, 1024)
+    grids = S.DeviceGrids(ms, torch.device("cuda", torch.cuda.current_device()))
+    server = Cs.Server(budget_bytes=int(args.serve_budget_gb * (1 << 30)), slots=args.serve_slots)
+    warm = I.serving_requests(120, rate_hz=1e6, seed=I.MASTER_SEED + 50)
+    S.run_stream(server, grids, warm, rate_hz=None)
+    burst = I.serving_requests(min(200, n_req), rate_hz=1e6, seed=I.MASTER_SEED + 51)
+    sat = S.summarize(S.run_stream(server, grids, burst, rate_hz=None))
+    rate = 0.7 * sat["requests_per_s"]
+    reqs = I.serving_requests(n_req, rate_hz=rate, seed=I.MASTER_SEED + 5)
+    recs = S.run_stream(server, grids, reqs, rate_hz=rate)
+    summ = S.summarize(recs)
+    st = server.stats()
+    server.close()
+    summ.update({"arrival_rate_hz": rate, "saturation_requests_per_s": sat["requests_per_s"],
+                 "saturation_targets_per_s": sat["targets_per_s"], "slots": args.serve_slots,
+                 "budget_gb": args.serve_budget_gb, "plans_built": st["plans_built"],
+                 "plans_evicted": st["plans_evicted"],
+                 "peak_bytes_held_gb": st["peak_bytes_held"] / 2 ** 30,
+                 "max_in_flight": st["max_in_flight"]})
+    return summ
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="newton-6m", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="newton-6m", choices=sorted(WORKLOADS) + ["serving"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--err-samples", type=int, default=2048)
     ap.add_argument("--cpu-leaves", type=int, default=16384)
     ap.add_argument("--ref-leaves", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", dest="fp64_compare", action="store_false")
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-sample", type=int, default=300,
+                    help="requests of the serving stream measured in the default line (0: none)")
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-budget-gb", type=float, default=96.0)
     args = ap.parse_args()
     if args.warmup < 3:
         log("warning: fewer than 3 warm-up steps")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serving":
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        summ = run_serving(args)
+        print(json.dumps({"metric": "serving p50/p99 latency", "value": summ["p99_ms"],
+                          "unit": "ms (p99)", "higher_is_better": False, "n_gpus": 1,
+                          "dtype": "f32", "data": "synthetic",
+                          "config": {"workload": "serving", "requests": summ["requests"]},
+                          "serving": summ}), flush=True)
+        return 0
     return run_ours(args)
 
 
