@@ -77,7 +77,9 @@ typedef struct {
                      than the legacy default stream is captured into a CUDA graph that later
                      evaluations replay (only the weight and output pointers are updated);
                      evaluations with phase timing enabled are launched directly (default 0) */
-  int reserved[5];
+  int rhs_chunk;  /* FP32 bulk, scalar kernels: right-hand sides sharing one kernel evaluation
+                     in the interaction kernels, 16, 8 or 4 (0 = 16) */
+  int reserved[4];
 } csfmm_options;
 
 typedef struct csfmm_plan_s *csfmm_plan;
@@ -193,6 +195,32 @@ csfmm_status csfmm_direct(const double *points, int64_t N, int kernel_id, const 
 csfmm_status csfmm_direct_targets(const double *points, int64_t N, int kernel_id,
                                   const double *weights, int nrhs, const int64_t *targets,
                                   int64_t ntargets, double *out, int precision, void *stream);
+
+/* Autotuner (no counterpart in the paper).  Builds plans of the given point
+ * set with maximum leaf sizes N0 in {n^2, 2n^2, 3n^2, 4n^2, 6n^2, 8n^2} (at
+ * least 8) and, for several right-hand sides in the FP32-bulk form, right-hand-
+ * side chunks of 16, 8 and 4; times three evaluations of each with CUDA events
+ * and measures the relative l2 error of the first right-hand side against an
+ * FP64 direct sum on up to 256 fixed sampled targets.  It returns the fastest
+ * candidate whose error is at most err_factor times the error of the paper's
+ * default N0 = 4 n^2 (Sec. 10).  With a cache path the choice is read from /
+ * appended to that text file, keyed by device name, kernel, degree, theta,
+ * precision, nrhs and N.
+ *   points device [N][3]; weights device [nrhs][N] (1 <= nrhs <= 64)
+ * Synchronous.  Errors: INVALID_ARG, OUT_OF_MEMORY, CUDA. */
+typedef struct {
+  int max_leaf;          /* chosen N0 */
+  int rhs_chunk;         /* chosen csfmm_options.rhs_chunk */
+  double ms_per_eval;    /* its evaluation time */
+  double rel_err;        /* its error against the FP64 direct sum on the samples */
+  double default_ms;     /* the same for N0 = 4 n^2, rhs_chunk 0 */
+  double default_rel_err;
+  int candidates;        /* candidates timed (0 when read from the cache) */
+  int from_cache;
+} csfmm_tune_result;
+csfmm_status csfmm_autotune(const double *points, int64_t N, int kernel_id, int degree,
+                            double theta, const double *weights, int nrhs, int precision,
+                            const char *cache_path, double err_factor, csfmm_tune_result *out);
 
 /* Plan statistics (host struct). */
 csfmm_status csfmm_plan_stats(csfmm_plan plan, csfmm_stats *stats);

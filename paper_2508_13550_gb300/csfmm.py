@@ -45,7 +45,18 @@ class CsfmmError(RuntimeError):
 
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("max_nrhs", ctypes.c_int),
-                ("use_graphs", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("use_graphs", ctypes.c_int), ("rhs_chunk", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("max_leaf", ctypes.c_int), ("rhs_chunk", ctypes.c_int),
+                ("ms_per_eval", ctypes.c_double), ("rel_err", ctypes.c_double),
+                ("default_ms", ctypes.c_double), ("default_rel_err", ctypes.c_double),
+                ("candidates", ctypes.c_int), ("from_cache", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class Stats(ctypes.Structure):
@@ -107,6 +118,8 @@ _SIGS = {
     "csfmm_direct_targets": [_VP, _I64, ctypes.c_int, _VP, ctypes.c_int, _VP, _I64, _VP,
                              ctypes.c_int, _VP],
     "csfmm_plan_stats": [_VP, ctypes.POINTER(Stats)],
+    "csfmm_autotune": [_VP, _I64, ctypes.c_int, ctypes.c_int, _D, _VP, ctypes.c_int, ctypes.c_int,
+                       ctypes.c_char_p, _D, ctypes.POINTER(TuneResult)],
     "csfmm_plan_export_cells": [_VP] + [_VP] * 10,
     "csfmm_plan_export_list": [_VP, ctypes.c_int, _VP, _VP],
     "csfmm_plan_export_order": [_VP, _VP],
@@ -196,10 +209,11 @@ class Plan:
 
 
 def plan_create(points, kernel_id: int, degree: int, theta: float, max_leaf: int,
-                precision: int = FP64, max_nrhs: int = 16, use_graphs: int = 0, stream=None):
+                precision: int = FP64, max_nrhs: int = 16, use_graphs: int = 0, rhs_chunk: int = 0,
+                stream=None):
     import torch
     lib = load()
-    opt = Options(precision, max_nrhs, use_graphs)
+    opt = Options(precision, max_nrhs, use_graphs, rhs_chunk)
     h = ctypes.c_void_p()
     N = points.shape[0]
     rc = lib.csfmm_plan_create(_dev(points, torch.float64), N, kernel_id, degree, theta,
@@ -298,6 +312,20 @@ def direct(points, kernel_id: int, weights, precision: int = FP64, targets=None,
                                         _dev(targets, torch.int64), nt,
                                         _dev(out, torch.float64), precision, _stream(stream)))
     return out
+
+
+def autotune(points, kernel_id: int, degree: int, theta: float, weights, precision: int = FP64,
+             cache_path: str | None = None, err_factor: float = 2.0) -> dict:
+    """csfmm_autotune: fastest leaf size / right-hand-side chunk within
+    err_factor of the default's error (see include/csfmm.h)."""
+    import torch
+    w = weights if weights.dim() == 2 else weights.unsqueeze(0)
+    res = TuneResult()
+    _check(load().csfmm_autotune(_dev(points, torch.float64), points.shape[0], kernel_id, degree,
+                                 theta, _dev(w, torch.float64), w.shape[0], precision,
+                                 cache_path.encode() if cache_path else None, err_factor,
+                                 ctypes.byref(res)))
+    return res.as_dict()
 
 
 def plan_stats(plan: Plan) -> dict:

@@ -101,6 +101,7 @@ struct Plan {
   int64_t N = 0;
   int kernel_id = 0, n = 0, p = 0, P = 0, N0 = 0, precision = 0, dim = 1, max_nrhs = 16;
   int use_graphs = 0;
+  int rhs_chunk = 16;   // FP32 bulk, scalar kernels: 16, 8 or 4
   double theta = 0.7;
   int ncells = 0, nleaves = 0, nlevels = 0;
   std::vector<int> level_begin;  // cells of level l: [level_begin[l], level_begin[l+1])

@@ -582,8 +582,8 @@ csfmm_status run_passes(Plan &pl, Workspace &W, const double *w, int nrhs, doubl
   const bool multi = sizeof(Real) == 4 && KID != CSFMM_KERNEL_BIOT_SAVART;
   auto chunk = [&](int r0) {
     const int left = nrhs - r0;
-    if (multi && left >= 16) return 16;
-    if (multi && left >= 8) return 8;
+    if (multi && left >= 16 && pl.rhs_chunk >= 16) return 16;
+    if (multi && left >= 8 && pl.rhs_chunk >= 8) return 8;
     return min(kRB, left);
   };
   for (int r0 = 0; r0 < nrhs; r0 += chunk(r0)) {
