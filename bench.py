@@ -387,19 +387,60 @@ def run_serving(args, sample=None):
     return summ
 
 
+def run_accuracy_sweep(args):
+    """E(FS64, DS) (FMM truncation) and E(FS32, DS) (FP32-bulk form) against
+    an FP64 GPU direct sum on sampled targets, for degrees n = 2..12 (N0 = 4n^2,
+    MAC 0.7), land-masked Newtonian field and Y43 Poisson field on the cubed
+    sphere with m = args.sweep_m."""
+    import torch
+    from paper_2508_13550_gb300 import csfmm as Cs
+    from paper_2508_13550_gb300 import inputs as I
+    m = args.sweep_m
+    rows = []
+    fields = {"newton": (Cs.KERNEL_NEWTON, None), "laplace_y43": (Cs.KERNEL_LAPLACE, None)}
+    pts, A = I.cubed_sphere_grid(m)
+    f_newton = I.land_mask_field(pts, I.MASTER_SEED + 3) * A
+    f_y43 = I.real_sph_harm(4, 3, pts) * A
+    dp = torch.from_numpy(pts).cuda()
+    rng = np.random.default_rng(20250813)
+    tg = torch.from_numpy(np.sort(rng.choice(len(pts), args.err_samples, replace=False))
+                          .astype(np.int64)).cuda()
+    for name, kid, w in (("newton", Cs.KERNEL_NEWTON, f_newton),
+                         ("laplace_y43", Cs.KERNEL_LAPLACE, f_y43)):
+        dw = torch.from_numpy(w[None].copy()).cuda()
+        ds = Cs.direct(dp, kid, dw, precision=Cs.FP64, targets=tg)
+        nrm = torch.linalg.norm(ds)
+        for n in range(2, 13, 2):
+            row = {"field": name, "n": n, "N0": 4 * n * n}
+            for key, prec in (("E64", Cs.FP64), ("E32", Cs.FP32_BULK)):
+                P = Cs.plan_create(dp, kid, n, 0.7, 4 * n * n, precision=prec, max_nrhs=1)
+                out = Cs.evaluate(P, dw)
+                torch.cuda.synchronize()
+                row[key] = float(torch.linalg.norm(out[:, tg] - ds) / nrm)
+                Cs.plan_destroy(P)
+            row["E32_over_E64"] = row["E32"] / row["E64"]
+            rows.append(row)
+            log(row)
+    return {"metric": "FMM rel err vs FP64 direct sum (degree sweep)", "unit": "rel l2",
+            "config": {"workload": "accuracy-sweep", "m": m, "N": len(pts), "theta": 0.7,
+                       "err_samples": args.err_samples}, "rows": rows}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="newton-6m", choices=sorted(WORKLOADS) + ["serving"])
+    ap.add_argument("--workload", default="newton-6m",
+                    choices=sorted(WORKLOADS) + ["serving", "accuracy-sweep"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--err-samples", type=int, default=2048)
     ap.add_argument("--cpu-leaves", type=int, default=16384)
     ap.add_argument("--ref-leaves", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", dest="fp64_compare", action="store_false")
+    ap.add_argument("--sweep-m", type=int, default=256)
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-sample", type=int, default=300,
                     help="requests of the serving stream measured in the default line (0: none)")
@@ -410,6 +451,11 @@ def main():
         log("warning: fewer than 3 warm-up steps")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "accuracy-sweep":
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        print(json.dumps(run_accuracy_sweep(args)), flush=True)
+        return 0
     if args.workload == "serving":
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))

@@ -62,9 +62,10 @@ enum {
 /* Precision forms. */
 enum {
   CSFMM_FP64 = 0,      /* every step in FP64 */
-  CSFMM_FP32_BULK = 1  /* kernel evaluations and per-tile sums in FP32 on pair-relative
-                          coordinates; geometry, interpolation weights and the final
-                          per-target accumulation in FP64 */
+  CSFMM_FP32_BULK = 1  /* kernel evaluations, tile sums and the upward pass in FP32 on
+                          pair-relative coordinates; geometry, interpolation weights,
+                          proxy potentials, the downward pass (FP64 L2L, double-float
+                          L2P) and the final per-target accumulation in FP64 */
 };
 
 /* Interaction list types (Sec. 5). */
@@ -163,7 +164,7 @@ csfmm_status csfmm_evaluate_ws(csfmm_plan plan, csfmm_workspace ws, const double
  * library keeps until the process exits.
  *   plan    a plan of the current device (built earlier, e.g. at start-up)
  *   weights device [nrhs][N]; out device [nrhs][N][dim]; 1 <= nrhs <= 64
- * Needs 8 N nrhs (1 + dim) + ncells nrhs P (1 + dim) s bytes of scratch
+ * Needs 8 N nrhs (1 + dim) + ncells nrhs P (s + 8 dim) bytes of scratch
  * (s = 8 for CSFMM_FP64, 4 for CSFMM_FP32_BULK, which also needs 4 N nrhs;
  * each part rounded up to 256 bytes); larger requests fail with CSFMM_ERR_INVALID_ARG and a message that
  * states the size.  The first call on a device looks up the array's device

@@ -6,7 +6,8 @@
 //   perm[N]            tree position -> input index
 //   La[N][p], Lb[N][p] barycentric Lagrange values L_k(u_i), L_k(v_i) of every
 //                      point in its leaf (Sec. 4, Eq. barycentric); FP64 for
-//                      the FP64 form, FP32 for the FP32-bulk form
+//                      the FP64 form, an FP32 hi + lo pair for the FP32-bulk
+//                      form (P2M uses hi, the double-float L2P both)
 //   off32[N]           float4 offset of each point from its leaf centre
 //   cells (SoA)        face, level, ia, ib, begin, end, parent, child[4],
 //                      centre[3], radius, xi_mid, eta_mid, half
@@ -81,7 +82,8 @@ struct PlanView {
   const double *x;       // [3][N]
   const int32_t *perm;   // [N]
   const double *La64, *Lb64;  // [N][p]
-  const float *La32, *Lb32;   // [N][p]
+  const float *La32, *Lb32;   // [N][p] FP32 rounding of La64, Lb64 ...
+  const float *La32lo, *Lb32lo;  // ... and of the remainders
   const float4 *off32;   // [N]
   const int32_t *cbegin, *cend, *clevel, *cface, *cparent, *cchild;
   const double *ccentre; // [nc][3]
@@ -109,7 +111,7 @@ struct Plan {
   double *x = nullptr;
   int32_t *perm = nullptr;
   double *La64 = nullptr, *Lb64 = nullptr;
-  float *La32 = nullptr, *Lb32 = nullptr;
+  float *La32 = nullptr, *Lb32 = nullptr, *La32lo = nullptr, *Lb32lo = nullptr;
   float4 *off32 = nullptr;
   int32_t *leaf_of = nullptr;
   int32_t *cface = nullptr, *clevel = nullptr, *cbegin = nullptr, *cend = nullptr,
@@ -175,7 +177,7 @@ struct Workspace {
   float *wsf = nullptr;     // [max_nrhs][N] the same in FP32 (FP32 form only)
   double *wbar = nullptr;   // [nc][max_nrhs][P] proxy weights (FP64 form)
   float *wbar32 = nullptr;  // [nc][max_nrhs][P] proxy weights (FP32 form)
-  double *psi = nullptr;    // [nc][max_nrhs][dim][P] proxy potentials
+  double *psi = nullptr;    // [nc][max_nrhs][dim][P] proxy potentials (FP64 in both forms)
   double *phi = nullptr;    // [max_nrhs][N][dim] near-field potentials, tree order
   double *stage_w = nullptr;    // device staging for host-buffer evaluations [max_nrhs][N]
   double *stage_out = nullptr;  // [max_nrhs][N][dim]
@@ -204,10 +206,10 @@ csfmm_status workspace_alloc(Plan &pl, Workspace &ws, int max_nrhs);
 // right-hand sides from r0, scalar kernels only (interact32.cu).
 void launch_multi32(const PlanView &v, bool far, int ngrid, const int32_t *leaves,
                     const float *wsf, const float *wbar, int ldr, int r0, int nr, double *phi,
-                    float *psi, cudaStream_t st);
+                    double *psi, cudaStream_t st);
 // FP32-bulk far field (interact32.cu): nr <= 4 right-hand sides from r0.
 void launch_far32(const PlanView &v, int ncells, const float *wsf, const float *wbar, int ldr,
-                  int r0, int nr, float *psi, cudaStream_t st);
+                  int r0, int nr, double *psi, cudaStream_t st);
 // FP32-bulk near field (interact32.cu): nr <= 4 right-hand sides from r0.
 void launch_near32(const PlanView &v, const int32_t *leaves, int nleaves, const float *wsf, int ldw,
                    const float *wbar, int ldr, int r0, int nr, double *phi, cudaStream_t st);

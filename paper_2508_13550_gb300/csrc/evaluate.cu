@@ -514,9 +514,79 @@ __global__ void __launch_bounds__(kL2PThreads) l2p_kernel(PlanView v, const int3
   }
 }
 
+// L2P + finalize of the FP32-bulk form in double-float arithmetic: the proxy
+// potentials (FP64) and the Lagrange rows (FP32 hi + lo pairs) enter as
+// pairs of FP32 numbers; each product is formed exactly with an FMA and the
+// sums are compensated (two-sum), so the interpolation adds no FP32-level
+// rounding to the per-target value (a chain of FP32 contractions through
+// every tree level would otherwise dominate the bulk form's error).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (S, C) += (ah + al) (bh + bl)
+__device__ __forceinline__ void df_fma(float &S, float &C, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, fmaf(al, bh, e));
+  float q;
+  two_sum(S, p, S, q);
+  C = __fadd_rn(C, __fadd_rn(q, e));
+}
+
+__global__ void __launch_bounds__(kL2PThreads) l2p_df_kernel(PlanView v, const int32_t *leaves,
+                                                             const double *psi, int ldr, int nrhs,
+                                                             int dim, const double *phi,
+                                                             double *out) {
+  __shared__ float sph[kMaxP * kMaxP], spl[kMaxP * kMaxP];
+  __shared__ float sLa[kL2PThreads * kMaxP], sLal[kL2PThreads * kMaxP];
+  __shared__ float sLb[kL2PThreads * kMaxP], sLbl[kL2PThreads * kMaxP];
+  const int c = leaves[blockIdx.x];
+  const int b = v.cbegin[c], e = v.cend[c], p = v.p, P = v.P;
+  for (int i0 = b; i0 < e; i0 += kL2PThreads) {
+    const int nj = min(kL2PThreads, e - i0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < nj * p; t += kL2PThreads) {
+      const int64_t o = (int64_t)i0 * p + t;
+      sLa[t] = v.La32[o];
+      sLal[t] = v.La32lo[o];
+      sLb[t] = v.Lb32[o];
+      sLbl[t] = v.Lb32lo[o];
+    }
+    const int t = threadIdx.x;
+    const int i = i0 + t;
+    for (int r = 0; r < nrhs; ++r)
+      for (int d = 0; d < dim; ++d) {
+        __syncthreads();
+        for (int u = threadIdx.x; u < P; u += kL2PThreads) {
+          const double x = psi[(((int64_t)c * ldr + r) * dim + d) * P + u];
+          const float hi = (float)x;
+          sph[u] = hi;
+          spl[u] = (float)(x - (double)hi);
+        }
+        __syncthreads();
+        if (t < nj) {
+          const float *lah = sLa + t * p, *lal = sLal + t * p;
+          const float *lbh = sLb + t * p, *lbl = sLbl + t * p;
+          float S = 0.f, C = 0.f;
+          for (int m1 = 0; m1 < p; ++m1) {
+            float sh = 0.f, sl = 0.f;
+            for (int m2 = 0; m2 < p; ++m2)
+              df_fma(sh, sl, sph[m1 * p + m2], spl[m1 * p + m2], lbh[m2], lbl[m2]);
+            df_fma(S, C, lah[m1], lal[m1], sh, sl);
+          }
+          const int64_t oi = ((int64_t)r * v.N + i) * dim + d;
+          out[((int64_t)r * v.N + v.perm[i]) * dim + d] = phi[oi] + ((double)S + (double)C);
+        }
+      }
+  }
+}
+
 template <int KID, typename Real>
 void launch_far(const PlanView &v, Plan &pl, Workspace &W, int nr, int r0, int tb_prox,
-                Real *wbar, Real *psi, cudaStream_t st) {
+                Real *wbar, double *psi, cudaStream_t st) {
   const int N = (int)pl.N, ldr = W.max_nrhs;
   switch (nr) {
     case 1: far_kernel<KID, Real, 1><<<pl.ncells, tb_prox, 0, st>>>(v, W.ws, N, wbar, ldr, r0, psi); break;
@@ -546,7 +616,7 @@ csfmm_status run_passes(Plan &pl, Workspace &W, const double *w, int nrhs, doubl
   const int ldr = W.max_nrhs;  // rhs stride of wbar / psi
   Real *wbar;
   if constexpr (sizeof(Real) == 4) wbar = W.wbar32; else wbar = W.wbar;
-  Real *psi = reinterpret_cast<Real *>(W.psi);
+  double *psi = W.psi;  // FP64 proxy potentials in both forms
   pl.launches = 0;
 #define CSFMM_MARK(ph)                              \
   do {                                              \
@@ -614,11 +684,14 @@ csfmm_status run_passes(Plan &pl, Workspace &W, const double *w, int nrhs, doubl
   CSFMM_MARK(CSFMM_PHASE_L2L);
   for (int l = 0; l + 1 < pl.nlevels; ++l) {
     int c0 = pl.level_begin[l], nlev = pl.level_begin[l + 1] - c0;
-    l2l_kernel<Real><<<nlev, 128, 0, st>>>(v, c0, 0, nrhs, dim, psi, ldr);
+    l2l_kernel<double><<<nlev, 128, 0, st>>>(v, c0, 0, nrhs, dim, psi, ldr);
     ++pl.launches;
   }
   CSFMM_MARK(CSFMM_PHASE_L2P);
-  l2p_kernel<Real><<<pl.nleaves, kL2PThreads, 0, st>>>(v, pl.leaves, psi, ldr, nrhs, dim, W.phi, out);
+  if constexpr (sizeof(Real) == 4)
+    l2p_df_kernel<<<pl.nleaves, kL2PThreads, 0, st>>>(v, pl.leaves, psi, ldr, nrhs, dim, W.phi, out);
+  else
+    l2p_kernel<double><<<pl.nleaves, kL2PThreads, 0, st>>>(v, pl.leaves, psi, ldr, nrhs, dim, W.phi, out);
   ++pl.launches;
   CSFMM_MARK(CSFMM_NUM_PHASES);
 #undef CSFMM_MARK
@@ -666,13 +739,11 @@ csfmm_status workspace_alloc(Plan &pl, Workspace &W, int max_nrhs) {
   if ((s = W.arena.alloc(&W.ws, R * N)) != CSFMM_OK) return s;
   if (pl.precision == CSFMM_FP64) {
     if ((s = W.arena.alloc(&W.wbar, nc * R * P)) != CSFMM_OK) return s;
-    if ((s = W.arena.alloc(&W.psi, nc * R * pl.dim * P)) != CSFMM_OK) return s;
   } else {
     if ((s = W.arena.alloc(&W.wbar32, nc * R * P)) != CSFMM_OK) return s;
     if ((s = W.arena.alloc(&W.wsf, R * N)) != CSFMM_OK) return s;
-    // FP32 proxy potentials live in the psi buffer (half of its FP64 size is used)
-    if ((s = W.arena.alloc(&W.psi, (nc * R * pl.dim * P + 1) / 2)) != CSFMM_OK) return s;
   }
+  if ((s = W.arena.alloc(&W.psi, nc * R * pl.dim * P)) != CSFMM_OK) return s;
   if ((s = W.arena.alloc(&W.phi, R * N * pl.dim)) != CSFMM_OK) return s;
   return CSFMM_OK;
 }
@@ -704,7 +775,7 @@ csfmm_status capture(Plan &pl, Workspace &W, const double *w, int nrhs, double *
   CSFMM_CUDA(cudaGraphGetNodes(graph, nodes.data(), &n));
   const void *f_gather = (const void *)gather_kernel;
   const void *f_l2p = pl.precision == CSFMM_FP64 ? (const void *)l2p_kernel<double>
-                                                 : (const void *)l2p_kernel<float>;
+                                                 : (const void *)l2p_df_kernel;
   for (cudaGraphNode_t nd : nodes) {
     cudaGraphNodeType ty;
     CSFMM_CUDA(cudaGraphNodeGetType(nd, &ty));

@@ -431,7 +431,7 @@ __global__ void __launch_bounds__(kThreads, CSFMM_NEAR_MINB) near32x2_kernel(Pla
 template <int KID>
 __global__ void __launch_bounds__(160) far32x2_kernel(PlanView v, const float *wsf,
                                                       const float *wbar, int ldr, int r0,
-                                                      float *psi) {
+                                                      double *psi) {
   __shared__ ulonglong2 sA[kTile], sB[kTile];
   __shared__ float wsum[8];
   const int c = blockIdx.x, P = v.P, nth = blockDim.x;
@@ -510,14 +510,14 @@ __global__ void __launch_bounds__(160) far32x2_kernel(PlanView v, const float *w
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int m = threadIdx.x + h * nth;
-    if (m < P) psi[((int64_t)c * ldr + r0) * P + m] = (float)out[h];
+    if (m < P) psi[((int64_t)c * ldr + r0) * P + m] = out[h];
   }
 }
 
 // Scalar far field for Biot-Savart and for several right-hand sides.
 template <int KID, int NR>
 __global__ void __launch_bounds__(160) far32_kernel(PlanView v, const float *wsf, const float *wbar,
-                                                    int ldr, int r0, float *psi) {
+                                                    int ldr, int r0, double *psi) {
   constexpr int DIM = kdim32<KID>();
   constexpr int NT = 2;
   __shared__ float4 sp[kTile];
@@ -636,13 +636,13 @@ __global__ void __launch_bounds__(160) far32_kernel(PlanView v, const float *wsf
     for (int q = 0; q < NR; ++q)
 #pragma unroll
       for (int d = 0; d < DIM; ++d)
-        psi[(((int64_t)c * ldr + r0 + q) * DIM + d) * P + m] = (float)out[h][q][d];
+        psi[(((int64_t)c * ldr + r0 + q) * DIM + d) * P + m] = out[h][q][d];
   }
 }
 
 template <int KID>
 void launch_far_kid(const PlanView &v, int ncells, const float *wsf, const float *wbar, int ldr,
-                    int r0, int nr, float *psi, cudaStream_t st) {
+                    int r0, int nr, double *psi, cudaStream_t st) {
   const int nth = ((v.P + 63) / 64) * 32;  // 2 targets per thread
   if constexpr (KID != CSFMM_KERNEL_BIOT_SAVART) {
     if (nr == 1) {
@@ -696,7 +696,7 @@ __device__ __forceinline__ void tile_sum_multi(const float4 *__restrict__ sp,
 }
 
 // FAR = false: near field of leaf leaves[blockIdx.x] into phi (FP64);
-// FAR = true: far field of cell blockIdx.x into psi (FP32).  NT targets per
+// FAR = true: far field of cell blockIdx.x into psi (FP64).  NT targets per
 // thread, strided by blockDim; each tile's FP32 sums are added to the
 // block-owned output rows, which hold the running per-target totals.
 // Targets per thread and threads per block of the near-field launch of the
@@ -711,7 +711,7 @@ __device__ __forceinline__ void tile_sum_multi(const float4 *__restrict__ sp,
 template <int KID, int NR, bool FAR>
 __global__ void __launch_bounds__(CSFMM_MULTI_THREADS) multi32_kernel(
     PlanView v, const int32_t *leaves, const float *wsf, const float *wbar, int ldr, int r0,
-    double *phi, float *psi) {
+    double *phi, double *psi) {
   constexpr int NT = CSFMM_MULTI_NT;
   // one partial weight sum per warp; every launch uses at most
   // CSFMM_MULTI_THREADS threads
@@ -742,7 +742,7 @@ __global__ void __launch_bounds__(CSFMM_MULTI_THREADS) multi32_kernel(
       if (i < te) {
 #pragma unroll
         for (int q = 0; q < NR; ++q) {
-          if (FAR) psi[((int64_t)c * ldr + r0 + q) * P + i] = 0.f;
+          if (FAR) psi[((int64_t)c * ldr + r0 + q) * P + i] = 0.0;
           else phi[(int64_t)(r0 + q) * v.N + i] = 0.0;
         }
       }
@@ -834,7 +834,7 @@ __global__ void __launch_bounds__(CSFMM_MULTI_THREADS) multi32_kernel(
                   if (self_tile && self[k] >= 0 && self[k] < nj) tot -= swf[self[k] * NR + qq];
                   val = -(0.69314718055994530942 * kInv4Pi) * (val - (double)tot);
                 }
-                if (FAR) psi[((int64_t)c * ldr + r0 + qq) * P + i] += (float)val;
+                if (FAR) psi[((int64_t)c * ldr + r0 + qq) * P + i] += val;
                 else phi[(int64_t)(r0 + qq) * v.N + i] += val;
               }
             }
@@ -847,7 +847,7 @@ __global__ void __launch_bounds__(CSFMM_MULTI_THREADS) multi32_kernel(
 
 template <int KID, int NR>
 void launch_multi(const PlanView &v, bool far, int ngrid, const int32_t *leaves, const float *wsf,
-                  const float *wbar, int ldr, int r0, double *phi, float *psi, cudaStream_t st) {
+                  const float *wbar, int ldr, int r0, double *phi, double *psi, cudaStream_t st) {
   if (far) {
     const int per = 32 * CSFMM_MULTI_NT;  // targets covered by one warp
     const int nth = std::min(CSFMM_MULTI_THREADS, std::max(32, ((v.P + per - 1) / per) * 32));
@@ -861,7 +861,7 @@ void launch_multi(const PlanView &v, bool far, int ngrid, const int32_t *leaves,
 template <int KID>
 void launch_multi_kid(const PlanView &v, bool far, int ngrid, const int32_t *leaves,
                       const float *wsf, const float *wbar, int ldr, int r0, int nr, double *phi,
-                      float *psi, cudaStream_t st) {
+                      double *psi, cudaStream_t st) {
   if (nr == 16) launch_multi<KID, 16>(v, far, ngrid, leaves, wsf, wbar, ldr, r0, phi, psi, st);
   else launch_multi<KID, 8>(v, far, ngrid, leaves, wsf, wbar, ldr, r0, phi, psi, st);
 }
@@ -893,7 +893,7 @@ void launch_kid(const PlanView &v, const int32_t *leaves, int nleaves, const flo
 // near field (far = false, one block per leaf) or far field (far = true).
 void launch_multi32(const PlanView &v, bool far, int ngrid, const int32_t *leaves,
                     const float *wsf, const float *wbar, int ldr, int r0, int nr, double *phi,
-                    float *psi, cudaStream_t st) {
+                    double *psi, cudaStream_t st) {
   switch (v.kernel_id) {
     case CSFMM_KERNEL_LAPLACE: launch_multi_kid<CSFMM_KERNEL_LAPLACE>(v, far, ngrid, leaves, wsf, wbar, ldr, r0, nr, phi, psi, st); break;
     case CSFMM_KERNEL_NEWTON: launch_multi_kid<CSFMM_KERNEL_NEWTON>(v, far, ngrid, leaves, wsf, wbar, ldr, r0, nr, phi, psi, st); break;
@@ -901,9 +901,9 @@ void launch_multi32(const PlanView &v, bool far, int ngrid, const int32_t *leave
   }
 }
 
-// nr right-hand sides r0 .. r0+nr-1 (nr <= 4); psi [nc][ldr][dim][P] FP32.
+// nr right-hand sides r0 .. r0+nr-1 (nr <= 4); psi [nc][ldr][dim][P] FP64.
 void launch_far32(const PlanView &v, int ncells, const float *wsf, const float *wbar, int ldr,
-                  int r0, int nr, float *psi, cudaStream_t st) {
+                  int r0, int nr, double *psi, cudaStream_t st) {
   switch (v.kernel_id) {
     case CSFMM_KERNEL_LAPLACE: launch_far_kid<CSFMM_KERNEL_LAPLACE>(v, ncells, wsf, wbar, ldr, r0, nr, psi, st); break;
     case CSFMM_KERNEL_BIOT_SAVART: launch_far_kid<CSFMM_KERNEL_BIOT_SAVART>(v, ncells, wsf, wbar, ldr, r0, nr, psi, st); break;

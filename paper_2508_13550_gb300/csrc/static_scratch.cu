@@ -80,7 +80,7 @@ extern "C" csfmm_status csfmm_evaluate_static(csfmm_plan plan, const double *wei
   const size_t real = pl.precision == CSFMM_FP64 ? sizeof(double) : sizeof(float);
   const size_t b_ws = round256(R * N * sizeof(double));
   const size_t b_wbar = round256(nc * R * P * real);
-  const size_t b_psi = round256(nc * R * dim * P * real);
+  const size_t b_psi = round256(nc * R * dim * P * sizeof(double));
   const size_t b_phi = round256(R * N * dim * sizeof(double));
   const size_t b_wsf = pl.precision == CSFMM_FP64 ? 0 : round256(R * N * sizeof(float));
   const size_t need = b_ws + b_wbar + b_psi + b_phi + b_wsf;

@@ -491,7 +491,7 @@ __global__ void proxies_kernel(PlanView v, double *proxy, float *proxy32) {
 // the Lagrange values in the leaf's local coordinates.
 __global__ void leaf_points_kernel(PlanView v, const int32_t *leaves, int32_t *leaf_of,
                                    float4 *off32, double *La64, double *Lb64, float *La32,
-                                   float *Lb32) {
+                                   float *Lb32, float *La32lo, float *Lb32lo) {
   int c = leaves[blockIdx.x];
   int b = v.cbegin[c], e = v.cend[c];
   const int p = v.p, n = v.n;
@@ -521,13 +521,21 @@ __global__ void leaf_points_kernel(PlanView v, const int32_t *leaves, int32_t *l
     double L[kMaxP];
     lagrange_dev(n, s, u, L);
     for (int k = 0; k < p; ++k) {
-      if (La64) La64[(int64_t)i * p + k] = L[k];
-      if (La32) La32[(int64_t)i * p + k] = (float)L[k];
+      const int64_t o = (int64_t)i * p + k;
+      if (La64) La64[o] = L[k];
+      if (La32) {
+        La32[o] = (float)L[k];
+        La32lo[o] = (float)(L[k] - (double)La32[o]);
+      }
     }
     lagrange_dev(n, s, w, L);
     for (int k = 0; k < p; ++k) {
-      if (Lb64) Lb64[(int64_t)i * p + k] = L[k];
-      if (Lb32) Lb32[(int64_t)i * p + k] = (float)L[k];
+      const int64_t o = (int64_t)i * p + k;
+      if (Lb64) Lb64[o] = L[k];
+      if (Lb32) {
+        Lb32[o] = (float)L[k];
+        Lb32lo[o] = (float)(L[k] - (double)Lb32[o]);
+      }
     }
   }
 }
@@ -709,6 +717,7 @@ PlanView Plan::view() const {
   v.N = (int)N; v.n = n; v.p = p; v.P = P; v.N0 = N0; v.ncells = ncells; v.dim = dim;
   v.kernel_id = kernel_id;
   v.x = x; v.perm = perm; v.La64 = La64; v.Lb64 = Lb64; v.La32 = La32; v.Lb32 = Lb32;
+  v.La32lo = La32lo; v.Lb32lo = Lb32lo;
   v.off32 = off32;
   v.cbegin = cbegin; v.cend = cend; v.clevel = clevel; v.cface = cface; v.cparent = cparent;
   v.cchild = cchild; v.ccentre = ccentre; v.cradius = cradius; v.cxmid = cxmid; v.cymid = cymid;
@@ -886,6 +895,8 @@ csfmm_status build_tree(Plan &pl, const double *points, cudaStream_t st) {
   } else {
     CSFMM_TRY(A.alloc(&pl.La32, (size_t)N * pl.p));
     CSFMM_TRY(A.alloc(&pl.Lb32, (size_t)N * pl.p));
+    CSFMM_TRY(A.alloc(&pl.La32lo, (size_t)N * pl.p));
+    CSFMM_TRY(A.alloc(&pl.Lb32lo, (size_t)N * pl.p));
   }
   CSFMM_TRY(A.alloc(&pl.m2m64, (size_t)2 * pl.p * pl.p));
   CSFMM_TRY(A.alloc(&pl.m2m32, (size_t)2 * pl.p * pl.p));
@@ -894,7 +905,7 @@ csfmm_status build_tree(Plan &pl, const double *points, cudaStream_t st) {
     proxies_kernel<<<nc, 128, 0, st>>>(v, pl.proxy, pl.proxy32);
     CSFMM_CUDA(cudaGetLastError());
     leaf_points_kernel<<<nleaves, 128, 0, st>>>(v, pl.leaves, pl.leaf_of, pl.off32, pl.La64,
-                                                pl.Lb64, pl.La32, pl.Lb32);
+                                                pl.Lb64, pl.La32, pl.Lb32, pl.La32lo, pl.Lb32lo);
     CSFMM_CUDA(cudaGetLastError());
     m2m_matrix_kernel<<<1, 64, 0, st>>>(pl.n, pl.cheb, pl.m2m64, pl.m2m32);
     CSFMM_CUDA(cudaGetLastError());
