@@ -115,6 +115,26 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x: float, dist=None) -> float:
+    """Maximum of x over the ranks of the default process group (x itself
+    without one).  NCCL groups reduce on the current CUDA device, others on
+    the CPU."""
+    if dist is None or not dist.is_initialized():
+        return float(x)
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" \
+        else torch.device("cpu")
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds_max: float) -> float:
+    """Units processed by all ranks divided by the slowest rank's time
+    (replicas: every rank processes the same number of units)."""
+    return world * units_per_rank / seconds_max
+
+
 def make_workload(name):
     from paper_2508_13550_gb300 import inputs as I
     wl = WORKLOADS[name]
@@ -242,12 +262,9 @@ def run_ours(args):
     phases, calls = Cs.plan_phase_times(plan)
     Cs.plan_sync(plan)
     launches = Cs.plan_stats(plan)["launches_per_evaluate"] * args.steps
-    if dist:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist)
     ms_step = ms / args.steps
-    value = world * N * nrhs / (ms_step / 1e3)
+    value = whole_job_rate(N * nrhs, world, ms_step / 1e3)
 
     # end to end through the host-buffer entry point: H2D weights, evaluate, D2H result
     hw = torch.from_numpy(w).pin_memory()
@@ -266,12 +283,8 @@ def run_ours(args):
         Cs._check(lib.csfmm_evaluate_host(plan.handle, ctypes.c_void_p(hw.data_ptr()), nrhs,
                                           ctypes.c_void_p(hout.data_ptr()),
                                           ctypes.c_void_p(stream.cuda_stream)))
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if dist:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_val = world * N * nrhs / e2e_s
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dist)
+    e2e_val = whole_job_rate(N * nrhs, world, e2e_s)
 
     # accuracy against the FP64 direct sum on sampled targets (GPU direct sum)
     rng = np.random.default_rng(20250813)
