@@ -97,6 +97,7 @@ typedef struct {
   int64_t device_bytes;    /* device memory held by the plan (including its workspace) */
   double build_ms;         /* wall time of csfmm_plan_create */
   int64_t launches_per_evaluate; /* kernels launched by the last evaluation */
+  int64_t sym_pairs;       /* FP32 bulk: PP leaf pairs evaluated once for both directions */
 } csfmm_stats;
 
 /* Evaluation phases timed by csfmm_plan_phase_times. */

@@ -67,7 +67,7 @@ class Stats(ctypes.Structure):
                 ("n_list", ctypes.c_int64 * 4), ("evals", ctypes.c_int64 * 4),
                 ("pairs_covered", ctypes.c_int64), ("mac_margin", ctypes.c_double),
                 ("device_bytes", ctypes.c_int64), ("build_ms", ctypes.c_double),
-                ("launches_per_evaluate", ctypes.c_int64)]
+                ("launches_per_evaluate", ctypes.c_int64), ("sym_pairs", ctypes.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

@@ -92,6 +92,7 @@ struct PlanView {
   const double *proxy;   // [nc][3][P]
   const float *proxy32;  // [nc][3][P]
   const int32_t *loff[4], *lsrc[4];
+  const int32_t *sym_contrib;
   const double *m2m64;   // [2][p][p]: M[q][k][m] = L_k((s_m + 2q - 1)/2)
   const float *m2m32;
   const double *cheb;    // [p]
@@ -130,6 +131,17 @@ struct Plan {
   int32_t *far_targets = nullptr;   // cells with CP or CC entries
   int n_far_targets = 0;
   int32_t *leaves = nullptr;        // all leaf cells
+  // Symmetric near field (FP32 bulk, single right-hand side, K(x,y) = K(y,x)):
+  // every PP entry (T, S) with S > T whose mirror (S, T) is also a PP entry is
+  // one "cross pair" evaluated once for both directions; its partial sums
+  // (rows: T's points, then columns: S's points) live at sym_off[pair] of the
+  // workspace's partial buffer.
+  int2 *sym_pairs = nullptr;        // [n_sym_pairs] (T, S), T < S
+  int32_t *sym_off = nullptr;       // [n_sym_pairs] partial-buffer offset of the pair
+  int32_t *sym_contrib = nullptr;   // [nPP] offset of the target leaf's partials of this
+                                    // PP entry (-1: evaluated directly)
+  int n_sym_pairs = 0;
+  int64_t sym_part_len = 0;         // floats in one partial buffer
   double *m2m64 = nullptr;
   float *m2m32 = nullptr;
   double *cheb = nullptr;
@@ -179,6 +191,7 @@ struct Workspace {
   float *wbar32 = nullptr;  // [nc][max_nrhs][P] proxy weights (FP32 form)
   double *psi = nullptr;    // [nc][max_nrhs][dim][P] proxy potentials (FP64 in both forms)
   double *phi = nullptr;    // [max_nrhs][N][dim] near-field potentials, tree order
+  float *sym_part = nullptr;     // [plan.sym_part_len] cross-pair partial sums (FP32 form)
   double *stage_w = nullptr;    // device staging for host-buffer evaluations [max_nrhs][N]
   double *stage_out = nullptr;  // [max_nrhs][N][dim]
   int last_nrhs = 0;
@@ -210,9 +223,16 @@ void launch_multi32(const PlanView &v, bool far, int ngrid, const int32_t *leave
 // FP32-bulk far field (interact32.cu): nr <= 4 right-hand sides from r0.
 void launch_far32(const PlanView &v, int ncells, const float *wsf, const float *wbar, int ldr,
                   int r0, int nr, double *psi, cudaStream_t st);
-// FP32-bulk near field (interact32.cu): nr <= 4 right-hand sides from r0.
+// Symmetric PP evaluation of the cross pairs (interact32.cu), one right-hand
+// side, scalar kernels; writes the pairs' partial sums into part.
+void launch_pp_sym32(const PlanView &v, const int2 *pairs, const int32_t *off, int npairs,
+                     const float *wsf, float *part, cudaStream_t st);
+// FP32-bulk near field (interact32.cu): nr <= 4 right-hand sides from r0.  With
+// part != nullptr (one right-hand side) the PP entries other than the self
+// entry are read from the cross-pair partials instead of being evaluated.
 void launch_near32(const PlanView &v, const int32_t *leaves, int nleaves, const float *wsf, int ldw,
-                   const float *wbar, int ldr, int r0, int nr, double *phi, cudaStream_t st);
+                   const float *wbar, int ldr, int r0, int nr, double *phi, cudaStream_t st,
+                   const float *part = nullptr);
 // Direct sum (direct.cu).
 csfmm_status direct_impl(const double *points, int64_t N, int kernel_id, const double *w,
                          int nrhs, const int64_t *targets, int64_t ntargets, double *out,

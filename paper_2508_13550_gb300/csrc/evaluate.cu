@@ -669,13 +669,22 @@ csfmm_status run_passes(Plan &pl, Workspace &W, const double *w, int nrhs, doubl
     ++pl.launches;
   }
   CSFMM_MARK(CSFMM_PHASE_NEAR);
+  // single right-hand side, symmetric scalar kernel: the cross pairs of the PP
+  // lists are evaluated once for both directions first
+  const bool sym = sizeof(Real) == 4 && nrhs == 1 && KID != CSFMM_KERNEL_BIOT_SAVART &&
+                   pl.n_sym_pairs > 0 && W.sym_part != nullptr;
+  if (sym) {
+    launch_pp_sym32(v, pl.sym_pairs, pl.sym_off, pl.n_sym_pairs, W.wsf, W.sym_part, st);
+    ++pl.launches;
+  }
   for (int r0 = 0; r0 < nrhs; r0 += chunk(r0)) {
     const int nr = chunk(r0);
     if constexpr (sizeof(Real) == 4) {
       if (nr > kRB)
         launch_multi32(v, false, pl.nleaves, pl.leaves, W.wsf, wbar, ldr, r0, nr, W.phi, psi, st);
       else
-        launch_near32(v, pl.leaves, pl.nleaves, W.wsf, N, wbar, ldr, r0, nr, W.phi, st);
+        launch_near32(v, pl.leaves, pl.nleaves, W.wsf, N, wbar, ldr, r0, nr, W.phi, st,
+                      sym ? W.sym_part : nullptr);
     } else {
       launch_near<KID, Real>(v, pl, W, nr, r0, wbar, st);
     }
@@ -742,6 +751,9 @@ csfmm_status workspace_alloc(Plan &pl, Workspace &W, int max_nrhs) {
   } else {
     if ((s = W.arena.alloc(&W.wbar32, nc * R * P)) != CSFMM_OK) return s;
     if ((s = W.arena.alloc(&W.wsf, R * N)) != CSFMM_OK) return s;
+    if (pl.n_sym_pairs > 0 && pl.kernel_id != CSFMM_KERNEL_BIOT_SAVART &&
+        (s = W.arena.alloc(&W.sym_part, (size_t)pl.sym_part_len)) != CSFMM_OK)
+      return s;
   }
   if ((s = W.arena.alloc(&W.psi, nc * R * pl.dim * P)) != CSFMM_OK) return s;
   if ((s = W.arena.alloc(&W.phi, R * N * pl.dim)) != CSFMM_OK) return s;

@@ -299,12 +299,188 @@ __global__ void __launch_bounds__(kThreads) near32_kernel(PlanView v, const int3
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Symmetric PP (Eq. PP) for K(x, y) = K(y, x): one block per cross pair
+// (T, S), T < S, evaluates each kernel value once and produces both
+//     rows:    sum_{j in S} K(x_i, y_j) w_j   for the points i of T,
+//     columns: sum_{i in T} K(x_i, y_j) w_i   for the points j of S,
+// written to part[off[pair] ...] (rows first, then columns) as final FP32
+// potentials.  Two warps, each lane owns four rows of T (two packed pairs);
+// columns of S are staged as (x,x,y,y)/(z,z,w,w) tiles and processed in
+// groups of 32: every lane accumulates its rows' contributions to the 32
+// columns, then a butterfly transpose-reduction over the warp leaves the sum
+// of column g*32 + lane in lane `lane`; the two warps are combined in a fixed
+// order, so results are deterministic.
+// ---------------------------------------------------------------------------
+constexpr int kSymThreads = 64;
+constexpr int kSymRows = 4 * kSymThreads;  // rows per pass
+constexpr int kSymCols = 256;              // columns per staged tile
+
+// v[32] held by each lane -> returns sum over the warp of v[lane].
+__device__ __forceinline__ float transpose_reduce32(float (&v)[32], int lane) {
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const bool up = (lane & s) != 0;
+#pragma unroll
+    for (int k = 0; k < s; ++k) {
+      const float send = up ? v[k] : v[k + s];
+      const float keep = up ? v[k + s] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+    }
+  }
+  return v[0];
+}
+
+template <int KID>
+__global__ void __launch_bounds__(kSymThreads) pp_sym_kernel(PlanView v, const int2 *pairs,
+                                                             const int32_t *off, const float *wsf,
+                                                             float *part) {
+  __shared__ ulonglong2 sA[kSymCols], sB[kSymCols];
+  __shared__ float colacc[kSymThreads / 32][kSymCols];
+  __shared__ float wred[2][kSymThreads / 32];
+  const int2 pr = pairs[blockIdx.x];
+  const int T = pr.x, S = pr.y;
+  const int tb = v.cbegin[T], te = v.cend[T], sb = v.cbegin[S], se = v.cend[S];
+  const int nT = te - tb, nS = se - sb;
+  float *rowpart = part + off[blockIdx.x];
+  float *colpart = rowpart + nT;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float dcx = (float)(v.ccentre[3 * T] - v.ccentre[3 * S]);
+  const float dcy = (float)(v.ccentre[3 * T + 1] - v.ccentre[3 * S + 1]);
+  const float dcz = (float)(v.ccentre[3 * T + 2] - v.ccentre[3 * S + 2]);
+  // Laplace: total weights of T and S for -(ln2/4pi)(sum w log2 d2 - sum w)
+  float WT = 0.f, WS = 0.f;
+  if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
+    float a = 0.f, c = 0.f;
+    for (int t = threadIdx.x; t < nT; t += kSymThreads) a += wsf[tb + t];
+    for (int t = threadIdx.x; t < nS; t += kSymThreads) c += wsf[sb + t];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    if (lane == 0) {
+      wred[0][warp] = a;
+      wred[1][warp] = c;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < kSymThreads / 32; ++u) {
+      WT += wred[0][u];
+      WS += wred[1][u];
+    }
+  }
+  for (int r0 = 0; r0 < nT; r0 += kSymRows) {
+    // rows of this lane: r0 + warp*128 + lane + 32k, k = 0..3 (pairs (0,1), (2,3))
+    f2x tx[2], ty[2], tz[2], wr[2], racc[2];
+    bool act[4];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      float x[2], y[2], z[2], w[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = 2 * q + h;
+        const int i = r0 + warp * 128 + lane + 32 * k;
+        act[k] = i < nT;
+        const int ii = tb + (act[k] ? i : 0);
+        const float4 o = v.off32[ii];
+        x[h] = o.x + dcx;
+        y[h] = o.y + dcy;
+        z[h] = o.z + dcz;
+        w[h] = act[k] ? wsf[ii] : 0.f;
+      }
+      tx[q] = f2_pack(x[0], x[1]);
+      ty[q] = f2_pack(y[0], y[1]);
+      tz[q] = f2_pack(z[0], z[1]);
+      wr[q] = f2_pack(w[0], w[1]);
+      racc[q] = 0ull;
+    }
+    for (int c0 = 0; c0 < nS; c0 += kSymCols) {
+      const int nj = min(kSymCols, nS - c0);
+      __syncthreads();
+      for (int t = threadIdx.x; t < kSymCols; t += kSymThreads) {
+        float x = 1.0e4f, y = 1.0e4f, z = 1.0e4f, w = 0.f;  // padding: far away, no weight
+        if (t < nj) {
+          const float4 o = v.off32[sb + c0 + t];
+          x = o.x; y = o.y; z = o.z;
+          w = wsf[sb + c0 + t];
+        }
+        sA[t] = make_ulonglong2(f2_pack(x, x), f2_pack(y, y));
+        sB[t] = make_ulonglong2(f2_pack(z, z), f2_pack(w, w));
+      }
+      __syncthreads();
+      const int ng = (nj + 31) / 32;
+      for (int g = 0; g < ng; ++g) {
+        f2x colv[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const ulonglong2 A = sA[g * 32 + j], B = sB[g * 32 + j];
+          colv[j] = 0ull;
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const f2x rx = f2_sub(tx[q], A.x), ry = f2_sub(ty[q], A.y), rz = f2_sub(tz[q], B.x);
+            f2x d2 = f2_mul(rx, rx);
+            d2 = f2_fma(ry, ry, d2);
+            d2 = f2_fma(rz, rz, d2);
+            float d0, d1;
+            f2_unpack(d2, d0, d1);
+            const f2x f = f2_pack(kfactor<KID>(d0), kfactor<KID>(d1));
+            racc[q] = f2_fma(B.y, f, racc[q]);
+            colv[j] = f2_fma(f, wr[q], colv[j]);
+          }
+        }
+        float cv[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          float lo, hi;
+          f2_unpack(colv[j], lo, hi);
+          cv[j] = lo + hi;
+        }
+        colacc[warp][g * 32 + lane] = transpose_reduce32(cv, lane);
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < nj; t += kSymThreads) {
+        float val = 0.f;
+#pragma unroll
+        for (int u = 0; u < kSymThreads / 32; ++u) val += colacc[u][t];
+        if (r0 == 0) colpart[c0 + t] = val;
+        else colpart[c0 + t] += val;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      float a[2];
+      f2_unpack(racc[q], a[0], a[1]);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = 2 * q + h;
+        if (!act[k]) continue;
+        const int i = r0 + warp * 128 + lane + 32 * k;
+        float val = a[h];
+        if constexpr (KID == CSFMM_KERNEL_LAPLACE)
+          val = (float)(-(0.69314718055994530942 * kInv4Pi) * ((double)val - (double)WS));
+        rowpart[i] = val;
+      }
+    }
+  }
+  if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < nS; t += kSymThreads)
+      colpart[t] = (float)(-(0.69314718055994530942 * kInv4Pi) * ((double)colpart[t] - (double)WT));
+  }
+}
+
 // Packed variant for one right-hand side and a scalar kernel (Laplace,
 // Newtonian, K = 1): same arithmetic per pair, two targets per instruction.
+// With part != nullptr the PP entries that belong to a cross pair come from the
+// symmetric cross-pair partials (final potentials, added in list order); the
+// self entry and entries without a mirror are evaluated here.
 template <int KID, int NP>
 __global__ void __launch_bounds__(kThreads, CSFMM_NEAR_MINB) near32x2_kernel(PlanView v, const int32_t *leaves,
                                                             const float *wsf, const float *wbar,
-                                                            int ldr, int r0, double *phi) {
+                                                            int ldr, int r0, double *phi,
+                                                            const float *part) {
   constexpr int NT = 2 * NP;
   __shared__ ulonglong2 sA[kTile], sB[kTile];
   __shared__ float wsum[kThreads / 32];
@@ -315,19 +491,29 @@ __global__ void __launch_bounds__(kThreads, CSFMM_NEAR_MINB) near32x2_kernel(Pla
   const float *wr = wsf + (int64_t)r0 * v.N;
   for (int i0 = b; i0 < e; i0 += kThreads * NT) {
     float ox[NT], oy[NT], oz[NT];
-    double out[NT];
+    double out[NT], pre[NT];  // evaluated here; read from the cross-pair partials
 #pragma unroll
     for (int k = 0; k < NT; ++k) {
       const int i = i0 + threadIdx.x + k * kThreads;
       const float4 o = v.off32[i < e ? i : b];
       ox[k] = o.x; oy[k] = o.y; oz[k] = o.z;
       out[k] = 0.0;
+      pre[k] = 0.0;
     }
     for (int pass = 0; pass < 2; ++pass) {
       const int type = pass == 0 ? CSFMM_LIST_PP : CSFMM_LIST_PC;
       const int e0 = v.loff[type][c], e1 = v.loff[type][c + 1];
       for (int ee = e0; ee < e1; ++ee) {
         const int s = v.lsrc[type][ee];
+        if (part && type == CSFMM_LIST_PP && v.sym_contrib[ee] >= 0) {
+          const float *pp = part + v.sym_contrib[ee] - b;
+#pragma unroll
+          for (int k = 0; k < NT; ++k) {
+            const int i = i0 + threadIdx.x + k * kThreads;
+            if (i < e) pre[k] += (double)pp[i];
+          }
+          continue;
+        }
         const float dcx = (float)(cTx - v.ccentre[3 * s]);
         const float dcy = (float)(cTy - v.ccentre[3 * s + 1]);
         const float dcz = (float)(cTz - v.ccentre[3 * s + 2]);
@@ -412,7 +598,7 @@ __global__ void __launch_bounds__(kThreads, CSFMM_NEAR_MINB) near32x2_kernel(Pla
 #pragma unroll
     for (int k = 0; k < NT; ++k) {
       const int i = i0 + threadIdx.x + k * kThreads;
-      if (i < e) phi[((int64_t)r0 * v.N + i)] = out[k];
+      if (i < e) phi[((int64_t)r0 * v.N + i)] = out[k] + pre[k];
     }
   }
 }
@@ -868,9 +1054,10 @@ void launch_multi_kid(const PlanView &v, bool far, int ngrid, const int32_t *lea
 
 template <int KID, int NR>
 void launch_nr(const PlanView &v, const int32_t *leaves, int nleaves, const float *wsf, int ldw,
-               const float *wbar, int ldr, int r0, double *phi, cudaStream_t st) {
+               const float *wbar, int ldr, int r0, double *phi, cudaStream_t st,
+               const float *part) {
   if constexpr (NR == 1 && KID != CSFMM_KERNEL_BIOT_SAVART) {
-    near32x2_kernel<KID, 2><<<nleaves, kThreads, 0, st>>>(v, leaves, wsf, wbar, ldr, r0, phi);
+    near32x2_kernel<KID, 2><<<nleaves, kThreads, 0, st>>>(v, leaves, wsf, wbar, ldr, r0, phi, part);
   } else {
     near32_kernel<KID, 2, NR><<<nleaves, kThreads, 0, st>>>(v, leaves, wsf, ldw, wbar, ldr, r0, phi);
   }
@@ -878,12 +1065,13 @@ void launch_nr(const PlanView &v, const int32_t *leaves, int nleaves, const floa
 
 template <int KID>
 void launch_kid(const PlanView &v, const int32_t *leaves, int nleaves, const float *wsf, int ldw,
-                const float *wbar, int ldr, int r0, int nr, double *phi, cudaStream_t st) {
+                const float *wbar, int ldr, int r0, int nr, double *phi, cudaStream_t st,
+                const float *part) {
   switch (nr) {
-    case 1: launch_nr<KID, 1>(v, leaves, nleaves, wsf, ldw, wbar, ldr, r0, phi, st); break;
-    case 2: launch_nr<KID, 2>(v, leaves, nleaves, wsf, ldw, wbar, ldr, r0, phi, st); break;
-    case 3: launch_nr<KID, 3>(v, leaves, nleaves, wsf, ldw, wbar, ldr, r0, phi, st); break;
-    default: launch_nr<KID, 4>(v, leaves, nleaves, wsf, ldw, wbar, ldr, r0, phi, st); break;
+    case 1: launch_nr<KID, 1>(v, leaves, nleaves, wsf, ldw, wbar, ldr, r0, phi, st, part); break;
+    case 2: launch_nr<KID, 2>(v, leaves, nleaves, wsf, ldw, wbar, ldr, r0, phi, st, nullptr); break;
+    case 3: launch_nr<KID, 3>(v, leaves, nleaves, wsf, ldw, wbar, ldr, r0, phi, st, nullptr); break;
+    default: launch_nr<KID, 4>(v, leaves, nleaves, wsf, ldw, wbar, ldr, r0, phi, st, nullptr); break;
   }
 }
 
@@ -914,12 +1102,23 @@ void launch_far32(const PlanView &v, int ncells, const float *wsf, const float *
 
 // nr right-hand sides r0 .. r0+nr-1 (nr <= 4).
 void launch_near32(const PlanView &v, const int32_t *leaves, int nleaves, const float *wsf, int ldw,
-                   const float *wbar, int ldr, int r0, int nr, double *phi, cudaStream_t st) {
+                   const float *wbar, int ldr, int r0, int nr, double *phi, cudaStream_t st,
+                   const float *part) {
   switch (v.kernel_id) {
-    case CSFMM_KERNEL_LAPLACE: launch_kid<CSFMM_KERNEL_LAPLACE>(v, leaves, nleaves, wsf, ldw, wbar, ldr, r0, nr, phi, st); break;
-    case CSFMM_KERNEL_BIOT_SAVART: launch_kid<CSFMM_KERNEL_BIOT_SAVART>(v, leaves, nleaves, wsf, ldw, wbar, ldr, r0, nr, phi, st); break;
-    case CSFMM_KERNEL_NEWTON: launch_kid<CSFMM_KERNEL_NEWTON>(v, leaves, nleaves, wsf, ldw, wbar, ldr, r0, nr, phi, st); break;
-    default: launch_kid<CSFMM_KERNEL_ONE>(v, leaves, nleaves, wsf, ldw, wbar, ldr, r0, nr, phi, st); break;
+    case CSFMM_KERNEL_LAPLACE: launch_kid<CSFMM_KERNEL_LAPLACE>(v, leaves, nleaves, wsf, ldw, wbar, ldr, r0, nr, phi, st, part); break;
+    case CSFMM_KERNEL_BIOT_SAVART: launch_kid<CSFMM_KERNEL_BIOT_SAVART>(v, leaves, nleaves, wsf, ldw, wbar, ldr, r0, nr, phi, st, nullptr); break;
+    case CSFMM_KERNEL_NEWTON: launch_kid<CSFMM_KERNEL_NEWTON>(v, leaves, nleaves, wsf, ldw, wbar, ldr, r0, nr, phi, st, part); break;
+    default: launch_kid<CSFMM_KERNEL_ONE>(v, leaves, nleaves, wsf, ldw, wbar, ldr, r0, nr, phi, st, part); break;
+  }
+}
+
+void launch_pp_sym32(const PlanView &v, const int2 *pairs, const int32_t *off, int npairs,
+                     const float *wsf, float *part, cudaStream_t st) {
+  if (npairs <= 0) return;
+  switch (v.kernel_id) {
+    case CSFMM_KERNEL_LAPLACE: pp_sym_kernel<CSFMM_KERNEL_LAPLACE><<<npairs, kSymThreads, 0, st>>>(v, pairs, off, wsf, part); break;
+    case CSFMM_KERNEL_NEWTON: pp_sym_kernel<CSFMM_KERNEL_NEWTON><<<npairs, kSymThreads, 0, st>>>(v, pairs, off, wsf, part); break;
+    default: pp_sym_kernel<CSFMM_KERNEL_ONE><<<npairs, kSymThreads, 0, st>>>(v, pairs, off, wsf, part); break;
   }
 }
 

@@ -73,8 +73,10 @@ int kdim(int k) { return k == CSFMM_KERNEL_BIOT_SAVART ? 3 : 1; }
 // Device bytes of one workspace for R right-hand sides (mirrors workspace_alloc).
 int64_t workspace_bytes_estimate(int64_t N, int64_t cells, int64_t P, int64_t dim, int64_t real,
                                  int64_t R) {
-  return R * N * 8 + (real == 4 ? R * N * 4 : 0) + cells * R * P * (real + 8 * dim) +
-         R * N * dim * 8;
+  // FP32 form: single-precision weights and the symmetric near field's
+  // cross-pair partials (one float per point and PP partner, ~36 partners)
+  return R * N * 8 + (real == 4 ? R * N * 4 + 36 * N * 4 : 0) +
+         cells * R * P * (real + 8 * dim) + R * N * dim * 8;
 }
 
 // Device bytes of a plan built with CSFMM_SERVER_MAX_NRHS right-hand sides

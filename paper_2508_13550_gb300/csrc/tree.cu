@@ -664,6 +664,67 @@ __global__ void leaf_flags_kernel(const int32_t *cchild, int ncells, int32_t *fl
 }
 
 // ---------------------------------------------------------------------------
+// Cross pairs of the symmetric near field.
+// ---------------------------------------------------------------------------
+// Index of the PP entry (s, c) in s's row (sources sorted), or -1.
+__device__ __forceinline__ int mirror_entry(const int32_t *off, const int32_t *src, int s, int c) {
+  int lo = off[s], hi = off[s + 1];
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (src[mid] < c) lo = mid + 1;
+    else hi = mid;
+  }
+  return (lo < off[s + 1] && src[lo] == c) ? lo : -1;
+}
+
+// The lists are not mirror-symmetric in general (the two traversal orders can
+// resolve a region at different levels), so a PP entry (c, s), s > c, is a
+// cross pair only if (s, c) is also a PP entry.
+__global__ void sym_flag_kernel(const int32_t *off, const int32_t *src, int ncells, int32_t *flag) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncells) return;
+  for (int q = off[c]; q < off[c + 1]; ++q) {
+    const int s = src[q];
+    flag[q] = s > c && mirror_entry(off, src, s, c) >= 0;
+  }
+}
+
+__global__ void sym_emit_kernel(const int32_t *off, const int32_t *src, int ncells,
+                                const int32_t *flag, const int32_t *pidx, const int32_t *cbegin,
+                                const int32_t *cend, int2 *pairs, int32_t *sizes) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncells) return;
+  for (int q = off[c]; q < off[c + 1]; ++q) {
+    if (!flag[q]) continue;
+    const int s = src[q];
+    pairs[pidx[q]] = make_int2(c, s);
+    sizes[pidx[q]] = (cend[c] - cbegin[c]) + (cend[s] - cbegin[s]);
+  }
+}
+
+// contrib[q] for PP entry q = (c, s): where leaf c's partial sums of this
+// interaction start in the partial buffer (rows of pair (c, s) if s > c,
+// columns of pair (s, c) if s < c), -1 for the self entry.
+__global__ void sym_contrib_kernel(const int32_t *off, const int32_t *src, int ncells,
+                                   const int32_t *flag, const int32_t *pidx,
+                                   const int32_t *sym_off, const int32_t *cbegin,
+                                   const int32_t *cend, int32_t *contrib) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncells) return;
+  for (int q = off[c]; q < off[c + 1]; ++q) {
+    const int s = src[q];
+    int val = -1;  // evaluated directly by the near-field kernel
+    if (s > c) {
+      if (flag[q]) val = sym_off[pidx[q]];
+    } else if (s < c) {
+      const int m = mirror_entry(off, src, s, c);
+      if (m >= 0 && flag[m]) val = sym_off[pidx[m]] + (cend[s] - cbegin[s]);
+    }
+    contrib[q] = val;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Host driver.
 // ---------------------------------------------------------------------------
 namespace {
@@ -723,6 +784,7 @@ PlanView Plan::view() const {
   v.cchild = cchild; v.ccentre = ccentre; v.cradius = cradius; v.cxmid = cxmid; v.cymid = cymid;
   v.chalf = chalf; v.proxy = proxy; v.proxy32 = proxy32;
   for (int t = 0; t < 4; ++t) { v.loff[t] = loff[t]; v.lsrc[t] = lsrc[t]; }
+  v.sym_contrib = sym_contrib;
   v.m2m64 = m2m64; v.m2m32 = m2m32; v.cheb = cheb; v.status = status;
   return v;
 }
@@ -1020,6 +1082,49 @@ csfmm_status build_tree(Plan &pl, const double *points, cudaStream_t st) {
     list_offsets_kernel<<<grid_for(nc + 1, 128), 128, 0, st>>>(lk, lo, hi, ty, bits, nc,
                                                                 pl.loff[ty], pl.lsrc[ty]);
     CSFMM_CUDA(cudaGetLastError());
+  }
+
+  // symmetric near field: cross pairs of the PP lists (FP32 form)
+  if (pl.precision == CSFMM_FP32_BULK && pl.nlist[CSFMM_LIST_PP] > 0) {
+    const int npp = (int)pl.nlist[CSFMM_LIST_PP];
+    int32_t *flag, *pidx, *sizes;
+    CSFMM_TRY(tmp.alloc(&flag, npp));
+    CSFMM_TRY(tmp.alloc(&pidx, npp));
+    sym_flag_kernel<<<grid_for(nc, 128), 128, 0, st>>>(pl.loff[CSFMM_LIST_PP],
+                                                        pl.lsrc[CSFMM_LIST_PP], nc, flag);
+    CSFMM_CUDA(cudaGetLastError());
+    need = scan_tmp_elems(npp);
+    if (need > scan_tmp_cap) {
+      CSFMM_TRY(tmp.alloc(&scan_tmp, need));
+      scan_tmp_cap = need;
+    }
+    int32_t npairs = 0;
+    CSFMM_TRY(exclusive_scan_i32(flag, pidx, npp, &npairs, scan_tmp, st));
+    if (npairs > 0) {
+      CSFMM_TRY(A.alloc(&pl.sym_pairs, npairs));
+      CSFMM_TRY(A.alloc(&pl.sym_off, npairs));
+      CSFMM_TRY(tmp.alloc(&sizes, npairs));
+      sym_emit_kernel<<<grid_for(nc, 128), 128, 0, st>>>(pl.loff[CSFMM_LIST_PP],
+                                                          pl.lsrc[CSFMM_LIST_PP], nc, flag, pidx,
+                                                          pl.cbegin, pl.cend, pl.sym_pairs, sizes);
+      CSFMM_CUDA(cudaGetLastError());
+      need = scan_tmp_elems(npairs);
+      if (need > scan_tmp_cap) {
+        CSFMM_TRY(tmp.alloc(&scan_tmp, need));
+        scan_tmp_cap = need;
+      }
+      // sizes sum to < 2^31 floats: each point appears once per PP partner
+      int32_t part_len = 0;
+      CSFMM_TRY(exclusive_scan_i32(sizes, pl.sym_off, npairs, &part_len, scan_tmp, st));
+      CSFMM_TRY(A.alloc(&pl.sym_contrib, npp));
+      sym_contrib_kernel<<<grid_for(nc, 128), 128, 0, st>>>(pl.loff[CSFMM_LIST_PP],
+                                                             pl.lsrc[CSFMM_LIST_PP], nc, flag,
+                                                             pidx, pl.sym_off, pl.cbegin, pl.cend,
+                                                             pl.sym_contrib);
+      CSFMM_CUDA(cudaGetLastError());
+      pl.n_sym_pairs = npairs;
+      pl.sym_part_len = part_len;
+    }
   }
 
   // statistics from the host copies

@@ -321,3 +321,21 @@ def test_graph_replay_matches_direct_launches(torch, C, precision):
             s.synchronize()
             assert np.array_equal(got.cpu().numpy(), ref.cpu().numpy()), call
     C.plan_sync(graph, stream=s.cuda_stream)
+
+
+@pytest.mark.parametrize("kernel", [O.KERNEL_NEWTON, O.KERNEL_LAPLACE, O.KERNEL_ONE])
+def test_fp32_symmetric_near_field(torch, C, kernel):
+    """One right-hand side in FP32 bulk evaluates mirrored PP leaf pairs once
+    for both directions; the result agrees with the two-RHS launch (which
+    evaluates every PP entry directly) and with the FP64 FMM."""
+    pts = I.random_sphere_points(20000, 31)
+    w = np.random.default_rng(32).uniform(0.5, 1.5, len(pts)) * (4 * math.pi / len(pts))
+    P32 = C.plan_create(dev(torch, pts), kernel, 5, 0.7, 40, precision=C.FP32_BULK)
+    st = C.plan_stats(P32)
+    assert st["sym_pairs"] > 0.3 * st["n_list"][0] / 2
+    one = C.evaluate(P32, dev(torch, w[None])).cpu().numpy()[0]
+    two = C.evaluate(P32, dev(torch, np.stack([w, w]))).cpu().numpy()
+    P64 = C.plan_create(dev(torch, pts), kernel, 5, 0.7, 40, precision=C.FP64)
+    ref = C.evaluate(P64, dev(torch, w[None])).cpu().numpy()[0]
+    assert rel(one, two[0]) <= 1e-6
+    assert rel(one, ref) <= 1e-5
