@@ -317,14 +317,24 @@ def run_ours(args):
 
     peaks, peak_kind = load_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    near_ms = phases["near"] / max(calls, 1)
-    near_evals = st["evals"][0] + st["evals"][1]
-    # ALU roofline of the near-field kernel: per evaluation 7 FP32-pipe
-    # operations and one MUFU operation; GB300 SM: 128 FP32 lanes and 16 MUFU
+    # ALU roofline: per kernel evaluation 7 FP32-pipe operations and one MUFU
+    # operation (rsqrt / lg2 / rcp); a GB300 SM has 128 FP32 lanes and 16 MUFU
     # lanes per clock, so the MUFU pipe bounds at 16 evaluations/clock/SM.
     per_sm_clk = {2: 16.0, 0: 16.0, 1: 128.0 / 11.0, 100: 128.0 / 4.0}[wl["kernel"]]
     peak_evals = 152 * per_sm_clk * sm_max * 1e6 * nrhs
-    achieved = near_evals * nrhs / (near_ms / 1e3)
+    ncalls = max(calls, 1)
+    ev_sym = st.get("sym_evals", 0) if nrhs == 1 else 0
+    kern = {
+        # kernel: (kernel evaluations per launch, ms per launch)
+        "pp_sym_kernel (mirrored PP pairs, one evaluation per pair)":
+            (ev_sym, phases.get("ppsym", 0.0) / ncalls),
+        "near32x2_kernel (self and unmirrored PP, PC)":
+            (st["evals"][0] + st["evals"][1] - 2 * ev_sym, phases["near"] / ncalls),
+        "far32x2_kernel (CC, CP)": (st["evals"][2] + st["evals"][3], phases["far"] / ncalls),
+    }
+    dom = max(kern, key=lambda k: kern[k][1])
+    dom_evals, dom_ms = kern[dom]
+    achieved = dom_evals * nrhs / (dom_ms / 1e3)
     traffic = None
     line = {
         "metric": "FMM targets/s at N=6.3M", "value": value, "unit": "targets/s",
@@ -345,11 +355,15 @@ def run_ours(args):
         "gpu_launches": launches,
         "e2e": {"value": e2e_val, "unit": "targets/s",
                 "h2d_bytes_per_step": int(w.nbytes), "d2h_bytes_per_step": int(8 * nrhs * N * dim)},
-        "roofline": {"kernel": "near_kernel (PP + PC)", "bound": "alu",
+        "roofline": {"kernel": dom, "bound": "alu",
                      "achieved": achieved / 1e9, "peak": peak_evals / 1e9, "unit": "Geval/s",
                      "frac": achieved / peak_evals, "traffic": traffic,
                      "peak_source": f"{peak_kind} sm_max_mhz x 152 SMs x {per_sm_clk:.1f} "
                                     "evals/clk/SM"},
+        "kernels": {k: {"evals_per_launch": e, "ms_per_launch": m,
+                        "geval_per_s": (e * nrhs / (m / 1e3) / 1e9) if m > 0 else None,
+                        "frac_of_alu_peak": (e * nrhs / (m / 1e3) / peak_evals) if m > 0 else None}
+                    for k, (e, m) in kern.items()},
         "clocks": clk.summary(),
     }
     if rank == 0 and world == 1 and args.serve_sample > 0:

@@ -98,12 +98,14 @@ typedef struct {
   double build_ms;         /* wall time of csfmm_plan_create */
   int64_t launches_per_evaluate; /* kernels launched by the last evaluation */
   int64_t sym_pairs;       /* FP32 bulk: PP leaf pairs evaluated once for both directions */
+  int64_t sym_evals;       /* kernel evaluations of those pairs (each serves two interactions) */
 } csfmm_stats;
 
 /* Evaluation phases timed by csfmm_plan_phase_times. */
 enum {
   CSFMM_PHASE_GATHER = 0, CSFMM_PHASE_P2M = 1, CSFMM_PHASE_M2M = 2, CSFMM_PHASE_FAR = 3,
-  CSFMM_PHASE_NEAR = 4, CSFMM_PHASE_L2L = 5, CSFMM_PHASE_L2P = 6, CSFMM_NUM_PHASES = 7
+  CSFMM_PHASE_PPSYM = 4, /* FP32 bulk, one RHS: mirrored PP pairs (empty otherwise) */
+  CSFMM_PHASE_NEAR = 5, CSFMM_PHASE_L2L = 6, CSFMM_PHASE_L2P = 7, CSFMM_NUM_PHASES = 8
 };
 
 /* Builds a plan on the current device: sorts the points into cubed-sphere

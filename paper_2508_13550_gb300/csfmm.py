@@ -67,7 +67,8 @@ class Stats(ctypes.Structure):
                 ("n_list", ctypes.c_int64 * 4), ("evals", ctypes.c_int64 * 4),
                 ("pairs_covered", ctypes.c_int64), ("mac_margin", ctypes.c_double),
                 ("device_bytes", ctypes.c_int64), ("build_ms", ctypes.c_double),
-                ("launches_per_evaluate", ctypes.c_int64), ("sym_pairs", ctypes.c_int64)]
+                ("launches_per_evaluate", ctypes.c_int64), ("sym_pairs", ctypes.c_int64),
+                ("sym_evals", ctypes.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -380,7 +381,7 @@ def plan_export_proxy_weights(plan: Plan, nrhs: int = 1):
     return wb
 
 
-PHASES = ("gather", "p2m", "m2m", "far", "near", "l2l", "l2p")
+PHASES = ("gather", "p2m", "m2m", "far", "ppsym", "near", "l2l", "l2p")
 
 
 def plan_enable_timing(plan: Plan, on: bool = True):

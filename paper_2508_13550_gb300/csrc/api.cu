@@ -198,7 +198,6 @@ csfmm_status csfmm_plan_create(const double *points, int64_t N, int kernel_id, i
   S.ncells = pl.ncells;
   S.nleaves = pl.nleaves;
   S.device_bytes = pl.arena.bytes + pl.ws->arena.bytes;
-  S.sym_pairs = pl.n_sym_pairs;
   S.build_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   *out = h;
   return CSFMM_OK;

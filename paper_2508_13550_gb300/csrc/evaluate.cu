@@ -668,7 +668,7 @@ csfmm_status run_passes(Plan &pl, Workspace &W, const double *w, int nrhs, doubl
     }
     ++pl.launches;
   }
-  CSFMM_MARK(CSFMM_PHASE_NEAR);
+  CSFMM_MARK(CSFMM_PHASE_PPSYM);
   // single right-hand side, symmetric scalar kernel: the cross pairs of the PP
   // lists are evaluated once for both directions first
   const bool sym = sizeof(Real) == 4 && nrhs == 1 && KID != CSFMM_KERNEL_BIOT_SAVART &&
@@ -677,6 +677,7 @@ csfmm_status run_passes(Plan &pl, Workspace &W, const double *w, int nrhs, doubl
     launch_pp_sym32(v, pl.sym_pairs, pl.sym_off, pl.n_sym_pairs, W.wsf, W.sym_part, st);
     ++pl.launches;
   }
+  CSFMM_MARK(CSFMM_PHASE_NEAR);
   for (int r0 = 0; r0 < nrhs; r0 += chunk(r0)) {
     const int nr = chunk(r0);
     if constexpr (sizeof(Real) == 4) {

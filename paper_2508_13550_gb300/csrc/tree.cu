@@ -1151,6 +1151,16 @@ csfmm_status build_tree(Plan &pl, const double *points, cudaStream_t st) {
       pl.stats.n_list[t] = pl.nlist[t];
     }
     pl.stats.pairs_covered = covered;
+    if (pl.n_sym_pairs > 0) {
+      std::vector<int2> hp((size_t)pl.n_sym_pairs);
+      CSFMM_CUDA(cudaMemcpyAsync(hp.data(), pl.sym_pairs, sizeof(int2) * hp.size(),
+                                 cudaMemcpyDeviceToHost, st));
+      CSFMM_CUDA(cudaStreamSynchronize(st));
+      int64_t se = 0;
+      for (const int2 &q : hp) se += (int64_t)(he[q.x] - hb[q.x]) * (he[q.y] - hb[q.y]);
+      pl.stats.sym_pairs = pl.n_sym_pairs;
+      pl.stats.sym_evals = se;
+    }
   }
   CSFMM_CUDA(cudaStreamSynchronize(st));
   return CSFMM_OK;
