@@ -536,6 +536,9 @@ __device__ __forceinline__ void df_fma(float &S, float &C, float ah, float al, f
   C = __fadd_rn(C, __fadd_rn(q, e));
 }
 
+// PC = p as a compile-time constant (0: runtime p) keeps each point's rows in
+// registers and unrolls the contractions.
+template <int PC>
 __global__ void __launch_bounds__(kL2PThreads) l2p_df_kernel(PlanView v, const int32_t *leaves,
                                                              const double *psi, int ldr, int nrhs,
                                                              int dim, const double *phi,
@@ -544,7 +547,8 @@ __global__ void __launch_bounds__(kL2PThreads) l2p_df_kernel(PlanView v, const i
   __shared__ float sLa[kL2PThreads * kMaxP], sLal[kL2PThreads * kMaxP];
   __shared__ float sLb[kL2PThreads * kMaxP], sLbl[kL2PThreads * kMaxP];
   const int c = leaves[blockIdx.x];
-  const int b = v.cbegin[c], e = v.cend[c], p = v.p, P = v.P;
+  const int b = v.cbegin[c], e = v.cend[c];
+  const int p = PC > 0 ? PC : v.p, P = p * p;
   for (int i0 = b; i0 < e; i0 += kL2PThreads) {
     const int nj = min(kL2PThreads, e - i0);
     __syncthreads();
@@ -571,16 +575,57 @@ __global__ void __launch_bounds__(kL2PThreads) l2p_df_kernel(PlanView v, const i
           const float *lah = sLa + t * p, *lal = sLal + t * p;
           const float *lbh = sLb + t * p, *lbl = sLbl + t * p;
           float S = 0.f, C = 0.f;
-          for (int m1 = 0; m1 < p; ++m1) {
-            float sh = 0.f, sl = 0.f;
-            for (int m2 = 0; m2 < p; ++m2)
-              df_fma(sh, sl, sph[m1 * p + m2], spl[m1 * p + m2], lbh[m2], lbl[m2]);
-            df_fma(S, C, lah[m1], lal[m1], sh, sl);
+          if constexpr (PC > 0) {
+            float bh[PC], bl[PC];
+#pragma unroll
+            for (int m2 = 0; m2 < PC; ++m2) {
+              bh[m2] = lbh[m2];
+              bl[m2] = lbl[m2];
+            }
+#pragma unroll
+            for (int m1 = 0; m1 < PC; ++m1) {
+              float sh = 0.f, sl = 0.f;
+#pragma unroll
+              for (int m2 = 0; m2 < PC; ++m2)
+                df_fma(sh, sl, sph[m1 * PC + m2], spl[m1 * PC + m2], bh[m2], bl[m2]);
+              df_fma(S, C, lah[m1], lal[m1], sh, sl);
+            }
+          } else {
+            for (int m1 = 0; m1 < p; ++m1) {
+              float sh = 0.f, sl = 0.f;
+              for (int m2 = 0; m2 < p; ++m2)
+                df_fma(sh, sl, sph[m1 * p + m2], spl[m1 * p + m2], lbh[m2], lbl[m2]);
+              df_fma(S, C, lah[m1], lal[m1], sh, sl);
+            }
           }
           const int64_t oi = ((int64_t)r * v.N + i) * dim + d;
           out[((int64_t)r * v.N + v.perm[i]) * dim + d] = phi[oi] + ((double)S + (double)C);
         }
       }
+  }
+}
+
+void launch_l2p_df(int p, int nleaves, const PlanView &v, const int32_t *leaves, const double *psi,
+                   int ldr, int nrhs, int dim, const double *phi, double *out, cudaStream_t st) {
+#define CSFMM_L2P(PC) \
+  l2p_df_kernel<PC><<<nleaves, kL2PThreads, 0, st>>>(v, leaves, psi, ldr, nrhs, dim, phi, out)
+  switch (p) {
+    case 7: CSFMM_L2P(7); break;
+    case 9: CSFMM_L2P(9); break;
+    case 11: CSFMM_L2P(11); break;
+    case 13: CSFMM_L2P(13); break;
+    default: CSFMM_L2P(0); break;
+  }
+#undef CSFMM_L2P
+}
+
+const void *l2p_df_function(int p) {
+  switch (p) {
+    case 7: return (const void *)l2p_df_kernel<7>;
+    case 9: return (const void *)l2p_df_kernel<9>;
+    case 11: return (const void *)l2p_df_kernel<11>;
+    case 13: return (const void *)l2p_df_kernel<13>;
+    default: return (const void *)l2p_df_kernel<0>;
   }
 }
 
@@ -699,7 +744,7 @@ csfmm_status run_passes(Plan &pl, Workspace &W, const double *w, int nrhs, doubl
   }
   CSFMM_MARK(CSFMM_PHASE_L2P);
   if constexpr (sizeof(Real) == 4)
-    l2p_df_kernel<<<pl.nleaves, kL2PThreads, 0, st>>>(v, pl.leaves, psi, ldr, nrhs, dim, W.phi, out);
+    launch_l2p_df(pl.p, pl.nleaves, v, pl.leaves, psi, ldr, nrhs, dim, W.phi, out, st);
   else
     l2p_kernel<double><<<pl.nleaves, kL2PThreads, 0, st>>>(v, pl.leaves, psi, ldr, nrhs, dim, W.phi, out);
   ++pl.launches;
@@ -788,7 +833,7 @@ csfmm_status capture(Plan &pl, Workspace &W, const double *w, int nrhs, double *
   CSFMM_CUDA(cudaGraphGetNodes(graph, nodes.data(), &n));
   const void *f_gather = (const void *)gather_kernel;
   const void *f_l2p = pl.precision == CSFMM_FP64 ? (const void *)l2p_kernel<double>
-                                                 : (const void *)l2p_df_kernel;
+                                                 : l2p_df_function(pl.p);
   for (cudaGraphNode_t nd : nodes) {
     cudaGraphNodeType ty;
     CSFMM_CUDA(cudaGraphNodeGetType(nd, &ty));
