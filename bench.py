@@ -164,6 +164,41 @@ def cpu_oracle_sample(pts, w, wl, n_leaves, seed, repeats=1):
     return len(tg) / dt, dt, len(tg), O.num_threads()
 
 
+def fp64_at_matched_accuracy(Cs, torch, dpts, dw, wl, dim, dtg, ds, err32, ms32_per_rhs):
+    """The plain single-RHS FP64 GPU FMM at the accuracy of the FP32-bulk
+    form: the smallest degree n' (N0 = 4 n'^2, same MAC) whose error against
+    the FP64 direct sum on the same sampled targets is at most err32, timed
+    with CUDA events.  Returns the degrees tried and the speedup of the
+    FP32-bulk evaluation over that FP64 evaluation."""
+    dev = dpts.device
+    stream = torch.cuda.current_stream(dev)
+    tried = []
+    for n in range(4, wl["n"] + 1):
+        p = Cs.plan_create(dpts, wl["kernel"], n, wl["theta"], 4 * n * n, precision=Cs.FP64,
+                           max_nrhs=1)
+        o = torch.empty((1, dpts.shape[0], dim), dtype=torch.float64, device=dev)
+        Cs.evaluate(p, dw[:1], out=o)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        Cs.evaluate(p, dw[:1], out=o)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        e = float(torch.linalg.norm(o[:1, dtg] - ds) / torch.linalg.norm(ds))
+        ms = e0.elapsed_time(e1)
+        Cs.plan_destroy(p)
+        del o
+        tried.append({"degree": n, "max_leaf": 4 * n * n, "rel_err_vs_fp64_ds": e,
+                      "ms_per_eval_1rhs": ms})
+        if e <= err32:
+            return {"degree": n, "ms_per_eval_1rhs": ms, "rel_err_vs_fp64_ds": e,
+                    "fp32_bulk_rel_err": err32,
+                    "speedup_of_fp32_bulk_per_rhs": ms / ms32_per_rhs, "tried": tried}
+    return {"degree": None, "fp32_bulk_rel_err": err32, "tried": tried,
+            "note": "no FP64 degree up to the workload's reaches the FP32-bulk error"}
+
+
 def run_reference(args):
     """CPU oracle arm: each step evaluates a bounded sample of the workload."""
     rank = int(os.environ.get("RANK", "0"))
@@ -296,6 +331,7 @@ def run_ours(args):
 
     # the plain single-RHS FP64 GPU FMM on the same workload, for the speedup
     fp64 = None
+    fp64_matched = None
     if args.fp64_compare and prec == Cs.FP32_BULK:
         p64 = Cs.plan_create(dpts, wl["kernel"], wl["n"], wl["theta"], wl["N0"],
                              precision=Cs.FP64, max_nrhs=1)
@@ -314,6 +350,8 @@ def run_ours(args):
                 "speedup_of_fp32_bulk_per_rhs": ms64 / (ms_step / nrhs)}
         Cs.plan_destroy(p64)
         del o64
+        fp64_matched = fp64_at_matched_accuracy(Cs, torch, dpts, dw, wl, dim, dtg, ds, err,
+                                                ms_step / nrhs)
 
     peaks, peak_kind = load_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -352,6 +390,7 @@ def run_ours(args):
         "phase_ms": {k: v / max(calls, 1) for k, v in phases.items()},
         "plan_build_ms": st["build_ms"],
         "fp64_gpu_fmm": fp64,
+        "fp64_gpu_fmm_at_matched_accuracy": fp64_matched,
         "gpu_launches": launches,
         "e2e": {"value": e2e_val, "unit": "targets/s",
                 "h2d_bytes_per_step": int(w.nbytes), "d2h_bytes_per_step": int(8 * nrhs * N * dim)},
@@ -416,40 +455,60 @@ def run_serving(args, sample=None):
 
 def run_accuracy_sweep(args):
     """E(FS64, DS) (FMM truncation) and E(FS32, DS) (FP32-bulk form) against
-    an FP64 GPU direct sum on sampled targets, for degrees n = 2..12 (N0 = 4n^2,
-    MAC 0.7), land-masked Newtonian field and Y43 Poisson field on the cubed
-    sphere with m = args.sweep_m."""
+    an FP64 GPU direct sum on sampled targets (MAC 0.7, N0 = 4 n^2):
+    land-masked Newtonian field on the cubed sphere with m = args.sweep_m and
+    the Y43 Poisson field with m = args.sweep_m / 2, for the degrees in
+    args.sweep_degrees; then the 16-RHS Poisson workload (m = 512, n = 10)
+    over all right-hand sides."""
     import torch
     from paper_2508_13550_gb300 import csfmm as Cs
     from paper_2508_13550_gb300 import inputs as I
-    m = args.sweep_m
     rows = []
-    fields = {"newton": (Cs.KERNEL_NEWTON, None), "laplace_y43": (Cs.KERNEL_LAPLACE, None)}
-    pts, A = I.cubed_sphere_grid(m)
-    f_newton = I.land_mask_field(pts, I.MASTER_SEED + 3) * A
-    f_y43 = I.real_sph_harm(4, 3, pts) * A
-    dp = torch.from_numpy(pts).cuda()
-    rng = np.random.default_rng(20250813)
-    tg = torch.from_numpy(np.sort(rng.choice(len(pts), args.err_samples, replace=False))
-                          .astype(np.int64)).cuda()
-    for name, kid, w in (("newton", Cs.KERNEL_NEWTON, f_newton),
-                         ("laplace_y43", Cs.KERNEL_LAPLACE, f_y43)):
+    degrees = [int(x) for x in args.sweep_degrees.split(",")]
+
+    def errors(dp, kid, dw, tg, ds, n, N0, nrhs):
+        row = {}
+        for key, prec in (("E64", Cs.FP64), ("E32", Cs.FP32_BULK)):
+            P = Cs.plan_create(dp, kid, n, 0.7, N0, precision=prec, max_nrhs=nrhs)
+            out = Cs.evaluate(P, dw)
+            torch.cuda.synchronize()
+            d = out[:, tg] - ds
+            row[key] = float(torch.linalg.norm(d) / torch.linalg.norm(ds))
+            row[key + "_bias"] = float(d.sum() / ds.abs().sum())
+            Cs.plan_destroy(P)
+        row["E32_over_E64"] = row["E32"] / row["E64"]
+        return row
+
+    def sample(N, seed=20250813):
+        rng = np.random.default_rng(seed)
+        return torch.from_numpy(np.sort(rng.choice(N, args.err_samples, replace=False))
+                                .astype(np.int64)).cuda()
+
+    for name, kid, m in (("newton", Cs.KERNEL_NEWTON, args.sweep_m),
+                         ("laplace_y43", Cs.KERNEL_LAPLACE, args.sweep_m // 2)):
+        pts, A = I.cubed_sphere_grid(m)
+        w = (I.land_mask_field(pts, I.MASTER_SEED + 3) if name == "newton"
+             else I.real_sph_harm(4, 3, pts)) * A
+        dp = torch.from_numpy(pts).cuda()
         dw = torch.from_numpy(w[None].copy()).cuda()
+        tg = sample(len(pts))
         ds = Cs.direct(dp, kid, dw, precision=Cs.FP64, targets=tg)
-        nrm = torch.linalg.norm(ds)
-        for n in range(2, 13, 2):
-            row = {"field": name, "n": n, "N0": 4 * n * n}
-            for key, prec in (("E64", Cs.FP64), ("E32", Cs.FP32_BULK)):
-                P = Cs.plan_create(dp, kid, n, 0.7, 4 * n * n, precision=prec, max_nrhs=1)
-                out = Cs.evaluate(P, dw)
-                torch.cuda.synchronize()
-                row[key] = float(torch.linalg.norm(out[:, tg] - ds) / nrm)
-                Cs.plan_destroy(P)
-            row["E32_over_E64"] = row["E32"] / row["E64"]
+        for n in degrees:
+            row = {"field": name, "m": m, "N": len(pts), "n": n, "N0": 4 * n * n}
+            row.update(errors(dp, kid, dw, tg, ds, n, 4 * n * n, 1))
             rows.append(row)
             log(row)
+    pts, A, w, _ = I.workload_multi_rhs(512, 16, with_exact=False)
+    dp = torch.from_numpy(pts).cuda()
+    dw = torch.from_numpy(np.ascontiguousarray(w)).cuda()
+    tg = sample(len(pts))
+    ds = Cs.direct(dp, Cs.KERNEL_LAPLACE, dw, precision=Cs.FP64, targets=tg)
+    row = {"field": "poisson_16rhs", "m": 512, "N": len(pts), "n": 10, "N0": 400}
+    row.update(errors(dp, Cs.KERNEL_LAPLACE, dw, tg, ds, 10, 400, 16))
+    rows.append(row)
+    log(row)
     return {"metric": "FMM rel err vs FP64 direct sum (degree sweep)", "unit": "rel l2",
-            "config": {"workload": "accuracy-sweep", "m": m, "N": len(pts), "theta": 0.7,
+            "config": {"workload": "accuracy-sweep", "theta": 0.7,
                        "err_samples": args.err_samples}, "rows": rows}
 
 
@@ -467,7 +526,8 @@ def main():
     ap.add_argument("--ref-leaves", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", dest="fp64_compare", action="store_false")
-    ap.add_argument("--sweep-m", type=int, default=256)
+    ap.add_argument("--sweep-m", type=int, default=1024)
+    ap.add_argument("--sweep-degrees", default="6,8,10,12")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-sample", type=int, default=300,
                     help="requests of the serving stream measured in the default line (0: none)")

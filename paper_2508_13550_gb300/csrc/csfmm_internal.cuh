@@ -82,7 +82,7 @@ struct PlanView {
   const double *x;       // [3][N]
   const int32_t *perm;   // [N]
   const double *La64, *Lb64;  // [N][p]
-  const float *La32, *Lb32;   // [N][p] FP32 rounding of La64, Lb64 ...
+  const float *La32, *Lb32;   // [N][p] stochastic FP32 rounding of the rows ...
   const float *La32lo, *Lb32lo;  // ... and of the remainders
   const float4 *off32;   // [N]
   const int32_t *cbegin, *cend, *clevel, *cface, *cparent, *cchild;
@@ -94,7 +94,7 @@ struct PlanView {
   const int32_t *loff[4], *lsrc[4];
   const int32_t *sym_contrib;
   const double *m2m64;   // [2][p][p]: M[q][k][m] = L_k((s_m + 2q - 1)/2)
-  const float *m2m32;
+  const float *m2m32;    // [2][2][p][p]: FP32 rounding of m2m64, then the remainders
   const double *cheb;    // [p]
   int *status;
 };

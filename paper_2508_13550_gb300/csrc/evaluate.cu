@@ -134,7 +134,11 @@ __global__ void gather_kernel(const int32_t *perm, const double *w, double *ws, 
 // ---------------------------------------------------------------------------
 // P2M: for leaf c, wbar[c][r][k1 p + k2] = sum_j La[j][k1] Lb[j][k2] w_r[j].
 // One block per leaf (blockDim >= P), one thread per proxy; the Lagrange
-// rows of CH points at a time are staged through shared memory (coalesced).
+// rows of CH points at a time are staged through shared memory (coalesced)
+// and each chunk's sum is added to an FP64 total.  The FP32 form reads the
+// stochastically rounded rows, so the rounding errors of the rows (and of
+// their products) differ from leaf to leaf even where every leaf holds the
+// same local point pattern.
 // ---------------------------------------------------------------------------
 template <typename Real, int NR>
 __global__ void p2m_kernel(PlanView v, const int32_t *leaves, const double *ws, int ldw, int r0,
@@ -146,9 +150,9 @@ __global__ void p2m_kernel(PlanView v, const int32_t *leaves, const double *ws, 
   const Real *La = La_of<Real>(v), *Lb = Lb_of<Real>(v);
   const int k = threadIdx.x;
   const int k1 = k / p, k2 = k - (k / p) * p;
-  Real acc[NR];
+  double acc[NR];
 #pragma unroll
-  for (int q = 0; q < NR; ++q) acc[q] = 0;
+  for (int q = 0; q < NR; ++q) acc[q] = 0.0;
   for (int j0 = b; j0 < e; j0 += CH) {
     const int nj = min(CH, e - j0);
     __syncthreads();
@@ -162,16 +166,21 @@ __global__ void p2m_kernel(PlanView v, const int32_t *leaves, const double *ws, 
     }
     __syncthreads();
     if (k < P) {
+      Real ch[NR];
+#pragma unroll
+      for (int q = 0; q < NR; ++q) ch[q] = 0;
       for (int j = 0; j < nj; ++j) {
         const Real l = sLa[j * p + k1] * sLb[j * p + k2];
 #pragma unroll
-        for (int q = 0; q < NR; ++q) acc[q] += l * sw[q * CH + j];
+        for (int q = 0; q < NR; ++q) ch[q] += l * sw[q * CH + j];
       }
+#pragma unroll
+      for (int q = 0; q < NR; ++q) acc[q] += (double)ch[q];
     }
   }
   if (k < P) {
 #pragma unroll
-    for (int q = 0; q < NR; ++q) wbar[((int64_t)c * ldr + r0 + q) * P + k] = acc[q];
+    for (int q = 0; q < NR; ++q) wbar[((int64_t)c * ldr + r0 + q) * P + k] = (Real)acc[q];
   }
 }
 
@@ -224,6 +233,84 @@ __global__ void m2m_kernel(PlanView v, int cell0, int r0, int nr, Real *wbar, in
 }
 
 // ---------------------------------------------------------------------------
+// Double-float arithmetic on the FP32 pipes for the FP32-form passes: a value
+// is an unevaluated pair (h, l), products carry their exact FP32 rounding
+// error (FMA) and sums use Knuth's two-sum.  The rounded intrinsics keep the
+// compiler from contracting a product into the following sum.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void df_acc_prod(float &sh, float &sl, float ah, float al, float bh,
+                                            float bl) {
+  const float ph = __fmul_rn(ah, bh);
+  float pe = fmaf(ah, bh, -ph);
+  pe = fmaf(ah, bl, pe);
+  pe = fmaf(al, bh, pe);
+  const float s = __fadd_rn(sh, ph);
+  const float bb = __fadd_rn(s, -sh);
+  const float e = __fadd_rn(__fadd_rn(sh, -__fadd_rn(s, -bb)), __fadd_rn(ph, -bb));
+  sh = s;
+  sl = __fadd_rn(sl, __fadd_rn(e, pe));
+}
+__device__ __forceinline__ void df_acc(float &sh, float &sl, float bh, float bl) {
+  const float s = __fadd_rn(sh, bh);
+  const float bb = __fadd_rn(s, -sh);
+  const float e = __fadd_rn(__fadd_rn(sh, -__fadd_rn(s, -bb)), __fadd_rn(bh, -bb));
+  sh = s;
+  sl = __fadd_rn(sl, __fadd_rn(e, bl));
+}
+
+// M2M of the FP32 form: same contraction as m2m_kernel with the matrices as
+// FP32 rounding + remainder (m2m32) and every sum in double-float; proxy
+// weights are stored in FP32.  The same constant matrices act on every cell
+// of every level, and the proxy weights of a smooth field repeat nearly the
+// same pattern from cell to cell, so rounding the contraction to FP32 biases
+// all proxy weights alike (measured: a relative bias of up to 8e-8 in the
+// potentials at degree 8); in double-float that bias is gone.
+__global__ void m2m_df_kernel(PlanView v, int cell0, int r0, int nr, float *wbar, int ldr) {
+  __shared__ float sMh[2 * kMaxP * kMaxP], sMl[2 * kMaxP * kMaxP];
+  __shared__ float sw[kMaxP * kMaxP], sth[kMaxP * kMaxP], stl[kMaxP * kMaxP];
+  const int c = cell0 + blockIdx.x;
+  const int p = v.p, P = v.P;
+  const int32_t *ch = v.cchild + 4 * c;
+  if (ch[0] < 0 && ch[1] < 0 && ch[2] < 0 && ch[3] < 0) return;
+  for (int t = threadIdx.x; t < 2 * p * p; t += blockDim.x) {
+    sMh[t] = v.m2m32[t];
+    sMl[t] = v.m2m32[2 * p * p + t];
+  }
+  for (int r = r0; r < r0 + nr; ++r) {
+    constexpr int kPer = (kMaxP * kMaxP + 127) / 128;
+    float ah[kPer], al[kPer];
+    for (int u = 0; u < kPer; ++u) ah[u] = al[u] = 0.f;
+    for (int q = 0; q < 4; ++q) {
+      const int cc = ch[q];
+      if (cc < 0) continue;
+      const int qa = q & 1, qb = q >> 1;
+      __syncthreads();
+      for (int t = threadIdx.x; t < P; t += blockDim.x) sw[t] = wbar[((int64_t)cc * ldr + r) * P + t];
+      __syncthreads();
+      // st[m1][k2] = sum_m2 M[qb][k2][m2] w[m1][m2]
+      for (int t = threadIdx.x; t < P; t += blockDim.x) {
+        const int m1 = t / p, k2 = t - m1 * p;
+        const int o = (qb * p + k2) * p;
+        float sh = 0.f, sl = 0.f;
+        for (int m2 = 0; m2 < p; ++m2) df_acc_prod(sh, sl, sMh[o + m2], sMl[o + m2], sw[m1 * p + m2], 0.f);
+        sth[t] = sh;
+        stl[t] = sl;
+      }
+      __syncthreads();
+      // acc[k1][k2] += sum_m1 M[qa][k1][m1] st[m1][k2]
+      for (int u = 0, t = threadIdx.x; t < P; ++u, t += blockDim.x) {
+        const int k1 = t / p, k2 = t - k1 * p;
+        const int o = (qa * p + k1) * p;
+        for (int m1 = 0; m1 < p; ++m1)
+          df_acc_prod(ah[u], al[u], sMh[o + m1], sMl[o + m1], sth[m1 * p + k2], stl[m1 * p + k2]);
+      }
+    }
+    for (int u = 0, t = threadIdx.x; t < P; ++u, t += blockDim.x)
+      wbar[((int64_t)c * ldr + r) * P + t] = __fadd_rn(ah[u], al[u]);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // L2L at one level: child psi += (M_qa (x) M_qb)^T parent psi.
 // ---------------------------------------------------------------------------
 template <typename Real>
@@ -260,6 +347,61 @@ __global__ void l2l_kernel(PlanView v, int cell0, int r0, int nr, int dim, Real 
           Real s = 0;
           for (int m1 = 0; m1 < p; ++m1) s += sM[(qa * p + m1) * p + n1] * st[m1 * p + n2];
           dst[t] += s;
+        }
+      }
+    }
+}
+
+// L2L of the FP32 form: the contraction of l2l_kernel in double-float on the
+// FP32 pipes (FP64 proxy potentials split into FP32 pairs on load, matrices
+// as FP32 rounding + remainder), each child value added to its FP64 slot.
+__global__ void l2l_df_kernel(PlanView v, int cell0, int r0, int nr, int dim, double *psi,
+                              int ldr) {
+  __shared__ float sMh[2 * kMaxP * kMaxP], sMl[2 * kMaxP * kMaxP];
+  __shared__ float sph[kMaxP * kMaxP], spl[kMaxP * kMaxP], sth[kMaxP * kMaxP], stl[kMaxP * kMaxP];
+  const int c = cell0 + blockIdx.x;
+  const int p = v.p, P = v.P;
+  const int32_t *ch = v.cchild + 4 * c;
+  if (ch[0] < 0 && ch[1] < 0 && ch[2] < 0 && ch[3] < 0) return;
+  for (int t = threadIdx.x; t < 2 * p * p; t += blockDim.x) {
+    sMh[t] = v.m2m32[t];
+    sMl[t] = v.m2m32[2 * p * p + t];
+  }
+  for (int r = r0; r < r0 + nr; ++r)
+    for (int d = 0; d < dim; ++d) {
+      __syncthreads();
+      for (int t = threadIdx.x; t < P; t += blockDim.x) {
+        const double x = psi[(((int64_t)c * ldr + r) * dim + d) * P + t];
+        const float h = __double2float_rn(x);
+        sph[t] = h;
+        spl[t] = __double2float_rn(x - (double)h);
+      }
+      for (int q = 0; q < 4; ++q) {
+        const int cc = ch[q];
+        if (cc < 0) continue;
+        const int qa = q & 1, qb = q >> 1;
+        __syncthreads();
+        // st[m1][n2] = sum_m2 psi[m1][m2] M[qb][m2][n2]
+        for (int t = threadIdx.x; t < P; t += blockDim.x) {
+          const int m1 = t / p, n2 = t - m1 * p;
+          float sh = 0.f, sl = 0.f;
+          for (int m2 = 0; m2 < p; ++m2) {
+            const int o = (qb * p + m2) * p + n2;
+            df_acc_prod(sh, sl, sph[m1 * p + m2], spl[m1 * p + m2], sMh[o], sMl[o]);
+          }
+          sth[t] = sh;
+          stl[t] = sl;
+        }
+        __syncthreads();
+        double *dst = psi + (((int64_t)cc * ldr + r) * dim + d) * P;
+        for (int t = threadIdx.x; t < P; t += blockDim.x) {
+          const int n1 = t / p, n2 = t - n1 * p;
+          float sh = 0.f, sl = 0.f;
+          for (int m1 = 0; m1 < p; ++m1) {
+            const int o = (qa * p + m1) * p + n1;
+            df_acc_prod(sh, sl, sMh[o], sMl[o], sth[m1 * p + n2], stl[m1 * p + n2]);
+          }
+          dst[t] += (double)sh + (double)sl;
         }
       }
     }
@@ -688,7 +830,10 @@ csfmm_status run_passes(Plan &pl, Workspace &W, const double *w, int nrhs, doubl
   CSFMM_MARK(CSFMM_PHASE_M2M);
   for (int l = pl.nlevels - 2; l >= 0; --l) {
     int c0 = pl.level_begin[l], nlev = pl.level_begin[l + 1] - c0;
-    m2m_kernel<Real><<<nlev, 128, 0, st>>>(v, c0, 0, nrhs, wbar, ldr);
+    if constexpr (sizeof(Real) == 4)
+      m2m_df_kernel<<<nlev, 128, 0, st>>>(v, c0, 0, nrhs, wbar, ldr);
+    else
+      m2m_kernel<Real><<<nlev, 128, 0, st>>>(v, c0, 0, nrhs, wbar, ldr);
     ++pl.launches;
   }
   CSFMM_MARK(CSFMM_PHASE_FAR);
@@ -739,7 +884,10 @@ csfmm_status run_passes(Plan &pl, Workspace &W, const double *w, int nrhs, doubl
   CSFMM_MARK(CSFMM_PHASE_L2L);
   for (int l = 0; l + 1 < pl.nlevels; ++l) {
     int c0 = pl.level_begin[l], nlev = pl.level_begin[l + 1] - c0;
-    l2l_kernel<double><<<nlev, 128, 0, st>>>(v, c0, 0, nrhs, dim, psi, ldr);
+    if constexpr (sizeof(Real) == 4)
+      l2l_df_kernel<<<nlev, 128, 0, st>>>(v, c0, 0, nrhs, dim, psi, ldr);
+    else
+      l2l_kernel<double><<<nlev, 128, 0, st>>>(v, c0, 0, nrhs, dim, psi, ldr);
     ++pl.launches;
   }
   CSFMM_MARK(CSFMM_PHASE_L2P);

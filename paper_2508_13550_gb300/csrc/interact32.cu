@@ -89,6 +89,11 @@ __device__ __forceinline__ f2x f2_fma(f2x a, f2x b, f2x c) {
   asm("fma.rn.ftz.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
   return d;
 }
+__device__ __forceinline__ f2x f2_add(f2x a, f2x b) {
+  f2x d;
+  asm("add.rn.ftz.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
 __device__ __forceinline__ f2x f2_pack(float lo, float hi) {
   f2x d;
   asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
@@ -98,32 +103,80 @@ __device__ __forceinline__ void f2_unpack(f2x a, float &lo, float &hi) {
   asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a));
 }
 
+// Accumulation of a tile: FP32 sums over chunks of kChunk sources, each chunk
+// folded into an unevaluated FP32 pair (hi, lo) by Knuth's two-sum, so that
+// the rounding error of a tile sum is that of a kChunk-term sum rather than
+// of a kTile-term one (errors of long same-signed FP32 sums do not average
+// out across targets that share the same tile geometry).
+constexpr int kChunk = 32;
+__device__ __forceinline__ void two_sum_fold(float &hi, float &lo, float c) {
+  const float s = hi + c;
+  const float bb = s - hi;
+  lo += (hi - (s - bb)) + (c - bb);
+  hi = s;
+}
+__device__ __forceinline__ void two_sum_fold(f2x &hi, f2x &lo, f2x c) {
+  const f2x s = f2_add(hi, c);
+  const f2x bb = f2_sub(s, hi);
+  lo = f2_add(lo, f2_add(f2_sub(hi, f2_sub(s, bb)), f2_sub(c, bb)));
+  hi = s;
+}
+__device__ __forceinline__ double f2_total(f2x hi, f2x lo, int h) {
+  float a0, a1, b0, b1;
+  f2_unpack(hi, a0, a1);
+  f2_unpack(lo, b0, b1);
+  return h == 0 ? (double)a0 + (double)b0 : (double)a1 + (double)b1;
+}
 // One tile for NP pairs of targets (2 NP targets) and one right-hand side:
 // sA[j] = (x, x, y, y), sB[j] = (z, z, w, w) of source j.
+template <int KID, int NP, bool SELF>
+__device__ __forceinline__ void eval_x2(const ulonglong2 *__restrict__ sA,
+                                        const ulonglong2 *__restrict__ sB, int j,
+                                        const f2x (&tx)[NP], const f2x (&ty)[NP],
+                                        const f2x (&tz)[NP], const int (&self)[2 * NP],
+                                        f2x (&acc)[NP]) {
+  const ulonglong2 A = sA[j], B = sB[j];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    const f2x rx = f2_sub(tx[q], A.x), ry = f2_sub(ty[q], A.y), rz = f2_sub(tz[q], B.x);
+    f2x d2 = f2_mul(rx, rx);
+    d2 = f2_fma(ry, ry, d2);
+    d2 = f2_fma(rz, rz, d2);
+    float d0, d1;
+    f2_unpack(d2, d0, d1);
+    float f0 = kfactor<KID>(d0), f1 = kfactor<KID>(d1);
+    if constexpr (SELF) {
+      f0 = (j == self[2 * q]) ? 0.0f : f0;
+      f1 = (j == self[2 * q + 1]) ? 0.0f : f1;
+    }
+    acc[q] = f2_fma(B.y, f2_pack(f0, f1), acc[q]);
+  }
+}
+
 template <int KID, int NP, bool SELF>
 __device__ __forceinline__ void tile_sum_x2(const ulonglong2 *__restrict__ sA,
                                             const ulonglong2 *__restrict__ sB, int nj,
                                             const f2x (&tx)[NP], const f2x (&ty)[NP],
                                             const f2x (&tz)[NP], const int (&self)[2 * NP],
-                                            f2x (&acc)[NP]) {
-#pragma unroll 4
-  for (int j = 0; j < nj; ++j) {
-    const ulonglong2 A = sA[j], B = sB[j];
+                                            f2x (&hi)[NP], f2x (&lo)[NP]) {
+  int jc = 0;
+  for (; jc + kChunk <= nj; jc += kChunk) {  // full chunks: constant trip count
+    f2x acc[NP];
 #pragma unroll
-    for (int q = 0; q < NP; ++q) {
-      const f2x rx = f2_sub(tx[q], A.x), ry = f2_sub(ty[q], A.y), rz = f2_sub(tz[q], B.x);
-      f2x d2 = f2_mul(rx, rx);
-      d2 = f2_fma(ry, ry, d2);
-      d2 = f2_fma(rz, rz, d2);
-      float d0, d1;
-      f2_unpack(d2, d0, d1);
-      float f0 = kfactor<KID>(d0), f1 = kfactor<KID>(d1);
-      if constexpr (SELF) {
-        f0 = (j == self[2 * q]) ? 0.0f : f0;
-        f1 = (j == self[2 * q + 1]) ? 0.0f : f1;
-      }
-      acc[q] = f2_fma(B.y, f2_pack(f0, f1), acc[q]);
-    }
+    for (int q = 0; q < NP; ++q) acc[q] = 0ull;
+#pragma unroll 4
+    for (int jj = 0; jj < kChunk; ++jj) eval_x2<KID, NP, SELF>(sA, sB, jc + jj, tx, ty, tz, self, acc);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) two_sum_fold(hi[q], lo[q], acc[q]);
+  }
+  if (jc < nj) {
+    f2x acc[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) acc[q] = 0ull;
+#pragma unroll 4
+    for (int j = jc; j < nj; ++j) eval_x2<KID, NP, SELF>(sA, sB, j, tx, ty, tz, self, acc);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) two_sum_fold(hi[q], lo[q], acc[q]);
   }
 }
 
@@ -131,32 +184,47 @@ template <int KID, int NT, int NR, bool SELF>
 __device__ __forceinline__ void tile_sum(const float4 *__restrict__ sp, const float *__restrict__ sw,
                                          int nj, const float (&tx)[NT], const float (&ty)[NT],
                                          const float (&tz)[NT], const int (&self)[NT],
-                                         float (&a)[NT][NR][3]) {
+                                         float (&ahi)[NT][NR][3], float (&alo)[NT][NR][3]) {
+  constexpr int D = KID == CSFMM_KERNEL_BIOT_SAVART ? 3 : 1;
+  for (int jc = 0; jc < nj; jc += kChunk) {
+    const int je = min(nj, jc + kChunk);
+    float a[NT][NR][3];
+#pragma unroll
+    for (int k = 0; k < NT; ++k)
+#pragma unroll
+      for (int q = 0; q < NR; ++q) a[k][q][0] = a[k][q][1] = a[k][q][2] = 0.f;
 #pragma unroll 4
-  for (int j = 0; j < nj; ++j) {
-    const float4 s = sp[j];
-    float wq[NR];
-    wq[0] = s.w;
+    for (int j = jc; j < je; ++j) {
+      const float4 s = sp[j];
+      float wq[NR];
+      wq[0] = s.w;
 #pragma unroll
-    for (int q = 1; q < NR; ++q) wq[q] = sw[q * kTile + j];
+      for (int q = 1; q < NR; ++q) wq[q] = sw[q * kTile + j];
 #pragma unroll
-    for (int k = 0; k < NT; ++k) {
-      const float rx = tx[k] - s.x, ry = ty[k] - s.y, rz = tz[k] - s.z;
-      const float d2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
-      float f = kfactor<KID>(d2);
-      if constexpr (SELF) f = (j == self[k]) ? 0.0f : f;
+      for (int k = 0; k < NT; ++k) {
+        const float rx = tx[k] - s.x, ry = ty[k] - s.y, rz = tz[k] - s.z;
+        const float d2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+        float f = kfactor<KID>(d2);
+        if constexpr (SELF) f = (j == self[k]) ? 0.0f : f;
 #pragma unroll
-      for (int q = 0; q < NR; ++q) {
-        if constexpr (KID == CSFMM_KERNEL_BIOT_SAVART) {
-          const float g = wq[q] * f;
-          a[k][q][0] = fmaf(g, rx, a[k][q][0]);
-          a[k][q][1] = fmaf(g, ry, a[k][q][1]);
-          a[k][q][2] = fmaf(g, rz, a[k][q][2]);
-        } else {
-          a[k][q][0] = fmaf(wq[q], f, a[k][q][0]);
+        for (int q = 0; q < NR; ++q) {
+          if constexpr (KID == CSFMM_KERNEL_BIOT_SAVART) {
+            const float g = wq[q] * f;
+            a[k][q][0] = fmaf(g, rx, a[k][q][0]);
+            a[k][q][1] = fmaf(g, ry, a[k][q][1]);
+            a[k][q][2] = fmaf(g, rz, a[k][q][2]);
+          } else {
+            a[k][q][0] = fmaf(wq[q], f, a[k][q][0]);
+          }
         }
       }
     }
+#pragma unroll
+    for (int k = 0; k < NT; ++k)
+#pragma unroll
+      for (int q = 0; q < NR; ++q)
+#pragma unroll
+        for (int d = 0; d < D; ++d) two_sum_fold(ahi[k][q][d], alo[k][q][d], a[k][q][d]);
   }
 }
 
@@ -168,7 +236,7 @@ __global__ void __launch_bounds__(kThreads) near32_kernel(PlanView v, const int3
   constexpr int DIM = kdim32<KID>();
   __shared__ float4 sp[kTile];
   __shared__ float sw[NR * kTile];
-  __shared__ float wsum[NR][kThreads / 32];
+  __shared__ double wsum[NR][kThreads / 32];
   const int c = leaves[blockIdx.x];
   const int b = v.cbegin[c], e = v.cend[c], P = v.P;
   const double cTx = v.ccentre[3 * c], cTy = v.ccentre[3 * c + 1], cTz = v.ccentre[3 * c + 2];
@@ -215,9 +283,9 @@ __global__ void __launch_bounds__(kThreads) near32_kernel(PlanView v, const int3
         for (int j0 = 0; j0 < nsrc; j0 += kTile) {
           const int nj = min(kTile, nsrc - j0);
           __syncthreads();
-          float part[NR];
+          double part[NR];
 #pragma unroll
-          for (int q = 0; q < NR; ++q) part[q] = 0.f;
+          for (int q = 0; q < NR; ++q) part[q] = 0.0;
           for (int t = threadIdx.x; t < nj; t += kThreads) {
             float4 val;
             float wv[NR];
@@ -238,49 +306,54 @@ __global__ void __launch_bounds__(kThreads) near32_kernel(PlanView v, const int3
 #pragma unroll
             for (int q = 1; q < NR; ++q) sw[q * kTile + t] = wv[q];
 #pragma unroll
-            for (int q = 0; q < NR; ++q) part[q] += wv[q];
+            for (int q = 0; q < NR; ++q) part[q] += (double)wv[q];
           }
           if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
 #pragma unroll
             for (int q = 0; q < NR; ++q) {
-              float x = part[q];
+              double x = part[q];
 #pragma unroll
               for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
               if (lane == 0) wsum[q][warp] = x;
             }
           }
           __syncthreads();
-          float a[NT][NR][3];
+          float ahi[NT][NR][3], alo[NT][NR][3];
 #pragma unroll
           for (int k = 0; k < NT; ++k)
 #pragma unroll
-            for (int q = 0; q < NR; ++q) a[k][q][0] = a[k][q][1] = a[k][q][2] = 0.f;
+            for (int q = 0; q < NR; ++q)
+#pragma unroll
+              for (int d = 0; d < 3; ++d) ahi[k][q][d] = alo[k][q][d] = 0.f;
           int self[NT];
 #pragma unroll
           for (int k = 0; k < NT; ++k) self[k] = (i0 + (int)threadIdx.x + k * kThreads) - (sb + j0);
           if (self_tile)
-            tile_sum<KID, NT, NR, true>(sp, sw, nj, tx, ty, tz, self, a);
+            tile_sum<KID, NT, NR, true>(sp, sw, nj, tx, ty, tz, self, ahi, alo);
           else
-            tile_sum<KID, NT, NR, false>(sp, sw, nj, tx, ty, tz, self, a);
+            tile_sum<KID, NT, NR, false>(sp, sw, nj, tx, ty, tz, self, ahi, alo);
 #pragma unroll
           for (int k = 0; k < NT; ++k) {
 #pragma unroll
             for (int q = 0; q < NR; ++q) {
               if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
                 // -(1/4pi) sum w ln(d2/2) = -(ln2/4pi) (sum w log2 d2 - sum w)
-                float tot = 0.f;
+                double tot = 0.0;
 #pragma unroll
                 for (int u = 0; u < kThreads / 32; ++u) tot += wsum[q][u];
                 if (self_tile && self[k] >= 0 && self[k] < nj)
-                  tot -= (q == 0) ? sp[self[k]].w : sw[q * kTile + self[k]];
-                out[k][q][0] += -(0.69314718055994530942 * kInv4Pi) * ((double)a[k][q][0] - (double)tot);
+                  tot -= (double)((q == 0) ? sp[self[k]].w : sw[q * kTile + self[k]]);
+                out[k][q][0] += -(0.69314718055994530942 * kInv4Pi) *
+                                (((double)ahi[k][q][0] + (double)alo[k][q][0]) - tot);
               } else if constexpr (KID == CSFMM_KERNEL_BIOT_SAVART) {
-                const double b0 = a[k][q][0], b1 = a[k][q][1], b2 = a[k][q][2];
+                const double b0 = (double)ahi[k][q][0] + (double)alo[k][q][0];
+                const double b1 = (double)ahi[k][q][1] + (double)alo[k][q][1];
+                const double b2 = (double)ahi[k][q][2] + (double)alo[k][q][2];
                 out[k][q][0] += kInv2Pi * (xa[k][1] * b2 - xa[k][2] * b1);
                 out[k][q][1] += kInv2Pi * (xa[k][2] * b0 - xa[k][0] * b2);
                 out[k][q][2] += kInv2Pi * (xa[k][0] * b1 - xa[k][1] * b0);
               } else {
-                out[k][q][0] += (double)a[k][q][0];
+                out[k][q][0] += (double)ahi[k][q][0] + (double)alo[k][q][0];
               }
             }
           }
@@ -338,7 +411,7 @@ __global__ void __launch_bounds__(kSymThreads) pp_sym_kernel(PlanView v, const i
                                                              float *part) {
   __shared__ ulonglong2 sA[kSymCols], sB[kSymCols];
   __shared__ float colacc[kSymThreads / 32][kSymCols];
-  __shared__ float wred[2][kSymThreads / 32];
+  __shared__ double wred[2][kSymThreads / 32];
   const int2 pr = pairs[blockIdx.x];
   const int T = pr.x, S = pr.y;
   const int tb = v.cbegin[T], te = v.cend[T], sb = v.cbegin[S], se = v.cend[S];
@@ -350,11 +423,11 @@ __global__ void __launch_bounds__(kSymThreads) pp_sym_kernel(PlanView v, const i
   const float dcy = (float)(v.ccentre[3 * T + 1] - v.ccentre[3 * S + 1]);
   const float dcz = (float)(v.ccentre[3 * T + 2] - v.ccentre[3 * S + 2]);
   // Laplace: total weights of T and S for -(ln2/4pi)(sum w log2 d2 - sum w)
-  float WT = 0.f, WS = 0.f;
+  double WT = 0.0, WS = 0.0;
   if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
-    float a = 0.f, c = 0.f;
-    for (int t = threadIdx.x; t < nT; t += kSymThreads) a += wsf[tb + t];
-    for (int t = threadIdx.x; t < nS; t += kSymThreads) c += wsf[sb + t];
+    double a = 0.0, c = 0.0;
+    for (int t = threadIdx.x; t < nT; t += kSymThreads) a += (double)wsf[tb + t];
+    for (int t = threadIdx.x; t < nS; t += kSymThreads) c += (double)wsf[sb + t];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       a += __shfl_xor_sync(0xffffffffu, a, o);
@@ -373,7 +446,7 @@ __global__ void __launch_bounds__(kSymThreads) pp_sym_kernel(PlanView v, const i
   }
   for (int r0 = 0; r0 < nT; r0 += kSymRows) {
     // rows of this lane: r0 + warp*128 + lane + 32k, k = 0..3 (pairs (0,1), (2,3))
-    f2x tx[2], ty[2], tz[2], wr[2], racc[2];
+    f2x tx[2], ty[2], tz[2], wr[2], rhi[2], rlo[2];
     bool act[4];
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
@@ -394,7 +467,8 @@ __global__ void __launch_bounds__(kSymThreads) pp_sym_kernel(PlanView v, const i
       ty[q] = f2_pack(y[0], y[1]);
       tz[q] = f2_pack(z[0], z[1]);
       wr[q] = f2_pack(w[0], w[1]);
-      racc[q] = 0ull;
+      rhi[q] = 0ull;
+      rlo[q] = 0ull;
     }
     for (int c0 = 0; c0 < nS; c0 += kSymCols) {
       const int nj = min(kSymCols, nS - c0);
@@ -412,7 +486,7 @@ __global__ void __launch_bounds__(kSymThreads) pp_sym_kernel(PlanView v, const i
       __syncthreads();
       const int ng = (nj + 31) / 32;
       for (int g = 0; g < ng; ++g) {
-        f2x colv[32];
+        f2x colv[32], racc[2] = {0ull, 0ull};
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const ulonglong2 A = sA[g * 32 + j], B = sB[g * 32 + j];
@@ -430,6 +504,8 @@ __global__ void __launch_bounds__(kSymThreads) pp_sym_kernel(PlanView v, const i
             colv[j] = f2_fma(f, wr[q], colv[j]);
           }
         }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) two_sum_fold(rhi[q], rlo[q], racc[q]);
         float cv[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
@@ -450,24 +526,22 @@ __global__ void __launch_bounds__(kSymThreads) pp_sym_kernel(PlanView v, const i
     }
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
-      float a[2];
-      f2_unpack(racc[q], a[0], a[1]);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int k = 2 * q + h;
         if (!act[k]) continue;
         const int i = r0 + warp * 128 + lane + 32 * k;
-        float val = a[h];
+        double val = f2_total(rhi[q], rlo[q], h);
         if constexpr (KID == CSFMM_KERNEL_LAPLACE)
-          val = (float)(-(0.69314718055994530942 * kInv4Pi) * ((double)val - (double)WS));
-        rowpart[i] = val;
+          val = -(0.69314718055994530942 * kInv4Pi) * (val - WS);
+        rowpart[i] = (float)val;
       }
     }
   }
   if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
     __syncthreads();
     for (int t = threadIdx.x; t < nS; t += kSymThreads)
-      colpart[t] = (float)(-(0.69314718055994530942 * kInv4Pi) * ((double)colpart[t] - (double)WT));
+      colpart[t] = (float)(-(0.69314718055994530942 * kInv4Pi) * ((double)colpart[t] - WT));
   }
 }
 
@@ -483,7 +557,7 @@ __global__ void __launch_bounds__(kThreads, CSFMM_NEAR_MINB) near32x2_kernel(Pla
                                                             const float *part) {
   constexpr int NT = 2 * NP;
   __shared__ ulonglong2 sA[kTile], sB[kTile];
-  __shared__ float wsum[kThreads / 32];
+  __shared__ double wsum[kThreads / 32];
   const int c = leaves[blockIdx.x];
   const int b = v.cbegin[c], e = v.cend[c], P = v.P;
   const double cTx = v.ccentre[3 * c], cTy = v.ccentre[3 * c + 1], cTz = v.ccentre[3 * c + 2];
@@ -531,7 +605,7 @@ __global__ void __launch_bounds__(kThreads, CSFMM_NEAR_MINB) near32x2_kernel(Pla
         for (int j0 = 0; j0 < nsrc; j0 += kTile) {
           const int nj = min(kTile, nsrc - j0);
           __syncthreads();
-          float part = 0.f;
+          double part = 0.0;
           for (int t = threadIdx.x; t < nj; t += kThreads) {
             float x, y, z, w;
             if (pp) {
@@ -547,7 +621,7 @@ __global__ void __launch_bounds__(kThreads, CSFMM_NEAR_MINB) near32x2_kernel(Pla
             }
             sA[t] = make_ulonglong2(f2_pack(x, x), f2_pack(y, y));
             sB[t] = make_ulonglong2(f2_pack(z, z), f2_pack(w, w));
-            part += w;
+            part += (double)w;
           }
           if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
 #pragma unroll
@@ -555,40 +629,38 @@ __global__ void __launch_bounds__(kThreads, CSFMM_NEAR_MINB) near32x2_kernel(Pla
             if (lane == 0) wsum[warp] = part;
           }
           __syncthreads();
-          f2x acc[NP];
+          f2x hi[NP], lo[NP];
 #pragma unroll
-          for (int q = 0; q < NP; ++q) acc[q] = 0ull;
+          for (int q = 0; q < NP; ++q) hi[q] = lo[q] = 0ull;
           int self[NT];
 #pragma unroll
           for (int k = 0; k < NT; ++k) self[k] = (i0 + (int)threadIdx.x + k * kThreads) - (sb + j0);
           if (self_tile)
-            tile_sum_x2<KID, NP, true>(sA, sB, nj, tx, ty, tz, self, acc);
+            tile_sum_x2<KID, NP, true>(sA, sB, nj, tx, ty, tz, self, hi, lo);
           else
-            tile_sum_x2<KID, NP, false>(sA, sB, nj, tx, ty, tz, self, acc);
-          float tot = 0.f;
+            tile_sum_x2<KID, NP, false>(sA, sB, nj, tx, ty, tz, self, hi, lo);
+          double tot = 0.0;
           if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
 #pragma unroll
             for (int u = 0; u < kThreads / 32; ++u) tot += wsum[u];
           }
 #pragma unroll
           for (int q = 0; q < NP; ++q) {
-            float a0, a1;
-            f2_unpack(acc[q], a0, a1);
-            float aa[2] = {a0, a1};
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
               const int k = 2 * q + h;
+              const double a = f2_total(hi[q], lo[q], h);
               if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
-                float t = tot;
+                double t = tot;
                 if (self_tile && self[k] >= 0 && self[k] < nj) {
                   float wself, dummy;
                   f2_unpack(sB[self[k]].y, wself, dummy);
-                  t -= wself;
+                  t -= (double)wself;
                 }
                 // -(1/4pi) sum w ln(d2/2) = -(ln2/4pi) (sum w log2 d2 - sum w)
-                out[k] += -(0.69314718055994530942 * kInv4Pi) * ((double)aa[h] - (double)t);
+                out[k] += -(0.69314718055994530942 * kInv4Pi) * (a - t);
               } else {
-                out[k] += (double)aa[h];
+                out[k] += a;
               }
             }
           }
@@ -619,7 +691,7 @@ __global__ void __launch_bounds__(160) far32x2_kernel(PlanView v, const float *w
                                                       const float *wbar, int ldr, int r0,
                                                       double *psi) {
   __shared__ ulonglong2 sA[kTile], sB[kTile];
-  __shared__ float wsum[8];
+  __shared__ double wsum[8];
   const int c = blockIdx.x, P = v.P, nth = blockDim.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = nth >> 5;
   const int64_t po = (int64_t)c * 3 * P;
@@ -653,7 +725,7 @@ __global__ void __launch_bounds__(160) far32x2_kernel(PlanView v, const float *w
       for (int j0 = 0; j0 < nsrc; j0 += kTile) {
         const int nj = min(kTile, nsrc - j0);
         __syncthreads();
-        float part = 0.f;
+        double part = 0.0;
         for (int t = threadIdx.x; t < nj; t += nth) {
           float x, y, z, w;
           if (cp) {
@@ -669,7 +741,7 @@ __global__ void __launch_bounds__(160) far32x2_kernel(PlanView v, const float *w
           }
           sA[t] = make_ulonglong2(f2_pack(x, x), f2_pack(y, y));
           sB[t] = make_ulonglong2(f2_pack(z, z), f2_pack(w, w));
-          part += w;
+          part += (double)w;
         }
         if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
 #pragma unroll
@@ -677,18 +749,17 @@ __global__ void __launch_bounds__(160) far32x2_kernel(PlanView v, const float *w
           if (lane == 0) wsum[warp] = part;
         }
         __syncthreads();
-        f2x acc[1] = {0ull};
-        tile_sum_x2<KID, 1, false>(sA, sB, nj, tx, ty, tz, self_none, acc);
-        float a0, a1;
-        f2_unpack(acc[0], a0, a1);
+        f2x hi[1] = {0ull}, lo[1] = {0ull};
+        tile_sum_x2<KID, 1, false>(sA, sB, nj, tx, ty, tz, self_none, hi, lo);
+        const double a0 = f2_total(hi[0], lo[0], 0), a1 = f2_total(hi[0], lo[0], 1);
         if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
-          float tot = 0.f;
+          double tot = 0.0;
           for (int u = 0; u < nwarp; ++u) tot += wsum[u];
-          out[0] += -(0.69314718055994530942 * kInv4Pi) * ((double)a0 - (double)tot);
-          out[1] += -(0.69314718055994530942 * kInv4Pi) * ((double)a1 - (double)tot);
+          out[0] += -(0.69314718055994530942 * kInv4Pi) * (a0 - tot);
+          out[1] += -(0.69314718055994530942 * kInv4Pi) * (a1 - tot);
         } else {
-          out[0] += (double)a0;
-          out[1] += (double)a1;
+          out[0] += a0;
+          out[1] += a1;
         }
       }
     }
@@ -708,7 +779,7 @@ __global__ void __launch_bounds__(160) far32_kernel(PlanView v, const float *wsf
   constexpr int NT = 2;
   __shared__ float4 sp[kTile];
   __shared__ float sw[NR * kTile];
-  __shared__ float wsum[NR][8];
+  __shared__ double wsum[NR][8];
   const int c = blockIdx.x, P = v.P, nth = blockDim.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = nth >> 5;
   const int64_t po = (int64_t)c * 3 * P;
@@ -753,9 +824,9 @@ __global__ void __launch_bounds__(160) far32_kernel(PlanView v, const float *wsf
       for (int j0 = 0; j0 < nsrc; j0 += kTile) {
         const int nj = min(kTile, nsrc - j0);
         __syncthreads();
-        float part[NR];
+        double part[NR];
 #pragma unroll
-        for (int q = 0; q < NR; ++q) part[q] = 0.f;
+        for (int q = 0; q < NR; ++q) part[q] = 0.0;
         for (int t = threadIdx.x; t < nj; t += nth) {
           float4 val;
           float wv[NR];
@@ -776,39 +847,44 @@ __global__ void __launch_bounds__(160) far32_kernel(PlanView v, const float *wsf
 #pragma unroll
           for (int q = 1; q < NR; ++q) sw[q * kTile + t] = wv[q];
 #pragma unroll
-          for (int q = 0; q < NR; ++q) part[q] += wv[q];
+          for (int q = 0; q < NR; ++q) part[q] += (double)wv[q];
         }
         if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
 #pragma unroll
           for (int q = 0; q < NR; ++q) {
-            float x = part[q];
+            double x = part[q];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
             if (lane == 0) wsum[q][warp] = x;
           }
         }
         __syncthreads();
-        float a[NT][NR][3];
+        float ahi[NT][NR][3], alo[NT][NR][3];
 #pragma unroll
         for (int h = 0; h < NT; ++h)
 #pragma unroll
-          for (int q = 0; q < NR; ++q) a[h][q][0] = a[h][q][1] = a[h][q][2] = 0.f;
-        tile_sum<KID, NT, NR, false>(sp, sw, nj, tx, ty, tz, self_none, a);
+          for (int q = 0; q < NR; ++q)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) ahi[h][q][d] = alo[h][q][d] = 0.f;
+        tile_sum<KID, NT, NR, false>(sp, sw, nj, tx, ty, tz, self_none, ahi, alo);
 #pragma unroll
         for (int h = 0; h < NT; ++h)
 #pragma unroll
           for (int q = 0; q < NR; ++q) {
             if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
-              float tot = 0.f;
+              double tot = 0.0;
               for (int u = 0; u < nwarp; ++u) tot += wsum[q][u];
-              out[h][q][0] += -(0.69314718055994530942 * kInv4Pi) * ((double)a[h][q][0] - (double)tot);
+              out[h][q][0] += -(0.69314718055994530942 * kInv4Pi) *
+                              (((double)ahi[h][q][0] + (double)alo[h][q][0]) - tot);
             } else if constexpr (KID == CSFMM_KERNEL_BIOT_SAVART) {
-              const double b0 = a[h][q][0], b1 = a[h][q][1], b2 = a[h][q][2];
+              const double b0 = (double)ahi[h][q][0] + (double)alo[h][q][0];
+              const double b1 = (double)ahi[h][q][1] + (double)alo[h][q][1];
+              const double b2 = (double)ahi[h][q][2] + (double)alo[h][q][2];
               out[h][q][0] += kInv2Pi * (xa[h][1] * b2 - xa[h][2] * b1);
               out[h][q][1] += kInv2Pi * (xa[h][2] * b0 - xa[h][0] * b2);
               out[h][q][2] += kInv2Pi * (xa[h][0] * b1 - xa[h][1] * b0);
             } else {
-              out[h][q][0] += (double)a[h][q][0];
+              out[h][q][0] += (double)ahi[h][q][0] + (double)alo[h][q][0];
             }
           }
       }
@@ -853,31 +929,55 @@ void launch_far_kid(const PlanView &v, int ncells, const float *wsf, const float
 // the far field (targets = proxies of a cell, CP and CC sources).
 // ---------------------------------------------------------------------------
 template <int KID, int NT, int NR, bool SELF>
+__device__ __forceinline__ void eval_multi(const float4 *__restrict__ sp,
+                                           const ulonglong2 *__restrict__ sw4, int j,
+                                           const float (&tx)[NT], const float (&ty)[NT],
+                                           const float (&tz)[NT], const int (&self)[NT],
+                                           f2x (&acc)[NT][NR / 2]) {
+  const float4 s = sp[j];
+  f2x w2[NR / 2];
+#pragma unroll
+  for (int q = 0; q < NR / 4; ++q) {
+    const ulonglong2 u = sw4[j * (NR / 4) + q];
+    w2[2 * q] = u.x;
+    w2[2 * q + 1] = u.y;
+  }
+#pragma unroll
+  for (int k = 0; k < NT; ++k) {
+    const float rx = tx[k] - s.x, ry = ty[k] - s.y, rz = tz[k] - s.z;
+    const float d2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
+    float f = kfactor<KID>(d2);
+    if constexpr (SELF) f = (j == self[k]) ? 0.0f : f;
+    const f2x ff = f2_pack(f, f);
+#pragma unroll
+    for (int q = 0; q < NR / 2; ++q) acc[k][q] = f2_fma(w2[q], ff, acc[k][q]);
+  }
+}
+
+template <int KID, int NT, int NR, bool SELF>
 __device__ __forceinline__ void tile_sum_multi(const float4 *__restrict__ sp,
                                                const ulonglong2 *__restrict__ sw4, int nj,
                                                const float (&tx)[NT], const float (&ty)[NT],
                                                const float (&tz)[NT], const int (&self)[NT],
-                                               f2x (&acc)[NT][NR / 2]) {
+                                               f2x (&hi)[NT][NR / 2], f2x (&lo)[NT][NR / 2]) {
+  for (int jc = 0; jc < nj; jc += kChunk) {
+    f2x acc[NT][NR / 2];
+#pragma unroll
+    for (int k = 0; k < NT; ++k)
+#pragma unroll
+      for (int q = 0; q < NR / 2; ++q) acc[k][q] = 0ull;
+    if (jc + kChunk <= nj) {  // full chunk: constant trip count
 #pragma unroll 2
-  for (int j = 0; j < nj; ++j) {
-    const float4 s = sp[j];
-    f2x w2[NR / 2];
-#pragma unroll
-    for (int q = 0; q < NR / 4; ++q) {
-      const ulonglong2 u = sw4[j * (NR / 4) + q];
-      w2[2 * q] = u.x;
-      w2[2 * q + 1] = u.y;
+      for (int jj = 0; jj < kChunk; ++jj)
+        eval_multi<KID, NT, NR, SELF>(sp, sw4, jc + jj, tx, ty, tz, self, acc);
+    } else {
+#pragma unroll 2
+      for (int j = jc; j < nj; ++j) eval_multi<KID, NT, NR, SELF>(sp, sw4, j, tx, ty, tz, self, acc);
     }
 #pragma unroll
-    for (int k = 0; k < NT; ++k) {
-      const float rx = tx[k] - s.x, ry = ty[k] - s.y, rz = tz[k] - s.z;
-      const float d2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
-      float f = kfactor<KID>(d2);
-      if constexpr (SELF) f = (j == self[k]) ? 0.0f : f;
-      const f2x ff = f2_pack(f, f);
+    for (int k = 0; k < NT; ++k)
 #pragma unroll
-      for (int q = 0; q < NR / 2; ++q) acc[k][q] = f2_fma(w2[q], ff, acc[k][q]);
-    }
+      for (int q = 0; q < NR / 2; ++q) two_sum_fold(hi[k][q], lo[k][q], acc[k][q]);
   }
 }
 
@@ -904,7 +1004,7 @@ __global__ void __launch_bounds__(CSFMM_MULTI_THREADS) multi32_kernel(
   static_assert(CSFMM_MULTI_THREADS % 32 == 0 && CSFMM_MULTI_THREADS <= 1024, "block size");
   __shared__ float4 sp[kTile];
   __shared__ ulonglong2 sw4[(NR / 4) * kTile];
-  __shared__ float wsum[NR][CSFMM_MULTI_THREADS / 32];
+  __shared__ double wsum[NR][CSFMM_MULTI_THREADS / 32];
   const int c = FAR ? (int)blockIdx.x : leaves[blockIdx.x];
   const int P = v.P, nth = blockDim.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = nth >> 5;
@@ -956,9 +1056,9 @@ __global__ void __launch_bounds__(CSFMM_MULTI_THREADS) multi32_kernel(
         for (int j0 = 0; j0 < nsrc; j0 += kTile) {
           const int nj = min(kTile, nsrc - j0);
           __syncthreads();
-          float part[NR];
+          double part[NR];
 #pragma unroll
-          for (int q = 0; q < NR; ++q) part[q] = 0.f;
+          for (int q = 0; q < NR; ++q) part[q] = 0.0;
           for (int t = threadIdx.x; t < nj; t += nth) {
             float wv[NR];
             if (particles) {
@@ -978,47 +1078,45 @@ __global__ void __launch_bounds__(CSFMM_MULTI_THREADS) multi32_kernel(
               reinterpret_cast<float4 *>(swf)[t * (NR / 4) + q] =
                   make_float4(wv[4 * q], wv[4 * q + 1], wv[4 * q + 2], wv[4 * q + 3]);
 #pragma unroll
-            for (int q = 0; q < NR; ++q) part[q] += wv[q];
+            for (int q = 0; q < NR; ++q) part[q] += (double)wv[q];
           }
           if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
 #pragma unroll
             for (int q = 0; q < NR; ++q) {
-              float x = part[q];
+              double x = part[q];
 #pragma unroll
               for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
               if (lane == 0) wsum[q][warp] = x;
             }
           }
           __syncthreads();
-          f2x acc[NT][NR / 2];
+          f2x hi[NT][NR / 2], lo[NT][NR / 2];
 #pragma unroll
           for (int k = 0; k < NT; ++k)
 #pragma unroll
-            for (int q = 0; q < NR / 2; ++q) acc[k][q] = 0ull;
+            for (int q = 0; q < NR / 2; ++q) hi[k][q] = lo[k][q] = 0ull;
           int self[NT];
 #pragma unroll
           for (int k = 0; k < NT; ++k) self[k] = (i0 + (int)threadIdx.x + k * nth) - (sb + j0);
           if (self_tile)
-            tile_sum_multi<KID, NT, NR, true>(sp, sw4, nj, tx, ty, tz, self, acc);
+            tile_sum_multi<KID, NT, NR, true>(sp, sw4, nj, tx, ty, tz, self, hi, lo);
           else
-            tile_sum_multi<KID, NT, NR, false>(sp, sw4, nj, tx, ty, tz, self, acc);
+            tile_sum_multi<KID, NT, NR, false>(sp, sw4, nj, tx, ty, tz, self, hi, lo);
 #pragma unroll
           for (int k = 0; k < NT; ++k) {
             const int i = i0 + threadIdx.x + k * nth;
             if (i >= te) continue;
 #pragma unroll
             for (int q = 0; q < NR / 2; ++q) {
-              float a2[2];
-              f2_unpack(acc[k][q], a2[0], a2[1]);
 #pragma unroll
               for (int h = 0; h < 2; ++h) {
                 const int qq = 2 * q + h;
-                double val = (double)a2[h];
+                double val = f2_total(hi[k][q], lo[k][q], h);
                 if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
-                  float tot = 0.f;
+                  double tot = 0.0;
                   for (int u = 0; u < nwarp; ++u) tot += wsum[qq][u];
-                  if (self_tile && self[k] >= 0 && self[k] < nj) tot -= swf[self[k] * NR + qq];
-                  val = -(0.69314718055994530942 * kInv4Pi) * (val - (double)tot);
+                  if (self_tile && self[k] >= 0 && self[k] < nj) tot -= (double)swf[self[k] * NR + qq];
+                  val = -(0.69314718055994530942 * kInv4Pi) * (val - tot);
                 }
                 if (FAR) psi[((int64_t)c * ldr + r0 + qq) * P + i] += val;
                 else phi[(int64_t)(r0 + qq) * v.N + i] += val;

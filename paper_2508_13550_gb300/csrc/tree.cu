@@ -487,8 +487,36 @@ __global__ void proxies_kernel(PlanView v, double *proxy, float *proxy32) {
   }
 }
 
+// Unbiased stochastic rounding of x to FP32: the representable neighbour on
+// the far side of x is chosen with probability |x - RN(x)| / gap, decided by
+// the 24 high bits of the hash h, so the expected value is x.  The FP32
+// Lagrange rows use it with a hash of (point, axis, node): points of a uniform
+// grid repeat the same local coordinates in every leaf, and round-to-nearest
+// would give every leaf the same rounding errors, which then add up in the
+// proxy weights instead of averaging out.
+__device__ __forceinline__ uint32_t hash32(uint32_t x) {
+  // integer finaliser "lowbias32" (C. Wellons, hash-prospector)
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
+__device__ __forceinline__ float round_stochastic(double x, uint32_t h) {
+  const float r = __double2float_rn(x);
+  const double d = x - (double)r;
+  if (d == 0.0) return r;
+  const float o = nextafterf(r, d > 0.0 ? INFINITY : -INFINITY);
+  const double gap = fabs((double)o - (double)r);
+  const double u = (double)(h >> 8) * (1.0 / 16777216.0);
+  return u * gap < fabs(d) ? o : r;
+}
+
 // One block per leaf: leaf id of each point, FP32 offset from the leaf centre and
-// the Lagrange values in the leaf's local coordinates.
+// the Lagrange values in the leaf's local coordinates (FP64 rows for the FP64
+// form; stochastically rounded FP32 rows plus their FP32 remainders for the
+// FP32 form).
 __global__ void leaf_points_kernel(PlanView v, const int32_t *leaves, int32_t *leaf_of,
                                    float4 *off32, double *La64, double *Lb64, float *La32,
                                    float *Lb32, float *La32lo, float *Lb32lo) {
@@ -524,8 +552,9 @@ __global__ void leaf_points_kernel(PlanView v, const int32_t *leaves, int32_t *l
       const int64_t o = (int64_t)i * p + k;
       if (La64) La64[o] = L[k];
       if (La32) {
-        La32[o] = (float)L[k];
-        La32lo[o] = (float)(L[k] - (double)La32[o]);
+        const float hi = round_stochastic(L[k], hash32((uint32_t)(2 * o)));
+        La32[o] = hi;
+        La32lo[o] = (float)(L[k] - (double)hi);
       }
     }
     lagrange_dev(n, s, w, L);
@@ -533,8 +562,9 @@ __global__ void leaf_points_kernel(PlanView v, const int32_t *leaves, int32_t *l
       const int64_t o = (int64_t)i * p + k;
       if (Lb64) Lb64[o] = L[k];
       if (Lb32) {
-        Lb32[o] = (float)L[k];
-        Lb32lo[o] = (float)(L[k] - (double)Lb32[o]);
+        const float hi = round_stochastic(L[k], hash32((uint32_t)(2 * o + 1)));
+        Lb32[o] = hi;
+        Lb32lo[o] = (float)(L[k] - (double)hi);
       }
     }
   }
@@ -549,8 +579,10 @@ __global__ void m2m_matrix_kernel(int n, const double *s, double *m64, float *m3
   double L[kMaxP];
   lagrange_dev(n, s, 0.5 * (s[m] + (double)(2 * q - 1)), L);
   for (int k = 0; k < p; ++k) {
+    const float hi = (float)L[k];
     m64[(q * p + k) * p + m] = L[k];
-    m32[(q * p + k) * p + m] = (float)L[k];
+    m32[(q * p + k) * p + m] = hi;                          // FP32 rounding ...
+    m32[2 * p * p + (q * p + k) * p + m] = (float)(L[k] - (double)hi);  // ... and remainder
   }
 }
 
@@ -961,7 +993,7 @@ csfmm_status build_tree(Plan &pl, const double *points, cudaStream_t st) {
     CSFMM_TRY(A.alloc(&pl.Lb32lo, (size_t)N * pl.p));
   }
   CSFMM_TRY(A.alloc(&pl.m2m64, (size_t)2 * pl.p * pl.p));
-  CSFMM_TRY(A.alloc(&pl.m2m32, (size_t)2 * pl.p * pl.p));
+  CSFMM_TRY(A.alloc(&pl.m2m32, (size_t)4 * pl.p * pl.p));
   {
     PlanView v = pl.view();
     proxies_kernel<<<nc, 128, 0, st>>>(v, pl.proxy, pl.proxy32);
