@@ -50,6 +50,31 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the FP32
+# interaction kernels per kernel evaluation, from one ncu capture of the
+# 6 x 512^2 Newtonian case (profiles/pp_sym_newton_1.5m.md and
+# profiles/near32x2_far32x2_newton_1.5m.md), valid for the kernel source with
+# the given SHA-256 prefix only; the bench scales it to a launch by the
+# evaluations the launch performs (the traffic of these kernels grows with the
+# number of leaf pairs and points, as the evaluations do).
+KERNEL_SOURCE = os.path.join(ROOT, "paper_2508_13550_gb300", "csrc", "interact32.cu")
+TRAFFIC_PER_EVAL = {
+    "source_sha256": "cb77dd55f3529230",
+    "pp_sym_kernel": (34.968832e6 + 129.568768e6) / 6083051520,
+    "near32x2_kernel": (233.240576e6 + 12.256256e6) / 3743870976,
+    "far32x2_kernel": 18.471424e6 / 1503908016,
+}
+
+
+def traffic_per_launch(kernel, evals):
+    import hashlib
+    with open(KERNEL_SOURCE, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    if sha != TRAFFIC_PER_EVAL["source_sha256"] or kernel not in TRAFFIC_PER_EVAL:
+        return None
+    return TRAFFIC_PER_EVAL[kernel] * evals
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -355,25 +380,43 @@ def run_ours(args):
 
     peaks, peak_kind = load_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    # ALU roofline: per kernel evaluation 7 FP32-pipe operations and one MUFU
-    # operation (rsqrt / lg2 / rcp); a GB300 SM has 128 FP32 lanes and 16 MUFU
-    # lanes per clock, so the MUFU pipe bounds at 16 evaluations/clock/SM.
-    per_sm_clk = {2: 16.0, 0: 16.0, 1: 128.0 / 11.0, 100: 128.0 / 4.0}[wl["kernel"]]
-    peak_evals = 152 * per_sm_clk * sm_max * 1e6 * nrhs
+    # ALU roofline of the interaction kernels, in kernel evaluations (one
+    # K(x, y) per target-source pair, shared by all right-hand sides):
+    #  - one right-hand side: 7 FP32-pipe operations and one MUFU operation
+    #    (rsqrt / lg2 / rcp) per evaluation; a GB300 SM has 128 FP32 lanes and
+    #    16 MUFU lanes per clock, so the MUFU pipe bounds at 16/clock/SM;
+    #  - nrhs = 8 or 16 (multi32_kernel): 6 FP32 operations for |r|^2 plus
+    #    one FMA per right-hand side, so the FP32 pipe bounds at
+    #    128 / (6 + nrhs) evaluations/clock/SM.
+    if nrhs == 1:
+        per_sm_clk = {2: 16.0, 0: 16.0, 1: 128.0 / 11.0, 100: 128.0 / 4.0}[wl["kernel"]]
+    else:
+        per_sm_clk = min(16.0, 128.0 / (6 + min(nrhs, 16)))
+    peak_evals = 152 * per_sm_clk * sm_max * 1e6
     ncalls = max(calls, 1)
     ev_sym = st.get("sym_evals", 0) if nrhs == 1 else 0
-    kern = {
-        # kernel: (kernel evaluations per launch, ms per launch)
-        "pp_sym_kernel (mirrored PP pairs, one evaluation per pair)":
-            (ev_sym, phases.get("ppsym", 0.0) / ncalls),
-        "near32x2_kernel (self and unmirrored PP, PC)":
-            (st["evals"][0] + st["evals"][1] - 2 * ev_sym, phases["near"] / ncalls),
-        "far32x2_kernel (CC, CP)": (st["evals"][2] + st["evals"][3], phases["far"] / ncalls),
-    }
+    if nrhs == 1:
+        kern = {
+            # kernel: (kernel evaluations per launch, ms per launch)
+            "pp_sym_kernel": (ev_sym, phases.get("ppsym", 0.0) / ncalls),
+            "near32x2_kernel": (st["evals"][0] + st["evals"][1] - 2 * ev_sym, phases["near"] / ncalls),
+            "far32x2_kernel": (st["evals"][2] + st["evals"][3], phases["far"] / ncalls),
+        }
+        what = {"pp_sym_kernel": "mirrored PP leaf pairs, one evaluation per pair",
+                "near32x2_kernel": "self and unmirrored PP, PC",
+                "far32x2_kernel": "CC, CP"}
+    else:
+        # per evaluation of all right-hand sides (chunks of 16 in one launch)
+        kern = {
+            "multi32_kernel (near)": (st["evals"][0] + st["evals"][1], phases["near"] / ncalls),
+            "multi32_kernel (far)": (st["evals"][2] + st["evals"][3], phases["far"] / ncalls),
+        }
+        what = {"multi32_kernel (near)": f"PP, PC for {nrhs} right-hand sides",
+                "multi32_kernel (far)": f"CC, CP for {nrhs} right-hand sides"}
     dom = max(kern, key=lambda k: kern[k][1])
     dom_evals, dom_ms = kern[dom]
-    achieved = dom_evals * nrhs / (dom_ms / 1e3)
-    traffic = None
+    achieved = dom_evals / (dom_ms / 1e3)
+    traffic = traffic_per_launch(dom, dom_evals) if nrhs == 1 else None
     line = {
         "metric": "FMM targets/s at N=6.3M", "value": value, "unit": "targets/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -386,7 +429,8 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (plan + workspace "
                          f"{st['device_bytes'] / 1e9:.2f} GB resident)"},
         "rel_err_vs_fp64_ds": err, "err_samples": args.err_samples,
-        "kernel_evals_per_s": world * sum(st["evals"]) * nrhs / (ms_step / 1e3),
+        "kernel_evals_per_s": world * sum(st["evals"]) / (ms_step / 1e3),
+        "interactions_per_s": world * sum(st["evals"]) * nrhs / (ms_step / 1e3),
         "phase_ms": {k: v / max(calls, 1) for k, v in phases.items()},
         "plan_build_ms": st["build_ms"],
         "fp64_gpu_fmm": fp64,
@@ -394,14 +438,18 @@ def run_ours(args):
         "gpu_launches": launches,
         "e2e": {"value": e2e_val, "unit": "targets/s",
                 "h2d_bytes_per_step": int(w.nbytes), "d2h_bytes_per_step": int(8 * nrhs * N * dim)},
-        "roofline": {"kernel": dom, "bound": "alu",
+        "roofline": {"kernel": f"{dom} ({what[dom]})", "bound": "alu",
                      "achieved": achieved / 1e9, "peak": peak_evals / 1e9, "unit": "Geval/s",
-                     "frac": achieved / peak_evals, "traffic": traffic,
-                     "peak_source": f"{peak_kind} sm_max_mhz x 152 SMs x {per_sm_clk:.1f} "
+                     "frac": achieved / peak_evals,
+                     "traffic": traffic, "traffic_unit": "bytes per launch",
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the "
+                                       "6 x 512^2 case, scaled by evaluations per launch"
+                                       if traffic is not None else None,
+                     "peak_source": f"{peak_kind} sm_max_mhz x 152 SMs x {per_sm_clk:.2f} "
                                     "evals/clk/SM"},
         "kernels": {k: {"evals_per_launch": e, "ms_per_launch": m,
-                        "geval_per_s": (e * nrhs / (m / 1e3) / 1e9) if m > 0 else None,
-                        "frac_of_alu_peak": (e * nrhs / (m / 1e3) / peak_evals) if m > 0 else None}
+                        "geval_per_s": (e / (m / 1e3) / 1e9) if m > 0 else None,
+                        "frac_of_alu_peak": (e / (m / 1e3) / peak_evals) if m > 0 else None}
                     for k, (e, m) in kern.items()},
         "clocks": clk.summary(),
     }

@@ -135,8 +135,8 @@ csfmm_status csfmm_plan_create(const double *points, int64_t N, int kernel_id, i
     return CSFMM_ERR_INVALID_ARG;
   }
   if (o.max_nrhs < 1) o.max_nrhs = 16;
-  if (o.max_nrhs > 64) {
-    set_error("max_nrhs must be <= 64 (got %d)", o.max_nrhs);
+  if (o.max_nrhs > csfmm::kMaxNrhs) {
+    set_error("max_nrhs must be <= %d (got %d)", csfmm::kMaxNrhs, o.max_nrhs);
     return CSFMM_ERR_INVALID_ARG;
   }
   csfmm_status s = check_device_pointer(points, "points");
@@ -241,7 +241,7 @@ csfmm_status csfmm_evaluate_host(csfmm_plan plan, const double *weights, int nrh
 }
 
 csfmm_status csfmm_workspace_create(csfmm_plan plan, int max_nrhs, csfmm_workspace *out) {
-  if (!plan || !out || max_nrhs < 1 || max_nrhs > 64) {
+  if (!plan || !out || max_nrhs < 1 || max_nrhs > csfmm::kMaxNrhs) {
     set_error("plan and out must be non-NULL and 1 <= max_nrhs <= 64");
     return CSFMM_ERR_INVALID_ARG;
   }

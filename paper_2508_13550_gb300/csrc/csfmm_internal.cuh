@@ -76,6 +76,9 @@ struct DeviceArena {
   }
 };
 
+// Largest number of right-hand sides of one evaluation (checked by the API).
+constexpr int kMaxNrhs = 64;
+
 // Read-only view of a plan passed to kernels by value.
 struct PlanView {
   int N, n, p, P, N0, ncells, dim, kernel_id;
@@ -97,6 +100,11 @@ struct PlanView {
   const float *m2m32;    // [2][2][p][p]: FP32 rounding of m2m64, then the remainders
   const double *cheb;    // [p]
   int *status;
+  // Per evaluation (FP32 form, log kernel): weight totals of every cell as
+  // unevaluated FP32 pairs, [nc][wtot_ld][2] = (particle weights of a leaf,
+  // proxy weights of a cell), each summed in FP64 from the FP32 weights.
+  const float2 *wtot;
+  int wtot_ld;
 };
 
 struct Plan {
@@ -192,6 +200,7 @@ struct Workspace {
   double *psi = nullptr;    // [nc][max_nrhs][dim][P] proxy potentials (FP64 in both forms)
   double *phi = nullptr;    // [max_nrhs][N][dim] near-field potentials, tree order
   float *sym_part = nullptr;     // [plan.sym_part_len] cross-pair partial sums (FP32 form)
+  float2 *wtot = nullptr;        // [nc][max_nrhs][2] weight totals (FP32 form)
   double *stage_w = nullptr;    // device staging for host-buffer evaluations [max_nrhs][N]
   double *stage_out = nullptr;  // [max_nrhs][N][dim]
   int last_nrhs = 0;

@@ -131,6 +131,11 @@ __global__ void gather_kernel(const int32_t *perm, const double *w, double *ws, 
   }
 }
 
+__device__ __forceinline__ float2 split_f32(double x) {
+  const float h = __double2float_rn(x);
+  return make_float2(h, __double2float_rn(x - (double)h));
+}
+
 // ---------------------------------------------------------------------------
 // P2M: for leaf c, wbar[c][r][k1 p + k2] = sum_j La[j][k1] Lb[j][k2] w_r[j].
 // One block per leaf (blockDim >= P), one thread per proxy; the Lagrange
@@ -142,7 +147,7 @@ __global__ void gather_kernel(const int32_t *perm, const double *w, double *ws, 
 // ---------------------------------------------------------------------------
 template <typename Real, int NR>
 __global__ void p2m_kernel(PlanView v, const int32_t *leaves, const double *ws, int ldw, int r0,
-                           Real *wbar, int ldr) {
+                           Real *wbar, int ldr, float2 *wtot) {
   constexpr int CH = 64;
   __shared__ Real sLa[CH * kMaxP], sLb[CH * kMaxP], sw[NR * CH];
   const int c = leaves[blockIdx.x];
@@ -181,6 +186,34 @@ __global__ void p2m_kernel(PlanView v, const int32_t *leaves, const double *ws, 
   if (k < P) {
 #pragma unroll
     for (int q = 0; q < NR; ++q) wbar[((int64_t)c * ldr + r0 + q) * P + k] = (Real)acc[q];
+  }
+  if constexpr (sizeof(Real) == 4) {
+    if (wtot) {
+      // totals of the leaf's FP32 particle weights (u < NR) and of its FP32
+      // proxy weights (u >= NR), summed in FP64 in a fixed order
+      __shared__ double red[2 * NR][32];
+      double a[2 * NR];
+#pragma unroll
+      for (int q = 0; q < NR; ++q) {
+        a[q] = 0.0;
+        for (int j = b + threadIdx.x; j < e; j += blockDim.x)
+          a[q] += (double)(float)ws[(int64_t)(r0 + q) * ldw + j];
+        a[NR + q] = k < P ? (double)(Real)acc[q] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 2 * NR; ++u) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a[u] += __shfl_xor_sync(0xffffffffu, a[u], o);
+        if ((threadIdx.x & 31) == 0) red[u][threadIdx.x >> 5] = a[u];
+      }
+      __syncthreads();
+      if (threadIdx.x < 2 * NR) {
+        const int u = threadIdx.x, q = u % NR, kind = u / NR;
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[u][w];
+        wtot[((int64_t)c * ldr + r0 + q) * 2 + kind] = split_f32(t);
+      }
+    }
   }
 }
 
@@ -265,7 +298,11 @@ __device__ __forceinline__ void df_acc(float &sh, float &sl, float bh, float bl)
 // same pattern from cell to cell, so rounding the contraction to FP32 biases
 // all proxy weights alike (measured: a relative bias of up to 8e-8 in the
 // potentials at degree 8); in double-float that bias is gone.
-__global__ void m2m_df_kernel(PlanView v, int cell0, int r0, int nr, float *wbar, int ldr) {
+__global__ void m2m_df_kernel(PlanView v, int cell0, int r0, int nr, float *wbar, int ldr,
+                              float2 *wtot) {
+  // per right-hand side and warp (launched with 128 threads): partial totals
+  // of the cell's proxy weights
+  __shared__ double red[kMaxNrhs][4];
   __shared__ float sMh[2 * kMaxP * kMaxP], sMl[2 * kMaxP * kMaxP];
   __shared__ float sw[kMaxP * kMaxP], sth[kMaxP * kMaxP], stl[kMaxP * kMaxP];
   const int c = cell0 + blockIdx.x;
@@ -305,8 +342,23 @@ __global__ void m2m_df_kernel(PlanView v, int cell0, int r0, int nr, float *wbar
           df_acc_prod(ah[u], al[u], sMh[o + m1], sMl[o + m1], sth[m1 * p + k2], stl[m1 * p + k2]);
       }
     }
-    for (int u = 0, t = threadIdx.x; t < P; ++u, t += blockDim.x)
-      wbar[((int64_t)c * ldr + r) * P + t] = __fadd_rn(ah[u], al[u]);
+    double tq = 0.0;
+    for (int u = 0, t = threadIdx.x; t < P; ++u, t += blockDim.x) {
+      const float o = __fadd_rn(ah[u], al[u]);
+      wbar[((int64_t)c * ldr + r) * P + t] = o;
+      tq += (double)o;
+    }
+    if (wtot) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) tq += __shfl_xor_sync(0xffffffffu, tq, o);
+      if ((threadIdx.x & 31) == 0) red[r - r0][threadIdx.x >> 5] = tq;
+    }
+  }
+  if (wtot) {  // totals of the cell's FP32 proxy weights, fixed summation order
+    __syncthreads();
+    for (int r = threadIdx.x; r < nr; r += blockDim.x)
+      wtot[((int64_t)c * ldr + r0 + r) * 2 + 1] =
+          split_f32(red[r][0] + red[r][1] + red[r][2] + red[r][3]);
   }
 }
 
@@ -804,6 +856,10 @@ csfmm_status run_passes(Plan &pl, Workspace &W, const double *w, int nrhs, doubl
   Real *wbar;
   if constexpr (sizeof(Real) == 4) wbar = W.wbar32; else wbar = W.wbar;
   double *psi = W.psi;  // FP64 proxy potentials in both forms
+  // weight totals per cell for the log kernel's FP32 sums
+  float2 *wtot = (sizeof(Real) == 4 && KID == CSFMM_KERNEL_LAPLACE) ? W.wtot : nullptr;
+  v.wtot = wtot;
+  v.wtot_ld = ldr;
   pl.launches = 0;
 #define CSFMM_MARK(ph)                              \
   do {                                              \
@@ -820,10 +876,10 @@ csfmm_status run_passes(Plan &pl, Workspace &W, const double *w, int nrhs, doubl
   for (int r0 = 0; r0 < nrhs; r0 += kRB) {
     int nr = min(kRB, nrhs - r0);
     switch (nr) {
-      case 1: p2m_kernel<Real, 1><<<pl.nleaves, tb_p2m, 0, st>>>(v, pl.leaves, W.ws, N, r0, wbar, ldr); break;
-      case 2: p2m_kernel<Real, 2><<<pl.nleaves, tb_p2m, 0, st>>>(v, pl.leaves, W.ws, N, r0, wbar, ldr); break;
-      case 3: p2m_kernel<Real, 3><<<pl.nleaves, tb_p2m, 0, st>>>(v, pl.leaves, W.ws, N, r0, wbar, ldr); break;
-      default: p2m_kernel<Real, 4><<<pl.nleaves, tb_p2m, 0, st>>>(v, pl.leaves, W.ws, N, r0, wbar, ldr); break;
+      case 1: p2m_kernel<Real, 1><<<pl.nleaves, tb_p2m, 0, st>>>(v, pl.leaves, W.ws, N, r0, wbar, ldr, wtot); break;
+      case 2: p2m_kernel<Real, 2><<<pl.nleaves, tb_p2m, 0, st>>>(v, pl.leaves, W.ws, N, r0, wbar, ldr, wtot); break;
+      case 3: p2m_kernel<Real, 3><<<pl.nleaves, tb_p2m, 0, st>>>(v, pl.leaves, W.ws, N, r0, wbar, ldr, wtot); break;
+      default: p2m_kernel<Real, 4><<<pl.nleaves, tb_p2m, 0, st>>>(v, pl.leaves, W.ws, N, r0, wbar, ldr, wtot); break;
     }
     ++pl.launches;
   }
@@ -831,7 +887,7 @@ csfmm_status run_passes(Plan &pl, Workspace &W, const double *w, int nrhs, doubl
   for (int l = pl.nlevels - 2; l >= 0; --l) {
     int c0 = pl.level_begin[l], nlev = pl.level_begin[l + 1] - c0;
     if constexpr (sizeof(Real) == 4)
-      m2m_df_kernel<<<nlev, 128, 0, st>>>(v, c0, 0, nrhs, wbar, ldr);
+      m2m_df_kernel<<<nlev, 128, 0, st>>>(v, c0, 0, nrhs, wbar, ldr, wtot);
     else
       m2m_kernel<Real><<<nlev, 128, 0, st>>>(v, c0, 0, nrhs, wbar, ldr);
     ++pl.launches;
@@ -945,6 +1001,7 @@ csfmm_status workspace_alloc(Plan &pl, Workspace &W, int max_nrhs) {
   } else {
     if ((s = W.arena.alloc(&W.wbar32, nc * R * P)) != CSFMM_OK) return s;
     if ((s = W.arena.alloc(&W.wsf, R * N)) != CSFMM_OK) return s;
+    if ((s = W.arena.alloc(&W.wtot, nc * R * 2)) != CSFMM_OK) return s;
     if (pl.n_sym_pairs > 0 && pl.kernel_id != CSFMM_KERNEL_BIOT_SAVART &&
         (s = W.arena.alloc(&W.sym_part, (size_t)pl.sym_part_len)) != CSFMM_OK)
       return s;

@@ -72,6 +72,20 @@ __device__ __forceinline__ float kfactor(float d2) {
   else return 1.0f;
 }
 
+// Log kernel: a list entry (target cell c, source cell s) scales its
+// pair-relative coordinates by sigma = 2^e, exact in FP32, with 2^-e of the
+// order of the distance between the two cells (or of the source radius), so
+// that log2(sigma^2 d^2) stays near zero.  The FP32 sums of w log2(sigma^2 d^2)
+// then have small partial sums; the shift 2 e sum(w) is removed in FP64.
+__device__ __forceinline__ int log_scale_exp(const PlanView &v, int c, int s) {
+  const double dx = v.ccentre[3 * c] - v.ccentre[3 * s];
+  const double dy = v.ccentre[3 * c + 1] - v.ccentre[3 * s + 1];
+  const double dz = v.ccentre[3 * c + 2] - v.ccentre[3 * s + 2];
+  const double ref = fmax(fmax(sqrt(dx * dx + dy * dy + dz * dz), v.cradius[s]), 1e-18);
+  return -ilogb(ref);
+}
+__device__ __forceinline__ float exp2i(int e) { return __int_as_float((127 + e) << 23); }
+
 // Packed pairs of FP32 values in one 64-bit register (Blackwell f32x2 math).
 typedef unsigned long long f2x;
 __device__ __forceinline__ f2x f2_sub(f2x a, f2x b) {
@@ -108,7 +122,10 @@ __device__ __forceinline__ void f2_unpack(f2x a, float &lo, float &hi) {
 // the rounding error of a tile sum is that of a kChunk-term sum rather than
 // of a kTile-term one (errors of long same-signed FP32 sums do not average
 // out across targets that share the same tile geometry).
-constexpr int kChunk = 32;
+#ifndef CSFMM_CHUNK
+#define CSFMM_CHUNK 32
+#endif
+constexpr int kChunk = CSFMM_CHUNK;
 __device__ __forceinline__ void two_sum_fold(float &hi, float &lo, float c) {
   const float s = hi + c;
   const float bb = s - hi;
@@ -127,6 +144,21 @@ __device__ __forceinline__ double f2_total(f2x hi, f2x lo, int h) {
   f2_unpack(lo, b0, b1);
   return h == 0 ? (double)a0 + (double)b0 : (double)a1 + (double)b1;
 }
+// Weight total of source cell s for right-hand side r: particles (kind 0, a
+// leaf's weights) or proxies (kind 1), as an FP32 pair.
+__device__ __forceinline__ float2 weight_total(const PlanView &v, int s, int r, int kind) {
+  return v.wtot[((int64_t)s * v.wtot_ld + r) * 2 + kind];
+}
+// (hi, lo) -= (t.x, t.y) for both halves of a packed pair.
+__device__ __forceinline__ void fold_minus(f2x &hi, f2x &lo, float2 t) {
+  two_sum_fold(hi, lo, f2_pack(-t.x, -t.x));
+  lo = f2_add(lo, f2_pack(-t.y, -t.y));
+}
+__device__ __forceinline__ void fold_minus(float &hi, float &lo, float2 t) {
+  two_sum_fold(hi, lo, -t.x);
+  lo -= t.y;
+}
+
 // One tile for NP pairs of targets (2 NP targets) and one right-hand side:
 // sA[j] = (x, x, y, y), sB[j] = (z, z, w, w) of source j.
 template <int KID, int NP, bool SELF>
@@ -236,30 +268,25 @@ __global__ void __launch_bounds__(kThreads) near32_kernel(PlanView v, const int3
   constexpr int DIM = kdim32<KID>();
   __shared__ float4 sp[kTile];
   __shared__ float sw[NR * kTile];
-  __shared__ double wsum[NR][kThreads / 32];
   const int c = leaves[blockIdx.x];
   const int b = v.cbegin[c], e = v.cend[c], P = v.P;
   const double cTx = v.ccentre[3 * c], cTy = v.ccentre[3 * c + 1], cTz = v.ccentre[3 * c + 2];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i0 = b; i0 < e; i0 += kThreads * NT) {
     float ox[NT], oy[NT], oz[NT];
-    double xa[NT][3];   // absolute target position (Biot-Savart cross product)
     bool act[NT];
-    double out[NT][NR][DIM];
+    // running totals over all list entries as FP32 (hi, lo) pairs: the kernel
+    // sums (log kernel: sum w (log2 d2 - 1); Biot-Savart: sum w r / d2)
+    float ahi[NT][NR][3], alo[NT][NR][3];
 #pragma unroll
     for (int k = 0; k < NT; ++k) {
       const int i = i0 + threadIdx.x + k * kThreads;
       act[k] = i < e;
-      const int ii = act[k] ? i : b;
-      const float4 o = v.off32[ii];
+      const float4 o = v.off32[act[k] ? i : b];
       ox[k] = o.x; oy[k] = o.y; oz[k] = o.z;
-      if constexpr (KID == CSFMM_KERNEL_BIOT_SAVART) {
-        xa[k][0] = v.x[ii]; xa[k][1] = v.x[v.N + ii]; xa[k][2] = v.x[2 * (int64_t)v.N + ii];
-      }
 #pragma unroll
       for (int q = 0; q < NR; ++q)
 #pragma unroll
-        for (int d = 0; d < DIM; ++d) out[k][q][d] = 0.0;
+        for (int d = 0; d < 3; ++d) ahi[k][q][d] = alo[k][q][d] = 0.f;
     }
     for (int pass = 0; pass < 2; ++pass) {
       const int type = pass == 0 ? CSFMM_LIST_PP : CSFMM_LIST_PC;
@@ -280,12 +307,24 @@ __global__ void __launch_bounds__(kThreads) near32_kernel(PlanView v, const int3
         const int sb = pp ? v.cbegin[s] : 0;
         const int nsrc = pp ? v.cend[s] - sb : P;
         const bool self_tile = pp && s == c;
+        if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
+          // -(1/4pi) sum w ln(d2/2) = -(ln2/4pi) (sum w log2 d2 - sum w); the
+          // target's own weight is not part of the sum over the self leaf
+#pragma unroll
+          for (int q = 0; q < NR; ++q) {
+            const float2 W = weight_total(v, s, r0 + q, pp ? 0 : 1);
+#pragma unroll
+            for (int k = 0; k < NT; ++k) {
+              fold_minus(ahi[k][q][0], alo[k][q][0], W);
+              if (self_tile && act[k])
+                two_sum_fold(ahi[k][q][0], alo[k][q][0],
+                             wsf[(int64_t)(r0 + q) * ldw + i0 + threadIdx.x + k * kThreads]);
+            }
+          }
+        }
         for (int j0 = 0; j0 < nsrc; j0 += kTile) {
           const int nj = min(kTile, nsrc - j0);
           __syncthreads();
-          double part[NR];
-#pragma unroll
-          for (int q = 0; q < NR; ++q) part[q] = 0.0;
           for (int t = threadIdx.x; t < nj; t += kThreads) {
             float4 val;
             float wv[NR];
@@ -305,26 +344,8 @@ __global__ void __launch_bounds__(kThreads) near32_kernel(PlanView v, const int3
             sp[t] = val;
 #pragma unroll
             for (int q = 1; q < NR; ++q) sw[q * kTile + t] = wv[q];
-#pragma unroll
-            for (int q = 0; q < NR; ++q) part[q] += (double)wv[q];
-          }
-          if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
-#pragma unroll
-            for (int q = 0; q < NR; ++q) {
-              double x = part[q];
-#pragma unroll
-              for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-              if (lane == 0) wsum[q][warp] = x;
-            }
           }
           __syncthreads();
-          float ahi[NT][NR][3], alo[NT][NR][3];
-#pragma unroll
-          for (int k = 0; k < NT; ++k)
-#pragma unroll
-            for (int q = 0; q < NR; ++q)
-#pragma unroll
-              for (int d = 0; d < 3; ++d) ahi[k][q][d] = alo[k][q][d] = 0.f;
           int self[NT];
 #pragma unroll
           for (int k = 0; k < NT; ++k) self[k] = (i0 + (int)threadIdx.x + k * kThreads) - (sb + j0);
@@ -332,31 +353,6 @@ __global__ void __launch_bounds__(kThreads) near32_kernel(PlanView v, const int3
             tile_sum<KID, NT, NR, true>(sp, sw, nj, tx, ty, tz, self, ahi, alo);
           else
             tile_sum<KID, NT, NR, false>(sp, sw, nj, tx, ty, tz, self, ahi, alo);
-#pragma unroll
-          for (int k = 0; k < NT; ++k) {
-#pragma unroll
-            for (int q = 0; q < NR; ++q) {
-              if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
-                // -(1/4pi) sum w ln(d2/2) = -(ln2/4pi) (sum w log2 d2 - sum w)
-                double tot = 0.0;
-#pragma unroll
-                for (int u = 0; u < kThreads / 32; ++u) tot += wsum[q][u];
-                if (self_tile && self[k] >= 0 && self[k] < nj)
-                  tot -= (double)((q == 0) ? sp[self[k]].w : sw[q * kTile + self[k]]);
-                out[k][q][0] += -(0.69314718055994530942 * kInv4Pi) *
-                                (((double)ahi[k][q][0] + (double)alo[k][q][0]) - tot);
-              } else if constexpr (KID == CSFMM_KERNEL_BIOT_SAVART) {
-                const double b0 = (double)ahi[k][q][0] + (double)alo[k][q][0];
-                const double b1 = (double)ahi[k][q][1] + (double)alo[k][q][1];
-                const double b2 = (double)ahi[k][q][2] + (double)alo[k][q][2];
-                out[k][q][0] += kInv2Pi * (xa[k][1] * b2 - xa[k][2] * b1);
-                out[k][q][1] += kInv2Pi * (xa[k][2] * b0 - xa[k][0] * b2);
-                out[k][q][2] += kInv2Pi * (xa[k][0] * b1 - xa[k][1] * b0);
-              } else {
-                out[k][q][0] += (double)ahi[k][q][0] + (double)alo[k][q][0];
-              }
-            }
-          }
         }
       }
     }
@@ -365,21 +361,35 @@ __global__ void __launch_bounds__(kThreads) near32_kernel(PlanView v, const int3
       if (!act[k]) continue;
       const int i = i0 + threadIdx.x + k * kThreads;
 #pragma unroll
-      for (int q = 0; q < NR; ++q)
+      for (int q = 0; q < NR; ++q) {
+        double o[3];
 #pragma unroll
-        for (int d = 0; d < DIM; ++d) phi[((int64_t)(r0 + q) * v.N + i) * DIM + d] = out[k][q][d];
+        for (int d = 0; d < 3; ++d) o[d] = (double)ahi[k][q][d] + (double)alo[k][q][d];
+        double* dst = phi + ((int64_t)(r0 + q) * v.N + i) * DIM;
+        if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
+          dst[0] = -(0.69314718055994530942 * kInv4Pi) * o[0];
+        } else if constexpr (KID == CSFMM_KERNEL_BIOT_SAVART) {
+          // (1/2pi) x × sum_j w_j r_j / |r_j|^2, with the FP64 target position
+          const double x0 = v.x[i], x1 = v.x[v.N + i], x2 = v.x[2 * (int64_t)v.N + i];
+          dst[0] = kInv2Pi * (x1 * o[2] - x2 * o[1]);
+          dst[1] = kInv2Pi * (x2 * o[0] - x0 * o[2]);
+          dst[2] = kInv2Pi * (x0 * o[1] - x1 * o[0]);
+        } else {
+          dst[0] = o[0];
+        }
+      }
     }
   }
 }
-
 
 // ---------------------------------------------------------------------------
 // Symmetric PP (Eq. PP) for K(x, y) = K(y, x): one block per cross pair
 // (T, S), T < S, evaluates each kernel value once and produces both
 //     rows:    sum_{j in S} K(x_i, y_j) w_j   for the points i of T,
 //     columns: sum_{i in T} K(x_i, y_j) w_i   for the points j of S,
-// written to part[off[pair] ...] (rows first, then columns) as final FP32
-// potentials.  Two warps, each lane owns four rows of T (two packed pairs);
+// written to part[off[pair] ...] (rows first, then columns) as FP32 sums
+// (the log kernel stores sum w (log2 d2 - 1); the factor -ln2/4pi is applied
+// with the rest of the near field).  Two warps, each lane owns four rows of T (two packed pairs);
 // columns of S are staged as (x,x,y,y)/(z,z,w,w) tiles and processed in
 // groups of 32: every lane accumulates its rows' contributions to the 32
 // columns, then a butterfly transpose-reduction over the warp leaves the sum
@@ -406,12 +416,11 @@ __device__ __forceinline__ float transpose_reduce32(float (&v)[32], int lane) {
 }
 
 template <int KID>
-__global__ void __launch_bounds__(kSymThreads) pp_sym_kernel(PlanView v, const int2 *pairs,
+__global__ void __launch_bounds__(kSymThreads, 8) pp_sym_kernel(PlanView v, const int2 *pairs,
                                                              const int32_t *off, const float *wsf,
                                                              float *part) {
   __shared__ ulonglong2 sA[kSymCols], sB[kSymCols];
   __shared__ float colacc[kSymThreads / 32][kSymCols];
-  __shared__ double wred[2][kSymThreads / 32];
   const int2 pr = pairs[blockIdx.x];
   const int T = pr.x, S = pr.y;
   const int tb = v.cbegin[T], te = v.cend[T], sb = v.cbegin[S], se = v.cend[S];
@@ -422,27 +431,18 @@ __global__ void __launch_bounds__(kSymThreads) pp_sym_kernel(PlanView v, const i
   const float dcx = (float)(v.ccentre[3 * T] - v.ccentre[3 * S]);
   const float dcy = (float)(v.ccentre[3 * T + 1] - v.ccentre[3 * S + 1]);
   const float dcz = (float)(v.ccentre[3 * T + 2] - v.ccentre[3 * S + 2]);
-  // Laplace: total weights of T and S for -(ln2/4pi)(sum w log2 d2 - sum w)
+  int lse = 0;
+  float sg = 1.f;
+  if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
+    lse = log_scale_exp(v, T, S);
+    sg = exp2i(lse);
+  }
+  // log kernel: weight totals of T and S for -(ln2/4pi)(sum w log2 d2 - sum w)
   double WT = 0.0, WS = 0.0;
   if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
-    double a = 0.0, c = 0.0;
-    for (int t = threadIdx.x; t < nT; t += kSymThreads) a += (double)wsf[tb + t];
-    for (int t = threadIdx.x; t < nS; t += kSymThreads) c += (double)wsf[sb + t];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      a += __shfl_xor_sync(0xffffffffu, a, o);
-      c += __shfl_xor_sync(0xffffffffu, c, o);
-    }
-    if (lane == 0) {
-      wred[0][warp] = a;
-      wred[1][warp] = c;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int u = 0; u < kSymThreads / 32; ++u) {
-      WT += wred[0][u];
-      WS += wred[1][u];
-    }
+    const float2 a = weight_total(v, T, 0, 0), b2 = weight_total(v, S, 0, 0);
+    WT = (double)a.x + (double)a.y;
+    WS = (double)b2.x + (double)b2.y;
   }
   for (int r0 = 0; r0 < nT; r0 += kSymRows) {
     // rows of this lane: r0 + warp*128 + lane + 32k, k = 0..3 (pairs (0,1), (2,3))
@@ -458,9 +458,9 @@ __global__ void __launch_bounds__(kSymThreads) pp_sym_kernel(PlanView v, const i
         act[k] = i < nT;
         const int ii = tb + (act[k] ? i : 0);
         const float4 o = v.off32[ii];
-        x[h] = o.x + dcx;
-        y[h] = o.y + dcy;
-        z[h] = o.z + dcz;
+        x[h] = (o.x + dcx) * sg;
+        y[h] = (o.y + dcy) * sg;
+        z[h] = (o.z + dcz) * sg;
         w[h] = act[k] ? wsf[ii] : 0.f;
       }
       tx[q] = f2_pack(x[0], x[1]);
@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(kSymThreads) pp_sym_kernel(PlanView v, const i
         float x = 1.0e4f, y = 1.0e4f, z = 1.0e4f, w = 0.f;  // padding: far away, no weight
         if (t < nj) {
           const float4 o = v.off32[sb + c0 + t];
-          x = o.x; y = o.y; z = o.z;
+          x = o.x * sg; y = o.y * sg; z = o.z * sg;
           w = wsf[sb + c0 + t];
         }
         sA[t] = make_ulonglong2(f2_pack(x, x), f2_pack(y, y));
@@ -532,8 +532,7 @@ __global__ void __launch_bounds__(kSymThreads) pp_sym_kernel(PlanView v, const i
         if (!act[k]) continue;
         const int i = r0 + warp * 128 + lane + 32 * k;
         double val = f2_total(rhi[q], rlo[q], h);
-        if constexpr (KID == CSFMM_KERNEL_LAPLACE)
-          val = -(0.69314718055994530942 * kInv4Pi) * (val - WS);
+        if constexpr (KID == CSFMM_KERNEL_LAPLACE) val -= (1 + 2 * lse) * WS;
         rowpart[i] = (float)val;
       }
     }
@@ -541,7 +540,7 @@ __global__ void __launch_bounds__(kSymThreads) pp_sym_kernel(PlanView v, const i
   if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
     __syncthreads();
     for (int t = threadIdx.x; t < nS; t += kSymThreads)
-      colpart[t] = (float)(-(0.69314718055994530942 * kInv4Pi) * ((double)colpart[t] - WT));
+      colpart[t] = (float)((double)colpart[t] - (1 + 2 * lse) * WT);
   }
 }
 
@@ -557,23 +556,24 @@ __global__ void __launch_bounds__(kThreads, CSFMM_NEAR_MINB) near32x2_kernel(Pla
                                                             const float *part) {
   constexpr int NT = 2 * NP;
   __shared__ ulonglong2 sA[kTile], sB[kTile];
-  __shared__ double wsum[kThreads / 32];
   const int c = leaves[blockIdx.x];
   const int b = v.cbegin[c], e = v.cend[c], P = v.P;
   const double cTx = v.ccentre[3 * c], cTy = v.ccentre[3 * c + 1], cTz = v.ccentre[3 * c + 2];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const float *wr = wsf + (int64_t)r0 * v.N;
   for (int i0 = b; i0 < e; i0 += kThreads * NT) {
     float ox[NT], oy[NT], oz[NT];
-    double out[NT], pre[NT];  // evaluated here; read from the cross-pair partials
+    // running totals of the target pairs over all list entries (and the
+    // cross-pair partials) as FP32 (hi, lo) pairs; the log kernel holds
+    // sum w (log2 d2 - 1) and is scaled by -ln2/4pi at the end
+    f2x hi[NP], lo[NP];
 #pragma unroll
     for (int k = 0; k < NT; ++k) {
       const int i = i0 + threadIdx.x + k * kThreads;
       const float4 o = v.off32[i < e ? i : b];
       ox[k] = o.x; oy[k] = o.y; oz[k] = o.z;
-      out[k] = 0.0;
-      pre[k] = 0.0;
     }
+#pragma unroll
+    for (int q = 0; q < NP; ++q) hi[q] = lo[q] = 0ull;
     for (int pass = 0; pass < 2; ++pass) {
       const int type = pass == 0 ? CSFMM_LIST_PP : CSFMM_LIST_PC;
       const int e0 = v.loff[type][c], e1 = v.loff[type][c + 1];
@@ -582,9 +582,9 @@ __global__ void __launch_bounds__(kThreads, CSFMM_NEAR_MINB) near32x2_kernel(Pla
         if (part && type == CSFMM_LIST_PP && v.sym_contrib[ee] >= 0) {
           const float *pp = part + v.sym_contrib[ee] - b;
 #pragma unroll
-          for (int k = 0; k < NT; ++k) {
-            const int i = i0 + threadIdx.x + k * kThreads;
-            if (i < e) pre[k] += (double)pp[i];
+          for (int q = 0; q < NP; ++q) {
+            const int i = i0 + threadIdx.x + 2 * q * kThreads, i1 = i + kThreads;
+            two_sum_fold(hi[q], lo[q], f2_pack(i < e ? pp[i] : 0.f, i1 < e ? pp[i1] : 0.f));
           }
           continue;
         }
@@ -602,10 +602,22 @@ __global__ void __launch_bounds__(kThreads, CSFMM_NEAR_MINB) near32x2_kernel(Pla
         const int sb = pp ? v.cbegin[s] : 0;
         const int nsrc = pp ? v.cend[s] - sb : P;
         const bool self_tile = pp && s == c;
+        if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
+          // -(1/4pi) sum w ln(d2/2) = -(ln2/4pi) (sum w log2 d2 - sum w); the
+          // target's own weight is not part of the sum over the self leaf
+          const float2 W = weight_total(v, s, r0, pp ? 0 : 1);
+#pragma unroll
+          for (int q = 0; q < NP; ++q) {
+            fold_minus(hi[q], lo[q], W);
+            if (self_tile) {
+              const int i = i0 + threadIdx.x + 2 * q * kThreads, i1 = i + kThreads;
+              two_sum_fold(hi[q], lo[q], f2_pack(i < e ? wr[i] : 0.f, i1 < e ? wr[i1] : 0.f));
+            }
+          }
+        }
         for (int j0 = 0; j0 < nsrc; j0 += kTile) {
           const int nj = min(kTile, nsrc - j0);
           __syncthreads();
-          double part = 0.0;
           for (int t = threadIdx.x; t < nj; t += kThreads) {
             float x, y, z, w;
             if (pp) {
@@ -621,17 +633,8 @@ __global__ void __launch_bounds__(kThreads, CSFMM_NEAR_MINB) near32x2_kernel(Pla
             }
             sA[t] = make_ulonglong2(f2_pack(x, x), f2_pack(y, y));
             sB[t] = make_ulonglong2(f2_pack(z, z), f2_pack(w, w));
-            part += (double)w;
-          }
-          if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-            if (lane == 0) wsum[warp] = part;
           }
           __syncthreads();
-          f2x hi[NP], lo[NP];
-#pragma unroll
-          for (int q = 0; q < NP; ++q) hi[q] = lo[q] = 0ull;
           int self[NT];
 #pragma unroll
           for (int k = 0; k < NT; ++k) self[k] = (i0 + (int)threadIdx.x + k * kThreads) - (sb + j0);
@@ -639,39 +642,18 @@ __global__ void __launch_bounds__(kThreads, CSFMM_NEAR_MINB) near32x2_kernel(Pla
             tile_sum_x2<KID, NP, true>(sA, sB, nj, tx, ty, tz, self, hi, lo);
           else
             tile_sum_x2<KID, NP, false>(sA, sB, nj, tx, ty, tz, self, hi, lo);
-          double tot = 0.0;
-          if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
-#pragma unroll
-            for (int u = 0; u < kThreads / 32; ++u) tot += wsum[u];
-          }
-#pragma unroll
-          for (int q = 0; q < NP; ++q) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const int k = 2 * q + h;
-              const double a = f2_total(hi[q], lo[q], h);
-              if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
-                double t = tot;
-                if (self_tile && self[k] >= 0 && self[k] < nj) {
-                  float wself, dummy;
-                  f2_unpack(sB[self[k]].y, wself, dummy);
-                  t -= (double)wself;
-                }
-                // -(1/4pi) sum w ln(d2/2) = -(ln2/4pi) (sum w log2 d2 - sum w)
-                out[k] += -(0.69314718055994530942 * kInv4Pi) * (a - t);
-              } else {
-                out[k] += a;
-              }
-            }
-          }
         }
       }
     }
 #pragma unroll
-    for (int k = 0; k < NT; ++k) {
-      const int i = i0 + threadIdx.x + k * kThreads;
-      if (i < e) phi[((int64_t)r0 * v.N + i)] = out[k] + pre[k];
-    }
+    for (int q = 0; q < NP; ++q)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int i = i0 + threadIdx.x + (2 * q + h) * kThreads;
+        double o = f2_total(hi[q], lo[q], h);
+        if constexpr (KID == CSFMM_KERNEL_LAPLACE) o *= -(0.69314718055994530942 * kInv4Pi);
+        if (i < e) phi[((int64_t)r0 * v.N + i)] = o;
+      }
   }
 }
 
@@ -687,13 +669,11 @@ __global__ void __launch_bounds__(kThreads, CSFMM_NEAR_MINB) near32x2_kernel(Pla
 // proxy never coincides with a source (the pair is well separated).
 // ---------------------------------------------------------------------------
 template <int KID>
-__global__ void __launch_bounds__(160) far32x2_kernel(PlanView v, const float *wsf,
+__global__ void __launch_bounds__(160, 8) far32x2_kernel(PlanView v, const float *wsf,
                                                       const float *wbar, int ldr, int r0,
                                                       double *psi) {
   __shared__ ulonglong2 sA[kTile], sB[kTile];
-  __shared__ double wsum[8];
   const int c = blockIdx.x, P = v.P, nth = blockDim.x;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = nth >> 5;
   const int64_t po = (int64_t)c * 3 * P;
   float ox[2], oy[2], oz[2];
 #pragma unroll
@@ -704,7 +684,8 @@ __global__ void __launch_bounds__(160) far32x2_kernel(PlanView v, const float *w
     oy[h] = v.proxy32[po + P + mm];
     oz[h] = v.proxy32[po + 2 * P + mm];
   }
-  double out[2] = {0.0, 0.0};
+  // running totals of the two target proxies over all entries (FP32 pairs)
+  f2x hi[1] = {0ull}, lo[1] = {0ull};
   const double cTx = v.ccentre[3 * c], cTy = v.ccentre[3 * c + 1], cTz = v.ccentre[3 * c + 2];
   const float *wr = wsf + (int64_t)r0 * v.N;
   const int self_none[2] = {-1, -1};
@@ -722,10 +703,10 @@ __global__ void __launch_bounds__(160) far32x2_kernel(PlanView v, const float *w
       const bool cp = type == CSFMM_LIST_CP;
       const int sb = cp ? v.cbegin[s] : 0;
       const int nsrc = cp ? v.cend[s] - sb : P;
+      if constexpr (KID == CSFMM_KERNEL_LAPLACE) fold_minus(hi[0], lo[0], weight_total(v, s, r0, cp ? 0 : 1));
       for (int j0 = 0; j0 < nsrc; j0 += kTile) {
         const int nj = min(kTile, nsrc - j0);
         __syncthreads();
-        double part = 0.0;
         for (int t = threadIdx.x; t < nj; t += nth) {
           float x, y, z, w;
           if (cp) {
@@ -741,33 +722,18 @@ __global__ void __launch_bounds__(160) far32x2_kernel(PlanView v, const float *w
           }
           sA[t] = make_ulonglong2(f2_pack(x, x), f2_pack(y, y));
           sB[t] = make_ulonglong2(f2_pack(z, z), f2_pack(w, w));
-          part += (double)w;
-        }
-        if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-          if (lane == 0) wsum[warp] = part;
         }
         __syncthreads();
-        f2x hi[1] = {0ull}, lo[1] = {0ull};
         tile_sum_x2<KID, 1, false>(sA, sB, nj, tx, ty, tz, self_none, hi, lo);
-        const double a0 = f2_total(hi[0], lo[0], 0), a1 = f2_total(hi[0], lo[0], 1);
-        if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
-          double tot = 0.0;
-          for (int u = 0; u < nwarp; ++u) tot += wsum[u];
-          out[0] += -(0.69314718055994530942 * kInv4Pi) * (a0 - tot);
-          out[1] += -(0.69314718055994530942 * kInv4Pi) * (a1 - tot);
-        } else {
-          out[0] += a0;
-          out[1] += a1;
-        }
       }
     }
   }
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int m = threadIdx.x + h * nth;
-    if (m < P) psi[((int64_t)c * ldr + r0) * P + m] = out[h];
+    double o = f2_total(hi[0], lo[0], h);
+    if constexpr (KID == CSFMM_KERNEL_LAPLACE) o *= -(0.69314718055994530942 * kInv4Pi);
+    if (m < P) psi[((int64_t)c * ldr + r0) * P + m] = o;
   }
 }
 
@@ -779,13 +745,11 @@ __global__ void __launch_bounds__(160) far32_kernel(PlanView v, const float *wsf
   constexpr int NT = 2;
   __shared__ float4 sp[kTile];
   __shared__ float sw[NR * kTile];
-  __shared__ double wsum[NR][8];
   const int c = blockIdx.x, P = v.P, nth = blockDim.x;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = nth >> 5;
   const int64_t po = (int64_t)c * 3 * P;
   float ox[NT], oy[NT], oz[NT];
-  double xa[NT][3];
-  double out[NT][NR][DIM];
+  // running totals over all entries as FP32 (hi, lo) pairs
+  float ahi[NT][NR][3], alo[NT][NR][3];
 #pragma unroll
   for (int h = 0; h < NT; ++h) {
     const int m = threadIdx.x + h * nth;
@@ -793,13 +757,10 @@ __global__ void __launch_bounds__(160) far32_kernel(PlanView v, const float *wsf
     ox[h] = v.proxy32[po + mm];
     oy[h] = v.proxy32[po + P + mm];
     oz[h] = v.proxy32[po + 2 * P + mm];
-    xa[h][0] = v.proxy[po + mm];
-    xa[h][1] = v.proxy[po + P + mm];
-    xa[h][2] = v.proxy[po + 2 * P + mm];
 #pragma unroll
     for (int q = 0; q < NR; ++q)
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) out[h][q][d] = 0.0;
+      for (int d = 0; d < 3; ++d) ahi[h][q][d] = alo[h][q][d] = 0.f;
   }
   const double cTx = v.ccentre[3 * c], cTy = v.ccentre[3 * c + 1], cTz = v.ccentre[3 * c + 2];
   const int self_none[NT] = {-1, -1};
@@ -821,12 +782,17 @@ __global__ void __launch_bounds__(160) far32_kernel(PlanView v, const float *wsf
       const bool cp = type == CSFMM_LIST_CP;
       const int sb = cp ? v.cbegin[s] : 0;
       const int nsrc = cp ? v.cend[s] - sb : P;
+      if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+          const float2 W = weight_total(v, s, r0 + q, cp ? 0 : 1);
+#pragma unroll
+          for (int h = 0; h < NT; ++h) fold_minus(ahi[h][q][0], alo[h][q][0], W);
+        }
+      }
       for (int j0 = 0; j0 < nsrc; j0 += kTile) {
         const int nj = min(kTile, nsrc - j0);
         __syncthreads();
-        double part[NR];
-#pragma unroll
-        for (int q = 0; q < NR; ++q) part[q] = 0.0;
         for (int t = threadIdx.x; t < nj; t += nth) {
           float4 val;
           float wv[NR];
@@ -846,47 +812,9 @@ __global__ void __launch_bounds__(160) far32_kernel(PlanView v, const float *wsf
           sp[t] = val;
 #pragma unroll
           for (int q = 1; q < NR; ++q) sw[q * kTile + t] = wv[q];
-#pragma unroll
-          for (int q = 0; q < NR; ++q) part[q] += (double)wv[q];
-        }
-        if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
-#pragma unroll
-          for (int q = 0; q < NR; ++q) {
-            double x = part[q];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-            if (lane == 0) wsum[q][warp] = x;
-          }
         }
         __syncthreads();
-        float ahi[NT][NR][3], alo[NT][NR][3];
-#pragma unroll
-        for (int h = 0; h < NT; ++h)
-#pragma unroll
-          for (int q = 0; q < NR; ++q)
-#pragma unroll
-            for (int d = 0; d < 3; ++d) ahi[h][q][d] = alo[h][q][d] = 0.f;
         tile_sum<KID, NT, NR, false>(sp, sw, nj, tx, ty, tz, self_none, ahi, alo);
-#pragma unroll
-        for (int h = 0; h < NT; ++h)
-#pragma unroll
-          for (int q = 0; q < NR; ++q) {
-            if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
-              double tot = 0.0;
-              for (int u = 0; u < nwarp; ++u) tot += wsum[q][u];
-              out[h][q][0] += -(0.69314718055994530942 * kInv4Pi) *
-                              (((double)ahi[h][q][0] + (double)alo[h][q][0]) - tot);
-            } else if constexpr (KID == CSFMM_KERNEL_BIOT_SAVART) {
-              const double b0 = (double)ahi[h][q][0] + (double)alo[h][q][0];
-              const double b1 = (double)ahi[h][q][1] + (double)alo[h][q][1];
-              const double b2 = (double)ahi[h][q][2] + (double)alo[h][q][2];
-              out[h][q][0] += kInv2Pi * (xa[h][1] * b2 - xa[h][2] * b1);
-              out[h][q][1] += kInv2Pi * (xa[h][2] * b0 - xa[h][0] * b2);
-              out[h][q][2] += kInv2Pi * (xa[h][0] * b1 - xa[h][1] * b0);
-            } else {
-              out[h][q][0] += (double)ahi[h][q][0] + (double)alo[h][q][0];
-            }
-          }
       }
     }
   }
@@ -894,11 +822,28 @@ __global__ void __launch_bounds__(160) far32_kernel(PlanView v, const float *wsf
   for (int h = 0; h < NT; ++h) {
     const int m = threadIdx.x + h * nth;
     if (m >= P) continue;
+    double xa[3] = {0.0, 0.0, 0.0};
+    if constexpr (KID == CSFMM_KERNEL_BIOT_SAVART) {
+      xa[0] = v.proxy[po + m];
+      xa[1] = v.proxy[po + P + m];
+      xa[2] = v.proxy[po + 2 * P + m];
+    }
 #pragma unroll
-    for (int q = 0; q < NR; ++q)
+    for (int q = 0; q < NR; ++q) {
+      double o[3];
 #pragma unroll
-      for (int d = 0; d < DIM; ++d)
-        psi[(((int64_t)c * ldr + r0 + q) * DIM + d) * P + m] = out[h][q][d];
+      for (int d = 0; d < 3; ++d) o[d] = (double)ahi[h][q][d] + (double)alo[h][q][d];
+      double *dst = psi + ((int64_t)c * ldr + r0 + q) * DIM * P + m;
+      if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
+        dst[0] = -(0.69314718055994530942 * kInv4Pi) * o[0];
+      } else if constexpr (KID == CSFMM_KERNEL_BIOT_SAVART) {
+        dst[0] = kInv2Pi * (xa[1] * o[2] - xa[2] * o[1]);
+        dst[P] = kInv2Pi * (xa[2] * o[0] - xa[0] * o[2]);
+        dst[2 * P] = kInv2Pi * (xa[0] * o[1] - xa[1] * o[0]);
+      } else {
+        dst[0] = o[0];
+      }
+    }
   }
 }
 
@@ -1004,10 +949,8 @@ __global__ void __launch_bounds__(CSFMM_MULTI_THREADS) multi32_kernel(
   static_assert(CSFMM_MULTI_THREADS % 32 == 0 && CSFMM_MULTI_THREADS <= 1024, "block size");
   __shared__ float4 sp[kTile];
   __shared__ ulonglong2 sw4[(NR / 4) * kTile];
-  __shared__ double wsum[NR][CSFMM_MULTI_THREADS / 32];
   const int c = FAR ? (int)blockIdx.x : leaves[blockIdx.x];
   const int P = v.P, nth = blockDim.x;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = nth >> 5;
   const int tb = FAR ? 0 : v.cbegin[c];
   const int te = FAR ? P : v.cend[c];
   const double cTx = v.ccentre[3 * c], cTy = v.ccentre[3 * c + 1], cTz = v.ccentre[3 * c + 2];
@@ -1015,6 +958,9 @@ __global__ void __launch_bounds__(CSFMM_MULTI_THREADS) multi32_kernel(
   float *swf = reinterpret_cast<float *>(sw4);
   for (int i0 = tb; i0 < te; i0 += nth * NT) {
     float ox[NT], oy[NT], oz[NT];
+    // running totals over all list entries, FP32 (hi, lo) pairs per pair of
+    // right-hand sides; the log kernel holds sum w (log2 d2 - 1)
+    f2x hi[NT][NR / 2], lo[NT][NR / 2];
 #pragma unroll
     for (int k = 0; k < NT; ++k) {
       const int i = i0 + threadIdx.x + k * nth;
@@ -1025,13 +971,8 @@ __global__ void __launch_bounds__(CSFMM_MULTI_THREADS) multi32_kernel(
         const float4 o = v.off32[ii];
         ox[k] = o.x; oy[k] = o.y; oz[k] = o.z;
       }
-      if (i < te) {
 #pragma unroll
-        for (int q = 0; q < NR; ++q) {
-          if (FAR) psi[((int64_t)c * ldr + r0 + q) * P + i] = 0.0;
-          else phi[(int64_t)(r0 + q) * v.N + i] = 0.0;
-        }
-      }
+      for (int q = 0; q < NR / 2; ++q) hi[k][q] = lo[k][q] = 0ull;
     }
     for (int pass = 0; pass < 2; ++pass) {
       const int type = FAR ? (pass == 0 ? CSFMM_LIST_CP : CSFMM_LIST_CC)
@@ -1053,12 +994,27 @@ __global__ void __launch_bounds__(CSFMM_MULTI_THREADS) multi32_kernel(
         const int sb = particles ? v.cbegin[s] : 0;
         const int nsrc = particles ? v.cend[s] - sb : P;
         const bool self_tile = !FAR && type == CSFMM_LIST_PP && s == c;
+        if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
+          // -(1/4pi) sum w ln(d2/2) = -(ln2/4pi) (sum w log2 d2 - sum w); the
+          // target's own weight is not part of the sum over the self leaf
+#pragma unroll
+          for (int q = 0; q < NR / 2; ++q) {
+            const float2 W0 = weight_total(v, s, r0 + 2 * q, particles ? 0 : 1);
+            const float2 W1 = weight_total(v, s, r0 + 2 * q + 1, particles ? 0 : 1);
+#pragma unroll
+            for (int k = 0; k < NT; ++k) {
+              two_sum_fold(hi[k][q], lo[k][q], f2_pack(-W0.x, -W1.x));
+              lo[k][q] = f2_add(lo[k][q], f2_pack(-W0.y, -W1.y));
+              const int i = i0 + threadIdx.x + k * nth;
+              if (self_tile && i < te)
+                two_sum_fold(hi[k][q], lo[k][q], f2_pack(wsf[(int64_t)(r0 + 2 * q) * v.N + i],
+                                                         wsf[(int64_t)(r0 + 2 * q + 1) * v.N + i]));
+            }
+          }
+        }
         for (int j0 = 0; j0 < nsrc; j0 += kTile) {
           const int nj = min(kTile, nsrc - j0);
           __syncthreads();
-          double part[NR];
-#pragma unroll
-          for (int q = 0; q < NR; ++q) part[q] = 0.0;
           for (int t = threadIdx.x; t < nj; t += nth) {
             float wv[NR];
             if (particles) {
@@ -1077,24 +1033,8 @@ __global__ void __launch_bounds__(CSFMM_MULTI_THREADS) multi32_kernel(
             for (int q = 0; q < NR / 4; ++q)
               reinterpret_cast<float4 *>(swf)[t * (NR / 4) + q] =
                   make_float4(wv[4 * q], wv[4 * q + 1], wv[4 * q + 2], wv[4 * q + 3]);
-#pragma unroll
-            for (int q = 0; q < NR; ++q) part[q] += (double)wv[q];
-          }
-          if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
-#pragma unroll
-            for (int q = 0; q < NR; ++q) {
-              double x = part[q];
-#pragma unroll
-              for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-              if (lane == 0) wsum[q][warp] = x;
-            }
           }
           __syncthreads();
-          f2x hi[NT][NR / 2], lo[NT][NR / 2];
-#pragma unroll
-          for (int k = 0; k < NT; ++k)
-#pragma unroll
-            for (int q = 0; q < NR / 2; ++q) hi[k][q] = lo[k][q] = 0ull;
           int self[NT];
 #pragma unroll
           for (int k = 0; k < NT; ++k) self[k] = (i0 + (int)threadIdx.x + k * nth) - (sb + j0);
@@ -1102,29 +1042,23 @@ __global__ void __launch_bounds__(CSFMM_MULTI_THREADS) multi32_kernel(
             tile_sum_multi<KID, NT, NR, true>(sp, sw4, nj, tx, ty, tz, self, hi, lo);
           else
             tile_sum_multi<KID, NT, NR, false>(sp, sw4, nj, tx, ty, tz, self, hi, lo);
-#pragma unroll
-          for (int k = 0; k < NT; ++k) {
-            const int i = i0 + threadIdx.x + k * nth;
-            if (i >= te) continue;
-#pragma unroll
-            for (int q = 0; q < NR / 2; ++q) {
-#pragma unroll
-              for (int h = 0; h < 2; ++h) {
-                const int qq = 2 * q + h;
-                double val = f2_total(hi[k][q], lo[k][q], h);
-                if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
-                  double tot = 0.0;
-                  for (int u = 0; u < nwarp; ++u) tot += wsum[qq][u];
-                  if (self_tile && self[k] >= 0 && self[k] < nj) tot -= (double)swf[self[k] * NR + qq];
-                  val = -(0.69314718055994530942 * kInv4Pi) * (val - tot);
-                }
-                if (FAR) psi[((int64_t)c * ldr + r0 + qq) * P + i] += val;
-                else phi[(int64_t)(r0 + qq) * v.N + i] += val;
-              }
-            }
-          }
         }
       }
+    }
+#pragma unroll
+    for (int k = 0; k < NT; ++k) {
+      const int i = i0 + threadIdx.x + k * nth;
+      if (i >= te) continue;
+#pragma unroll
+      for (int q = 0; q < NR / 2; ++q)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int qq = 2 * q + h;
+          double val = f2_total(hi[k][q], lo[k][q], h);
+          if constexpr (KID == CSFMM_KERNEL_LAPLACE) val *= -(0.69314718055994530942 * kInv4Pi);
+          if (FAR) psi[((int64_t)c * ldr + r0 + qq) * P + i] = val;
+          else phi[(int64_t)(r0 + qq) * v.N + i] = val;
+        }
     }
   }
 }

@@ -83,7 +83,8 @@ extern "C" csfmm_status csfmm_evaluate_static(csfmm_plan plan, const double *wei
   const size_t b_psi = round256(nc * R * dim * P * sizeof(double));
   const size_t b_phi = round256(R * N * dim * sizeof(double));
   const size_t b_wsf = pl.precision == CSFMM_FP64 ? 0 : round256(R * N * sizeof(float));
-  const size_t need = b_ws + b_wbar + b_psi + b_phi + b_wsf;
+  const size_t b_wtot = pl.precision == CSFMM_FP64 ? 0 : round256(nc * R * 2 * sizeof(float2));
+  const size_t need = b_ws + b_wbar + b_psi + b_phi + b_wsf + b_wtot;
   if (need > (size_t)CSFMM_STATIC_SCRATCH_BYTES) {
     set_error("this evaluation needs %zu bytes of scratch; the static scratch holds %zu bytes "
               "(use csfmm_evaluate, or fewer right-hand sides)",
@@ -105,5 +106,6 @@ extern "C" csfmm_status csfmm_evaluate_static(csfmm_plan plan, const double *wei
   W.psi = reinterpret_cast<double *>(base + b_ws + b_wbar);
   W.phi = reinterpret_cast<double *>(base + b_ws + b_wbar + b_psi);
   if (b_wsf) W.wsf = reinterpret_cast<float *>(base + b_ws + b_wbar + b_psi + b_phi);
+  if (b_wtot) W.wtot = reinterpret_cast<float2 *>(base + b_ws + b_wbar + b_psi + b_phi + b_wsf);
   return evaluate_impl(pl, W, weights, nrhs, out, (cudaStream_t)stream);
 }

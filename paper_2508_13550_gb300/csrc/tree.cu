@@ -818,6 +818,7 @@ PlanView Plan::view() const {
   for (int t = 0; t < 4; ++t) { v.loff[t] = loff[t]; v.lsrc[t] = lsrc[t]; }
   v.sym_contrib = sym_contrib;
   v.m2m64 = m2m64; v.m2m32 = m2m32; v.cheb = cheb; v.status = status;
+  v.wtot = nullptr; v.wtot_ld = 0;
   return v;
 }
 
