@@ -80,6 +80,9 @@ def _load():
         lib.oracle_fmm_evaluate_targets.argtypes = [vp, ctypes.c_int, P(d), ctypes.c_int,
                                                     P(i64), i64, P(d)]
         lib.oracle_fmm_upward.argtypes = [vp, P(d), ctypes.c_int, P(d)]
+        lib.oracle_cstc_evaluate.argtypes = [vp, ctypes.c_int, P(d), ctypes.c_int, P(i64), i64,
+                                             P(d), P(i64), P(d)]
+        lib.oracle_cstc_evaluate.restype = ctypes.c_int
         lib.oracle_fmm_local.argtypes = [vp, P(d), P(d), P(i32)]
         lib.oracle_cheb_nodes.argtypes = [ctypes.c_int, P(d)]
         lib.oracle_lagrange.argtypes = [ctypes.c_int, P(d), d, P(d)]
@@ -258,6 +261,30 @@ class FMM:
         rc = self._lib.oracle_fmm_evaluate(self._h, kernel, _ptr(w), nrhs, _ptr(out))
         if rc != 0:
             raise ValueError("oracle_fmm_evaluate: invalid arguments")
+        return out
+
+    def evaluate_cstc(self, kernel: int, w, targets=None, with_stats=False):
+        """Cubed sphere tree code (Algorithm "CSTC") on the same tree, degree
+        and MAC: potentials [nrhs, N or len(targets), dim] in input order.
+        With with_stats, also {"pc", "pp", "evals", "margin"}: interaction
+        counts and kernel evaluations over the targets, and the smallest
+        relative distance of a separation test from its threshold."""
+        w = _weights(w, self.N)
+        nrhs = w.shape[0]
+        tg = None if targets is None else np.ascontiguousarray(np.asarray(targets, dtype=np.int64))
+        nt = self.N if tg is None else len(tg)
+        out = np.zeros((nrhs, nt, kernel_dim(kernel)))
+        st = np.zeros(3, dtype=np.int64)
+        m = ctypes.c_double(0.0)
+        rc = self._lib.oracle_cstc_evaluate(
+            self._h, kernel, _ptr(w), nrhs,
+            None if tg is None else _ptr(tg, ctypes.c_int64), nt, _ptr(out),
+            _ptr(st, ctypes.c_int64), ctypes.byref(m))
+        if rc != 0:
+            raise ValueError("oracle_cstc_evaluate: invalid arguments")
+        if with_stats:
+            return out, {"pc": int(st[0]), "pp": int(st[1]), "evals": int(st[2]),
+                         "margin": m.value}
         return out
 
 

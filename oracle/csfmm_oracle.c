@@ -17,6 +17,8 @@
  *     CP, CC), the upward pass (Sec. 6, Eq. upwardpass2), the dual tree
  *     traversal (Sec. 8, Algorithm "CSFMM") and the downward pass (Sec. 8.1,
  *     Eq. downward_2),
+ *   - the cubed sphere tree code (CSTC, Sec. 7, Algorithm "CSTC") on the
+ *     same tree, proxies and upward pass,
  * all in double precision, written for clarity rather than speed (OpenMP over
  * independent targets only).
  *
@@ -33,6 +35,10 @@
  *     at least one cluster is big, the shallower cluster is split (equal
  *     levels: the target), and if that one is a leaf the other one is split.
  *   - If the evaluation point equals a Chebyshev node exactly, L_k = delta.
+ *   - CSTC: x_i and C_s are well separated iff r_s < MAC * R, R the chord from
+ *     x_i to the centre of C_s; "|C_s| > N0" means C_s has children; a leaf
+ *     that is not well separated interacts directly (it has no children to
+ *     pass x_i to).
  *
  * Conventions (agreed with the CUDA library, implemented independently):
  *   - face f = 2*axis + (component < 0), axis = argmax |x_axis| (ties: lowest
@@ -848,6 +854,114 @@ int oracle_fmm_evaluate_targets(void *h, int kid, const double *w, int nrhs,
   oplan *pl = (oplan *)h;
   if (!pl || !kernel_valid(kid) || nrhs < 1 || !w || !out || !tgt || ntgt < 0) return 1;
   return fmm_evaluate(pl, kid, w, nrhs, tgt, ntgt, out);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Cubed sphere tree code (Sec. 7, Algorithm "CSTC").  Each target particle  */
+/* x_i walks the source tree from the six root cells.  A cluster C_s that is */
+/* well separated from x_i (r_s < MAC R, R = |x_i - c_s|) contributes through */
+/* its proxies by Eq. (PC) if it has more than N0 particles (it has           */
+/* children) and directly by Eq. (PP) otherwise; a cluster that is not well  */
+/* separated passes x_i on to its children, and a leaf that is not well      */
+/* separated contributes directly.  The proxy weights come from the same     */
+/* upward pass as the CSFMM (Sec. 6).                                        */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  const oplan *pl;
+  int kid, nrhs, dim;
+  const double *ws, *wbar;
+  int64_t i;          /* target, sorted position */
+  ksum *acc;          /* [nrhs][dim] */
+  int64_t npc, npp, evals;
+  double margin;
+} cstc_walk;
+
+static void cstc_visit(cstc_walk *X, int c) {
+  const oplan *pl = X->pl;
+  const ocell *C = &pl->cells[c];
+  const double *x = pl->x + 3 * X->i;
+  const int P = pl->P, nrhs = X->nrhs, dim = X->dim;
+  const int64_t N = pl->N;
+  double R = chord(x, C->c);
+  double rhs = pl->theta * R;
+  int sep = (g_mutation == 11) ? (C->r > rhs) : (C->r < rhs);
+  if (R > 0.0) {
+    double m = fabs(C->r - rhs) / rhs;
+    if (m < X->margin) X->margin = m;
+  }
+  double k[3];
+  if (sep && C->nchild > 0) {
+    /* PC: x_i against the proxies of C_s with their proxy weights */
+    for (int q = 0; q < P; ++q) {
+      kernel_eval(X->kid, x, pl->proxy + 3 * ((int64_t)c * P + q), k);
+      for (int r = 0; r < nrhs; ++r) {
+        double wq = X->wbar[((int64_t)c * nrhs + r) * P + q];
+        for (int d = 0; d < dim; ++d) ksum_add(&X->acc[r * dim + d], k[d] * wq);
+      }
+    }
+    X->npc++;
+    X->evals += P;
+  } else if (sep || C->nchild == 0) {
+    if (!sep && g_mutation == 12) return;
+    /* PP: x_i against the particles of C_s, j = i omitted */
+    for (int64_t j = C->begin; j < C->end; ++j) {
+      if (j == X->i) continue;
+      kernel_eval(X->kid, x, pl->x + 3 * j, k);
+      for (int r = 0; r < nrhs; ++r) {
+        double wj = X->ws[(int64_t)r * N + j];
+        for (int d = 0; d < dim; ++d) ksum_add(&X->acc[r * dim + d], k[d] * wj);
+      }
+      X->evals++;
+    }
+    X->npp++;
+  } else {
+    for (int q = 0; q < 4; ++q)
+      if (C->child[q] >= 0) cstc_visit(X, (g_mutation == 13 && q == 3) ? C->child[0] : C->child[q]);
+  }
+}
+
+/* CSTC potentials out[r][t][dim] of the input indices tgt[t] (every point if
+ * tgt == NULL); stats (optional) = {PC interactions, PP interactions, kernel
+ * evaluations} summed over the targets, and *margin the smallest
+ * |r_s - MAC R| / (MAC R) over all separation tests. */
+int oracle_cstc_evaluate(void *h, int kid, const double *w, int nrhs, const int64_t *tgt,
+                         int64_t ntgt, double *out, int64_t *stats, double *margin) {
+  oplan *pl = (oplan *)h;
+  if (!pl || !kernel_valid(kid) || nrhs < 1 || nrhs > 64 || !w || !out || (tgt && ntgt < 0))
+    return 1;
+  const int64_t N = pl->N;
+  const int dim = oracle_kernel_dim(kid), P = pl->P;
+  if (!tgt) ntgt = N;
+  int64_t *inv = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
+  for (int64_t i = 0; i < N; ++i) inv[pl->order[i]] = i;
+  for (int64_t t = 0; tgt && t < ntgt; ++t)
+    if (tgt[t] < 0 || tgt[t] >= N) { free(inv); return 1; }
+  double *ws = (double *)malloc(sizeof(double) * (size_t)N * (size_t)nrhs);
+  for (int r = 0; r < nrhs; ++r)
+    for (int64_t i = 0; i < N; ++i) ws[(int64_t)r * N + i] = w[(int64_t)r * N + pl->order[i]];
+  double *wbar = (double *)malloc(sizeof(double) * (size_t)pl->ncells * (size_t)nrhs * (size_t)P);
+  upward_pass(pl, ws, nrhs, wbar);
+  int64_t tot_pc = 0, tot_pp = 0, tot_ev = 0;
+  double mg = INFINITY;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : tot_pc, tot_pp, tot_ev) reduction(min : mg)
+  for (int64_t t = 0; t < ntgt; ++t) {
+    ksum acc[64 * 3];
+    for (int u = 0; u < nrhs * dim; ++u) { acc[u].s = 0.0; acc[u].c = 0.0; }
+    const int64_t in = tgt ? tgt[t] : t;
+    cstc_walk X = {pl, kid, nrhs, dim, ws, wbar, inv[in], acc, 0, 0, 0, INFINITY};
+    for (int c = pl->level_begin[0]; c < pl->level_begin[1]; ++c) cstc_visit(&X, c);
+    for (int r = 0; r < nrhs; ++r)
+      for (int d = 0; d < dim; ++d)
+        out[((int64_t)r * ntgt + t) * dim + d] = acc[r * dim + d].s + acc[r * dim + d].c;
+    tot_pc += X.npc;
+    tot_pp += X.npp;
+    tot_ev += X.evals;
+    if (X.margin < mg) mg = X.margin;
+  }
+  if (stats) { stats[0] = tot_pc; stats[1] = tot_pp; stats[2] = tot_ev; }
+  if (margin) *margin = mg;
+  free(ws); free(wbar); free(inv);
+  return 0;
 }
 
 /* Proxy weights of every cell after the upward pass, [ncells][nrhs][P],

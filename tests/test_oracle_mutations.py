@@ -71,8 +71,24 @@ def _pin_moments():
     return True
 
 
+def _pin_cstc_constant_kernel():
+    pts = I.random_sphere_points(2000, 5)
+    w = np.random.default_rng(6).standard_normal(2000)
+    out = O.FMM(pts, 3, 0.7, 12).evaluate_cstc(O.KERNEL_ONE, w)[0, :, 0]
+    return np.max(np.abs(out - (w.sum() - w))) < 1e-12
+
+
+def _pin_cstc_high_degree_vs_direct():
+    pts, A = I.cubed_sphere_grid(8)
+    w = I.real_sph_harm(4, 3, pts) * A
+    ds = O.direct(pts, O.KERNEL_LAPLACE, w)[0, :, 0]
+    cs = O.FMM(pts, 14, 0.5, 16).evaluate_cstc(O.KERNEL_LAPLACE, w)[0, :, 0]
+    return O.rel_l2(cs, ds, A) < 1e-11
+
+
 PINS = [_pin_constant_kernel, _pin_high_degree_vs_direct, _pin_funk_hecke,
-        _pin_coverage, _pin_lagrange, _pin_moments]
+        _pin_coverage, _pin_lagrange, _pin_moments, _pin_cstc_constant_kernel,
+        _pin_cstc_high_degree_vs_direct]
 
 MUTATIONS = {
     1: "PC term dropped",
@@ -85,6 +101,9 @@ MUTATIONS = {
     8: "barycentric end weights not halved",
     9: "deepest L2L level skipped",
     10: "P2M reads weights by input index instead of sorted position",
+    11: "CSTC separation test reversed",
+    12: "CSTC drops a leaf that is not well separated",
+    13: "CSTC visits the first child twice instead of the fourth",
 }
 
 
