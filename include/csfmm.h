@@ -138,6 +138,20 @@ csfmm_status csfmm_plan_create(const double *points, int64_t N, int kernel_id, i
 csfmm_status csfmm_evaluate(csfmm_plan plan, const double *weights, int nrhs, double *out,
                             void *stream);
 
+/* Evaluates phi with the cubed sphere tree code instead (Sec. 7, Algorithm
+ * "CSTC") on the plan's tree, degree, MAC and precision form: the upward pass
+ * (P2M, M2M), then every target particle x_i walks the source tree from the
+ * root cells; a cluster C_s with r_s < MAC |x_i - c_s| contributes through
+ * its proxies (Eq. PC) if it has children and directly (Eq. PP) otherwise,
+ * one that is not well separated passes x_i to its children, and a leaf that
+ * is not well separated contributes directly.  O(N log N) work against the
+ * CSFMM's O(N); same arguments, layout and asynchrony as csfmm_evaluate, and
+ * the same rule against overlapping calls on one plan.
+ * Errors: INVALID_ARG, UNSUPPORTED (a tree of more than 18 levels), CUDA,
+ * DEVICE. */
+csfmm_status csfmm_evaluate_cstc(csfmm_plan plan, const double *weights, int nrhs, double *out,
+                                 void *stream);
+
 /* Same as csfmm_evaluate with HOST weights and output: copies the weights
  * to the device, evaluates, copies phi back and synchronises the stream.
  * Pinned host memory makes the copies asynchronous DMA.

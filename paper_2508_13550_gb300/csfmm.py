@@ -8,6 +8,7 @@ library cannot be loaded, every call raises.
     plan = plan_create(points, kernel_id, degree, theta, max_leaf, precision=FP64)
     out  = evaluate(plan, weights)            # weights [nrhs, N] -> [nrhs, N, dim]
     out  = evaluate_host(plan, weights_np)    # host numpy in/out (copies inside)
+    out  = evaluate_cstc(plan, weights)       # tree code on the same tree
     out  = direct(points, kernel_id, weights, precision=FP64)
     plan_stats(plan), plan_export_cells(plan), plan_export_list(plan, type), ...
     plan_destroy(plan)
@@ -110,6 +111,7 @@ _SIGS = {
     "csfmm_plan_create": [_VP, _I64, ctypes.c_int, ctypes.c_int, _D, ctypes.c_int,
                           ctypes.POINTER(Options), _VP, ctypes.POINTER(_VP)],
     "csfmm_evaluate": [_VP, _VP, ctypes.c_int, _VP, _VP],
+    "csfmm_evaluate_cstc": [_VP, _VP, ctypes.c_int, _VP, _VP],
     "csfmm_evaluate_host": [_VP, _VP, ctypes.c_int, _VP, _VP],
     "csfmm_evaluate_static": [_VP, _VP, ctypes.c_int, _VP, _VP],
     "csfmm_workspace_create": [_VP, ctypes.c_int, ctypes.POINTER(_VP)],
@@ -237,6 +239,19 @@ def evaluate(plan: Plan, weights, out=None, stream=None):
         out = torch.empty((nrhs, plan.N, plan.dim), dtype=torch.float64, device=w.device)
     _check(load().csfmm_evaluate(plan.handle, _dev(w, torch.float64), nrhs,
                                  _dev(out, torch.float64), _stream(stream)))
+    return out
+
+
+def evaluate_cstc(plan: Plan, weights, out=None, stream=None):
+    """csfmm_evaluate_cstc: the cubed sphere tree code (Algorithm "CSTC") on the
+    plan's tree, degree, MAC and precision form; [nrhs, N] -> [nrhs, N, dim]."""
+    import torch
+    w = weights if weights.dim() == 2 else weights.unsqueeze(0)
+    nrhs = w.shape[0]
+    if out is None:
+        out = torch.empty((nrhs, plan.N, plan.dim), dtype=torch.float64, device=w.device)
+    _check(load().csfmm_evaluate_cstc(plan.handle, _dev(w, torch.float64), nrhs,
+                                      _dev(out, torch.float64), _stream(stream)))
     return out
 
 

@@ -210,6 +210,21 @@ csfmm_status csfmm_evaluate(csfmm_plan plan, const double *weights, int nrhs, do
   return evaluate_chunks(plan->impl, *plan->impl.ws, weights, nrhs, out, (cudaStream_t)stream);
 }
 
+csfmm_status csfmm_evaluate_cstc(csfmm_plan plan, const double *weights, int nrhs, double *out,
+                                 void *stream) {
+  csfmm_status s = check_eval_args(plan, weights, nrhs, out);
+  if (s != CSFMM_OK) return s;
+  Plan &pl = plan->impl;
+  Workspace &W = *pl.ws;
+  for (int r0 = 0; r0 < nrhs; r0 += W.max_nrhs) {
+    const int nr = nrhs - r0 < W.max_nrhs ? nrhs - r0 : W.max_nrhs;
+    s = cstc_impl(pl, W, weights + (size_t)r0 * pl.N, nr, out + (size_t)r0 * pl.N * pl.dim,
+                  (cudaStream_t)stream);
+    if (s != CSFMM_OK) return s;
+  }
+  return CSFMM_OK;
+}
+
 csfmm_status csfmm_evaluate_host(csfmm_plan plan, const double *weights, int nrhs, double *out,
                                  void *stream) {
   if (!plan || !weights || !out || nrhs < 1) {

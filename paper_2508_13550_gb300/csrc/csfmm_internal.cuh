@@ -224,6 +224,13 @@ csfmm_status build_tree(Plan &pl, const double *points, cudaStream_t st);
 csfmm_status evaluate_impl(Plan &pl, Workspace &ws, const double *w, int nrhs, double *out,
                            cudaStream_t st);
 csfmm_status workspace_alloc(Plan &pl, Workspace &ws, int max_nrhs);
+// Tree code (Algorithm "CSTC") on the plan's tree: upward pass, then one
+// tree walk per target (evaluate.cu, cstc.cu).
+csfmm_status cstc_impl(Plan &pl, Workspace &ws, const double *w, int nrhs, double *out,
+                       cudaStream_t st);
+void launch_cstc(const PlanView &v, bool f32, double theta, int nroots, int nrhs, int ldr,
+                 const double *ws, const float *wsf, const double *wbar, const float *wbar32,
+                 double *out, cudaStream_t st);
 // FP32-bulk near (far = false) or far (far = true) field for nr = 8 or 16
 // right-hand sides from r0, scalar kernels only (interact32.cu).
 void launch_multi32(const PlanView &v, bool far, int ngrid, const int32_t *leaves,

@@ -959,6 +959,62 @@ csfmm_status run_passes(Plan &pl, Workspace &W, const double *w, int nrhs, doubl
   return CSFMM_OK;
 }
 
+// Tree code (Algorithm "CSTC"): gather, the upward pass (P2M, M2M) of the
+// plan's precision form, then the per-target walks of cstc.cu.
+template <int KID, typename Real>
+csfmm_status run_cstc(Plan &pl, Workspace &W, const double *w, int nrhs, double *out,
+                      cudaStream_t st) {
+  PlanView v = pl.view();
+  const int N = (int)pl.N, P = pl.P;
+  const int ldr = W.max_nrhs;
+  Real *wbar;
+  if constexpr (sizeof(Real) == 4) wbar = W.wbar32; else wbar = W.wbar;
+  float2 *wtot = (sizeof(Real) == 4 && KID == CSFMM_KERNEL_LAPLACE) ? W.wtot : nullptr;
+  v.wtot = wtot;
+  v.wtot_ld = ldr;
+  gather_kernel<<<grid_for((int64_t)N * nrhs, 256, 152 * 32), 256, 0, st>>>(
+      pl.perm, w, W.ws, sizeof(Real) == 4 ? W.wsf : nullptr, N, nrhs, N);
+  const int tb_prox = ((P + 31) / 32) * 32;
+  const int tb_p2m = tb_prox < 64 ? 64 : tb_prox;
+  for (int r0 = 0; r0 < nrhs; r0 += kRB) {
+    const int nr = min(kRB, nrhs - r0);
+    switch (nr) {
+      case 1: p2m_kernel<Real, 1><<<pl.nleaves, tb_p2m, 0, st>>>(v, pl.leaves, W.ws, N, r0, wbar, ldr, wtot); break;
+      case 2: p2m_kernel<Real, 2><<<pl.nleaves, tb_p2m, 0, st>>>(v, pl.leaves, W.ws, N, r0, wbar, ldr, wtot); break;
+      case 3: p2m_kernel<Real, 3><<<pl.nleaves, tb_p2m, 0, st>>>(v, pl.leaves, W.ws, N, r0, wbar, ldr, wtot); break;
+      default: p2m_kernel<Real, 4><<<pl.nleaves, tb_p2m, 0, st>>>(v, pl.leaves, W.ws, N, r0, wbar, ldr, wtot); break;
+    }
+  }
+  for (int l = pl.nlevels - 2; l >= 0; --l) {
+    const int c0 = pl.level_begin[l], nlev = pl.level_begin[l + 1] - c0;
+    if constexpr (sizeof(Real) == 4)
+      m2m_df_kernel<<<nlev, 128, 0, st>>>(v, c0, 0, nrhs, wbar, ldr, wtot);
+    else
+      m2m_kernel<Real><<<nlev, 128, 0, st>>>(v, c0, 0, nrhs, wbar, ldr);
+  }
+  if constexpr (sizeof(Real) == 4)
+    launch_cstc(v, true, pl.theta, pl.level_begin[1], nrhs, ldr, W.ws, W.wsf, nullptr, W.wbar32,
+                out, st);
+  else
+    launch_cstc(v, false, pl.theta, pl.level_begin[1], nrhs, ldr, W.ws, nullptr, W.wbar, nullptr,
+                out, st);
+  CSFMM_CUDA(cudaGetLastError());
+  return CSFMM_OK;
+}
+
+template <typename Real>
+csfmm_status dispatch_cstc(Plan &pl, Workspace &W, const double *w, int nrhs, double *out,
+                           cudaStream_t st) {
+  switch (pl.kernel_id) {
+    case CSFMM_KERNEL_LAPLACE: return run_cstc<CSFMM_KERNEL_LAPLACE, Real>(pl, W, w, nrhs, out, st);
+    case CSFMM_KERNEL_BIOT_SAVART: return run_cstc<CSFMM_KERNEL_BIOT_SAVART, Real>(pl, W, w, nrhs, out, st);
+    case CSFMM_KERNEL_NEWTON: return run_cstc<CSFMM_KERNEL_NEWTON, Real>(pl, W, w, nrhs, out, st);
+    case CSFMM_KERNEL_ONE: return run_cstc<CSFMM_KERNEL_ONE, Real>(pl, W, w, nrhs, out, st);
+  }
+  set_error("unknown kernel id %d", pl.kernel_id);
+  return CSFMM_ERR_INVALID_ARG;
+}
+
 template <typename Real>
 csfmm_status dispatch_kernel(Plan &pl, Workspace &W, const double *w, int nrhs, double *out,
                              cudaStream_t st) {
@@ -1104,6 +1160,20 @@ csfmm_status retarget(Plan &pl, Workspace &W, GraphEntry &g, const double *w, do
 // Evaluates nrhs <= W.max_nrhs right-hand sides.  With use_graphs (and no
 // phase timing, on a stream other than the legacy default stream) the launch
 // sequence is captured once per right-hand-side count and replayed.
+csfmm_status cstc_impl(Plan &pl, Workspace &W, const double *w, int nrhs, double *out,
+                       cudaStream_t st) {
+  if (nrhs > W.max_nrhs) {
+    set_error("nrhs %d exceeds the workspace capacity %d", nrhs, W.max_nrhs);
+    return CSFMM_ERR_INVALID_ARG;
+  }
+  if (pl.nlevels > 18) {
+    set_error("the tree code walks trees of at most 18 levels (this plan has %d)", pl.nlevels);
+    return CSFMM_ERR_UNSUPPORTED;
+  }
+  if (pl.precision == CSFMM_FP64) return dispatch_cstc<double>(pl, W, w, nrhs, out, st);
+  return dispatch_cstc<float>(pl, W, w, nrhs, out, st);
+}
+
 csfmm_status evaluate_impl(Plan &pl, Workspace &W, const double *w, int nrhs, double *out,
                            cudaStream_t st) {
   if (nrhs > W.max_nrhs) {
