@@ -53,23 +53,27 @@ def log(*a):
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the FP32
 # interaction kernels per kernel evaluation, from one ncu capture of the
 # 6 x 512^2 Newtonian case (profiles/pp_sym_newton_1.5m.md and
-# profiles/near32x2_far32x2_newton_1.5m.md), valid for the kernel source with
-# the given SHA-256 prefix only; the bench scales it to a launch by the
+# profiles/near32x2_far32x2_newton_1.5m.md), valid only while the kernel
+# sources (interact32.cu, fp32_math.cuh) hash to the given SHA-256 prefix; the bench scales it to a launch by the
 # evaluations the launch performs (the traffic of these kernels grows with the
 # number of leaf pairs and points, as the evaluations do).
-KERNEL_SOURCE = os.path.join(ROOT, "paper_2508_13550_gb300", "csrc", "interact32.cu")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2508_13550_gb300", "csrc", f)
+                  for f in ("interact32.cu", "fp32_math.cuh")]
 TRAFFIC_PER_EVAL = {
-    "source_sha256": "cb77dd55f3529230",
-    "pp_sym_kernel": (34.968832e6 + 129.568768e6) / 6083051520,
-    "near32x2_kernel": (233.240576e6 + 12.256256e6) / 3743870976,
-    "far32x2_kernel": 18.471424e6 / 1503908016,
+    "source_sha256": "7ddfdbcc98e51cdf",
+    "pp_sym_kernel": (35.019008e6 + 129.817856e6) / 6083051520,
+    "near32x2_kernel": (233.308416e6 + 12.380160e6) / 3743870976,
+    "far32x2_kernel": 18.471680e6 / 1503908016,
 }
 
 
 def traffic_per_launch(kernel, evals):
     import hashlib
-    with open(KERNEL_SOURCE, "rb") as f:
-        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for path in KERNEL_SOURCES:
+        with open(path, "rb") as f:
+            h.update(f.read())
+    sha = h.hexdigest()[:16]
     if sha != TRAFFIC_PER_EVAL["source_sha256"] or kernel not in TRAFFIC_PER_EVAL:
         return None
     return TRAFFIC_PER_EVAL[kernel] * evals
@@ -560,6 +564,69 @@ def run_accuracy_sweep(args):
                        "err_samples": args.err_samples}, "rows": rows}
 
 
+def run_cstc_vs_fmm(args):
+    """Runtime of the tree code against the CSFMM and the direct sum on the
+    GPU (the paper's serial runtime comparison: Laplace kernel, MAC 0.7,
+    degree 6): Poisson Y43 field on 6 x m^2 cubed-sphere points, N0 = 4 n^2.
+    Each fast sum is timed with CUDA events after a warm-up evaluation; the
+    FP32 direct sum covers all N^2 pairs, the FP64 direct sum a sample of
+    targets scaled to N.  Errors are against the FP64 direct sum on sampled
+    targets."""
+    import torch
+    from paper_2508_13550_gb300 import csfmm as Cs
+    from paper_2508_13550_gb300 import inputs as I
+    m, n, theta = args.sweep_m, 6, 0.7
+    pts, A, w, _ = I.workload_poisson_y43(m)
+    N = len(pts)
+    dp = torch.from_numpy(pts).cuda()
+    dw = torch.from_numpy(w).cuda()
+    rng = np.random.default_rng(20250813)
+    tg = torch.from_numpy(np.sort(rng.choice(N, args.err_samples, replace=False))
+                          .astype(np.int64)).cuda()
+
+    def timed(fn, reps=1):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, out
+
+    ms_ds64_sample, ds = timed(lambda: Cs.direct(dp, Cs.KERNEL_LAPLACE, dw, precision=Cs.FP64,
+                                                   targets=tg))
+    rows = {"direct FP64 (scaled from the sample)": {"ms": ms_ds64_sample * N / len(tg)}}
+    ms_ds32, o = timed(lambda: Cs.direct(dp, Cs.KERNEL_LAPLACE, dw, precision=Cs.FP32_BULK))
+    rows["direct FP32 (all pairs)"] = {"ms": ms_ds32, "rel_err": float(
+        torch.linalg.norm(o[:, tg] - ds) / torch.linalg.norm(ds))}
+    for name, prec in (("FP64", Cs.FP64), ("FP32", Cs.FP32_BULK)):
+        P = Cs.plan_create(dp, Cs.KERNEL_LAPLACE, n, theta, 4 * n * n, precision=prec)
+        for meth, fn in (("CSFMM", Cs.evaluate), ("CSTC", Cs.evaluate_cstc)):
+            ms, o = timed(lambda: fn(P, dw), reps=3)
+            rows[f"{meth} {name}"] = {"ms": ms, "rel_err": float(
+                torch.linalg.norm(o[:, tg] - ds) / torch.linalg.norm(ds))}
+            log(meth, name, rows[f"{meth} {name}"])
+        Cs.plan_destroy(P)
+    ratios = {
+        "CSTC_FP64_over_CSFMM_FP64": rows["CSTC FP64"]["ms"] / rows["CSFMM FP64"]["ms"],
+        "direct_FP64_over_CSTC_FP64": rows["direct FP64 (scaled from the sample)"]["ms"]
+                                      / rows["CSTC FP64"]["ms"],
+        "CSTC_FP32_over_CSFMM_FP32": rows["CSTC FP32"]["ms"] / rows["CSFMM FP32"]["ms"],
+        "direct_FP32_over_CSTC_FP32": rows["direct FP32 (all pairs)"]["ms"]
+                                      / rows["CSTC FP32"]["ms"],
+    }
+    return {"metric": "runtime of direct sum, CSTC and CSFMM (Laplace, MAC 0.7, n = 6)",
+            "unit": "ms", "config": {"workload": "cstc-vs-fmm", "m": m, "N": N, "degree": n,
+                                     "theta": theta, "max_leaf": 4 * n * n,
+                                     "err_samples": args.err_samples},
+            "rows": rows, "ratios": ratios,
+            "paper_context": "serial CPU, icosahedral N = 2,621,442: CSTC 25x faster than the "
+                             "direct sum, CSFMM 30x faster than CSTC"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -567,7 +634,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="newton-6m",
-                    choices=sorted(WORKLOADS) + ["serving", "accuracy-sweep"])
+                    choices=sorted(WORKLOADS) + ["serving", "accuracy-sweep", "cstc-vs-fmm"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--err-samples", type=int, default=2048)
     ap.add_argument("--cpu-leaves", type=int, default=16384)
@@ -590,6 +657,11 @@ def main():
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         print(json.dumps(run_accuracy_sweep(args)), flush=True)
+        return 0
+    if args.workload == "cstc-vs-fmm":
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        print(json.dumps(run_cstc_vs_fmm(args)), flush=True)
         return 0
     if args.workload == "serving":
         import torch

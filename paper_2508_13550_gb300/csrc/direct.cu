@@ -1,12 +1,17 @@
 // direct.cu -- direct summation of Eq. (nbodysum), phi_i = sum_{j != i} K(x_i, x_j) w_j
 // (Sec. 1), tiled: one thread per target, sources staged through shared memory
-// in tiles of kTile points (split across grid rows when there are few targets).  FP64 form: FP64 kernel values, plain sums within a
-// tile and Neumaier-compensated sums across tiles.  FP32 form: the difference
-// x_i - y_j is formed in FP64 and rounded once, kernel values and tile sums in
-// FP32, FP64 sums across tiles.
+// in tiles of kTile points (split across grid rows when there are few targets).
+// FP64 form: FP64 kernel values, plain sums within a tile and
+// Neumaier-compensated sums across tiles.  FP32 form: coordinates as
+// double-float pairs (x = x_hi + x_lo), the difference formed as
+// (x_hi - y_hi) + (x_lo - y_lo) (the first term is exact for nearby points, so
+// d is accurate to FP32 rounding of d itself), one-instruction kernel factors,
+// FP32 sums over chunks of 32 sources folded by two-sum, and FP64 sums across
+// tiles -- no FP64 arithmetic per pair.
 #include <math.h>
 
 #include "csfmm_internal.cuh"
+#include "fp32_math.cuh"
 
 namespace csfmm {
 
@@ -120,6 +125,120 @@ __global__ void direct_kernel(const double *pts, int N, const double *w, int r0,
   }
 }
 
+// FP32 form.  Shared tile: A[u] = (x_hi, y_hi, z_hi, w_0), B[u] = (x_lo, y_lo,
+// z_lo, -), further weights in sw.  Same output contract as direct_kernel.
+template <int KID, int NR>
+__global__ void direct32_kernel(const double *pts, int N, const double *w, int r0, int nr,
+                                const int64_t *targets, int nt, double *out, int chunk,
+                                double *part, int64_t n_out) {
+  constexpr int DIM = KID == CSFMM_KERNEL_BIOT_SAVART ? 3 : 1;
+  __shared__ float4 sA[kTile], sB[kTile];
+  __shared__ float sw[NR * kTile];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = t < nt;
+  int64_t i = -1;
+  double x0 = 0, x1 = 0, x2 = 0;
+  if (active) {
+    i = targets ? targets[t] : t;
+    x0 = pts[3 * i];
+    x1 = pts[3 * i + 1];
+    x2 = pts[3 * i + 2];
+  }
+  const float xh0 = (float)x0, xh1 = (float)x1, xh2 = (float)x2;
+  const float xl0 = (float)(x0 - (double)xh0), xl1 = (float)(x1 - (double)xh1),
+              xl2 = (float)(x2 - (double)xh2);
+  double s[NR][DIM], c[NR][DIM];
+#pragma unroll
+  for (int q = 0; q < NR; ++q)
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) s[q][d] = c[q][d] = 0.0;
+  const int j_lo = (int)min((int64_t)blockIdx.y * chunk, (int64_t)N);
+  const int j_hi = (int)min((int64_t)j_lo + chunk, (int64_t)N);
+  for (int j0 = j_lo; j0 < j_hi; j0 += kTile) {
+    const int nj = min(kTile, j_hi - j0);
+    __syncthreads();
+    for (int u = threadIdx.x; u < nj; u += blockDim.x) {
+      const int64_t j = j0 + u;
+      const double y0 = pts[3 * j], y1 = pts[3 * j + 1], y2 = pts[3 * j + 2];
+      const float yh0 = (float)y0, yh1 = (float)y1, yh2 = (float)y2;
+      sA[u] = make_float4(yh0, yh1, yh2, (float)w[(int64_t)r0 * N + j]);
+      sB[u] = make_float4((float)(y0 - (double)yh0), (float)(y1 - (double)yh1),
+                          (float)(y2 - (double)yh2), 0.f);
+#pragma unroll
+      for (int q = 1; q < NR; ++q) sw[q * kTile + u] = (float)w[(int64_t)(r0 + q) * N + j];
+    }
+    __syncthreads();
+    if (!active) continue;
+    float hi[NR][3], lo[NR][3];
+#pragma unroll
+    for (int q = 0; q < NR; ++q)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) hi[q][d] = lo[q][d] = 0.f;
+    for (int u0 = 0; u0 < nj; u0 += kChunk) {
+      const int u1 = min(nj, u0 + kChunk);
+      float a[NR][3];
+#pragma unroll
+      for (int q = 0; q < NR; ++q) a[q][0] = a[q][1] = a[q][2] = 0.f;
+      for (int u = u0; u < u1; ++u) {
+        if (j0 + u == i) continue;
+        const float4 A = sA[u], B = sB[u];
+        const float rx = (xh0 - A.x) + (xl0 - B.x);
+        const float ry = (xh1 - A.y) + (xl1 - B.y);
+        const float rz = (xh2 - A.z) + (xl2 - B.z);
+        const float f = kfactor<KID>(fmaf(rz, rz, fmaf(ry, ry, rx * rx)));
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+          const float wq = q == 0 ? A.w : sw[q * kTile + u];
+          if constexpr (KID == CSFMM_KERNEL_BIOT_SAVART) {
+            const float g = wq * f;
+            a[q][0] = fmaf(g, rx, a[q][0]);
+            a[q][1] = fmaf(g, ry, a[q][1]);
+            a[q][2] = fmaf(g, rz, a[q][2]);
+          } else if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
+            a[q][0] = fmaf(wq, f - 1.0f, a[q][0]);  // log2(d2) - 1 = log2(d2 / 2)
+          } else {
+            a[q][0] = fmaf(wq, f, a[q][0]);
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < NR; ++q)
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) two_sum_fold(hi[q][d], lo[q][d], a[q][d]);
+    }
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+      double b[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) b[d] = (double)hi[q][d] + (double)lo[q][d];
+      if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
+        neumaier(s[q][0], c[q][0], -(0.69314718055994530942 * kInv4Pi) * b[0]);
+      } else if constexpr (KID == CSFMM_KERNEL_BIOT_SAVART) {
+        neumaier(s[q][0], c[q][0], kInv2Pi * (x1 * b[2] - x2 * b[1]));
+        neumaier(s[q][1], c[q][1], kInv2Pi * (x2 * b[0] - x0 * b[2]));
+        neumaier(s[q][2], c[q][2], kInv2Pi * (x0 * b[1] - x1 * b[0]));
+      } else {
+        neumaier(s[q][0], c[q][0], b[0]);
+      }
+    }
+  }
+  if (active) {
+#pragma unroll
+    for (int q = 0; q < NR; ++q)
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        const int64_t o = ((int64_t)(r0 + q) * nt + t) * DIM + d;
+        if (part) {
+          double *pp = part + 2 * ((int64_t)blockIdx.y * n_out + o);
+          pp[0] = s[q][d];
+          pp[1] = c[q][d];
+        } else {
+          out[o] = s[q][d] + c[q][d];
+        }
+      }
+  }
+}
+
 // out[o] = Neumaier sum over splits of part[split][o] (o over nrhs * nt * dim).
 __global__ void direct_reduce_kernel(const double *part, int nsplit, int64_t n_out, double *out) {
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n_out;
@@ -130,6 +249,18 @@ __global__ void direct_reduce_kernel(const double *part, int nsplit, int64_t n_o
       c += part[2 * (k * n_out + o) + 1];
     }
     out[o] = s + c;
+  }
+}
+
+template <int KID>
+void launch_direct32(dim3 grid, cudaStream_t st, const double *pts, int N, const double *w, int r0,
+                     int nr, const int64_t *targets, int nt, double *out, int chunk, double *part,
+                     int64_t n_out) {
+  switch (nr) {
+    case 1: direct32_kernel<KID, 1><<<grid, kTile, 0, st>>>(pts, N, w, r0, nr, targets, nt, out, chunk, part, n_out); break;
+    case 2: direct32_kernel<KID, 2><<<grid, kTile, 0, st>>>(pts, N, w, r0, nr, targets, nt, out, chunk, part, n_out); break;
+    case 3: direct32_kernel<KID, 3><<<grid, kTile, 0, st>>>(pts, N, w, r0, nr, targets, nt, out, chunk, part, n_out); break;
+    default: direct32_kernel<KID, 4><<<grid, kTile, 0, st>>>(pts, N, w, r0, nr, targets, nt, out, chunk, part, n_out); break;
   }
 }
 
@@ -159,19 +290,28 @@ csfmm_status launch_direct(const double *pts, int N, int kid, const double *w, i
   csfmm_status result = CSFMM_OK;
   for (int r0 = 0; r0 < nrhs && result == CSFMM_OK; r0 += kRBd) {
     int nr = min(kRBd, nrhs - r0);
-    switch (kid) {
-      case CSFMM_KERNEL_LAPLACE:
-        direct_kernel<CSFMM_KERNEL_LAPLACE, Real><<<grid, kTile, 0, st>>>(pts, N, w, r0, nr, targets, nt, out, chunk, part, n_out);
-        break;
-      case CSFMM_KERNEL_BIOT_SAVART:
-        direct_kernel<CSFMM_KERNEL_BIOT_SAVART, Real><<<grid, kTile, 0, st>>>(pts, N, w, r0, nr, targets, nt, out, chunk, part, n_out);
-        break;
-      case CSFMM_KERNEL_NEWTON:
-        direct_kernel<CSFMM_KERNEL_NEWTON, Real><<<grid, kTile, 0, st>>>(pts, N, w, r0, nr, targets, nt, out, chunk, part, n_out);
-        break;
-      default:
-        direct_kernel<CSFMM_KERNEL_ONE, Real><<<grid, kTile, 0, st>>>(pts, N, w, r0, nr, targets, nt, out, chunk, part, n_out);
-        break;
+    if constexpr (sizeof(Real) == 4) {
+      switch (kid) {
+        case CSFMM_KERNEL_LAPLACE: launch_direct32<CSFMM_KERNEL_LAPLACE>(grid, st, pts, N, w, r0, nr, targets, nt, out, chunk, part, n_out); break;
+        case CSFMM_KERNEL_BIOT_SAVART: launch_direct32<CSFMM_KERNEL_BIOT_SAVART>(grid, st, pts, N, w, r0, nr, targets, nt, out, chunk, part, n_out); break;
+        case CSFMM_KERNEL_NEWTON: launch_direct32<CSFMM_KERNEL_NEWTON>(grid, st, pts, N, w, r0, nr, targets, nt, out, chunk, part, n_out); break;
+        default: launch_direct32<CSFMM_KERNEL_ONE>(grid, st, pts, N, w, r0, nr, targets, nt, out, chunk, part, n_out); break;
+      }
+    } else {
+      switch (kid) {
+        case CSFMM_KERNEL_LAPLACE:
+          direct_kernel<CSFMM_KERNEL_LAPLACE, Real><<<grid, kTile, 0, st>>>(pts, N, w, r0, nr, targets, nt, out, chunk, part, n_out);
+          break;
+        case CSFMM_KERNEL_BIOT_SAVART:
+          direct_kernel<CSFMM_KERNEL_BIOT_SAVART, Real><<<grid, kTile, 0, st>>>(pts, N, w, r0, nr, targets, nt, out, chunk, part, n_out);
+          break;
+        case CSFMM_KERNEL_NEWTON:
+          direct_kernel<CSFMM_KERNEL_NEWTON, Real><<<grid, kTile, 0, st>>>(pts, N, w, r0, nr, targets, nt, out, chunk, part, n_out);
+          break;
+        default:
+          direct_kernel<CSFMM_KERNEL_ONE, Real><<<grid, kTile, 0, st>>>(pts, N, w, r0, nr, targets, nt, out, chunk, part, n_out);
+          break;
+      }
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) result = cuda_status(e, "direct_kernel launch");
