@@ -627,6 +627,67 @@ def run_cstc_vs_fmm(args):
                              "direct sum, CSFMM 30x faster than CSTC"}
 
 
+def run_paper_table(args):
+    """Table "csfmmerrors" of the paper on the GPU: CSFMM approximation error
+    E(phi_FS, phi_DS) (normalised by phi_EX, area-weighted, Sec. 10.2) for the
+    Poisson problem with Y00, Y43 and Y85 on the icosahedral grid (level 8:
+    N = 655362), MAC 0.5 / 0.7 / 0.9, degree n = 2:2:14, N0 = 4 n^2, FP64
+    form; the three fields are the three right-hand sides of one evaluation
+    and the FP64 direct sum is taken on sampled targets.  Prints each entry
+    beside the paper's (tests/golden/csfmm_errors_table.txt)."""
+    import torch
+    from paper_2508_13550_gb300 import csfmm as Cs
+    from paper_2508_13550_gb300 import inputs as I
+    pts, A = I.icosahedral_grid(args.ico_level)
+    N = len(pts)
+    Y = np.stack([I.real_sph_harm(0, 0, pts), I.real_sph_harm(4, 3, pts),
+                  I.real_sph_harm(8, 5, pts)])
+    # exact potentials: Funk-Hecke eigenvalues 1/(n(n+1)) and, for n = 0,
+    # int G_L dS = 1 - ln 2 (Eqs. G_L_1, G_L_2)
+    EX = np.stack([(1.0 - math.log(2.0)) * Y[0], Y[1] / 20.0, Y[2] / 72.0])
+    W = np.ascontiguousarray(Y * A)
+    dp = torch.from_numpy(pts).cuda()
+    dW = torch.from_numpy(W).cuda()
+    rng = np.random.default_rng(20250813)
+    tg = np.sort(rng.choice(N, min(args.err_samples, N), replace=False)).astype(np.int64)
+    dtg = torch.from_numpy(tg).cuda()
+    ds = Cs.direct(dp, Cs.KERNEL_LAPLACE, dW, precision=Cs.FP64, targets=dtg)[:, :, 0].cpu().numpy()
+    At = A[tg]
+    den = np.sum(EX[:, tg] ** 2 * At, axis=1)
+    e_ds = np.sqrt(np.sum((ds - EX[:, tg]) ** 2 * At, axis=1) / den)
+    paper = {}
+    with open(os.path.join(ROOT, "tests", "golden", "csfmm_errors_table.txt")) as f:
+        for line in f:
+            line = line.split("#", 1)[0].split()
+            if line:
+                paper[(line[0], float(line[1]))] = [float(x) for x in line[2:]]
+    rows = []
+    names = ("Y00", "Y43", "Y85")
+    for mac in (0.9, 0.7, 0.5):
+        for n in range(2, 15, 2):
+            P = Cs.plan_create(dp, Cs.KERNEL_LAPLACE, n, mac, 4 * n * n, precision=Cs.FP64,
+                               max_nrhs=3)
+            out = Cs.evaluate(P, dW)
+            torch.cuda.synchronize()
+            fs = out[:, dtg, 0].cpu().numpy()
+            Cs.plan_destroy(P)
+            e = np.sqrt(np.sum((fs - ds) ** 2 * At, axis=1) / den)
+            for k, nm in enumerate(names):
+                ref = paper[(nm, mac)][n // 2 - 1]
+                rows.append({"field": nm, "mac": mac, "n": n, "E_FS_DS": float(e[k]),
+                             "paper": ref, "ratio": float(e[k]) / ref})
+            log(mac, n, [f"{x:.2e}" for x in e])
+    ratios = np.array([r["ratio"] for r in rows])
+    return {"metric": "CSFMM approximation error E(phi_FS, phi_DS) vs Table csfmmerrors",
+            "unit": "rel l2 (normalised by phi_EX)",
+            "config": {"workload": "paper-table", "grid": f"icosahedral level {args.ico_level}",
+                       "N": N, "err_samples": len(tg), "precision": "fp64"},
+            "E_DS_EX": {nm: float(x) for nm, x in zip(names, e_ds)},
+            "rows": rows,
+            "ratio_ours_over_paper": {"median": float(np.median(ratios)),
+                                      "min": float(ratios.min()), "max": float(ratios.max())}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -634,7 +695,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="newton-6m",
-                    choices=sorted(WORKLOADS) + ["serving", "accuracy-sweep", "cstc-vs-fmm"])
+                    choices=sorted(WORKLOADS) + ["serving", "accuracy-sweep", "cstc-vs-fmm",
+                                                 "paper-table"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--err-samples", type=int, default=2048)
     ap.add_argument("--cpu-leaves", type=int, default=16384)
@@ -643,6 +705,7 @@ def main():
     ap.add_argument("--no-fp64-compare", dest="fp64_compare", action="store_false")
     ap.add_argument("--sweep-m", type=int, default=1024)
     ap.add_argument("--sweep-degrees", default="6,8,10,12")
+    ap.add_argument("--ico-level", type=int, default=8)
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-sample", type=int, default=300,
                     help="requests of the serving stream measured in the default line (0: none)")
@@ -657,6 +720,11 @@ def main():
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         print(json.dumps(run_accuracy_sweep(args)), flush=True)
+        return 0
+    if args.workload == "paper-table":
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        print(json.dumps(run_paper_table(args)), flush=True)
         return 0
     if args.workload == "cstc-vs-fmm":
         import torch

@@ -8,8 +8,10 @@ that both the CUDA path's tests/benchmark and the CPU oracle draw inputs from.
 
 Point sets: the equiangular gnomonic cubed-sphere grid of Sec. 3 (cell centres
 are the images of uniform (xi, eta) grid points; Table "grids" lists
-N = 6 m^2 for m = 2^L).  Cell areas are the exact geodesic areas of the
-gnomonic cells.  Data fields: real spherical harmonics Y_{n,m} (Sec. 2.1),
+N = 6 m^2 for m = 2^L), and the icosahedral and latitude-longitude grids of
+the same table.  Cell areas are exact: geodesic areas of the gnomonic cells,
+of the spherical Voronoi cells of the icosahedral vertices, and of the
+latitude-longitude bands.  Data fields: real spherical harmonics Y_{n,m} (Sec. 2.1),
 the Rossby-Haurwitz wave-4 vorticity (Sec. 12, Eq. RH_initial), a land-masked
 random field, and random spherical-harmonic combinations.
 
@@ -77,6 +79,94 @@ def cubed_sphere_grid(m: int, shuffle_seed: int | None = None):
         pts = np.ascontiguousarray(pts[perm])
         areas = np.ascontiguousarray(areas[perm])
     return pts, areas
+
+
+def _spherical_triangle_area(a, b, c):
+    """Signed area of the spherical triangles (a, b, c) of unit vectors
+    ([..., 3] arrays), by tan(E/2) = a.(b x c) / (1 + a.b + b.c + c.a)
+    (Van Oosterom and Strackee, 1983); positive for counter-clockwise
+    triangles seen from outside the sphere."""
+    num = np.einsum("...i,...i->...", a, np.cross(b, c))
+    den = 1.0 + np.einsum("...i,...i->...", a, b) + np.einsum("...i,...i->...", b, c) \
+        + np.einsum("...i,...i->...", c, a)
+    return 2.0 * np.arctan2(num, den)
+
+
+def icosahedral_triangulation(level: int):
+    """Vertices and faces of the icosahedron refined `level` times (each
+    triangle split into four through its edge midpoints, new vertices
+    projected to the sphere): N = 10 * 4^level + 2 vertices (Table "grids":
+    2562 at level 4)."""
+    t = (1.0 + math.sqrt(5.0)) / 2.0
+    v = [(-1, t, 0), (1, t, 0), (-1, -t, 0), (1, -t, 0), (0, -1, t), (0, 1, t),
+         (0, -1, -t), (0, 1, -t), (t, 0, -1), (t, 0, 1), (-t, 0, -1), (-t, 0, 1)]
+    verts = [np.array(x, dtype=np.float64) / np.linalg.norm(x) for x in v]
+    faces = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4),
+             (11, 10, 2), (10, 7, 6), (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8),
+             (3, 8, 9), (4, 9, 5), (2, 4, 11), (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    for _ in range(level):
+        mid = {}
+
+        def midpoint(i, j):
+            key = (i, j) if i < j else (j, i)
+            if key not in mid:
+                x = verts[i] + verts[j]
+                verts.append(x / np.linalg.norm(x))
+                mid[key] = len(verts) - 1
+            return mid[key]
+
+        nf = []
+        for a, b, c in faces:
+            ab, bc, ca = midpoint(a, b), midpoint(b, c), midpoint(c, a)
+            nf += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        faces = nf
+    return np.array(verts), np.array(faces, dtype=np.int64)
+
+
+def icosahedral_grid(level: int):
+    """Icosahedral grid of Table "grids": the cell centres are the vertices of
+    the refined icosahedral triangulation and the cells are their spherical
+    Voronoi (hexagonal, and 12 pentagonal) cells.  Returns (points [N, 3],
+    exact cell areas [N]).  Each triangle (a, b, c) with circumcentre q adds
+    to the cell of each vertex the quadrilateral (vertex, midpoint of one
+    incident edge, q, midpoint of the other), bounded by the perpendicular
+    bisectors through those midpoints; signed areas keep the sum exact."""
+    verts, faces = icosahedral_triangulation(level)
+    a, b, c = verts[faces[:, 0]], verts[faces[:, 1]], verts[faces[:, 2]]
+    q = np.cross(b - a, c - a)
+    q /= np.linalg.norm(q, axis=1)[:, None]
+    q *= np.sign(np.einsum("ij,ij->i", q, a + b + c))[:, None]
+
+    def mid(x, y):
+        m = x + y
+        return m / np.linalg.norm(m, axis=1)[:, None]
+
+    mab, mbc, mca = mid(a, b), mid(b, c), mid(c, a)
+    areas = np.zeros(len(verts))
+    T = _spherical_triangle_area
+    np.add.at(areas, faces[:, 0], T(a, mab, q) + T(a, q, mca))
+    np.add.at(areas, faces[:, 1], T(b, mbc, q) + T(b, q, mab))
+    np.add.at(areas, faces[:, 2], T(c, mca, q) + T(c, q, mbc))
+    return verts, np.abs(areas)
+
+
+def latlon_grid(level: int):
+    """Latitude-longitude grid of Table "grids": spacing 4 / 2^(level-4)
+    degrees, 45 * 2^(level-4) latitude bands by 90 * 2^(level-4) longitudes;
+    the cell centre is at the mean latitude and mean longitude of the cell
+    edges.  Returns (points [N, 3], exact cell areas dlambda (sin phi2 -
+    sin phi1) [N])."""
+    nlat = 45 * 2 ** (level - 4)
+    nlon = 2 * nlat
+    phi = np.linspace(-0.5 * math.pi, 0.5 * math.pi, nlat + 1)
+    lam = np.linspace(0.0, 2.0 * math.pi, nlon + 1)
+    pc = 0.5 * (phi[:-1] + phi[1:])
+    lc = 0.5 * (lam[:-1] + lam[1:])
+    P, L = np.meshgrid(pc, lc, indexing="ij")
+    pts = np.stack([np.cos(P) * np.cos(L), np.cos(P) * np.sin(L), np.sin(P)], axis=-1)
+    band = (np.sin(phi[1:]) - np.sin(phi[:-1])) * (2.0 * math.pi / nlon)
+    areas = np.repeat(band, nlon)
+    return pts.reshape(-1, 3), areas
 
 
 def random_sphere_points(N: int, seed: int):

@@ -55,6 +55,8 @@ TREE_CASES = [
     ("shuffled cubed m=64, n=5, N0=40, MAC 0.5",
      lambda: I.cubed_sphere_grid(64, shuffle_seed=9)[0], 5, 0.5, 40),
     ("random 3,001 points, n=3, N0=1, MAC 0.9", lambda: I.random_sphere_points(3001, 4), 3, 0.9, 1),
+    ("icosahedral 10,242 points, n=6, N0=144", lambda: I.icosahedral_grid(5)[0], 6, 0.7, 144),
+    ("latitude-longitude 16,200 points, n=5, N0=40", lambda: I.latlon_grid(5)[0], 5, 0.7, 40),
 ]
 
 
@@ -100,6 +102,8 @@ FMM_CASES = [
     ("K=1 random 7,777 n=3 N0=12", "rand_7777", O.KERNEL_ONE, 3, 0.7, 12),
     ("Laplace degree 1 m=16 N0=8", "y43_16", O.KERNEL_LAPLACE, 1, 0.7, 8),
     ("Laplace degree 16 m=32 N0=64", "y43_32", O.KERNEL_LAPLACE, 16, 0.7, 64),
+    ("Laplace Y43 icosahedral 40,962 n=6 N0=144", "ico_6", O.KERNEL_LAPLACE, 6, 0.7, 144),
+    ("Biot-Savart RH latitude-longitude 16,200 n=6 N0=60", "latlon_5", O.KERNEL_BIOT_SAVART, 6, 0.7, 60),
 ]
 
 
@@ -111,6 +115,12 @@ def _points(tag):
     if tag.startswith("rh_"):
         m = int(tag[3:])
         pts, A = I.cubed_sphere_grid(m)
+        return pts, I.rossby_haurwitz_vorticity(pts) * A
+    if tag.startswith("ico_"):
+        pts, A = I.icosahedral_grid(int(tag[4:]))
+        return pts, I.real_sph_harm(4, 3, pts) * A
+    if tag.startswith("latlon_"):
+        pts, A = I.latlon_grid(int(tag[7:]))
         return pts, I.rossby_haurwitz_vorticity(pts) * A
     N = int(tag.split("_")[1])
     pts = I.random_sphere_points(N, 17)

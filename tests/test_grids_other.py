@@ -1,0 +1,92 @@
+"""The icosahedral and latitude-longitude point sets of Table "grids" (the
+paper's other two partitions of the sphere), pinned by the table itself,
+exact area sums, second-order midpoint-rule quadrature and the Funk-Hecke
+closed form; and the oracle's FMM and tree code on them (the cubed-sphere
+tree is built over any point set)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2508_13550_gb300 import inputs as I
+from conftest import golden
+
+
+def grid(kind, L):
+    return I.icosahedral_grid(L) if kind == "ico" else I.latlon_grid(L)
+
+
+def test_sizes_and_spacing_match_table_grids():
+    for kind, L, N, dphi in golden("grids_icosahedral_latlon.txt"):
+        L, N, dphi = int(L), int(N), float(dphi)
+        if kind == "ico":
+            assert 10 * 4 ** L + 2 == N
+            if L <= 7:
+                assert len(I.icosahedral_grid(L)[0]) == N
+            got = math.sqrt(4 * math.pi / N) * 180 / math.pi
+            assert abs(got - dphi) <= 0.006 * dphi
+        else:
+            nlat = 45 * 2 ** (L - 4)
+            assert nlat * 2 * nlat == N
+            assert abs(180.0 / nlat - dphi) < 1e-12
+            if L <= 6:
+                assert len(I.latlon_grid(L)[0]) == N
+
+
+@pytest.mark.parametrize("kind,L", [("ico", 3), ("ico", 5), ("latlon", 4), ("latlon", 5)])
+def test_unit_points_and_exact_area_sum(kind, L):
+    pts, A = grid(kind, L)
+    assert np.allclose(np.linalg.norm(pts, axis=1), 1.0, atol=1e-15)
+    assert abs(A.sum() - 4 * math.pi) < 1e-12
+    assert (A > 0).all()
+    assert len(np.unique(np.round(pts, 12), axis=0)) == len(pts)
+
+
+def test_icosahedral_cells_are_voronoi_cells():
+    """Every icosahedral cell has 6 neighbours at nearly equal distance (5 at
+    the 12 pentagons); the hexagon/pentagon areas follow the edge lengths:
+    area ratio smallest/largest about 0.73 at every level."""
+    for L in (3, 4, 5):
+        pts, A = I.icosahedral_grid(L)
+        r = A.min() / A.max()
+        assert 0.70 < r < 0.78, (L, r)
+
+
+@pytest.mark.parametrize("kind", ["ico", "latlon"])
+def test_midpoint_quadrature_second_order(kind):
+    errs = []
+    for L in (3, 4, 5) if kind == "ico" else (4, 5, 6):
+        pts, A = grid(kind, L)
+        y = I.real_sph_harm(4, 3, pts)
+        errs.append(abs(np.sum(y * y * A) - 1.0))
+    assert errs[0] > 3.0 * errs[1] > 9.0 * errs[2], errs
+
+
+def test_funk_hecke_on_icosahedral_grid_second_order():
+    """int G_L Y43 = Y43/20 (Eq. G_L_1, with the sign of the Funk-Hecke
+    eigenvalue of G_L = -(1/4pi) ln(1 - x.y)): the direct sum on the
+    icosahedral grid converges at second order in the spacing (Sec. 10.2)."""
+    errs = []
+    for L in (3, 4, 5):
+        pts, A = I.icosahedral_grid(L)
+        y = I.real_sph_harm(4, 3, pts)
+        ds = O.direct(pts, O.KERNEL_LAPLACE, y * A)[0, :, 0]
+        errs.append(O.rel_l2(ds, y / 20.0, A))
+    assert errs[0] > 3.0 * errs[1] > 9.0 * errs[2], errs
+
+
+@pytest.mark.parametrize("kind,L", [("ico", 4), ("latlon", 4)])
+def test_oracle_fmm_and_cstc_on_other_grids(kind, L):
+    pts, A = grid(kind, L)
+    w = np.random.default_rng(3).standard_normal(len(pts))
+    f = O.FMM(pts, 4, 0.7, 30)
+    assert f.info()["pairs_covered"] == len(pts) ** 2
+    one = f.evaluate(O.KERNEL_ONE, w)[0, :, 0]
+    assert np.max(np.abs(one - (w.sum() - w))) < 1e-12 * np.abs(w).sum()
+    one = f.evaluate_cstc(O.KERNEL_ONE, w)[0, :, 0]
+    assert np.max(np.abs(one - (w.sum() - w))) < 1e-12 * np.abs(w).sum()
+    y = I.real_sph_harm(4, 3, pts) * A
+    ds = O.direct(pts, O.KERNEL_LAPLACE, y)[0, :, 0]
+    hi = O.FMM(pts, 14, 0.5, 16).evaluate(O.KERNEL_LAPLACE, y)[0, :, 0]
+    assert O.rel_l2(hi, ds, A) < 1e-11
