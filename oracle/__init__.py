@@ -36,6 +36,7 @@ _lib = None
 KERNEL_LAPLACE = 0
 KERNEL_BIOT_SAVART = 1
 KERNEL_NEWTON = 2
+KERNEL_BIHARMONIC = 3
 KERNEL_ONE = 100
 
 PP, PC, CP, CC = 0, 1, 2, 3
@@ -88,6 +89,8 @@ def _load():
         lib.oracle_lagrange.argtypes = [ctypes.c_int, P(d), d, P(d)]
         lib.oracle_set_mutation.argtypes = [ctypes.c_int]
         lib.oracle_kernel_dim.argtypes = [ctypes.c_int]
+        lib.oracle_dilog.argtypes = [d]
+        lib.oracle_dilog.restype = d
         lib.oracle_num_threads.restype = ctypes.c_int
         _lib = lib
         return lib
@@ -142,6 +145,11 @@ def direct(pts, kernel: int, w, targets=None):
     if rc != 0:
         raise ValueError("oracle_direct: invalid arguments")
     return out
+
+
+def dilog(x: float) -> float:
+    """dilog(x) = -int_0^x log(1 - t)/t dt for 0 <= x <= 1 (Eq. G_B)."""
+    return float(_load().oracle_dilog(float(x)))
 
 
 def cheb_nodes(n: int):

@@ -65,6 +65,7 @@
 #define OR_KERNEL_LAPLACE 0
 #define OR_KERNEL_BIOT_SAVART 1
 #define OR_KERNEL_NEWTON 2
+#define OR_KERNEL_BIHARMONIC 3
 #define OR_KERNEL_ONE 100
 
 #define OR_D 18            /* tangent table resolution: 2^D intervals per face */
@@ -87,13 +88,35 @@ int oracle_get_mutation(void) { return g_mutation; }
 
 int oracle_kernel_dim(int kid) { return kid == OR_KERNEL_BIOT_SAVART ? 3 : 1; }
 
+/* Dilogarithm dilog(x) = -int_0^x log(1 - t)/t dt = Li2(x), 0 <= x <= 1, by the
+ * Bernoulli-number series Li2(x) = sum_{n>=0} B_n u^(n+1)/(n+1)!, u = -log(1 - x)
+ * (convergent for |u| < 2 pi), used for x <= 1/2 (u <= log 2), and Euler's
+ * reflection Li2(x) = pi^2/6 - log(x) log(1 - x) - Li2(1 - x) for x > 1/2. */
+static double li2_series(double u) {
+  /* B_{2k} / (2k+1)!, k = 1..10 */
+  static const double c[10] = {
+      1.0 / 36.0, -1.0 / 3600.0, 1.0 / 211680.0, -1.0 / 10886400.0, 1.0 / 526901760.0,
+      -691.0 / 16999766784000.0, 7.0 / 6.0 / 1307674368000.0, -3617.0 / 510.0 / 355687428096000.0,
+      43867.0 / 798.0 / 121645100408832000.0, -174611.0 / 330.0 / 51090942171709440000.0};
+  double u2 = u * u, p = u * u2, s = 0.0;
+  for (int k = 0; k < 10; ++k) { s += c[k] * p; p *= u2; }
+  return u - 0.25 * u2 + s;
+}
+double oracle_dilog(double x) {
+  if (x <= 0.5) return li2_series(-log1p(-x));
+  if (x >= 1.0) return OR_PI * OR_PI / 6.0;
+  return OR_PI * OR_PI / 6.0 - ((g_mutation == 14) ? 0.0 : log(x) * log1p(-x)) -
+         li2_series(-log(x));
+}
+
 static int kernel_valid(int kid) {
   return kid == OR_KERNEL_LAPLACE || kid == OR_KERNEL_BIOT_SAVART ||
-         kid == OR_KERNEL_NEWTON || kid == OR_KERNEL_ONE;
+         kid == OR_KERNEL_NEWTON || kid == OR_KERNEL_BIHARMONIC || kid == OR_KERNEL_ONE;
 }
 
 /* ------------------------------------------------------------------------ */
 /* Kernels (Sec. 2): Laplace G_L = -(1/4pi) ln(1 - x.y)  (Eq. G_L);          */
+/* biharmonic G_B = (1/4pi) dilog((1 + x.y)/2)  (Eq. G_B);                    */
 /* Biot-Savart K_BS = -(1/4pi) (x cross y)/(1 - x.y)  (Eq. K_BS);            */
 /* Newtonian 1/sqrt(2(1 - x.y)), the leading term 1/gamma of Eq.             */
 /* G_SAL_approx;  K = 1 (test kernel).                                        */
@@ -120,6 +143,9 @@ static void kernel_eval(int kid, const double *x, const double *y, double *k) {
   }
   case OR_KERNEL_NEWTON:
     k[0] = 1.0 / sqrt(d2);
+    break;
+  case OR_KERNEL_BIHARMONIC: /* Eq. G_B: dilog((1 + x.y)/2) / (4 pi), (1 + x.y)/2 = 1 - d2/4 */
+    k[0] = oracle_dilog(1.0 - 0.25 * d2) / (4.0 * OR_PI);
     break;
   default:
     k[0] = 1.0;

@@ -86,7 +86,14 @@ def _pin_cstc_high_degree_vs_direct():
     return O.rel_l2(cs, ds, A) < 1e-11
 
 
-PINS = [_pin_constant_kernel, _pin_high_degree_vs_direct, _pin_funk_hecke,
+def _pin_biharmonic_eigenvalue():
+    pts, A = I.cubed_sphere_grid(32)
+    y = I.real_sph_harm(1, 0, pts)
+    ds = O.direct(pts, O.KERNEL_BIHARMONIC, y * A)[0, :, 0]
+    return O.rel_l2(ds, y / 4.0, A) < 2e-3 and abs(O.dilog(0.5) - 0.5822405264650125) < 1e-15
+
+
+PINS = [_pin_biharmonic_eigenvalue, _pin_constant_kernel, _pin_high_degree_vs_direct, _pin_funk_hecke,
         _pin_coverage, _pin_lagrange, _pin_moments, _pin_cstc_constant_kernel,
         _pin_cstc_high_degree_vs_direct]
 
@@ -104,6 +111,7 @@ MUTATIONS = {
     11: "CSTC separation test reversed",
     12: "CSTC drops a leaf that is not well separated",
     13: "CSTC visits the first child twice instead of the fourth",
+    14: "dilogarithm reflection drops the log(x) log(1 - x) term",
 }
 
 
