@@ -56,6 +56,7 @@ enum {
   CSFMM_KERNEL_LAPLACE = 0,     /* G_L = -(1/4pi) ln(1 - x.y), Eq. G_L; dim 1 */
   CSFMM_KERNEL_BIOT_SAVART = 1, /* K_BS = -(1/4pi) (x cross y)/(1 - x.y), Eq. K_BS; dim 3 */
   CSFMM_KERNEL_NEWTON = 2,      /* 1/sqrt(2(1 - x.y)) = 1/|x - y|, leading term of Eq. G_SAL_approx; dim 1 */
+  CSFMM_KERNEL_BIHARMONIC = 3,  /* G_B = (1/4pi) dilog((1 + x.y)/2), Eq. G_B; dim 1 */
   CSFMM_KERNEL_ONE = 100        /* K = 1, a test kernel (every interpolation is exact) */
 };
 

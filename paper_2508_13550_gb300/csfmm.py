@@ -24,6 +24,7 @@ import numpy as np
 KERNEL_LAPLACE = 0
 KERNEL_BIOT_SAVART = 1
 KERNEL_NEWTON = 2
+KERNEL_BIHARMONIC = 3
 KERNEL_ONE = 100
 FP64 = 0
 FP32_BULK = 1

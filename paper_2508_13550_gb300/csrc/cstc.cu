@@ -22,6 +22,7 @@
 #include <math.h>
 
 #include "csfmm_internal.cuh"
+#include "dilog.cuh"
 #include "fp32_math.cuh"
 
 namespace csfmm {
@@ -42,8 +43,9 @@ __device__ __forceinline__ double chord_rn(double x0, double x1, double x2, cons
 }
 
 // FP64 kernel term added to acc: Laplace -(1/4pi) ln(d2/2) w, Newtonian
-// w / d, K = 1: w; Biot-Savart accumulates w r / d2 (r = x - y), crossed with
-// x at the end (x cross y = -x cross r for unit vectors).
+// w / d, biharmonic dilog(1 - d2/4) w (times 1/4pi at the end), K = 1: w;
+// Biot-Savart accumulates w r / d2 (r = x - y), crossed with x at the end
+// (x cross y = -x cross r for unit vectors).
 template <int KID>
 __device__ __forceinline__ void term64(double rx, double ry, double rz, double w,
                                        double (&acc)[3]) {
@@ -52,6 +54,8 @@ __device__ __forceinline__ void term64(double rx, double ry, double rz, double w
     acc[0] += -kInv4Pi * log(0.5 * d2) * w;
   } else if constexpr (KID == CSFMM_KERNEL_NEWTON) {
     acc[0] += rsqrt(d2) * w;
+  } else if constexpr (KID == CSFMM_KERNEL_BIHARMONIC) {
+    acc[0] += dilog64(1.0 - 0.25 * d2) * w;  // (1/4pi) applied at the end
   } else if constexpr (KID == CSFMM_KERNEL_BIOT_SAVART) {
     const double g = w / d2;
     acc[0] += g * rx;
@@ -63,7 +67,8 @@ __device__ __forceinline__ void term64(double rx, double ry, double rz, double w
 }
 
 // FP32 kernel term: the sum of w f(d2) over a chunk of sources, with
-// f = log2 d2 (Laplace), 1/d (Newtonian), 1/d2 times r (Biot-Savart), 1.
+// f = log2 d2 (Laplace), 1/d (Newtonian), dilog(1 - d2/4) (biharmonic),
+// 1/d2 times r (Biot-Savart), 1.
 template <int KID>
 __device__ __forceinline__ void term32(float rx, float ry, float rz, float w, float (&acc)[3]) {
   const float d2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
@@ -196,6 +201,8 @@ __global__ void __launch_bounds__(kCstcThreads) cstc_kernel(PlanView v, double t
     dst[2] = kInv2Pi * (x0 * o[1] - x1 * o[0]);
   } else if constexpr (KID == CSFMM_KERNEL_LAPLACE && F32) {
     dst[0] = -(0.69314718055994530942 * kInv4Pi) * o[0];
+  } else if constexpr (KID == CSFMM_KERNEL_BIHARMONIC) {
+    dst[0] = kInv4Pi * o[0];
   } else {
     dst[0] = o[0];
   }
@@ -231,6 +238,9 @@ void launch_cstc(const PlanView &v, bool f32, double theta, int nroots, int nrhs
       break;
     case CSFMM_KERNEL_NEWTON:
       launch_cstc_kid<CSFMM_KERNEL_NEWTON>(v, f32, theta, nroots, nrhs, ldr, ws, wsf, wbar, wbar32, out, st);
+      break;
+    case CSFMM_KERNEL_BIHARMONIC:
+      launch_cstc_kid<CSFMM_KERNEL_BIHARMONIC>(v, f32, theta, nroots, nrhs, ldr, ws, wsf, wbar, wbar32, out, st);
       break;
     default:
       launch_cstc_kid<CSFMM_KERNEL_ONE>(v, f32, theta, nroots, nrhs, ldr, ws, wsf, wbar, wbar32, out, st);

@@ -11,6 +11,7 @@
 #include <math.h>
 
 #include "csfmm_internal.cuh"
+#include "dilog.cuh"
 #include "fp32_math.cuh"
 
 namespace csfmm {
@@ -81,6 +82,7 @@ __global__ void direct_kernel(const double *pts, int N, const double *w, int r0,
       if constexpr (KID == CSFMM_KERNEL_LAPLACE) kv = log(d2 * (Real)0.5);
       else if constexpr (KID == CSFMM_KERNEL_NEWTON) kv = (Real)1 / sqrt(d2);
       else if constexpr (KID == CSFMM_KERNEL_BIOT_SAVART) q3 = (Real)1 / d2;
+      else if constexpr (KID == CSFMM_KERNEL_BIHARMONIC) kv = (Real)dilog64(1.0 - 0.25 * (double)d2);
       else kv = 1;
 #pragma unroll
       for (int q = 0; q < kRBd; ++q) {
@@ -104,6 +106,8 @@ __global__ void direct_kernel(const double *pts, int N, const double *w, int r0,
         neumaier(s[q][0], c[q][0], kInv2Pi * (x1 * b2 - x2 * b1));
         neumaier(s[q][1], c[q][1], kInv2Pi * (x2 * b0 - x0 * b2));
         neumaier(s[q][2], c[q][2], kInv2Pi * (x0 * b1 - x1 * b0));
+      } else if constexpr (KID == CSFMM_KERNEL_BIHARMONIC) {
+        neumaier(s[q][0], c[q][0], kInv4Pi * (double)a[q][0]);
       } else {
         neumaier(s[q][0], c[q][0], (double)a[q][0]);
       }
@@ -217,6 +221,8 @@ __global__ void direct32_kernel(const double *pts, int N, const double *w, int r
         neumaier(s[q][0], c[q][0], kInv2Pi * (x1 * b[2] - x2 * b[1]));
         neumaier(s[q][1], c[q][1], kInv2Pi * (x2 * b[0] - x0 * b[2]));
         neumaier(s[q][2], c[q][2], kInv2Pi * (x0 * b[1] - x1 * b[0]));
+      } else if constexpr (KID == CSFMM_KERNEL_BIHARMONIC) {
+        neumaier(s[q][0], c[q][0], kInv4Pi * b[0]);
       } else {
         neumaier(s[q][0], c[q][0], b[0]);
       }
@@ -295,6 +301,7 @@ csfmm_status launch_direct(const double *pts, int N, int kid, const double *w, i
         case CSFMM_KERNEL_LAPLACE: launch_direct32<CSFMM_KERNEL_LAPLACE>(grid, st, pts, N, w, r0, nr, targets, nt, out, chunk, part, n_out); break;
         case CSFMM_KERNEL_BIOT_SAVART: launch_direct32<CSFMM_KERNEL_BIOT_SAVART>(grid, st, pts, N, w, r0, nr, targets, nt, out, chunk, part, n_out); break;
         case CSFMM_KERNEL_NEWTON: launch_direct32<CSFMM_KERNEL_NEWTON>(grid, st, pts, N, w, r0, nr, targets, nt, out, chunk, part, n_out); break;
+        case CSFMM_KERNEL_BIHARMONIC: launch_direct32<CSFMM_KERNEL_BIHARMONIC>(grid, st, pts, N, w, r0, nr, targets, nt, out, chunk, part, n_out); break;
         default: launch_direct32<CSFMM_KERNEL_ONE>(grid, st, pts, N, w, r0, nr, targets, nt, out, chunk, part, n_out); break;
       }
     } else {
@@ -307,6 +314,9 @@ csfmm_status launch_direct(const double *pts, int N, int kid, const double *w, i
           break;
         case CSFMM_KERNEL_NEWTON:
           direct_kernel<CSFMM_KERNEL_NEWTON, Real><<<grid, kTile, 0, st>>>(pts, N, w, r0, nr, targets, nt, out, chunk, part, n_out);
+          break;
+        case CSFMM_KERNEL_BIHARMONIC:
+          direct_kernel<CSFMM_KERNEL_BIHARMONIC, Real><<<grid, kTile, 0, st>>>(pts, N, w, r0, nr, targets, nt, out, chunk, part, n_out);
           break;
         default:
           direct_kernel<CSFMM_KERNEL_ONE, Real><<<grid, kTile, 0, st>>>(pts, N, w, r0, nr, targets, nt, out, chunk, part, n_out);

@@ -22,6 +22,7 @@
 #include <math.h>
 
 #include "csfmm_internal.cuh"
+#include "dilog.cuh"
 
 namespace csfmm {
 
@@ -63,6 +64,7 @@ __device__ __forceinline__ double fast_rcp(double x) { return 1.0 / x; }
 //   Newtonian    f = 1/sqrt(d2);  a += w f
 //   Biot-Savart  f = 1/d2;  a += w f r (3 components);  value = (1/(2 pi)) x cross a
 //                (since x cross y = -x cross r and 1 - x.y = d2/2)
+//   biharmonic   f = dilog(1 - d2/4);  a += w f;  value = a / (4 pi)
 //   K = 1        a += w
 // ---------------------------------------------------------------------------
 template <int KID, typename Real>
@@ -73,6 +75,7 @@ struct KFac {
     if constexpr (KID == CSFMM_KERNEL_LAPLACE) f = fast_log2(d2);
     else if constexpr (KID == CSFMM_KERNEL_NEWTON) f = fast_rsqrt(d2);
     else if constexpr (KID == CSFMM_KERNEL_BIOT_SAVART) f = fast_rcp(d2);
+    else if constexpr (KID == CSFMM_KERNEL_BIHARMONIC) f = (Real)dilog64(1.0 - 0.25 * (double)d2);
     else f = 1;
   }
 };
@@ -89,7 +92,7 @@ struct Acc {
       a0 += q * k.rx;
       a1 += q * k.ry;
       a2 += q * k.rz;
-    } else if constexpr (KID == CSFMM_KERNEL_NEWTON) {
+    } else if constexpr (KID == CSFMM_KERNEL_NEWTON || KID == CSFMM_KERNEL_BIHARMONIC) {
       a0 += w * k.f;
     } else {
       a0 += w;
@@ -104,6 +107,8 @@ struct Acc {
       out[0] += kInv2Pi * (x1 * b2 - x2 * b1);
       out[1] += kInv2Pi * (x2 * b0 - x0 * b2);
       out[2] += kInv2Pi * (x0 * b1 - x1 * b0);
+    } else if constexpr (KID == CSFMM_KERNEL_BIHARMONIC) {
+      out[0] += kInv4Pi * (double)a0;
     } else {
       out[0] += (double)a0;
     }
@@ -1009,6 +1014,7 @@ csfmm_status dispatch_cstc(Plan &pl, Workspace &W, const double *w, int nrhs, do
     case CSFMM_KERNEL_LAPLACE: return run_cstc<CSFMM_KERNEL_LAPLACE, Real>(pl, W, w, nrhs, out, st);
     case CSFMM_KERNEL_BIOT_SAVART: return run_cstc<CSFMM_KERNEL_BIOT_SAVART, Real>(pl, W, w, nrhs, out, st);
     case CSFMM_KERNEL_NEWTON: return run_cstc<CSFMM_KERNEL_NEWTON, Real>(pl, W, w, nrhs, out, st);
+    case CSFMM_KERNEL_BIHARMONIC: return run_cstc<CSFMM_KERNEL_BIHARMONIC, Real>(pl, W, w, nrhs, out, st);
     case CSFMM_KERNEL_ONE: return run_cstc<CSFMM_KERNEL_ONE, Real>(pl, W, w, nrhs, out, st);
   }
   set_error("unknown kernel id %d", pl.kernel_id);
@@ -1022,6 +1028,7 @@ csfmm_status dispatch_kernel(Plan &pl, Workspace &W, const double *w, int nrhs, 
     case CSFMM_KERNEL_LAPLACE: return run_passes<CSFMM_KERNEL_LAPLACE, Real>(pl, W, w, nrhs, out, st);
     case CSFMM_KERNEL_BIOT_SAVART: return run_passes<CSFMM_KERNEL_BIOT_SAVART, Real>(pl, W, w, nrhs, out, st);
     case CSFMM_KERNEL_NEWTON: return run_passes<CSFMM_KERNEL_NEWTON, Real>(pl, W, w, nrhs, out, st);
+    case CSFMM_KERNEL_BIHARMONIC: return run_passes<CSFMM_KERNEL_BIHARMONIC, Real>(pl, W, w, nrhs, out, st);
     case CSFMM_KERNEL_ONE: return run_passes<CSFMM_KERNEL_ONE, Real>(pl, W, w, nrhs, out, st);
   }
   set_error("unknown kernel id %d", pl.kernel_id);

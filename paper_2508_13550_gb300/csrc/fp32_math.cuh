@@ -7,11 +7,12 @@
 #include <math.h>
 
 #include "csfmm_internal.cuh"
+#include "dilog.cuh"
 
 namespace csfmm {
 
-// Kernel factor f(d2) (Laplace: log2 d2, Newton: 1/sqrt d2, Biot-Savart: 1/d2),
-// one MUFU instruction each.  Flush-to-zero is safe: d2 of two distinct
+// Kernel factor f(d2) (Laplace: log2 d2, Newton: 1/sqrt d2, Biot-Savart: 1/d2:
+// one MUFU instruction each; biharmonic: dilog(1 - d2/4), one or two).  Flush-to-zero is safe: d2 of two distinct
 // points on the unit sphere is far above the FP32 denormal range.
 __device__ __forceinline__ float mufu_rsqrt(float x) {
   float y;
@@ -34,6 +35,8 @@ __device__ __forceinline__ float kfactor(float d2) {
   if constexpr (KID == CSFMM_KERNEL_LAPLACE) return mufu_lg2(d2);
   else if constexpr (KID == CSFMM_KERNEL_NEWTON) return mufu_rsqrt(d2);
   else if constexpr (KID == CSFMM_KERNEL_BIOT_SAVART) return mufu_rcp(d2);
+  else if constexpr (KID == CSFMM_KERNEL_BIHARMONIC)
+    return li2_one_minus(0.25f * d2, [](float v) { return mufu_lg2(v); });
   else return 1.0f;
 }
 

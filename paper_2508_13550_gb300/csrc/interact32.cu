@@ -256,6 +256,8 @@ __global__ void __launch_bounds__(kThreads) near32_kernel(PlanView v, const int3
         double* dst = phi + ((int64_t)(r0 + q) * v.N + i) * DIM;
         if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
           dst[0] = -(0.69314718055994530942 * kInv4Pi) * o[0];
+        } else if constexpr (KID == CSFMM_KERNEL_BIHARMONIC) {
+          dst[0] = kInv4Pi * o[0];
         } else if constexpr (KID == CSFMM_KERNEL_BIOT_SAVART) {
           // (1/2pi) x × sum_j w_j r_j / |r_j|^2, with the FP64 target position
           const double x0 = v.x[i], x1 = v.x[v.N + i], x2 = v.x[2 * (int64_t)v.N + i];
@@ -540,6 +542,7 @@ __global__ void __launch_bounds__(kThreads, CSFMM_NEAR_MINB) near32x2_kernel(Pla
         const int i = i0 + threadIdx.x + (2 * q + h) * kThreads;
         double o = f2_total(hi[q], lo[q], h);
         if constexpr (KID == CSFMM_KERNEL_LAPLACE) o *= -(0.69314718055994530942 * kInv4Pi);
+        if constexpr (KID == CSFMM_KERNEL_BIHARMONIC) o *= kInv4Pi;
         if (i < e) phi[((int64_t)r0 * v.N + i)] = o;
       }
   }
@@ -621,6 +624,7 @@ __global__ void __launch_bounds__(160, 8) far32x2_kernel(PlanView v, const float
     const int m = threadIdx.x + h * nth;
     double o = f2_total(hi[0], lo[0], h);
     if constexpr (KID == CSFMM_KERNEL_LAPLACE) o *= -(0.69314718055994530942 * kInv4Pi);
+    if constexpr (KID == CSFMM_KERNEL_BIHARMONIC) o *= kInv4Pi;
     if (m < P) psi[((int64_t)c * ldr + r0) * P + m] = o;
   }
 }
@@ -724,6 +728,8 @@ __global__ void __launch_bounds__(160) far32_kernel(PlanView v, const float *wsf
       double *dst = psi + ((int64_t)c * ldr + r0 + q) * DIM * P + m;
       if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
         dst[0] = -(0.69314718055994530942 * kInv4Pi) * o[0];
+      } else if constexpr (KID == CSFMM_KERNEL_BIHARMONIC) {
+        dst[0] = kInv4Pi * o[0];
       } else if constexpr (KID == CSFMM_KERNEL_BIOT_SAVART) {
         dst[0] = kInv2Pi * (xa[1] * o[2] - xa[2] * o[1]);
         dst[P] = kInv2Pi * (xa[2] * o[0] - xa[0] * o[2]);
@@ -947,6 +953,7 @@ __global__ void __launch_bounds__(CSFMM_MULTI_THREADS) multi32_kernel(
           const int qq = 2 * q + h;
           double val = f2_total(hi[k][q], lo[k][q], h);
           if constexpr (KID == CSFMM_KERNEL_LAPLACE) val *= -(0.69314718055994530942 * kInv4Pi);
+          if constexpr (KID == CSFMM_KERNEL_BIHARMONIC) val *= kInv4Pi;
           if (FAR) psi[((int64_t)c * ldr + r0 + qq) * P + i] = val;
           else phi[(int64_t)(r0 + qq) * v.N + i] = val;
         }
@@ -1008,6 +1015,7 @@ void launch_multi32(const PlanView &v, bool far, int ngrid, const int32_t *leave
   switch (v.kernel_id) {
     case CSFMM_KERNEL_LAPLACE: launch_multi_kid<CSFMM_KERNEL_LAPLACE>(v, far, ngrid, leaves, wsf, wbar, ldr, r0, nr, phi, psi, st); break;
     case CSFMM_KERNEL_NEWTON: launch_multi_kid<CSFMM_KERNEL_NEWTON>(v, far, ngrid, leaves, wsf, wbar, ldr, r0, nr, phi, psi, st); break;
+    case CSFMM_KERNEL_BIHARMONIC: launch_multi_kid<CSFMM_KERNEL_BIHARMONIC>(v, far, ngrid, leaves, wsf, wbar, ldr, r0, nr, phi, psi, st); break;
     default: launch_multi_kid<CSFMM_KERNEL_ONE>(v, far, ngrid, leaves, wsf, wbar, ldr, r0, nr, phi, psi, st); break;
   }
 }
@@ -1019,6 +1027,7 @@ void launch_far32(const PlanView &v, int ncells, const float *wsf, const float *
     case CSFMM_KERNEL_LAPLACE: launch_far_kid<CSFMM_KERNEL_LAPLACE>(v, ncells, wsf, wbar, ldr, r0, nr, psi, st); break;
     case CSFMM_KERNEL_BIOT_SAVART: launch_far_kid<CSFMM_KERNEL_BIOT_SAVART>(v, ncells, wsf, wbar, ldr, r0, nr, psi, st); break;
     case CSFMM_KERNEL_NEWTON: launch_far_kid<CSFMM_KERNEL_NEWTON>(v, ncells, wsf, wbar, ldr, r0, nr, psi, st); break;
+    case CSFMM_KERNEL_BIHARMONIC: launch_far_kid<CSFMM_KERNEL_BIHARMONIC>(v, ncells, wsf, wbar, ldr, r0, nr, psi, st); break;
     default: launch_far_kid<CSFMM_KERNEL_ONE>(v, ncells, wsf, wbar, ldr, r0, nr, psi, st); break;
   }
 }
@@ -1031,6 +1040,7 @@ void launch_near32(const PlanView &v, const int32_t *leaves, int nleaves, const 
     case CSFMM_KERNEL_LAPLACE: launch_kid<CSFMM_KERNEL_LAPLACE>(v, leaves, nleaves, wsf, ldw, wbar, ldr, r0, nr, phi, st, part); break;
     case CSFMM_KERNEL_BIOT_SAVART: launch_kid<CSFMM_KERNEL_BIOT_SAVART>(v, leaves, nleaves, wsf, ldw, wbar, ldr, r0, nr, phi, st, nullptr); break;
     case CSFMM_KERNEL_NEWTON: launch_kid<CSFMM_KERNEL_NEWTON>(v, leaves, nleaves, wsf, ldw, wbar, ldr, r0, nr, phi, st, part); break;
+    case CSFMM_KERNEL_BIHARMONIC: launch_kid<CSFMM_KERNEL_BIHARMONIC>(v, leaves, nleaves, wsf, ldw, wbar, ldr, r0, nr, phi, st, part); break;
     default: launch_kid<CSFMM_KERNEL_ONE>(v, leaves, nleaves, wsf, ldw, wbar, ldr, r0, nr, phi, st, part); break;
   }
 }
@@ -1041,6 +1051,7 @@ void launch_pp_sym32(const PlanView &v, const int2 *pairs, const int32_t *off, i
   switch (v.kernel_id) {
     case CSFMM_KERNEL_LAPLACE: pp_sym_kernel<CSFMM_KERNEL_LAPLACE><<<npairs, kSymThreads, 0, st>>>(v, pairs, off, wsf, part); break;
     case CSFMM_KERNEL_NEWTON: pp_sym_kernel<CSFMM_KERNEL_NEWTON><<<npairs, kSymThreads, 0, st>>>(v, pairs, off, wsf, part); break;
+    case CSFMM_KERNEL_BIHARMONIC: pp_sym_kernel<CSFMM_KERNEL_BIHARMONIC><<<npairs, kSymThreads, 0, st>>>(v, pairs, off, wsf, part); break;
     default: pp_sym_kernel<CSFMM_KERNEL_ONE><<<npairs, kSymThreads, 0, st>>>(v, pairs, off, wsf, part); break;
   }
 }

@@ -61,6 +61,7 @@ CASES = [
     ("Biot-Savart, cubed m=48, n=5, N0=30", O.KERNEL_BIOT_SAVART, lambda: I.cubed_sphere_grid(48)[0], 5, 0.7, 30),
     ("Laplace, clustered 6,000 + 1,500, n=4, N0=20, MAC 0.8", O.KERNEL_LAPLACE, lambda: clustered(6000, 4), 4, 0.8, 20),
     ("Newtonian, random 3,001, n=3, N0=1, MAC 0.9", O.KERNEL_NEWTON, lambda: I.random_sphere_points(3001, 5), 3, 0.9, 1),
+    ("biharmonic, cubed m=32, n=6, N0=64", O.KERNEL_BIHARMONIC, lambda: I.cubed_sphere_grid(32)[0], 6, 0.7, 64),
 ]
 
 

@@ -103,6 +103,8 @@ FMM_CASES = [
     ("Laplace degree 1 m=16 N0=8", "y43_16", O.KERNEL_LAPLACE, 1, 0.7, 8),
     ("Laplace degree 16 m=32 N0=64", "y43_32", O.KERNEL_LAPLACE, 16, 0.7, 64),
     ("Laplace Y43 icosahedral 40,962 n=6 N0=144", "ico_6", O.KERNEL_LAPLACE, 6, 0.7, 144),
+    ("biharmonic Y43 m=32 n=8 N0=64", "y43_32", O.KERNEL_BIHARMONIC, 8, 0.7, 64),
+    ("biharmonic random 7,777 n=5 N0=37 MAC 0.5", "rand_7777", O.KERNEL_BIHARMONIC, 5, 0.5, 37),
     ("Biot-Savart RH latitude-longitude 16,200 n=6 N0=60", "latlon_5", O.KERNEL_BIOT_SAVART, 6, 0.7, 60),
 ]
 
@@ -171,7 +173,7 @@ def test_fmm_multi_rhs_consistent_with_single(torch, C):
 
 
 @pytest.mark.parametrize("kernel", [O.KERNEL_LAPLACE, O.KERNEL_BIOT_SAVART, O.KERNEL_NEWTON,
-                                    O.KERNEL_ONE])
+                                    O.KERNEL_BIHARMONIC, O.KERNEL_ONE])
 def test_direct_matches_oracle(torch, C, kernel):
     pts = I.random_sphere_points(3001, 8)
     W = np.random.default_rng(9).standard_normal((5, 3001))
@@ -292,7 +294,8 @@ def test_argument_errors(torch, C):
 
 
 @pytest.mark.parametrize("kernel,nrhs", [(O.KERNEL_LAPLACE, 16), (O.KERNEL_NEWTON, 9),
-                                         (O.KERNEL_ONE, 8), (O.KERNEL_BIOT_SAVART, 6)])
+                                         (O.KERNEL_ONE, 8), (O.KERNEL_BIOT_SAVART, 6),
+                                         (O.KERNEL_BIHARMONIC, 16)])
 def test_fp32_multi_rhs_matches_single_and_fp64(torch, C, kernel, nrhs):
     """FP32-bulk with many right-hand sides (chunks of 16 / 8 share each kernel
     value) against one-at-a-time FP32 evaluations and the FP64 FMM."""
@@ -333,7 +336,8 @@ def test_graph_replay_matches_direct_launches(torch, C, precision):
     C.plan_sync(graph, stream=s.cuda_stream)
 
 
-@pytest.mark.parametrize("kernel", [O.KERNEL_NEWTON, O.KERNEL_LAPLACE, O.KERNEL_ONE])
+@pytest.mark.parametrize("kernel", [O.KERNEL_NEWTON, O.KERNEL_LAPLACE, O.KERNEL_BIHARMONIC,
+                                    O.KERNEL_ONE])
 def test_fp32_symmetric_near_field(torch, C, kernel):
     """One right-hand side in FP32 bulk evaluates mirrored PP leaf pairs once
     for both directions; the result agrees with the two-RHS launch (which

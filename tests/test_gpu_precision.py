@@ -63,3 +63,14 @@ def test_fp32_bulk_poisson_uniform_grid(torch, C):
     print(f"\nPoisson Y43 m=256 n=8: E={e:.3e} bias={bias:.3e}")
     assert e < 2.6e-7
     assert abs(bias) < 3e-8
+
+
+def test_fp32_bulk_biharmonic_against_direct(torch, C):
+    """Biharmonic kernel (Eq. G_B) in the FP32-bulk form: the FP32 dilogarithm
+    (two MUFU logarithms and a Bernoulli series) keeps the error against the
+    FP64 direct sum near FP32 rounding."""
+    pts, A = I.cubed_sphere_grid(128)
+    w = I.land_mask_field(pts, 21) * A
+    e, bias = errors(torch, C, pts, O.KERNEL_BIHARMONIC, w, 8, 256)
+    print(f"\nbiharmonic m=128 n=8: E={e:.3e} bias={bias:.3e}")
+    assert e < 1e-6
