@@ -688,6 +688,77 @@ def run_paper_table(args):
                                       "min": float(ratios.min()), "max": float(ratios.max())}}
 
 
+def run_runtime_table(args):
+    """The paper's Table "runtimes" setting on the GPU: the N-body sum with
+    the Laplace, biharmonic, Biot-Savart and Newtonian kernels (the SAL
+    kernel's leading term) on the icosahedral grid (level args.ico_level),
+    CSFMM with MAC 0.7, degree 6, N0 = 144, in both precision forms (CUDA
+    events, plan resident, median of 5), and the direct sum (FP32: all N^2
+    pairs; FP64: sampled targets, scaled to N).  Prints the paper's serial CPU
+    times beside them (context only: other hardware)."""
+    import torch
+    from paper_2508_13550_gb300 import csfmm as Cs
+    from paper_2508_13550_gb300 import inputs as I
+    pts, A = I.icosahedral_grid(args.ico_level)
+    N = len(pts)
+    dp = torch.from_numpy(pts).cuda()
+    rng = np.random.default_rng(20250813)
+    tg = torch.from_numpy(np.sort(rng.choice(N, min(args.err_samples, N), replace=False))
+                          .astype(np.int64)).cuda()
+    paper = {}
+    with open(os.path.join(ROOT, "tests", "golden", "runtimes_table.txt")) as f:
+        hdr = None
+        for line in f:
+            if line.startswith("# kernel"):
+                hdr = [int(x.split("=")[-1]) for x in line.split()[3:]]
+            line = line.split("#", 1)[0].split()
+            if line:
+                paper[(line[0], line[1])] = dict(zip(hdr, map(float, line[2:])))
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            out = fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts), out
+
+    rows = []
+    for name, paper_name, kid in (("Laplace", "Laplace", Cs.KERNEL_LAPLACE),
+                                  ("biharmonic", "biharmonic", Cs.KERNEL_BIHARMONIC),
+                                  ("Biot-Savart", "Biot-Savart", Cs.KERNEL_BIOT_SAVART),
+                                  ("Newtonian", "SAL", Cs.KERNEL_NEWTON)):
+        f = I.rossby_haurwitz_vorticity(pts) if kid == Cs.KERNEL_BIOT_SAVART else \
+            I.real_sph_harm(4, 3, pts)
+        dw = torch.from_numpy(np.ascontiguousarray((f * A)[None])).cuda()
+        ms_ds64, ds = timed(lambda: Cs.direct(dp, kid, dw, precision=Cs.FP64, targets=tg), 1)
+        ms_ds32, _ = timed(lambda: Cs.direct(dp, kid, dw, precision=Cs.FP32_BULK), 1)
+        row = {"kernel": name, "N": N, "direct_fp64_ms_scaled": ms_ds64 * N / len(tg),
+               "direct_fp32_ms": ms_ds32,
+               "paper_direct_s": paper[(paper_name, "direct")].get(N),
+               "paper_csfmm_s": paper[(paper_name, "csfmm")].get(N)}
+        for tag, prec in (("fp64", Cs.FP64), ("fp32", Cs.FP32_BULK)):
+            P = Cs.plan_create(dp, kid, 6, 0.7, 144, precision=prec)
+            ms, out = timed(lambda: Cs.evaluate(P, dw), 5)
+            Cs.plan_destroy(P)
+            row[f"csfmm_{tag}_ms"] = ms
+            row[f"csfmm_{tag}_rel_err"] = float(torch.linalg.norm(out[:, tg] - ds)
+                                                / torch.linalg.norm(ds))
+        rows.append(row)
+        log(row)
+    return {"metric": "N-body sum runtime per kernel (Table runtimes setting)", "unit": "ms",
+            "config": {"workload": "runtime-table", "grid": f"icosahedral level {args.ico_level}",
+                       "N": N, "degree": 6, "theta": 0.7, "max_leaf": 144},
+            "rows": rows,
+            "paper_context": "serial CPU (one AMD EPYC 7763 core), FP64 C++"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -696,7 +767,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="newton-6m",
                     choices=sorted(WORKLOADS) + ["serving", "accuracy-sweep", "cstc-vs-fmm",
-                                                 "paper-table"])
+                                                 "paper-table", "runtime-table"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--err-samples", type=int, default=2048)
     ap.add_argument("--cpu-leaves", type=int, default=16384)
@@ -720,6 +791,11 @@ def main():
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         print(json.dumps(run_accuracy_sweep(args)), flush=True)
+        return 0
+    if args.workload == "runtime-table":
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        print(json.dumps(run_runtime_table(args)), flush=True)
         return 0
     if args.workload == "paper-table":
         import torch
