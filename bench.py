@@ -759,6 +759,73 @@ def run_runtime_table(args):
             "paper_context": "serial CPU (one AMD EPYC 7763 core), FP64 C++"}
 
 
+def run_bve(args):
+    """The paper's BVE runs (Sec. 12) on the GPU: the RH wave-4 on the
+    icosahedral grid of level args.bve_level (N = 163842 at level 7), RK4 with
+    dt = 0.01 day and Omega = 2 pi per day, the velocity by the CSFMM (MAC 0.7,
+    degree 6, N0 = 144; a plan built at every stage) in both precision forms
+    or by the direct sum.  Times one RK4 step with CUDA events (median over
+    args.steps steps after args.warmup; the FP64 direct step once) and
+    reports E_zeta (Eq. bveerr) after args.bve_days days for the CSFMM forms
+    and the FP32 direct sum.  The paper's ratio (CSFMM 36x faster than the
+    direct sum at N = 163842, serial CPU) is printed as context."""
+    import torch
+    from paper_2508_13550_gb300 import csfmm as Cs
+    from paper_2508_13550_gb300 import inputs as I
+    x, z, A = I.workload_bve(args.bve_level)
+    N = len(x)
+    dx, dz, dA = (torch.from_numpy(a).cuda() for a in (x, z, A))
+    dt, om = I.BVE_DT, I.BVE_OMEGA
+    forms = {"csfmm_fp64": (6, Cs.FP64), "csfmm_fp32": (6, Cs.FP32_BULK),
+             "direct_fp32": (0, Cs.FP32_BULK), "direct_fp64": (0, Cs.FP64)}
+
+    def step(deg, prec, xi, zi):
+        return Cs.bve_step(xi, zi, dA, dt, om, deg, 0.7, 144, prec)
+
+    def time_steps(deg, prec, k, w):
+        xi, zi = dx, dz
+        for _ in range(w):
+            xi, zi = step(deg, prec, xi, zi)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(k):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            xi, zi = step(deg, prec, xi, zi)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    rows = {}
+    for tag, (deg, prec) in forms.items():
+        slow = tag == "direct_fp64"
+        ms = time_steps(deg, prec, 1 if slow else args.steps, 0 if slow else args.warmup)
+        rows[tag] = {"ms_per_step": ms}
+        log(tag, f"{ms:.2f} ms per RK4 step")
+    nsteps = int(round(args.bve_days / dt))
+    for tag in ("csfmm_fp64", "csfmm_fp32", "direct_fp32"):
+        deg, prec = forms[tag]
+        xi, zi = dx, dz
+        for _ in range(nsteps):
+            xi, zi = step(deg, prec, xi, zi)
+        torch.cuda.synchronize()
+        xs, zs = xi.cpu().numpy(), zi.cpu().numpy()
+        ex = I.rossby_haurwitz_vorticity(xs)
+        rows[tag]["E_zeta"] = float(np.sqrt(np.sum((zs - ex) ** 2 * A) / np.sum(ex ** 2 * A)))
+        log(tag, "E_zeta", rows[tag]["E_zeta"])
+    d64 = rows["direct_fp64"]["ms_per_step"]
+    return {"metric": "BVE vortex-method RK4 step time (Sec. 12 setting)", "unit": "ms",
+            "config": {"workload": "bve-rh-wave", "grid": f"icosahedral level {args.bve_level}",
+                       "N": N, "dt_day": dt, "omega": om, "degree": 6, "theta": 0.7,
+                       "max_leaf": 144, "days": args.bve_days},
+            "rows": rows,
+            "speedup_over_direct_fp64": {k: d64 / v["ms_per_step"] for k, v in rows.items()},
+            "paper_context": "CSFMM 36x faster than direct summation at N = 163842 "
+                             "(serial CPU, FP64)"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -767,7 +834,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="newton-6m",
                     choices=sorted(WORKLOADS) + ["serving", "accuracy-sweep", "cstc-vs-fmm",
-                                                 "paper-table", "runtime-table"])
+                                                 "paper-table", "runtime-table", "bve"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--err-samples", type=int, default=2048)
     ap.add_argument("--cpu-leaves", type=int, default=16384)
@@ -777,6 +844,8 @@ def main():
     ap.add_argument("--sweep-m", type=int, default=1024)
     ap.add_argument("--sweep-degrees", default="6,8,10,12")
     ap.add_argument("--ico-level", type=int, default=8)
+    ap.add_argument("--bve-level", type=int, default=7)
+    ap.add_argument("--bve-days", type=float, default=1.0)
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-sample", type=int, default=300,
                     help="requests of the serving stream measured in the default line (0: none)")
@@ -796,6 +865,11 @@ def main():
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         print(json.dumps(run_runtime_table(args)), flush=True)
+        return 0
+    if args.workload == "bve":
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        print(json.dumps(run_bve(args)), flush=True)
         return 0
     if args.workload == "paper-table":
         import torch

@@ -336,6 +336,33 @@ csfmm_status csfmm_server_stats_get(csfmm_server s, csfmm_server_stats *stats);
 /* Drains, then frees every plan, workspace and stream of the server. */
 csfmm_status csfmm_server_destroy(csfmm_server s);
 
+/* One fourth-order Runge-Kutta step of the barotropic vorticity equation on
+ * a sphere rotating at angular frequency omega about the z axis, by the
+ * vortex method of Sec. 2.3 (Eq. BVE_ODEs): particle i at x_i with relative
+ * vorticity zeta_i and fixed area A_i moves with
+ *     dx_i/dt = sum_j K_BS(x_i, x_j) zeta_j A_j   (Eq. K_BS, j != i)
+ * and dzeta_i/dt = -2 omega dz_i/dt, so that zeta + 2 omega z is carried by
+ * each particle (Eq. BVE).  Every one of the four stages evaluates the
+ * velocity at that stage's positions: with degree > 0 a CSFMM plan is built
+ * there (csfmm_plan_create with the given degree, theta, max_leaf and
+ * precision form) and evaluated once; with degree == 0 the velocity is the
+ * direct sum (csfmm_direct in the given precision form).  The stage
+ * positions and the result are projected back onto the unit sphere, on
+ * which K_BS is defined.  The remeshing that the paper applies after each
+ * step is not part of this call.
+ *   x, zeta, area  device FP64 [N][3] unit vectors, [N], [N]
+ *   dt             time step (> 0), in the time unit of 1/omega
+ *   x_out, zeta_out device [N][3], [N]: the state at t + dt, in input order;
+ *                  may be x and zeta themselves (an in-place step)
+ * Stage scratch (9 N doubles) is allocated and freed in stream order
+ * (cudaMallocAsync / cudaFreeAsync).  Each plan build synchronises the
+ * stream, so the call returns after its last plan evaluation; the final
+ * update is still enqueued on stream when it returns.
+ * Errors: INVALID_ARG, NOT_ON_SPHERE, OUT_OF_MEMORY, CUDA, DEVICE, TIMEOUT. */
+csfmm_status csfmm_bve_step(const double *x, const double *zeta, const double *area, int64_t N,
+                            double dt, double omega, int degree, double theta, int max_leaf,
+                            int precision, double *x_out, double *zeta_out, void *stream);
+
 /* Waits for the plan's work on stream and returns a deferred device status
  * (CSFMM_ERR_DEVICE / CSFMM_ERR_TIMEOUT) if a kernel reported one. */
 csfmm_status csfmm_plan_sync(csfmm_plan plan, void *stream);

@@ -122,6 +122,8 @@ _SIGS = {
     "csfmm_direct_targets": [_VP, _I64, ctypes.c_int, _VP, ctypes.c_int, _VP, _I64, _VP,
                              ctypes.c_int, _VP],
     "csfmm_plan_stats": [_VP, ctypes.POINTER(Stats)],
+    "csfmm_bve_step": [_VP, _VP, _VP, _I64, _D, _D, ctypes.c_int, _D, ctypes.c_int, ctypes.c_int,
+                       _VP, _VP, _VP],
     "csfmm_autotune": [_VP, _I64, ctypes.c_int, ctypes.c_int, _D, _VP, ctypes.c_int, ctypes.c_int,
                        ctypes.c_char_p, _D, ctypes.POINTER(TuneResult)],
     "csfmm_plan_export_cells": [_VP] + [_VP] * 10,
@@ -329,6 +331,26 @@ def direct(points, kernel_id: int, weights, precision: int = FP64, targets=None,
                                         _dev(targets, torch.int64), nt,
                                         _dev(out, torch.float64), precision, _stream(stream)))
     return out
+
+
+def bve_step(x, zeta, area, dt: float, omega: float, degree: int = 6, theta: float = 0.7,
+             max_leaf: int = 0, precision: int = FP64, x_out=None, zeta_out=None, stream=None):
+    """csfmm_bve_step: one RK4 step of the vortex method for the barotropic
+    vorticity equation (Sec. 2.3, Eq. BVE_ODEs); degree 0 = direct sum.
+    max_leaf 0 = 4 degree^2.  Returns (x_out, zeta_out) on the device."""
+    import torch
+    N = x.shape[0]
+    if x_out is None:
+        x_out = torch.empty((N, 3), dtype=torch.float64, device=x.device)
+    if zeta_out is None:
+        zeta_out = torch.empty((N,), dtype=torch.float64, device=x.device)
+    leaf = max_leaf if max_leaf > 0 else max(1, 4 * degree * degree)
+    _check(load().csfmm_bve_step(_dev(x, torch.float64), _dev(zeta, torch.float64),
+                                 _dev(area, torch.float64), N, float(dt), float(omega),
+                                 int(degree), float(theta), int(leaf), int(precision),
+                                 _dev(x_out, torch.float64), _dev(zeta_out, torch.float64),
+                                 _stream(stream)))
+    return x_out, zeta_out
 
 
 def autotune(points, kernel_id: int, degree: int, theta: float, weights, precision: int = FP64,

@@ -1,0 +1,114 @@
+// bve.cu -- one fourth-order Runge-Kutta step of the barotropic vorticity
+// equation on a rotating sphere by the vortex method of Sec. 2.3
+// (Eq. BVE_ODEs): particles x_i with relative vorticity zeta_i and fixed areas
+// A_i move with the velocity of the Biot-Savart N-body sum,
+//     dx_i/dt = sum_j K_BS(x_i, x_j) zeta_j A_j,    dzeta_i/dt = -2 Omega dz_i/dt,
+// the velocity computed by the CSFMM (a plan built at every stage's positions)
+// or by direct summation.  Stage positions are projected back onto the
+// sphere (the kernel is defined there).  The paper's remeshing is not part of
+// the step.
+#include <math.h>
+
+#include <cuda_runtime.h>
+
+#include "csfmm_internal.cuh"
+
+namespace csfmm {
+
+namespace {
+
+// w = zeta * A
+__global__ void bve_weights_kernel(const double *zeta, const double *area, int64_t N, double *w) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x)
+    w[i] = zeta[i] * area[i];
+}
+
+// Stage update from the stage velocity u [N][3] (b = the stage's weight in
+// the RK4 combination, the running sum ksum initialised by the first stage):
+//   ksum += b u;  xs = P(x + a u), zs = zeta - 2 Omega a u_z   (next stage)
+// and on the last stage the step result
+//   xs = P(x + c ksum), zs = zeta - 2 Omega c ksum_z           (c = dt/6),
+// P the projection onto the unit sphere.
+__global__ void bve_stage_kernel(const double *x, const double *zeta, const double *u, int64_t N,
+                                 int first, int last, double a, double b, double c,
+                                 double two_omega, double *ksum, double *xs, double *zs) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double k[3];
+    for (int d = 0; d < 3; ++d) {
+      k[d] = (first ? 0.0 : ksum[3 * i + d]) + b * u[3 * i + d];
+      ksum[3 * i + d] = k[d];
+    }
+    const double s = last ? c : a;
+    double v[3];
+    for (int d = 0; d < 3; ++d) v[d] = last ? k[d] : u[3 * i + d];
+    double y[3], nrm = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      y[d] = x[3 * i + d] + s * v[d];
+      nrm += y[d] * y[d];
+    }
+    nrm = sqrt(nrm);
+    for (int d = 0; d < 3; ++d) xs[3 * i + d] = y[d] / nrm;
+    zs[i] = zeta[i] - two_omega * s * v[2];
+  }
+}
+
+}  // namespace
+
+}  // namespace csfmm
+
+using namespace csfmm;
+
+extern "C" csfmm_status csfmm_bve_step(const double *x, const double *zeta, const double *area,
+                                       int64_t N, double dt, double omega, int degree,
+                                       double theta, int max_leaf, int precision, double *x_out,
+                                       double *zeta_out, void *stream) {
+  if (!x || !zeta || !area || !x_out || !zeta_out || N < 1 || !(dt > 0.0) || degree < 0) {
+    set_error("csfmm_bve_step: non-NULL device arrays, N >= 1, dt > 0 and degree >= 0 required");
+    return CSFMM_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  // scratch: stage positions and vorticity, weights, velocity, running sum
+  double *buf = nullptr;
+  const size_t n3 = (size_t)3 * N;
+  CSFMM_CUDA(cudaMallocAsync((void **)&buf, sizeof(double) * (3 * n3 + 2 * (size_t)N), st));
+  double *xs = buf, *u = buf + n3, *ksum = buf + 2 * n3, *zs = buf + 3 * n3,
+         *w = buf + 3 * n3 + N;
+  const int grid = grid_for(N, 256, 152 * 8);
+  const double two_omega = 2.0 * omega;
+  // RK4: stage s evaluates the velocity at (xs, zs); a = offset of the next
+  // stage, b = weight of this stage in the combination (1, 2, 2, 1)
+  const double a_next[4] = {0.5 * dt, 0.5 * dt, dt, 0.0};
+  const double b_w[4] = {1.0, 2.0, 2.0, 1.0};
+  csfmm_status s = CSFMM_OK;
+  const double *xcur = x, *zcur = zeta;
+  csfmm_options opt{};
+  opt.precision = precision;
+  opt.max_nrhs = 1;
+  for (int stage = 0; stage < 4 && s == CSFMM_OK; ++stage) {
+    bve_weights_kernel<<<grid, 256, 0, st>>>(zcur, area, N, w);
+    if (degree > 0) {
+      csfmm_plan plan = nullptr;
+      s = csfmm_plan_create(xcur, N, CSFMM_KERNEL_BIOT_SAVART, degree, theta, max_leaf, &opt,
+                            stream, &plan);
+      if (s == CSFMM_OK) s = csfmm_evaluate(plan, w, 1, u, stream);
+      if (s == CSFMM_OK) s = csfmm_plan_sync(plan, stream);
+      csfmm_plan_destroy(plan);
+    } else {
+      s = csfmm_direct(xcur, N, CSFMM_KERNEL_BIOT_SAVART, w, 1, u, precision, stream);
+    }
+    if (s != CSFMM_OK) break;
+    const bool last = stage == 3;
+    bve_stage_kernel<<<grid, 256, 0, st>>>(x, zeta, u, N, stage == 0, last, a_next[stage],
+                                           b_w[stage], dt / 6.0, two_omega, ksum,
+                                           last ? x_out : xs, last ? zeta_out : zs);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) s = cuda_status(e, "bve_stage_kernel launch");
+    xcur = xs;
+    zcur = zs;
+  }
+  cudaError_t e = cudaFreeAsync(buf, st);
+  if (e != cudaSuccess && s == CSFMM_OK) s = cuda_status(e, "cudaFreeAsync");
+  return s;
+}

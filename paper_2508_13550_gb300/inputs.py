@@ -317,6 +317,16 @@ def rossby_haurwitz_velocity(pts):
     return np.cross(g, pts)
 
 
+def gaussian_vortex_vorticity(pts):
+    """Gaussian vortex initial vorticity (Sec. 12, Eq. Gaussian_ic): a core
+    4 pi exp(-16 |x - x_c|^2) at latitude pi/20, longitude 0, on the
+    constant background -0.196353 printed with it (zero total vorticity)."""
+    lat = math.pi / 20
+    xc = np.array([math.cos(lat), 0.0, math.sin(lat)])
+    d2 = np.sum((pts - xc) ** 2, axis=1)
+    return 4 * math.pi * np.exp(-16.0 * d2) - 0.196353
+
+
 def land_mask_field(pts, seed: int, land_fraction: float = 0.7,
                     nmax: int = 8):
     """Seeded 'land' field: U[0,1] values on the cells where a smooth random
@@ -370,6 +380,26 @@ def workload_rh_biot_savart(m: int = 256, noise: float = 1e-3,
     zeta_n = zeta + noise * rms * rng.standard_normal(len(pts))
     w = (zeta_n * areas)[None, :]
     return pts, areas, np.ascontiguousarray(w), rossby_haurwitz_velocity(pts)[None]
+
+
+BVE_OMEGA = 2 * math.pi  # rotation rate of the BVE runs, 2 pi per day (Sec. 12)
+BVE_DT = 0.01            # RK4 time step of the BVE runs, in days (Sec. 12)
+
+
+def workload_bve(level: int = 7, field: str = "rh"):
+    """Vortex-method particles for the barotropic vorticity equation (Sec. 12):
+    icosahedral cell centres and areas of the given refinement level
+    (N = 10 4^level + 2) with the RH wave-4 ("rh", Eq. RH_initial) or the
+    Gaussian vortex ("gaussian", Eq. Gaussian_ic) vorticity; returns
+    (x [N,3], zeta [N], area [N])."""
+    pts, areas = icosahedral_grid(level)
+    if field == "rh":
+        zeta = rossby_haurwitz_vorticity(pts)
+    elif field == "gaussian":
+        zeta = gaussian_vortex_vorticity(pts)
+    else:
+        raise ValueError(f"unknown BVE field {field!r}")
+    return pts, np.ascontiguousarray(zeta), areas
 
 
 def workload_newton_land(m: int = 1024, seed: int = MASTER_SEED + 3):
