@@ -123,6 +123,19 @@ def icosahedral_triangulation(level: int):
     return np.array(verts), np.array(faces, dtype=np.int64)
 
 
+def grid_adjacency(faces, N: int):
+    """Neighbour lists of a triangulated grid in CSR form: (offsets [N+1],
+    neighbours int64), the vertices joined to each vertex by a triangle edge,
+    ascending within each row."""
+    f = np.asarray(faces, dtype=np.int64)
+    e = np.concatenate([f[:, [0, 1]], f[:, [1, 2]], f[:, [2, 0]]])
+    e = np.concatenate([e, e[:, ::-1]])
+    e = np.unique(e, axis=0)
+    offsets = np.zeros(N + 1, dtype=np.int64)
+    np.add.at(offsets, e[:, 0] + 1, 1)
+    return np.cumsum(offsets), np.ascontiguousarray(e[:, 1])
+
+
 def icosahedral_grid(level: int):
     """Icosahedral grid of Table "grids": the cell centres are the vertices of
     the refined icosahedral triangulation and the cells are their spherical
@@ -386,12 +399,13 @@ BVE_OMEGA = 2 * math.pi  # rotation rate of the BVE runs, 2 pi per day (Sec. 12)
 BVE_DT = 0.01            # RK4 time step of the BVE runs, in days (Sec. 12)
 
 
-def workload_bve(level: int = 7, field: str = "rh"):
+def workload_bve(level: int = 7, field: str = "rh", with_adjacency: bool = False):
     """Vortex-method particles for the barotropic vorticity equation (Sec. 12):
     icosahedral cell centres and areas of the given refinement level
     (N = 10 4^level + 2) with the RH wave-4 ("rh", Eq. RH_initial) or the
     Gaussian vortex ("gaussian", Eq. Gaussian_ic) vorticity; returns
-    (x [N,3], zeta [N], area [N])."""
+    (x [N,3], zeta [N], area [N]), plus the grid's neighbour lists
+    (offsets, neighbours) with with_adjacency."""
     pts, areas = icosahedral_grid(level)
     if field == "rh":
         zeta = rossby_haurwitz_vorticity(pts)
@@ -399,6 +413,9 @@ def workload_bve(level: int = 7, field: str = "rh"):
         zeta = gaussian_vortex_vorticity(pts)
     else:
         raise ValueError(f"unknown BVE field {field!r}")
+    if with_adjacency:
+        off, nb = grid_adjacency(icosahedral_triangulation(level)[1], len(pts))
+        return pts, np.ascontiguousarray(zeta), areas, off, nb
     return pts, np.ascontiguousarray(zeta), areas
 
 
