@@ -20,7 +20,8 @@ Remeshing (Sec. 12 remeshes at every step by local biquadratic interpolation,
 without further detail).  Reading: after a step the particles return to the
 fixed grid points g_k, which keep their areas, and the vorticity at g_k is
 read off a local quadratic fitted to the moved particles near g_k:
-  1. each moved particle belongs to the Voronoi cell of its nearest grid point;
+  1. each moved particle belongs to the Voronoi cell of its nearest grid point
+     (of two equally near ones, the one with the smaller index);
   2. the stencil of g_k is the set of grid points within `ring` edges of g_k in
      the grid's triangulation (ring 2: g_k, its neighbours and theirs), and the
      particles of their cells are the data;
@@ -114,9 +115,23 @@ def vorticity_error(zeta, zeta_exact, area):
 
 
 def nearest_grid_point(grid, x):
-    """Index of the grid point nearest to each x (Voronoi cell membership)."""
+    """Index of the grid point nearest to each x (Voronoi cell membership).
+    Squared chords are formed as ((d0 d0 + d1 d1) + d2 d2) in FP64, and
+    equally near grid points go to the smaller index: symmetric inputs (the
+    icosahedral grid and RH wave share mirror symmetries) put particles
+    exactly on cell boundaries.  The four nearest candidates of a k-d tree are
+    compared in that arithmetic."""
     from scipy.spatial import cKDTree
-    return cKDTree(np.asarray(grid)).query(np.asarray(x))[1].astype(np.int64)
+    grid = np.asarray(grid, dtype=np.float64)
+    x = np.asarray(x, dtype=np.float64)
+    k = min(4, len(grid))
+    cand = cKDTree(grid).query(x, k=k)[1].reshape(len(x), k)
+    d = x[:, None, :] - grid[cand]
+    d2 = (d[..., 0] * d[..., 0] + d[..., 1] * d[..., 1]) + d[..., 2] * d[..., 2]
+    best = np.empty(len(x), dtype=np.int64)
+    for i in range(len(x)):
+        best[i] = min(zip(d2[i], cand[i]))[1]
+    return best
 
 
 def ring_stencil(offsets, nbrs, k: int, ring: int):
