@@ -763,65 +763,99 @@ def run_bve(args):
     """The paper's BVE runs (Sec. 12) on the GPU: the RH wave-4 on the
     icosahedral grid of level args.bve_level (N = 163842 at level 7), RK4 with
     dt = 0.01 day and Omega = 2 pi per day, the velocity by the CSFMM (MAC 0.7,
-    degree 6, N0 = 144; a plan built at every stage) in both precision forms
-    or by the direct sum.  Times one RK4 step with CUDA events (median over
-    args.steps steps after args.warmup; the FP64 direct step once) and
-    reports E_zeta (Eq. bveerr) after args.bve_days days for the CSFMM forms
-    and the FP32 direct sum.  The paper's ratio (CSFMM 36x faster than the
-    direct sum at N = 163842, serial CPU) is printed as context."""
+    degree 6, N0 = 144; a plan built at every stage, the grid's plan reused
+    for the first stage of remeshed steps) in both precision forms or by the
+    direct sum, with and without remeshing onto the grid after every step.
+    Times one RK4 step with CUDA events (median over args.steps steps after
+    args.warmup; the FP64 direct step once) and reports E_zeta (Eq. bveerr)
+    after args.bve_days days; then E_zeta of the remeshed method against N
+    (levels 4 .. args.bve_level) with the CSFMM and the direct sum, the
+    setting of the paper's Figure bveerr.  The paper's ratio (CSFMM 36x faster
+    than the direct sum at N = 163842, serial CPU) is printed as context."""
     import torch
     from paper_2508_13550_gb300 import csfmm as Cs
     from paper_2508_13550_gb300 import inputs as I
-    x, z, A = I.workload_bve(args.bve_level)
-    N = len(x)
-    dx, dz, dA = (torch.from_numpy(a).cuda() for a in (x, z, A))
     dt, om = I.BVE_DT, I.BVE_OMEGA
+    nsteps = int(round(args.bve_days / dt))
     forms = {"csfmm_fp64": (6, Cs.FP64), "csfmm_fp32": (6, Cs.FP32_BULK),
              "direct_fp32": (0, Cs.FP32_BULK), "direct_fp64": (0, Cs.FP64)}
 
-    def step(deg, prec, xi, zi):
-        return Cs.bve_step(xi, zi, dA, dt, om, deg, 0.7, 144, prec)
+    def setup(level):
+        x, z, A, off, nb = I.workload_bve(level, with_adjacency=True)
+        dx, dz, dA = (torch.from_numpy(a).cuda() for a in (x, z, A))
+        G = Cs.remesh_grid_create(dx, torch.from_numpy(off).cuda(), torch.from_numpy(nb).cuda())
+        return x, z, A, dx, dz, dA, G
 
-    def time_steps(deg, prec, k, w):
+    def e_zeta(zs, xs, A):
+        ex = I.rossby_haurwitz_vorticity(xs)
+        return float(np.sqrt(np.sum((zs - ex) ** 2 * A) / np.sum(ex ** 2 * A)))
+
+    def stepper(deg, prec, dx, dA, G, remeshed):
+        plan = (Cs.plan_create(dx, Cs.KERNEL_BIOT_SAVART, deg, 0.7, 144, precision=prec,
+                               max_nrhs=1) if remeshed and deg > 0 else None)
+        if remeshed:
+            return lambda xi, zi: (xi, Cs.bve_step_remeshed(G, zi, dA, dt, om, deg, 0.7, 144,
+                                                            prec, grid_plan=plan))
+        return lambda xi, zi: Cs.bve_step(xi, zi, dA, dt, om, deg, 0.7, 144, prec)
+
+    def timed(step, dx, dz, k, w):
         xi, zi = dx, dz
         for _ in range(w):
-            xi, zi = step(deg, prec, xi, zi)
+            xi, zi = step(xi, zi)
         torch.cuda.synchronize()
         ts = []
         for _ in range(k):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
-            xi, zi = step(deg, prec, xi, zi)
+            xi, zi = step(xi, zi)
             e1.record()
             torch.cuda.synchronize()
             ts.append(e0.elapsed_time(e1))
         return statistics.median(ts)
 
+    x, z, A, dx, dz, dA, G = setup(args.bve_level)
+    N = len(x)
     rows = {}
     for tag, (deg, prec) in forms.items():
         slow = tag == "direct_fp64"
-        ms = time_steps(deg, prec, 1 if slow else args.steps, 0 if slow else args.warmup)
-        rows[tag] = {"ms_per_step": ms}
-        log(tag, f"{ms:.2f} ms per RK4 step")
-    nsteps = int(round(args.bve_days / dt))
-    for tag in ("csfmm_fp64", "csfmm_fp32", "direct_fp32"):
-        deg, prec = forms[tag]
-        xi, zi = dx, dz
-        for _ in range(nsteps):
-            xi, zi = step(deg, prec, xi, zi)
-        torch.cuda.synchronize()
-        xs, zs = xi.cpu().numpy(), zi.cpu().numpy()
-        ex = I.rossby_haurwitz_vorticity(xs)
-        rows[tag]["E_zeta"] = float(np.sqrt(np.sum((zs - ex) ** 2 * A) / np.sum(ex ** 2 * A)))
-        log(tag, "E_zeta", rows[tag]["E_zeta"])
+        rows[tag] = {}
+        for rm in (False, True):
+            st = stepper(deg, prec, dx, dA, G, rm)
+            ms = timed(st, dx, dz, 1 if slow else args.steps, 0 if slow else args.warmup)
+            rows[tag]["ms_per_step_remeshed" if rm else "ms_per_step"] = ms
+            log(tag, "remeshed" if rm else "", f"{ms:.2f} ms per RK4 step")
+            if slow:
+                continue
+            xi, zi = dx, dz
+            for _ in range(nsteps):
+                xi, zi = st(xi, zi)
+            torch.cuda.synchronize()
+            e = e_zeta(zi.cpu().numpy(), xi.cpu().numpy(), A)
+            rows[tag]["E_zeta_remeshed" if rm else "E_zeta"] = e
+            log(tag, "remeshed" if rm else "", "E_zeta", e)
+    conv = []
+    for level in range(4, args.bve_level + 1):
+        xl, zl, Al, dxl, dzl, dAl, Gl = (x, z, A, dx, dz, dA, G) if level == args.bve_level \
+            else setup(level)
+        row = {"level": level, "N": len(xl)}
+        for tag in ("csfmm_fp32", "direct_fp32"):
+            st = stepper(*forms[tag], dxl, dAl, Gl, True)
+            zi = dzl
+            for _ in range(nsteps):
+                _, zi = st(dxl, zi)
+            torch.cuda.synchronize()
+            row[tag] = e_zeta(zi.cpu().numpy(), xl, Al)
+        conv.append(row)
+        log("E_zeta remeshed", row)
     d64 = rows["direct_fp64"]["ms_per_step"]
     return {"metric": "BVE vortex-method RK4 step time (Sec. 12 setting)", "unit": "ms",
             "config": {"workload": "bve-rh-wave", "grid": f"icosahedral level {args.bve_level}",
                        "N": N, "dt_day": dt, "omega": om, "degree": 6, "theta": 0.7,
-                       "max_leaf": 144, "days": args.bve_days},
+                       "max_leaf": 144, "days": args.bve_days, "remesh_ring": 2},
             "rows": rows,
             "speedup_over_direct_fp64": {k: d64 / v["ms_per_step"] for k, v in rows.items()},
+            "E_zeta_remeshed_vs_N": conv,
             "paper_context": "CSFMM 36x faster than direct summation at N = 163842 "
                              "(serial CPU, FP64)"}
 

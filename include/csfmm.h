@@ -363,6 +363,56 @@ csfmm_status csfmm_bve_step(const double *x, const double *zeta, const double *a
                             double dt, double omega, int degree, double theta, int max_leaf,
                             int precision, double *x_out, double *zeta_out, void *stream);
 
+/* Remeshing onto a fixed grid (Sec. 12 remeshes the vortex method at every
+ * time step by local interpolation).  A remeshing grid holds M grid points g_k
+ * (the particles' home positions, e.g. icosahedral cell centres) and the
+ * neighbour lists of their triangulation, which must be the Delaunay
+ * triangulation of the points (the convex hull; the refined icosahedron is
+ * one).  csfmm_remesh maps M moved particles, particle p having started at
+ * g_p, carrying values f_p, to values at the grid points:
+ *   1. a particle belongs to the Voronoi cell of its nearest grid point (a
+ *      greedy walk on the triangulation from g_p);
+ *   2. the stencil of g_k is the grid points within `ring` triangulation edges
+ *      of g_k, its data the particles of their cells;
+ *   3. with h_k the chord from g_k to its nearest neighbour and (u, v) the
+ *      gnomonic coordinates of the tangent plane at g_k divided by h_k, the
+ *      quadratic c0 + c1 u + c2 v + c3 u^2 + c4 uv + c5 v^2 is fitted by least
+ *      squares with weights exp(-(u^2 + v^2)), and f_out[k] = c0.
+ * The fit reproduces quadratics in (u, v) exactly and is third-order
+ * accurate for smooth data.
+ *   grid         device [M][3] FP64 unit vectors (copied), 7 <= M < 2^30
+ *   adj_offsets  device int64 [M+1], adj device int64 [adj_offsets[M]]: the
+ *                neighbours of g_k are adj[adj_offsets[k] .. adj_offsets[k+1])
+ *                (read during the call only)
+ *   ring         1..3 (2: 19 grid points around a hexagonal cell)
+ * create is synchronous.  Errors: INVALID_ARG (bad neighbour lists, a stencil
+ * wider than 64 grid points), NOT_ON_SPHERE, OUT_OF_MEMORY, CUDA. */
+typedef struct csfmm_remesh_grid_s *csfmm_remesh_grid;
+csfmm_status csfmm_remesh_grid_create(const double *grid, int64_t M, const int64_t *adj_offsets,
+                                      const int64_t *adj, int ring, void *stream,
+                                      csfmm_remesh_grid *out);
+/*   x device [M][3] moved particles, f device [M], f_out device [M] (may be f).
+ * Allocates nothing; synchronises the stream before returning (it reads the
+ * grid's status word).  Calls on one grid must not overlap.
+ * Errors: INVALID_ARG, CUDA, DEVICE (a walk that did not end, a cell holding
+ * more than 4096 particles, a stencil with fewer than 6 particles or a
+ * singular fit). */
+csfmm_status csfmm_remesh(csfmm_remesh_grid grid, const double *x, const double *f,
+                          double *f_out, void *stream);
+csfmm_status csfmm_remesh_grid_destroy(csfmm_remesh_grid grid);
+
+/* One remeshed step of the vortex method (Sec. 12): csfmm_bve_step from the
+ * grid points with vorticity zeta, then csfmm_remesh of the moved particles
+ * onto the grid.  grid_plan, if not NULL, is a Biot-Savart plan built on the
+ * grid's points (the first RK4 stage always starts there, so one plan serves
+ * every step); NULL builds one per step like the other stages.
+ *   zeta, area device [M]; zeta_out device [M] (may be zeta)
+ * Synchronous.  Errors: those of csfmm_bve_step and csfmm_remesh. */
+csfmm_status csfmm_bve_step_remeshed(csfmm_remesh_grid grid, csfmm_plan grid_plan,
+                                     const double *zeta, const double *area, double dt,
+                                     double omega, int degree, double theta, int max_leaf,
+                                     int precision, double *zeta_out, void *stream);
+
 /* Waits for the plan's work on stream and returns a deferred device status
  * (CSFMM_ERR_DEVICE / CSFMM_ERR_TIMEOUT) if a kernel reported one. */
 csfmm_status csfmm_plan_sync(csfmm_plan plan, void *stream);

@@ -56,19 +56,13 @@ __global__ void bve_stage_kernel(const double *x, const double *zeta, const doub
 
 }  // namespace
 
-}  // namespace csfmm
-
-using namespace csfmm;
-
-extern "C" csfmm_status csfmm_bve_step(const double *x, const double *zeta, const double *area,
-                                       int64_t N, double dt, double omega, int degree,
-                                       double theta, int max_leaf, int precision, double *x_out,
-                                       double *zeta_out, void *stream) {
-  if (!x || !zeta || !area || !x_out || !zeta_out || N < 1 || !(dt > 0.0) || degree < 0) {
-    set_error("csfmm_bve_step: non-NULL device arrays, N >= 1, dt > 0 and degree >= 0 required");
-    return CSFMM_ERR_INVALID_ARG;
-  }
-  cudaStream_t st = (cudaStream_t)stream;
+// One RK4 step from (x, zeta); stage 0 evaluates on first_plan when it is not
+// NULL (a Biot-Savart plan built at x), every other stage on a plan built at
+// its positions (or by the direct sum when degree == 0).
+csfmm_status bve_rk4(const double *x, const double *zeta, const double *area, int64_t N,
+                     double dt, double omega, int degree, double theta, int max_leaf,
+                     int precision, csfmm_plan first_plan, double *x_out, double *zeta_out,
+                     cudaStream_t st) {
   // scratch: stage positions and vorticity, weights, velocity, running sum
   double *buf = nullptr;
   const size_t n3 = (size_t)3 * N;
@@ -86,9 +80,13 @@ extern "C" csfmm_status csfmm_bve_step(const double *x, const double *zeta, cons
   csfmm_options opt{};
   opt.precision = precision;
   opt.max_nrhs = 1;
+  void *stream = (void *)st;
   for (int stage = 0; stage < 4 && s == CSFMM_OK; ++stage) {
     bve_weights_kernel<<<grid, 256, 0, st>>>(zcur, area, N, w);
-    if (degree > 0) {
+    if (stage == 0 && first_plan) {
+      s = csfmm_evaluate(first_plan, w, 1, u, stream);
+      if (s == CSFMM_OK) s = csfmm_plan_sync(first_plan, stream);
+    } else if (degree > 0) {
       csfmm_plan plan = nullptr;
       s = csfmm_plan_create(xcur, N, CSFMM_KERNEL_BIOT_SAVART, degree, theta, max_leaf, &opt,
                             stream, &plan);
@@ -108,6 +106,60 @@ extern "C" csfmm_status csfmm_bve_step(const double *x, const double *zeta, cons
     xcur = xs;
     zcur = zs;
   }
+  cudaError_t e = cudaFreeAsync(buf, st);
+  if (e != cudaSuccess && s == CSFMM_OK) s = cuda_status(e, "cudaFreeAsync");
+  return s;
+}
+
+}  // namespace csfmm
+
+using namespace csfmm;
+
+static bool bve_args_ok(int64_t N, double dt, int degree, const char *who) {
+  if (N < 1 || !(dt > 0.0) || degree < 0) {
+    set_error("%s: N >= 1, dt > 0 and degree >= 0 required", who);
+    return false;
+  }
+  return true;
+}
+
+extern "C" csfmm_status csfmm_bve_step(const double *x, const double *zeta, const double *area,
+                                       int64_t N, double dt, double omega, int degree,
+                                       double theta, int max_leaf, int precision, double *x_out,
+                                       double *zeta_out, void *stream) {
+  if (!x || !zeta || !area || !x_out || !zeta_out) {
+    set_error("csfmm_bve_step: NULL array");
+    return CSFMM_ERR_INVALID_ARG;
+  }
+  if (!bve_args_ok(N, dt, degree, "csfmm_bve_step")) return CSFMM_ERR_INVALID_ARG;
+  return bve_rk4(x, zeta, area, N, dt, omega, degree, theta, max_leaf, precision, nullptr, x_out,
+                 zeta_out, (cudaStream_t)stream);
+}
+
+extern "C" csfmm_status csfmm_bve_step_remeshed(csfmm_remesh_grid grid, csfmm_plan grid_plan,
+                                                const double *zeta, const double *area, double dt,
+                                                double omega, int degree, double theta,
+                                                int max_leaf, int precision, double *zeta_out,
+                                                void *stream) {
+  if (!grid || !zeta || !area || !zeta_out) {
+    set_error("csfmm_bve_step_remeshed: NULL argument");
+    return CSFMM_ERR_INVALID_ARG;
+  }
+  const int64_t M = remesh_grid_size(grid);
+  if (!bve_args_ok(M, dt, degree, "csfmm_bve_step_remeshed")) return CSFMM_ERR_INVALID_ARG;
+  if (grid_plan && (grid_plan->impl.N != M ||
+                    grid_plan->impl.kernel_id != CSFMM_KERNEL_BIOT_SAVART)) {
+    set_error("csfmm_bve_step_remeshed: grid_plan must be a Biot-Savart plan of the grid's %lld "
+              "points", (long long)M);
+    return CSFMM_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  double *buf = nullptr;
+  CSFMM_CUDA(cudaMallocAsync((void **)&buf, sizeof(double) * 4 * (size_t)M, st));
+  double *xm = buf, *zm = buf + 3 * (size_t)M;
+  csfmm_status s = bve_rk4(remesh_grid_points(grid), zeta, area, M, dt, omega, degree,
+                           theta, max_leaf, precision, grid_plan, xm, zm, st);
+  if (s == CSFMM_OK) s = remesh_impl(grid, xm, zm, zeta_out, st);
   cudaError_t e = cudaFreeAsync(buf, st);
   if (e != cudaSuccess && s == CSFMM_OK) s = cuda_status(e, "cudaFreeAsync");
   return s;

@@ -254,6 +254,14 @@ csfmm_status direct_impl(const double *points, int64_t N, int kernel_id, const d
                          int nrhs, const int64_t *targets, int64_t ntargets, double *out,
                          int precision, cudaStream_t st);
 
+// Remeshing (remesh.cu): synchronous remeshing of particles x (particle p
+// started at grid point p) carrying f onto the grid, and the grid's size and
+// points ([M][3], device).
+csfmm_status remesh_impl(csfmm_remesh_grid G, const double *x, const double *f, double *f_out,
+                         cudaStream_t st);
+int64_t remesh_grid_size(csfmm_remesh_grid G);
+const double *remesh_grid_points(csfmm_remesh_grid G);
+
 // Host helpers shared by the library's own files.
 const double *host_tan_table();  // T[k] = tan(k (pi/2)/2^kD - pi/4), k = 0..2^kD
 int grid_for(int64_t n, int block, int max_blocks = 1 << 30);

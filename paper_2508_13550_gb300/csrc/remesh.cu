@@ -1,0 +1,474 @@
+// remesh.cu -- remeshing of the vortex method for the barotropic vorticity
+// equation onto a fixed grid (Sec. 12 remeshes at every time step by local
+// interpolation), and the remeshed RK4 step.
+//
+// After a step the particles return to the grid points g_k, which keep their
+// areas, and the new vorticity at g_k is the value there of a local quadratic
+// fitted to the moved particles:
+//   1. a particle belongs to the Voronoi cell of its nearest grid point (of
+//      two equally near ones, the one with the smaller index), found by a
+//      greedy walk on the grid's triangulation from the grid point the
+//      particle started at (on a Delaunay triangulation a vertex that is not
+//      the nearest always has a strictly nearer neighbour);
+//   2. the stencil of g_k is the grid points within `ring` triangulation edges
+//      of g_k, its data the particles of their cells;
+//   3. in gnomonic coordinates of the tangent plane at g_k divided by h_k (the
+//      chord from g_k to its nearest neighbour), u = x.e1 / (x.g_k h_k),
+//      v = x.e2 / (x.g_k h_k), the quadratic c0 + c1 u + c2 v + c3 u^2 + c4 u v
+//      + c5 v^2 is fitted by least squares with weights exp(-(u^2 + v^2)) and
+//      zeta_k = c0.
+// Work per remeshing: one walk per particle, a counting sort of the particles
+// by cell (buckets sorted by particle index so that every sum below runs in a
+// fixed order), and one 6x6 weighted normal-equation solve per grid point
+// (Cholesky, FP64; the scaled coordinates keep its condition number near 1e2).
+#include <math.h>
+
+#include <cuda_runtime.h>
+
+#include "csfmm_internal.cuh"
+
+struct csfmm_remesh_grid_s {
+  int M = 0, ring = 2;
+  int64_t nadj = 0;
+  csfmm::DeviceArena arena;
+  double *g = nullptr;        // [M][3] grid points
+  double *h = nullptr;        // [M] chord to the nearest neighbour
+  int32_t *aoff = nullptr;    // [M+1] triangulation neighbours (CSR)
+  int32_t *adj = nullptr;     // [nadj]
+  int32_t *soff = nullptr;    // [M+1] stencils (CSR)
+  int32_t *sten = nullptr;    // [soff[M]]
+  // per-remeshing scratch
+  int32_t *cell = nullptr;    // [M] cell of each particle
+  int32_t *cnt = nullptr;     // [M+1] particles per cell
+  int32_t *boff = nullptr;    // [M+1] bucket offsets
+  int32_t *cursor = nullptr;  // [M]
+  int32_t *bucket = nullptr;  // [M] particles by cell
+  int32_t *scan_tmp = nullptr;
+  int *status = nullptr;
+};
+
+namespace csfmm {
+
+namespace {
+
+constexpr int kRemeshMaxRing = 3;
+constexpr int kRemeshMaxStencil = 64;  // grid points in one stencil
+constexpr int kRemeshMaxWalk = 1 << 16;  // greedy steps of one particle (M < 2^31 vertices,
+                                         // but a step of the remeshed method moves a few cells)
+constexpr int kRemeshMaxBucketSort = 4096;
+
+// Bits of the remeshing status word.
+constexpr int kRmAdjacency = 1;  // a neighbour index out of range or a vertex without neighbours
+constexpr int kRmStencil = 2;    // a stencil wider than kRemeshMaxStencil
+constexpr int kRmWalk = 4;       // a walk that did not end within kRemeshMaxWalk steps
+constexpr int kRmBucket = 8;     // a cell holding more than kRemeshMaxBucketSort particles
+constexpr int kRmFit = 16;       // a stencil with fewer than 6 particles or a singular fit
+constexpr int kRmNotOnSphere = 32;
+
+// Squared chord ((d0 d0 + d1 d1) + d2 d2), rounded after every operation, so
+// that a particle on a cell boundary (symmetric inputs put some exactly there)
+// is assigned by the same comparison on every platform.
+__device__ __forceinline__ double dist2(const double *a, const double *b) {
+  const double d0 = a[0] - b[0], d1 = a[1] - b[1], d2 = a[2] - b[2];
+  return __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2));
+}
+
+__global__ void adj_convert_kernel(const int64_t *off, const int64_t *adj, int M, int64_t nadj,
+                                   const double *g, int32_t *aoff, int32_t *adj32, double *h,
+                                   int *status) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= M; k += gridDim.x * blockDim.x) {
+    const int64_t b = off[k];
+    if (b < 0 || b > nadj) {
+      atomicOr(status, kRmAdjacency);
+      aoff[k] = 0;
+      continue;
+    }
+    aoff[k] = (int32_t)b;
+    if (k == M) continue;
+    const int64_t e = off[k + 1];
+    const double *gk = g + 3 * (size_t)k;
+    const double r2 = gk[0] * gk[0] + gk[1] * gk[1] + gk[2] * gk[2];
+    if (!(fabs(r2 - 1.0) <= 1e-12)) atomicOr(status, kRmNotOnSphere);
+    if (e <= b || e > nadj) {
+      atomicOr(status, kRmAdjacency);
+      h[k] = 1.0;
+      continue;
+    }
+    double best = 1e300;
+    for (int64_t i = b; i < e; ++i) {
+      const int64_t j = adj[i];
+      if (j < 0 || j >= M || j == k) {
+        atomicOr(status, kRmAdjacency);
+        adj32[i] = k;
+        continue;
+      }
+      adj32[i] = (int32_t)j;
+      best = fmin(best, dist2(gk, g + 3 * (size_t)j));
+    }
+    h[k] = best < 1e300 ? sqrt(best) : 1.0;
+  }
+}
+
+// Grid points within `ring` edges of k, ascending, into S; returns the count or
+// -1 if there are more than kRemeshMaxStencil.
+__device__ int ring_set(int k, const int32_t *aoff, const int32_t *adj, int ring, int *S) {
+  int n = 1, lo = 0;
+  S[0] = k;
+  for (int r = 0; r < ring; ++r) {
+    const int hi = n;
+    for (int i = lo; i < hi; ++i) {
+      const int v = S[i];
+      for (int e = aoff[v]; e < aoff[v + 1]; ++e) {
+        const int w = adj[e];
+        bool seen = false;
+        for (int t = 0; t < n && !seen; ++t) seen = S[t] == w;
+        if (seen) continue;
+        if (n == kRemeshMaxStencil) return -1;
+        S[n++] = w;
+      }
+    }
+    lo = hi;
+  }
+  for (int i = 1; i < n; ++i) {
+    const int v = S[i];
+    int j = i - 1;
+    while (j >= 0 && S[j] > v) {
+      S[j + 1] = S[j];
+      --j;
+    }
+    S[j + 1] = v;
+  }
+  return n;
+}
+
+__global__ void stencil_count_kernel(const int32_t *aoff, const int32_t *adj, int M, int ring,
+                                     int32_t *cnt, int *status) {
+  int S[kRemeshMaxStencil];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) {
+    const int n = ring_set(k, aoff, adj, ring, S);
+    if (n < 0) atomicOr(status, kRmStencil);
+    cnt[k] = n < 0 ? 0 : n;
+  }
+}
+
+__global__ void stencil_fill_kernel(const int32_t *aoff, const int32_t *adj, int M, int ring,
+                                    const int32_t *soff, int32_t *sten) {
+  int S[kRemeshMaxStencil];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) {
+    const int n = ring_set(k, aoff, adj, ring, S);
+    if (n < 0) continue;
+    for (int i = 0; i < n; ++i) sten[soff[k] + i] = S[i];
+  }
+}
+
+// Step 1: nearest grid point of particle p by a greedy walk from grid point p,
+// in the order (squared chord, index): of two equally near grid points the one
+// with the smaller index wins (they are Delaunay neighbours, so the walk sees
+// both).
+__global__ void walk_kernel(const double *x, const double *g, const int32_t *aoff,
+                            const int32_t *adj, int M, int32_t *cell, int32_t *cnt, int *status) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < M; p += gridDim.x * blockDim.x) {
+    const double xp[3] = {x[3 * (size_t)p], x[3 * (size_t)p + 1], x[3 * (size_t)p + 2]};
+    int v = p;
+    double d = dist2(xp, g + 3 * (size_t)v);
+    int it = 0;
+    for (; it < kRemeshMaxWalk; ++it) {
+      int best = v;
+      double bd = d;
+      for (int e = aoff[v]; e < aoff[v + 1]; ++e) {
+        const int w = adj[e];
+        const double dw = dist2(xp, g + 3 * (size_t)w);
+        if (dw < bd || (dw == bd && w < best)) {
+          bd = dw;
+          best = w;
+        }
+      }
+      if (best == v) break;
+      v = best;
+      d = bd;
+    }
+    if (it == kRemeshMaxWalk) atomicOr(status, kRmWalk);
+    cell[p] = v;
+    atomicAdd(&cnt[v], 1);
+  }
+}
+
+__global__ void bucket_fill_kernel(const int32_t *cell, int M, const int32_t *boff,
+                                   int32_t *cursor, int32_t *bucket) {
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < M; p += gridDim.x * blockDim.x) {
+    const int c = cell[p];
+    bucket[boff[c] + atomicAdd(&cursor[c], 1)] = p;
+  }
+}
+
+__global__ void bucket_sort_kernel(const int32_t *boff, int M, int32_t *bucket, int *status) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < M; c += gridDim.x * blockDim.x) {
+    const int b = boff[c], e = boff[c + 1];
+    if (e - b > kRemeshMaxBucketSort) {
+      atomicOr(status, kRmBucket);
+      continue;
+    }
+    for (int i = b + 1; i < e; ++i) {
+      const int v = bucket[i];
+      int j = i - 1;
+      while (j >= b && bucket[j] > v) {
+        bucket[j + 1] = bucket[j];
+        --j;
+      }
+      bucket[j + 1] = v;
+    }
+  }
+}
+
+// Step 3: weighted quadratic least squares at every grid point.
+__global__ void __launch_bounds__(128) fit_kernel(const double *x, const double *f,
+                                                  const double *g, const double *h,
+                                                  const int32_t *soff, const int32_t *sten,
+                                                  const int32_t *boff, const int32_t *bucket,
+                                                  int M, double *out, int *status) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) {
+    const double gk[3] = {g[3 * (size_t)k], g[3 * (size_t)k + 1], g[3 * (size_t)k + 2]};
+    // e1 = a x g / |a x g| with a = e_z, or e_x near the poles; e2 = g x e1
+    double e1[3];
+    if (fabs(gk[2]) < 0.9) {
+      e1[0] = -gk[1];
+      e1[1] = gk[0];
+      e1[2] = 0.0;
+    } else {
+      e1[0] = 0.0;
+      e1[1] = -gk[2];
+      e1[2] = gk[1];
+    }
+    const double in = 1.0 / sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+    e1[0] *= in;
+    e1[1] *= in;
+    e1[2] *= in;
+    const double e2[3] = {gk[1] * e1[2] - gk[2] * e1[1], gk[2] * e1[0] - gk[0] * e1[2],
+                          gk[0] * e1[1] - gk[1] * e1[0]};
+    const double hk = h[k];
+    double A[21], b[6];  // packed lower triangle of sum w phi phi^T, sum w phi f
+#pragma unroll
+    for (int i = 0; i < 21; ++i) A[i] = 0.0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) b[i] = 0.0;
+    int n = 0;
+    for (int s = soff[k]; s < soff[k + 1]; ++s) {
+      const int c = sten[s];
+      for (int q = boff[c]; q < boff[c + 1]; ++q) {
+        const int p = bucket[q];
+        const double *xp = x + 3 * (size_t)p;
+        const double den = (xp[0] * gk[0] + xp[1] * gk[1] + xp[2] * gk[2]) * hk;
+        const double u = (xp[0] * e1[0] + xp[1] * e1[1] + xp[2] * e1[2]) / den;
+        const double v = (xp[0] * e2[0] + xp[1] * e2[1] + xp[2] * e2[2]) / den;
+        const double w = exp(-(u * u + v * v));
+        const double phi[6] = {1.0, u, v, u * u, u * v, v * v};
+        const double wf = w * f[p];
+        int t = 0;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+          const double wi = w * phi[i];
+#pragma unroll
+          for (int j = 0; j <= i; ++j) A[t++] += wi * phi[j];
+          b[i] += wf * phi[i];
+        }
+        ++n;
+      }
+    }
+    if (n < 6) {
+      atomicOr(status, kRmFit);
+      out[k] = 0.0;
+      continue;
+    }
+    // Cholesky A = L L^T in place (packed lower triangle), then L y = b, L^T c = y.
+    double amax = 0.0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) amax = fmax(amax, A[i * (i + 1) / 2 + i]);
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      double d = A[j * (j + 1) / 2 + j];
+#pragma unroll
+      for (int m = 0; m < j; ++m) d -= A[j * (j + 1) / 2 + m] * A[j * (j + 1) / 2 + m];
+      if (!(d > 1e-13 * amax)) ok = false;
+      const double ljj = sqrt(fmax(d, 1e-300));
+      A[j * (j + 1) / 2 + j] = ljj;
+#pragma unroll
+      for (int i = j + 1; i < 6; ++i) {
+        double s = A[i * (i + 1) / 2 + j];
+#pragma unroll
+        for (int m = 0; m < j; ++m) s -= A[i * (i + 1) / 2 + m] * A[j * (j + 1) / 2 + m];
+        A[i * (i + 1) / 2 + j] = s / ljj;
+      }
+    }
+    if (!ok) {
+      atomicOr(status, kRmFit);
+      out[k] = 0.0;
+      continue;
+    }
+    double y[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      double s = b[i];
+#pragma unroll
+      for (int m = 0; m < i; ++m) s -= A[i * (i + 1) / 2 + m] * y[m];
+      y[i] = s / A[i * (i + 1) / 2 + i];
+    }
+    double c[6];
+#pragma unroll
+    for (int i = 5; i >= 0; --i) {
+      double s = y[i];
+#pragma unroll
+      for (int m = i + 1; m < 6; ++m) s -= A[m * (m + 1) / 2 + i] * c[m];
+      c[i] = s / A[i * (i + 1) / 2 + i];
+    }
+    out[k] = c[0];
+  }
+}
+
+csfmm_status remesh_status(int st) {
+  if (st == 0) return CSFMM_OK;
+  set_error("remeshing failed (status 0x%x:%s%s%s%s%s%s)", st,
+            st & kRmAdjacency ? " bad neighbour lists" : "",
+            st & kRmStencil ? " stencil wider than 64 grid points" : "",
+            st & kRmWalk ? " nearest-point walk did not end" : "",
+            st & kRmBucket ? " too many particles in one cell" : "",
+            st & kRmFit ? " fewer than 6 particles or a singular fit in a stencil" : "",
+            st & kRmNotOnSphere ? " grid point off the unit sphere" : "");
+  return (st & kRmNotOnSphere) ? CSFMM_ERR_NOT_ON_SPHERE
+         : (st & (kRmAdjacency | kRmStencil)) ? CSFMM_ERR_INVALID_ARG
+                                               : CSFMM_ERR_DEVICE;
+}
+
+}  // namespace
+
+// Remeshing of moved particles x (particle p started at grid point p) carrying
+// f onto the grid; enqueued on st, then the status word is read (synchronous).
+csfmm_status remesh_impl(csfmm_remesh_grid G, const double *x, const double *f, double *f_out,
+                         cudaStream_t st) {
+  const int M = G->M;
+  const int grid = grid_for(M, 256, 152 * 8);
+  CSFMM_CUDA(cudaMemsetAsync(G->status, 0, sizeof(int), st));
+  CSFMM_CUDA(cudaMemsetAsync(G->cnt, 0, sizeof(int32_t) * (M + 1), st));
+  CSFMM_CUDA(cudaMemsetAsync(G->cursor, 0, sizeof(int32_t) * M, st));
+  walk_kernel<<<grid, 256, 0, st>>>(x, G->g, G->aoff, G->adj, M, G->cell, G->cnt, G->status);
+  CSFMM_CUDA(cudaGetLastError());
+  csfmm_status s = exclusive_scan_i32(G->cnt, G->boff, M + 1, nullptr, G->scan_tmp, st);
+  if (s != CSFMM_OK) return s;
+  bucket_fill_kernel<<<grid, 256, 0, st>>>(G->cell, M, G->boff, G->cursor, G->bucket);
+  bucket_sort_kernel<<<grid, 256, 0, st>>>(G->boff, M, G->bucket, G->status);
+  fit_kernel<<<grid_for(M, 128, 152 * 16), 128, 0, st>>>(x, f, G->g, G->h, G->soff, G->sten,
+                                                           G->boff, G->bucket, M, f_out,
+                                                           G->status);
+  CSFMM_CUDA(cudaGetLastError());
+  int hs = 0;
+  CSFMM_CUDA(cudaMemcpyAsync(&hs, G->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CSFMM_CUDA(cudaStreamSynchronize(st));
+  return remesh_status(hs);
+}
+
+int64_t remesh_grid_size(csfmm_remesh_grid G) { return G->M; }
+const double *remesh_grid_points(csfmm_remesh_grid G) { return G->g; }
+
+}  // namespace csfmm
+
+using namespace csfmm;
+
+extern "C" csfmm_status csfmm_remesh_grid_create(const double *grid, int64_t M,
+                                                 const int64_t *adj_offsets, const int64_t *adj,
+                                                 int ring, void *stream, csfmm_remesh_grid *out) {
+  if (!out) {
+    set_error("out is NULL");
+    return CSFMM_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  if (!grid || !adj_offsets || !adj || M < 7 || M >= ((int64_t)1 << 30) || ring < 1 ||
+      ring > kRemeshMaxRing) {
+    set_error("csfmm_remesh_grid_create: device arrays, 7 <= M < 2^30 and 1 <= ring <= %d "
+              "required", kRemeshMaxRing);
+    return CSFMM_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  int64_t nadj = 0;
+  CSFMM_CUDA(cudaMemcpyAsync(&nadj, adj_offsets + M, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  CSFMM_CUDA(cudaStreamSynchronize(st));
+  if (nadj < M || nadj >= ((int64_t)1 << 31)) {
+    set_error("csfmm_remesh_grid_create: adj_offsets[M] = %lld is not a neighbour count in "
+              "[M, 2^31)", (long long)nadj);
+    return CSFMM_ERR_INVALID_ARG;
+  }
+  auto *G = new csfmm_remesh_grid_s();
+  G->M = (int)M;
+  G->ring = ring;
+  G->nadj = nadj;
+  csfmm_status s = CSFMM_OK;
+  auto A = [&](auto **p, size_t n) {
+    if (s == CSFMM_OK) s = G->arena.alloc(p, n);
+  };
+  A(&G->g, 3 * (size_t)M);
+  A(&G->h, (size_t)M);
+  A(&G->aoff, (size_t)M + 1);
+  A(&G->adj, (size_t)nadj);
+  A(&G->soff, (size_t)M + 1);
+  A(&G->cell, (size_t)M);
+  A(&G->cnt, (size_t)M + 1);
+  A(&G->boff, (size_t)M + 1);
+  A(&G->cursor, (size_t)M);
+  A(&G->bucket, (size_t)M);
+  A(&G->scan_tmp, scan_tmp_elems((int)M + 1));
+  A(&G->status, 1);
+  auto fail = [&](csfmm_status e) {
+    cudaStreamSynchronize(st);
+    G->arena.release();
+    delete G;
+    return e;
+  };
+  if (s != CSFMM_OK) return fail(s);
+  const int gr = grid_for(M + 1, 256, 152 * 8);
+  cudaError_t e = cudaMemcpyAsync(G->g, grid, sizeof(double) * 3 * (size_t)M,
+                                  cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(G->status, 0, sizeof(int), st);
+  if (e != cudaSuccess) return fail(cuda_status(e, "csfmm_remesh_grid_create copy"));
+  adj_convert_kernel<<<gr, 256, 0, st>>>(adj_offsets, adj, (int)M, nadj, G->g, G->aoff, G->adj,
+                                         G->h, G->status);
+  int hs = 0;
+  e = cudaMemcpyAsync(&hs, G->status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(cuda_status(e, "adj_convert_kernel"));
+  if (hs) return fail(remesh_status(hs));
+  // offsets must increase: checked above per vertex (e > b) together with the range
+  stencil_count_kernel<<<gr, 256, 0, st>>>(G->aoff, G->adj, (int)M, ring, G->cnt, G->status);
+  int32_t total = 0;
+  e = cudaMemsetAsync(G->cnt + M, 0, sizeof(int32_t), st);
+  if (e != cudaSuccess) return fail(cuda_status(e, "cudaMemsetAsync"));
+  s = exclusive_scan_i32(G->cnt, G->soff, (int)M + 1, &total, G->scan_tmp, st);
+  if (s != CSFMM_OK) return fail(s);
+  e = cudaMemcpyAsync(&hs, G->status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(cuda_status(e, "stencil_count_kernel"));
+  if (hs) return fail(remesh_status(hs));
+  A(&G->sten, (size_t)total);
+  if (s != CSFMM_OK) return fail(s);
+  stencil_fill_kernel<<<gr, 256, 0, st>>>(G->aoff, G->adj, (int)M, ring, G->soff, G->sten);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(cuda_status(e, "stencil_fill_kernel"));
+  *out = G;
+  return CSFMM_OK;
+}
+
+extern "C" csfmm_status csfmm_remesh(csfmm_remesh_grid G, const double *x, const double *f,
+                                     double *f_out, void *stream) {
+  if (!G || !x || !f || !f_out) {
+    set_error("csfmm_remesh: NULL argument");
+    return CSFMM_ERR_INVALID_ARG;
+  }
+  return remesh_impl(G, x, f, f_out, (cudaStream_t)stream);
+}
+
+extern "C" csfmm_status csfmm_remesh_grid_destroy(csfmm_remesh_grid G) {
+  if (!G) return CSFMM_OK;
+  cudaDeviceSynchronize();
+  G->arena.release();
+  delete G;
+  return CSFMM_OK;
+}

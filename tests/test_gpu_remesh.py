@@ -1,0 +1,131 @@
+"""GPU parity of the remeshing (csfmm_remesh) and of the remeshed vortex-method
+step (csfmm_bve_step_remeshed) through the C ABI against the oracle
+(oracle/bve.py) on the same seeded inputs.
+
+Bars: remeshing and FP64 remeshed steps agree with the oracle to 1e-12 of
+max|zeta| (same cells and stencils, the same weighted fit solved by Cholesky
+on the GPU and by an SVD least-squares solver in the oracle); FP32-bulk
+remeshed steps to 1e-7.
+"""
+import numpy as np
+import pytest
+
+import oracle.bve as B
+from paper_2508_13550_gb300 import inputs as I
+from gpu_util import cuda_or_skip, dev
+
+pytestmark = pytest.mark.gpu
+
+OMEGA = I.BVE_OMEGA
+DT = I.BVE_DT
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return cuda_or_skip()
+
+
+@pytest.fixture(scope="module")
+def C():
+    from paper_2508_13550_gb300 import csfmm
+    return csfmm
+
+
+def grid(torch, C, level, ring=2, field="rh"):
+    x, z, A, off, nb = I.workload_bve(level, field, with_adjacency=True)
+    G = C.remesh_grid_create(dev(torch, x), dev(torch, off), dev(torch, nb), ring)
+    return G, x, z, A, off, nb
+
+
+@pytest.mark.parametrize("level,steps,ring", [(4, 1, 2), (3, 10, 2), (3, 4, 3), (1, 1, 2)])
+def test_remesh_matches_oracle(torch, C, level, steps, ring):
+    G, x, z, A, off, nb = grid(torch, C, level, ring)
+    xs, zs = B.integrate(x, z, A, DT, steps, OMEGA)
+    ref = B.remesh(x, off, nb, xs, zs, ring)
+    got = C.remesh(G, dev(torch, xs), dev(torch, zs)).cpu().numpy()
+    err = np.abs(got - ref).max() / np.abs(zs).max()
+    cells = (B.nearest_grid_point(x, xs) != np.arange(len(x))).sum()
+    print(f"\nlevel {level}, {steps} steps, ring {ring}: {cells} particles changed cell, "
+          f"max err {err:.2e}")
+    assert err < 1e-12
+
+
+CASES = [("direct", 0, None), ("CSFMM n=6, plan per step", 6, False),
+         ("CSFMM n=6, grid plan reused", 6, True)]
+
+
+@pytest.mark.parametrize("name,degree,reuse", CASES)
+def test_remeshed_step_fp64_matches_oracle(torch, C, name, degree, reuse):
+    G, x, z, A, off, nb = grid(torch, C, 4)
+    ref = B.remeshed_step(x, off, nb, z, A, DT, OMEGA, degree, 0.7, 144 if degree else None)
+    P = C.plan_create(dev(torch, x), C.KERNEL_BIOT_SAVART, degree, 0.7, 144) if reuse else None
+    got = C.bve_step_remeshed(G, dev(torch, z), dev(torch, A), DT, OMEGA, degree, 0.7, 144,
+                              C.FP64, grid_plan=P).cpu().numpy()
+    err = np.abs(got - ref).max() / np.abs(z).max()
+    print(f"\n{name}: max err {err:.2e}")
+    assert err < 1e-12
+
+
+def test_remeshed_trajectory_fp64_matches_oracle(torch, C):
+    G, x, z, A, off, nb = grid(torch, C, 3, field="gaussian")
+    zr = z.copy()
+    dz, dA = dev(torch, z), dev(torch, A)
+    for _ in range(10):
+        zr = B.remeshed_step(x, off, nb, zr, A, DT, OMEGA)
+        dz = C.bve_step_remeshed(G, dz, dA, DT, OMEGA, 0, precision=C.FP64)
+    err = np.abs(dz.cpu().numpy() - zr).max() / np.abs(z).max()
+    print(f"\n10 remeshed steps, Gaussian vortex, level 3: max err {err:.2e}")
+    assert err < 1e-11
+
+
+def test_remeshed_step_fp32_bulk(torch, C):
+    G, x, z, A, off, nb = grid(torch, C, 4)
+    ref = B.remeshed_step(x, off, nb, z, A, DT, OMEGA, 6, 0.7, 144)
+    got = C.bve_step_remeshed(G, dev(torch, z), dev(torch, A), DT, OMEGA, 6, 0.7, 144,
+                              C.FP32_BULK).cpu().numpy()
+    err = np.abs(got - ref).max() / np.abs(z).max()
+    print(f"\nFP32 bulk remeshed step: max err {err:.2e}")
+    assert err < 1e-7
+
+
+def test_in_place_remesh(torch, C):
+    G, x, z, A, off, nb = grid(torch, C, 3)
+    xs, zs = B.integrate(x, z, A, DT, 2, OMEGA)
+    dxs, dzs = dev(torch, xs), dev(torch, zs)
+    a = C.remesh(G, dxs, dzs)
+    C.remesh(G, dxs, dzs, out=dzs)
+    torch.cuda.synchronize()
+    assert torch.equal(a, dzs)
+
+
+def test_remesh_errors(torch, C):
+    x, z, A, off, nb = I.workload_bve(1, with_adjacency=True)
+    bad = nb.copy()
+    bad[5] = len(x)
+    with pytest.raises(C.CsfmmError) as e:
+        C.remesh_grid_create(dev(torch, x), dev(torch, off), dev(torch, bad))
+    assert e.value.status == 1
+    off_s = x.copy()
+    off_s[3] *= 1.01
+    with pytest.raises(C.CsfmmError) as e:
+        C.remesh_grid_create(dev(torch, off_s), dev(torch, off), dev(torch, nb))
+    assert e.value.status == 2
+    with pytest.raises(C.CsfmmError) as e:
+        C.remesh_grid_create(dev(torch, x), dev(torch, off), dev(torch, nb), ring=4)
+    assert e.value.status == 1
+    G = C.remesh_grid_create(dev(torch, x), dev(torch, off), dev(torch, nb))
+    # every particle at one point: each stencil's data are collinear, the fit is singular
+    same = np.repeat(x[:1], len(x), axis=0)
+    with pytest.raises(C.CsfmmError) as e:
+        C.remesh(G, dev(torch, same), dev(torch, z))
+    assert e.value.status == 8
+    # a plan of another kernel is refused as the grid plan
+    P = C.plan_create(dev(torch, x), C.KERNEL_LAPLACE, 3, 0.7, 8)
+    with pytest.raises(C.CsfmmError) as e:
+        C.bve_step_remeshed(G, dev(torch, z), dev(torch, A), DT, OMEGA, 3, 0.7, 8, C.FP64,
+                            grid_plan=P)
+    assert e.value.status == 1
+    # the grid still works after the errors
+    xs, zs = B.integrate(x, z, A, DT, 1, OMEGA)
+    got = C.remesh(G, dev(torch, xs), dev(torch, zs)).cpu().numpy()
+    assert np.abs(got - B.remesh(x, off, nb, xs, zs)).max() < 1e-12 * np.abs(zs).max()
