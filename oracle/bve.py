@@ -18,22 +18,22 @@ exact flow is tangent to the sphere, so this keeps the method's order).
 
 Remeshing (Sec. 12 remeshes at every step by local biquadratic interpolation,
 without further detail).  Reading: after a step the particles return to the
-fixed grid points g_k, which keep their areas, and the vorticity at g_k is
-read off a local quadratic fitted to the moved particles near g_k:
-  1. each moved particle belongs to the Voronoi cell of its nearest grid point
-     (of two equally near ones, the one with the smaller index);
-  2. the stencil of g_k is the set of grid points within `ring` edges of g_k in
-     the grid's triangulation (ring 2: g_k, its neighbours and theirs), and the
-     particles of their cells are the data;
-  3. in gnomonic coordinates of the tangent plane at g_k scaled by h_k, the
-     chord from g_k to its nearest neighbour in the triangulation,
-     (u, v) = (x.e1, x.e2) / ((x.g_k) h_k) for an orthonormal pair e1, e2
-     orthogonal to g_k, the quadratic c0 + c1 u + c2 v + c3 u^2 + c4 u v + c5 v^2
-     is fitted by least squares with weights exp(-(u^2 + v^2)), and its value c0
-     at g_k is the new zeta_k.
-The fit reproduces quadratics in (u, v) exactly and is third-order accurate
-for smooth fields; the tensor-product biquadratic of a structured grid has
-no stencil on the icosahedral grid.  The choice of e1, e2 does not change c0.
+fixed grid points g_k, which keep their areas, and the value at g_k of each
+carried field is read off a local quadratic fitted to the moved particles
+near g_k.  With h_k the chord from g_k to its nearest neighbour in the grid's
+triangulation, an orthonormal pair e1, e2 orthogonal to g_k, and a particle
+x with x.g_k > 0 in scaled gnomonic coordinates
+    (u, v) = (x.e1, x.e2) / ((x.g_k) h_k),   s^2 = u^2 + v^2,
+the data are the particles with s < S_C = 2.2, weighted by
+(1 - s^2/S_C^2)^4, and c0 + c1 u + c2 v + c3 u^2 + c4 u v + c5 v^2 is fitted by
+weighted least squares; the new value at g_k is c0.  The fit reproduces
+quadratics in (u, v) exactly, is third-order accurate for smooth fields, and
+-- the weights vanish smoothly at the edge of the data disc -- depends
+continuously on the particle positions (a remeshing whose data set jumped
+when a particle crossed a boundary would turn rounding-level asymmetries of
+the velocity into truncation-level ones).  The tensor-product biquadratic of
+a structured grid has no stencil on the icosahedral grid.  The choice of e1,
+e2 does not change c0.
 """
 from __future__ import annotations
 
@@ -45,9 +45,8 @@ from . import FMM, KERNEL_BIOT_SAVART, direct
 # the wrong sign, 2 the second RK4 stage weighted 1 instead of 2, 3 the third
 # stage started from the first stage's slope, 4 the last stage taken at
 # t + dt/2, 5 the particle areas dropped from the weights; in the remeshing
-# 6 orthographic instead of gnomonic coordinates, 7 a one-ring stencil, 8 the
-# particle's starting grid point as its cell, 9 the u v term dropped, 10 the
-# weights dropped.
+# 6 orthographic instead of gnomonic coordinates, 7 the h_k scaling dropped,
+# 8 the u v term dropped, 9 the weights dropped.
 _mutation = 0
 
 
@@ -114,37 +113,7 @@ def vorticity_error(zeta, zeta_exact, area):
     return float(np.sqrt(np.sum(d * d * A) / np.sum(np.asarray(zeta_exact) ** 2 * A)))
 
 
-def nearest_grid_point(grid, x):
-    """Index of the grid point nearest to each x (Voronoi cell membership).
-    Squared chords are formed as ((d0 d0 + d1 d1) + d2 d2) in FP64, and
-    equally near grid points go to the smaller index: symmetric inputs (the
-    icosahedral grid and RH wave share mirror symmetries) put particles
-    exactly on cell boundaries.  The four nearest candidates of a k-d tree are
-    compared in that arithmetic."""
-    from scipy.spatial import cKDTree
-    grid = np.asarray(grid, dtype=np.float64)
-    x = np.asarray(x, dtype=np.float64)
-    k = min(4, len(grid))
-    cand = cKDTree(grid).query(x, k=k)[1].reshape(len(x), k)
-    d = x[:, None, :] - grid[cand]
-    d2 = (d[..., 0] * d[..., 0] + d[..., 1] * d[..., 1]) + d[..., 2] * d[..., 2]
-    best = np.empty(len(x), dtype=np.int64)
-    for i in range(len(x)):
-        best[i] = min(zip(d2[i], cand[i]))[1]
-    return best
-
-
-def ring_stencil(offsets, nbrs, k: int, ring: int):
-    """Grid points within `ring` triangulation edges of grid point k, ascending."""
-    S = {int(k)}
-    frontier = {int(k)}
-    for _ in range(ring):
-        new = set()
-        for v in frontier:
-            new.update(int(j) for j in nbrs[offsets[v]:offsets[v + 1]])
-        frontier = new - S
-        S |= new
-    return sorted(S)
+S_C = 2.2  # radius of the data disc, in units of h_k
 
 
 def tangent_basis(g):
@@ -155,57 +124,75 @@ def tangent_basis(g):
     return e1, np.cross(g, e1)
 
 
-def remesh_members(grid, offsets, nbrs, x, ring: int = 2):
-    """For every grid point, the particles whose data enter its fit (steps 1-2
-    of the remeshing), as lists of particle indices."""
-    M = len(grid)
-    cell = np.arange(len(x)) if _mutation == 8 else nearest_grid_point(grid, x)
-    members = [[] for _ in range(M)]
-    for p, c in enumerate(cell):
-        members[c].append(p)
-    r = 1 if _mutation == 7 else ring
-    return [[p for s in ring_stencil(offsets, nbrs, k, r) for p in members[s]]
-            for k in range(M)]
-
-
 def neighbour_scale(grid, offsets, nbrs):
     """h_k: chord from each grid point to its nearest triangulation neighbour."""
     return np.array([min(np.linalg.norm(grid[j] - grid[k]) for j in nbrs[offsets[k]:offsets[k + 1]])
                      for k in range(len(grid))])
 
 
-def remesh(grid, offsets, nbrs, x, f, ring: int = 2, points=None):
-    """Vorticity at the grid points from the moved particles (x, f) by the
-    local quadratic fit described in the module header.  Returns [M], or the
-    values at the grid points listed in `points`."""
+def remesh_data(grid, h, x, k: int, tree=None):
+    """Particles entering the fit at grid point k: (indices, u, v, weights)."""
+    from scipy.spatial import cKDTree
+    g = grid[k]
+    hk = 1.0 if _mutation == 7 else h[k]
+    tree = tree if tree is not None else cKDTree(x)
+    # every particle with s < S_C lies within this chord of g_k
+    r = 2.0 * np.sin(0.5 * np.arctan(S_C * hk)) * (1.0 + 1e-9)
+    Q = np.asarray(tree.query_ball_point(g, r), dtype=np.int64)
+    X = x[Q]
+    e1, e2 = tangent_basis(g)
+    dot = X @ g
+    if _mutation == 6:
+        u, v = (X @ e1) / hk, (X @ e2) / hk
+    else:
+        den = np.where(dot > 0, dot * hk, 1.0)
+        u, v = (X @ e1) / den, (X @ e2) / den
+    s2 = u * u + v * v
+    keep = (dot > 0) & (s2 < S_C * S_C)
+    w = np.ones(int(keep.sum())) if _mutation == 9 else (1.0 - s2[keep] / (S_C * S_C)) ** 4
+    return Q[keep], u[keep], v[keep], w
+
+
+def remesh(grid, offsets, nbrs, x, f, points=None):
+    """Values at the grid points from the moved particles x carrying f ([M]
+    or [nfield, M]) by the local quadratic fit described in the module
+    header.  Returns f's shape with M replaced by the grid points (or by the
+    grid points listed in `points`)."""
+    from scipy.spatial import cKDTree
     grid = np.asarray(grid, dtype=np.float64)
     x = np.asarray(x, dtype=np.float64)
     f = np.asarray(f, dtype=np.float64)
-    Q = remesh_members(grid, offsets, nbrs, x, ring)
+    F = f.reshape(-1, f.shape[-1])
     h = neighbour_scale(grid, offsets, nbrs)
+    tree = cKDTree(x)
     ks = range(len(grid)) if points is None else points
-    out = np.empty(len(ks))
+    out = np.empty((len(F), len(ks)))
     for i, k in enumerate(ks):
-        g = grid[k]
-        e1, e2 = tangent_basis(g)
-        X = x[Q[k]]
-        if _mutation == 6:
-            u, v = (X @ e1) / h[k], (X @ e2) / h[k]
-        else:
-            den = (X @ g) * h[k]
-            u, v = (X @ e1) / den, (X @ e2) / den
+        Q, u, v, w = remesh_data(grid, h, x, k, tree)
         cols = [np.ones_like(u), u, v, u * u, u * v, v * v]
-        if _mutation == 9:
+        if _mutation == 8:
             cols[4] = np.zeros_like(u)
-        sw = np.ones_like(u) if _mutation == 10 else np.exp(-0.5 * (u * u + v * v))
-        c = np.linalg.lstsq(np.stack(cols, axis=1) * sw[:, None], f[Q[k]] * sw, rcond=None)[0]
-        out[i] = c[0]
-    return out
+        sw = np.sqrt(w)
+        c = np.linalg.lstsq(np.stack(cols, axis=1) * sw[:, None], (F[:, Q] * sw).T,
+                            rcond=None)[0]
+        out[:, i] = c[0]
+    return out[0] if f.ndim == 1 else out
 
 
 def remeshed_step(grid, offsets, nbrs, zeta, area, dt: float, omega: float, degree: int = 0,
-                  theta: float = 0.7, N0=None, ring: int = 2):
+                  theta: float = 0.7, N0=None, tracer=None):
     """One RK4 step from the grid points followed by remeshing onto them
-    (Sec. 12): returns the new vorticity at the grid points."""
+    (Sec. 12): returns the new vorticity at the grid points, or (vorticity,
+    tracer) with a passive tracer, which the particles carry unchanged
+    (dq/dt = 0 along paths) and which is remeshed with the vorticity."""
     x, z = rk4_step(grid, zeta, area, dt, omega, degree, theta, N0)
-    return remesh(grid, offsets, nbrs, x, z, ring)
+    if tracer is None:
+        return remesh(grid, offsets, nbrs, x, z)
+    out = remesh(grid, offsets, nbrs, x, np.stack([z, np.asarray(tracer, dtype=np.float64)]))
+    return out[0], out[1]
+
+
+def tracer_properties(q, area):
+    """Tracer mass m = sum q_i A_i and bound q_max = max |q_i| (Sec. 12)."""
+    q = np.asarray(q)
+    return float(np.sum(q * np.asarray(area))), float(np.max(np.abs(q)))
