@@ -848,6 +848,31 @@ def run_bve(args):
             row[tag] = e_zeta(zi.cpu().numpy(), xl, Al)
         conv.append(row)
         log("E_zeta remeshed", row)
+    # Table tracer_errors: tracer q = z, remeshed, FP64 CSFMM, Day 2
+    paper_tr = {}
+    with open(os.path.join(ROOT, "tests", "golden", "tracer_errors_table.txt")) as fh:
+        for line in fh:
+            line = line.split("#", 1)[0].split()
+            if line:
+                paper_tr[line[0]] = [float(v) for v in line[1:]]
+    tracer = []
+    for i, level in enumerate(range(5, args.bve_level + 1)):
+        xl, zl, Al, dxl, dzl, dAl, Gl = (x, z, A, dx, dz, dA, G) if level == args.bve_level \
+            else setup(level)
+        plan = Cs.plan_create(dxl, Cs.KERNEL_BIOT_SAVART, 6, 0.7, 144, precision=Cs.FP64,
+                              max_nrhs=1)
+        zi, qi = dzl, dxl[:, 2].contiguous()
+        for _ in range(2 * nsteps):
+            zi, qi = Cs.bve_step_remeshed(Gl, zi, dAl, dt, om, 6, 0.7, 144, Cs.FP64,
+                                          grid_plan=plan, tracer=qi)
+        q = qi.cpu().numpy()
+        row = {"level": level, "N": len(xl), "abs_mass": abs(float(np.sum(q * Al))),
+               "qmax_minus_1": float(np.abs(q).max() - 1.0)}
+        if i < 3:
+            row["paper_abs_mass"] = paper_tr["abs_mass"][i]
+            row["paper_qmax_minus_1"] = paper_tr["qmax_minus_1"][i]
+        tracer.append(row)
+        log("tracer Day 2", row)
     d64 = rows["direct_fp64"]["ms_per_step"]
     return {"metric": "BVE vortex-method RK4 step time (Sec. 12 setting)", "unit": "ms",
             "config": {"workload": "bve-rh-wave", "grid": f"icosahedral level {args.bve_level}",
@@ -856,6 +881,7 @@ def run_bve(args):
             "rows": rows,
             "speedup_over_direct_fp64": {k: d64 / v["ms_per_step"] for k, v in rows.items()},
             "E_zeta_remeshed_vs_N": conv,
+            "tracer_day2": tracer,
             "paper_context": "CSFMM 36x faster than direct summation at N = 163842 "
                              "(serial CPU, FP64)"}
 

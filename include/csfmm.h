@@ -369,49 +369,54 @@ csfmm_status csfmm_bve_step(const double *x, const double *zeta, const double *a
  * neighbour lists of their triangulation, which must be the Delaunay
  * triangulation of the points (the convex hull; the refined icosahedron is
  * one).  csfmm_remesh maps M moved particles, particle p having started at
- * g_p, carrying values f_p, to values at the grid points:
- *   1. a particle belongs to the Voronoi cell of its nearest grid point (a
- *      greedy walk on the triangulation from g_p);
- *   2. the stencil of g_k is the grid points within `ring` triangulation edges
- *      of g_k, its data the particles of their cells;
- *   3. with h_k the chord from g_k to its nearest neighbour and (u, v) the
- *      gnomonic coordinates of the tangent plane at g_k divided by h_k, the
- *      quadratic c0 + c1 u + c2 v + c3 u^2 + c4 uv + c5 v^2 is fitted by least
- *      squares with weights exp(-(u^2 + v^2)), and f_out[k] = c0.
- * The fit reproduces quadratics in (u, v) exactly and is third-order
- * accurate for smooth data.
+ * g_p, carrying values f_p, to values at the grid points: with h_k the chord
+ * from g_k to its nearest neighbour and (u, v) the gnomonic coordinates of a
+ * particle x (x.g_k > 0) in the tangent plane at g_k divided by h_k,
+ * s^2 = u^2 + v^2, the particles with s < 2.2 are fitted with weights
+ * (1 - s^2/2.2^2)^4 by c0 + c1 u + c2 v + c3 u^2 + c4 uv + c5 v^2 (least
+ * squares) and f_out[k] = c0.  The fit reproduces quadratics in (u, v)
+ * exactly, is third-order accurate for smooth data and depends continuously
+ * on the particle positions.  The particles are found through their nearest
+ * grid points (a greedy walk on the triangulation from g_p) and per-point
+ * stencils of whole triangulation rings sized when the grid is made.
  *   grid         device [M][3] FP64 unit vectors (copied), 7 <= M < 2^30
  *   adj_offsets  device int64 [M+1], adj device int64 [adj_offsets[M]]: the
  *                neighbours of g_k are adj[adj_offsets[k] .. adj_offsets[k+1])
  *                (read during the call only)
- *   ring         1..3 (2: 19 grid points around a hexagonal cell)
- * create is synchronous.  Errors: INVALID_ARG (bad neighbour lists, a stencil
- * wider than 64 grid points), NOT_ON_SPHERE, OUT_OF_MEMORY, CUDA. */
+ * create is synchronous.  Errors: INVALID_ARG (bad neighbour lists, a grid so
+ * irregular that 8 rings do not hold a data disc), NOT_ON_SPHERE,
+ * OUT_OF_MEMORY, CUDA. */
 typedef struct csfmm_remesh_grid_s *csfmm_remesh_grid;
 csfmm_status csfmm_remesh_grid_create(const double *grid, int64_t M, const int64_t *adj_offsets,
-                                      const int64_t *adj, int ring, void *stream,
-                                      csfmm_remesh_grid *out);
-/*   x device [M][3] moved particles, f device [M], f_out device [M] (may be f).
+                                      const int64_t *adj, void *stream, csfmm_remesh_grid *out);
+/*   x device [M][3] moved particles; f device [nfield][M] values carried by
+ *   them (1 <= nfield <= 64, e.g. vorticity and tracers; all fields share the
+ *   cells, stencils and fit matrix); f_out device [nfield][M], not
+ *   overlapping f (INVALID_ARG).
  * Allocates nothing; synchronises the stream before returning (it reads the
  * grid's status word).  Calls on one grid must not overlap.
  * Errors: INVALID_ARG, CUDA, DEVICE (a walk that did not end, a cell holding
- * more than 4096 particles, a stencil with fewer than 6 particles or a
+ * more than 4096 particles, a data disc with fewer than 6 particles or a
  * singular fit). */
-csfmm_status csfmm_remesh(csfmm_remesh_grid grid, const double *x, const double *f,
+csfmm_status csfmm_remesh(csfmm_remesh_grid grid, const double *x, const double *f, int nfield,
                           double *f_out, void *stream);
 csfmm_status csfmm_remesh_grid_destroy(csfmm_remesh_grid grid);
 
 /* One remeshed step of the vortex method (Sec. 12): csfmm_bve_step from the
  * grid points with vorticity zeta, then csfmm_remesh of the moved particles
- * onto the grid.  grid_plan, if not NULL, is a Biot-Savart plan built on the
- * grid's points (the first RK4 stage always starts there, so one plan serves
- * every step); NULL builds one per step like the other stages.
+ * onto the grid.  A passive tracer q (Sec. 12, dq/dt = 0 along particle
+ * paths) rides on the same particles and is remeshed with the vorticity.
+ * grid_plan, if not NULL, is a Biot-Savart plan built on the grid's points
+ * (the first RK4 stage always starts there, so one plan serves every step);
+ * NULL builds one per step like the other stages.
  *   zeta, area device [M]; zeta_out device [M] (may be zeta)
+ *   tracer, tracer_out device [M] (may be the same array), or both NULL
  * Synchronous.  Errors: those of csfmm_bve_step and csfmm_remesh. */
 csfmm_status csfmm_bve_step_remeshed(csfmm_remesh_grid grid, csfmm_plan grid_plan,
-                                     const double *zeta, const double *area, double dt,
-                                     double omega, int degree, double theta, int max_leaf,
-                                     int precision, double *zeta_out, void *stream);
+                                     const double *zeta, const double *tracer, const double *area,
+                                     double dt, double omega, int degree, double theta,
+                                     int max_leaf, int precision, double *zeta_out,
+                                     double *tracer_out, void *stream);
 
 /* Waits for the plan's work on stream and returns a deferred device status
  * (CSFMM_ERR_DEVICE / CSFMM_ERR_TIMEOUT) if a kernel reported one. */

@@ -124,10 +124,10 @@ _SIGS = {
     "csfmm_plan_stats": [_VP, ctypes.POINTER(Stats)],
     "csfmm_bve_step": [_VP, _VP, _VP, _I64, _D, _D, ctypes.c_int, _D, ctypes.c_int, ctypes.c_int,
                        _VP, _VP, _VP],
-    "csfmm_bve_step_remeshed": [_VP, _VP, _VP, _VP, _D, _D, ctypes.c_int, _D, ctypes.c_int,
-                                ctypes.c_int, _VP, _VP],
-    "csfmm_remesh_grid_create": [_VP, _I64, _VP, _VP, ctypes.c_int, _VP, ctypes.POINTER(_VP)],
-    "csfmm_remesh": [_VP, _VP, _VP, _VP, _VP],
+    "csfmm_bve_step_remeshed": [_VP, _VP, _VP, _VP, _VP, _D, _D, ctypes.c_int, _D, ctypes.c_int,
+                                ctypes.c_int, _VP, _VP, _VP],
+    "csfmm_remesh_grid_create": [_VP, _I64, _VP, _VP, _VP, ctypes.POINTER(_VP)],
+    "csfmm_remesh": [_VP, _VP, _VP, ctypes.c_int, _VP, _VP],
     "csfmm_remesh_grid_destroy": [_VP],
     "csfmm_autotune": [_VP, _I64, ctypes.c_int, ctypes.c_int, _D, _VP, ctypes.c_int, ctypes.c_int,
                        ctypes.c_char_p, _D, ctypes.POINTER(TuneResult)],
@@ -375,7 +375,7 @@ class RemeshGrid:
             self.handle = None
 
 
-def remesh_grid_create(grid, adj_offsets, adj, ring: int = 2, stream=None) -> RemeshGrid:
+def remesh_grid_create(grid, adj_offsets, adj, stream=None) -> RemeshGrid:
     """csfmm_remesh_grid_create: grid device [M,3] FP64, neighbour lists of
     its (Delaunay) triangulation as device int64 CSR (adj_offsets [M+1], adj)."""
     import torch
@@ -383,7 +383,7 @@ def remesh_grid_create(grid, adj_offsets, adj, ring: int = 2, stream=None) -> Re
     M = grid.shape[0]
     _check(load().csfmm_remesh_grid_create(_dev(grid, torch.float64), M,
                                            _dev(adj_offsets, torch.int64), _dev(adj, torch.int64),
-                                           int(ring), _stream(stream), ctypes.byref(h)))
+                                           _stream(stream), ctypes.byref(h)))
     return RemeshGrid(h, M, grid)
 
 
@@ -395,30 +395,36 @@ def remesh_grid_destroy(g: RemeshGrid):
 
 def remesh(g: RemeshGrid, x, f, out=None, stream=None):
     """csfmm_remesh: values at the grid points from moved particles x [M,3]
-    (particle p started at grid point p) carrying f [M]."""
+    (particle p started at grid point p) carrying f [M] or [nfield, M]."""
     import torch
+    nf = 1 if f.dim() == 1 else f.shape[0]
     if out is None:
-        out = torch.empty((g.M,), dtype=torch.float64, device=x.device)
-    _check(load().csfmm_remesh(g.handle, _dev(x, torch.float64), _dev(f, torch.float64),
+        out = torch.empty(f.shape, dtype=torch.float64, device=x.device)
+    _check(load().csfmm_remesh(g.handle, _dev(x, torch.float64), _dev(f, torch.float64), nf,
                                _dev(out, torch.float64), _stream(stream)))
     return out
 
 
 def bve_step_remeshed(g: RemeshGrid, zeta, area, dt: float, omega: float, degree: int = 6,
                       theta: float = 0.7, max_leaf: int = 0, precision: int = FP64,
-                      grid_plan: Plan | None = None, zeta_out=None, stream=None):
+                      grid_plan: Plan | None = None, tracer=None, zeta_out=None,
+                      tracer_out=None, stream=None):
     """csfmm_bve_step_remeshed: one RK4 step from the grid points followed by
-    remeshing; returns the vorticity at the grid points."""
+    remeshing; returns the vorticity at the grid points, or (vorticity,
+    tracer) when a tracer is given."""
     import torch
     if zeta_out is None:
         zeta_out = torch.empty((g.M,), dtype=torch.float64, device=zeta.device)
+    if tracer is not None and tracer_out is None:
+        tracer_out = torch.empty((g.M,), dtype=torch.float64, device=zeta.device)
     leaf = max_leaf if max_leaf > 0 else max(1, 4 * degree * degree)
-    _check(load().csfmm_bve_step_remeshed(g.handle, grid_plan.handle if grid_plan else None,
-                                          _dev(zeta, torch.float64), _dev(area, torch.float64),
-                                          float(dt), float(omega), int(degree), float(theta),
-                                          int(leaf), int(precision),
-                                          _dev(zeta_out, torch.float64), _stream(stream)))
-    return zeta_out
+    _check(load().csfmm_bve_step_remeshed(
+        g.handle, grid_plan.handle if grid_plan else None, _dev(zeta, torch.float64),
+        _dev(tracer, torch.float64) if tracer is not None else None, _dev(area, torch.float64),
+        float(dt), float(omega), int(degree), float(theta), int(leaf), int(precision),
+        _dev(zeta_out, torch.float64),
+        _dev(tracer_out, torch.float64) if tracer is not None else None, _stream(stream)))
+    return zeta_out if tracer is None else (zeta_out, tracer_out)
 
 
 def autotune(points, kernel_id: int, degree: int, theta: float, weights, precision: int = FP64,

@@ -137,12 +137,13 @@ extern "C" csfmm_status csfmm_bve_step(const double *x, const double *zeta, cons
 }
 
 extern "C" csfmm_status csfmm_bve_step_remeshed(csfmm_remesh_grid grid, csfmm_plan grid_plan,
-                                                const double *zeta, const double *area, double dt,
-                                                double omega, int degree, double theta,
-                                                int max_leaf, int precision, double *zeta_out,
-                                                void *stream) {
-  if (!grid || !zeta || !area || !zeta_out) {
-    set_error("csfmm_bve_step_remeshed: NULL argument");
+                                                const double *zeta, const double *tracer,
+                                                const double *area, double dt, double omega,
+                                                int degree, double theta, int max_leaf,
+                                                int precision, double *zeta_out,
+                                                double *tracer_out, void *stream) {
+  if (!grid || !zeta || !area || !zeta_out || (!tracer) != (!tracer_out)) {
+    set_error("csfmm_bve_step_remeshed: NULL argument (tracer and tracer_out go together)");
     return CSFMM_ERR_INVALID_ARG;
   }
   const int64_t M = remesh_grid_size(grid);
@@ -154,12 +155,26 @@ extern "C" csfmm_status csfmm_bve_step_remeshed(csfmm_remesh_grid grid, csfmm_pl
     return CSFMM_ERR_INVALID_ARG;
   }
   cudaStream_t st = (cudaStream_t)stream;
+  const int nf = tracer ? 2 : 1;
   double *buf = nullptr;
-  CSFMM_CUDA(cudaMallocAsync((void **)&buf, sizeof(double) * 4 * (size_t)M, st));
-  double *xm = buf, *zm = buf + 3 * (size_t)M;
-  csfmm_status s = bve_rk4(remesh_grid_points(grid), zeta, area, M, dt, omega, degree,
-                           theta, max_leaf, precision, grid_plan, xm, zm, st);
-  if (s == CSFMM_OK) s = remesh_impl(grid, xm, zm, zeta_out, st);
+  CSFMM_CUDA(cudaMallocAsync((void **)&buf, sizeof(double) * (3 + 2 * nf) * (size_t)M, st));
+  // moved positions; moved fields [nf][M] (vorticity, tracer); remeshed fields
+  double *xm = buf, *fm = buf + 3 * (size_t)M, *fo = fm + nf * (size_t)M;
+  csfmm_status s = bve_rk4(remesh_grid_points(grid), zeta, area, M, dt, omega, degree, theta,
+                           max_leaf, precision, grid_plan, xm, fm, st);
+  // the tracer is carried unchanged by the particles (dq/dt = 0 along paths)
+  if (s == CSFMM_OK && tracer) {
+    cudaError_t e = cudaMemcpyAsync(fm + M, tracer, sizeof(double) * M, cudaMemcpyDeviceToDevice,
+                                    st);
+    if (e != cudaSuccess) s = cuda_status(e, "cudaMemcpyAsync");
+  }
+  if (s == CSFMM_OK) s = remesh_impl(grid, xm, fm, nf, fo, st);
+  if (s == CSFMM_OK) {
+    cudaError_t e = cudaMemcpyAsync(zeta_out, fo, sizeof(double) * M, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && tracer)
+      e = cudaMemcpyAsync(tracer_out, fo + M, sizeof(double) * M, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) s = cuda_status(e, "cudaMemcpyAsync");
+  }
   cudaError_t e = cudaFreeAsync(buf, st);
   if (e != cudaSuccess && s == CSFMM_OK) s = cuda_status(e, "cudaFreeAsync");
   return s;

@@ -255,10 +255,10 @@ csfmm_status direct_impl(const double *points, int64_t N, int kernel_id, const d
                          int precision, cudaStream_t st);
 
 // Remeshing (remesh.cu): synchronous remeshing of particles x (particle p
-// started at grid point p) carrying f onto the grid, and the grid's size and
-// points ([M][3], device).
-csfmm_status remesh_impl(csfmm_remesh_grid G, const double *x, const double *f, double *f_out,
-                         cudaStream_t st);
+// started at grid point p) carrying nfield fields f [nfield][M] onto the grid,
+// and the grid's size and points ([M][3], device).
+csfmm_status remesh_impl(csfmm_remesh_grid G, const double *x, const double *f, int nfield,
+                         double *f_out, cudaStream_t st);
 int64_t remesh_grid_size(csfmm_remesh_grid G);
 const double *remesh_grid_points(csfmm_remesh_grid G);
 

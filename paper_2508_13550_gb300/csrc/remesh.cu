@@ -3,24 +3,34 @@
 // interpolation), and the remeshed RK4 step.
 //
 // After a step the particles return to the grid points g_k, which keep their
-// areas, and the new vorticity at g_k is the value there of a local quadratic
-// fitted to the moved particles:
-//   1. a particle belongs to the Voronoi cell of its nearest grid point (of
-//      two equally near ones, the one with the smaller index), found by a
-//      greedy walk on the grid's triangulation from the grid point the
-//      particle started at (on a Delaunay triangulation a vertex that is not
-//      the nearest always has a strictly nearer neighbour);
-//   2. the stencil of g_k is the grid points within `ring` triangulation edges
-//      of g_k, its data the particles of their cells;
-//   3. in gnomonic coordinates of the tangent plane at g_k divided by h_k (the
-//      chord from g_k to its nearest neighbour), u = x.e1 / (x.g_k h_k),
-//      v = x.e2 / (x.g_k h_k), the quadratic c0 + c1 u + c2 v + c3 u^2 + c4 u v
-//      + c5 v^2 is fitted by least squares with weights exp(-(u^2 + v^2)) and
-//      zeta_k = c0.
-// Work per remeshing: one walk per particle, a counting sort of the particles
-// by cell (buckets sorted by particle index so that every sum below runs in a
-// fixed order), and one 6x6 weighted normal-equation solve per grid point
-// (Cholesky, FP64; the scaled coordinates keep its condition number near 1e2).
+// areas, and the value at g_k of each carried field is that of a local
+// quadratic fitted to the moved particles near g_k.  With h_k the chord from
+// g_k to its nearest neighbour, e1, e2 orthonormal and orthogonal to g_k, and
+// a particle x with x.g_k > 0 in scaled gnomonic coordinates
+//     (u, v) = (x.e1, x.e2) / ((x.g_k) h_k),   s^2 = u^2 + v^2,
+// the data are the particles with s < kSc = 2.2, weighted by
+// (1 - s^2/kSc^2)^4, and c0 + c1 u + c2 v + c3 u^2 + c4 u v + c5 v^2 is fitted
+// by weighted least squares; the value is c0.  The weights vanish smoothly at
+// the edge of the data disc, so the result depends continuously on the
+// particle positions.
+//
+// Finding the data: every particle is put in the Voronoi cell of its nearest
+// grid point by a greedy walk on the grid's triangulation from the grid point
+// it started at (on a Delaunay triangulation a vertex that is not the nearest
+// always has a strictly nearer neighbour), and the particles are counting-
+// sorted by cell (buckets sorted by particle index, so every sum runs in a
+// fixed order).  A particle in the cell of grid point c is at least
+// |g_c - g_k|/2 from g_k (c is its nearest grid point), and the grid point
+// nearest to g_k outside the ring-R neighbourhood of g_k lies on ring R+1 (the
+// cells met by the segment from g_k to any outer grid point are no farther
+// from g_k).  So the cells of the smallest ring R whose next ring stays at
+// least twice the data-disc chord from g_k hold every datum of g_k; that
+// stencil is fixed per grid point when the grid is made.
+//
+// Work per remeshing: one walk per particle, the counting sort, and one
+// thread per grid point that filters the stencil's particles, accumulates the
+// 21 + 6 weighted normal-equation sums in FP64 and solves by an unrolled 6x6
+// Cholesky (the scaled coordinates keep its condition number near 1e2).
 #include <math.h>
 
 #include <cuda_runtime.h>
@@ -28,7 +38,7 @@
 #include "csfmm_internal.cuh"
 
 struct csfmm_remesh_grid_s {
-  int M = 0, ring = 2;
+  int M = 0, max_ring = 0;
   int64_t nadj = 0;
   csfmm::DeviceArena arena;
   double *g = nullptr;        // [M][3] grid points
@@ -51,15 +61,16 @@ namespace csfmm {
 
 namespace {
 
-constexpr int kRemeshMaxRing = 3;
-constexpr int kRemeshMaxStencil = 64;  // grid points in one stencil
+constexpr double kSc = 2.2;        // radius of the data disc in units of h_k
+constexpr int kRemeshMaxRing = 8;    // rings searched for a stencil
+constexpr int kRemeshMaxStencil = 384;  // grid points in one stencil search
 constexpr int kRemeshMaxWalk = 1 << 16;  // greedy steps of one particle (M < 2^31 vertices,
                                          // but a step of the remeshed method moves a few cells)
 constexpr int kRemeshMaxBucketSort = 4096;
 
 // Bits of the remeshing status word.
 constexpr int kRmAdjacency = 1;  // a neighbour index out of range or a vertex without neighbours
-constexpr int kRmStencil = 2;    // a stencil wider than kRemeshMaxStencil
+constexpr int kRmStencil = 2;    // no stencil within kRemeshMaxRing rings / kRemeshMaxStencil points
 constexpr int kRmWalk = 4;       // a walk that did not end within kRemeshMaxWalk steps
 constexpr int kRmBucket = 8;     // a cell holding more than kRemeshMaxBucketSort particles
 constexpr int kRmFit = 16;       // a stencil with fewer than 6 particles or a singular fit
@@ -109,13 +120,26 @@ __global__ void adj_convert_kernel(const int64_t *off, const int64_t *adj, int M
   }
 }
 
-// Grid points within `ring` edges of k, ascending, into S; returns the count or
-// -1 if there are more than kRemeshMaxStencil.
-__device__ int ring_set(int k, const int32_t *aoff, const int32_t *adj, int ring, int *S) {
+// Chord of the data disc's edge at g_k: s = kSc is the angle atan(kSc h_k)
+// from g_k; slightly enlarged so that rounding cannot drop a datum.
+__device__ __forceinline__ double data_chord(double hk) {
+  return 2.0 * sin(0.5 * atan(kSc * hk)) * (1.0 + 1e-9);
+}
+
+// Breadth-first rings around k in S (S[0] = k); stops after the smallest ring
+// R whose next ring lies at least twice the data chord away, then sorts
+// S[0..n) ascending.  Returns n (the stencil size) and R, or -1 when no ring
+// up to kRemeshMaxRing qualifies within kRemeshMaxStencil points.
+__device__ int stencil_set(int k, const double *g, const double *h, const int32_t *aoff,
+                           const int32_t *adj, int *S, int *ring_out) {
+  const double need = 2.0 * data_chord(h[k]);
+  const double *gk = g + 3 * (size_t)k;
   int n = 1, lo = 0;
   S[0] = k;
-  for (int r = 0; r < ring; ++r) {
+  for (int r = 0; r <= kRemeshMaxRing; ++r) {
+    // grow ring r + 1 from ring r = S[lo..hi)
     const int hi = n;
+    double dmin = 1e300;
     for (int i = lo; i < hi; ++i) {
       const int v = S[i];
       for (int e = aoff[v]; e < aoff[v + 1]; ++e) {
@@ -125,46 +149,58 @@ __device__ int ring_set(int k, const int32_t *aoff, const int32_t *adj, int ring
         if (seen) continue;
         if (n == kRemeshMaxStencil) return -1;
         S[n++] = w;
+        dmin = fmin(dmin, sqrt(dist2(gk, g + 3 * (size_t)w)));
       }
     }
-    lo = hi;
-  }
-  for (int i = 1; i < n; ++i) {
-    const int v = S[i];
-    int j = i - 1;
-    while (j >= 0 && S[j] > v) {
-      S[j + 1] = S[j];
-      --j;
+    if (dmin >= need) {
+      // rings 0..r qualify: S[0..hi) is the stencil
+      n = hi;
+      *ring_out = r;
+      for (int a = 1; a < n; ++a) {
+        const int v = S[a];
+        int b = a - 1;
+        while (b >= 0 && S[b] > v) {
+          S[b + 1] = S[b];
+          --b;
+        }
+        S[b + 1] = v;
+      }
+      return n;
     }
-    S[j + 1] = v;
+    lo = hi;  // (a ring with no new grid point has dmin = 1e300: the whole grid)
   }
-  return n;
+  return -1;
 }
 
-__global__ void stencil_count_kernel(const int32_t *aoff, const int32_t *adj, int M, int ring,
-                                     int32_t *cnt, int *status) {
+__global__ void stencil_count_kernel(const double *g, const double *h, const int32_t *aoff,
+                                     const int32_t *adj, int M, int32_t *cnt, int *max_ring,
+                                     int *status) {
   int S[kRemeshMaxStencil];
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) {
-    const int n = ring_set(k, aoff, adj, ring, S);
+    int r = 0;
+    const int n = stencil_set(k, g, h, aoff, adj, S, &r);
     if (n < 0) atomicOr(status, kRmStencil);
+    else atomicMax(max_ring, r);
     cnt[k] = n < 0 ? 0 : n;
   }
 }
 
-__global__ void stencil_fill_kernel(const int32_t *aoff, const int32_t *adj, int M, int ring,
-                                    const int32_t *soff, int32_t *sten) {
+__global__ void stencil_fill_kernel(const double *g, const double *h, const int32_t *aoff,
+                                    const int32_t *adj, int M, const int32_t *soff,
+                                    int32_t *sten) {
   int S[kRemeshMaxStencil];
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) {
-    const int n = ring_set(k, aoff, adj, ring, S);
+    int r = 0;
+    const int n = stencil_set(k, g, h, aoff, adj, S, &r);
     if (n < 0) continue;
     for (int i = 0; i < n; ++i) sten[soff[k] + i] = S[i];
   }
 }
 
-// Step 1: nearest grid point of particle p by a greedy walk from grid point p,
-// in the order (squared chord, index): of two equally near grid points the one
-// with the smaller index wins (they are Delaunay neighbours, so the walk sees
-// both).
+// Nearest grid point of particle p by a greedy walk from grid point p, in the
+// order (squared chord, index) so that the walk is deterministic; which of two
+// equally near grid points a particle gets does not change any result (both
+// are nearest, which is all the stencil bound uses).
 __global__ void walk_kernel(const double *x, const double *g, const int32_t *aoff,
                             const int32_t *adj, int M, int32_t *cell, int32_t *cnt, int *status) {
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < M; p += gridDim.x * blockDim.x) {
@@ -221,6 +257,9 @@ __global__ void bucket_sort_kernel(const int32_t *boff, int M, int32_t *bucket, 
 }
 
 // Step 3: weighted quadratic least squares at every grid point.
+// NF fields f[0..NF) (stride M) share the normal matrix; each gets its own
+// right-hand side and solve.
+template <int NF>
 __global__ void __launch_bounds__(128) fit_kernel(const double *x, const double *f,
                                                   const double *g, const double *h,
                                                   const int32_t *soff, const int32_t *sten,
@@ -246,37 +285,50 @@ __global__ void __launch_bounds__(128) fit_kernel(const double *x, const double 
     const double e2[3] = {gk[1] * e1[2] - gk[2] * e1[1], gk[2] * e1[0] - gk[0] * e1[2],
                           gk[0] * e1[1] - gk[1] * e1[0]};
     const double hk = h[k];
-    double A[21], b[6];  // packed lower triangle of sum w phi phi^T, sum w phi f
+    double A[21], b[NF][6];  // packed lower triangle of sum w phi phi^T, sum w phi f
 #pragma unroll
     for (int i = 0; i < 21; ++i) A[i] = 0.0;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) b[i] = 0.0;
+    for (int q = 0; q < NF; ++q)
+#pragma unroll
+      for (int i = 0; i < 6; ++i) b[q][i] = 0.0;
     int n = 0;
     for (int s = soff[k]; s < soff[k + 1]; ++s) {
       const int c = sten[s];
       for (int q = boff[c]; q < boff[c + 1]; ++q) {
         const int p = bucket[q];
         const double *xp = x + 3 * (size_t)p;
-        const double den = (xp[0] * gk[0] + xp[1] * gk[1] + xp[2] * gk[2]) * hk;
+        const double dot = xp[0] * gk[0] + xp[1] * gk[1] + xp[2] * gk[2];
+        if (!(dot > 0.0)) continue;
+        const double den = dot * hk;
         const double u = (xp[0] * e1[0] + xp[1] * e1[1] + xp[2] * e1[2]) / den;
         const double v = (xp[0] * e2[0] + xp[1] * e2[1] + xp[2] * e2[2]) / den;
-        const double w = exp(-(u * u + v * v));
+        const double s2 = u * u + v * v;
+        if (!(s2 < kSc * kSc)) continue;
+        const double om = 1.0 - s2 * (1.0 / (kSc * kSc));
+        const double om2 = om * om;
+        const double w = om2 * om2;
         const double phi[6] = {1.0, u, v, u * u, u * v, v * v};
-        const double wf = w * f[p];
         int t = 0;
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
           const double wi = w * phi[i];
 #pragma unroll
           for (int j = 0; j <= i; ++j) A[t++] += wi * phi[j];
-          b[i] += wf * phi[i];
+        }
+#pragma unroll
+        for (int q = 0; q < NF; ++q) {
+          const double wf = w * f[(size_t)q * M + p];
+#pragma unroll
+          for (int i = 0; i < 6; ++i) b[q][i] += wf * phi[i];
         }
         ++n;
       }
     }
     if (n < 6) {
       atomicOr(status, kRmFit);
-      out[k] = 0.0;
+#pragma unroll
+      for (int q = 0; q < NF; ++q) out[(size_t)q * M + k] = 0.0;
       continue;
     }
     // Cholesky A = L L^T in place (packed lower triangle), then L y = b, L^T c = y.
@@ -302,26 +354,30 @@ __global__ void __launch_bounds__(128) fit_kernel(const double *x, const double 
     }
     if (!ok) {
       atomicOr(status, kRmFit);
-      out[k] = 0.0;
+#pragma unroll
+      for (int q = 0; q < NF; ++q) out[(size_t)q * M + k] = 0.0;
       continue;
     }
-    double y[6];
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
-      double s = b[i];
+    for (int q = 0; q < NF; ++q) {
+      double y[6];
 #pragma unroll
-      for (int m = 0; m < i; ++m) s -= A[i * (i + 1) / 2 + m] * y[m];
-      y[i] = s / A[i * (i + 1) / 2 + i];
+      for (int i = 0; i < 6; ++i) {
+        double s = b[q][i];
+#pragma unroll
+        for (int m = 0; m < i; ++m) s -= A[i * (i + 1) / 2 + m] * y[m];
+        y[i] = s / A[i * (i + 1) / 2 + i];
+      }
+      double c[6];
+#pragma unroll
+      for (int i = 5; i >= 0; --i) {
+        double s = y[i];
+#pragma unroll
+        for (int m = i + 1; m < 6; ++m) s -= A[m * (m + 1) / 2 + i] * c[m];
+        c[i] = s / A[i * (i + 1) / 2 + i];
+      }
+      out[(size_t)q * M + k] = c[0];
     }
-    double c[6];
-#pragma unroll
-    for (int i = 5; i >= 0; --i) {
-      double s = y[i];
-#pragma unroll
-      for (int m = i + 1; m < 6; ++m) s -= A[m * (m + 1) / 2 + i] * c[m];
-      c[i] = s / A[i * (i + 1) / 2 + i];
-    }
-    out[k] = c[0];
   }
 }
 
@@ -329,10 +385,10 @@ csfmm_status remesh_status(int st) {
   if (st == 0) return CSFMM_OK;
   set_error("remeshing failed (status 0x%x:%s%s%s%s%s%s)", st,
             st & kRmAdjacency ? " bad neighbour lists" : "",
-            st & kRmStencil ? " stencil wider than 64 grid points" : "",
+            st & kRmStencil ? " no stencil holds the data disc (grid too irregular or too small)" : "",
             st & kRmWalk ? " nearest-point walk did not end" : "",
             st & kRmBucket ? " too many particles in one cell" : "",
-            st & kRmFit ? " fewer than 6 particles or a singular fit in a stencil" : "",
+            st & kRmFit ? " fewer than 6 particles or a singular fit in a data disc" : "",
             st & kRmNotOnSphere ? " grid point off the unit sphere" : "");
   return (st & kRmNotOnSphere) ? CSFMM_ERR_NOT_ON_SPHERE
          : (st & (kRmAdjacency | kRmStencil)) ? CSFMM_ERR_INVALID_ARG
@@ -343,8 +399,8 @@ csfmm_status remesh_status(int st) {
 
 // Remeshing of moved particles x (particle p started at grid point p) carrying
 // f onto the grid; enqueued on st, then the status word is read (synchronous).
-csfmm_status remesh_impl(csfmm_remesh_grid G, const double *x, const double *f, double *f_out,
-                         cudaStream_t st) {
+csfmm_status remesh_impl(csfmm_remesh_grid G, const double *x, const double *f, int nfield,
+                         double *f_out, cudaStream_t st) {
   const int M = G->M;
   const int grid = grid_for(M, 256, 152 * 8);
   CSFMM_CUDA(cudaMemsetAsync(G->status, 0, sizeof(int), st));
@@ -356,9 +412,18 @@ csfmm_status remesh_impl(csfmm_remesh_grid G, const double *x, const double *f, 
   if (s != CSFMM_OK) return s;
   bucket_fill_kernel<<<grid, 256, 0, st>>>(G->cell, M, G->boff, G->cursor, G->bucket);
   bucket_sort_kernel<<<grid, 256, 0, st>>>(G->boff, M, G->bucket, G->status);
-  fit_kernel<<<grid_for(M, 128, 152 * 16), 128, 0, st>>>(x, f, G->g, G->h, G->soff, G->sten,
-                                                           G->boff, G->bucket, M, f_out,
-                                                           G->status);
+  // fields in pairs (the second pair re-reads the stencil; the walk and sort are shared)
+  const int fg = grid_for(M, 128, 152 * 16);
+  for (int q = 0; q < nfield; q += 2) {
+    const double *fq = f + (size_t)q * M;
+    double *oq = f_out + (size_t)q * M;
+    if (nfield - q >= 2)
+      fit_kernel<2><<<fg, 128, 0, st>>>(x, fq, G->g, G->h, G->soff, G->sten, G->boff, G->bucket,
+                                        M, oq, G->status);
+    else
+      fit_kernel<1><<<fg, 128, 0, st>>>(x, fq, G->g, G->h, G->soff, G->sten, G->boff, G->bucket,
+                                        M, oq, G->status);
+  }
   CSFMM_CUDA(cudaGetLastError());
   int hs = 0;
   CSFMM_CUDA(cudaMemcpyAsync(&hs, G->status, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -375,16 +440,14 @@ using namespace csfmm;
 
 extern "C" csfmm_status csfmm_remesh_grid_create(const double *grid, int64_t M,
                                                  const int64_t *adj_offsets, const int64_t *adj,
-                                                 int ring, void *stream, csfmm_remesh_grid *out) {
+                                                 void *stream, csfmm_remesh_grid *out) {
   if (!out) {
     set_error("out is NULL");
     return CSFMM_ERR_INVALID_ARG;
   }
   *out = nullptr;
-  if (!grid || !adj_offsets || !adj || M < 7 || M >= ((int64_t)1 << 30) || ring < 1 ||
-      ring > kRemeshMaxRing) {
-    set_error("csfmm_remesh_grid_create: device arrays, 7 <= M < 2^30 and 1 <= ring <= %d "
-              "required", kRemeshMaxRing);
+  if (!grid || !adj_offsets || !adj || M < 7 || M >= ((int64_t)1 << 30)) {
+    set_error("csfmm_remesh_grid_create: device arrays and 7 <= M < 2^30 required");
     return CSFMM_ERR_INVALID_ARG;
   }
   cudaStream_t st = (cudaStream_t)stream;
@@ -398,7 +461,6 @@ extern "C" csfmm_status csfmm_remesh_grid_create(const double *grid, int64_t M,
   }
   auto *G = new csfmm_remesh_grid_s();
   G->M = (int)M;
-  G->ring = ring;
   G->nadj = nadj;
   csfmm_status s = CSFMM_OK;
   auto A = [&](auto **p, size_t n) {
@@ -436,7 +498,11 @@ extern "C" csfmm_status csfmm_remesh_grid_create(const double *grid, int64_t M,
   if (e != cudaSuccess) return fail(cuda_status(e, "adj_convert_kernel"));
   if (hs) return fail(remesh_status(hs));
   // offsets must increase: checked above per vertex (e > b) together with the range
-  stencil_count_kernel<<<gr, 256, 0, st>>>(G->aoff, G->adj, (int)M, ring, G->cnt, G->status);
+  // the scan of the stencil sizes reuses cnt; cursor[0] receives the largest ring
+  e = cudaMemsetAsync(G->cursor, 0, sizeof(int32_t), st);
+  if (e != cudaSuccess) return fail(cuda_status(e, "cudaMemsetAsync"));
+  stencil_count_kernel<<<gr, 256, 0, st>>>(G->g, G->h, G->aoff, G->adj, (int)M, G->cnt, G->cursor,
+                                           G->status);
   int32_t total = 0;
   e = cudaMemsetAsync(G->cnt + M, 0, sizeof(int32_t), st);
   if (e != cudaSuccess) return fail(cuda_status(e, "cudaMemsetAsync"));
@@ -448,7 +514,9 @@ extern "C" csfmm_status csfmm_remesh_grid_create(const double *grid, int64_t M,
   if (hs) return fail(remesh_status(hs));
   A(&G->sten, (size_t)total);
   if (s != CSFMM_OK) return fail(s);
-  stencil_fill_kernel<<<gr, 256, 0, st>>>(G->aoff, G->adj, (int)M, ring, G->soff, G->sten);
+  e = cudaMemcpyAsync(&G->max_ring, G->cursor, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return fail(cuda_status(e, "cudaMemcpyAsync"));
+  stencil_fill_kernel<<<gr, 256, 0, st>>>(G->g, G->h, G->aoff, G->adj, (int)M, G->soff, G->sten);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(cuda_status(e, "stencil_fill_kernel"));
@@ -457,12 +525,18 @@ extern "C" csfmm_status csfmm_remesh_grid_create(const double *grid, int64_t M,
 }
 
 extern "C" csfmm_status csfmm_remesh(csfmm_remesh_grid G, const double *x, const double *f,
-                                     double *f_out, void *stream) {
-  if (!G || !x || !f || !f_out) {
-    set_error("csfmm_remesh: NULL argument");
+                                     int nfield, double *f_out, void *stream) {
+  if (!G || !x || !f || !f_out || nfield < 1 || nfield > 64) {
+    set_error("csfmm_remesh: non-NULL arguments and 1 <= nfield <= 64 required");
     return CSFMM_ERR_INVALID_ARG;
   }
-  return remesh_impl(G, x, f, f_out, (cudaStream_t)stream);
+  const size_t bytes = sizeof(double) * (size_t)nfield * G->M;
+  const char *a = (const char *)f, *b = (const char *)f_out;
+  if (a < b + bytes && b < a + bytes) {
+    set_error("csfmm_remesh: f_out overlaps f (every output reads many inputs)");
+    return CSFMM_ERR_INVALID_ARG;
+  }
+  return remesh_impl(G, x, f, nfield, f_out, (cudaStream_t)stream);
 }
 
 extern "C" csfmm_status csfmm_remesh_grid_destroy(csfmm_remesh_grid G) {
