@@ -16,6 +16,7 @@ Functions
     .upward(w)                            proxy weights, Sec. 6
     .cells(), .lists(), .order(), .info() the plan's structures
   cheb_nodes(n), lagrange(n, u)           Sec. 4, Eq. (barycentric)
+  direct_targets, fmm_targets             separate target and source sets (Sec. 1)
 """
 from __future__ import annotations
 
@@ -294,6 +295,36 @@ class FMM:
             return out, {"pc": int(st[0]), "pp": int(st[1]), "evals": int(st[2]),
                          "margin": m.value}
         return out
+
+
+def _union(sources, targets, w):
+    src = np.asarray(sources, dtype=np.float64)
+    tgt = np.asarray(targets, dtype=np.float64)
+    w = np.atleast_2d(np.asarray(w, dtype=np.float64))
+    pts = np.ascontiguousarray(np.vstack([src, tgt]))
+    wu = np.ascontiguousarray(np.hstack([w, np.zeros((w.shape[0], len(tgt)))]))
+    return pts, wu, np.arange(len(src), len(src) + len(tgt))
+
+
+def direct_targets(sources, kernel: int, w, targets):
+    """phi(y_t) = sum_j K(y_t, x_j) w_j at target points that are not the
+    sources (Sec. 1: separate target and source sets; the targets distinct
+    from every source and from each other).  Computed as Eq. (nbodysum) over
+    the union of both sets with weight zero at the targets, read at the
+    targets: every added term is K(y_t, y_s) * 0.  Returns [nrhs, Nt, dim]."""
+    pts, wu, tg = _union(sources, targets, w)
+    return direct(pts, kernel, wu, tg)
+
+
+def fmm_targets(sources, targets, n: int, theta: float, N0: int, kernel: int, w,
+                cstc: bool = False):
+    """The CSFMM (or, with cstc, the CSTC) for separate targets on one tree
+    built over the sources followed by the targets (a cell splits while it
+    holds more than N0 points of both kinds together), the targets weighted
+    zero, read at the targets.  Returns [nrhs, Nt, dim]."""
+    pts, wu, tg = _union(sources, targets, w)
+    f = FMM(pts, n, theta, N0)
+    return f.evaluate_cstc(kernel, wu, tg) if cstc else f.evaluate(kernel, wu, tg)
 
 
 def rel_l2(a, b, areas=None, ref=None):
