@@ -128,6 +128,26 @@ csfmm_status csfmm_plan_create(const double *points, int64_t N, int kernel_id, i
                                double theta, int max_leaf, const csfmm_options *opt,
                                void *stream, csfmm_plan *out);
 
+/* Builds a plan for target points that are not the sources (Sec. 1: the
+ * scheme accommodates separate target and source sets): evaluations of it
+ * compute phi(y_t) = sum_j K(y_t, x_j) w_j at every target y_t.  One cubed-
+ * sphere tree holds the sources and the targets (a cell splits while it holds
+ * more than max_leaf points, sources and targets together); the sources carry the
+ * weights and the targets weight zero, so the dual traversal, upward pass,
+ * interactions and downward pass are those of csfmm_plan_create on the
+ * union, and the results are returned at the targets only.  The targets must
+ * be distinct from the sources and from each other (a coincident pair makes
+ * a singular kernel infinite, as in Eq. nbodysum).
+ *   sources device [Ns][3], targets device [Nt][3] FP64 unit vectors (copied)
+ *   other arguments as csfmm_plan_create
+ * Evaluations of the plan (csfmm_evaluate, _ws, _static, _host, _cstc) take
+ * weights [nrhs][Ns] and write out [nrhs][Nt][dim].
+ * Errors: those of csfmm_plan_create. */
+csfmm_status csfmm_plan_create_targets(const double *sources, int64_t Ns, const double *targets,
+                                       int64_t Nt, int kernel_id, int degree, double theta,
+                                       int max_leaf, const csfmm_options *opt, void *stream,
+                                       csfmm_plan *out);
+
 /* Evaluates phi for nrhs weight vectors with the plan's tree (Algorithm
  * "CSFMM": upward pass, PP/PC/CP/CC interactions, downward pass).
  * Asynchronous on stream.

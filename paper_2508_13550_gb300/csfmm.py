@@ -111,6 +111,8 @@ _VP, _I64, _I32, _D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_
 _SIGS = {
     "csfmm_plan_create": [_VP, _I64, ctypes.c_int, ctypes.c_int, _D, ctypes.c_int,
                           ctypes.POINTER(Options), _VP, ctypes.POINTER(_VP)],
+    "csfmm_plan_create_targets": [_VP, _I64, _VP, _I64, ctypes.c_int, ctypes.c_int, _D,
+                                  ctypes.c_int, ctypes.POINTER(Options), _VP, ctypes.POINTER(_VP)],
     "csfmm_evaluate": [_VP, _VP, ctypes.c_int, _VP, _VP],
     "csfmm_evaluate_cstc": [_VP, _VP, ctypes.c_int, _VP, _VP],
     "csfmm_evaluate_host": [_VP, _VP, ctypes.c_int, _VP, _VP],
@@ -204,9 +206,11 @@ def kernel_dim(kernel_id: int) -> int:
 class Plan:
     """Owns a csfmm_plan handle (destroyed with the object)."""
 
-    def __init__(self, handle, N, kernel_id, points):
+    def __init__(self, handle, N, kernel_id, points, nsrc=None, ntgt=None):
         self.handle = handle
-        self.N = N
+        self.N = N  # points in the tree (sources and separate targets)
+        self.nsrc = N if nsrc is None else nsrc
+        self.ntgt = N if ntgt is None else ntgt
         self.kernel_id = kernel_id
         self.dim = kernel_dim(kernel_id)
 
@@ -233,6 +237,22 @@ def plan_create(points, kernel_id: int, degree: int, theta: float, max_leaf: int
     return Plan(h, N, kernel_id, points)
 
 
+def plan_create_targets(sources, targets, kernel_id: int, degree: int, theta: float,
+                        max_leaf: int, precision: int = FP64, max_nrhs: int = 16,
+                        use_graphs: int = 0, rhs_chunk: int = 0, stream=None):
+    """csfmm_plan_create_targets: a plan whose evaluations take weights at the
+    sources [nrhs, Ns] and return the sum at separate targets [nrhs, Nt, dim]."""
+    import torch
+    opt = Options(precision, max_nrhs, use_graphs, rhs_chunk)
+    h = ctypes.c_void_p()
+    Ns, Nt = sources.shape[0], targets.shape[0]
+    _check(load().csfmm_plan_create_targets(_dev(sources, torch.float64), Ns,
+                                            _dev(targets, torch.float64), Nt, kernel_id, degree,
+                                            theta, max_leaf, ctypes.byref(opt), _stream(stream),
+                                            ctypes.byref(h)))
+    return Plan(h, Ns + Nt, kernel_id, None, nsrc=Ns, ntgt=Nt)
+
+
 def plan_destroy(plan: Plan):
     if plan.handle:
         _check(load().csfmm_plan_destroy(plan.handle))
@@ -244,7 +264,7 @@ def evaluate(plan: Plan, weights, out=None, stream=None):
     w = weights if weights.dim() == 2 else weights.unsqueeze(0)
     nrhs = w.shape[0]
     if out is None:
-        out = torch.empty((nrhs, plan.N, plan.dim), dtype=torch.float64, device=w.device)
+        out = torch.empty((nrhs, plan.ntgt, plan.dim), dtype=torch.float64, device=w.device)
     _check(load().csfmm_evaluate(plan.handle, _dev(w, torch.float64), nrhs,
                                  _dev(out, torch.float64), _stream(stream)))
     return out
@@ -257,7 +277,7 @@ def evaluate_cstc(plan: Plan, weights, out=None, stream=None):
     w = weights if weights.dim() == 2 else weights.unsqueeze(0)
     nrhs = w.shape[0]
     if out is None:
-        out = torch.empty((nrhs, plan.N, plan.dim), dtype=torch.float64, device=w.device)
+        out = torch.empty((nrhs, plan.ntgt, plan.dim), dtype=torch.float64, device=w.device)
     _check(load().csfmm_evaluate_cstc(plan.handle, _dev(w, torch.float64), nrhs,
                                       _dev(out, torch.float64), _stream(stream)))
     return out
@@ -274,7 +294,7 @@ def evaluate_static(plan: Plan, weights, out=None, stream=None):
     w = weights if weights.dim() == 2 else weights.unsqueeze(0)
     nrhs = w.shape[0]
     if out is None:
-        out = torch.empty((nrhs, plan.N, plan.dim), dtype=torch.float64, device=w.device)
+        out = torch.empty((nrhs, plan.ntgt, plan.dim), dtype=torch.float64, device=w.device)
     _check(load().csfmm_evaluate_static(plan.handle, _dev(w, torch.float64), nrhs,
                                         _dev(out, torch.float64), _stream(stream)))
     return out
@@ -286,7 +306,7 @@ def evaluate_host(plan: Plan, weights, out=None, stream=None):
         w = w[None]
     nrhs = w.shape[0]
     if out is None:
-        out = np.empty((nrhs, plan.N, plan.dim))
+        out = np.empty((nrhs, plan.ntgt, plan.dim))
     _check(load().csfmm_evaluate_host(plan.handle, ctypes.c_void_p(w.ctypes.data), nrhs,
                                       ctypes.c_void_p(out.ctypes.data), _stream(stream)))
     return out
@@ -307,7 +327,7 @@ def evaluate_ws(plan: Plan, ws, weights, out=None, stream=None):
     w = weights if weights.dim() == 2 else weights.unsqueeze(0)
     nrhs = w.shape[0]
     if out is None:
-        out = torch.empty((nrhs, plan.N, plan.dim), dtype=torch.float64, device=w.device)
+        out = torch.empty((nrhs, plan.ntgt, plan.dim), dtype=torch.float64, device=w.device)
     _check(load().csfmm_evaluate_ws(plan.handle, ws, _dev(w, torch.float64), nrhs,
                                     _dev(out, torch.float64), _stream(stream)))
     return out

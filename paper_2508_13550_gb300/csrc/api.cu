@@ -67,8 +67,8 @@ csfmm_status evaluate_chunks(Plan &pl, Workspace &W, const double *w, int nrhs, 
                              cudaStream_t st) {
   for (int r0 = 0; r0 < nrhs; r0 += W.max_nrhs) {
     int nr = nrhs - r0 < W.max_nrhs ? nrhs - r0 : W.max_nrhs;
-    csfmm_status s = evaluate_impl(pl, W, w + (size_t)r0 * pl.N, nr,
-                                   out + (size_t)r0 * pl.N * pl.dim, st);
+    csfmm_status s = evaluate_impl(pl, W, w + (size_t)r0 * pl.nsrc, nr,
+                                   out + (size_t)r0 * pl.ntgt * pl.dim, st);
     if (s != CSFMM_OK) return s;
   }
   return CSFMM_OK;
@@ -150,6 +150,9 @@ csfmm_status csfmm_plan_create(const double *points, int64_t N, int kernel_id, i
   Plan &pl = h->impl;
   cudaGetDevice(&pl.device);
   pl.N = N;
+  pl.nsrc = N;
+  pl.ntgt = N;
+  pl.tbase = 0;
   pl.kernel_id = kernel_id;
   pl.n = degree;
   pl.p = degree + 1;
@@ -203,6 +206,43 @@ csfmm_status csfmm_plan_create(const double *points, int64_t N, int kernel_id, i
   return CSFMM_OK;
 }
 
+csfmm_status csfmm_plan_create_targets(const double *sources, int64_t Ns, const double *targets,
+                                       int64_t Nt, int kernel_id, int degree, double theta,
+                                       int max_leaf, const csfmm_options *opt, void *stream,
+                                       csfmm_plan *out) {
+  if (!out || !sources || !targets || Ns < 1 || Nt < 1 || Ns + Nt >= ((int64_t)1 << 31)) {
+    set_error("csfmm_plan_create_targets: non-NULL arrays, Ns, Nt >= 1 and Ns + Nt < 2^31 "
+              "required");
+    if (out) *out = nullptr;
+    return CSFMM_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  double *u = nullptr;
+  CSFMM_CUDA(cudaMallocAsync((void **)&u, sizeof(double) * 3 * (size_t)(Ns + Nt), st));
+  cudaError_t e = cudaMemcpyAsync(u, sources, sizeof(double) * 3 * (size_t)Ns,
+                                  cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(u + 3 * (size_t)Ns, targets, sizeof(double) * 3 * (size_t)Nt,
+                        cudaMemcpyDeviceToDevice, st);
+  csfmm_status s = e == cudaSuccess ? CSFMM_OK : cuda_status(e, "cudaMemcpyAsync");
+  // one tree over sources then targets; the build synchronises the stream
+  if (s == CSFMM_OK)
+    s = csfmm_plan_create(u, Ns + Nt, kernel_id, degree, theta, max_leaf, opt, stream, out);
+  e = cudaFreeAsync(u, st);
+  if (s == CSFMM_OK && e != cudaSuccess) s = cuda_status(e, "cudaFreeAsync");
+  if (s != CSFMM_OK) {
+    if (*out) csfmm_plan_destroy(*out);
+    *out = nullptr;
+    return s;
+  }
+  Plan &pl = (*out)->impl;
+  pl.nsrc = Ns;
+  pl.ntgt = Nt;
+  pl.tbase = Ns;
+  return CSFMM_OK;
+}
+
 csfmm_status csfmm_evaluate(csfmm_plan plan, const double *weights, int nrhs, double *out,
                             void *stream) {
   csfmm_status s = check_eval_args(plan, weights, nrhs, out);
@@ -218,7 +258,7 @@ csfmm_status csfmm_evaluate_cstc(csfmm_plan plan, const double *weights, int nrh
   Workspace &W = *pl.ws;
   for (int r0 = 0; r0 < nrhs; r0 += W.max_nrhs) {
     const int nr = nrhs - r0 < W.max_nrhs ? nrhs - r0 : W.max_nrhs;
-    s = cstc_impl(pl, W, weights + (size_t)r0 * pl.N, nr, out + (size_t)r0 * pl.N * pl.dim,
+    s = cstc_impl(pl, W, weights + (size_t)r0 * pl.nsrc, nr, out + (size_t)r0 * pl.ntgt * pl.dim,
                   (cudaStream_t)stream);
     if (s != CSFMM_OK) return s;
   }
@@ -235,20 +275,20 @@ csfmm_status csfmm_evaluate_host(csfmm_plan plan, const double *weights, int nrh
   Workspace &W = *pl.ws;
   cudaStream_t st = (cudaStream_t)stream;
   if (!W.stage_w) {
-    csfmm_status s = W.arena.alloc(&W.stage_w, (size_t)W.max_nrhs * pl.N);
+    csfmm_status s = W.arena.alloc(&W.stage_w, (size_t)W.max_nrhs * pl.nsrc);
     if (s != CSFMM_OK) return s;
-    s = W.arena.alloc(&W.stage_out, (size_t)W.max_nrhs * pl.N * pl.dim);
+    s = W.arena.alloc(&W.stage_out, (size_t)W.max_nrhs * pl.ntgt * pl.dim);
     if (s != CSFMM_OK) return s;
     pl.stats.device_bytes = pl.arena.bytes + W.arena.bytes;
   }
   for (int r0 = 0; r0 < nrhs; r0 += W.max_nrhs) {
     int nr = nrhs - r0 < W.max_nrhs ? nrhs - r0 : W.max_nrhs;
-    CSFMM_CUDA(cudaMemcpyAsync(W.stage_w, weights + (size_t)r0 * pl.N,
-                               sizeof(double) * (size_t)nr * pl.N, cudaMemcpyHostToDevice, st));
+    CSFMM_CUDA(cudaMemcpyAsync(W.stage_w, weights + (size_t)r0 * pl.nsrc,
+                               sizeof(double) * (size_t)nr * pl.nsrc, cudaMemcpyHostToDevice, st));
     csfmm_status s = evaluate_impl(pl, W, W.stage_w, nr, W.stage_out, st);
     if (s != CSFMM_OK) return s;
-    CSFMM_CUDA(cudaMemcpyAsync(out + (size_t)r0 * pl.N * pl.dim, W.stage_out,
-                               sizeof(double) * (size_t)nr * pl.N * pl.dim, cudaMemcpyDeviceToHost,
+    CSFMM_CUDA(cudaMemcpyAsync(out + (size_t)r0 * pl.ntgt * pl.dim, W.stage_out,
+                               sizeof(double) * (size_t)nr * pl.ntgt * pl.dim, cudaMemcpyDeviceToHost,
                                st));
   }
   CSFMM_CUDA(cudaStreamSynchronize(st));

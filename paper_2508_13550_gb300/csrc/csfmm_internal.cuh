@@ -82,6 +82,7 @@ constexpr int kMaxNrhs = 64;
 // Read-only view of a plan passed to kernels by value.
 struct PlanView {
   int N, n, p, P, N0, ncells, dim, kernel_id;
+  int nsrc, ntgt, tbase;  // weights [nrhs][nsrc]; out [nrhs][ntgt][dim] at input index - tbase
   const double *x;       // [3][N]
   const int32_t *perm;   // [N]
   const double *La64, *Lb64;  // [N][p]
@@ -110,6 +111,11 @@ struct PlanView {
 struct Plan {
   int device = 0;
   int64_t N = 0;
+  // Separate targets (csfmm_plan_create_targets): the tree holds the sources
+  // (input indices [0, nsrc)) and then the targets ([tbase, tbase + ntgt));
+  // weights are given for the sources, results returned for the targets.  A
+  // plan of one point set has nsrc = ntgt = N, tbase = 0.
+  int64_t nsrc = 0, ntgt = 0, tbase = 0;
   int kernel_id = 0, n = 0, p = 0, P = 0, N0 = 0, precision = 0, dim = 1, max_nrhs = 16;
   int use_graphs = 0;
   int rhs_chunk = 16;   // FP32 bulk, scalar kernels: 16, 8 or 4

@@ -190,11 +190,11 @@ __global__ void __launch_bounds__(kCstcThreads) cstc_kernel(PlanView v, double t
       }
     }
   }
-  if (!act) return;
+  if (!act || v.perm[i] < v.tbase) return;
   double o[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) o[d] = F32 ? (double)hi[d] + (double)lo[d] : acc64[d];
-  double *dst = out + ((int64_t)r * N + v.perm[i]) * D;
+  double *dst = out + ((int64_t)r * v.ntgt + v.perm[i] - v.tbase) * D;
   if constexpr (KID == CSFMM_KERNEL_BIOT_SAVART) {
     dst[0] = kInv2Pi * (x1 * o[2] - x2 * o[1]);
     dst[1] = kInv2Pi * (x2 * o[0] - x0 * o[2]);

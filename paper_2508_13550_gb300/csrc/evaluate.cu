@@ -121,16 +121,17 @@ constexpr int kdim() {
 }
 
 // ---------------------------------------------------------------------------
-// gather: ws[r][i] = w[r][perm[i]]
+// gather: ws[r][i] = w[r][perm[i]] (zero for a target-only point, perm[i] >= nsrc)
 // ---------------------------------------------------------------------------
 __global__ void gather_kernel(const int32_t *perm, const double *w, double *ws, float *wsf, int N,
-                              int nrhs, int ld_ws) {
+                              int nrhs, int ld_ws, int nsrc) {
   int64_t total = (int64_t)N * nrhs;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
        q += (int64_t)gridDim.x * blockDim.x) {
     int r = (int)(q / N);
     int i = (int)(q - (int64_t)r * N);
-    double x = w[(int64_t)r * N + perm[i]];
+    const int j = perm[i];
+    double x = j < nsrc ? w[(int64_t)r * nsrc + j] : 0.0;
     ws[(int64_t)r * ld_ws + i] = x;
     if (wsf) wsf[(int64_t)r * ld_ws + i] = (float)x;
   }
@@ -668,7 +669,8 @@ __global__ void near_kernel(PlanView v, const int32_t *leaves, const double *ws,
 }
 
 // ---------------------------------------------------------------------------
-// L2P + finalize: out[r][perm[i]][d] = phi[r][i][d] + sum_m psi_leaf[m] La[i][m1] Lb[i][m2].
+// L2P + finalize: out[r][perm[i] - tbase][d] = phi[r][i][d] + sum_m psi_leaf[m] La[i][m1] Lb[i][m2]
+// for the targets (perm[i] >= tbase).
 // One block per leaf, one thread per point of a chunk; the chunk's Lagrange
 // rows are staged through shared memory once for every (r, d).
 // ---------------------------------------------------------------------------
@@ -698,7 +700,7 @@ __global__ void __launch_bounds__(kL2PThreads) l2p_kernel(PlanView v, const int3
         for (int u = threadIdx.x; u < P; u += kL2PThreads)
           sp[u] = psi[(((int64_t)c * ldr + r) * dim + d) * P + u];
         __syncthreads();
-        if (t < nj) {
+        if (t < nj && v.perm[i] >= v.tbase) {
           const Real *la = sLa + t * p, *lb = sLb + t * p;
           Real acc = 0;
           for (int m1 = 0; m1 < p; ++m1) {
@@ -707,7 +709,7 @@ __global__ void __launch_bounds__(kL2PThreads) l2p_kernel(PlanView v, const int3
             acc += la[m1] * s;
           }
           const int64_t oi = ((int64_t)r * v.N + i) * dim + d;
-          out[((int64_t)r * v.N + v.perm[i]) * dim + d] = phi[oi] + (double)acc;
+          out[((int64_t)r * v.ntgt + v.perm[i] - v.tbase) * dim + d] = phi[oi] + (double)acc;
         }
       }
   }
@@ -770,7 +772,7 @@ __global__ void __launch_bounds__(kL2PThreads) l2p_df_kernel(PlanView v, const i
           spl[u] = (float)(x - (double)hi);
         }
         __syncthreads();
-        if (t < nj) {
+        if (t < nj && v.perm[i] >= v.tbase) {
           const float *lah = sLa + t * p, *lal = sLal + t * p;
           const float *lbh = sLb + t * p, *lbl = sLbl + t * p;
           float S = 0.f, C = 0.f;
@@ -798,7 +800,7 @@ __global__ void __launch_bounds__(kL2PThreads) l2p_df_kernel(PlanView v, const i
             }
           }
           const int64_t oi = ((int64_t)r * v.N + i) * dim + d;
-          out[((int64_t)r * v.N + v.perm[i]) * dim + d] = phi[oi] + ((double)S + (double)C);
+          out[((int64_t)r * v.ntgt + v.perm[i] - v.tbase) * dim + d] = phi[oi] + ((double)S + (double)C);
         }
       }
   }
@@ -873,7 +875,7 @@ csfmm_status run_passes(Plan &pl, Workspace &W, const double *w, int nrhs, doubl
   } while (0)
   CSFMM_MARK(CSFMM_PHASE_GATHER);
   gather_kernel<<<grid_for((int64_t)N * nrhs, 256, 152 * 32), 256, 0, st>>>(
-      pl.perm, w, W.ws, sizeof(Real) == 4 ? W.wsf : nullptr, N, nrhs, N);
+      pl.perm, w, W.ws, sizeof(Real) == 4 ? W.wsf : nullptr, N, nrhs, N, (int)pl.nsrc);
   ++pl.launches;
   const int tb_prox = ((P + 31) / 32) * 32;
   CSFMM_MARK(CSFMM_PHASE_P2M);
@@ -978,7 +980,7 @@ csfmm_status run_cstc(Plan &pl, Workspace &W, const double *w, int nrhs, double 
   v.wtot = wtot;
   v.wtot_ld = ldr;
   gather_kernel<<<grid_for((int64_t)N * nrhs, 256, 152 * 32), 256, 0, st>>>(
-      pl.perm, w, W.ws, sizeof(Real) == 4 ? W.wsf : nullptr, N, nrhs, N);
+      pl.perm, w, W.ws, sizeof(Real) == 4 ? W.wsf : nullptr, N, nrhs, N, (int)pl.nsrc);
   const int tb_prox = ((P + 31) / 32) * 32;
   const int tb_p2m = tb_prox < 64 ? 64 : tb_prox;
   for (int r0 = 0; r0 < nrhs; r0 += kRB) {
@@ -1130,15 +1132,25 @@ csfmm_status capture(Plan &pl, Workspace &W, const double *w, int nrhs, double *
 
 // Points the captured gather and L2P nodes at new caller buffers; the other
 // arguments are rebuilt from the plan and workspace exactly as at capture.
+// The argument arrays must list every kernel parameter: the checks below tie
+// their lengths to the kernels' signatures.
+template <class... A>
+constexpr int arity(void (*)(A...)) {
+  return (int)sizeof...(A);
+}
+static_assert(arity(gather_kernel) == 8, "retarget: gather_kernel arguments");
+static_assert(arity(l2p_kernel<double>) == 8 && arity(l2p_df_kernel<7>) == 8,
+              "retarget: L2P arguments");
 csfmm_status retarget(Plan &pl, Workspace &W, GraphEntry &g, const double *w, double *out) {
   const int N = (int)pl.N;
   {
     const int32_t *perm = pl.perm;
     double *ws = W.ws;
     float *wsf = pl.precision == CSFMM_FP64 ? nullptr : W.wsf;
-    int nrhs = g.nrhs, ld = N, n = N;
+    int nrhs = g.nrhs, ld = N, n = N, nsrc = (int)pl.nsrc;
+    // one entry per parameter of gather_kernel, in order
     void *args[] = {(void *)&perm, (void *)&w, (void *)&ws, (void *)&wsf, (void *)&n,
-                    (void *)&nrhs, (void *)&ld};
+                    (void *)&nrhs, (void *)&ld, (void *)&nsrc};
     cudaKernelNodeParams kp = g.gather_params;
     kp.kernelParams = args;
     kp.extra = nullptr;

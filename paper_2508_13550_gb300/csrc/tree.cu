@@ -809,6 +809,7 @@ PlanView Plan::view() const {
   PlanView v{};
   v.N = (int)N; v.n = n; v.p = p; v.P = P; v.N0 = N0; v.ncells = ncells; v.dim = dim;
   v.kernel_id = kernel_id;
+  v.nsrc = (int)nsrc; v.ntgt = (int)ntgt; v.tbase = (int)tbase;
   v.x = x; v.perm = perm; v.La64 = La64; v.Lb64 = Lb64; v.La32 = La32; v.Lb32 = Lb32;
   v.La32lo = La32lo; v.Lb32lo = Lb32lo;
   v.off32 = off32;
