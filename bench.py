@@ -60,9 +60,9 @@ def log(*a):
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2508_13550_gb300", "csrc", f)
                   for f in ("interact32.cu", "fp32_math.cuh")]
 TRAFFIC_PER_EVAL = {
-    "source_sha256": "7ddfdbcc98e51cdf",
-    "pp_sym_kernel": (35.019008e6 + 129.817856e6) / 6083051520,
-    "near32x2_kernel": (233.308416e6 + 12.380160e6) / 3743870976,
+    "source_sha256": "1d6bbb0db6146c45",
+    "pp_sym_kernel": (34.958848e6 + 129.207808e6) / 6083051520,
+    "near32x2_kernel": (233.088000e6 + 12.340992e6) / 3743870976,
     "far32x2_kernel": 18.471680e6 / 1503908016,
 }
 
