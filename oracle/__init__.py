@@ -11,7 +11,8 @@ multiply-add.  This module only marshals numpy arrays through ctypes.
 
 Functions
   direct(pts, kernel, w, targets=None)   Eq. (nbodysum), i = j omitted
-  FMM(pts, n, theta, N0)                  tree + lists (Sec. 3, Sec. 8)
+  FMM(pts, n, theta, N0, shrink=False)    tree + lists (Sec. 3, Sec. 8); with shrink
+                                          the cells' boxes bound their points (Sec. 3)
     .evaluate(kernel, w)                  Algorithm "CSFMM"
     .upward(w)                            proxy weights, Sec. 6
     .cells(), .lists(), .order(), .info() the plan's structures
@@ -69,7 +70,7 @@ def _load():
         lib.oracle_direct.argtypes = [P(d), i64, ctypes.c_int, P(d), ctypes.c_int,
                                       P(i64), i64, P(d)]
         lib.oracle_direct.restype = ctypes.c_int
-        lib.oracle_fmm_create.argtypes = [P(d), i64, ctypes.c_int, d, ctypes.c_int]
+        lib.oracle_fmm_create.argtypes = [P(d), i64, ctypes.c_int, d, ctypes.c_int, ctypes.c_int]
         lib.oracle_fmm_create.restype = vp
         lib.oracle_fmm_destroy.argtypes = [vp]
         lib.oracle_fmm_info.argtypes = [vp, P(i64), P(d)]
@@ -171,14 +172,15 @@ def lagrange(n: int, u: float):
 class FMM:
     """Tree and interaction lists of the oracle CSFMM for a point set."""
 
-    def __init__(self, pts, n: int, theta: float, N0: int):
+    def __init__(self, pts, n: int, theta: float, N0: int, shrink: bool = False):
         self._lib = _load()
         self.pts = np.ascontiguousarray(np.asarray(pts, dtype=np.float64))
         self.N = len(self.pts)
         self.n, self.theta, self.N0 = int(n), float(theta), int(N0)
+        self.shrink = bool(shrink)
         self.P = (self.n + 1) ** 2
         self._h = self._lib.oracle_fmm_create(_ptr(self.pts), self.N, self.n,
-                                              self.theta, self.N0)
+                                              self.theta, self.N0, int(self.shrink))
         if not self._h:
             raise ValueError("oracle_fmm_create: invalid arguments")
 
@@ -317,13 +319,13 @@ def direct_targets(sources, kernel: int, w, targets):
 
 
 def fmm_targets(sources, targets, n: int, theta: float, N0: int, kernel: int, w,
-                cstc: bool = False):
+                cstc: bool = False, shrink: bool = False):
     """The CSFMM (or, with cstc, the CSTC) for separate targets on one tree
     built over the sources followed by the targets (a cell splits while it
     holds more than N0 points of both kinds together), the targets weighted
     zero, read at the targets.  Returns [nrhs, Nt, dim]."""
     pts, wu, tg = _union(sources, targets, w)
-    f = FMM(pts, n, theta, N0)
+    f = FMM(pts, n, theta, N0, shrink)
     return f.evaluate_cstc(kernel, wu, tg) if cstc else f.evaluate(kernel, wu, tg)
 
 

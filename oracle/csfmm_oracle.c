@@ -27,9 +27,15 @@
  *   - A cell splits iff it holds more than N0 points; "big" (|C| > N0) means
  *     "has children", "small" means "leaf".  Empty children are dropped.
  *   - Children split their parent's (xi, eta) square at its midpoint; a
- *     coordinate on the midpoint goes to the upper child.  No shrinking.
- *   - Centre = sphere image of the (xi, eta) midpoint; radius = largest chord
- *     from the centre to the four corners; R = chord between centres.
+ *     coordinate on the midpoint goes to the upper child.
+ *   - A cell's box is its dyadic square, or, when the plan shrinks cells
+ *     (Sec. 3: cells shrunk to bound their particles), the smallest box of
+ *     fine cells holding its points, each edge moved out to an even fine
+ *     coordinate so that the midpoint is a table entry.  The Chebyshev grid
+ *     spans the box (separate half-widths along xi and eta); a child's nodes
+ *     are placed in its parent's coordinates from the boxes' integer edges.
+ *   - Centre = sphere image of the box midpoint; radius = largest chord from
+ *     the centre to the four corners; R = chord between centres.
  *   - Well separated iff (r_t + r_s) < MAC * R.  In Algorithm "CSFMM" the
  *     PC / CP / CC choice is read as exclusive; when not well separated and
  *     at least one cluster is big, the shallower cluster is split (equal
@@ -302,7 +308,11 @@ typedef struct {
   int child[4];       /* by quadrant c = 2*bit_b + bit_a; -1 if empty */
   int nchild;
   double c[3], r;
-  double xi_mid, eta_mid, half; /* angles of the (xi, eta) midpoint, half-width */
+  /* the cell's box in fine face coordinates (even edges): a in [alo, ahi],
+   * b in [blo, bhi]; the dyadic square of the cell, or with shrinking the
+   * smallest such box around its points */
+  int64_t alo, ahi, blo, bhi;
+  double xi_mid, eta_mid, hx, hy; /* box midpoint and half-widths in angle */
 } ocell;
 
 typedef struct { int t, s; } opair;
@@ -310,6 +320,7 @@ typedef struct { int t, s; } opair;
 typedef struct {
   int64_t N;
   int n, p, P, N0;
+  int shrink;       /* boxes shrunk to bound their points */
   double theta;
   double *x;        /* points in sorted order [N][3] */
   int64_t *order;   /* sorted position -> input index */
@@ -344,24 +355,34 @@ static int okey_cmp(const void *A, const void *B) {
   return a->idx < b->idx ? -1 : (a->idx > b->idx);
 }
 
+/* Geometry of a cell from its box: centre at the box midpoint (an integer
+ * fine coordinate: the edges are even), radius the largest chord to the four
+ * corners, midpoint angles and half-widths for the Chebyshev grid. */
 static void cell_geometry(oplan *pl, ocell *C) {
   const double *T = tan_table();
-  int sh = OR_D - C->level;
-  int64_t alo = C->ia << sh, ahi = (C->ia + 1) << sh, amid = (2 * C->ia + 1) << (sh - 1);
-  int64_t blo = C->ib << sh, bhi = (C->ib + 1) << sh, bmid = (2 * C->ib + 1) << (sh - 1);
+  int64_t amid = (C->alo + C->ahi) / 2, bmid = (C->blo + C->bhi) / 2;
   face_point(C->face, T[amid], T[bmid], C->c);
   double corner[3];
   double r = 0.0, d;
-  face_point(C->face, T[alo], T[blo], corner); d = chord(corner, C->c); if (d > r) r = d;
-  face_point(C->face, T[ahi], T[blo], corner); d = chord(corner, C->c); if (d > r) r = d;
-  face_point(C->face, T[alo], T[bhi], corner); d = chord(corner, C->c); if (d > r) r = d;
-  face_point(C->face, T[ahi], T[bhi], corner); d = chord(corner, C->c); if (d > r) r = d;
+  face_point(C->face, T[C->alo], T[C->blo], corner); d = chord(corner, C->c); if (d > r) r = d;
+  face_point(C->face, T[C->ahi], T[C->blo], corner); d = chord(corner, C->c); if (d > r) r = d;
+  face_point(C->face, T[C->alo], T[C->bhi], corner); d = chord(corner, C->c); if (d > r) r = d;
+  face_point(C->face, T[C->ahi], T[C->bhi], corner); d = chord(corner, C->c); if (d > r) r = d;
   C->r = r;
-  double h = ldexp(OR_HALF_PI, -(C->level + 1));
-  C->half = h;
-  C->xi_mid = (double)(2 * C->ia + 1) * h - OR_QUARTER_PI;
-  C->eta_mid = (double)(2 * C->ib + 1) * h - OR_QUARTER_PI;
+  double H = ldexp(OR_HALF_PI, -OR_D);      /* angle of one fine step */
+  double H2 = ldexp(OR_HALF_PI, -(OR_D + 1));
+  C->hx = (double)(C->ahi - C->alo) * H2;
+  C->hy = (double)(C->bhi - C->blo) * H2;
+  C->xi_mid = (double)amid * H - OR_QUARTER_PI;
+  C->eta_mid = (double)bmid * H - OR_QUARTER_PI;
   (void)pl;
+}
+
+/* Position of child node s in the parent's interpolation coordinate along
+ * one axis, from the boxes in fine units: (2 (mid_c - mid_p) + w_c s) / w_p. */
+static double child_node(int64_t clo, int64_t chi, int64_t plo, int64_t phi, double s) {
+  double dm = (double)((clo + chi) - (plo + phi));
+  return (dm + (double)(chi - clo) * s) / (double)(phi - plo);
 }
 
 /* Dual tree traversal, Algorithm "CSFMM" (Sec. 8). */
@@ -400,11 +421,12 @@ void oracle_fmm_destroy(void *h);
 
 /* Builds the tree (Sec. 3), the cell geometry and proxies (Sec. 4) and the
  * interaction lists (Sec. 8).  Returns NULL on invalid input. */
-void *oracle_fmm_create(const double *pts, int64_t N, int n, double theta, int N0) {
+void *oracle_fmm_create(const double *pts, int64_t N, int n, double theta, int N0, int shrink) {
   if (!pts || N < 1 || n < 1 || n > 64 || !(theta > 0.0) || N0 < 1) return NULL;
   const double *T = tan_table();
   oplan *pl = (oplan *)calloc(1, sizeof(oplan));
   pl->N = N; pl->n = n; pl->p = n + 1; pl->P = (n + 1) * (n + 1); pl->N0 = N0;
+  pl->shrink = shrink != 0;
   pl->theta = theta;
   pl->margin = INFINITY;
 
@@ -427,9 +449,13 @@ void *oracle_fmm_create(const double *pts, int64_t N, int n, double theta, int N
   pl->order = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
   pl->x = (double *)malloc(sizeof(double) * 3 * (size_t)N);
   uint64_t *skey = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)N);
+  int64_t *sqa = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
+  int64_t *sqb = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
   for (int64_t i = 0; i < N; ++i) {
     pl->order[i] = keys[i].idx;
     skey[i] = keys[i].key;
+    sqa[i] = qa[keys[i].idx];
+    sqb[i] = qb[keys[i].idx];
     memcpy(pl->x + 3 * i, pts + 3 * keys[i].idx, 3 * sizeof(double));
   }
   free(keys);
@@ -485,7 +511,27 @@ void *oracle_fmm_create(const double *pts, int64_t N, int n, double theta, int N
   pl->level_begin[nlev] = nc;
   pl->ncells = nc;
   pl->nlevels = nlev;
-  free(skey); free(qa); free(qb); free(fc);
+  /* boxes: the dyadic square, or (shrinking) the fine cells of the points
+   * widened to even edges */
+  for (int ci = 0; ci < nc; ++ci) {
+    ocell *C = &pl->cells[ci];
+    int sh = OR_D - C->level;
+    C->alo = C->ia << sh; C->ahi = (C->ia + 1) << sh;
+    C->blo = C->ib << sh; C->bhi = (C->ib + 1) << sh;
+    if (pl->shrink) {
+      int64_t amin = INT64_MAX, amax = -1, bmin = INT64_MAX, bmax = -1;
+      for (int64_t i = C->begin; i < C->end; ++i) {
+        if (sqa[i] < amin) amin = sqa[i];
+        if (sqa[i] > amax) amax = sqa[i];
+        if (sqb[i] < bmin) bmin = sqb[i];
+        if (sqb[i] > bmax) bmax = sqb[i];
+      }
+      C->alo = amin & ~(int64_t)1;
+      C->ahi = (amax + (g_mutation == 15 ? 0 : 2)) & ~(int64_t)1;
+      C->blo = bmin & ~(int64_t)1; C->bhi = (bmax + 2) & ~(int64_t)1;
+    }
+  }
+  free(skey); free(qa); free(qb); free(fc); free(sqa); free(sqb);
 
   /* geometry, proxies, leaf membership and local coordinates */
   pl->s = (double *)malloc(sizeof(double) * (size_t)pl->p);
@@ -500,8 +546,8 @@ void *oracle_fmm_create(const double *pts, int64_t N, int n, double theta, int N
     cell_geometry(pl, C);
     for (int k1 = 0; k1 <= n; ++k1)
       for (int k2 = 0; k2 <= n; ++k2) {
-        double a = tan(C->xi_mid + C->half * pl->s[k1]);
-        double b = tan(C->eta_mid + C->half * pl->s[k2]);
+        double a = tan(C->xi_mid + C->hx * pl->s[k1]);
+        double b = tan(C->eta_mid + C->hy * pl->s[k2]);
         face_point(C->face, a, b, pl->proxy + 3 * ((int64_t)ci * pl->P + k1 * pl->p + k2));
       }
     if (C->nchild == 0) {
@@ -509,8 +555,8 @@ void *oracle_fmm_create(const double *pts, int64_t N, int n, double theta, int N
         int f; double a, b;
         face_coords(pl->x + 3 * i, &f, &a, &b);
         pl->leaf_of[i] = ci;
-        pl->u[i] = (atan(a) - C->xi_mid) / C->half;
-        pl->v[i] = (atan(b) - C->eta_mid) / C->half;
+        pl->u[i] = (atan(a) - C->xi_mid) / C->hx;
+        pl->v[i] = (atan(b) - C->eta_mid) / C->hy;
       }
     }
   }
@@ -652,12 +698,15 @@ static void upward_pass(const oplan *pl, const double *ws, int nrhs, double *wba
       for (int q = 0; q < 4; ++q) {
         int ch = C->child[q];
         if (ch < 0) continue;
-        int qa = q & 1, qb = q >> 1;
-        if (g_mutation == 3) { qa = 1 - qa; }
+        const ocell *K = &pl->cells[ch];
         double La[65 * 65], Lb[65 * 65]; /* [m][k]: parent L_k at child node m */
         for (int m = 0; m <= n; ++m) {
-          oracle_lagrange(n, pl->s, 0.5 * (pl->s[m] + (2 * qa - 1)), La + m * p);
-          oracle_lagrange(n, pl->s, 0.5 * (pl->s[m] + (2 * qb - 1)), Lb + m * p);
+          double ta = child_node(K->alo, K->ahi, C->alo, C->ahi, pl->s[m]);
+          if (g_mutation == 3)  /* the child's box mirrored inside the parent */
+            ta = child_node(C->alo + C->ahi - K->ahi, C->alo + C->ahi - K->alo, C->alo, C->ahi,
+                            pl->s[m]);
+          oracle_lagrange(n, pl->s, ta, La + m * p);
+          oracle_lagrange(n, pl->s, child_node(K->blo, K->bhi, C->blo, C->bhi, pl->s[m]), Lb + m * p);
         }
         const double *wc = wbar + (int64_t)ch * nrhs * P;
         for (int r = 0; r < nrhs; ++r)
@@ -809,11 +858,13 @@ static int fmm_evaluate(oplan *pl, int kid, const double *w, int nrhs,
       for (int q = 0; q < 4; ++q) {
         int ch = C->child[q];
         if (ch < 0 || !need_cell[ch]) continue;
-        int qa = q & 1, qb = q >> 1;
+        const ocell *K = &pl->cells[ch];
         double La[65 * 65], Lb[65 * 65]; /* [nn][m]: parent L_m at child node nn */
         for (int nn = 0; nn <= n; ++nn) {
-          oracle_lagrange(n, pl->s, 0.5 * (pl->s[nn] + (2 * qa - 1)), La + nn * p);
-          oracle_lagrange(n, pl->s, 0.5 * (pl->s[nn] + (2 * qb - 1)), Lb + nn * p);
+          oracle_lagrange(n, pl->s, child_node(K->alo, K->ahi, C->alo, C->ahi, pl->s[nn]),
+                          La + nn * p);
+          oracle_lagrange(n, pl->s, child_node(K->blo, K->bhi, C->blo, C->bhi, pl->s[nn]),
+                          Lb + nn * p);
         }
         double *pc = psi + (int64_t)ch * nrhs * P * dim;
         for (int r = 0; r < nrhs; ++r)
