@@ -23,7 +23,8 @@
  * independent targets only).
  *
  * Readings of points the paper leaves open (each listed in the design notes):
- *   - 1 - x.y is evaluated as |x - y|^2 / 2 for unit vectors.
+ *   - 1 - x.y is evaluated as |x - y|^2 / 2 for unit vectors, and x cross y
+ *     as x cross (y - x), so that neither cancels for nearby points.
  *   - A cell splits iff it holds more than N0 points; "big" (|C| > N0) means
  *     "has children", "small" means "leaf".  Empty children are dropped.
  *   - Children split their parent's (xi, eta) square at its midpoint; a
@@ -138,9 +139,11 @@ static void kernel_eval(int kid, const double *x, const double *y, double *k) {
     break;
   }
   case OR_KERNEL_BIOT_SAVART: {
-    double cx = x[1] * y[2] - x[2] * y[1];
-    double cy = x[2] * y[0] - x[0] * y[2];
-    double cz = x[0] * y[1] - x[1] * y[0];
+    /* x cross y = x cross (y - x): the same vector, without the cancellation
+     * of x cross y for nearby unit vectors (as 1 - x.y is |x - y|^2 / 2) */
+    double cx = -(x[1] * dz - x[2] * dy);
+    double cy = -(x[2] * dx - x[0] * dz);
+    double cz = -(x[0] * dy - x[1] * dx);
     double s = -1.0 / (4.0 * OR_PI * omc);
     k[0] = s * cx;
     k[1] = s * cy;
