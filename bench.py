@@ -422,7 +422,8 @@ def run_ours(args):
     achieved = dom_evals / (dom_ms / 1e3)
     traffic = traffic_per_launch(dom, dom_evals) if nrhs == 1 else None
     line = {
-        "metric": "FMM targets/s at N=6.3M", "value": value, "unit": "targets/s",
+        "metric": "FMM targets/s at N=6.3M" if N == 6291456 else f"FMM targets/s at N={N}",
+        "value": value, "unit": "targets/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if prec == Cs.FP32_BULK else "f64", "data": "synthetic",

@@ -81,7 +81,10 @@ typedef struct {
                      evaluations with phase timing enabled are launched directly (default 0) */
   int rhs_chunk;  /* FP32 bulk, scalar kernels: right-hand sides sharing one kernel evaluation
                      in the interaction kernels, 16, 8 or 4 (0 = 16) */
-  int reserved[4];
+  int shrink;     /* 1: every cell's interpolation box is shrunk to bound its points (Sec. 3;
+                     fewer direct pairs on clustered points); 0: the cell's own square
+                     (default) */
+  int reserved[3];
 } csfmm_options;
 
 typedef struct csfmm_plan_s *csfmm_plan;

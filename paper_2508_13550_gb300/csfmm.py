@@ -48,7 +48,7 @@ class CsfmmError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("max_nrhs", ctypes.c_int),
                 ("use_graphs", ctypes.c_int), ("rhs_chunk", ctypes.c_int),
-                ("reserved", ctypes.c_int * 4)]
+                ("shrink", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class TuneResult(ctypes.Structure):
@@ -225,10 +225,10 @@ class Plan:
 
 def plan_create(points, kernel_id: int, degree: int, theta: float, max_leaf: int,
                 precision: int = FP64, max_nrhs: int = 16, use_graphs: int = 0, rhs_chunk: int = 0,
-                stream=None):
+                shrink: bool = False, stream=None):
     import torch
     lib = load()
-    opt = Options(precision, max_nrhs, use_graphs, rhs_chunk)
+    opt = Options(precision, max_nrhs, use_graphs, rhs_chunk, int(bool(shrink)))
     h = ctypes.c_void_p()
     N = points.shape[0]
     rc = lib.csfmm_plan_create(_dev(points, torch.float64), N, kernel_id, degree, theta,
@@ -239,11 +239,12 @@ def plan_create(points, kernel_id: int, degree: int, theta: float, max_leaf: int
 
 def plan_create_targets(sources, targets, kernel_id: int, degree: int, theta: float,
                         max_leaf: int, precision: int = FP64, max_nrhs: int = 16,
-                        use_graphs: int = 0, rhs_chunk: int = 0, stream=None):
+                        use_graphs: int = 0, rhs_chunk: int = 0, shrink: bool = False,
+                        stream=None):
     """csfmm_plan_create_targets: a plan whose evaluations take weights at the
     sources [nrhs, Ns] and return the sum at separate targets [nrhs, Nt, dim]."""
     import torch
-    opt = Options(precision, max_nrhs, use_graphs, rhs_chunk)
+    opt = Options(precision, max_nrhs, use_graphs, rhs_chunk, int(bool(shrink)))
     h = ctypes.c_void_p()
     Ns, Nt = sources.shape[0], targets.shape[0]
     _check(load().csfmm_plan_create_targets(_dev(sources, torch.float64), Ns,

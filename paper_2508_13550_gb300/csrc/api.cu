@@ -163,6 +163,7 @@ csfmm_status csfmm_plan_create(const double *points, int64_t N, int kernel_id, i
   pl.dim = kernel_dim(kernel_id);
   pl.max_nrhs = o.max_nrhs;
   pl.use_graphs = o.use_graphs;
+  pl.shrink = o.shrink != 0;
   pl.rhs_chunk = o.rhs_chunk == 0 ? 16 : o.rhs_chunk;
   if (pl.rhs_chunk != 16 && pl.rhs_chunk != 8 && pl.rhs_chunk != 4) {
     set_error("rhs_chunk must be 0, 4, 8 or 16 (got %d)", o.rhs_chunk);

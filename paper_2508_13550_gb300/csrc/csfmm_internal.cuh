@@ -92,7 +92,9 @@ struct PlanView {
   const int32_t *cbegin, *cend, *clevel, *cface, *cparent, *cchild;
   const double *ccentre; // [nc][3]
   const double *cradius;
-  const double *cxmid, *cymid, *chalf;
+  const double *cxmid, *cymid, *chalf, *chy;  // box midpoints, half-widths (xi, eta)
+  const double *mcell64;  // shrunk boxes: [cell][2][p][p] matrices to the parent, else null
+  const float *mcell32;   // [cell][2 (rounding, remainder)][2][p][p]
   const double *proxy;   // [nc][3][P]
   const float *proxy32;  // [nc][3][P]
   const int32_t *loff[4], *lsrc[4];
@@ -119,6 +121,7 @@ struct Plan {
   int kernel_id = 0, n = 0, p = 0, P = 0, N0 = 0, precision = 0, dim = 1, max_nrhs = 16;
   int use_graphs = 0;
   int rhs_chunk = 16;   // FP32 bulk, scalar kernels: 16, 8 or 4
+  int shrink = 0;       // cell boxes shrunk to their points
   double theta = 0.7;
   int ncells = 0, nleaves = 0, nlevels = 0;
   std::vector<int> level_begin;  // cells of level l: [level_begin[l], level_begin[l+1])
@@ -133,7 +136,11 @@ struct Plan {
           *cparent = nullptr, *cchild = nullptr;
   int64_t *cia = nullptr, *cib = nullptr;
   double *ccentre = nullptr, *cradius = nullptr, *cxmid = nullptr, *cymid = nullptr,
-         *chalf = nullptr;
+         *chalf = nullptr, *chy = nullptr;  // box midpoint angles, half-widths along xi, eta
+  // shrunk boxes: per-child interpolation matrices [cell][2 axes][p][p]
+  // (parent L_k at the child's nodes), FP64 and FP32 rounding + remainder
+  double *mcell64 = nullptr;
+  float *mcell32 = nullptr;
   double *proxy = nullptr;
   float *proxy32 = nullptr;
   int32_t *loff[4] = {nullptr, nullptr, nullptr, nullptr};

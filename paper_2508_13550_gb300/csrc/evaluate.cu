@@ -48,6 +48,17 @@ template <>
 __device__ __forceinline__ const double *M_of<double>(const PlanView &v) { return v.m2m64; }
 template <>
 __device__ __forceinline__ const float *M_of<float>(const PlanView &v) { return v.m2m32; }
+// Shrunk boxes: the [2][p][p] matrices from child cell c to its parent.
+template <typename Real>
+__device__ __forceinline__ const Real *Mcell_of(const PlanView &v, int c);
+template <>
+__device__ __forceinline__ const double *Mcell_of<double>(const PlanView &v, int c) {
+  return v.mcell64 + (int64_t)c * 2 * v.p * v.p;
+}
+template <>
+__device__ __forceinline__ const float *Mcell_of<float>(const PlanView &v, int c) {
+  return v.mcell32 + (int64_t)c * 4 * v.p * v.p;
+}
 
 // FP64 kernel factors of the reference form (the FP32-bulk kernels live in
 // interact32.cu).
@@ -246,6 +257,12 @@ __global__ void m2m_kernel(PlanView v, int cell0, int r0, int nr, Real *wbar, in
       if (cc < 0) continue;
       int qa = q & 1, qb = q >> 1;
       __syncthreads();
+      if (v.mcell64) {  // shrunk boxes: this child's own matrices
+        const Real *Mc = Mcell_of<Real>(v, cc);
+        for (int t = threadIdx.x; t < 2 * p * p; t += blockDim.x) sM[t] = Mc[t];
+        qa = 0;
+        qb = 1;
+      }
       for (int t = threadIdx.x; t < P; t += blockDim.x) sw[t] = wbar[((int64_t)cc * ldr + r) * P + t];
       __syncthreads();
       // st[m1][k2] = sum_m2 M[qb][k2][m2] w[m1][m2]
@@ -326,8 +343,17 @@ __global__ void m2m_df_kernel(PlanView v, int cell0, int r0, int nr, float *wbar
     for (int q = 0; q < 4; ++q) {
       const int cc = ch[q];
       if (cc < 0) continue;
-      const int qa = q & 1, qb = q >> 1;
+      int qa = q & 1, qb = q >> 1;
       __syncthreads();
+      if (v.mcell32) {  // shrunk boxes: this child's own matrices
+        const float *Mc = v.mcell32 + (int64_t)cc * 4 * p * p;
+        for (int t = threadIdx.x; t < 2 * p * p; t += blockDim.x) {
+          sMh[t] = Mc[t];
+          sMl[t] = Mc[2 * p * p + t];
+        }
+        qa = 0;
+        qb = 1;
+      }
       for (int t = threadIdx.x; t < P; t += blockDim.x) sw[t] = wbar[((int64_t)cc * ldr + r) * P + t];
       __syncthreads();
       // st[m1][k2] = sum_m2 M[qb][k2][m2] w[m1][m2]
@@ -391,6 +417,13 @@ __global__ void l2l_kernel(PlanView v, int cell0, int r0, int nr, int dim, Real 
         if (cc < 0) continue;
         int qa = q & 1, qb = q >> 1;
         __syncthreads();
+        if (v.mcell64) {  // shrunk boxes: this child's own matrices
+          const Real *Mc = Mcell_of<Real>(v, cc);
+          for (int t = threadIdx.x; t < 2 * p * p; t += blockDim.x) sM[t] = Mc[t];
+          qa = 0;
+          qb = 1;
+          __syncthreads();
+        }
         // st[m1][n2] = sum_m2 psi[m1][m2] M[qb][m2][n2]
         for (int t = threadIdx.x; t < P; t += blockDim.x) {
           int m1 = t / p, n2 = t - m1 * p;
@@ -437,8 +470,18 @@ __global__ void l2l_df_kernel(PlanView v, int cell0, int r0, int nr, int dim, do
       for (int q = 0; q < 4; ++q) {
         const int cc = ch[q];
         if (cc < 0) continue;
-        const int qa = q & 1, qb = q >> 1;
+        int qa = q & 1, qb = q >> 1;
         __syncthreads();
+        if (v.mcell32) {  // shrunk boxes: this child's own matrices
+          const float *Mc = v.mcell32 + (int64_t)cc * 4 * p * p;
+          for (int t = threadIdx.x; t < 2 * p * p; t += blockDim.x) {
+            sMh[t] = Mc[t];
+            sMl[t] = Mc[2 * p * p + t];
+          }
+          qa = 0;
+          qb = 1;
+          __syncthreads();
+        }
         // st[m1][n2] = sum_m2 psi[m1][m2] M[qb][m2][n2]
         for (int t = threadIdx.x; t < P; t += blockDim.x) {
           const int m1 = t / p, n2 = t - m1 * p;

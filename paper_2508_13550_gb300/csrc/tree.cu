@@ -438,18 +438,81 @@ __global__ void finalize_level_kernel(LevelArrays L, int base, int child_base, i
 // ---------------------------------------------------------------------------
 // Step 4: geometry, proxies, per-point interpolation data.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t compact18(uint64_t x) {
+  uint64_t r = 0;
+#pragma unroll
+  for (int i = 0; i < kD; ++i) r |= ((x >> (2 * i)) & 1ull) << i;
+  return r;
+}
+
+// Box of every cell in fine face coordinates, box[c] = (alo, ahi, blo, bhi):
+// the dyadic square of (level, ia, ib), or with shrinking the fine cells of
+// its points (from the sorted keys) with each edge moved out to an even
+// coordinate, so that the midpoint is a tangent-table entry.  One block per
+// cell.
+__global__ void cell_box_kernel(PlanView v, const uint64_t *keys, const int64_t *cia,
+                                const int64_t *cib, int shrink, int64_t *box) {
+  const int c = blockIdx.x;
+  const int sh = kD - v.clevel[c];
+  if (!shrink) {
+    if (threadIdx.x == 0) {
+      box[4 * c] = cia[c] << sh;
+      box[4 * c + 1] = (cia[c] + 1) << sh;
+      box[4 * c + 2] = cib[c] << sh;
+      box[4 * c + 3] = (cib[c] + 1) << sh;
+    }
+    return;
+  }
+  __shared__ int64_t red[4][32];
+  int64_t amin = INT64_MAX, amax = -1, bmin = INT64_MAX, bmax = -1;
+  const uint64_t mask = (1ull << (2 * kD)) - 1;
+  for (int i = v.cbegin[c] + threadIdx.x; i < v.cend[c]; i += blockDim.x) {
+    const uint64_t k = keys[i] & mask;
+    const int64_t qa = (int64_t)compact18(k), qb = (int64_t)compact18(k >> 1);
+    amin = qa < amin ? qa : amin;
+    amax = qa > amax ? qa : amax;
+    bmin = qb < bmin ? qb : bmin;
+    bmax = qb > bmax ? qb : bmax;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    int64_t t;
+    t = __shfl_xor_sync(0xffffffffu, amin, o); amin = t < amin ? t : amin;
+    t = __shfl_xor_sync(0xffffffffu, amax, o); amax = t > amax ? t : amax;
+    t = __shfl_xor_sync(0xffffffffu, bmin, o); bmin = t < bmin ? t : bmin;
+    t = __shfl_xor_sync(0xffffffffu, bmax, o); bmax = t > bmax ? t : bmax;
+  }
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    red[0][w] = amin; red[1][w] = amax; red[2][w] = bmin; red[3][w] = bmax;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int j = 1; j < nw; ++j) {
+      amin = red[0][j] < amin ? red[0][j] : amin;
+      amax = red[1][j] > amax ? red[1][j] : amax;
+      bmin = red[2][j] < bmin ? red[2][j] : bmin;
+      bmax = red[3][j] > bmax ? red[3][j] : bmax;
+    }
+    box[4 * c] = amin & ~(int64_t)1;
+    box[4 * c + 1] = (amax + 2) & ~(int64_t)1;
+    box[4 * c + 2] = bmin & ~(int64_t)1;
+    box[4 * c + 3] = (bmax + 2) & ~(int64_t)1;
+  }
+}
+
+// Centre = sphere image of the box midpoint, radius = largest chord to the four
+// corners (all tangent-table entries), midpoint angles and half-widths.
 __global__ void cell_geometry_kernel(PlanView v, const double *T, double *ccentre, double *cradius,
-                                     double *cxmid, double *cymid, double *chalf,
-                                     const int64_t *cia, const int64_t *cib) {
+                                     double *cxmid, double *cymid, double *chalf, double *chy,
+                                     const int64_t *box) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= v.ncells) return;
   const double kHalfPi = 1.57079632679489661923;
   const double kQuarterPi = 0.78539816339744830962;
-  int f = v.cface[c], l = v.clevel[c];
-  int64_t ia = cia[c], ib = cib[c];
-  int sh = kD - l;
-  int64_t alo = ia << sh, ahi = (ia + 1) << sh, amid = (2 * ia + 1) << (sh - 1);
-  int64_t blo = ib << sh, bhi = (ib + 1) << sh, bmid = (2 * ib + 1) << (sh - 1);
+  const int f = v.cface[c];
+  const int64_t alo = box[4 * c], ahi = box[4 * c + 1], blo = box[4 * c + 2], bhi = box[4 * c + 3];
+  const int64_t amid = (alo + ahi) / 2, bmid = (blo + bhi) / 2;
   double cc[3], corner[3];
   face_point_rn(f, T[amid], T[bmid], cc);
   double r = 0.0, d;
@@ -461,10 +524,41 @@ __global__ void cell_geometry_kernel(PlanView v, const double *T, double *ccentr
   ccentre[3 * c + 1] = cc[1];
   ccentre[3 * c + 2] = cc[2];
   cradius[c] = r;
-  double h = scalbn(kHalfPi, -(l + 1));
-  chalf[c] = h;
-  cxmid[c] = __dsub_rn(__dmul_rn((double)(2 * ia + 1), h), kQuarterPi);
-  cymid[c] = __dsub_rn(__dmul_rn((double)(2 * ib + 1), h), kQuarterPi);
+  const double H = scalbn(kHalfPi, -kD), H2 = scalbn(kHalfPi, -(kD + 1));
+  chalf[c] = __dmul_rn((double)(ahi - alo), H2);
+  chy[c] = __dmul_rn((double)(bhi - blo), H2);
+  cxmid[c] = __dsub_rn(__dmul_rn((double)amid, H), kQuarterPi);
+  cymid[c] = __dsub_rn(__dmul_rn((double)bmid, H), kQuarterPi);
+}
+
+// Shrunk boxes: for every cell with a parent, parent Lagrange polynomial k at
+// the child's node m along each axis, M[c][axis][k][m] = L_k(t_m) with
+// t_m = (2 (mid_c - mid_p) + w_c s_m) / w_p from the integer box edges.
+__global__ void cell_matrix_kernel(PlanView v, const int64_t *box, double *m64, float *m32) {
+  const int c = blockIdx.x;
+  const int pa = v.cparent[c];
+  if (pa < 0) return;
+  const int p = v.p, pp = p * p;
+  __shared__ double s[kMaxP];
+  if (threadIdx.x < p) s[threadIdx.x] = v.cheb[threadIdx.x];
+  __syncthreads();
+  for (int t = threadIdx.x; t < 2 * p; t += blockDim.x) {
+    const int axis = t / p, m = t - axis * p;
+    const int64_t clo = box[4 * c + 2 * axis], chi = box[4 * c + 2 * axis + 1];
+    const int64_t plo = box[4 * pa + 2 * axis], phi = box[4 * pa + 2 * axis + 1];
+    const double dm = (double)((clo + chi) - (plo + phi));
+    const double tm = __ddiv_rn(__dadd_rn(dm, __dmul_rn((double)(chi - clo), s[m])),
+                                (double)(phi - plo));
+    double L[kMaxP];
+    lagrange_dev(v.n, s, tm, L);
+    for (int k = 0; k < p; ++k) {
+      const int64_t o = (int64_t)c * 2 * pp + axis * pp + k * p + m;
+      m64[o] = L[k];
+      const float hi = __double2float_rn(L[k]);
+      m32[(int64_t)c * 4 * pp + axis * pp + k * p + m] = hi;
+      m32[(int64_t)c * 4 * pp + 2 * pp + axis * pp + k * p + m] = __double2float_rn(L[k] - (double)hi);
+    }
+  }
 }
 
 __global__ void proxies_kernel(PlanView v, double *proxy, float *proxy32) {
@@ -474,7 +568,7 @@ __global__ void proxies_kernel(PlanView v, double *proxy, float *proxy32) {
   for (int k = threadIdx.x; k < P; k += blockDim.x) {
     int k1 = k / p, k2 = k - k1 * p;
     double a = tan(v.cxmid[c] + v.chalf[c] * v.cheb[k1]);
-    double b = tan(v.cymid[c] + v.chalf[c] * v.cheb[k2]);
+    double b = tan(v.cymid[c] + v.chy[c] * v.cheb[k2]);
     double x[3];
     face_point_rn(v.cface[c], a, b, x);
     int64_t o = (int64_t)c * 3 * P;
@@ -527,7 +621,7 @@ __global__ void leaf_points_kernel(PlanView v, const int32_t *leaves, int32_t *l
   if (threadIdx.x < p) s[threadIdx.x] = v.cheb[threadIdx.x];
   __syncthreads();
   double cx = v.ccentre[3 * c], cy = v.ccentre[3 * c + 1], cz = v.ccentre[3 * c + 2];
-  double xm = v.cxmid[c], ym = v.cymid[c], h = v.chalf[c];
+  double xm = v.cxmid[c], ym = v.cymid[c], h = v.chalf[c], hy = v.chy[c];
   for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
     double x[3] = {v.x[i], v.x[v.N + i], v.x[2 * v.N + i]};
     leaf_of[i] = c;
@@ -545,7 +639,7 @@ __global__ void leaf_points_kernel(PlanView v, const int32_t *leaves, int32_t *l
       bb = x[vv] / m;
     }
     double u = (atan(a) - xm) / h;
-    double w = (atan(bb) - ym) / h;
+    double w = (atan(bb) - ym) / hy;
     double L[kMaxP];
     lagrange_dev(n, s, u, L);
     for (int k = 0; k < p; ++k) {
@@ -815,7 +909,8 @@ PlanView Plan::view() const {
   v.off32 = off32;
   v.cbegin = cbegin; v.cend = cend; v.clevel = clevel; v.cface = cface; v.cparent = cparent;
   v.cchild = cchild; v.ccentre = ccentre; v.cradius = cradius; v.cxmid = cxmid; v.cymid = cymid;
-  v.chalf = chalf; v.proxy = proxy; v.proxy32 = proxy32;
+  v.chalf = chalf; v.chy = chy; v.proxy = proxy; v.proxy32 = proxy32;
+  v.mcell64 = mcell64; v.mcell32 = mcell32;
   for (int t = 0; t < 4; ++t) { v.loff[t] = loff[t]; v.lsrc[t] = lsrc[t]; }
   v.sym_contrib = sym_contrib;
   v.m2m64 = m2m64; v.m2m32 = m2m32; v.cheb = cheb; v.status = status;
@@ -975,10 +1070,15 @@ csfmm_status build_tree(Plan &pl, const double *points, cudaStream_t st) {
   CSFMM_TRY(A.alloc(&pl.cxmid, nc));
   CSFMM_TRY(A.alloc(&pl.cymid, nc));
   CSFMM_TRY(A.alloc(&pl.chalf, nc));
+  CSFMM_TRY(A.alloc(&pl.chy, nc));
+  int64_t *cbox;
+  CSFMM_TRY(tmp.alloc(&cbox, (size_t)4 * nc));
   {
     PlanView v = pl.view();
+    cell_box_kernel<<<nc, 256, 0, st>>>(v, keys, pl.cia, pl.cib, pl.shrink, cbox);
+    CSFMM_CUDA(cudaGetLastError());
     cell_geometry_kernel<<<grid_for(nc, 128), 128, 0, st>>>(v, T, pl.ccentre, pl.cradius, pl.cxmid,
-                                                            pl.cymid, pl.chalf, pl.cia, pl.cib);
+                                                            pl.cymid, pl.chalf, pl.chy, cbox);
     CSFMM_CUDA(cudaGetLastError());
   }
   CSFMM_TRY(A.alloc(&pl.proxy, (size_t)3 * nc * pl.P));
@@ -1004,6 +1104,13 @@ csfmm_status build_tree(Plan &pl, const double *points, cudaStream_t st) {
                                                 pl.Lb64, pl.La32, pl.Lb32, pl.La32lo, pl.Lb32lo);
     CSFMM_CUDA(cudaGetLastError());
     m2m_matrix_kernel<<<1, 64, 0, st>>>(pl.n, pl.cheb, pl.m2m64, pl.m2m32);
+    CSFMM_CUDA(cudaGetLastError());
+  }
+  if (pl.shrink) {
+    CSFMM_TRY(A.alloc(&pl.mcell64, (size_t)2 * nc * pl.p * pl.p));
+    CSFMM_TRY(A.alloc(&pl.mcell32, (size_t)4 * nc * pl.p * pl.p));
+    PlanView v = pl.view();
+    cell_matrix_kernel<<<nc, 64, 0, st>>>(v, cbox, pl.mcell64, pl.mcell32);
     CSFMM_CUDA(cudaGetLastError());
   }
 
