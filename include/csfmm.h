@@ -18,7 +18,10 @@
  *   - Memory: "device" pointers are CUDA global memory of the current
  *     device, owned by the caller; "host" pointers are host memory owned by
  *     the caller.  A plan owns every device buffer it allocates and frees it
- *     in csfmm_plan_destroy.
+ *     in csfmm_plan_destroy.  The library's buffers (plans, workspaces,
+ *     remeshing grids, build and step scratch) come from one stream-ordered
+ *     memory pool per device that keeps up to 4 GiB of freed memory for
+ *     reuse, so repeated plan builds do not go back to the driver.
  *   - Streams: a stream argument is a cudaStream_t passed as void* (NULL =
  *     the legacy default stream).  Calls marked "asynchronous" only enqueue
  *     work; their inputs and outputs must stay valid until the stream reaches
@@ -226,7 +229,7 @@ csfmm_status csfmm_evaluate_static(csfmm_plan plan, const double *weights, int n
  *             accumulation across 128-source tiles)
  * When there are few targets the sources are split across thread blocks; the
  * partial sums then live in temporary device memory allocated and freed in
- * stream order (cudaMallocAsync / cudaFreeAsync) and are reduced in a fixed
+ * stream order (from the library's memory pool) and are reduced in a fixed
  * order, so results are deterministic.
  * Errors: INVALID_ARG, CUDA, OUT_OF_MEMORY. */
 csfmm_status csfmm_direct(const double *points, int64_t N, int kernel_id, const double *weights,
@@ -377,8 +380,8 @@ csfmm_status csfmm_server_destroy(csfmm_server s);
  *   dt             time step (> 0), in the time unit of 1/omega
  *   x_out, zeta_out device [N][3], [N]: the state at t + dt, in input order;
  *                  may be x and zeta themselves (an in-place step)
- * Stage scratch (9 N doubles) is allocated and freed in stream order
- * (cudaMallocAsync / cudaFreeAsync).  Each plan build synchronises the
+ * Stage scratch (9 N doubles) is allocated and freed in stream order (from
+ * the library's memory pool).  Each plan build synchronises the
  * stream, so the call returns after its last plan evaluation; the final
  * update is still enqueued on stream when it returns.
  * Errors: INVALID_ARG, NOT_ON_SPHERE, OUT_OF_MEMORY, CUDA, DEVICE, TIMEOUT. */

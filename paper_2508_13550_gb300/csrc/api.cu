@@ -178,6 +178,7 @@ csfmm_status csfmm_plan_create(const double *points, int64_t N, int kernel_id, i
       set_error("host allocation failed");
       s = CSFMM_ERR_OUT_OF_MEMORY;
     } else {
+      pl.ws->arena.stream = st;
       s = workspace_alloc(pl, *pl.ws, pl.max_nrhs);
     }
   }
@@ -220,7 +221,7 @@ csfmm_status csfmm_plan_create_targets(const double *sources, int64_t Ns, const 
   *out = nullptr;
   cudaStream_t st = (cudaStream_t)stream;
   double *u = nullptr;
-  CSFMM_CUDA(cudaMallocAsync((void **)&u, sizeof(double) * 3 * (size_t)(Ns + Nt), st));
+  CSFMM_CUDA(cudaMallocFromPoolAsync((void **)&u, sizeof(double) * 3 * (size_t)(Ns + Nt), memory_pool(), st));
   cudaError_t e = cudaMemcpyAsync(u, sources, sizeof(double) * 3 * (size_t)Ns,
                                   cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess)
@@ -276,6 +277,7 @@ csfmm_status csfmm_evaluate_host(csfmm_plan plan, const double *weights, int nrh
   Workspace &W = *pl.ws;
   cudaStream_t st = (cudaStream_t)stream;
   if (!W.stage_w) {
+    W.arena.stream = st;
     csfmm_status s = W.arena.alloc(&W.stage_w, (size_t)W.max_nrhs * pl.nsrc);
     if (s != CSFMM_OK) return s;
     s = W.arena.alloc(&W.stage_out, (size_t)W.max_nrhs * pl.ntgt * pl.dim);
@@ -307,7 +309,11 @@ csfmm_status csfmm_workspace_create(csfmm_plan plan, int max_nrhs, csfmm_workspa
     set_error("host allocation failed");
     return CSFMM_ERR_OUT_OF_MEMORY;
   }
+  w->impl.arena.stream = release_stream();
   csfmm_status s = workspace_alloc(plan->impl, w->impl, max_nrhs);
+  // the buffers are used on the caller's streams: wait for the allocations
+  cudaError_t e = cudaStreamSynchronize(w->impl.arena.stream);
+  if (s == CSFMM_OK && e != cudaSuccess) s = cuda_status(e, "cudaStreamSynchronize");
   if (s != CSFMM_OK) {
     w->impl.arena.release();
     delete w;

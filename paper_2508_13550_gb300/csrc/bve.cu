@@ -66,7 +66,7 @@ csfmm_status bve_rk4(const double *x, const double *zeta, const double *area, in
   // scratch: stage positions and vorticity, weights, velocity, running sum
   double *buf = nullptr;
   const size_t n3 = (size_t)3 * N;
-  CSFMM_CUDA(cudaMallocAsync((void **)&buf, sizeof(double) * (3 * n3 + 2 * (size_t)N), st));
+  CSFMM_CUDA(cudaMallocFromPoolAsync((void **)&buf, sizeof(double) * (3 * n3 + 2 * (size_t)N), memory_pool(), st));
   double *xs = buf, *u = buf + n3, *ksum = buf + 2 * n3, *zs = buf + 3 * n3,
          *w = buf + 3 * n3 + N;
   const int grid = grid_for(N, 256, 152 * 8);
@@ -157,7 +157,7 @@ extern "C" csfmm_status csfmm_bve_step_remeshed(csfmm_remesh_grid grid, csfmm_pl
   cudaStream_t st = (cudaStream_t)stream;
   const int nf = tracer ? 2 : 1;
   double *buf = nullptr;
-  CSFMM_CUDA(cudaMallocAsync((void **)&buf, sizeof(double) * (3 + 2 * nf) * (size_t)M, st));
+  CSFMM_CUDA(cudaMallocFromPoolAsync((void **)&buf, sizeof(double) * (3 + 2 * nf) * (size_t)M, memory_pool(), st));
   // moved positions; moved fields [nf][M] (vorticity, tracer); remeshed fields
   double *xm = buf, *fm = buf + 3 * (size_t)M, *fo = fm + nf * (size_t)M;
   csfmm_status s = bve_rk4(remesh_grid_points(grid), zeta, area, M, dt, omega, degree, theta,

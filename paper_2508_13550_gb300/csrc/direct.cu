@@ -290,7 +290,7 @@ csfmm_status launch_direct(const double *pts, int N, int kid, const double *w, i
   const int64_t n_out = (int64_t)nrhs * nt * dim;
   double *part = nullptr;
   if (nsplit > 1) {
-    CSFMM_CUDA(cudaMallocAsync((void **)&part, sizeof(double) * 2 * (size_t)nsplit * n_out, st));
+    CSFMM_CUDA(cudaMallocFromPoolAsync((void **)&part, sizeof(double) * 2 * (size_t)nsplit * n_out, memory_pool(), st));
   }
   dim3 grid(tiles, nsplit);
   csfmm_status result = CSFMM_OK;

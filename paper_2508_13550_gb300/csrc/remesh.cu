@@ -460,6 +460,7 @@ extern "C" csfmm_status csfmm_remesh_grid_create(const double *grid, int64_t M,
     return CSFMM_ERR_INVALID_ARG;
   }
   auto *G = new csfmm_remesh_grid_s();
+  G->arena.stream = st;
   G->M = (int)M;
   G->nadj = nadj;
   csfmm_status s = CSFMM_OK;

@@ -49,6 +49,77 @@ const double *host_tan_table() {
   return g_tan.data();
 }
 
+namespace {
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kMaxPoolDevices] = {};
+cudaStream_t g_release[kMaxPoolDevices] = {};
+const double *g_dev_tan[kMaxPoolDevices] = {};
+
+int current_device() {
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kMaxPoolDevices) {
+    cudaGetLastError();
+    d = 0;
+  }
+  return d;
+}
+}  // namespace
+
+cudaMemPool_t memory_pool() {
+  const int d = current_device();
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pool[d]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = d;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+      cudaGetLastError();
+      cudaDeviceGetDefaultMemPool(&pool, d);  // still stream-ordered
+    } else {
+      uint64_t keep = kPoolKeepBytes;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    g_pool[d] = pool;
+  }
+  return g_pool[d];
+}
+
+cudaStream_t release_stream() {
+  const int d = current_device();
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_release[d]) {
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      s = nullptr;  // the legacy default stream
+    }
+    g_release[d] = s;
+  }
+  return g_release[d];
+}
+
+const double *device_tan_table() {
+  const int d = current_device();
+  const double *Th = host_tan_table();
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_dev_tan[d]) {
+    const size_t bytes = sizeof(double) * (((size_t)1 << kD) + 1);
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e == cudaSuccess) e = cudaMemcpy(p, Th, bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      if (p) cudaFree(p);
+      set_error("uploading the tangent table failed: %s", cudaGetErrorString(e));
+      return nullptr;
+    }
+    g_dev_tan[d] = (const double *)p;
+  }
+  return g_dev_tan[d];
+}
+
 int grid_for(int64_t n, int block, int max_blocks) {
   int64_t g = (n + block - 1) / block;
   if (g < 1) g = 1;
@@ -855,20 +926,23 @@ __global__ void sym_contrib_kernel(const int32_t *off, const int32_t *src, int n
 // ---------------------------------------------------------------------------
 namespace {
 
-// Temporary device buffers of the build, freed on every return path.
+// Temporary device buffers of the build, freed in stream order on every
+// return path.
 struct TempArena {
   std::vector<void *> ptrs;
+  cudaStream_t stream;
+  explicit TempArena(cudaStream_t s) : stream(s) {}
   ~TempArena() {
-    for (void *p : ptrs) cudaFree(p);
+    for (void *p : ptrs) cudaFreeAsync(p, stream);
   }
   template <class T>
   csfmm_status alloc(T **p, size_t count) {
     if (count == 0) count = 1;
     void *q = nullptr;
-    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    cudaError_t e = cudaMallocFromPoolAsync(&q, count * sizeof(T), memory_pool(), stream);
     if (e != cudaSuccess) {
       cudaGetLastError();
-      set_error("cudaMalloc of %zu bytes failed during plan build", count * sizeof(T));
+      set_error("device allocation of %zu bytes failed during plan build", count * sizeof(T));
       return CSFMM_ERR_OUT_OF_MEMORY;
     }
     ptrs.push_back(q);
@@ -920,15 +994,13 @@ PlanView Plan::view() const {
 
 csfmm_status build_tree(Plan &pl, const double *points, cudaStream_t st) {
   const int N = (int)pl.N;
-  TempArena tmp;
+  TempArena tmp(st);
   DeviceArena &A = pl.arena;
+  A.stream = st;
 
-  // tangent table and Chebyshev nodes
-  const double *Th = host_tan_table();
-  double *T = nullptr;
-  CSFMM_TRY(tmp.alloc(&T, ((size_t)1 << kD) + 1));
-  CSFMM_CUDA(cudaMemcpyAsync(T, Th, sizeof(double) * (((size_t)1 << kD) + 1),
-                             cudaMemcpyHostToDevice, st));
+  // tangent table (resident on the device) and Chebyshev nodes
+  const double *T = device_tan_table();
+  if (!T) return CSFMM_ERR_CUDA;
   std::vector<double> cheb_h(pl.p);
   for (int k = 0; k <= pl.n; ++k) cheb_h[k] = cos((double)k * 3.14159265358979323846 / pl.n);
   CSFMM_TRY(A.alloc(&pl.cheb, pl.p));
