@@ -39,6 +39,7 @@ KERNEL_LAPLACE = 0
 KERNEL_BIOT_SAVART = 1
 KERNEL_NEWTON = 2
 KERNEL_BIHARMONIC = 3
+KERNEL_SAL = 4
 KERNEL_ONE = 100
 
 PP, PC, CP, CC = 0, 1, 2, 3

@@ -73,7 +73,13 @@
 #define OR_KERNEL_BIOT_SAVART 1
 #define OR_KERNEL_NEWTON 2
 #define OR_KERNEL_BIHARMONIC 3
+#define OR_KERNEL_SAL 4
 #define OR_KERNEL_ONE 100
+
+/* Load Love number fit of Sec. 2.4: k'_n ~ a1/n, h'_n ~ b0 + b1/n. */
+#define OR_SAL_A1 (-2.7)
+#define OR_SAL_B0 (-6.21196)
+#define OR_SAL_B1 (6.1)
 
 #define OR_D 18            /* tangent table resolution: 2^D intervals per face */
 #define OR_LMAX 17         /* deepest cell level */
@@ -118,7 +124,8 @@ double oracle_dilog(double x) {
 
 static int kernel_valid(int kid) {
   return kid == OR_KERNEL_LAPLACE || kid == OR_KERNEL_BIOT_SAVART ||
-         kid == OR_KERNEL_NEWTON || kid == OR_KERNEL_BIHARMONIC || kid == OR_KERNEL_ONE;
+         kid == OR_KERNEL_NEWTON || kid == OR_KERNEL_BIHARMONIC || kid == OR_KERNEL_SAL ||
+         kid == OR_KERNEL_ONE;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -126,7 +133,9 @@ static int kernel_valid(int kid) {
 /* biharmonic G_B = (1/4pi) dilog((1 + x.y)/2)  (Eq. G_B);                    */
 /* Biot-Savart K_BS = -(1/4pi) (x cross y)/(1 - x.y)  (Eq. K_BS);            */
 /* Newtonian 1/sqrt(2(1 - x.y)), the leading term 1/gamma of Eq.             */
-/* G_SAL_approx;  K = 1 (test kernel).                                        */
+/* G_SAL_approx;  SAL: the bracket of Eq. G_SAL_approx,                       */
+/* (1 - b0)/gamma - (a1 - b1) ln(gamma/2 + gamma^2/4), gamma = |x - y|,       */
+/* without the factor 3 rho_w / (4 pi rho_e);  K = 1 (test kernel).           */
 /* ------------------------------------------------------------------------ */
 static void kernel_eval(int kid, const double *x, const double *y, double *k) {
   double dx = x[0] - y[0], dy = x[1] - y[1], dz = x[2] - y[2];
@@ -153,6 +162,11 @@ static void kernel_eval(int kid, const double *x, const double *y, double *k) {
   case OR_KERNEL_NEWTON:
     k[0] = 1.0 / sqrt(d2);
     break;
+  case OR_KERNEL_SAL: {
+    double g = sqrt(d2);
+    k[0] = (1.0 - OR_SAL_B0) / g - (OR_SAL_A1 - OR_SAL_B1) * log(0.5 * g + 0.25 * d2);
+    break;
+  }
   case OR_KERNEL_BIHARMONIC: /* Eq. G_B: dilog((1 + x.y)/2) / (4 pi), (1 + x.y)/2 = 1 - d2/4 */
     k[0] = oracle_dilog(1.0 - 0.25 * d2) / (4.0 * OR_PI);
     break;
