@@ -691,8 +691,8 @@ def run_paper_table(args):
 
 def run_runtime_table(args):
     """The paper's Table "runtimes" setting on the GPU: the N-body sum with
-    the Laplace, biharmonic, Biot-Savart and Newtonian kernels (the SAL
-    kernel's leading term) on the icosahedral grid (level args.ico_level),
+    the Laplace, biharmonic, Biot-Savart and SAL kernels (and the SAL kernel's
+    leading term, the Newtonian kernel) on the icosahedral grid (level args.ico_level),
     CSFMM with MAC 0.7, degree 6, N0 = 144, in both precision forms (CUDA
     events, plan resident, median of 5), and the direct sum (FP32: all N^2
     pairs; FP64: sampled targets, scaled to N).  Prints the paper's serial CPU
@@ -734,6 +734,7 @@ def run_runtime_table(args):
     for name, paper_name, kid in (("Laplace", "Laplace", Cs.KERNEL_LAPLACE),
                                   ("biharmonic", "biharmonic", Cs.KERNEL_BIHARMONIC),
                                   ("Biot-Savart", "Biot-Savart", Cs.KERNEL_BIOT_SAVART),
+                                  ("SAL", "SAL", Cs.KERNEL_SAL),
                                   ("Newtonian", "SAL", Cs.KERNEL_NEWTON)):
         f = I.rossby_haurwitz_vorticity(pts) if kid == Cs.KERNEL_BIOT_SAVART else \
             I.real_sph_harm(4, 3, pts)

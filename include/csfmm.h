@@ -60,6 +60,10 @@ enum {
   CSFMM_KERNEL_BIOT_SAVART = 1, /* K_BS = -(1/4pi) (x cross y)/(1 - x.y), Eq. K_BS; dim 3 */
   CSFMM_KERNEL_NEWTON = 2,      /* 1/sqrt(2(1 - x.y)) = 1/|x - y|, leading term of Eq. G_SAL_approx; dim 1 */
   CSFMM_KERNEL_BIHARMONIC = 3,  /* G_B = (1/4pi) dilog((1 + x.y)/2), Eq. G_B; dim 1 */
+  CSFMM_KERNEL_SAL = 4,         /* (1 - b0)/g - (a1 - b1) ln(g/2 + g^2/4), g = sqrt(2(1 - x.y)):
+                                   the bracket of Eq. G_SAL_approx with the paper's Love number
+                                   fit a1 = -2.7, b0 = -6.21196, b1 = 6.1; multiply the result by
+                                   3 rho_w / (4 pi rho_e) for the SAL potential; dim 1 */
   CSFMM_KERNEL_ONE = 100        /* K = 1, a test kernel (every interpolation is exact) */
 };
 

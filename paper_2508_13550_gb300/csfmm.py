@@ -25,6 +25,7 @@ KERNEL_LAPLACE = 0
 KERNEL_BIOT_SAVART = 1
 KERNEL_NEWTON = 2
 KERNEL_BIHARMONIC = 3
+KERNEL_SAL = 4  # bracket of Eq. G_SAL_approx (times 3 rho_w / (4 pi rho_e) for eta_SAL)
 KERNEL_ONE = 100
 FP64 = 0
 FP32_BULK = 1

@@ -39,7 +39,7 @@ namespace {
 
 bool kernel_ok(int k) {
   return k == CSFMM_KERNEL_LAPLACE || k == CSFMM_KERNEL_BIOT_SAVART || k == CSFMM_KERNEL_NEWTON ||
-         k == CSFMM_KERNEL_BIHARMONIC || k == CSFMM_KERNEL_ONE;
+         k == CSFMM_KERNEL_BIHARMONIC || k == CSFMM_KERNEL_SAL || k == CSFMM_KERNEL_ONE;
 }
 
 int kernel_dim(int k) { return k == CSFMM_KERNEL_BIOT_SAVART ? 3 : 1; }

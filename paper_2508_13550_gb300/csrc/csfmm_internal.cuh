@@ -305,6 +305,14 @@ csfmm_status radix_sort_u64(uint64_t *keys, int32_t *vals, uint64_t *keys_alt, i
                             cudaStream_t st, bool *result_in_alt);
 size_t radix_tmp_elems(int n);
 
+// SAL kernel in FP64, the bracket of Eq. G_SAL_approx with the Love number fit
+// a1 = -2.7, b0 = -6.21196, b1 = 6.1: (1 - b0)/g - (a1 - b1) ln(g/2 + g^2/4),
+// g = |x - y| = sqrt(d2).
+__device__ __forceinline__ double sal64(double d2) {
+  const double g = sqrt(d2), t = 0.5 * g;
+  return 7.21196 / g + 8.8 * log(t + t * t);
+}
+
 // ---------------------------------------------------------------------------
 // Device helpers
 // ---------------------------------------------------------------------------

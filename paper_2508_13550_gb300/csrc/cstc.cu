@@ -56,6 +56,8 @@ __device__ __forceinline__ void term64(double rx, double ry, double rz, double w
     acc[0] += rsqrt(d2) * w;
   } else if constexpr (KID == CSFMM_KERNEL_BIHARMONIC) {
     acc[0] += dilog64(1.0 - 0.25 * d2) * w;  // (1/4pi) applied at the end
+  } else if constexpr (KID == CSFMM_KERNEL_SAL) {
+    acc[0] += sal64(d2) * w;
   } else if constexpr (KID == CSFMM_KERNEL_BIOT_SAVART) {
     const double g = w / d2;
     acc[0] += g * rx;
@@ -241,6 +243,9 @@ void launch_cstc(const PlanView &v, bool f32, double theta, int nroots, int nrhs
       break;
     case CSFMM_KERNEL_BIHARMONIC:
       launch_cstc_kid<CSFMM_KERNEL_BIHARMONIC>(v, f32, theta, nroots, nrhs, ldr, ws, wsf, wbar, wbar32, out, st);
+      break;
+    case CSFMM_KERNEL_SAL:
+      launch_cstc_kid<CSFMM_KERNEL_SAL>(v, f32, theta, nroots, nrhs, ldr, ws, wsf, wbar, wbar32, out, st);
       break;
     default:
       launch_cstc_kid<CSFMM_KERNEL_ONE>(v, f32, theta, nroots, nrhs, ldr, ws, wsf, wbar, wbar32, out, st);

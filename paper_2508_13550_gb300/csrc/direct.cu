@@ -83,6 +83,7 @@ __global__ void direct_kernel(const double *pts, int N, const double *w, int r0,
       else if constexpr (KID == CSFMM_KERNEL_NEWTON) kv = (Real)1 / sqrt(d2);
       else if constexpr (KID == CSFMM_KERNEL_BIOT_SAVART) q3 = (Real)1 / d2;
       else if constexpr (KID == CSFMM_KERNEL_BIHARMONIC) kv = (Real)dilog64(1.0 - 0.25 * (double)d2);
+      else if constexpr (KID == CSFMM_KERNEL_SAL) kv = (Real)sal64((double)d2);
       else kv = 1;
 #pragma unroll
       for (int q = 0; q < kRBd; ++q) {
@@ -302,6 +303,7 @@ csfmm_status launch_direct(const double *pts, int N, int kid, const double *w, i
         case CSFMM_KERNEL_BIOT_SAVART: launch_direct32<CSFMM_KERNEL_BIOT_SAVART>(grid, st, pts, N, w, r0, nr, targets, nt, out, chunk, part, n_out); break;
         case CSFMM_KERNEL_NEWTON: launch_direct32<CSFMM_KERNEL_NEWTON>(grid, st, pts, N, w, r0, nr, targets, nt, out, chunk, part, n_out); break;
         case CSFMM_KERNEL_BIHARMONIC: launch_direct32<CSFMM_KERNEL_BIHARMONIC>(grid, st, pts, N, w, r0, nr, targets, nt, out, chunk, part, n_out); break;
+        case CSFMM_KERNEL_SAL: launch_direct32<CSFMM_KERNEL_SAL>(grid, st, pts, N, w, r0, nr, targets, nt, out, chunk, part, n_out); break;
         default: launch_direct32<CSFMM_KERNEL_ONE>(grid, st, pts, N, w, r0, nr, targets, nt, out, chunk, part, n_out); break;
       }
     } else {
@@ -317,6 +319,9 @@ csfmm_status launch_direct(const double *pts, int N, int kid, const double *w, i
           break;
         case CSFMM_KERNEL_BIHARMONIC:
           direct_kernel<CSFMM_KERNEL_BIHARMONIC, Real><<<grid, kTile, 0, st>>>(pts, N, w, r0, nr, targets, nt, out, chunk, part, n_out);
+          break;
+        case CSFMM_KERNEL_SAL:
+          direct_kernel<CSFMM_KERNEL_SAL, Real><<<grid, kTile, 0, st>>>(pts, N, w, r0, nr, targets, nt, out, chunk, part, n_out);
           break;
         default:
           direct_kernel<CSFMM_KERNEL_ONE, Real><<<grid, kTile, 0, st>>>(pts, N, w, r0, nr, targets, nt, out, chunk, part, n_out);

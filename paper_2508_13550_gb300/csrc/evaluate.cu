@@ -76,6 +76,7 @@ __device__ __forceinline__ double fast_rcp(double x) { return 1.0 / x; }
 //   Biot-Savart  f = 1/d2;  a += w f r (3 components);  value = (1/(2 pi)) x cross a
 //                (since x cross y = -x cross r and 1 - x.y = d2/2)
 //   biharmonic   f = dilog(1 - d2/4);  a += w f;  value = a / (4 pi)
+//   SAL          f = (1 - b0)/sqrt(d2) - (a1 - b1) ln(t + t^2), t = sqrt(d2)/2;  a += w f
 //   K = 1        a += w
 // ---------------------------------------------------------------------------
 template <int KID, typename Real>
@@ -87,6 +88,7 @@ struct KFac {
     else if constexpr (KID == CSFMM_KERNEL_NEWTON) f = fast_rsqrt(d2);
     else if constexpr (KID == CSFMM_KERNEL_BIOT_SAVART) f = fast_rcp(d2);
     else if constexpr (KID == CSFMM_KERNEL_BIHARMONIC) f = (Real)dilog64(1.0 - 0.25 * (double)d2);
+    else if constexpr (KID == CSFMM_KERNEL_SAL) f = sal64(d2);
     else f = 1;
   }
 };
@@ -103,7 +105,8 @@ struct Acc {
       a0 += q * k.rx;
       a1 += q * k.ry;
       a2 += q * k.rz;
-    } else if constexpr (KID == CSFMM_KERNEL_NEWTON || KID == CSFMM_KERNEL_BIHARMONIC) {
+    } else if constexpr (KID == CSFMM_KERNEL_NEWTON || KID == CSFMM_KERNEL_BIHARMONIC ||
+                         KID == CSFMM_KERNEL_SAL) {
       a0 += w * k.f;
     } else {
       a0 += w;
@@ -1059,6 +1062,7 @@ csfmm_status dispatch_cstc(Plan &pl, Workspace &W, const double *w, int nrhs, do
     case CSFMM_KERNEL_LAPLACE: return run_cstc<CSFMM_KERNEL_LAPLACE, Real>(pl, W, w, nrhs, out, st);
     case CSFMM_KERNEL_BIOT_SAVART: return run_cstc<CSFMM_KERNEL_BIOT_SAVART, Real>(pl, W, w, nrhs, out, st);
     case CSFMM_KERNEL_NEWTON: return run_cstc<CSFMM_KERNEL_NEWTON, Real>(pl, W, w, nrhs, out, st);
+    case CSFMM_KERNEL_SAL: return run_cstc<CSFMM_KERNEL_SAL, Real>(pl, W, w, nrhs, out, st);
     case CSFMM_KERNEL_BIHARMONIC: return run_cstc<CSFMM_KERNEL_BIHARMONIC, Real>(pl, W, w, nrhs, out, st);
     case CSFMM_KERNEL_ONE: return run_cstc<CSFMM_KERNEL_ONE, Real>(pl, W, w, nrhs, out, st);
   }
@@ -1073,6 +1077,7 @@ csfmm_status dispatch_kernel(Plan &pl, Workspace &W, const double *w, int nrhs, 
     case CSFMM_KERNEL_LAPLACE: return run_passes<CSFMM_KERNEL_LAPLACE, Real>(pl, W, w, nrhs, out, st);
     case CSFMM_KERNEL_BIOT_SAVART: return run_passes<CSFMM_KERNEL_BIOT_SAVART, Real>(pl, W, w, nrhs, out, st);
     case CSFMM_KERNEL_NEWTON: return run_passes<CSFMM_KERNEL_NEWTON, Real>(pl, W, w, nrhs, out, st);
+    case CSFMM_KERNEL_SAL: return run_passes<CSFMM_KERNEL_SAL, Real>(pl, W, w, nrhs, out, st);
     case CSFMM_KERNEL_BIHARMONIC: return run_passes<CSFMM_KERNEL_BIHARMONIC, Real>(pl, W, w, nrhs, out, st);
     case CSFMM_KERNEL_ONE: return run_passes<CSFMM_KERNEL_ONE, Real>(pl, W, w, nrhs, out, st);
   }

@@ -30,6 +30,11 @@ __device__ __forceinline__ float mufu_rcp(float x) {
   return y;
 }
 
+// SAL kernel coefficients from the Love number fit a1 = -2.7, b0 = -6.21196,
+// b1 = 6.1: (1 - b0) and -(a1 - b1) ln 2 (for the log2 form).
+constexpr float kSalC1 = 7.21196f;
+constexpr float kSalC2Log2 = (float)(8.8 * 0.69314718055994530942);
+
 template <int KID>
 __device__ __forceinline__ float kfactor(float d2) {
   if constexpr (KID == CSFMM_KERNEL_LAPLACE) return mufu_lg2(d2);
@@ -37,6 +42,13 @@ __device__ __forceinline__ float kfactor(float d2) {
   else if constexpr (KID == CSFMM_KERNEL_BIOT_SAVART) return mufu_rcp(d2);
   else if constexpr (KID == CSFMM_KERNEL_BIHARMONIC)
     return li2_one_minus(0.25f * d2, [](float v) { return mufu_lg2(v); });
+  else if constexpr (KID == CSFMM_KERNEL_SAL) {
+    // (1 - b0)/g - (a1 - b1) ln(t + t^2), g = sqrt(d2), t = g/2: one rsqrt and
+    // one log2 (the log's argument t(1 + t) is formed exactly enough in FP32)
+    const float r = mufu_rsqrt(d2);
+    const float t = 0.5f * (d2 * r);
+    return fmaf(kSalC1, r, kSalC2Log2 * mufu_lg2(fmaf(t, t, t)));
+  }
   else return 1.0f;
 }
 

@@ -1015,6 +1015,7 @@ void launch_multi32(const PlanView &v, bool far, int ngrid, const int32_t *leave
   switch (v.kernel_id) {
     case CSFMM_KERNEL_LAPLACE: launch_multi_kid<CSFMM_KERNEL_LAPLACE>(v, far, ngrid, leaves, wsf, wbar, ldr, r0, nr, phi, psi, st); break;
     case CSFMM_KERNEL_NEWTON: launch_multi_kid<CSFMM_KERNEL_NEWTON>(v, far, ngrid, leaves, wsf, wbar, ldr, r0, nr, phi, psi, st); break;
+    case CSFMM_KERNEL_SAL: launch_multi_kid<CSFMM_KERNEL_SAL>(v, far, ngrid, leaves, wsf, wbar, ldr, r0, nr, phi, psi, st); break;
     case CSFMM_KERNEL_BIHARMONIC: launch_multi_kid<CSFMM_KERNEL_BIHARMONIC>(v, far, ngrid, leaves, wsf, wbar, ldr, r0, nr, phi, psi, st); break;
     default: launch_multi_kid<CSFMM_KERNEL_ONE>(v, far, ngrid, leaves, wsf, wbar, ldr, r0, nr, phi, psi, st); break;
   }
@@ -1027,6 +1028,7 @@ void launch_far32(const PlanView &v, int ncells, const float *wsf, const float *
     case CSFMM_KERNEL_LAPLACE: launch_far_kid<CSFMM_KERNEL_LAPLACE>(v, ncells, wsf, wbar, ldr, r0, nr, psi, st); break;
     case CSFMM_KERNEL_BIOT_SAVART: launch_far_kid<CSFMM_KERNEL_BIOT_SAVART>(v, ncells, wsf, wbar, ldr, r0, nr, psi, st); break;
     case CSFMM_KERNEL_NEWTON: launch_far_kid<CSFMM_KERNEL_NEWTON>(v, ncells, wsf, wbar, ldr, r0, nr, psi, st); break;
+    case CSFMM_KERNEL_SAL: launch_far_kid<CSFMM_KERNEL_SAL>(v, ncells, wsf, wbar, ldr, r0, nr, psi, st); break;
     case CSFMM_KERNEL_BIHARMONIC: launch_far_kid<CSFMM_KERNEL_BIHARMONIC>(v, ncells, wsf, wbar, ldr, r0, nr, psi, st); break;
     default: launch_far_kid<CSFMM_KERNEL_ONE>(v, ncells, wsf, wbar, ldr, r0, nr, psi, st); break;
   }
@@ -1040,6 +1042,7 @@ void launch_near32(const PlanView &v, const int32_t *leaves, int nleaves, const 
     case CSFMM_KERNEL_LAPLACE: launch_kid<CSFMM_KERNEL_LAPLACE>(v, leaves, nleaves, wsf, ldw, wbar, ldr, r0, nr, phi, st, part); break;
     case CSFMM_KERNEL_BIOT_SAVART: launch_kid<CSFMM_KERNEL_BIOT_SAVART>(v, leaves, nleaves, wsf, ldw, wbar, ldr, r0, nr, phi, st, nullptr); break;
     case CSFMM_KERNEL_NEWTON: launch_kid<CSFMM_KERNEL_NEWTON>(v, leaves, nleaves, wsf, ldw, wbar, ldr, r0, nr, phi, st, part); break;
+    case CSFMM_KERNEL_SAL: launch_kid<CSFMM_KERNEL_SAL>(v, leaves, nleaves, wsf, ldw, wbar, ldr, r0, nr, phi, st, part); break;
     case CSFMM_KERNEL_BIHARMONIC: launch_kid<CSFMM_KERNEL_BIHARMONIC>(v, leaves, nleaves, wsf, ldw, wbar, ldr, r0, nr, phi, st, part); break;
     default: launch_kid<CSFMM_KERNEL_ONE>(v, leaves, nleaves, wsf, ldw, wbar, ldr, r0, nr, phi, st, part); break;
   }
@@ -1051,6 +1054,7 @@ void launch_pp_sym32(const PlanView &v, const int2 *pairs, const int32_t *off, i
   switch (v.kernel_id) {
     case CSFMM_KERNEL_LAPLACE: pp_sym_kernel<CSFMM_KERNEL_LAPLACE><<<npairs, kSymThreads, 0, st>>>(v, pairs, off, wsf, part); break;
     case CSFMM_KERNEL_NEWTON: pp_sym_kernel<CSFMM_KERNEL_NEWTON><<<npairs, kSymThreads, 0, st>>>(v, pairs, off, wsf, part); break;
+    case CSFMM_KERNEL_SAL: pp_sym_kernel<CSFMM_KERNEL_SAL><<<npairs, kSymThreads, 0, st>>>(v, pairs, off, wsf, part); break;
     case CSFMM_KERNEL_BIHARMONIC: pp_sym_kernel<CSFMM_KERNEL_BIHARMONIC><<<npairs, kSymThreads, 0, st>>>(v, pairs, off, wsf, part); break;
     default: pp_sym_kernel<CSFMM_KERNEL_ONE><<<npairs, kSymThreads, 0, st>>>(v, pairs, off, wsf, part); break;
   }

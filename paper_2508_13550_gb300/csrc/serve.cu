@@ -347,6 +347,7 @@ csfmm_status csfmm_server_submit(csfmm_server s, const csfmm_request *req, int64
       (r.precision != CSFMM_FP64 && r.precision != CSFMM_FP32_BULK) ||
       (r.kernel_id != CSFMM_KERNEL_LAPLACE && r.kernel_id != CSFMM_KERNEL_BIOT_SAVART &&
        r.kernel_id != CSFMM_KERNEL_NEWTON && r.kernel_id != CSFMM_KERNEL_BIHARMONIC &&
+       r.kernel_id != CSFMM_KERNEL_SAL &&
        r.kernel_id != CSFMM_KERNEL_ONE)) {
     set_error("invalid request");
     return CSFMM_ERR_INVALID_ARG;
