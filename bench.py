@@ -875,6 +875,29 @@ def run_bve(args):
             row["paper_qmax_minus_1"] = paper_tr["qmax_minus_1"][i]
         tracer.append(row)
         log("tracer Day 2", row)
+    # Gaussian vortex (Eq. Gaussian_ic, Figure gv): remeshed CSFMM FP32 run, the
+    # core's position (centroid of the vorticity above half its maximum) per day
+    xg, zg, Ag, offg, nbg = I.workload_bve(args.bve_level, "gaussian", with_adjacency=True)
+    dxg, dAg = torch.from_numpy(xg).cuda(), torch.from_numpy(Ag).cuda()
+    Gg = Cs.remesh_grid_create(dxg, torch.from_numpy(offg).cuda(), torch.from_numpy(nbg).cuda())
+    Pg = Cs.plan_create(dxg, Cs.KERNEL_BIOT_SAVART, 6, 0.7, 144, precision=Cs.FP32_BULK,
+                        max_nrhs=1)
+
+    def core(zv):
+        wv = np.maximum(zv - 0.5 * zv.max(), 0.0) * Ag
+        cv = (wv[:, None] * xg).sum(0)
+        cv /= np.linalg.norm(cv)
+        return [math.degrees(math.asin(cv[2])), math.degrees(math.atan2(cv[1], cv[0]))]
+
+    track = [core(zg)]
+    zi = torch.from_numpy(zg).cuda()
+    for day in range(3):
+        for _ in range(int(round(1.0 / dt))):
+            zi = Cs.bve_step_remeshed(Gg, zi, dAg, dt, om, 6, 0.7, 144, Cs.FP32_BULK,
+                                      grid_plan=Pg)
+        torch.cuda.synchronize()
+        track.append(core(zi.cpu().numpy()))
+    log("Gaussian vortex core (lat, lon) by day", track)
     d64 = rows["direct_fp64"]["ms_per_step"]
     return {"metric": "BVE vortex-method RK4 step time (Sec. 12 setting)", "unit": "ms",
             "config": {"workload": "bve-rh-wave", "grid": f"icosahedral level {args.bve_level}",
@@ -884,6 +907,7 @@ def run_bve(args):
             "speedup_over_direct_fp64": {k: d64 / v["ms_per_step"] for k, v in rows.items()},
             "E_zeta_remeshed_vs_N": conv,
             "tracer_day2": tracer,
+            "gaussian_vortex_core_lat_lon_by_day": track,
             "paper_context": "CSFMM 36x faster than direct summation at N = 163842 "
                              "(serial CPU, FP64)"}
 

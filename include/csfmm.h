@@ -294,12 +294,15 @@ csfmm_status csfmm_plan_export_proxies(csfmm_plan plan, double *proxies);
  * [ncells][nrhs][(n+1)^2] (first nrhs vectors of that call, nrhs <= its count). */
 csfmm_status csfmm_plan_export_proxy_weights(csfmm_plan plan, int nrhs, double *wbar);
 
-/* Phase timing.  While enabled, every evaluation of the plan records CUDA
- * events on its stream between its phases (no synchronisation).
- * csfmm_plan_phase_times synchronises those events, writes the summed
- * milliseconds per phase into ms[CSFMM_NUM_PHASES] (host), the number of
- * timed evaluations into *calls, and clears the record.  For the FAR and NEAR
- * phases the sum covers every launch of the phase in the evaluation. */
+/* Phase timing.  While enabled, every evaluation of the plan records a CUDA
+ * event before and after each phase on the stream the phase runs on (no
+ * synchronisation).  An evaluation runs the upward pass, the far field and
+ * L2L on a second stream of its workspace, concurrently with the near field
+ * on the caller's stream, so the phase times may add up to more than the
+ * evaluation's.  csfmm_plan_phase_times synchronises those events, writes the
+ * summed milliseconds per phase into ms[CSFMM_NUM_PHASES] (host), the number
+ * of timed evaluations into *calls, and clears the record.  For the FAR and
+ * NEAR phases the sum covers every launch of the phase in the evaluation. */
 csfmm_status csfmm_plan_enable_timing(csfmm_plan plan, int on);
 csfmm_status csfmm_plan_phase_times(csfmm_plan plan, double *ms, int64_t *calls);
 

@@ -512,13 +512,13 @@ csfmm_status csfmm_plan_phase_times(csfmm_plan plan, double *ms, int64_t *calls)
   }
   Plan &pl = plan->impl;
   for (int k = 0; k < CSFMM_NUM_PHASES; ++k) ms[k] = 0.0;
-  const size_t per = CSFMM_NUM_PHASES + 1;
+  const size_t per = 2 * CSFMM_NUM_PHASES;
   csfmm_status st = CSFMM_OK;
   for (size_t c = 0; c + per <= pl.events.size(); c += per) {
     for (int k = 0; k < CSFMM_NUM_PHASES; ++k) {
       float t = 0.f;
-      cudaError_t e = cudaEventSynchronize(pl.events[c + k + 1]);
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&t, pl.events[c + k], pl.events[c + k + 1]);
+      cudaError_t e = cudaEventSynchronize(pl.events[c + 2 * k + 1]);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&t, pl.events[c + 2 * k], pl.events[c + 2 * k + 1]);
       if (e != cudaSuccess && st == CSFMM_OK) st = cuda_status(e, "cudaEventElapsedTime");
       ms[k] += t;
     }

@@ -188,12 +188,13 @@ struct Plan {
   int *status = nullptr;
   Workspace *ws = nullptr;          // default workspace
   csfmm_stats stats{};
-  // phase timing: one set of CSFMM_NUM_PHASES + 1 events per timed evaluation
+  // phase timing: a begin and an end event per phase and timed evaluation,
+  // recorded on the stream the phase runs on
   bool timing = false;
   std::vector<cudaEvent_t> events;
   int timed_calls = 0;
   int launches = 0;                 // kernels launched by the current evaluation
-  csfmm_status mark(int phase, cudaStream_t st);  // records the event opening a phase
+  csfmm_status phase(int ph, bool begin, cudaStream_t st);
 
   PlanView view() const;
 };
@@ -213,6 +214,10 @@ struct GraphEntry {
 };
 
 struct Workspace {
+  Workspace() = default;
+  Workspace(const Workspace &) = delete;
+  Workspace &operator=(const Workspace &) = delete;
+  ~Workspace() { release_side(); }
   Plan *plan = nullptr;
   int max_nrhs = 0;
   bool graphs_ok = true;            // false for short-lived workspaces
@@ -236,6 +241,20 @@ struct Workspace {
   double *stage_w = nullptr;    // device staging for host-buffer evaluations [max_nrhs][N]
   double *stage_out = nullptr;  // [max_nrhs][N][dim]
   int last_nrhs = 0;
+  // Second stream of an evaluation: the upward pass, far field and L2L run on
+  // it while the near field runs on the caller's stream, joined by events
+  // (null for short-lived workspaces, which run every pass in order).
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_up = nullptr, ev_done = nullptr;
+  csfmm_status create_side();
+  void release_side() {
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_up) cudaEventDestroy(ev_up);
+    if (ev_done) cudaEventDestroy(ev_done);
+    if (side) cudaStreamDestroy(side);
+    side = nullptr;
+    ev_fork = ev_up = ev_done = nullptr;
+  }
 };
 
 }  // namespace csfmm

@@ -914,38 +914,66 @@ csfmm_status run_passes(Plan &pl, Workspace &W, const double *w, int nrhs, doubl
   v.wtot = wtot;
   v.wtot_ld = ldr;
   pl.launches = 0;
-#define CSFMM_MARK(ph)                              \
-  do {                                              \
-    csfmm_status s__ = pl.mark(ph, st);             \
-    if (s__ != CSFMM_OK) return s__;                \
+  // Two streams: after the gather the upward pass, the far field and L2L go
+  // to the workspace's side stream while the symmetric and the rest of the
+  // near field run on st; the near field waits for the upward pass (its PC
+  // entries read proxy weights) and L2P for L2L.  The log kernel's symmetric
+  // pass reads the leaves' weight totals of P2M, so there P2M stays on st
+  // before the fork.  Phase timing brackets every phase with its own events
+  // on the stream it runs on.
+  const bool overlap = W.side != nullptr;
+  cudaStream_t sf = overlap ? W.side : st;
+  const bool p2m_first = !overlap || (sizeof(Real) == 4 && KID == CSFMM_KERNEL_LAPLACE);
+#define CSFMM_BEGIN(ph, s)                           \
+  do {                                               \
+    csfmm_status s__ = pl.phase(ph, true, s);        \
+    if (s__ != CSFMM_OK) return s__;                 \
   } while (0)
-  CSFMM_MARK(CSFMM_PHASE_GATHER);
+#define CSFMM_END(ph, s)                             \
+  do {                                               \
+    csfmm_status s__ = pl.phase(ph, false, s);       \
+    if (s__ != CSFMM_OK) return s__;                 \
+  } while (0)
+  CSFMM_BEGIN(CSFMM_PHASE_GATHER, st);
   gather_kernel<<<grid_for((int64_t)N * nrhs, 256, 152 * 32), 256, 0, st>>>(
       pl.perm, w, W.ws, sizeof(Real) == 4 ? W.wsf : nullptr, N, nrhs, N, (int)pl.nsrc);
   ++pl.launches;
+  CSFMM_END(CSFMM_PHASE_GATHER, st);
   const int tb_prox = ((P + 31) / 32) * 32;
-  CSFMM_MARK(CSFMM_PHASE_P2M);
   const int tb_p2m = tb_prox < 64 ? 64 : tb_prox;
-  for (int r0 = 0; r0 < nrhs; r0 += kRB) {
-    int nr = min(kRB, nrhs - r0);
-    switch (nr) {
-      case 1: p2m_kernel<Real, 1><<<pl.nleaves, tb_p2m, 0, st>>>(v, pl.leaves, W.ws, N, r0, wbar, ldr, wtot); break;
-      case 2: p2m_kernel<Real, 2><<<pl.nleaves, tb_p2m, 0, st>>>(v, pl.leaves, W.ws, N, r0, wbar, ldr, wtot); break;
-      case 3: p2m_kernel<Real, 3><<<pl.nleaves, tb_p2m, 0, st>>>(v, pl.leaves, W.ws, N, r0, wbar, ldr, wtot); break;
-      default: p2m_kernel<Real, 4><<<pl.nleaves, tb_p2m, 0, st>>>(v, pl.leaves, W.ws, N, r0, wbar, ldr, wtot); break;
+  auto p2m = [&](cudaStream_t s) -> csfmm_status {
+    CSFMM_BEGIN(CSFMM_PHASE_P2M, s);
+    for (int r0 = 0; r0 < nrhs; r0 += kRB) {
+      int nr = min(kRB, nrhs - r0);
+      switch (nr) {
+        case 1: p2m_kernel<Real, 1><<<pl.nleaves, tb_p2m, 0, s>>>(v, pl.leaves, W.ws, N, r0, wbar, ldr, wtot); break;
+        case 2: p2m_kernel<Real, 2><<<pl.nleaves, tb_p2m, 0, s>>>(v, pl.leaves, W.ws, N, r0, wbar, ldr, wtot); break;
+        case 3: p2m_kernel<Real, 3><<<pl.nleaves, tb_p2m, 0, s>>>(v, pl.leaves, W.ws, N, r0, wbar, ldr, wtot); break;
+        default: p2m_kernel<Real, 4><<<pl.nleaves, tb_p2m, 0, s>>>(v, pl.leaves, W.ws, N, r0, wbar, ldr, wtot); break;
+      }
+      ++pl.launches;
     }
-    ++pl.launches;
+    CSFMM_END(CSFMM_PHASE_P2M, s);
+    return CSFMM_OK;
+  };
+  csfmm_status s0;
+  if (p2m_first && (s0 = p2m(st)) != CSFMM_OK) return s0;
+  if (overlap) {
+    CSFMM_CUDA(cudaEventRecord(W.ev_fork, st));
+    CSFMM_CUDA(cudaStreamWaitEvent(sf, W.ev_fork, 0));
   }
-  CSFMM_MARK(CSFMM_PHASE_M2M);
+  if (!p2m_first && (s0 = p2m(sf)) != CSFMM_OK) return s0;
+  CSFMM_BEGIN(CSFMM_PHASE_M2M, sf);
   for (int l = pl.nlevels - 2; l >= 0; --l) {
     int c0 = pl.level_begin[l], nlev = pl.level_begin[l + 1] - c0;
     if constexpr (sizeof(Real) == 4)
-      m2m_df_kernel<<<nlev, 128, 0, st>>>(v, c0, 0, nrhs, wbar, ldr, wtot);
+      m2m_df_kernel<<<nlev, 128, 0, sf>>>(v, c0, 0, nrhs, wbar, ldr, wtot);
     else
-      m2m_kernel<Real><<<nlev, 128, 0, st>>>(v, c0, 0, nrhs, wbar, ldr);
+      m2m_kernel<Real><<<nlev, 128, 0, sf>>>(v, c0, 0, nrhs, wbar, ldr);
     ++pl.launches;
   }
-  CSFMM_MARK(CSFMM_PHASE_FAR);
+  CSFMM_END(CSFMM_PHASE_M2M, sf);
+  if (overlap) CSFMM_CUDA(cudaEventRecord(W.ev_up, sf));
   // FP32 form, scalar kernels: chunks of 16 or 8 right-hand sides share every
   // kernel value; the rest goes in chunks of up to kRB
   const bool multi = sizeof(Real) == 4 && KID != CSFMM_KERNEL_BIOT_SAVART;
@@ -955,28 +983,49 @@ csfmm_status run_passes(Plan &pl, Workspace &W, const double *w, int nrhs, doubl
     if (multi && left >= 8 && pl.rhs_chunk >= 8) return 8;
     return min(kRB, left);
   };
+  CSFMM_BEGIN(CSFMM_PHASE_FAR, sf);
   for (int r0 = 0; r0 < nrhs; r0 += chunk(r0)) {
     const int nr = chunk(r0);
     if constexpr (sizeof(Real) == 4) {
       if (nr > kRB)
-        launch_multi32(v, true, pl.ncells, pl.leaves, W.wsf, wbar, ldr, r0, nr, W.phi, psi, st);
+        launch_multi32(v, true, pl.ncells, pl.leaves, W.wsf, wbar, ldr, r0, nr, W.phi, psi, sf);
       else
-        launch_far32(v, pl.ncells, W.wsf, wbar, ldr, r0, nr, psi, st);
+        launch_far32(v, pl.ncells, W.wsf, wbar, ldr, r0, nr, psi, sf);
     } else {
-      launch_far<KID, Real>(v, pl, W, nr, r0, tb_prox, wbar, psi, st);
+      launch_far<KID, Real>(v, pl, W, nr, r0, tb_prox, wbar, psi, sf);
     }
     ++pl.launches;
   }
-  CSFMM_MARK(CSFMM_PHASE_PPSYM);
+  CSFMM_END(CSFMM_PHASE_FAR, sf);
+  auto l2l = [&](cudaStream_t s) -> csfmm_status {
+    CSFMM_BEGIN(CSFMM_PHASE_L2L, s);
+    for (int l = 0; l + 1 < pl.nlevels; ++l) {
+      int c0 = pl.level_begin[l], nlev = pl.level_begin[l + 1] - c0;
+      if constexpr (sizeof(Real) == 4)
+        l2l_df_kernel<<<nlev, 128, 0, s>>>(v, c0, 0, nrhs, dim, psi, ldr);
+      else
+        l2l_kernel<double><<<nlev, 128, 0, s>>>(v, c0, 0, nrhs, dim, psi, ldr);
+      ++pl.launches;
+    }
+    CSFMM_END(CSFMM_PHASE_L2L, s);
+    return CSFMM_OK;
+  };
+  if (overlap) {
+    if ((s0 = l2l(sf)) != CSFMM_OK) return s0;
+    CSFMM_CUDA(cudaEventRecord(W.ev_done, sf));
+  }
   // single right-hand side, symmetric scalar kernel: the cross pairs of the PP
   // lists are evaluated once for both directions first
   const bool sym = sizeof(Real) == 4 && nrhs == 1 && KID != CSFMM_KERNEL_BIOT_SAVART &&
                    pl.n_sym_pairs > 0 && W.sym_part != nullptr;
+  CSFMM_BEGIN(CSFMM_PHASE_PPSYM, st);
   if (sym) {
     launch_pp_sym32(v, pl.sym_pairs, pl.sym_off, pl.n_sym_pairs, W.wsf, W.sym_part, st);
     ++pl.launches;
   }
-  CSFMM_MARK(CSFMM_PHASE_NEAR);
+  CSFMM_END(CSFMM_PHASE_PPSYM, st);
+  if (overlap) CSFMM_CUDA(cudaStreamWaitEvent(st, W.ev_up, 0));
+  CSFMM_BEGIN(CSFMM_PHASE_NEAR, st);
   for (int r0 = 0; r0 < nrhs; r0 += chunk(r0)) {
     const int nr = chunk(r0);
     if constexpr (sizeof(Real) == 4) {
@@ -990,23 +1039,18 @@ csfmm_status run_passes(Plan &pl, Workspace &W, const double *w, int nrhs, doubl
     }
     ++pl.launches;
   }
-  CSFMM_MARK(CSFMM_PHASE_L2L);
-  for (int l = 0; l + 1 < pl.nlevels; ++l) {
-    int c0 = pl.level_begin[l], nlev = pl.level_begin[l + 1] - c0;
-    if constexpr (sizeof(Real) == 4)
-      l2l_df_kernel<<<nlev, 128, 0, st>>>(v, c0, 0, nrhs, dim, psi, ldr);
-    else
-      l2l_kernel<double><<<nlev, 128, 0, st>>>(v, c0, 0, nrhs, dim, psi, ldr);
-    ++pl.launches;
-  }
-  CSFMM_MARK(CSFMM_PHASE_L2P);
+  CSFMM_END(CSFMM_PHASE_NEAR, st);
+  if (overlap) CSFMM_CUDA(cudaStreamWaitEvent(st, W.ev_done, 0));
+  else if ((s0 = l2l(st)) != CSFMM_OK) return s0;
+  CSFMM_BEGIN(CSFMM_PHASE_L2P, st);
   if constexpr (sizeof(Real) == 4)
     launch_l2p_df(pl.p, pl.nleaves, v, pl.leaves, psi, ldr, nrhs, dim, W.phi, out, st);
   else
     l2p_kernel<double><<<pl.nleaves, kL2PThreads, 0, st>>>(v, pl.leaves, psi, ldr, nrhs, dim, W.phi, out);
   ++pl.launches;
-  CSFMM_MARK(CSFMM_NUM_PHASES);
-#undef CSFMM_MARK
+  CSFMM_END(CSFMM_PHASE_L2P, st);
+#undef CSFMM_BEGIN
+#undef CSFMM_END
   CSFMM_CUDA(cudaGetLastError());
   pl.stats.launches_per_evaluate = pl.launches;
   return CSFMM_OK;
@@ -1087,19 +1131,32 @@ csfmm_status dispatch_kernel(Plan &pl, Workspace &W, const double *w, int nrhs, 
 
 }  // namespace
 
-csfmm_status Plan::mark(int phase, cudaStream_t st) {
+csfmm_status Plan::phase(int ph, bool begin, cudaStream_t st) {
   if (!timing) return CSFMM_OK;
-  if (phase == 0) {
-    // a new timed evaluation: CSFMM_NUM_PHASES + 1 fresh events
-    for (int k = 0; k <= CSFMM_NUM_PHASES; ++k) {
+  if (ph == 0 && begin) {
+    // a new timed evaluation: a begin and an end event for every phase
+    for (int k = 0; k < 2 * CSFMM_NUM_PHASES; ++k) {
       cudaEvent_t e;
       CSFMM_CUDA(cudaEventCreate(&e));
       events.push_back(e);
     }
     ++timed_calls;
   }
-  cudaEvent_t e = events[events.size() - (CSFMM_NUM_PHASES + 1) + phase];
+  cudaEvent_t e = events[events.size() - 2 * CSFMM_NUM_PHASES + 2 * ph + (begin ? 0 : 1)];
   CSFMM_CUDA(cudaEventRecord(e, st));
+  return CSFMM_OK;
+}
+
+csfmm_status Workspace::create_side() {
+  if (side) return CSFMM_OK;
+  cudaError_t e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_up, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_done, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    release_side();
+    return cuda_status(e, "workspace side stream");
+  }
   return CSFMM_OK;
 }
 
@@ -1121,7 +1178,7 @@ csfmm_status workspace_alloc(Plan &pl, Workspace &W, int max_nrhs) {
   }
   if ((s = W.arena.alloc(&W.psi, nc * R * pl.dim * P)) != CSFMM_OK) return s;
   if ((s = W.arena.alloc(&W.phi, R * N * pl.dim)) != CSFMM_OK) return s;
-  return CSFMM_OK;
+  return W.create_side();
 }
 
 namespace {
