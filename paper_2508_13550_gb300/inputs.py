@@ -145,6 +145,14 @@ def icosahedral_grid(level: int):
     incident edge, q, midpoint of the other), bounded by the perpendicular
     bisectors through those midpoints; signed areas keep the sum exact."""
     verts, faces = icosahedral_triangulation(level)
+    return verts, _dual_cell_areas(verts, faces)
+
+
+def _dual_cell_areas(verts, faces):
+    """Areas of the circumcentric dual cells of a spherical triangulation (the
+    Voronoi cells of a Delaunay one): each triangle adds to the cell of each
+    of its vertices the quadrilateral (vertex, midpoint of one incident edge,
+    circumcentre, midpoint of the other), with signed areas."""
     a, b, c = verts[faces[:, 0]], verts[faces[:, 1]], verts[faces[:, 2]]
     q = np.cross(b - a, c - a)
     q /= np.linalg.norm(q, axis=1)[:, None]
@@ -160,7 +168,37 @@ def icosahedral_grid(level: int):
     np.add.at(areas, faces[:, 0], T(a, mab, q) + T(a, q, mca))
     np.add.at(areas, faces[:, 1], T(b, mbc, q) + T(b, q, mab))
     np.add.at(areas, faces[:, 2], T(c, mca, q) + T(c, q, mbc))
-    return verts, np.abs(areas)
+    return np.abs(areas)
+
+
+def schmidt_transform(pts, stretch: float):
+    """Schmidt's conformal map of the sphere, tan(theta'/2) = stretch tan(theta/2)
+    with theta the co-latitude and the longitude kept: for stretch < 1 it
+    draws points toward the north pole, refining the spacing there by 1/stretch
+    and coarsening it at the south pole by stretch."""
+    x, y, z = pts[:, 0], pts[:, 1], pts[:, 2]
+    r = np.hypot(x, y)
+    south = 1.0 + z <= 1e-15
+    t = np.where(south, np.inf, stretch * r / np.where(south, 1.0, 1.0 + z))  # tan(theta'/2)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        zt = np.where(south, -1.0, (1.0 - t * t) / (1.0 + t * t))
+        st = np.where(south, 0.0, 2.0 * t / (1.0 + t * t))
+        ux = np.where(r > 0, x / np.where(r > 0, r, 1.0), 1.0)
+        uy = np.where(r > 0, y / np.where(r > 0, r, 1.0), 0.0)
+    out = np.stack([st * ux, st * uy, zt], axis=1)
+    return out / np.linalg.norm(out, axis=1, keepdims=True)
+
+
+def variable_resolution_grid(level: int, stretch: float = 0.5):
+    """A variable-resolution grid in the manner of MPAS meshes (which the
+    paper uses for SAL and are not available here): the icosahedral grid of
+    the given level mapped by schmidt_transform(stretch), its cells the dual
+    cells of the mapped triangulation.  With stretch 0.5 the spacing grows
+    smoothly 4x from the north pole to the south pole.  Returns (points [N, 3],
+    cell areas [N]) summing to 4 pi."""
+    verts, faces = icosahedral_triangulation(level)
+    pts = schmidt_transform(verts, stretch)
+    return pts, _dual_cell_areas(pts, faces)
 
 
 def latlon_grid(level: int):

@@ -111,3 +111,21 @@ def test_constant_kernel_and_separate_targets(torch, C):
     P = C.plan_create_targets(dev(torch, src), dev(torch, tgt), C.KERNEL_NEWTON, 6, 0.7, 30,
                               shrink=True)
     assert rel(C.evaluate(P, dev(torch, np.atleast_2d(w))).cpu().numpy(), ref) < 1e-12
+
+
+@pytest.mark.parametrize("shrink", [False, True])
+def test_variable_resolution_grid_sal(torch, C, shrink):
+    """The SAL kernel on a variable-resolution (Schmidt-mapped icosahedral)
+    grid, the stand-in for the paper's MPAS SAL runs: FP64 parity with the
+    oracle and the FP32-bulk error against the FP64 direct sum."""
+    pts, A = I.variable_resolution_grid(5)
+    eta = I.land_mask_field(pts, 72) * A  # a sea-surface-height-like field
+    ref = O.FMM(pts, 6, 0.7, 40, shrink=shrink).evaluate(O.KERNEL_SAL, eta)
+    P = C.plan_create(dev(torch, pts), C.KERNEL_SAL, 6, 0.7, 40, shrink=shrink)
+    assert rel(C.evaluate(P, dev(torch, np.atleast_2d(eta))).cpu().numpy(), ref) < 1e-12
+    ds = O.direct(pts, O.KERNEL_SAL, eta)
+    P32 = C.plan_create(dev(torch, pts), C.KERNEL_SAL, 8, 0.7, 64, precision=C.FP32_BULK,
+                        shrink=shrink)
+    e32 = rel(C.evaluate(P32, dev(torch, np.atleast_2d(eta))).cpu().numpy(), ds)
+    print(f"\nSAL on the variable-resolution grid, shrink={shrink}: FP32 bulk {e32:.2e}")
+    assert e32 < 1e-5
