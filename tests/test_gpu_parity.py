@@ -227,6 +227,29 @@ def test_full_size_newton_config_sampled(torch, C):
     assert e32 < 1e-5
 
 
+def test_full_size_multi_rhs_config_sampled(torch, C):
+    """The multi-RHS workload at full size: Poisson kernel, 6 x 512^2 =
+    1,572,864 points, 16 right-hand sides, n=10, MAC 0.7, N0=400, FP32 bulk in
+    the launch configuration the benchmark times (16 RHS per kernel value).
+    Every right-hand side is compared with the oracle direct sum on 64
+    sampled targets, and with the FP64 CSFMM of the same plan shape."""
+    pts, A, W, _ = I.workload_multi_rhs(512, 16, with_exact=False)
+    N = len(pts)
+    tg = np.sort(np.random.default_rng(12).choice(N, 64, replace=False))
+    ds = O.direct(pts, O.KERNEL_LAPLACE, W, tg)[:, :, 0]
+    P = C.plan_create(dev(torch, pts), C.KERNEL_LAPLACE, 10, 0.7, 400, precision=C.FP32_BULK,
+                      max_nrhs=16)
+    f32 = C.evaluate(P, dev(torch, W)).cpu().numpy()[:, tg, 0]
+    del P
+    errs = [rel(f32[r], ds[r]) for r in range(16)]
+    print(f"\nconfig-4 sample: max over 16 RHS of E(FS32,DS) = {max(errs):.3e}")
+    assert max(errs) < 1e-5
+    P64 = C.plan_create(dev(torch, pts), C.KERNEL_LAPLACE, 10, 0.7, 400, max_nrhs=4)
+    f64 = C.evaluate(P64, dev(torch, W[:4])).cpu().numpy()[:, tg, 0]
+    for r in range(4):
+        assert rel(f64[r], ds[r]) < 1e-8
+
+
 def test_edge_cases(torch, C):
     # one point: no sources, phi = 0
     p1 = np.array([[0.0, 0.0, 1.0]])
