@@ -21,7 +21,7 @@
  *     in csfmm_plan_destroy.  The library's buffers (plans, workspaces,
  *     remeshing grids, build and step scratch) come from one stream-ordered
  *     memory pool per device that keeps up to 4 GiB of freed memory for
- *     reuse, so repeated plan builds do not go back to the driver.
+ *     reuse, so repeated plan builds do not go back to the CUDA driver.
  *   - Streams: a stream argument is a cudaStream_t passed as void* (NULL =
  *     the legacy default stream).  Calls marked "asynchronous" only enqueue
  *     work; their inputs and outputs must stay valid until the stream reaches
@@ -48,7 +48,7 @@ typedef enum {
   CSFMM_ERR_OUT_OF_MEMORY = 3, /* a device allocation failed; nothing was leaked */
   CSFMM_ERR_CUDA = 4,          /* a CUDA runtime call failed (message in csfmm_last_error) */
   CSFMM_ERR_TIMEOUT = 5,       /* a bounded device-side wait gave up */
-  CSFMM_ERR_UNSUPPORTED = 6,   /* valid request outside what this build implements */
+  CSFMM_ERR_UNSUPPORTED = 6,   /* valid request outside what this library implements */
   CSFMM_ERR_BUSY = 7,          /* serving: no slot or memory free right now */
   CSFMM_ERR_DEVICE = 8         /* a kernel reported an internal error in the plan's status word */
 } csfmm_status;

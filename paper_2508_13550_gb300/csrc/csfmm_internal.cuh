@@ -52,7 +52,7 @@ struct Workspace;
 // Device memory of plans, workspaces, build scratch and remeshing grids comes
 // from one stream-ordered pool per device (cudaMallocFromPoolAsync) that keeps
 // up to kPoolKeepBytes of freed memory for the next allocations instead of
-// handing it back to the driver, so that a plan build costs some eighty
+// handing it back to the CUDA driver, so that a plan build costs some eighty
 // allocations of reused memory rather than eighty cudaMalloc calls and a
 // device-wide synchronisation in every cudaFree.
 constexpr uint64_t kPoolKeepBytes = 4ull << 30;

@@ -1,6 +1,6 @@
 """GPU parity of the vortex-method step for the barotropic vorticity equation
 (csfmm_bve_step; Sec. 2.3, Eq. BVE_ODEs, RK4 as in Sec. 12) through the C ABI
-against the oracle's RK4 driver on the same seeded inputs.
+against the oracle's RK4 integrator on the same seeded inputs.
 
 Bars.  FP64 direct and FP64 CSFMM velocity: the step agrees with the oracle's
 step to 1e-13 in the positions and 1e-12 max|zeta| in the vorticity (same

@@ -9,7 +9,7 @@ zeta_i(t) = zeta_0(x_i(t)) and E_zeta (Eq. bveerr) falls like the midpoint
 rule's O(dphi^2), about 4x per icosahedral level; the Gaussian vortex of
 Eq. Gaussian_ic has zero total vorticity (its background is pi/16 to the
 printed digits) and its core drifts north-west (Sec. 12).  Each planted
-mistake in the driver fails at least one of these.
+mistake in the RK4 integrator fails at least one of these.
 """
 import math
 
