@@ -992,6 +992,57 @@ PlanView Plan::view() const {
   return v;
 }
 
+// First index of each of nb boundary keys in the sorted keys[0..n):
+// out[b] = lower_bound(keys, bound_b), bound_b = b << shift.  One thread per
+// boundary (a handful of binary searches instead of copying the keys back).
+__global__ void key_bounds_kernel(const uint64_t *keys, int n, int nb, int shift, int32_t *out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  const uint64_t k = (uint64_t)b << shift;
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (keys[mid] < k) lo = mid + 1;
+    else hi = mid;
+  }
+  out[b] = lo;
+}
+
+// Plan statistics from the sorted list keys (type, target, source): kernel
+// evaluations per list type and the number of (target, source) point pairs
+// covered; 64-bit integer atomics, so the totals do not depend on the order.
+__global__ void list_stats_kernel(const uint64_t *lk, int n, int bits, const int32_t *cbegin,
+                                  const int32_t *cend, int P, unsigned long long *acc) {
+  unsigned long long ev[4] = {0, 0, 0, 0}, cov = 0;
+  const uint64_t mask = (1ull << bits) - 1;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const uint64_t k = lk[e];
+    const int ty = (int)(k >> (2 * bits));
+    const int t = (int)((k >> bits) & mask), s = (int)(k & mask);
+    const unsigned long long nt = (unsigned long long)(cend[t] - cbegin[t]);
+    const unsigned long long ns = (unsigned long long)(cend[s] - cbegin[s]);
+    cov += nt * ns;
+    if (ty == CSFMM_LIST_PP) ev[0] += nt * ns - (t == s ? nt : 0);
+    else if (ty == CSFMM_LIST_PC) ev[1] += nt * (unsigned long long)P;
+    else if (ty == CSFMM_LIST_CP) ev[2] += (unsigned long long)P * ns;
+    else ev[3] += (unsigned long long)P * (unsigned long long)P;
+  }
+  for (int q = 0; q < 4; ++q)
+    if (ev[q]) atomicAdd(&acc[q], ev[q]);
+  if (cov) atomicAdd(&acc[4], cov);
+}
+
+// Kernel evaluations of the symmetric near field's cross pairs.
+__global__ void sym_stats_kernel(const int2 *pairs, int n, const int32_t *cbegin,
+                                 const int32_t *cend, unsigned long long *acc) {
+  unsigned long long se = 0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const int2 q = pairs[e];
+    se += (unsigned long long)(cend[q.x] - cbegin[q.x]) * (unsigned long long)(cend[q.y] - cbegin[q.y]);
+  }
+  if (se) atomicAdd(acc, se);
+}
+
 csfmm_status build_tree(Plan &pl, const double *points, cudaStream_t st) {
   const int N = (int)pl.N;
   TempArena tmp(st);
@@ -1042,14 +1093,16 @@ csfmm_status build_tree(Plan &pl, const double *points, cudaStream_t st) {
   // 3. roots: non-empty faces, found from the sorted keys on the host side
   std::vector<int> root_begin, root_end, root_face;
   {
-    // face boundaries by binary search over a host copy of the face bits
-    std::vector<uint64_t> hk((size_t)N);
-    CSFMM_CUDA(cudaMemcpyAsync(hk.data(), keys, sizeof(uint64_t) * N, cudaMemcpyDeviceToHost, st));
+    // face boundaries: binary searches of the sorted keys on the device
+    int32_t *fb;
+    CSFMM_TRY(tmp.alloc(&fb, 7));
+    key_bounds_kernel<<<1, 32, 0, st>>>(keys, N, 7, 2 * kD, fb);
+    CSFMM_CUDA(cudaGetLastError());
+    int32_t hb7[7];
+    CSFMM_CUDA(cudaMemcpyAsync(hb7, fb, sizeof(hb7), cudaMemcpyDeviceToHost, st));
     CSFMM_CUDA(cudaStreamSynchronize(st));
     for (int f = 0; f < 6; ++f) {
-      uint64_t lo = (uint64_t)f << (2 * kD), hi = (uint64_t)(f + 1) << (2 * kD);
-      int b = (int)(std::lower_bound(hk.begin(), hk.end(), lo) - hk.begin());
-      int e = (int)(std::lower_bound(hk.begin(), hk.end(), hi) - hk.begin());
+      const int b = hb7[f], e = hb7[f + 1];
       if (e > b) {
         root_begin.push_back(b);
         root_end.push_back(e);
@@ -1277,15 +1330,15 @@ csfmm_status build_tree(Plan &pl, const double *points, cudaStream_t st) {
       std::swap(lv, lv2);
     }
   }
-  std::vector<uint64_t> hkeys((size_t)acc_n);
+  int type_lo[5] = {0, 0, 0, 0, 0};
   if (acc_n) {
-    CSFMM_CUDA(cudaMemcpyAsync(hkeys.data(), lk, sizeof(uint64_t) * acc_n, cudaMemcpyDeviceToHost, st));
+    // first entry of each list type: binary searches on the device
+    int32_t *tb;
+    CSFMM_TRY(tmp.alloc(&tb, 5));
+    key_bounds_kernel<<<1, 32, 0, st>>>(lk, acc_n, 5, 2 * bits, tb);
+    CSFMM_CUDA(cudaGetLastError());
+    CSFMM_CUDA(cudaMemcpyAsync(type_lo, tb, sizeof(type_lo), cudaMemcpyDeviceToHost, st));
     CSFMM_CUDA(cudaStreamSynchronize(st));
-  }
-  int type_lo[5];
-  for (int ty = 0; ty <= 4; ++ty) {
-    uint64_t k = (uint64_t)ty << (2 * bits);
-    type_lo[ty] = (int)(std::lower_bound(hkeys.begin(), hkeys.end(), k) - hkeys.begin());
   }
   for (int ty = 0; ty < 4; ++ty) {
     int lo = type_lo[ty], hi = type_lo[ty + 1];
@@ -1340,39 +1393,32 @@ csfmm_status build_tree(Plan &pl, const double *points, cudaStream_t st) {
     }
   }
 
-  // statistics from the host copies
+  // statistics: reductions over the lists and symmetric pairs on the device
   {
-    std::vector<int32_t> hb(nc), he(nc);
-    CSFMM_CUDA(cudaMemcpyAsync(hb.data(), pl.cbegin, 4 * (size_t)nc, cudaMemcpyDeviceToHost, st));
-    CSFMM_CUDA(cudaMemcpyAsync(he.data(), pl.cend, 4 * (size_t)nc, cudaMemcpyDeviceToHost, st));
-    CSFMM_CUDA(cudaStreamSynchronize(st));
-    int64_t ev[4] = {0, 0, 0, 0}, covered = 0;
-    uint64_t mask = (1ull << bits) - 1;
-    for (int e = 0; e < acc_n; ++e) {
-      uint64_t k = hkeys[(size_t)e];
-      int ty = (int)(k >> (2 * bits));
-      int t = (int)((k >> bits) & mask), s = (int)(k & mask);
-      int64_t nt = he[t] - hb[t], ns = he[s] - hb[s];
-      covered += nt * ns;
-      if (ty == CSFMM_LIST_PP) ev[0] += nt * ns - (t == s ? nt : 0);
-      else if (ty == CSFMM_LIST_PC) ev[1] += nt * pl.P;
-      else if (ty == CSFMM_LIST_CP) ev[2] += (int64_t)pl.P * ns;
-      else ev[3] += (int64_t)pl.P * pl.P;
+    unsigned long long *acc;
+    CSFMM_TRY(tmp.alloc(&acc, 6));
+    CSFMM_CUDA(cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * 6, st));
+    if (acc_n > 0) {
+      list_stats_kernel<<<grid_for(acc_n, 256, 152 * 8), 256, 0, st>>>(lk, acc_n, bits, pl.cbegin,
+                                                                      pl.cend, pl.P, acc);
+      CSFMM_CUDA(cudaGetLastError());
     }
+    if (pl.n_sym_pairs > 0) {
+      sym_stats_kernel<<<grid_for(pl.n_sym_pairs, 256, 152 * 8), 256, 0, st>>>(
+          pl.sym_pairs, (int)pl.n_sym_pairs, pl.cbegin, pl.cend, acc + 5);
+      CSFMM_CUDA(cudaGetLastError());
+    }
+    unsigned long long h[6];
+    CSFMM_CUDA(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, st));
+    CSFMM_CUDA(cudaStreamSynchronize(st));
     for (int t = 0; t < 4; ++t) {
-      pl.stats.evals[t] = ev[t];
+      pl.stats.evals[t] = (int64_t)h[t];
       pl.stats.n_list[t] = pl.nlist[t];
     }
-    pl.stats.pairs_covered = covered;
+    pl.stats.pairs_covered = (int64_t)h[4];
     if (pl.n_sym_pairs > 0) {
-      std::vector<int2> hp((size_t)pl.n_sym_pairs);
-      CSFMM_CUDA(cudaMemcpyAsync(hp.data(), pl.sym_pairs, sizeof(int2) * hp.size(),
-                                 cudaMemcpyDeviceToHost, st));
-      CSFMM_CUDA(cudaStreamSynchronize(st));
-      int64_t se = 0;
-      for (const int2 &q : hp) se += (int64_t)(he[q.x] - hb[q.x]) * (he[q.y] - hb[q.y]);
       pl.stats.sym_pairs = pl.n_sym_pairs;
-      pl.stats.sym_evals = se;
+      pl.stats.sym_evals = (int64_t)h[5];
     }
   }
   CSFMM_CUDA(cudaStreamSynchronize(st));
