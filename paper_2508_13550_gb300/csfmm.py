@@ -5,13 +5,19 @@ library libcsfmm.so.  Tensors are torch CUDA tensors (float64, contiguous);
 streams default to torch's current stream.  There is no CPU fallback: if the
 library cannot be loaded, every call raises.
 
-    plan = plan_create(points, kernel_id, degree, theta, max_leaf, precision=FP64)
+    plan = plan_create(points, kernel_id, degree, theta, max_leaf, precision=FP64,
+                       shrink=False)
+    plan = plan_create_targets(sources, targets, kernel_id, degree, theta, max_leaf)
     out  = evaluate(plan, weights)            # weights [nrhs, N] -> [nrhs, N, dim]
     out  = evaluate_host(plan, weights_np)    # host numpy in/out (copies inside)
     out  = evaluate_cstc(plan, weights)       # tree code on the same tree
     out  = direct(points, kernel_id, weights, precision=FP64)
     plan_stats(plan), plan_export_cells(plan), plan_export_list(plan, type), ...
     plan_destroy(plan)
+    x, zeta = bve_step(x, zeta, area, dt, omega, degree)        # BVE vortex method, RK4
+    grid = remesh_grid_create(grid_points, adj_offsets, adj)    # remeshing grid
+    zeta, q = bve_step_remeshed(grid, zeta, area, dt, omega, degree, tracer=q)
+    Server(...), autotune(...)                                   # serving, autotuner
 """
 from __future__ import annotations
 
