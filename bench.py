@@ -190,7 +190,17 @@ def cpu_oracle_sample(pts, w, wl, n_leaves, seed, repeats=1):
     for _ in range(repeats):
         f.evaluate(wl["kernel"], w, tg)
     dt = (time.perf_counter() - t0) / repeats
-    return len(tg) / dt, dt, len(tg), O.num_threads()
+    rate, threads = len(tg) / dt, O.num_threads()
+    # one thread on the first sixteenth of the leaves
+    tg1 = np.concatenate([order[C["begin"][c]:C["end"][c]] for c in pick[:max(1, len(pick) // 16)]])
+    O.set_num_threads(1)
+    try:
+        t0 = time.perf_counter()
+        f.evaluate(wl["kernel"], w, tg1)
+        dt1 = time.perf_counter() - t0
+    finally:
+        O.set_num_threads(threads)
+    return rate, dt, len(tg), threads, (len(tg1) / dt1, dt1, len(tg1))
 
 
 def fp64_at_matched_accuracy(Cs, torch, dpts, dw, wl, dim, dtg, ds, err32, ms32_per_rhs):
@@ -325,6 +335,16 @@ def run_ours(args):
     ms = ev0.elapsed_time(ev1)
     phases, calls = Cs.plan_phase_times(plan)
     Cs.plan_sync(plan)
+    # per-step times (after the timed region): median and minimum of K steps
+    step_ms = []
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        Cs.evaluate(plan, dw, out=out)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        step_ms.append(e0.elapsed_time(e1))
     launches = Cs.plan_stats(plan)["launches_per_evaluate"] * args.steps
     ms = max_over_ranks(ms, dist)
     ms_step = ms / args.steps
@@ -457,14 +477,18 @@ def run_ours(args):
                         "frac_of_alu_peak": (e / (m / 1e3) / peak_evals) if m > 0 else None}
                     for k, (e, m) in kern.items()},
         "clocks": clk.summary(),
+        "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms),
+                    "n": len(step_ms)},
     }
     if rank == 0 and world == 1 and args.serve_sample > 0:
         line["serving"] = run_serving(args, sample=args.serve_sample)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, dt, ntg, cores = cpu_oracle_sample(pts, w[:1], wl, args.cpu_leaves, 3)
+        v, dt, ntg, cores, one = cpu_oracle_sample(pts, w[:1], wl, args.cpu_leaves, 3)
         line["cpu_baseline"] = {"value": v, "unit": "targets/s", "cores": cores, "kind": "oracle",
                                 "sample": f"all {ntg} targets of {args.cpu_leaves} seeded random "
-                                          f"leaves, FP64 oracle FMM, {dt:.1f} s"}
+                                          f"leaves, FP64 oracle FMM, {dt:.1f} s",
+                                "single_thread": {"value": one[0], "unit": "targets/s",
+                                                  "sample": f"{one[2]} targets, {one[1]:.1f} s"}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     Cs.plan_destroy(plan)

@@ -95,6 +95,8 @@ def _load():
         lib.oracle_dilog.argtypes = [d]
         lib.oracle_dilog.restype = d
         lib.oracle_num_threads.restype = ctypes.c_int
+        lib.oracle_set_num_threads.argtypes = [ctypes.c_int]
+        lib.oracle_set_num_threads.restype = None
         _lib = lib
         return lib
 
@@ -109,6 +111,11 @@ def kernel_dim(kernel: int) -> int:
 
 def num_threads() -> int:
     return _load().oracle_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    """OpenMP threads of later oracle calls."""
+    _load().oracle_set_num_threads(int(n))
 
 
 def set_mutation(m: int) -> None:
