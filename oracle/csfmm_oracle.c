@@ -19,8 +19,12 @@
  *     Eq. downward_2),
  *   - the cubed sphere tree code (CSTC, Sec. 7, Algorithm "CSTC") on the
  *     same tree, proxies and upward pass,
+ *   - cells shrunk to bound their points (Sec. 3, optional),
+ *   - the Laplace, Biot-Savart, Newtonian, biharmonic (Eq. G_B) and SAL
+ *     (Eq. G_SAL_approx) kernels,
  * all in double precision, written for clarity rather than speed (OpenMP over
- * independent targets only).
+ * independent targets only).  Numbered planted mistakes (oracle_set_mutation)
+ * let the tests show that their pins catch each one.
  *
  * Readings of points the paper leaves open (each listed in the design notes):
  *   - 1 - x.y is evaluated as |x - y|^2 / 2 for unit vectors, and x cross y
