@@ -440,7 +440,8 @@ csfmm_status csfmm_remesh_grid_destroy(csfmm_remesh_grid grid);
  * onto the grid.  A passive tracer q (Sec. 12, dq/dt = 0 along particle
  * paths) rides on the same particles and is remeshed with the vorticity.
  * grid_plan, if not NULL, is a Biot-Savart plan built on the grid's points
- * (the first RK4 stage always starts there, so one plan serves every step);
+ * (the first RK4 stage always starts there, so one plan serves every step;
+ * that stage then uses the plan's own degree, MAC, leaf size and precision);
  * NULL builds one per step like the other stages.
  *   zeta, area device [M]; zeta_out device [M] (may be zeta)
  *   tracer, tracer_out device [M] (may be the same array), or both NULL
