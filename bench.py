@@ -304,8 +304,19 @@ def run_ours(args):
     prec = Cs.FP32_BULK if args.precision == "fp32" else Cs.FP64
     dpts = torch.from_numpy(pts).to(dev)
     dw = torch.from_numpy(w).to(dev)
+    tuned = None
+    if nrhs > 1 and args.autotune and prec == Cs.FP32_BULK:
+        # leaf size and right-hand-side chunk picked by the library's autotuner
+        # (timed evaluations, error within 2x of the default's), before timing
+        import tempfile
+        with tempfile.TemporaryDirectory() as td:
+            tuned = Cs.autotune(dpts, wl["kernel"], wl["n"], wl["theta"], dw, precision=prec,
+                                cache_path=os.path.join(td, "tune.txt"))
+        wl = dict(wl, N0=tuned["max_leaf"])
+        log("autotune", tuned)
     plan = Cs.plan_create(dpts, wl["kernel"], wl["n"], wl["theta"], wl["N0"], precision=prec,
-                          max_nrhs=max(nrhs, 1))
+                          max_nrhs=max(nrhs, 1),
+                          rhs_chunk=tuned["rhs_chunk"] if tuned else 0)
     st = Cs.plan_stats(plan)
     dim = Cs.kernel_dim(wl["kernel"])
     out = torch.empty((nrhs, N, dim), dtype=torch.float64, device=dev)
@@ -447,6 +458,7 @@ def run_ours(args):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if prec == Cs.FP32_BULK else "f64", "data": "synthetic",
+        "autotuned": tuned,
         "config": {"workload": args.workload, "desc": wl["desc"], "N": N, "nrhs": nrhs,
                    "kernel": wl["kernel"], "degree": wl["n"], "theta": wl["theta"],
                    "max_leaf": wl["N0"], "precision": args.precision,
@@ -951,6 +963,8 @@ def main():
     ap.add_argument("--ref-leaves", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", dest="fp64_compare", action="store_false")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="multi-RHS workloads: keep the default leaf size and RHS chunk")
     ap.add_argument("--sweep-m", type=int, default=1024)
     ap.add_argument("--sweep-degrees", default="6,8,10,12")
     ap.add_argument("--ico-level", type=int, default=8)
