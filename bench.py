@@ -854,6 +854,14 @@ def run_bve(args):
 
     x, z, A, dx, dz, dA, G = setup(args.bve_level)
     N = len(x)
+    if args.bve_quick:
+        # remeshed CSFMM FP32-bulk steps only (the case the profiles break down)
+        st = stepper(*forms["csfmm_fp32"], dx, dA, G, True)
+        ms = timed(st, dx, dz, args.steps, args.warmup)
+        return {"metric": "BVE remeshed RK4 step time, CSFMM FP32 bulk", "unit": "ms",
+                "value": ms, "higher_is_better": False,
+                "config": {"workload": "bve-rh-wave", "grid": f"icosahedral level {args.bve_level}",
+                           "N": N, "dt_day": dt, "degree": 6, "theta": 0.7, "max_leaf": 144}}
     rows = {}
     for tag, (deg, prec) in forms.items():
         slow = tag == "direct_fp64"
@@ -970,6 +978,8 @@ def main():
     ap.add_argument("--ico-level", type=int, default=8)
     ap.add_argument("--bve-level", type=int, default=7)
     ap.add_argument("--bve-days", type=float, default=1.0)
+    ap.add_argument("--bve-quick", action="store_true",
+                    help="bve workload: time remeshed CSFMM FP32 steps only")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-sample", type=int, default=300,
                     help="requests of the serving stream measured in the default line (0: none)")

@@ -126,74 +126,102 @@ __device__ __forceinline__ double data_chord(double hk) {
   return 2.0 * sin(0.5 * atan(kSc * hk)) * (1.0 + 1e-9);
 }
 
-// Breadth-first rings around k in S (S[0] = k); stops after the smallest ring
-// R whose next ring lies at least twice the data chord away, then sorts
-// S[0..n) ascending.  Returns n (the stencil size) and R, or -1 when no ring
-// up to kRemeshMaxRing qualifies within kRemeshMaxStencil points.
+// Breadth-first rings around k, one warp per grid point, in S (shared memory,
+// S[0] = k): stops after the smallest ring R whose next ring lies at least
+// twice the data chord away.  Returns n (the stencil size: S[0..n) holds rings
+// 0..R, in no particular order) and R, or -1 when no ring up to
+// kRemeshMaxRing qualifies within kRemeshMaxStencil points.  The lanes take
+// the vertices of a ring 32 at a time and step through their neighbour lists
+// together; a neighbour of ring r lies in ring r - 1, r or r + 1, so it is new
+// unless it is in S from the start of ring r - 1 on, and of equal new
+// neighbours met in one step the lowest lane's is kept.  Warp-uniform result.
 __device__ int stencil_set(int k, const double *g, const double *h, const int32_t *aoff,
                            const int32_t *adj, int *S, int *ring_out) {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned below = (1u << lane) - 1u;
   const double need = 2.0 * data_chord(h[k]);
   const double *gk = g + 3 * (size_t)k;
-  int n = 1, lo = 0;
-  S[0] = k;
+  if (lane == 0) S[0] = k;
+  __syncwarp();
+  int n = 1, lo = 0, plo = 0;
   for (int r = 0; r <= kRemeshMaxRing; ++r) {
     // grow ring r + 1 from ring r = S[lo..hi)
     const int hi = n;
     double dmin = 1e300;
-    for (int i = lo; i < hi; ++i) {
-      const int v = S[i];
-      for (int e = aoff[v]; e < aoff[v + 1]; ++e) {
-        const int w = adj[e];
-        bool seen = false;
-        for (int t = 0; t < n && !seen; ++t) seen = S[t] == w;
-        if (seen) continue;
-        if (n == kRemeshMaxStencil) return -1;
-        S[n++] = w;
-        dmin = fmin(dmin, sqrt(dist2(gk, g + 3 * (size_t)w)));
-      }
-    }
-    if (dmin >= need) {
-      // rings 0..r qualify: S[0..hi) is the stencil
-      n = hi;
-      *ring_out = r;
-      for (int a = 1; a < n; ++a) {
-        const int v = S[a];
-        int b = a - 1;
-        while (b >= 0 && S[b] > v) {
-          S[b + 1] = S[b];
-          --b;
+    for (int base = lo; base < hi; base += 32) {
+      const int i = base + (int)lane;
+      const int v = i < hi ? S[i] : 0;
+      const int eb = i < hi ? aoff[v] : 0;
+      const int deg = i < hi ? aoff[v + 1] - eb : 0;
+      int maxdeg = deg;
+      for (int o = 16; o; o >>= 1) maxdeg = max(maxdeg, __shfl_xor_sync(~0u, maxdeg, o));
+      for (int j = 0; j < maxdeg; ++j) {
+        const int w = j < deg ? adj[eb + j] : -1;
+        bool fresh = j < deg;
+        for (int t = plo; t < n && fresh; ++t) fresh = S[t] != w;
+        const unsigned same = __match_any_sync(~0u, w);
+        if (same & below) fresh = false;
+        const unsigned add = __ballot_sync(~0u, fresh);
+        if (n + __popc(add) > kRemeshMaxStencil) return -1;
+        if (fresh) {
+          S[n + __popc(add & below)] = w;
+          dmin = fmin(dmin, sqrt(dist2(gk, g + 3 * (size_t)w)));
         }
-        S[b + 1] = v;
+        n += __popc(add);
+        __syncwarp();
       }
-      return n;
     }
+    for (int o = 16; o; o >>= 1) dmin = fmin(dmin, __shfl_xor_sync(~0u, dmin, o));
+    if (dmin >= need) {
+      *ring_out = r;  // rings 0..r qualify: S[0..hi) is the stencil
+      return hi;
+    }
+    plo = lo;
     lo = hi;  // (a ring with no new grid point has dmin = 1e300: the whole grid)
   }
   return -1;
 }
 
-__global__ void stencil_count_kernel(const double *g, const double *h, const int32_t *aoff,
-                                     const int32_t *adj, int M, int32_t *cnt, int *max_ring,
-                                     int *status) {
-  int S[kRemeshMaxStencil];
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) {
+constexpr int kStencilWarps = 8;  // warps (grid points at a time) per block
+
+__global__ void __launch_bounds__(32 * kStencilWarps)
+stencil_count_kernel(const double *g, const double *h, const int32_t *aoff, const int32_t *adj,
+                     int M, int32_t *cnt, int *max_ring, int *status) {
+  __shared__ int Ss[kStencilWarps][kRemeshMaxStencil];
+  const int wid = threadIdx.x >> 5;
+  int *S = Ss[wid];
+  for (int k = blockIdx.x * kStencilWarps + wid; k < M; k += gridDim.x * kStencilWarps) {
     int r = 0;
     const int n = stencil_set(k, g, h, aoff, adj, S, &r);
-    if (n < 0) atomicOr(status, kRmStencil);
-    else atomicMax(max_ring, r);
-    cnt[k] = n < 0 ? 0 : n;
+    if ((threadIdx.x & 31) == 0) {
+      if (n < 0) atomicOr(status, kRmStencil);
+      else atomicMax(max_ring, r);
+      cnt[k] = n < 0 ? 0 : n;
+    }
+    __syncwarp();
   }
 }
 
-__global__ void stencil_fill_kernel(const double *g, const double *h, const int32_t *aoff,
-                                    const int32_t *adj, int M, const int32_t *soff,
-                                    int32_t *sten) {
-  int S[kRemeshMaxStencil];
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) {
+// The stencil of k in ascending order: each element goes to its rank (the
+// grid points are distinct).
+__global__ void __launch_bounds__(32 * kStencilWarps)
+stencil_fill_kernel(const double *g, const double *h, const int32_t *aoff, const int32_t *adj,
+                    int M, const int32_t *soff, int32_t *sten) {
+  __shared__ int Ss[kStencilWarps][kRemeshMaxStencil];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int *S = Ss[wid];
+  for (int k = blockIdx.x * kStencilWarps + wid; k < M; k += gridDim.x * kStencilWarps) {
     int r = 0;
     const int n = stencil_set(k, g, h, aoff, adj, S, &r);
-    if (n < 0) continue;
-    for (int i = 0; i < n; ++i) sten[soff[k] + i] = S[i];
+    if (n >= 0 && soff[k + 1] - soff[k] == n) {
+      for (int i = lane; i < n; i += 32) {
+        const int v = S[i];
+        int rank = 0;
+        for (int t = 0; t < n; ++t) rank += S[t] < v;
+        sten[soff[k] + rank] = v;
+      }
+    }
+    __syncwarp();
   }
 }
 
@@ -502,7 +530,8 @@ extern "C" csfmm_status csfmm_remesh_grid_create(const double *grid, int64_t M,
   // the scan of the stencil sizes reuses cnt; cursor[0] receives the largest ring
   e = cudaMemsetAsync(G->cursor, 0, sizeof(int32_t), st);
   if (e != cudaSuccess) return fail(cuda_status(e, "cudaMemsetAsync"));
-  stencil_count_kernel<<<gr, 256, 0, st>>>(G->g, G->h, G->aoff, G->adj, (int)M, G->cnt, G->cursor,
+  const int grs = grid_for(M, kStencilWarps, 152 * 16);
+  stencil_count_kernel<<<grs, 32 * kStencilWarps, 0, st>>>(G->g, G->h, G->aoff, G->adj, (int)M, G->cnt, G->cursor,
                                            G->status);
   int32_t total = 0;
   e = cudaMemsetAsync(G->cnt + M, 0, sizeof(int32_t), st);
@@ -517,7 +546,7 @@ extern "C" csfmm_status csfmm_remesh_grid_create(const double *grid, int64_t M,
   if (s != CSFMM_OK) return fail(s);
   e = cudaMemcpyAsync(&G->max_ring, G->cursor, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e != cudaSuccess) return fail(cuda_status(e, "cudaMemcpyAsync"));
-  stencil_fill_kernel<<<gr, 256, 0, st>>>(G->g, G->h, G->aoff, G->adj, (int)M, G->soff, G->sten);
+  stencil_fill_kernel<<<grs, 32 * kStencilWarps, 0, st>>>(G->g, G->h, G->aoff, G->adj, (int)M, G->soff, G->sten);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(cuda_status(e, "stencil_fill_kernel"));
