@@ -27,9 +27,9 @@
 // least twice the data-disc chord from g_k hold every datum of g_k; that
 // stencil is fixed per grid point when the grid is made.
 //
-// Work per remeshing: one walk per particle, the counting sort, and one
-// thread per grid point that filters the stencil's particles, accumulates the
-// 21 + 6 weighted normal-equation sums in FP64 and solves by an unrolled 6x6
+// Work per remeshing: one walk per particle, the counting sort, and four
+// lanes per grid point that filter the stencil's particles, accumulate the
+// 21 + 6 weighted normal-equation sums in FP64 and solve by an unrolled 6x6
 // Cholesky (the scaled coordinates keep its condition number near 1e2).
 #include <math.h>
 
@@ -286,14 +286,24 @@ __global__ void bucket_sort_kernel(const int32_t *boff, int M, int32_t *bucket, 
 
 // Step 3: weighted quadratic least squares at every grid point.
 // NF fields f[0..NF) (stride M) share the normal matrix; each gets its own
-// right-hand side and solve.
+// right-hand side and solve.  kFitLanes lanes serve one grid point: lane l
+// takes stencil cells l, l + kFitLanes, ... and the partial sums are added
+// across the lanes by a butterfly (every lane ends with the same bits, as
+// IEEE addition commutes), so the result does not depend on scheduling.  A
+// candidate is tested against the disc without division,
+// (x.e1)^2 + (x.e2)^2 < kSc^2 (x.g_k h_k)^2, and a datum costs one reciprocal.
+constexpr int kFitLanes = 4;
+
 template <int NF>
 __global__ void __launch_bounds__(128) fit_kernel(const double *x, const double *f,
                                                   const double *g, const double *h,
                                                   const int32_t *soff, const int32_t *sten,
                                                   const int32_t *boff, const int32_t *bucket,
                                                   int M, double *out, int *status) {
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) {
+  const int sub = threadIdx.x % kFitLanes;
+  const unsigned group = ((1u << kFitLanes) - 1u) << ((threadIdx.x & 31) & ~(kFitLanes - 1));
+  for (int k = (blockIdx.x * blockDim.x + threadIdx.x) / kFitLanes; k < M;
+       k += gridDim.x * blockDim.x / kFitLanes) {
     const double gk[3] = {g[3 * (size_t)k], g[3 * (size_t)k + 1], g[3 * (size_t)k + 2]};
     // e1 = a x g / |a x g| with a = e_z, or e_x near the poles; e2 = g x e1
     double e1[3];
@@ -306,13 +316,14 @@ __global__ void __launch_bounds__(128) fit_kernel(const double *x, const double 
       e1[1] = -gk[2];
       e1[2] = gk[1];
     }
-    const double in = 1.0 / sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+    const double in = rsqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
     e1[0] *= in;
     e1[1] *= in;
     e1[2] *= in;
     const double e2[3] = {gk[1] * e1[2] - gk[2] * e1[1], gk[2] * e1[0] - gk[0] * e1[2],
                           gk[0] * e1[1] - gk[1] * e1[0]};
     const double hk = h[k];
+    constexpr double kSc2 = kSc * kSc;
     double A[21], b[NF][6];  // packed lower triangle of sum w phi phi^T, sum w phi f
 #pragma unroll
     for (int i = 0; i < 21; ++i) A[i] = 0.0;
@@ -321,19 +332,20 @@ __global__ void __launch_bounds__(128) fit_kernel(const double *x, const double 
 #pragma unroll
       for (int i = 0; i < 6; ++i) b[q][i] = 0.0;
     int n = 0;
-    for (int s = soff[k]; s < soff[k + 1]; ++s) {
+    for (int s = soff[k] + sub; s < soff[k + 1]; s += kFitLanes) {
       const int c = sten[s];
       for (int q = boff[c]; q < boff[c + 1]; ++q) {
         const int p = bucket[q];
         const double *xp = x + 3 * (size_t)p;
-        const double dot = xp[0] * gk[0] + xp[1] * gk[1] + xp[2] * gk[2];
-        if (!(dot > 0.0)) continue;
+        const double x0 = xp[0], x1 = xp[1], x2 = xp[2];
+        const double dot = x0 * gk[0] + x1 * gk[1] + x2 * gk[2];
         const double den = dot * hk;
-        const double u = (xp[0] * e1[0] + xp[1] * e1[1] + xp[2] * e1[2]) / den;
-        const double v = (xp[0] * e2[0] + xp[1] * e2[1] + xp[2] * e2[2]) / den;
-        const double s2 = u * u + v * v;
-        if (!(s2 < kSc * kSc)) continue;
-        const double om = 1.0 - s2 * (1.0 / (kSc * kSc));
+        const double a1 = x0 * e1[0] + x1 * e1[1] + x2 * e1[2];
+        const double a2 = x0 * e2[0] + x1 * e2[1] + x2 * e2[2];
+        if (!(dot > 0.0) || !(a1 * a1 + a2 * a2 < kSc2 * (den * den))) continue;
+        const double r = 1.0 / den;
+        const double u = a1 * r, v = a2 * r;
+        const double om = fmax(1.0 - (u * u + v * v) * (1.0 / kSc2), 0.0);
         const double om2 = om * om;
         const double w = om2 * om2;
         const double phi[6] = {1.0, u, v, u * u, u * v, v * v};
@@ -353,37 +365,57 @@ __global__ void __launch_bounds__(128) fit_kernel(const double *x, const double 
         ++n;
       }
     }
-    if (n < 6) {
-      atomicOr(status, kRmFit);
 #pragma unroll
-      for (int q = 0; q < NF; ++q) out[(size_t)q * M + k] = 0.0;
+    for (int o = 1; o < kFitLanes; o <<= 1) {
+#pragma unroll
+      for (int i = 0; i < 21; ++i) A[i] += __shfl_xor_sync(group, A[i], o);
+#pragma unroll
+      for (int q = 0; q < NF; ++q)
+#pragma unroll
+        for (int i = 0; i < 6; ++i) b[q][i] += __shfl_xor_sync(group, b[q][i], o);
+      n += __shfl_xor_sync(group, n, o);
+    }
+    if (n < 6) {
+      if (sub == 0) {
+        atomicOr(status, kRmFit);
+#pragma unroll
+        for (int q = 0; q < NF; ++q) out[(size_t)q * M + k] = 0.0;
+      }
       continue;
     }
-    // Cholesky A = L L^T in place (packed lower triangle), then L y = b, L^T c = y.
+    // Cholesky A = L L^T in place (packed lower triangle), then L y = b, L^T c = y,
+    // with the reciprocals of the diagonal from rsqrt (no division).
     double amax = 0.0;
 #pragma unroll
     for (int i = 0; i < 6; ++i) amax = fmax(amax, A[i * (i + 1) / 2 + i]);
     bool ok = true;
+    double rl[6];
+    // (constant trip counts with guards, so that every loop unrolls and A stays
+    // in registers)
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
       double d = A[j * (j + 1) / 2 + j];
 #pragma unroll
-      for (int m = 0; m < j; ++m) d -= A[j * (j + 1) / 2 + m] * A[j * (j + 1) / 2 + m];
+      for (int m = 0; m < 6; ++m)
+        if (m < j) d -= A[j * (j + 1) / 2 + m] * A[j * (j + 1) / 2 + m];
       if (!(d > 1e-13 * amax)) ok = false;
-      const double ljj = sqrt(fmax(d, 1e-300));
-      A[j * (j + 1) / 2 + j] = ljj;
+      rl[j] = rsqrt(fmax(d, 1e-300));
 #pragma unroll
-      for (int i = j + 1; i < 6; ++i) {
+      for (int i = 0; i < 6; ++i) {
+        if (i <= j) continue;
         double s = A[i * (i + 1) / 2 + j];
 #pragma unroll
-        for (int m = 0; m < j; ++m) s -= A[i * (i + 1) / 2 + m] * A[j * (j + 1) / 2 + m];
-        A[i * (i + 1) / 2 + j] = s / ljj;
+        for (int m = 0; m < 6; ++m)
+          if (m < j) s -= A[i * (i + 1) / 2 + m] * A[j * (j + 1) / 2 + m];
+        A[i * (i + 1) / 2 + j] = s * rl[j];
       }
     }
     if (!ok) {
-      atomicOr(status, kRmFit);
+      if (sub == 0) {
+        atomicOr(status, kRmFit);
 #pragma unroll
-      for (int q = 0; q < NF; ++q) out[(size_t)q * M + k] = 0.0;
+        for (int q = 0; q < NF; ++q) out[(size_t)q * M + k] = 0.0;
+      }
       continue;
     }
 #pragma unroll
@@ -394,7 +426,7 @@ __global__ void __launch_bounds__(128) fit_kernel(const double *x, const double 
         double s = b[q][i];
 #pragma unroll
         for (int m = 0; m < i; ++m) s -= A[i * (i + 1) / 2 + m] * y[m];
-        y[i] = s / A[i * (i + 1) / 2 + i];
+        y[i] = s * rl[i];
       }
       double c[6];
 #pragma unroll
@@ -402,9 +434,9 @@ __global__ void __launch_bounds__(128) fit_kernel(const double *x, const double 
         double s = y[i];
 #pragma unroll
         for (int m = i + 1; m < 6; ++m) s -= A[m * (m + 1) / 2 + i] * c[m];
-        c[i] = s / A[i * (i + 1) / 2 + i];
+        c[i] = s * rl[i];
       }
-      out[(size_t)q * M + k] = c[0];
+      if (sub == 0) out[(size_t)q * M + k] = c[0];
     }
   }
 }
@@ -441,7 +473,7 @@ csfmm_status remesh_impl(csfmm_remesh_grid G, const double *x, const double *f, 
   bucket_fill_kernel<<<grid, 256, 0, st>>>(G->cell, M, G->boff, G->cursor, G->bucket);
   bucket_sort_kernel<<<grid, 256, 0, st>>>(G->boff, M, G->bucket, G->status);
   // fields in pairs (the second pair re-reads the stencil; the walk and sort are shared)
-  const int fg = grid_for(M, 128, 152 * 16);
+  const int fg = grid_for((int64_t)M * kFitLanes, 128, 152 * 16);
   for (int q = 0; q < nfield; q += 2) {
     const double *fq = f + (size_t)q * M;
     double *oq = f_out + (size_t)q * M;
