@@ -24,8 +24,10 @@
 // nearest to g_k outside the ring-R neighbourhood of g_k lies on ring R+1 (the
 // cells met by the segment from g_k to any outer grid point are no farther
 // from g_k).  So the cells of the smallest ring R whose next ring stays at
-// least twice the data-disc chord from g_k hold every datum of g_k; that
-// stencil is fixed per grid point when the grid is made.
+// least twice the data-disc chord from g_k hold every datum of g_k.  Of these,
+// the cells whose grid point is farther from g_k than the data chord plus the
+// cell's own radius (its farthest Voronoi vertex) hold none and are dropped;
+// the stencil is fixed per grid point when the grid is made.
 //
 // Work per remeshing: one walk per particle, the counting sort, and four
 // lanes per grid point that filter the stencil's particles, accumulate the
@@ -45,6 +47,7 @@ struct csfmm_remesh_grid_s {
   double *h = nullptr;        // [M] chord to the nearest neighbour
   int32_t *aoff = nullptr;    // [M+1] triangulation neighbours (CSR)
   int32_t *adj = nullptr;     // [nadj]
+  double *rho = nullptr;      // [M] largest chord from a grid point to its Voronoi cell
   int32_t *soff = nullptr;    // [M+1] stencils (CSR)
   int32_t *sten = nullptr;    // [soff[M]]
   // per-remeshing scratch
@@ -126,6 +129,51 @@ __device__ __forceinline__ double data_chord(double hk) {
   return 2.0 * sin(0.5 * atan(kSc * hk)) * (1.0 + 1e-9);
 }
 
+// rho_c: the largest chord from grid point c to a vertex of its Voronoi cell,
+// which bounds the chord from g_c to any particle in its cell (the cell is
+// convex and inside the hemisphere about g_c, so its farthest point is a
+// vertex).  The vertices are the circumcentres of the triangles (c, a, b) at c,
+// taken as the pairs of neighbours of c joined by an edge: three mutually
+// joined points that are not a face only add a candidate to the maximum.  A
+// degenerate triangle, or none at all, gives rho = 2 (the whole sphere).
+__global__ void cell_radius_kernel(const double *g, const int32_t *aoff, const int32_t *adj,
+                                   int M, double *rho) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < M; c += gridDim.x * blockDim.x) {
+    const double *gc = g + 3 * (size_t)c;
+    double best = 0.0;
+    bool any = false;
+    for (int e = aoff[c]; e < aoff[c + 1]; ++e) {
+      const int a = adj[e];
+      const double *ga = g + 3 * (size_t)a;
+      for (int f = aoff[a]; f < aoff[a + 1]; ++f) {
+        const int b = adj[f];
+        if (b <= a) continue;  // each pair once
+        bool joined = false;
+        for (int t = aoff[c]; t < aoff[c + 1] && !joined; ++t) joined = adj[t] == b;
+        if (!joined) continue;
+        const double *gb = g + 3 * (size_t)b;
+        const double d1[3] = {ga[0] - gc[0], ga[1] - gc[1], ga[2] - gc[2]};
+        const double d2[3] = {gb[0] - gc[0], gb[1] - gc[1], gb[2] - gc[2]};
+        double q[3] = {d1[1] * d2[2] - d1[2] * d2[1], d1[2] * d2[0] - d1[0] * d2[2],
+                       d1[0] * d2[1] - d1[1] * d2[0]};
+        const double nn = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+        any = true;
+        if (!(nn > 0.0)) {
+          best = 2.0;
+          continue;
+        }
+        double sc = rsqrt(nn);
+        if (q[0] * gc[0] + q[1] * gc[1] + q[2] * gc[2] < 0.0) sc = -sc;
+        q[0] *= sc;
+        q[1] *= sc;
+        q[2] *= sc;
+        best = fmax(best, sqrt(dist2(q, gc)));
+      }
+    }
+    rho[c] = any ? fmin(best, 2.0) : 2.0;
+  }
+}
+
 // Breadth-first rings around k, one warp per grid point, in S (shared memory,
 // S[0] = k): stops after the smallest ring R whose next ring lies at least
 // twice the data chord away.  Returns n (the stencil size: S[0..n) holds rings
@@ -134,9 +182,13 @@ __device__ __forceinline__ double data_chord(double hk) {
 // the vertices of a ring 32 at a time and step through their neighbour lists
 // together; a neighbour of ring r lies in ring r - 1, r or r + 1, so it is new
 // unless it is in S from the start of ring r - 1 on, and of equal new
-// neighbours met in one step the lowest lane's is kept.  Warp-uniform result.
-__device__ int stencil_set(int k, const double *g, const double *h, const int32_t *aoff,
-                           const int32_t *adj, int *S, int *ring_out) {
+// neighbours met in one step the lowest lane's is kept.  Of rings 0..R only
+// the cells that can hold a datum are kept: a particle in the cell of c is
+// within rho_c of g_c, so by the triangle inequality for chords the cell holds
+// none when |g_c - g_k| > data chord + rho_c (about 28 of 91 cells stay on the
+// icosahedral grids).  Warp-uniform result.
+__device__ int stencil_set(int k, const double *g, const double *h, const double *rho,
+                           const int32_t *aoff, const int32_t *adj, int *S, int *ring_out) {
   const unsigned lane = threadIdx.x & 31u;
   const unsigned below = (1u << lane) - 1u;
   const double need = 2.0 * data_chord(h[k]);
@@ -173,8 +225,21 @@ __device__ int stencil_set(int k, const double *g, const double *h, const int32_
     }
     for (int o = 16; o; o >>= 1) dmin = fmin(dmin, __shfl_xor_sync(~0u, dmin, o));
     if (dmin >= need) {
-      *ring_out = r;  // rings 0..r qualify: S[0..hi) is the stencil
-      return hi;
+      *ring_out = r;  // rings 0..r qualify: S[0..hi) holds every datum
+      const double chord = data_chord(h[k]);
+      int m = 0;  // compact in place: a write lands below the chunk being read
+      for (int base = 0; base < hi; base += 32) {
+        const int i = base + (int)lane;
+        const int c = i < hi ? S[i] : 0;
+        const bool keep =
+            i < hi && sqrt(dist2(gk, g + 3 * (size_t)c)) <= chord + rho[c] * (1.0 + 1e-9);
+        const unsigned kb = __ballot_sync(~0u, keep);
+        __syncwarp();  // every lane has read its S[i]
+        if (keep) S[m + __popc(kb & below)] = c;
+        m += __popc(kb);
+        __syncwarp();
+      }
+      return m;
     }
     plo = lo;
     lo = hi;  // (a ring with no new grid point has dmin = 1e300: the whole grid)
@@ -185,14 +250,14 @@ __device__ int stencil_set(int k, const double *g, const double *h, const int32_
 constexpr int kStencilWarps = 8;  // warps (grid points at a time) per block
 
 __global__ void __launch_bounds__(32 * kStencilWarps)
-stencil_count_kernel(const double *g, const double *h, const int32_t *aoff, const int32_t *adj,
-                     int M, int32_t *cnt, int *max_ring, int *status) {
+stencil_count_kernel(const double *g, const double *h, const double *rho, const int32_t *aoff,
+                     const int32_t *adj, int M, int32_t *cnt, int *max_ring, int *status) {
   __shared__ int Ss[kStencilWarps][kRemeshMaxStencil];
   const int wid = threadIdx.x >> 5;
   int *S = Ss[wid];
   for (int k = blockIdx.x * kStencilWarps + wid; k < M; k += gridDim.x * kStencilWarps) {
     int r = 0;
-    const int n = stencil_set(k, g, h, aoff, adj, S, &r);
+    const int n = stencil_set(k, g, h, rho, aoff, adj, S, &r);
     if ((threadIdx.x & 31) == 0) {
       if (n < 0) atomicOr(status, kRmStencil);
       else atomicMax(max_ring, r);
@@ -205,14 +270,14 @@ stencil_count_kernel(const double *g, const double *h, const int32_t *aoff, cons
 // The stencil of k in ascending order: each element goes to its rank (the
 // grid points are distinct).
 __global__ void __launch_bounds__(32 * kStencilWarps)
-stencil_fill_kernel(const double *g, const double *h, const int32_t *aoff, const int32_t *adj,
-                    int M, const int32_t *soff, int32_t *sten) {
+stencil_fill_kernel(const double *g, const double *h, const double *rho, const int32_t *aoff,
+                    const int32_t *adj, int M, const int32_t *soff, int32_t *sten) {
   __shared__ int Ss[kStencilWarps][kRemeshMaxStencil];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int *S = Ss[wid];
   for (int k = blockIdx.x * kStencilWarps + wid; k < M; k += gridDim.x * kStencilWarps) {
     int r = 0;
-    const int n = stencil_set(k, g, h, aoff, adj, S, &r);
+    const int n = stencil_set(k, g, h, rho, aoff, adj, S, &r);
     if (n >= 0 && soff[k + 1] - soff[k] == n) {
       for (int i = lane; i < n; i += 32) {
         const int v = S[i];
@@ -531,6 +596,7 @@ extern "C" csfmm_status csfmm_remesh_grid_create(const double *grid, int64_t M,
   A(&G->h, (size_t)M);
   A(&G->aoff, (size_t)M + 1);
   A(&G->adj, (size_t)nadj);
+  A(&G->rho, (size_t)M);
   A(&G->soff, (size_t)M + 1);
   A(&G->cell, (size_t)M);
   A(&G->cnt, (size_t)M + 1);
@@ -563,8 +629,9 @@ extern "C" csfmm_status csfmm_remesh_grid_create(const double *grid, int64_t M,
   e = cudaMemsetAsync(G->cursor, 0, sizeof(int32_t), st);
   if (e != cudaSuccess) return fail(cuda_status(e, "cudaMemsetAsync"));
   const int grs = grid_for(M, kStencilWarps, 152 * 16);
-  stencil_count_kernel<<<grs, 32 * kStencilWarps, 0, st>>>(G->g, G->h, G->aoff, G->adj, (int)M, G->cnt, G->cursor,
-                                           G->status);
+  cell_radius_kernel<<<gr, 256, 0, st>>>(G->g, G->aoff, G->adj, (int)M, G->rho);
+  stencil_count_kernel<<<grs, 32 * kStencilWarps, 0, st>>>(G->g, G->h, G->rho, G->aoff, G->adj,
+                                                            (int)M, G->cnt, G->cursor, G->status);
   int32_t total = 0;
   e = cudaMemsetAsync(G->cnt + M, 0, sizeof(int32_t), st);
   if (e != cudaSuccess) return fail(cuda_status(e, "cudaMemsetAsync"));
@@ -578,7 +645,8 @@ extern "C" csfmm_status csfmm_remesh_grid_create(const double *grid, int64_t M,
   if (s != CSFMM_OK) return fail(s);
   e = cudaMemcpyAsync(&G->max_ring, G->cursor, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e != cudaSuccess) return fail(cuda_status(e, "cudaMemcpyAsync"));
-  stencil_fill_kernel<<<grs, 32 * kStencilWarps, 0, st>>>(G->g, G->h, G->aoff, G->adj, (int)M, G->soff, G->sten);
+  stencil_fill_kernel<<<grs, 32 * kStencilWarps, 0, st>>>(G->g, G->h, G->rho, G->aoff, G->adj,
+                                                           (int)M, G->soff, G->sten);
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(cuda_status(e, "stencil_fill_kernel"));
