@@ -157,3 +157,32 @@ def test_remeshed_tracer_trajectory_matches_oracle(torch, C):
     eq = np.abs(dq.cpu().numpy() - qr).max()
     print(f"\n8 remeshed steps with tracer: zeta err {ez:.2e}, tracer err {eq:.2e}")
     assert ez < 1e-11 and eq < 1e-11
+
+
+@pytest.mark.parametrize("grid_kind", ["icosahedral", "variable"])
+def test_remesh_random_moves_matches_oracle(torch, C, grid_kind):
+    """Particles moved by seeded random tangent steps of up to 0.9 of the local
+    spacing: many cross cell boundaries and data-disc edges in every direction.
+    On the Schmidt-mapped grid (a conformal map, so the mapped triangulation
+    stays Delaunay) spacings and cell radii vary 4x over the sphere, which
+    exercises stencils sized and pruned per grid point."""
+    level = 4
+    verts, faces = I.icosahedral_triangulation(level)
+    x = verts if grid_kind == "icosahedral" else I.schmidt_transform(verts, 0.5)
+    off, nb = I.grid_adjacency(faces, len(x))
+    h = np.array([np.linalg.norm(x[nb[off[k]:off[k + 1]]] - x[k], axis=1).min()
+                  for k in range(len(x))])
+    rng = np.random.default_rng(I.MASTER_SEED + 71)
+    d = rng.normal(size=x.shape)
+    d -= (d * x).sum(1, keepdims=True) * x
+    d *= (0.9 * h * rng.uniform(size=len(x)) / np.linalg.norm(d, axis=1))[:, None]
+    xs = x + d
+    xs /= np.linalg.norm(xs, axis=1, keepdims=True)
+    f = np.stack([I.rossby_haurwitz_vorticity(xs), np.cos(3 * xs[:, 0]) * xs[:, 2]])
+    G = C.remesh_grid_create(dev(torch, x), dev(torch, off), dev(torch, nb))
+    got = C.remesh(G, dev(torch, xs), dev(torch, f)).cpu().numpy()
+    for q in range(2):
+        ref = B.remesh(x, off, nb, xs, f[q])
+        err = np.abs(got[q] - ref).max() / np.abs(f[q]).max()
+        print(f"\n{grid_kind} level {level}, field {q}: max err {err:.2e}")
+        assert err < 1e-12
