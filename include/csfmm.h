@@ -411,7 +411,10 @@ csfmm_status csfmm_bve_step(const double *x, const double *zeta, const double *a
  * exactly, is third-order accurate for smooth data and depends continuously
  * on the particle positions.  The particles are found through their nearest
  * grid points (a greedy walk on the triangulation from g_p) and per-point
- * stencils of whole triangulation rings sized when the grid is made.
+ * stencils made when the grid is made: the triangulation rings about g_k that
+ * hold its data disc, less the cells whose grid point is farther from g_k
+ * than the disc's chord plus the cell's own radius (the chord to its farthest
+ * Voronoi vertex, a circumcentre of the triangles at the cell's point).
  *   grid         device [M][3] FP64 unit vectors (copied), 7 <= M < 2^30
  *   adj_offsets  device int64 [M+1], adj device int64 [adj_offsets[M]]: the
  *                neighbours of g_k are adj[adj_offsets[k] .. adj_offsets[k+1])
