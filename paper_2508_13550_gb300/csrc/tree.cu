@@ -236,17 +236,31 @@ csfmm_status exclusive_scan_i32(const int32_t *in, int32_t *out, int n, int32_t 
 // ---------------------------------------------------------------------------
 // Stable LSD radix sort of (u64 key, i32 value), 4-bit digits.
 // ---------------------------------------------------------------------------
+// A block sorts a tile of kSortThreads x ITEMS keys; ITEMS shrinks with n so
+// that a pass has at least about two blocks per SM (a 164k-key sort with
+// 4096-key tiles ran 40 blocks on 152 SMs).
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
-constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kSortMinItems = 2;
 
+static int sort_items(int n) {
+  constexpr int64_t kBlocks = 2 * 152;
+  if (n >= kBlocks * kSortThreads * 16) return 16;
+  if (n >= kBlocks * kSortThreads * 8) return 8;
+  if (n >= kBlocks * kSortThreads * 4) return 4;
+  return kSortMinItems;
+}
+
+// Sized for the smallest tile, so that it never decreases with n.
 size_t radix_tmp_elems(int n) {
-  int nb = (n + kSortTile - 1) / kSortTile;
+  const int tile = kSortThreads * kSortMinItems;
+  int nb = (n + tile - 1) / tile;
   if (nb < 1) nb = 1;
   return (size_t)16 * nb + scan_tmp_elems(16 * nb) + 16;
 }
 
+template <int ITEMS>
 __global__ void radix_hist_kernel(const uint64_t *keys, int n, int shift, int32_t *hist, int nb) {
+  constexpr int kSortTile = kSortThreads * ITEMS;
   __shared__ int cnt[16];
   if (threadIdx.x < 16) cnt[threadIdx.x] = 0;
   __syncthreads();
@@ -259,8 +273,10 @@ __global__ void radix_hist_kernel(const uint64_t *keys, int n, int shift, int32_
   if (threadIdx.x < 16) hist[threadIdx.x * nb + blockIdx.x] = cnt[threadIdx.x];
 }
 
+template <int kSortItems>
 __global__ void radix_scatter_kernel(const uint64_t *keys, const int32_t *vals, uint64_t *okeys,
                                      int32_t *ovals, int n, int shift, const int32_t *offs, int nb) {
+  constexpr int kSortTile = kSortThreads * kSortItems;
   __shared__ int tcount[16][kSortThreads + 1];
   int t = threadIdx.x;
   int64_t base = (int64_t)blockIdx.x * kSortTile + (int64_t)t * kSortItems;
@@ -332,7 +348,8 @@ csfmm_status radix_sort_u64(uint64_t *keys, int32_t *vals, uint64_t *keys_alt, i
                             cudaStream_t st, bool *result_in_alt) {
   *result_in_alt = false;
   if (n <= 1) return CSFMM_OK;
-  int nb = (n + kSortTile - 1) / kSortTile;
+  const int items = sort_items(n);
+  const int nb = (n + kSortThreads * items - 1) / (kSortThreads * items);
   if (tmp_elems < radix_tmp_elems(n)) {
     set_error("radix sort: temporary buffer too small");
     return CSFMM_ERR_INVALID_ARG;
@@ -343,10 +360,28 @@ csfmm_status radix_sort_u64(uint64_t *keys, int32_t *vals, uint64_t *keys_alt, i
   int32_t *va = vals, *vb = vals_alt;
   bool alt = false;
   for (int shift = begin_bit; shift < end_bit; shift += 4) {
-    radix_hist_kernel<<<nb, kSortThreads, 0, st>>>(ka, n, shift, hist, nb);
+    switch (items) {
+      case 16: radix_hist_kernel<16><<<nb, kSortThreads, 0, st>>>(ka, n, shift, hist, nb); break;
+      case 8: radix_hist_kernel<8><<<nb, kSortThreads, 0, st>>>(ka, n, shift, hist, nb); break;
+      case 4: radix_hist_kernel<4><<<nb, kSortThreads, 0, st>>>(ka, n, shift, hist, nb); break;
+      default: radix_hist_kernel<2><<<nb, kSortThreads, 0, st>>>(ka, n, shift, hist, nb); break;
+    }
     csfmm_status s = exclusive_scan_i32(hist, hist, 16 * nb, nullptr, scan_tmp, st);
     if (s != CSFMM_OK) return s;
-    radix_scatter_kernel<<<nb, kSortThreads, 0, st>>>(ka, va, kb, vb, n, shift, hist, nb);
+    switch (items) {
+      case 16:
+        radix_scatter_kernel<16><<<nb, kSortThreads, 0, st>>>(ka, va, kb, vb, n, shift, hist, nb);
+        break;
+      case 8:
+        radix_scatter_kernel<8><<<nb, kSortThreads, 0, st>>>(ka, va, kb, vb, n, shift, hist, nb);
+        break;
+      case 4:
+        radix_scatter_kernel<4><<<nb, kSortThreads, 0, st>>>(ka, va, kb, vb, n, shift, hist, nb);
+        break;
+      default:
+        radix_scatter_kernel<2><<<nb, kSortThreads, 0, st>>>(ka, va, kb, vb, n, shift, hist, nb);
+        break;
+    }
     CSFMM_CUDA(cudaGetLastError());
     std::swap(ka, kb);
     std::swap(va, vb);
