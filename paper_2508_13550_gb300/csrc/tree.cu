@@ -211,6 +211,15 @@ static void scan_rec(const int32_t *in, int32_t *out, int n, int32_t *tmp, cudaS
   add_block_offsets_kernel<<<nb, kScanThreads, 0, st>>>(out, sums, n);
 }
 
+// total = last input + last exclusive prefix, for one or two scans, gathered
+// on the device so that a single read (one host synchronisation) returns them.
+__global__ void scan_totals_kernel(const int32_t *in1, const int32_t *out1, const int32_t *in2,
+                                   const int32_t *out2, int n, int32_t *dst) {
+  dst[0] = in1[n - 1] + out1[n - 1];
+  if (in2) dst[1] = in2[n - 1] + out2[n - 1];
+}
+
+// tmp[0..1] (kept free by scan_tmp_elems) receive the totals.
 csfmm_status exclusive_scan_i32(const int32_t *in, int32_t *out, int n, int32_t *total_host,
                                 int32_t *tmp, cudaStream_t st) {
   // in may alias out only if total_host == nullptr (the last input is needed).
@@ -218,18 +227,34 @@ csfmm_status exclusive_scan_i32(const int32_t *in, int32_t *out, int n, int32_t 
     if (total_host) *total_host = 0;
     return CSFMM_OK;
   }
-  int32_t last_in = 0;
-  if (total_host) {
-    CSFMM_CUDA(cudaMemcpyAsync(&last_in, in + n - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-  }
   scan_rec(in, out, n, tmp + 2, st);
   CSFMM_CUDA(cudaGetLastError());
   if (total_host) {
-    int32_t last_out = 0;
-    CSFMM_CUDA(cudaMemcpyAsync(&last_out, out + n - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    scan_totals_kernel<<<1, 1, 0, st>>>(in, out, nullptr, nullptr, n, tmp);
+    CSFMM_CUDA(cudaGetLastError());
+    CSFMM_CUDA(cudaMemcpyAsync(total_host, tmp, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     CSFMM_CUDA(cudaStreamSynchronize(st));
-    *total_host = last_out + last_in;
   }
+  return CSFMM_OK;
+}
+
+// Two exclusive scans of length n (no aliasing of in and out) and one host read
+// of both totals.
+static csfmm_status exclusive_scan2_i32(const int32_t *in1, int32_t *out1, const int32_t *in2,
+                                        int32_t *out2, int n, int32_t *total1, int32_t *total2,
+                                        int32_t *tmp, cudaStream_t st) {
+  *total1 = *total2 = 0;
+  if (n <= 0) return CSFMM_OK;
+  scan_rec(in1, out1, n, tmp + 2, st);
+  scan_rec(in2, out2, n, tmp + 2, st);
+  CSFMM_CUDA(cudaGetLastError());
+  scan_totals_kernel<<<1, 1, 0, st>>>(in1, out1, in2, out2, n, tmp);
+  CSFMM_CUDA(cudaGetLastError());
+  int32_t t[2] = {0, 0};
+  CSFMM_CUDA(cudaMemcpyAsync(t, tmp, sizeof(t), cudaMemcpyDeviceToHost, st));
+  CSFMM_CUDA(cudaStreamSynchronize(st));
+  *total1 = t[0];
+  *total2 = t[1];
   return CSFMM_OK;
 }
 
@@ -1106,13 +1131,8 @@ csfmm_status build_tree(Plan &pl, const double *points, cudaStream_t st) {
   CSFMM_TRY(tmp.alloc(&rtmp, rtmp_n));
   key_points_kernel<<<grid_for(N, 256, 152 * 64), 256, 0, st>>>(points, N, T, keys, idx, pl.status);
   CSFMM_CUDA(cudaGetLastError());
-  int hstat = 0;
-  CSFMM_CUDA(cudaMemcpyAsync(&hstat, pl.status, sizeof(int), cudaMemcpyDeviceToHost, st));
-  CSFMM_CUDA(cudaStreamSynchronize(st));
-  if (hstat & kStatusNotOnSphere) {
-    set_error("a point is not on the unit sphere (| |x|^2 - 1 | > 1e-12) or is not finite");
-    return CSFMM_ERR_NOT_ON_SPHERE;
-  }
+  // (the status word is read with the face bounds below: a point off the sphere
+  // has key 0 and sorts like any other)
   bool in_alt = false;
   CSFMM_TRY(radix_sort_u64(keys, idx, keys2, idx2, N, 0, 2 * kD + 4, rtmp, rtmp_n, st, &in_alt));
   if (in_alt) {
@@ -1130,12 +1150,17 @@ csfmm_status build_tree(Plan &pl, const double *points, cudaStream_t st) {
   {
     // face boundaries: binary searches of the sorted keys on the device
     int32_t *fb;
-    CSFMM_TRY(tmp.alloc(&fb, 7));
+    CSFMM_TRY(tmp.alloc(&fb, 8));
     key_bounds_kernel<<<1, 32, 0, st>>>(keys, N, 7, 2 * kD, fb);
     CSFMM_CUDA(cudaGetLastError());
-    int32_t hb7[7];
+    CSFMM_CUDA(cudaMemcpyAsync(fb + 7, pl.status, sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+    int32_t hb7[8];
     CSFMM_CUDA(cudaMemcpyAsync(hb7, fb, sizeof(hb7), cudaMemcpyDeviceToHost, st));
     CSFMM_CUDA(cudaStreamSynchronize(st));
+    if (hb7[7] & kStatusNotOnSphere) {
+      set_error("a point is not on the unit sphere (| |x|^2 - 1 | > 1e-12) or is not finite");
+      return CSFMM_ERR_NOT_ON_SPHERE;
+    }
     for (int f = 0; f < 6; ++f) {
       const int b = hb7[f], e = hb7[f + 1];
       if (e > b) {
@@ -1314,8 +1339,7 @@ csfmm_status build_tree(Plan &pl, const double *points, cudaStream_t st) {
       scan_tmp_cap = need;
     }
     int32_t nacc = 0, nnext = 0;
-    CSFMM_TRY(exclusive_scan_i32(is_list, loffs, nf, &nacc, scan_tmp, st));
-    CSFMM_TRY(exclusive_scan_i32(nkids, koffs, nf, &nnext, scan_tmp, st));
+    CSFMM_TRY(exclusive_scan2_i32(is_list, loffs, nkids, koffs, nf, &nacc, &nnext, scan_tmp, st));
     if (acc_n + nacc > acc_cap) {
       int ncap = std::max(2 * acc_cap, acc_n + nacc + 1024);
       int3 *na;
@@ -1331,14 +1355,6 @@ csfmm_status build_tree(Plan &pl, const double *points, cudaStream_t st) {
     acc_n += nacc;
     frontier = next;
     nf = nnext;
-  }
-  {
-    unsigned long long mb = 0;
-    CSFMM_CUDA(cudaMemcpyAsync(&mb, margin_bits, 8, cudaMemcpyDeviceToHost, st));
-    CSFMM_CUDA(cudaStreamSynchronize(st));
-    double m;
-    memcpy(&m, &mb, 8);
-    pl.stats.mac_margin = m;
   }
 
   // 6. lists: sort by (type, target, source), CSR per type
@@ -1366,14 +1382,24 @@ csfmm_status build_tree(Plan &pl, const double *points, cudaStream_t st) {
     }
   }
   int type_lo[5] = {0, 0, 0, 0, 0};
-  if (acc_n) {
-    // first entry of each list type: binary searches on the device
+  {
+    // first entry of each list type (binary searches on the device) and the
+    // traversal's MAC margin, in one read: tb[0..5) and the 8 bytes at tb + 6
     int32_t *tb;
-    CSFMM_TRY(tmp.alloc(&tb, 5));
-    key_bounds_kernel<<<1, 32, 0, st>>>(lk, acc_n, 5, 2 * bits, tb);
-    CSFMM_CUDA(cudaGetLastError());
-    CSFMM_CUDA(cudaMemcpyAsync(type_lo, tb, sizeof(type_lo), cudaMemcpyDeviceToHost, st));
+    CSFMM_TRY(tmp.alloc(&tb, 8));
+    CSFMM_CUDA(cudaMemsetAsync(tb, 0, 5 * sizeof(int32_t), st));
+    if (acc_n) {
+      key_bounds_kernel<<<1, 32, 0, st>>>(lk, acc_n, 5, 2 * bits, tb);
+      CSFMM_CUDA(cudaGetLastError());
+    }
+    CSFMM_CUDA(cudaMemcpyAsync(tb + 6, margin_bits, 8, cudaMemcpyDeviceToDevice, st));
+    int32_t h8[8];
+    CSFMM_CUDA(cudaMemcpyAsync(h8, tb, sizeof(h8), cudaMemcpyDeviceToHost, st));
     CSFMM_CUDA(cudaStreamSynchronize(st));
+    for (int t = 0; t < 5; ++t) type_lo[t] = h8[t];
+    double m;
+    memcpy(&m, h8 + 6, 8);
+    pl.stats.mac_margin = m;
   }
   for (int ty = 0; ty < 4; ++ty) {
     int lo = type_lo[ty], hi = type_lo[ty + 1];
