@@ -271,7 +271,7 @@ stencil_count_kernel(const double *g, const double *h, const double *rho, const 
 // grid points are distinct).
 __global__ void __launch_bounds__(32 * kStencilWarps)
 stencil_fill_kernel(const double *g, const double *h, const double *rho, const int32_t *aoff,
-                    const int32_t *adj, int M, const int32_t *soff, int32_t *sten) {
+                    const int32_t *adj, int M, const int32_t *soff, int32_t *sten, int *status) {
   __shared__ int Ss[kStencilWarps][kRemeshMaxStencil];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int *S = Ss[wid];
@@ -285,6 +285,11 @@ stencil_fill_kernel(const double *g, const double *h, const double *rho, const i
         for (int t = 0; t < n; ++t) rank += S[t] < v;
         sten[soff[k] + rank] = v;
       }
+    } else {
+      // the count pass found another size (the search is deterministic, so
+      // this does not happen): valid indices, and the grid is refused
+      for (int i = soff[k] + lane; i < soff[k + 1]; i += 32) sten[i] = k;
+      if (lane == 0) atomicOr(status, kRmStencil);
     }
     __syncwarp();
   }
@@ -646,10 +651,13 @@ extern "C" csfmm_status csfmm_remesh_grid_create(const double *grid, int64_t M,
   e = cudaMemcpyAsync(&G->max_ring, G->cursor, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e != cudaSuccess) return fail(cuda_status(e, "cudaMemcpyAsync"));
   stencil_fill_kernel<<<grs, 32 * kStencilWarps, 0, st>>>(G->g, G->h, G->rho, G->aoff, G->adj,
-                                                           (int)M, G->soff, G->sten);
+                                                           (int)M, G->soff, G->sten, G->status);
   e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&hs, G->status, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(cuda_status(e, "stencil_fill_kernel"));
+  if (hs) return fail(remesh_status(hs));
   *out = G;
   return CSFMM_OK;
 }
