@@ -98,7 +98,7 @@ def test_variable_resolution_grid():
     mapped triangulation stays Delaunay, and the midpoint rule on it is still
     second order (Funk-Hecke potential of Y_4^3 by the direct sum)."""
     from scipy.spatial import ConvexHull
-    for lev in (2, 3):
+    for lev in (2, 3, 4):  # level 4 is the GPU remeshing test's grid
         pts, A = I.variable_resolution_grid(lev)
         assert abs(A.sum() - 4 * np.pi) < 1e-12
         assert np.allclose(np.linalg.norm(pts, axis=1), 1.0, atol=1e-15)
