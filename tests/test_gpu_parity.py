@@ -1,7 +1,7 @@
 """GPU parity tests: the CUDA library through the C ABI against the CPU oracle
 on the same seeded inputs.
 
-Bars (written here, derived in the design doc):
+Bars (written here; each follows from the arithmetic on the two sides):
   - tree, tree order, cell centres and radii: identical (bitwise);
   - interaction lists: identical as sets per type;
   - FP64 FMM vs oracle FMM: relative l2 <= 1e-12;
