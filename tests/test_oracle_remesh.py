@@ -185,3 +185,35 @@ def test_planted_remesh_mistake_fails_a_pin(m):
     finally:
         B.set_mutation(0)
     assert caught, REMESH_MUTATIONS[m]
+
+
+def test_quadratics_reproduced_on_variable_resolution_grid():
+    """Quadratic exactness where h_k varies 4.5x over the sphere (Schmidt-mapped
+    icosahedral grid, particles moved by seeded random steps of up to 0.9 of
+    the local spacing), at the finest and coarsest grid points and between."""
+    v, faces = I.icosahedral_triangulation(3)
+    x = I.schmidt_transform(v, 0.5)
+    off, nb = I.grid_adjacency(faces, len(x))
+    h = B.neighbour_scale(x, off, nb)
+    assert h.max() / h.min() > 3.0
+    rng = np.random.default_rng(I.MASTER_SEED + 73)
+    d = rng.normal(size=x.shape)
+    d -= (d * x).sum(1, keepdims=True) * x
+    d *= (0.9 * h * rng.uniform(size=len(x)) / np.linalg.norm(d, axis=1))[:, None]
+    xs = x + d
+    xs /= np.linalg.norm(xs, axis=1, keepdims=True)
+    picks = [int(np.argmax(x[:, 2])), int(np.argmin(x[:, 2])), int(np.argmin(h)),
+             int(np.argmax(h)), 200, 400]
+    for k in picks:
+        g = x[k]
+        a = np.array([0.3, 0.8, -0.5]) if abs(g[0]) < 0.9 else np.array([0.0, 1.0, 0.2])
+        e1 = a - (a @ g) * g
+        e1 /= np.linalg.norm(e1)
+        e2 = np.cross(g, e1)
+        den = (xs @ g) * h[k]
+        u, w = (xs @ e1) / den, (xs @ e2) / den
+        c = rng.standard_normal(6)
+        f = c[0] + c[1] * u + c[2] * w + c[3] * u * u + c[4] * u * w + c[5] * w * w
+        f = np.where(xs @ g > 0.5, f, 0.0)
+        got = B.remesh(x, off, nb, xs, f, points=[k])[0]
+        assert abs(got - c[0]) <= 1e-11 * np.abs(c).max(), k
