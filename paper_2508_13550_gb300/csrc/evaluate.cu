@@ -46,18 +46,13 @@ template <typename Real>
 __device__ __forceinline__ const Real *M_of(const PlanView &v);
 template <>
 __device__ __forceinline__ const double *M_of<double>(const PlanView &v) { return v.m2m64; }
-template <>
-__device__ __forceinline__ const float *M_of<float>(const PlanView &v) { return v.m2m32; }
-// Shrunk boxes: the [2][p][p] matrices from child cell c to its parent.
+// Shrunk boxes: the [2][p][p] matrices from child cell c to its parent (the
+// FP32-bulk form reads its double-float copies in the _df kernels).
 template <typename Real>
 __device__ __forceinline__ const Real *Mcell_of(const PlanView &v, int c);
 template <>
 __device__ __forceinline__ const double *Mcell_of<double>(const PlanView &v, int c) {
   return v.mcell64 + (int64_t)c * 2 * v.p * v.p;
-}
-template <>
-__device__ __forceinline__ const float *Mcell_of<float>(const PlanView &v, int c) {
-  return v.mcell32 + (int64_t)c * 4 * v.p * v.p;
 }
 
 // FP64 kernel factors of the reference form (the FP32-bulk kernels live in
@@ -308,13 +303,6 @@ __device__ __forceinline__ void df_acc_prod(float &sh, float &sl, float ah, floa
   const float e = __fadd_rn(__fadd_rn(sh, -__fadd_rn(s, -bb)), __fadd_rn(ph, -bb));
   sh = s;
   sl = __fadd_rn(sl, __fadd_rn(e, pe));
-}
-__device__ __forceinline__ void df_acc(float &sh, float &sl, float bh, float bl) {
-  const float s = __fadd_rn(sh, bh);
-  const float bb = __fadd_rn(s, -sh);
-  const float e = __fadd_rn(__fadd_rn(sh, -__fadd_rn(s, -bb)), __fadd_rn(bh, -bb));
-  sh = s;
-  sl = __fadd_rn(sl, __fadd_rn(e, bl));
 }
 
 // M2M of the FP32 form: same contraction as m2m_kernel with the matrices as
