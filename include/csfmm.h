@@ -221,7 +221,10 @@ csfmm_status csfmm_evaluate_ws(csfmm_plan plan, csfmm_workspace ws, const double
  * keeps the last call's contents: calls that overlap on the GPU (other
  * streams, other threads, other plans) race, so serialise them.  Nothing in
  * the array needs clearing between calls (every part is written before it
- * is read).  Asynchronous on stream. */
+ * is read).  Asynchronous on stream.
+ * Errors: INVALID_ARG (NULL plan, nrhs outside [1, 64], weights or out not
+ * device memory, a current device other than the plan's, or more scratch
+ * than the array holds), CUDA. */
 #define CSFMM_STATIC_SCRATCH_BYTES (64u << 20)
 csfmm_status csfmm_evaluate_static(csfmm_plan plan, const double *weights, int nrhs, double *out,
                                    void *stream);
@@ -301,8 +304,11 @@ csfmm_status csfmm_plan_export_proxy_weights(csfmm_plan plan, int nrhs, double *
  * on the caller's stream, so the phase times may add up to more than the
  * evaluation's.  csfmm_plan_phase_times synchronises those events, writes the
  * summed milliseconds per phase into ms[CSFMM_NUM_PHASES] (host), the number
- * of timed evaluations into *calls, and clears the record.  For the FAR and
- * NEAR phases the sum covers every launch of the phase in the evaluation. */
+ * of timed evaluations into *calls (calls may be NULL), and clears the
+ * record.  For the FAR and NEAR phases the sum covers every launch of the
+ * phase in the evaluation.
+ * Errors: INVALID_ARG (NULL plan, or NULL ms for csfmm_plan_phase_times), CUDA
+ * (an event that failed; the record is cleared all the same). */
 csfmm_status csfmm_plan_enable_timing(csfmm_plan plan, int on);
 csfmm_status csfmm_plan_phase_times(csfmm_plan plan, double *ms, int64_t *calls);
 
