@@ -174,6 +174,15 @@ def make_workload(name):
     return wl, pts, A, np.ascontiguousarray(w)
 
 
+def workload_config(args, wl, N, nrhs, world):
+    """The `config` object of a bench line: the workload alone, identical for
+    the library's arm and the reference arm of the same command."""
+    return {"workload": args.workload, "desc": wl["desc"], "N": N, "nrhs": nrhs,
+            "kernel": wl["kernel"], "degree": wl["n"], "theta": wl["theta"],
+            "max_leaf": wl["N0"], "precision": args.precision,
+            "parallelism": f"replicas x{world}"}
+
+
 def cpu_oracle_sample(pts, w, wl, n_leaves, seed, repeats=1):
     """Times the CPU oracle FMM evaluation restricted to every target of
     n_leaves seeded random leaves (tree built beforehand, like a resident
@@ -273,9 +282,8 @@ def run_reference(args):
             "unit": "targets/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": args.workload, "N": len(pts),
-                                            "kernel": wl["kernel"], "degree": wl["n"],
-                                            "theta": wl["theta"], "max_leaf": wl["N0"]},
+            "data": "synthetic",
+            "config": workload_config(args, wl, len(pts), w.shape[0], args.gpus),
             "cpu_baseline": {"value": val, "unit": "targets/s", "cores": O.num_threads(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": "targets/s", "h2d_bytes_per_step": 0,
@@ -299,6 +307,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
 
     wl, pts, A, w = make_workload(args.workload)
+    wl_base = wl
     N = len(pts)
     nrhs = w.shape[0]
     prec = Cs.FP32_BULK if args.precision == "fp32" else Cs.FP64
@@ -427,7 +436,8 @@ def run_ours(args):
         per_sm_clk = {2: 16.0, 0: 16.0, 1: 128.0 / 11.0, 100: 128.0 / 4.0}[wl["kernel"]]
     else:
         per_sm_clk = min(16.0, 128.0 / (6 + min(nrhs, 16)))
-    peak_evals = 152 * per_sm_clk * sm_max * 1e6
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_evals = n_sm * per_sm_clk * sm_max * 1e6
     ncalls = max(calls, 1)
     ev_sym = st.get("sym_evals", 0) if nrhs == 1 else 0
     if nrhs == 1:
@@ -459,12 +469,9 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if prec == Cs.FP32_BULK else "f64", "data": "synthetic",
         "autotuned": tuned,
-        "config": {"workload": args.workload, "desc": wl["desc"], "N": N, "nrhs": nrhs,
-                   "kernel": wl["kernel"], "degree": wl["n"], "theta": wl["theta"],
-                   "max_leaf": wl["N0"], "precision": args.precision,
-                   "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (plan + workspace "
-                         f"{st['device_bytes'] / 1e9:.2f} GB resident)"},
+        "config": workload_config(args, wl_base, N, nrhs, world),
+        "l2": "inputs larger than L2 (plan + workspace "
+              f"{st['device_bytes'] / 1e9:.2f} GB resident)",
         "rel_err_vs_fp64_ds": err, "err_samples": args.err_samples,
         "kernel_evals_per_s": world * sum(st["evals"]) / (ms_step / 1e3),
         "interactions_per_s": world * sum(st["evals"]) * nrhs / (ms_step / 1e3),
@@ -482,8 +489,9 @@ def run_ours(args):
                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the "
                                        "6 x 512^2 case, scaled by evaluations per launch"
                                        if traffic is not None else None,
-                     "peak_source": f"{peak_kind} sm_max_mhz x 152 SMs x {per_sm_clk:.2f} "
-                                    "evals/clk/SM"},
+                     "peak_source": f"{peak_kind} sm_max_mhz x {n_sm} SMs (device "
+                                    f"attribute) x {per_sm_clk:.2f} evals/clk/SM",
+                     "sm_count": n_sm},
         "kernels": {k: {"evals_per_launch": e, "ms_per_launch": m,
                         "geval_per_s": (e / (m / 1e3) / 1e9) if m > 0 else None,
                         "frac_of_alu_peak": (e / (m / 1e3) / peak_evals) if m > 0 else None}

@@ -69,7 +69,7 @@ csfmm_status bve_rk4(const double *x, const double *zeta, const double *area, in
   CSFMM_CUDA(cudaMallocFromPoolAsync((void **)&buf, sizeof(double) * (3 * n3 + 2 * (size_t)N), memory_pool(), st));
   double *xs = buf, *u = buf + n3, *ksum = buf + 2 * n3, *zs = buf + 3 * n3,
          *w = buf + 3 * n3 + N;
-  const int grid = grid_for(N, 256, 152 * 8);
+  const int grid = grid_for(N, 256, sm_count() * 8);
   const double two_omega = 2.0 * omega;
   // RK4: stage s evaluates the velocity at (xs, zs); a = offset of the next
   // stage, b = weight of this stage in the combination (1, 2, 2, 1)

@@ -316,6 +316,7 @@ const double *remesh_grid_points(csfmm_remesh_grid G);
 // Host helpers shared by the library's own files.
 const double *host_tan_table();  // T[k] = tan(k (pi/2)/2^kD - pi/4), k = 0..2^kD
 int grid_for(int64_t n, int block, int max_blocks = 1 << 30);
+int sm_count();  // streaming multiprocessors of the current device (read once per device)
 csfmm_status exclusive_scan_i32(const int32_t *in, int32_t *out, int n, int32_t *total_host,
                                 int32_t *tmp, cudaStream_t st);
 size_t scan_tmp_elems(int n);

@@ -280,8 +280,9 @@ csfmm_status launch_direct(const double *pts, int N, int kid, const double *w, i
   const int tiles = grid_for(nt, kTile);
   const int dim = kid == CSFMM_KERNEL_BIOT_SAVART ? 3 : 1;
   int nsplit = 1;
-  if (tiles < 4 * 152) {
-    nsplit = (4 * 152 + tiles - 1) / tiles;
+  const int nsm = sm_count();
+  if (tiles < 4 * nsm) {
+    nsplit = (4 * nsm + tiles - 1) / tiles;
     const int max_split = (N + 4 * kTile - 1) / (4 * kTile);  // at least 4 tiles per split
     if (nsplit > max_split) nsplit = max_split;
     if (nsplit > 2048) nsplit = 2048;
@@ -333,7 +334,7 @@ csfmm_status launch_direct(const double *pts, int N, int kid, const double *w, i
   }
   if (part) {
     if (result == CSFMM_OK) {
-      direct_reduce_kernel<<<grid_for(n_out, 256, 152 * 8), 256, 0, st>>>(part, nsplit, n_out, out);
+      direct_reduce_kernel<<<grid_for(n_out, 256, sm_count() * 8), 256, 0, st>>>(part, nsplit, n_out, out);
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) result = cuda_status(e, "direct_reduce_kernel launch");
     }

@@ -923,7 +923,7 @@ csfmm_status run_passes(Plan &pl, Workspace &W, const double *w, int nrhs, doubl
     if (s__ != CSFMM_OK) return s__;                 \
   } while (0)
   CSFMM_BEGIN(CSFMM_PHASE_GATHER, st);
-  gather_kernel<<<grid_for((int64_t)N * nrhs, 256, 152 * 32), 256, 0, st>>>(
+  gather_kernel<<<grid_for((int64_t)N * nrhs, 256, sm_count() * 32), 256, 0, st>>>(
       pl.perm, w, W.ws, sizeof(Real) == 4 ? W.wsf : nullptr, N, nrhs, N, (int)pl.nsrc);
   ++pl.launches;
   CSFMM_END(CSFMM_PHASE_GATHER, st);
@@ -1057,7 +1057,7 @@ csfmm_status run_cstc(Plan &pl, Workspace &W, const double *w, int nrhs, double 
   float2 *wtot = (sizeof(Real) == 4 && KID == CSFMM_KERNEL_LAPLACE) ? W.wtot : nullptr;
   v.wtot = wtot;
   v.wtot_ld = ldr;
-  gather_kernel<<<grid_for((int64_t)N * nrhs, 256, 152 * 32), 256, 0, st>>>(
+  gather_kernel<<<grid_for((int64_t)N * nrhs, 256, sm_count() * 32), 256, 0, st>>>(
       pl.perm, w, W.ws, sizeof(Real) == 4 ? W.wsf : nullptr, N, nrhs, N, (int)pl.nsrc);
   const int tb_prox = ((P + 31) / 32) * 32;
   const int tb_p2m = tb_prox < 64 ? 64 : tb_prox;

@@ -532,7 +532,7 @@ csfmm_status remesh_status(int st) {
 csfmm_status remesh_impl(csfmm_remesh_grid G, const double *x, const double *f, int nfield,
                          double *f_out, cudaStream_t st) {
   const int M = G->M;
-  const int grid = grid_for(M, 256, 152 * 8);
+  const int grid = grid_for(M, 256, sm_count() * 8);
   CSFMM_CUDA(cudaMemsetAsync(G->status, 0, sizeof(int), st));
   CSFMM_CUDA(cudaMemsetAsync(G->cnt, 0, sizeof(int32_t) * (M + 1), st));
   CSFMM_CUDA(cudaMemsetAsync(G->cursor, 0, sizeof(int32_t) * M, st));
@@ -543,7 +543,7 @@ csfmm_status remesh_impl(csfmm_remesh_grid G, const double *x, const double *f, 
   bucket_fill_kernel<<<grid, 256, 0, st>>>(G->cell, M, G->boff, G->cursor, G->bucket);
   bucket_sort_kernel<<<grid, 256, 0, st>>>(G->boff, M, G->bucket, G->status);
   // fields in pairs (the second pair re-reads the stencil; the walk and sort are shared)
-  const int fg = grid_for((int64_t)M * kFitLanes, 128, 152 * 16);
+  const int fg = grid_for((int64_t)M * kFitLanes, 128, sm_count() * 16);
   for (int q = 0; q < nfield; q += 2) {
     const double *fq = f + (size_t)q * M;
     double *oq = f_out + (size_t)q * M;
@@ -617,7 +617,7 @@ extern "C" csfmm_status csfmm_remesh_grid_create(const double *grid, int64_t M,
     return e;
   };
   if (s != CSFMM_OK) return fail(s);
-  const int gr = grid_for(M + 1, 256, 152 * 8);
+  const int gr = grid_for(M + 1, 256, sm_count() * 8);
   cudaError_t e = cudaMemcpyAsync(G->g, grid, sizeof(double) * 3 * (size_t)M,
                                   cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(G->status, 0, sizeof(int), st);
@@ -633,7 +633,7 @@ extern "C" csfmm_status csfmm_remesh_grid_create(const double *grid, int64_t M,
   // the scan of the stencil sizes reuses cnt; cursor[0] receives the largest ring
   e = cudaMemsetAsync(G->cursor, 0, sizeof(int32_t), st);
   if (e != cudaSuccess) return fail(cuda_status(e, "cudaMemsetAsync"));
-  const int grs = grid_for(M, kStencilWarps, 152 * 16);
+  const int grs = grid_for(M, kStencilWarps, sm_count() * 16);
   cell_radius_kernel<<<gr, 256, 0, st>>>(G->g, G->aoff, G->adj, (int)M, G->rho);
   stencil_count_kernel<<<grs, 32 * kStencilWarps, 0, st>>>(G->g, G->h, G->rho, G->aoff, G->adj,
                                                             (int)M, G->cnt, G->cursor, G->status);

@@ -54,6 +54,7 @@ std::mutex g_pool_mu;
 cudaMemPool_t g_pool[kMaxPoolDevices] = {};
 cudaStream_t g_release[kMaxPoolDevices] = {};
 const double *g_dev_tan[kMaxPoolDevices] = {};
+int g_sms[kMaxPoolDevices] = {};
 
 int current_device() {
   int d = 0;
@@ -118,6 +119,20 @@ const double *device_tan_table() {
     g_dev_tan[d] = (const double *)p;
   }
   return g_dev_tan[d];
+}
+
+int sm_count() {
+  const int d = current_device();
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_sms[d]) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d) != cudaSuccess || n < 1) {
+      cudaGetLastError();
+      n = 1;
+    }
+    g_sms[d] = n;
+  }
+  return g_sms[d];
 }
 
 int grid_for(int64_t n, int block, int max_blocks) {
@@ -263,12 +278,12 @@ static csfmm_status exclusive_scan2_i32(const int32_t *in1, int32_t *out1, const
 // ---------------------------------------------------------------------------
 // A block sorts a tile of kSortThreads x ITEMS keys; ITEMS shrinks with n so
 // that a pass has at least about two blocks per SM (a 164k-key sort with
-// 4096-key tiles ran 40 blocks on 152 SMs).
+// 4096-key tiles ran 40 blocks on a GB300).
 constexpr int kSortThreads = 256;
 constexpr int kSortMinItems = 2;
 
 static int sort_items(int n) {
-  constexpr int64_t kBlocks = 2 * 152;
+  const int64_t kBlocks = 2 * (int64_t)sm_count();
   if (n >= kBlocks * kSortThreads * 16) return 16;
   if (n >= kBlocks * kSortThreads * 8) return 8;
   if (n >= kBlocks * kSortThreads * 4) return 4;
@@ -1129,7 +1144,7 @@ csfmm_status build_tree(Plan &pl, const double *points, cudaStream_t st) {
   size_t rtmp_n = radix_tmp_elems(N);
   int32_t *rtmp;
   CSFMM_TRY(tmp.alloc(&rtmp, rtmp_n));
-  key_points_kernel<<<grid_for(N, 256, 152 * 64), 256, 0, st>>>(points, N, T, keys, idx, pl.status);
+  key_points_kernel<<<grid_for(N, 256, sm_count() * 64), 256, 0, st>>>(points, N, T, keys, idx, pl.status);
   CSFMM_CUDA(cudaGetLastError());
   // (the status word is read with the face bounds below: a point off the sphere
   // has key 0 and sorts like any other)
@@ -1142,7 +1157,7 @@ csfmm_status build_tree(Plan &pl, const double *points, cudaStream_t st) {
   CSFMM_TRY(A.alloc(&pl.perm, N));
   CSFMM_CUDA(cudaMemcpyAsync(pl.perm, idx, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, st));
   CSFMM_TRY(A.alloc(&pl.x, (size_t)3 * N));
-  permute_points_kernel<<<grid_for(N, 256, 152 * 64), 256, 0, st>>>(points, pl.perm, pl.x, N);
+  permute_points_kernel<<<grid_for(N, 256, sm_count() * 64), 256, 0, st>>>(points, pl.perm, pl.x, N);
   CSFMM_CUDA(cudaGetLastError());
 
   // 3. roots: non-empty faces, found from the sorted keys on the host side
@@ -1460,12 +1475,12 @@ csfmm_status build_tree(Plan &pl, const double *points, cudaStream_t st) {
     CSFMM_TRY(tmp.alloc(&acc, 6));
     CSFMM_CUDA(cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * 6, st));
     if (acc_n > 0) {
-      list_stats_kernel<<<grid_for(acc_n, 256, 152 * 8), 256, 0, st>>>(lk, acc_n, bits, pl.cbegin,
+      list_stats_kernel<<<grid_for(acc_n, 256, sm_count() * 8), 256, 0, st>>>(lk, acc_n, bits, pl.cbegin,
                                                                       pl.cend, pl.P, acc);
       CSFMM_CUDA(cudaGetLastError());
     }
     if (pl.n_sym_pairs > 0) {
-      sym_stats_kernel<<<grid_for(pl.n_sym_pairs, 256, 152 * 8), 256, 0, st>>>(
+      sym_stats_kernel<<<grid_for(pl.n_sym_pairs, 256, sm_count() * 8), 256, 0, st>>>(
           pl.sym_pairs, (int)pl.n_sym_pairs, pl.cbegin, pl.cend, acc + 5);
       CSFMM_CUDA(cudaGetLastError());
     }
