@@ -205,26 +205,43 @@ csfmm_status csfmm_evaluate_ws(csfmm_plan plan, csfmm_workspace ws, const double
  * evaluate -- a serving loop whose free device memory is all promised to its
  * admission budget, or a host application whose device memory belongs to its
  * own allocator -- and that need a second evaluation of a plan while the
- * plan's workspace is busy.  It computes the same result with the same
- * kernels as csfmm_evaluate, but its scratch (weights in tree order, proxy
- * weights, proxy potentials, near-field potentials) comes from one static
- * device array of CSFMM_STATIC_SCRATCH_BYTES that every GPU loading the
- * library keeps until the process exits.
+ * plan's workspace is busy.  It runs the same kernels as csfmm_evaluate on
+ * the same data (including the mirrored-pair pass of the FP32-bulk form with
+ * one right-hand side) and gives the same result bit for bit; it runs every
+ * pass in order on `stream` (csfmm_evaluate overlaps the upward pass and far
+ * field with the near field on a second stream).  Its scratch (weights in
+ * tree order, proxy weights, proxy potentials, near-field potentials) comes
+ * from one static device array of CSFMM_STATIC_SCRATCH_BYTES that every GPU
+ * loading the library keeps until the process exits.
  *   plan    a plan of the current device (built earlier, e.g. at start-up)
- *   weights device [nrhs][N]; out device [nrhs][N][dim]; 1 <= nrhs <= 64
- * Needs 8 N nrhs (1 + dim) + ncells nrhs P (s + 8 dim) bytes of scratch
- * (s = 8 for CSFMM_FP64, 4 for CSFMM_FP32_BULK, which also needs 4 N nrhs;
- * each part rounded up to 256 bytes); larger requests fail with CSFMM_ERR_INVALID_ARG and a message that
- * states the size.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress with that device current); make that first
- * call before any stream capture.  Every call shares the one array, which
- * keeps the last call's contents: calls that overlap on the GPU (other
- * streams, other threads, other plans) race, so serialise them.  Nothing in
- * the array needs clearing between calls (every part is written before it
- * is read).  Asynchronous on stream.
+ *   weights device [nrhs][N]; out device [nrhs][N][dim], both memory of the
+ *           plan's device (or managed memory); 1 <= nrhs <= 64
+ * Scratch needed, each term rounded up to a multiple of 256 bytes:
+ *     8 N nrhs                      weights in tree order
+ *   + s ncells nrhs P               proxy weights (s = 8 for CSFMM_FP64, 4 for
+ *                                   CSFMM_FP32_BULK)
+ *   + 8 ncells nrhs dim P           proxy potentials
+ *   + 8 N nrhs dim                  near-field potentials
+ * and for CSFMM_FP32_BULK also
+ *   + 4 N nrhs                      FP32 weights
+ *   + 16 ncells nrhs                per-cell weight totals
+ *   + 4 L (nrhs = 1, kernels other than Biot-Savart; L = floats of the
+ *          mirrored-pair partial sums, about 2 N times the PP leaf pairs per
+ *          leaf that have a mirror)
+ * with N the points of the plan (sources and targets), P = (n+1)^2.  Larger
+ * requests fail with CSFMM_ERR_INVALID_ARG and a message that states the
+ * size.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress with that device current) and keeps it for the life
+ * of the process; make that first call before any stream capture.  A
+ * cudaDeviceReset invalidates the kept address as it invalidates plans: do
+ * not call this entry point after a reset of the device.  Every call shares
+ * the one array, which keeps the last call's contents: calls that overlap on
+ * the GPU (other streams, other threads, other plans) race, so serialise
+ * them.  Nothing in the array needs clearing between calls (every part is
+ * written before it is read).  Asynchronous on stream.
  * Errors: INVALID_ARG (NULL plan, nrhs outside [1, 64], weights or out not
- * device memory, a current device other than the plan's, or more scratch
- * than the array holds), CUDA. */
+ * memory of the plan's device, a current device other than the plan's, or
+ * more scratch than the array holds), CUDA. */
 #define CSFMM_STATIC_SCRATCH_BYTES (64u << 20)
 csfmm_status csfmm_evaluate_static(csfmm_plan plan, const double *weights, int nrhs, double *out,
                                    void *stream);

@@ -40,14 +40,17 @@ csfmm_status scratch_address(int device, unsigned char **out) {
   return CSFMM_OK;
 }
 
-bool is_device_memory(const void *p) {
+// Device memory of `device` (or managed memory): the kernels read and write
+// it directly, so memory of another GPU is refused.
+bool is_device_memory(const void *p, int device) {
   if (!p) return false;
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == device;
 }
 
 }  // namespace
@@ -64,15 +67,15 @@ extern "C" csfmm_status csfmm_evaluate_static(csfmm_plan plan, const double *wei
     set_error("nrhs must be in [1, 64] (got %d)", nrhs);
     return CSFMM_ERR_INVALID_ARG;
   }
-  if (!is_device_memory(weights) || !is_device_memory(out)) {
-    set_error("weights and out must be device memory");
-    return CSFMM_ERR_INVALID_ARG;
-  }
   int device = -1;
   cudaError_t e = cudaGetDevice(&device);
   if (e != cudaSuccess) return cuda_status(e, "cudaGetDevice");
   if (device != pl.device || device < 0 || device >= kMaxDevices) {
     set_error("the current device %d is not the plan's device %d", device, pl.device);
+    return CSFMM_ERR_INVALID_ARG;
+  }
+  if (!is_device_memory(weights, device) || !is_device_memory(out, device)) {
+    set_error("weights and out must be device memory of the plan's device %d", device);
     return CSFMM_ERR_INVALID_ARG;
   }
   const size_t N = (size_t)pl.N, nc = (size_t)pl.ncells, P = (size_t)pl.P, R = (size_t)nrhs;
@@ -84,7 +87,13 @@ extern "C" csfmm_status csfmm_evaluate_static(csfmm_plan plan, const double *wei
   const size_t b_phi = round256(R * N * dim * sizeof(double));
   const size_t b_wsf = pl.precision == CSFMM_FP64 ? 0 : round256(R * N * sizeof(float));
   const size_t b_wtot = pl.precision == CSFMM_FP64 ? 0 : round256(nc * R * 2 * sizeof(float2));
-  const size_t need = b_ws + b_wbar + b_psi + b_phi + b_wsf + b_wtot;
+  // FP32 bulk, one right-hand side, symmetric kernel: the partial sums of the
+  // mirrored PP leaf pairs, so that the same symmetric pass runs as in
+  // csfmm_evaluate
+  const bool sym = pl.precision != CSFMM_FP64 && nrhs == 1 && pl.n_sym_pairs > 0 &&
+                   pl.kernel_id != CSFMM_KERNEL_BIOT_SAVART;
+  const size_t b_sym = sym ? round256((size_t)pl.sym_part_len * sizeof(float)) : 0;
+  const size_t need = b_ws + b_wbar + b_psi + b_phi + b_wsf + b_wtot + b_sym;
   if (need > (size_t)CSFMM_STATIC_SCRATCH_BYTES) {
     set_error("this evaluation needs %zu bytes of scratch; the static scratch holds %zu bytes "
               "(use csfmm_evaluate, or fewer right-hand sides)",
@@ -95,7 +104,8 @@ extern "C" csfmm_status csfmm_evaluate_static(csfmm_plan plan, const double *wei
   csfmm_status s = scratch_address(device, &base);
   if (s != CSFMM_OK) return s;
   // Every scratch buffer is fully written before it is read (gather, P2M/M2M,
-  // far, near), so nothing needs clearing between calls.
+  // far, the symmetric pass, near), so nothing needs clearing between calls.
+  // W has no side stream: the passes run in order on `stream`.
   Workspace W;
   W.graphs_ok = false;  // W lives only for this call
   W.plan = &pl;
@@ -107,5 +117,7 @@ extern "C" csfmm_status csfmm_evaluate_static(csfmm_plan plan, const double *wei
   W.phi = reinterpret_cast<double *>(base + b_ws + b_wbar + b_psi);
   if (b_wsf) W.wsf = reinterpret_cast<float *>(base + b_ws + b_wbar + b_psi + b_phi);
   if (b_wtot) W.wtot = reinterpret_cast<float2 *>(base + b_ws + b_wbar + b_psi + b_phi + b_wsf);
+  if (b_sym)
+    W.sym_part = reinterpret_cast<float *>(base + b_ws + b_wbar + b_psi + b_phi + b_wsf + b_wtot);
   return evaluate_impl(pl, W, weights, nrhs, out, (cudaStream_t)stream);
 }

@@ -5,8 +5,10 @@ serving loop whose free device memory is all promised to admitted requests,
 or a host application that owns device memory through its own allocator).
 Its scratch is one static device array shared by every call, so this test
 checks, through the C ABI, that two calls in a row give the same potentials
-as csfmm_evaluate (the second call must not see the first call's data), and
-that a request larger than the array is refused with a clear message.
+as csfmm_evaluate bit for bit (the same kernels on the same data; the second
+call must not see the first call's data), that the FP32-bulk form with one
+right-hand side runs the mirrored-pair pass there too (same launch count),
+and that a request larger than the array is refused with a clear message.
 
 This file is collected last so that a failure here cannot hide another test.
 """
@@ -20,7 +22,7 @@ from gpu_util import cuda_or_skip, dev
 
 pytestmark = pytest.mark.gpu
 
-TOL = 1e-12  # the FP64 parity tolerance of the other GPU tests
+TOL = 1e-12  # the FP64 parity tolerance of the other GPU tests (here: bitwise)
 
 
 @pytest.fixture(scope="module")
@@ -39,12 +41,17 @@ def _rel(a, b):
     return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
 
 
-@pytest.mark.parametrize("kernel,precision,nrhs", [(0, 0, 1), (1, 1, 3), (2, 0, 5)],
-                         ids=["laplace-fp64", "biot-savart-fp32", "newton-fp64-5rhs"])
+@pytest.mark.parametrize("kernel,precision,nrhs",
+                         [(0, 0, 1), (1, 1, 3), (2, 0, 5), (2, 1, 1), (0, 1, 1), (0, 1, 16)],
+                         ids=["laplace-fp64", "biot-savart-fp32", "newton-fp64-5rhs",
+                              "newton-fp32-1rhs", "laplace-fp32-1rhs", "laplace-fp32-16rhs"])
 def test_static_scratch_matches_evaluate_twice(env, kernel, precision, nrhs):
     torch, C = env
     pts, A = I.cubed_sphere_grid(32)
-    plan = C.plan_create(dev(torch, pts), kernel, 8, 0.7, 64, precision=precision)
+    plan = C.plan_create(dev(torch, pts), kernel, 8, 0.7, 64, precision=precision,
+                         max_nrhs=max(16, nrhs))
+    if precision == 1 and nrhs == 1 and kernel != 1:
+        assert C.plan_stats(plan)["sym_pairs"] > 0  # the mirrored-pair pass has work
     stream = torch.cuda.current_stream().cuda_stream
     rng = np.random.default_rng(kernel + 10 * precision)
     dim = C.kernel_dim(kernel)
@@ -53,12 +60,15 @@ def test_static_scratch_matches_evaluate_twice(env, kernel, precision, nrhs):
         ref = torch.empty((nrhs, len(pts), dim), dtype=torch.float64, device="cuda")
         got = torch.full_like(ref, float("nan"))
         assert _call(C, "csfmm_evaluate", plan, w, ref, stream) == 0, C.last_error()
+        launches = C.plan_stats(plan)["launches_per_evaluate"]
         assert _call(C, "csfmm_evaluate_static", plan, w, got, stream) == 0, C.last_error()
+        assert C.plan_stats(plan)["launches_per_evaluate"] == launches
         torch.cuda.synchronize()
         C.plan_sync(plan)
         g, r = got.cpu().numpy(), ref.cpu().numpy()
         assert np.isfinite(g).all()
         assert _rel(g, r) <= TOL, (call, _rel(g, r))
+        assert np.array_equal(g, r), call
     C.plan_destroy(plan)
 
 
