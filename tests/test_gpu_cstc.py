@@ -2,8 +2,9 @@
 ABI against the oracle's CSTC on the same seeded inputs.
 
 Bars: FP64 form vs oracle CSTC, relative l2 <= 1e-12 (same decisions, same
-arithmetic in another rounding order); FP32 form vs oracle CSTC <= 1e-5 (the
-FP32-bulk bar); K = 1 reproduces sum_{j != i} w_j.
+arithmetic in another rounding order); FP32 form vs oracle CSTC at most the
+per-case bar of fp32_bars.py (about 4x the error measured on GB300); K = 1
+reproduces sum_{j != i} w_j.
 """
 import numpy as np
 import pytest
@@ -11,11 +12,11 @@ import pytest
 import oracle as O
 from paper_2508_13550_gb300 import inputs as I
 from gpu_util import cuda_or_skip, dev
+from fp32_bars import check as check32
 
 pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-12
-TOL32 = 1e-5
 
 
 @pytest.fixture(scope="module")
@@ -65,8 +66,9 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("name,kernel,mk,n,theta,N0", CASES)
-def test_cstc_matches_oracle(torch, C, name, kernel, mk, n, theta, N0):
+@pytest.mark.parametrize("case", range(len(CASES)), ids=[c[0] for c in CASES])
+def test_cstc_matches_oracle(torch, C, case):
+    name, kernel, mk, n, theta, N0 = CASES[case]
     pts = mk()
     rng = np.random.default_rng(8)
     W = rng.standard_normal((2, len(pts))) / len(pts)
@@ -74,7 +76,7 @@ def test_cstc_matches_oracle(torch, C, name, kernel, mk, n, theta, N0):
     g64 = gpu_cstc(torch, C, pts, kernel, W, n, theta, N0, C.FP64)
     assert rel(g64, ref) <= TOL64, (name, rel(g64, ref))
     g32 = gpu_cstc(torch, C, pts, kernel, W, n, theta, N0, C.FP32_BULK)
-    assert rel(g32, ref) <= TOL32, (name, rel(g32, ref))
+    check32(f"cstc32-case{case}", rel(g32, ref))
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -82,8 +84,11 @@ def test_cstc_constant_kernel_covers_every_source_once(torch, C, precision):
     pts = I.random_sphere_points(12000, 6)
     w = np.random.default_rng(1).standard_normal(len(pts))
     g = gpu_cstc(torch, C, pts, O.KERNEL_ONE, w, 4, 0.7, 25, precision)[0, :, 0]
-    tol = 1e-12 if precision == 0 else 1e-6
-    assert np.max(np.abs(g - (w.sum() - w))) <= tol * np.abs(w).sum()
+    err = np.max(np.abs(g - (w.sum() - w))) / np.abs(w).sum()
+    if precision == 0:
+        assert err <= 1e-12
+    else:
+        check32("cstc32-k1-max-over-sum-abs-w", err)
 
 
 def test_cstc_config2_biot_savart_sampled(torch, C):

@@ -6,7 +6,9 @@ Bars (written here; each follows from the arithmetic on the two sides):
   - interaction lists: identical as sets per type;
   - FP64 FMM vs oracle FMM: relative l2 <= 1e-12;
   - FP64 direct sum vs oracle direct sum: relative l2 <= 1e-13;
-  - FP32-bulk FMM: error against the FP64 direct sum measured and bounded.
+  - FP32-bulk FMM and direct sum: relative l2 error against the oracle (its
+    FP64 direct sum, or its FP64 FMM on the same tree, degree and MAC) at most
+    the per-case bar of fp32_bars.py (about 4x the error measured on GB300).
 """
 import math
 
@@ -16,6 +18,7 @@ import pytest
 import oracle as O
 from paper_2508_13550_gb300 import inputs as I
 from gpu_util import cuda_or_skip, dev, cell_keys
+from fp32_bars import check as check32
 
 pytestmark = pytest.mark.gpu
 
@@ -185,7 +188,7 @@ def test_direct_matches_oracle(torch, C, kernel):
     sub = C.direct(dev(torch, pts), kernel, dev(torch, W), targets=dev(torch, tg)).cpu().numpy()
     assert rel(sub, ref[:, tg]) <= TOL_DS64
     g32 = C.direct(dev(torch, pts), kernel, dev(torch, W), precision=C.FP32_BULK).cpu().numpy()
-    assert rel(g32, ref) <= 1e-5
+    check32(f"direct32-k{kernel}", rel(g32, ref))
 
 
 def test_fp32_bulk_error_against_fp64_direct(torch, C):
@@ -199,7 +202,7 @@ def test_fp32_bulk_error_against_fp64_direct(torch, C):
     e32 = O.rel_l2(f32[0, :, 0], ds, A, ex[0])
     print(f"\nE(FS64,DS)={e64:.3e}  E(FS32,DS)={e32:.3e}")
     assert e64 < 1e-7
-    assert e32 < 1e-5
+    check32("fmm32-poisson-y43-m64-n8", e32)
 
 
 def test_full_size_newton_config_sampled(torch, C):
@@ -224,7 +227,7 @@ def test_full_size_newton_config_sampled(torch, C):
     e64 = rel(f64[0, tg2, 0], ds)
     print(f"\nconfig-3 sample: E(FS64,DS)={e64:.3e}  E(FS32,DS)={e32:.3e}")
     assert e64 < 1e-8
-    assert e32 < 1e-5
+    check32("fmm32-newton-land-6m-n12", e32)
 
 
 def test_full_size_multi_rhs_config_sampled(torch, C):
@@ -243,7 +246,7 @@ def test_full_size_multi_rhs_config_sampled(torch, C):
     del P
     errs = [rel(f32[r], ds[r]) for r in range(16)]
     print(f"\nconfig-4 sample: max over 16 RHS of E(FS32,DS) = {max(errs):.3e}")
-    assert max(errs) < 1e-5
+    check32("fmm32-poisson16-1.5m-n10", max(errs))
     P64 = C.plan_create(dev(torch, pts), C.KERNEL_LAPLACE, 10, 0.7, 400, max_nrhs=4)
     f64 = C.evaluate(P64, dev(torch, W[:4])).cpu().numpy()[:, tg, 0]
     for r in range(4):
@@ -319,24 +322,27 @@ def test_argument_errors(torch, C):
 @pytest.mark.parametrize("kernel,nrhs", [(O.KERNEL_LAPLACE, 16), (O.KERNEL_NEWTON, 9),
                                          (O.KERNEL_ONE, 8), (O.KERNEL_BIOT_SAVART, 6),
                                          (O.KERNEL_BIHARMONIC, 16)])
-def test_fp32_multi_rhs_matches_single_and_fp64(torch, C, kernel, nrhs):
+def test_fp32_multi_rhs_matches_oracle_and_single(torch, C, kernel, nrhs):
     """FP32-bulk with many right-hand sides (chunks of 16 / 8 share each kernel
-    value) against one-at-a-time FP32 evaluations and the FP64 FMM."""
+    value) against the oracle FMM on the same tree, degree and MAC (so the
+    difference is the FP32 rounding alone), element by element, and against
+    one-at-a-time FP32 evaluations."""
     pts, A = I.cubed_sphere_grid(48)
     coeffs = I.random_sh_coeffs(6, nrhs, seed=kernel + 1)
     W = I.sph_harm_combination(pts, coeffs, nrhs=nrhs) * A[None, :]
     if kernel == O.KERNEL_ONE:
         # K = 1 sums all weights: keep that sum away from zero (no cancellation)
         W = W + A[None, :]
+    ref = O.FMM(pts, 8, 0.7, 64).evaluate(kernel, W)
     P32 = C.plan_create(dev(torch, pts), kernel, 8, 0.7, 64, precision=C.FP32_BULK, max_nrhs=nrhs)
-    P64 = C.plan_create(dev(torch, pts), kernel, 8, 0.7, 64, precision=C.FP64, max_nrhs=nrhs)
     dW = dev(torch, W)
     allr = C.evaluate(P32, dW).cpu().numpy()
-    ref = C.evaluate(P64, dW).cpu().numpy()
+    check32(f"fmm32-multi-k{kernel}-r{nrhs}", max(rel(allr[r], ref[r]) for r in range(nrhs)))
+    worst = 0.0
     for r in range(nrhs):
         one = C.evaluate(P32, dW[r:r + 1].contiguous()).cpu().numpy()[0]
-        assert rel(allr[r], one) <= 1e-5, (r, rel(allr[r], one))
-        assert rel(allr[r], ref[r]) <= 1e-5, (r, rel(allr[r], ref[r]))
+        worst = max(worst, rel(allr[r], one))
+    check32(f"fmm32-chunk-vs-single-k{kernel}", worst)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -359,20 +365,54 @@ def test_graph_replay_matches_direct_launches(torch, C, precision):
     C.plan_sync(graph, stream=s.cuda_stream)
 
 
+@pytest.mark.parametrize("sign", ["positive", "mixed"])
 @pytest.mark.parametrize("kernel", [O.KERNEL_NEWTON, O.KERNEL_LAPLACE, O.KERNEL_BIHARMONIC,
                                     O.KERNEL_ONE])
-def test_fp32_symmetric_near_field(torch, C, kernel):
+def test_fp32_symmetric_near_field(torch, C, kernel, sign):
     """One right-hand side in FP32 bulk evaluates mirrored PP leaf pairs once
-    for both directions; the result agrees with the two-RHS launch (which
-    evaluates every PP entry directly) and with the FP64 FMM."""
+    for both directions.  Compared element by element with the oracle FMM on
+    the same tree, degree and MAC (the difference is the FP32 rounding alone),
+    for a positive density and for zero-mean weights of mixed sign (whose sums
+    cancel), and with the two-RHS launch, which evaluates every PP entry
+    directly."""
     pts = I.random_sphere_points(20000, 31)
-    w = np.random.default_rng(32).uniform(0.5, 1.5, len(pts)) * (4 * math.pi / len(pts))
+    rng = np.random.default_rng(32)
+    if sign == "positive":
+        w = rng.uniform(0.5, 1.5, len(pts)) * (4 * math.pi / len(pts))
+    else:
+        w = rng.standard_normal(len(pts)) * (4 * math.pi / len(pts))
+        if kernel == O.KERNEL_ONE:
+            w = w + 4 * math.pi / len(pts)  # K = 1 needs a sum away from zero
     P32 = C.plan_create(dev(torch, pts), kernel, 5, 0.7, 40, precision=C.FP32_BULK)
     st = C.plan_stats(P32)
     assert st["sym_pairs"] > 0.3 * st["n_list"][0] / 2
     one = C.evaluate(P32, dev(torch, w[None])).cpu().numpy()[0]
     two = C.evaluate(P32, dev(torch, np.stack([w, w]))).cpu().numpy()
-    P64 = C.plan_create(dev(torch, pts), kernel, 5, 0.7, 40, precision=C.FP64)
-    ref = C.evaluate(P64, dev(torch, w[None])).cpu().numpy()[0]
-    assert rel(one, two[0]) <= 1e-6
-    assert rel(one, ref) <= 1e-5
+    ref = O.FMM(pts, 5, 0.7, 40).evaluate(kernel, w)[0]
+    check32(f"fmm32-sym-k{kernel}-{sign}", rel(one, ref))
+    check32(f"fmm32-sym-vs-2rhs-k{kernel}-{sign}", rel(one, two[0]))
+
+
+@pytest.mark.parametrize("kernel", [O.KERNEL_NEWTON, O.KERNEL_LAPLACE])
+def test_full_size_symmetric_near_field_mixed_sign(torch, C, kernel):
+    """The benchmarked launch shape (6 x 1024^2 = 6,291,456 cubed-sphere
+    points, n = 12, MAC 0.7, N0 = 576, one right-hand side, FP32 bulk, so the
+    mirrored-pair kernel carries most of the near field) on zero-mean weights
+    of mixed sign: a seeded random combination of real harmonics Y_nm,
+    n <= 16, plus white noise at 10% of its rms, times the cell areas.  The
+    FP32-bulk potential is compared with the oracle direct sum on 256 sampled
+    targets."""
+    pts, A = I.cubed_sphere_grid(1024)
+    N = len(pts)
+    coeffs = I.random_sh_coeffs(16, 1, seed=40 + kernel)
+    f = I.sph_harm_combination(pts, coeffs, nrhs=1)[0]
+    f = f + 0.1 * np.sqrt(np.mean(f * f)) * np.random.default_rng(41).standard_normal(N)
+    w = f * A
+    tg = np.sort(np.random.default_rng(42 + kernel).choice(N, 256, replace=False))
+    ds = O.direct(pts, kernel, w, tg)[0, :, 0]
+    P32, f32 = run_fmm(torch, C, pts, kernel, w, 12, 0.7, 576, precision=C.FP32_BULK)
+    st = C.plan_stats(P32)
+    assert st["sym_evals"] > 0.5 * st["evals"][0] / 2
+    del P32
+    e32 = rel(f32[0, tg, 0], ds)
+    check32(f"fmm32-sym-6m-mixed-k{kernel}", e32)

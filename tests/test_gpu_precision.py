@@ -17,6 +17,7 @@ import pytest
 import oracle as O
 from paper_2508_13550_gb300 import inputs as I
 from gpu_util import cuda_or_skip, dev
+from fp32_bars import check as check32
 
 pytestmark = pytest.mark.gpu
 
@@ -53,7 +54,7 @@ def test_fp32_bulk_newton_uniform_grid_unbiased(torch, C):
     w = I.land_mask_field(pts, I.MASTER_SEED + 3) * A
     e, bias = errors(torch, C, pts, O.KERNEL_NEWTON, w, 8, 256)
     print(f"\nNewtonian m=256 n=8: E={e:.3e} bias={bias:.3e}")
-    assert e < 2.5e-8
+    check32("fmm32-newton-land-m256-n8", e)
     assert abs(bias) < 2.2e-8
 
 
@@ -61,7 +62,7 @@ def test_fp32_bulk_poisson_uniform_grid(torch, C):
     pts, A, w, _ = I.workload_poisson_y43(256)
     e, bias = errors(torch, C, pts, O.KERNEL_LAPLACE, w, 8, 256)
     print(f"\nPoisson Y43 m=256 n=8: E={e:.3e} bias={bias:.3e}")
-    assert e < 2.6e-7
+    check32("fmm32-poisson-y43-m256-n8", e)
     assert abs(bias) < 3e-8
 
 
@@ -73,4 +74,4 @@ def test_fp32_bulk_biharmonic_against_direct(torch, C):
     w = I.land_mask_field(pts, 21) * A
     e, bias = errors(torch, C, pts, O.KERNEL_BIHARMONIC, w, 8, 256)
     print(f"\nbiharmonic m=128 n=8: E={e:.3e} bias={bias:.3e}")
-    assert e < 1e-6
+    check32("fmm32-biharmonic-land-m128-n8", e)

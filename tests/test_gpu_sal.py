@@ -3,8 +3,9 @@ G_SAL_approx with the paper's Love number fit) through the C ABI against the
 oracle on the same seeded inputs.
 
 Bars: FP64 CSFMM and CSTC vs the oracle's, relative l2 <= 1e-12; FP64 direct
-sum vs the oracle's <= 1e-13; FP32 bulk vs the FP64 direct sum <= 1e-5 (the
-FP32-bulk bar); several right-hand sides equal one at a time.
+sum vs the oracle's <= 1e-13; FP32 bulk vs the oracle's FP64 direct sum (or
+its FMM on the same tree) at most the per-case bar of fp32_bars.py (about 4x
+the error measured on GB300); several right-hand sides against one at a time.
 """
 import numpy as np
 import pytest
@@ -12,6 +13,7 @@ import pytest
 import oracle as O
 from paper_2508_13550_gb300 import inputs as I
 from gpu_util import cuda_or_skip, dev
+from fp32_bars import check as check32
 
 pytestmark = pytest.mark.gpu
 
@@ -62,7 +64,8 @@ def test_fp32_bulk_against_fp64_direct(torch, C):
     d32 = C.direct(dev(torch, pts), C.KERNEL_SAL, dev(torch, np.atleast_2d(w)),
                    precision=C.FP32_BULK).cpu().numpy()[0, tg, 0]
     print(f"\nSAL FP32 bulk m=128 n=8: FMM {rel(got, ds):.2e}, direct {rel(d32, ds):.2e}")
-    assert rel(got, ds) < 1e-5 and rel(d32, ds) < 1e-5
+    check32("fmm32-sal-land-m128-n8", rel(got, ds))
+    check32("direct32-sal-land-m128", rel(d32, ds))
 
 
 def test_fp32_multi_rhs_matches_single(torch, C):
@@ -71,6 +74,8 @@ def test_fp32_multi_rhs_matches_single(torch, C):
     P = C.plan_create(dev(torch, pts), C.KERNEL_SAL, 7, 0.7, 80, precision=C.FP32_BULK,
                       max_nrhs=8)
     allr = C.evaluate(P, dev(torch, W)).cpu().numpy()
-    for r in (0, 5):
+    ref = O.FMM(pts, 7, 0.7, 80).evaluate(O.KERNEL_SAL, W[[0, 5]])
+    for k, r in enumerate((0, 5)):
         one = C.evaluate(P, dev(torch, W[r:r + 1])).cpu().numpy()[0]
-        assert rel(allr[r], one) < 1e-5
+        check32("fmm32-sal-chunk-vs-single", rel(allr[r], one))
+        check32("fmm32-sal-multi-vs-oracle-fmm", rel(allr[r], ref[k]))

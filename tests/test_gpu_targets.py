@@ -2,9 +2,9 @@
 Sec. 1) through the C ABI against the oracle on the same seeded inputs.
 
 Bars: FP64 CSFMM and CSTC against the oracle's CSFMM and CSTC on the same
-tree, relative l2 <= 1e-12; FP32 bulk against the oracle direct sum <= 1e-5
-(the FP32-bulk bar of every parity test; measured 2e-7 to 1.6e-6, the most for
-the Biot-Savart velocity, whose sum cancels);
+tree, relative l2 <= 1e-12; FP32 bulk against the oracle direct sum at most
+the per-case bar of fp32_bars.py (about 4x the error measured on GB300; the
+Biot-Savart velocity, whose sum cancels, has the largest);
 K = 1 reproduces sum_j w_j at every target.
 """
 import numpy as np
@@ -13,6 +13,7 @@ import pytest
 import oracle as O
 from paper_2508_13550_gb300 import inputs as I
 from gpu_util import cuda_or_skip, dev
+from fp32_bars import check as check32
 
 pytestmark = pytest.mark.gpu
 
@@ -77,7 +78,7 @@ def test_fp32_bulk_against_direct(torch, C, kernel):
                               precision=C.FP32_BULK)
     got = C.evaluate(P, dev(torch, np.atleast_2d(w))).cpu().numpy()
     print(f"\nkernel {kernel} FP32 bulk at separate targets: {rel(got, ds):.2e}")
-    assert rel(got, ds) < 1e-5
+    check32(f"fmm32-targets-k{kernel}", rel(got, ds))
 
 
 def test_constant_kernel_and_host_entry(torch, C):
