@@ -247,6 +247,90 @@ def fp64_at_matched_accuracy(Cs, torch, dpts, dw, wl, dim, dtg, ds, err32, ms32_
             "note": "no FP64 degree up to the workload's reaches the FP32-bulk error"}
 
 
+def timed_steps(torch, Cs, plan, dw, out, stream, steps):
+    """CUDA-event time of each of `steps` evaluations (ms), synchronised."""
+    res = []
+    for _ in range(steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        Cs.evaluate(plan, dw, out=out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res.append(e0.elapsed_time(e1))
+    return res
+
+
+def side_workloads(args, torch, Cs, n_sm, sm_max):
+    """The other BASELINE workloads measured in the same run, each on its
+    own plan with inputs resident (CUDA events, median of the steps):
+    Biot-Savart on 6 x 256^2 points (n = 10, FP64 and FP32 bulk) and the
+    16-right-hand-side Poisson workload on 6 x 512^2 points (n = 10, FP32
+    bulk, persistent launch).  Errors against the FP64 direct sum on sampled
+    targets."""
+    from paper_2508_13550_gb300 import inputs as I
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    res = {}
+    rng = np.random.default_rng(20250814)
+
+    def case(pts, w, kid, n, N0, prec, nrhs, samples):
+        dp = torch.from_numpy(pts).to(dev)
+        dw = torch.from_numpy(np.ascontiguousarray(w)).to(dev)
+        dim = Cs.kernel_dim(kid)
+        tg = torch.from_numpy(np.sort(rng.choice(len(pts), samples, replace=False))
+                              .astype(np.int64)).to(dev)
+        ds = Cs.direct(dp, kid, dw, precision=Cs.FP64, targets=tg)
+        plan = Cs.plan_create(dp, kid, n, 0.7, N0, precision=prec, max_nrhs=nrhs)
+        out = torch.empty((nrhs, len(pts), dim), dtype=torch.float64, device=dev)
+        for _ in range(3):
+            Cs.evaluate(plan, dw, out=out)
+        torch.cuda.synchronize()
+        steps = timed_steps(torch, Cs, plan, dw, out, stream, args.side_steps)
+        Cs.plan_enable_timing(plan, True)
+        Cs.evaluate(plan, dw, out=out)
+        ph, calls = Cs.plan_phase_times(plan)
+        Cs.plan_enable_timing(plan, False)
+        Cs.plan_sync(plan)
+        st = Cs.plan_stats(plan)
+        d = out[:, tg] - ds
+        errs = [float(torch.linalg.norm(d[r]) / torch.linalg.norm(ds[r])) for r in range(nrhs)]
+        ms = statistics.median(steps)
+        Cs.plan_destroy(plan)
+        return {"N": len(pts), "nrhs": nrhs, "degree": n, "max_leaf": N0,
+                "precision": "fp32" if prec == Cs.FP32_BULK else "fp64",
+                "ms_per_eval": ms, "step_ms_min": min(steps), "steps": len(steps),
+                "targets_per_s": len(pts) * nrhs / (ms / 1e3),
+                "kernel_evals_per_s": sum(st["evals"]) / (ms / 1e3),
+                "rel_err_vs_fp64_ds_max_over_rhs": max(errs), "err_samples": samples,
+                "phase_ms": {k: v / max(calls, 1) for k, v in ph.items()},
+                "launches_per_evaluate": st["launches_per_evaluate"]}
+
+    pts, A, w, _ = I.workload_rh_biot_savart(256)
+    res["biot_savart_393k"] = {
+        "desc": "Biot-Savart, RH wave-4 vorticity + 1e-3 noise, cubed sphere 6x256^2 = 393,216 "
+                "points, n=10, MAC 0.7, N0=400",
+        "fp64": case(pts, w, Cs.KERNEL_BIOT_SAVART, 10, 400, Cs.FP64, 1, 512),
+        "fp32_bulk": case(pts, w, Cs.KERNEL_BIOT_SAVART, 10, 400, Cs.FP32_BULK, 1, 512)}
+    pts, A, W, _ = I.workload_multi_rhs(512, 16, with_exact=False)
+    mr = case(pts, W, Cs.KERNEL_LAPLACE, 10, 400, Cs.FP32_BULK, 16, 256)
+    ms_k = mr["phase_ms"].get("near", 0.0)
+    per_clk = 128.0 / (6 + 16)
+    mr["roofline"] = {"kernel": "persistent_kernel (CC, CP, PP, PC for 16 RHS, L2L, L2P)",
+                      "bound": "alu (FP32 pipe: 6 + 16 lane-ops per evaluation)",
+                      "achieved_geval_per_s": mr["kernel_evals_per_s"] / 1e9 if ms_k else None,
+                      "kernel_ms": ms_k,
+                      "kernel_geval_per_s": (mr["kernel_evals_per_s"] * mr["ms_per_eval"] / ms_k
+                                             / 1e9) if ms_k else None,
+                      "peak_geval_per_s": n_sm * per_clk * sm_max / 1e3,
+                      "frac": (mr["kernel_evals_per_s"] * mr["ms_per_eval"] / ms_k)
+                              / (n_sm * per_clk * sm_max * 1e6) if ms_k else None}
+    res["poisson_16rhs_1.5m"] = dict(
+        desc="Poisson log kernel, 16 RHS of random Y_nm combinations (n <= 32), cubed sphere "
+             "6x512^2 = 1,572,864 points, n=10, MAC 0.7, N0=400, FP32 bulk", **mr)
+    return res
+
+
 def run_reference(args):
     """CPU oracle arm: each step evaluates a bounded sample of the workload."""
     rank = int(os.environ.get("RANK", "0"))
@@ -325,7 +409,8 @@ def run_ours(args):
         log("autotune", tuned)
     plan = Cs.plan_create(dpts, wl["kernel"], wl["n"], wl["theta"], wl["N0"], precision=prec,
                           max_nrhs=max(nrhs, 1),
-                          rhs_chunk=tuned["rhs_chunk"] if tuned else 0)
+                          rhs_chunk=tuned["rhs_chunk"] if tuned else 0,
+                          no_persistent=args.no_persistent)
     st = Cs.plan_stats(plan)
     dim = Cs.kernel_dim(wl["kernel"])
     out = torch.empty((nrhs, N, dim), dtype=torch.float64, device=dev)
@@ -405,17 +490,15 @@ def run_ours(args):
         p64 = Cs.plan_create(dpts, wl["kernel"], wl["n"], wl["theta"], wl["N0"],
                              precision=Cs.FP64, max_nrhs=1)
         o64 = torch.empty((1, N, dim), dtype=torch.float64, device=dev)
-        Cs.evaluate(p64, dw[:1], out=o64)
+        Cs.evaluate(p64, dw[:1], out=o64)  # warm-up
         torch.cuda.synchronize(dev)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        Cs.evaluate(p64, dw[:1], out=o64)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        ms64 = e0.elapsed_time(e1)
+        steps64 = timed_steps(torch, Cs, p64, dw[:1], o64, stream, args.fp64_steps)
+        ms64 = sum(steps64) / len(steps64)
         err64 = float(torch.linalg.norm(o64[:1, dtg] - ds) / torch.linalg.norm(ds))
-        fp64 = {"ms_per_eval_1rhs": ms64, "rel_err_vs_fp64_ds": err64,
+        st64 = Cs.plan_stats(p64)
+        fp64 = {"ms_per_eval_1rhs": ms64, "steps": len(steps64), "step_ms_min": min(steps64),
+                "step_ms_max": max(steps64), "rel_err_vs_fp64_ds": err64,
+                "kernel_evals_per_s": sum(st64["evals"]) / (ms64 / 1e3),
                 "speedup_of_fp32_bulk_per_rhs": ms64 / (ms_step / nrhs)}
         Cs.plan_destroy(p64)
         del o64
@@ -450,6 +533,12 @@ def run_ours(args):
         what = {"pp_sym_kernel": "mirrored PP leaf pairs, one evaluation per pair",
                 "near32x2_kernel": "self and unmirrored PP, PC",
                 "far32x2_kernel": "CC, CP"}
+    elif phases.get("far", 0.0) == 0.0:
+        # the persistent launch: far field, near field, L2L and L2P of all
+        # right-hand sides in one kernel (its time is the NEAR phase)
+        kern = {"persistent_kernel": (sum(st["evals"]), phases["near"] / ncalls)}
+        what = {"persistent_kernel": f"CC, CP, PP, PC, L2L, L2P for {nrhs} right-hand sides "
+                                     "in one launch"}
     else:
         # per evaluation of all right-hand sides (chunks of 16 in one launch)
         kern = {
@@ -500,6 +589,8 @@ def run_ours(args):
         "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms),
                     "n": len(step_ms)},
     }
+    if rank == 0 and world == 1 and args.side_workloads:
+        line["other_workloads"] = side_workloads(args, torch, Cs, n_sm, sm_max)
     if rank == 0 and world == 1 and args.serve_sample > 0:
         line["serving"] = run_serving(args, sample=args.serve_sample)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -978,6 +1069,14 @@ def main():
     ap.add_argument("--cpu-leaves", type=int, default=16384)
     ap.add_argument("--ref-leaves", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=5,
+                    help="timed evaluations of the FP64 form on the same workload")
+    ap.add_argument("--side-steps", type=int, default=10)
+    ap.add_argument("--no-side-workloads", dest="side_workloads", action="store_false",
+                    help="skip the Biot-Savart 393k and 16-RHS 1.5M workloads")
+    ap.add_argument("--no-persistent", action="store_true",
+                    help="several right-hand sides: per-phase launches instead of the "
+                         "persistent launch")
     ap.add_argument("--no-fp64-compare", dest="fp64_compare", action="store_false")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="multi-RHS workloads: keep the default leaf size and RHS chunk")
@@ -989,7 +1088,7 @@ def main():
     ap.add_argument("--bve-quick", action="store_true",
                     help="bve workload: time remeshed CSFMM FP32 steps only")
     ap.add_argument("--serve-requests", type=int, default=2000)
-    ap.add_argument("--serve-sample", type=int, default=300,
+    ap.add_argument("--serve-sample", type=int, default=2000,
                     help="requests of the serving stream measured in the default line (0: none)")
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-budget-gb", type=float, default=96.0)

@@ -91,7 +91,12 @@ typedef struct {
   int shrink;     /* 1: every cell's interpolation box is shrunk to bound its points (Sec. 3;
                      fewer direct pairs on clustered points); 0: the cell's own square
                      (default) */
-  int reserved[3];
+  int no_persistent; /* FP32 bulk, scalar kernels, nrhs a multiple of 8: 0 (default) evaluates
+                     the far field, near field, L2L and L2P of all right-hand sides in one
+                     persistent launch whose blocks draw work from a device counter and wait
+                     (bounded in time) only for the downward pass's dependencies; the result
+                     equals the per-phase launches bit for bit.  1: per-phase launches */
+  int reserved[2];
 } csfmm_options;
 
 typedef struct csfmm_plan_s *csfmm_plan;
@@ -112,7 +117,10 @@ typedef struct {
   int64_t sym_evals;       /* kernel evaluations of those pairs (each serves two interactions) */
 } csfmm_stats;
 
-/* Evaluation phases timed by csfmm_plan_phase_times. */
+/* Evaluation phases timed by csfmm_plan_phase_times.  With the persistent
+ * launch (csfmm_options.no_persistent) the NEAR phase covers that whole
+ * launch (far field, near field, L2L, L2P) and FAR, PPSYM, L2L, L2P are
+ * empty. */
 enum {
   CSFMM_PHASE_GATHER = 0, CSFMM_PHASE_P2M = 1, CSFMM_PHASE_M2M = 2, CSFMM_PHASE_FAR = 3,
   CSFMM_PHASE_PPSYM = 4, /* FP32 bulk, one RHS: mirrored PP pairs (empty otherwise) */
@@ -479,8 +487,22 @@ csfmm_status csfmm_bve_step_remeshed(csfmm_remesh_grid grid, csfmm_plan grid_pla
                                      double *tracer_out, void *stream);
 
 /* Waits for the plan's work on stream and returns a deferred device status
- * (CSFMM_ERR_DEVICE / CSFMM_ERR_TIMEOUT) if a kernel reported one. */
+ * (CSFMM_ERR_DEVICE / CSFMM_ERR_TIMEOUT) if a kernel reported one.  A
+ * timeout is reported once (the status is cleared, the plan stays usable);
+ * the outputs of the evaluation that timed out are incomplete. */
 csfmm_status csfmm_plan_sync(csfmm_plan plan, void *stream);
+
+/* Dependency waits of the persistent launch (see csfmm_options.no_persistent):
+ * every wait gives up after limit_ms milliseconds of wall time (default
+ * 2000), sets the plan's status word and makes the other waits of the launch
+ * give up at once, so that the kernel returns and csfmm_plan_sync reports
+ * CSFMM_ERR_TIMEOUT.  never_ready = 1 is a test hook: every wait then needs
+ * one completion more than will ever happen, so that a test can check the
+ * timeout path without a fault; evaluations of such a plan are incomplete.
+ * The setting applies to evaluations launched afterwards (not to a CUDA graph
+ * captured earlier).
+ * Errors: INVALID_ARG (NULL plan, limit_ms outside (0, 60000]). */
+csfmm_status csfmm_plan_test_wait(csfmm_plan plan, int never_ready, double limit_ms);
 
 /* Frees every device buffer of the plan.  The caller must make sure no work
  * of the plan is still running. */

@@ -55,7 +55,8 @@ class CsfmmError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("max_nrhs", ctypes.c_int),
                 ("use_graphs", ctypes.c_int), ("rhs_chunk", ctypes.c_int),
-                ("shrink", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("shrink", ctypes.c_int), ("no_persistent", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 class TuneResult(ctypes.Structure):
@@ -148,6 +149,7 @@ _SIGS = {
     "csfmm_plan_enable_timing": [_VP, ctypes.c_int],
     "csfmm_plan_phase_times": [_VP, _VP, _VP],
     "csfmm_plan_sync": [_VP, _VP],
+    "csfmm_plan_test_wait": [_VP, ctypes.c_int, ctypes.c_double],
     "csfmm_plan_destroy": [_VP],
     "csfmm_server_create": [_I64, ctypes.c_int, ctypes.POINTER(_VP)],
     "csfmm_server_submit": [_VP, ctypes.POINTER(Request), ctypes.POINTER(_I64)],
@@ -232,10 +234,11 @@ class Plan:
 
 def plan_create(points, kernel_id: int, degree: int, theta: float, max_leaf: int,
                 precision: int = FP64, max_nrhs: int = 16, use_graphs: int = 0, rhs_chunk: int = 0,
-                shrink: bool = False, stream=None):
+                shrink: bool = False, stream=None, no_persistent: bool = False):
     import torch
     lib = load()
-    opt = Options(precision, max_nrhs, use_graphs, rhs_chunk, int(bool(shrink)))
+    opt = Options(precision, max_nrhs, use_graphs, rhs_chunk, int(bool(shrink)),
+                  int(bool(no_persistent)))
     h = ctypes.c_void_p()
     N = points.shape[0]
     rc = lib.csfmm_plan_create(_dev(points, torch.float64), N, kernel_id, degree, theta,
@@ -247,11 +250,12 @@ def plan_create(points, kernel_id: int, degree: int, theta: float, max_leaf: int
 def plan_create_targets(sources, targets, kernel_id: int, degree: int, theta: float,
                         max_leaf: int, precision: int = FP64, max_nrhs: int = 16,
                         use_graphs: int = 0, rhs_chunk: int = 0, shrink: bool = False,
-                        stream=None):
+                        stream=None, no_persistent: bool = False):
     """csfmm_plan_create_targets: a plan whose evaluations take weights at the
     sources [nrhs, Ns] and return the sum at separate targets [nrhs, Nt, dim]."""
     import torch
-    opt = Options(precision, max_nrhs, use_graphs, rhs_chunk, int(bool(shrink)))
+    opt = Options(precision, max_nrhs, use_graphs, rhs_chunk, int(bool(shrink)),
+                  int(bool(no_persistent)))
     h = ctypes.c_void_p()
     Ns, Nt = sources.shape[0], targets.shape[0]
     _check(load().csfmm_plan_create_targets(_dev(sources, torch.float64), Ns,
@@ -538,6 +542,12 @@ def plan_phase_times(plan: Plan):
 
 def plan_sync(plan: Plan, stream=None):
     _check(load().csfmm_plan_sync(plan.handle, _stream(stream)))
+
+
+def plan_test_wait(plan: Plan, never_ready: bool, limit_ms: float = 2000.0):
+    """csfmm_plan_test_wait: the bound of the persistent launch's dependency
+    waits, and the test hook that makes every wait unsatisfiable."""
+    _check(load().csfmm_plan_test_wait(plan.handle, int(bool(never_ready)), float(limit_ms)))
 
 
 class Server:

@@ -164,6 +164,7 @@ csfmm_status csfmm_plan_create(const double *points, int64_t N, int kernel_id, i
   pl.max_nrhs = o.max_nrhs;
   pl.use_graphs = o.use_graphs;
   pl.shrink = o.shrink != 0;
+  pl.no_persistent = o.no_persistent != 0;
   pl.rhs_chunk = o.rhs_chunk == 0 ? 16 : o.rhs_chunk;
   if (pl.rhs_chunk != 16 && pl.rhs_chunk != 8 && pl.rhs_chunk != 4) {
     set_error("rhs_chunk must be 0, 4, 8 or 16 (got %d)", o.rhs_chunk);
@@ -486,6 +487,10 @@ csfmm_status csfmm_plan_sync(csfmm_plan plan, void *stream) {
   int st = 0;
   CSFMM_CUDA(cudaMemcpy(&st, pl.status, sizeof(int), cudaMemcpyDeviceToHost));
   if (st & kStatusTimeout) {
+    // a timeout is reported once: the word is cleared so that the plan can
+    // be evaluated again
+    const int zero = 0;
+    CSFMM_CUDA(cudaMemcpy(pl.status, &zero, sizeof(int), cudaMemcpyHostToDevice));
     set_error("a bounded device-side wait timed out (status 0x%x)", st);
     return CSFMM_ERR_TIMEOUT;
   }
@@ -493,6 +498,16 @@ csfmm_status csfmm_plan_sync(csfmm_plan plan, void *stream) {
     set_error("device status word 0x%x", st);
     return CSFMM_ERR_DEVICE;
   }
+  return CSFMM_OK;
+}
+
+csfmm_status csfmm_plan_test_wait(csfmm_plan plan, int never_ready, double limit_ms) {
+  if (!plan || !(limit_ms > 0.0) || limit_ms > 60000.0) {
+    set_error("plan must be non-NULL and 0 < limit_ms <= 60000");
+    return CSFMM_ERR_INVALID_ARG;
+  }
+  plan->impl.wait_never_ready = never_ready != 0;
+  plan->impl.wait_limit_ms = limit_ms;
   return CSFMM_OK;
 }
 

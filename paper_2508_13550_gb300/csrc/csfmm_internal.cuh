@@ -129,6 +129,24 @@ struct PlanView {
   int wtot_ld;
 };
 
+// Arguments of the persistent multi-right-hand-side kernel (persistent.cu):
+// one launch evaluates the far field, the near field, L2L and L2P of every
+// chunk of NR right-hand sides, drawing items from a device work counter.
+struct PersistArgs {
+  const int32_t *leaves;
+  int nleaves, ncells;
+  int nl2l;                 // cells of levels 0 .. nlevels-2 (L2L items, in level order)
+  int nch, nrhs, ldr;       // nch chunks of NR right-hand sides; rhs stride of wbar / psi
+  int far_pair;             // 1: a far item holds two cells, one per half block
+  int nfar, nnear, total;   // items: far, then near, then L2L, then L2P
+  const float *wsf, *wbar;
+  double *phi, *psi, *out;
+  int *ctr;                 // [0] queue head, [1] abort flag, then far_done, l2l_done and
+                            // near_done counters, ncells each
+  int extra;                // test hook: completions every wait needs beyond the real count
+  long long limit_ns;       // bound of every dependency wait
+};
+
 struct Plan {
   int device = 0;
   int64_t N = 0;
@@ -141,6 +159,11 @@ struct Plan {
   int use_graphs = 0;
   int rhs_chunk = 16;   // FP32 bulk, scalar kernels: 16, 8 or 4
   int shrink = 0;       // cell boxes shrunk to their points
+  int no_persistent = 0; // 1: several right-hand sides always take the per-phase launches
+  // dependency waits of the persistent kernel: bound, and a test hook that
+  // makes every wait need one completion more than will ever happen
+  double wait_limit_ms = 2000.0;
+  int wait_never_ready = 0;
   double theta = 0.7;
   int ncells = 0, nleaves = 0, nlevels = 0;
   std::vector<int> level_begin;  // cells of level l: [level_begin[l], level_begin[l+1])
@@ -208,6 +231,11 @@ struct GraphEntry {
   cudaGraphExec_t exec = nullptr;
   cudaGraphNode_t gather = nullptr, l2p = nullptr;
   cudaKernelNodeParams gather_params{}, l2p_params{};
+  // persistent launch (several right-hand sides): its node takes the output
+  cudaGraphNode_t persist = nullptr;
+  cudaKernelNodeParams persist_params{};
+  PlanView persist_view{};
+  PersistArgs persist_args{};
   const double *w = nullptr;
   double *out = nullptr;
   int launches = 0;
@@ -238,9 +266,15 @@ struct Workspace {
   double *phi = nullptr;    // [max_nrhs][N][dim] near-field potentials, tree order
   float *sym_part = nullptr;     // [plan.sym_part_len] cross-pair partial sums (FP32 form)
   float2 *wtot = nullptr;        // [nc][max_nrhs][2] weight totals (FP32 form)
+  int *ctr = nullptr;            // [2 + 3 nc] work counter and dependency counters of the
+                                 // persistent kernel (FP32 form, scalar kernels)
   double *stage_w = nullptr;    // device staging for host-buffer evaluations [max_nrhs][N]
   double *stage_out = nullptr;  // [max_nrhs][N][dim]
   int last_nrhs = 0;
+  // the last evaluation took the persistent launch with these arguments
+  bool last_persistent = false;
+  PlanView last_persist_view{};
+  PersistArgs last_persist_args{};
   // Second stream of an evaluation: the upward pass, far field and L2L run on
   // it while the near field runs on the caller's stream, joined by events
   // (null for short-lived workspaces, which run every pass in order).
@@ -300,6 +334,17 @@ void launch_pp_sym32(const PlanView &v, const int2 *pairs, const int32_t *off, i
 void launch_near32(const PlanView &v, const int32_t *leaves, int nleaves, const float *wsf, int ldw,
                    const float *wbar, int ldr, int r0, int nr, double *phi, cudaStream_t st,
                    const float *part = nullptr);
+// Persistent multi-right-hand-side launch (persistent.cu).  Eligible: FP32
+// bulk, a scalar kernel, nrhs a multiple of the chunk (16 or 8) and a
+// workspace with counters; *chunk receives the chunk.
+bool persistent_eligible(const Plan &pl, const Workspace &W, int nrhs, int *chunk);
+size_t persistent_counter_ints(const Plan &pl);
+// Clears the counters and launches the kernel on st (far, near, L2L, L2P of
+// all nrhs right-hand sides into out); *used receives its arguments.
+csfmm_status launch_persistent(const PlanView &v, const Plan &pl, Workspace &W, int nrhs,
+                               int chunk, double *out, cudaStream_t st, PersistArgs *used);
+// The kernel function of a plan's persistent launch (graph node lookup).
+const void *persistent_function(const Plan &pl, int chunk);
 // Direct sum (direct.cu).
 csfmm_status direct_impl(const double *points, int64_t N, int kernel_id, const double *w,
                          int nrhs, const int64_t *targets, int64_t ntargets, double *out,

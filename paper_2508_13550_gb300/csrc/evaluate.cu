@@ -23,6 +23,7 @@
 
 #include "csfmm_internal.cuh"
 #include "dilog.cuh"
+#include "downward_df.cuh"
 
 namespace csfmm {
 
@@ -286,25 +287,6 @@ __global__ void m2m_kernel(PlanView v, int cell0, int r0, int nr, Real *wbar, in
   }
 }
 
-// ---------------------------------------------------------------------------
-// Double-float arithmetic on the FP32 pipes for the FP32-form passes: a value
-// is an unevaluated pair (h, l), products carry their exact FP32 rounding
-// error (FMA) and sums use Knuth's two-sum.  The rounded intrinsics keep the
-// compiler from contracting a product into the following sum.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void df_acc_prod(float &sh, float &sl, float ah, float al, float bh,
-                                            float bl) {
-  const float ph = __fmul_rn(ah, bh);
-  float pe = fmaf(ah, bh, -ph);
-  pe = fmaf(ah, bl, pe);
-  pe = fmaf(al, bh, pe);
-  const float s = __fadd_rn(sh, ph);
-  const float bb = __fadd_rn(s, -sh);
-  const float e = __fadd_rn(__fadd_rn(sh, -__fadd_rn(s, -bb)), __fadd_rn(ph, -bb));
-  sh = s;
-  sl = __fadd_rn(sl, __fadd_rn(e, pe));
-}
-
 // M2M of the FP32 form: same contraction as m2m_kernel with the matrices as
 // FP32 rounding + remainder (m2m32) and every sum in double-float; proxy
 // weights are stored in FP32.  The same constant matrices act on every cell
@@ -434,69 +416,11 @@ __global__ void l2l_kernel(PlanView v, int cell0, int r0, int nr, int dim, Real 
     }
 }
 
-// L2L of the FP32 form: the contraction of l2l_kernel in double-float on the
-// FP32 pipes (FP64 proxy potentials split into FP32 pairs on load, matrices
-// as FP32 rounding + remainder), each child value added to its FP64 slot.
+// L2L of the FP32 form (downward_df.cuh), one block per parent cell of a level.
 __global__ void l2l_df_kernel(PlanView v, int cell0, int r0, int nr, int dim, double *psi,
                               int ldr) {
-  __shared__ float sMh[2 * kMaxP * kMaxP], sMl[2 * kMaxP * kMaxP];
-  __shared__ float sph[kMaxP * kMaxP], spl[kMaxP * kMaxP], sth[kMaxP * kMaxP], stl[kMaxP * kMaxP];
-  const int c = cell0 + blockIdx.x;
-  const int p = v.p, P = v.P;
-  const int32_t *ch = v.cchild + 4 * c;
-  if (ch[0] < 0 && ch[1] < 0 && ch[2] < 0 && ch[3] < 0) return;
-  for (int t = threadIdx.x; t < 2 * p * p; t += blockDim.x) {
-    sMh[t] = v.m2m32[t];
-    sMl[t] = v.m2m32[2 * p * p + t];
-  }
-  for (int r = r0; r < r0 + nr; ++r)
-    for (int d = 0; d < dim; ++d) {
-      __syncthreads();
-      for (int t = threadIdx.x; t < P; t += blockDim.x) {
-        const double x = psi[(((int64_t)c * ldr + r) * dim + d) * P + t];
-        const float h = __double2float_rn(x);
-        sph[t] = h;
-        spl[t] = __double2float_rn(x - (double)h);
-      }
-      for (int q = 0; q < 4; ++q) {
-        const int cc = ch[q];
-        if (cc < 0) continue;
-        int qa = q & 1, qb = q >> 1;
-        __syncthreads();
-        if (v.mcell32) {  // shrunk boxes: this child's own matrices
-          const float *Mc = v.mcell32 + (int64_t)cc * 4 * p * p;
-          for (int t = threadIdx.x; t < 2 * p * p; t += blockDim.x) {
-            sMh[t] = Mc[t];
-            sMl[t] = Mc[2 * p * p + t];
-          }
-          qa = 0;
-          qb = 1;
-          __syncthreads();
-        }
-        // st[m1][n2] = sum_m2 psi[m1][m2] M[qb][m2][n2]
-        for (int t = threadIdx.x; t < P; t += blockDim.x) {
-          const int m1 = t / p, n2 = t - m1 * p;
-          float sh = 0.f, sl = 0.f;
-          for (int m2 = 0; m2 < p; ++m2) {
-            const int o = (qb * p + m2) * p + n2;
-            df_acc_prod(sh, sl, sph[m1 * p + m2], spl[m1 * p + m2], sMh[o], sMl[o]);
-          }
-          sth[t] = sh;
-          stl[t] = sl;
-        }
-        __syncthreads();
-        double *dst = psi + (((int64_t)cc * ldr + r) * dim + d) * P;
-        for (int t = threadIdx.x; t < P; t += blockDim.x) {
-          const int n1 = t / p, n2 = t - n1 * p;
-          float sh = 0.f, sl = 0.f;
-          for (int m1 = 0; m1 < p; ++m1) {
-            const int o = (qa * p + m1) * p + n1;
-            df_acc_prod(sh, sl, sMh[o], sMl[o], sth[m1 * p + n2], stl[m1 * p + n2]);
-          }
-          dst[t] += (double)sh + (double)sl;
-        }
-      }
-    }
+  __shared__ float sm[kL2LDfSmemFloats];
+  l2l_df_cell(v, cell0 + blockIdx.x, r0, nr, dim, psi, ldr, sm);
 }
 
 // ---------------------------------------------------------------------------
@@ -708,7 +632,6 @@ __global__ void near_kernel(PlanView v, const int32_t *leaves, const double *ws,
 // One block per leaf, one thread per point of a chunk; the chunk's Lagrange
 // rows are staged through shared memory once for every (r, d).
 // ---------------------------------------------------------------------------
-constexpr int kL2PThreads = 128;
 
 template <typename Real>
 __global__ void __launch_bounds__(kL2PThreads) l2p_kernel(PlanView v, const int32_t *leaves,
@@ -749,95 +672,15 @@ __global__ void __launch_bounds__(kL2PThreads) l2p_kernel(PlanView v, const int3
   }
 }
 
-// L2P + finalize of the FP32-bulk form in double-float arithmetic: the proxy
-// potentials (FP64) and the Lagrange rows (FP32 hi + lo pairs) enter as
-// pairs of FP32 numbers; each product is formed exactly with an FMA and the
-// sums are compensated (two-sum), so the interpolation adds no FP32-level
-// rounding to the per-target value (a chain of FP32 contractions through
-// every tree level would otherwise dominate the bulk form's error).
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-  s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-// (S, C) += (ah + al) (bh + bl)
-__device__ __forceinline__ void df_fma(float &S, float &C, float ah, float al, float bh, float bl) {
-  const float p = __fmul_rn(ah, bh);
-  float e = fmaf(ah, bh, -p);
-  e = fmaf(ah, bl, fmaf(al, bh, e));
-  float q;
-  two_sum(S, p, S, q);
-  C = __fadd_rn(C, __fadd_rn(q, e));
-}
-
-// PC = p as a compile-time constant (0: runtime p) keeps each point's rows in
-// registers and unrolls the contractions.
+// L2P + finalize of the FP32-bulk form (downward_df.cuh), one block of
+// kL2PThreads per leaf.
 template <int PC>
 __global__ void __launch_bounds__(kL2PThreads) l2p_df_kernel(PlanView v, const int32_t *leaves,
                                                              const double *psi, int ldr, int nrhs,
                                                              int dim, const double *phi,
                                                              double *out) {
-  __shared__ float sph[kMaxP * kMaxP], spl[kMaxP * kMaxP];
-  __shared__ float sLa[kL2PThreads * kMaxP], sLal[kL2PThreads * kMaxP];
-  __shared__ float sLb[kL2PThreads * kMaxP], sLbl[kL2PThreads * kMaxP];
-  const int c = leaves[blockIdx.x];
-  const int b = v.cbegin[c], e = v.cend[c];
-  const int p = PC > 0 ? PC : v.p, P = p * p;
-  for (int i0 = b; i0 < e; i0 += kL2PThreads) {
-    const int nj = min(kL2PThreads, e - i0);
-    __syncthreads();
-    for (int t = threadIdx.x; t < nj * p; t += kL2PThreads) {
-      const int64_t o = (int64_t)i0 * p + t;
-      sLa[t] = v.La32[o];
-      sLal[t] = v.La32lo[o];
-      sLb[t] = v.Lb32[o];
-      sLbl[t] = v.Lb32lo[o];
-    }
-    const int t = threadIdx.x;
-    const int i = i0 + t;
-    for (int r = 0; r < nrhs; ++r)
-      for (int d = 0; d < dim; ++d) {
-        __syncthreads();
-        for (int u = threadIdx.x; u < P; u += kL2PThreads) {
-          const double x = psi[(((int64_t)c * ldr + r) * dim + d) * P + u];
-          const float hi = (float)x;
-          sph[u] = hi;
-          spl[u] = (float)(x - (double)hi);
-        }
-        __syncthreads();
-        if (t < nj && v.perm[i] >= v.tbase) {
-          const float *lah = sLa + t * p, *lal = sLal + t * p;
-          const float *lbh = sLb + t * p, *lbl = sLbl + t * p;
-          float S = 0.f, C = 0.f;
-          if constexpr (PC > 0) {
-            float bh[PC], bl[PC];
-#pragma unroll
-            for (int m2 = 0; m2 < PC; ++m2) {
-              bh[m2] = lbh[m2];
-              bl[m2] = lbl[m2];
-            }
-#pragma unroll
-            for (int m1 = 0; m1 < PC; ++m1) {
-              float sh = 0.f, sl = 0.f;
-#pragma unroll
-              for (int m2 = 0; m2 < PC; ++m2)
-                df_fma(sh, sl, sph[m1 * PC + m2], spl[m1 * PC + m2], bh[m2], bl[m2]);
-              df_fma(S, C, lah[m1], lal[m1], sh, sl);
-            }
-          } else {
-            for (int m1 = 0; m1 < p; ++m1) {
-              float sh = 0.f, sl = 0.f;
-              for (int m2 = 0; m2 < p; ++m2)
-                df_fma(sh, sl, sph[m1 * p + m2], spl[m1 * p + m2], lbh[m2], lbl[m2]);
-              df_fma(S, C, lah[m1], lal[m1], sh, sl);
-            }
-          }
-          const int64_t oi = ((int64_t)r * v.N + i) * dim + d;
-          out[((int64_t)r * v.ntgt + v.perm[i] - v.tbase) * dim + d] = phi[oi] + ((double)S + (double)C);
-        }
-      }
-  }
+  __shared__ float sm[kL2PDfSmemFloats];
+  l2p_df_leaf<PC>(v, leaves[blockIdx.x], psi, ldr, nrhs, dim, phi, out, sm);
 }
 
 void launch_l2p_df(int p, int nleaves, const PlanView &v, const int32_t *leaves, const double *psi,
@@ -945,6 +788,38 @@ csfmm_status run_passes(Plan &pl, Workspace &W, const double *w, int nrhs, doubl
     return CSFMM_OK;
   };
   csfmm_status s0;
+  W.last_persistent = false;
+  if constexpr (sizeof(Real) == 4 && KID != CSFMM_KERNEL_BIOT_SAVART) {
+    // several right-hand sides: the upward pass, then one persistent launch
+    // for the far field, the near field, L2L and L2P (persistent.cu); its
+    // time is recorded as the NEAR phase
+    int pchunk = 0;
+    if (persistent_eligible(pl, W, nrhs, &pchunk)) {
+      if ((s0 = p2m(st)) != CSFMM_OK) return s0;
+      CSFMM_BEGIN(CSFMM_PHASE_M2M, st);
+      for (int l = pl.nlevels - 2; l >= 0; --l) {
+        const int c0 = pl.level_begin[l], nlev = pl.level_begin[l + 1] - c0;
+        m2m_df_kernel<<<nlev, 128, 0, st>>>(v, c0, 0, nrhs, wbar, ldr, wtot);
+        ++pl.launches;
+      }
+      CSFMM_END(CSFMM_PHASE_M2M, st);
+      CSFMM_BEGIN(CSFMM_PHASE_NEAR, st);
+      if ((s0 = launch_persistent(v, pl, W, nrhs, pchunk, out, st, &W.last_persist_args)) !=
+          CSFMM_OK)
+        return s0;
+      ++pl.launches;
+      CSFMM_END(CSFMM_PHASE_NEAR, st);
+      for (int ph : {CSFMM_PHASE_FAR, CSFMM_PHASE_PPSYM, CSFMM_PHASE_L2L, CSFMM_PHASE_L2P}) {
+        CSFMM_BEGIN(ph, st);  // empty: their work is inside the persistent launch
+        CSFMM_END(ph, st);
+      }
+      W.last_persistent = true;
+      W.last_persist_view = v;
+      CSFMM_CUDA(cudaGetLastError());
+      pl.stats.launches_per_evaluate = pl.launches;
+      return CSFMM_OK;
+    }
+  }
   if (p2m_first && (s0 = p2m(st)) != CSFMM_OK) return s0;
   if (overlap) {
     CSFMM_CUDA(cudaEventRecord(W.ev_fork, st));
@@ -1160,6 +1035,9 @@ csfmm_status workspace_alloc(Plan &pl, Workspace &W, int max_nrhs) {
     if ((s = W.arena.alloc(&W.wbar32, nc * R * P)) != CSFMM_OK) return s;
     if ((s = W.arena.alloc(&W.wsf, R * N)) != CSFMM_OK) return s;
     if ((s = W.arena.alloc(&W.wtot, nc * R * 2)) != CSFMM_OK) return s;
+    if (pl.kernel_id != CSFMM_KERNEL_BIOT_SAVART &&
+        (s = W.arena.alloc(&W.ctr, persistent_counter_ints(pl))) != CSFMM_OK)
+      return s;
     if (pl.n_sym_pairs > 0 && pl.kernel_id != CSFMM_KERNEL_BIOT_SAVART &&
         (s = W.arena.alloc(&W.sym_part, (size_t)pl.sym_part_len)) != CSFMM_OK)
       return s;
@@ -1197,6 +1075,10 @@ csfmm_status capture(Plan &pl, Workspace &W, const double *w, int nrhs, double *
   const void *f_gather = (const void *)gather_kernel;
   const void *f_l2p = pl.precision == CSFMM_FP64 ? (const void *)l2p_kernel<double>
                                                  : l2p_df_function(pl.p);
+  const void *f_persist =
+      W.last_persistent
+          ? persistent_function(pl, W.last_persist_args.nrhs / W.last_persist_args.nch)
+          : nullptr;
   for (cudaGraphNode_t nd : nodes) {
     cudaGraphNodeType ty;
     CSFMM_CUDA(cudaGraphNodeGetType(nd, &ty));
@@ -1209,11 +1091,18 @@ csfmm_status capture(Plan &pl, Workspace &W, const double *w, int nrhs, double *
     } else if (kp.func == f_l2p) {
       g.l2p = nd;
       g.l2p_params = kp;
+    } else if (f_persist && kp.func == f_persist) {
+      g.persist = nd;
+      g.persist_params = kp;
     }
   }
-  if (!g.gather || !g.l2p) {
-    set_error("graph capture: gather or L2P node not found");
+  if (!g.gather || (!g.l2p && !g.persist)) {
+    set_error("graph capture: gather or output node not found");
     return CSFMM_ERR_CUDA;
+  }
+  if (g.persist) {
+    g.persist_view = W.last_persist_view;
+    g.persist_args = W.last_persist_args;
   }
   CSFMM_CUDA(cudaGraphInstantiate(&g.exec, graph, 0));
   g.nrhs = nrhs;
@@ -1249,7 +1138,17 @@ csfmm_status retarget(Plan &pl, Workspace &W, GraphEntry &g, const double *w, do
     kp.extra = nullptr;
     CSFMM_CUDA(cudaGraphExecKernelNodeSetParams(g.exec, g.gather, &kp));
   }
-  {
+  if (g.persist) {
+    // the persistent kernel writes the output: same arguments, new out
+    PersistArgs a = g.persist_args;
+    a.out = out;
+    void *args[] = {(void *)&g.persist_view, (void *)&a};
+    cudaKernelNodeParams kp = g.persist_params;
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    CSFMM_CUDA(cudaGraphExecKernelNodeSetParams(g.exec, g.persist, &kp));
+    g.persist_args = a;
+  } else {
     PlanView v = pl.view();
     const int32_t *leaves = pl.leaves;
     const void *psi = W.psi;

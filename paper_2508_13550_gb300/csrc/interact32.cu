@@ -27,6 +27,7 @@
 
 #include "csfmm_internal.cuh"
 #include "fp32_math.cuh"
+#include "multi32.cuh"
 
 namespace csfmm {
 
@@ -279,21 +280,47 @@ __global__ void __launch_bounds__(kThreads) near32_kernel(PlanView v, const int3
 //     columns: sum_{i in T} K(x_i, y_j) w_i   for the points j of S,
 // written to part[off[pair] ...] (rows first, then columns) as FP32 sums
 // (the log kernel stores sum w (log2 d2 - 1); the factor -ln2/4pi is applied
-// with the rest of the near field).  Two warps, each lane owns four rows of T (two packed pairs);
-// columns of S are staged as (x,x,y,y)/(z,z,w,w) tiles and processed in
-// groups of 32: every lane accumulates its rows' contributions to the 32
-// columns, then a butterfly transpose-reduction over the warp leaves the sum
-// of column g*32 + lane in lane `lane`; the two warps are combined in a fixed
-// order, so results are deterministic.
+// with the rest of the near field).  kSymWarps warps; each lane owns
+// 2 kSymQP rows of T (kSymQP packed pairs); columns of S are staged as
+// (x,x,y,y)/(z,z,w,w) tiles and processed in groups of kSymGroup: every lane
+// accumulates its rows' contributions to the group's columns, then a
+// butterfly transpose-reduction over the warp leaves the sum of column
+// g*kSymGroup + (lane mod kSymGroup) in that lane; the warps are combined in
+// a fixed order, so results are deterministic.
+//
+// Per kernel evaluation the FP32 pipe does 8 lane-ops (3 differences, |r|^2,
+// the row and the column FMA) plus the column reduction, about
+// 2 / (2 kSymQP) lane-ops (one add to fold the packed halves, one in the
+// butterfly, per column and lane), next to one MUFU operation.
 // ---------------------------------------------------------------------------
-constexpr int kSymThreads = 64;
-constexpr int kSymRows = 4 * kSymThreads;  // rows per pass
-constexpr int kSymCols = 256;              // columns per staged tile
+#ifndef CSFMM_SYM_WARPS
+#define CSFMM_SYM_WARPS 2
+#endif
+#ifndef CSFMM_SYM_QP
+#define CSFMM_SYM_QP 2
+#endif
+#ifndef CSFMM_SYM_GROUP
+#define CSFMM_SYM_GROUP 32
+#endif
+#ifndef CSFMM_SYM_MINB
+#define CSFMM_SYM_MINB 8
+#endif
+constexpr int kSymWarps = CSFMM_SYM_WARPS;
+constexpr int kSymQP = CSFMM_SYM_QP;         // packed row pairs per lane
+constexpr int kSymGroup = CSFMM_SYM_GROUP;   // columns per transpose-reduction
+constexpr int kSymThreads = 32 * kSymWarps;
+constexpr int kSymRowsPerWarp = 2 * kSymQP * 32;
+constexpr int kSymRows = kSymRowsPerWarp * kSymWarps;  // rows per pass
+constexpr int kSymCols = 256;                          // columns per staged tile
+static_assert(kSymGroup == 8 || kSymGroup == 16 || kSymGroup == 32, "column group");
+static_assert(kSymCols % kSymGroup == 0, "a tile holds whole column groups");
 
-// v[32] held by each lane -> returns sum over the warp of v[lane].
-__device__ __forceinline__ float transpose_reduce32(float (&v)[32], int lane) {
+// v[G] held by each lane -> the sum over the warp of v[lane mod G] (every
+// lane of a G-lane group first sums its group, then the groups are added).
+template <int G>
+__device__ __forceinline__ float transpose_reduce(float (&v)[G], int lane) {
 #pragma unroll
-  for (int s = 16; s >= 1; s >>= 1) {
+  for (int s = G / 2; s >= 1; s >>= 1) {
     const bool up = (lane & s) != 0;
 #pragma unroll
     for (int k = 0; k < s; ++k) {
@@ -302,15 +329,18 @@ __device__ __forceinline__ float transpose_reduce32(float (&v)[32], int lane) {
       v[k] = keep + __shfl_xor_sync(0xffffffffu, send, s);
     }
   }
-  return v[0];
+  float r = v[0];
+#pragma unroll
+  for (int s = G; s < 32; s <<= 1) r += __shfl_xor_sync(0xffffffffu, r, s);
+  return r;
 }
 
 template <int KID>
-__global__ void __launch_bounds__(kSymThreads, 8) pp_sym_kernel(PlanView v, const int2 *pairs,
-                                                             const int32_t *off, const float *wsf,
-                                                             float *part) {
+__global__ void __launch_bounds__(kSymThreads, CSFMM_SYM_MINB) pp_sym_kernel(
+    PlanView v, const int2 *pairs, const int32_t *off, const float *wsf, float *part) {
+  constexpr int QP = kSymQP, G = kSymGroup;
   __shared__ ulonglong2 sA[kSymCols], sB[kSymCols];
-  __shared__ float colacc[kSymThreads / 32][kSymCols];
+  __shared__ float colacc[kSymWarps][kSymCols];
   const int2 pr = pairs[blockIdx.x];
   const int T = pr.x, S = pr.y;
   const int tb = v.cbegin[T], te = v.cend[T], sb = v.cbegin[S], se = v.cend[S];
@@ -335,16 +365,17 @@ __global__ void __launch_bounds__(kSymThreads, 8) pp_sym_kernel(PlanView v, cons
     WS = (double)b2.x + (double)b2.y;
   }
   for (int r0 = 0; r0 < nT; r0 += kSymRows) {
-    // rows of this lane: r0 + warp*128 + lane + 32k, k = 0..3 (pairs (0,1), (2,3))
-    f2x tx[2], ty[2], tz[2], wr[2], rhi[2], rlo[2];
-    bool act[4];
+    // rows of this lane: r0 + warp*kSymRowsPerWarp + lane + 32k, k = 0..2QP-1,
+    // packed as pairs (2q, 2q+1)
+    f2x tx[QP], ty[QP], tz[QP], wr[QP], rhi[QP], rlo[QP];
+    bool act[2 * QP];
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < QP; ++q) {
       float x[2], y[2], z[2], w[2];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int k = 2 * q + h;
-        const int i = r0 + warp * 128 + lane + 32 * k;
+        const int i = r0 + warp * kSymRowsPerWarp + lane + 32 * k;
         act[k] = i < nT;
         const int ii = tb + (act[k] ? i : 0);
         const float4 o = v.off32[ii];
@@ -374,15 +405,17 @@ __global__ void __launch_bounds__(kSymThreads, 8) pp_sym_kernel(PlanView v, cons
         sB[t] = make_ulonglong2(f2_pack(z, z), f2_pack(w, w));
       }
       __syncthreads();
-      const int ng = (nj + 31) / 32;
+      const int ng = (nj + G - 1) / G;
       for (int g = 0; g < ng; ++g) {
-        f2x colv[32], racc[2] = {0ull, 0ull};
+        f2x colv[G], racc[QP];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const ulonglong2 A = sA[g * 32 + j], B = sB[g * 32 + j];
+        for (int q = 0; q < QP; ++q) racc[q] = 0ull;
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+          const ulonglong2 A = sA[g * G + j], B = sB[g * G + j];
           colv[j] = 0ull;
 #pragma unroll
-          for (int q = 0; q < 2; ++q) {
+          for (int q = 0; q < QP; ++q) {
             const f2x rx = f2_sub(tx[q], A.x), ry = f2_sub(ty[q], A.y), rz = f2_sub(tz[q], B.x);
             f2x d2 = f2_mul(rx, rx);
             d2 = f2_fma(ry, ry, d2);
@@ -395,32 +428,33 @@ __global__ void __launch_bounds__(kSymThreads, 8) pp_sym_kernel(PlanView v, cons
           }
         }
 #pragma unroll
-        for (int q = 0; q < 2; ++q) two_sum_fold(rhi[q], rlo[q], racc[q]);
-        float cv[32];
+        for (int q = 0; q < QP; ++q) two_sum_fold(rhi[q], rlo[q], racc[q]);
+        float cv[G];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
+        for (int j = 0; j < G; ++j) {
           float lo, hi;
           f2_unpack(colv[j], lo, hi);
           cv[j] = lo + hi;
         }
-        colacc[warp][g * 32 + lane] = transpose_reduce32(cv, lane);
+        const float red = transpose_reduce<G>(cv, lane);
+        if (lane < G) colacc[warp][g * G + lane] = red;
       }
       __syncthreads();
       for (int t = threadIdx.x; t < nj; t += kSymThreads) {
         float val = 0.f;
 #pragma unroll
-        for (int u = 0; u < kSymThreads / 32; ++u) val += colacc[u][t];
+        for (int u = 0; u < kSymWarps; ++u) val += colacc[u][t];
         if (r0 == 0) colpart[c0 + t] = val;
         else colpart[c0 + t] += val;
       }
     }
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < QP; ++q) {
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int k = 2 * q + h;
         if (!act[k]) continue;
-        const int i = r0 + warp * 128 + lane + 32 * k;
+        const int i = r0 + warp * kSymRowsPerWarp + lane + 32 * k;
         double val = f2_total(rhi[q], rlo[q], h);
         if constexpr (KID == CSFMM_KERNEL_LAPLACE) val -= (1 + 2 * lse) * WS;
         rowpart[i] = (float)val;
@@ -760,205 +794,17 @@ void launch_far_kid(const PlanView &v, int ncells, const float *wsf, const float
 }
 
 
-// ---------------------------------------------------------------------------
-// Several right-hand sides (NR = 8 or 16, scalar kernels): the kernel factor
-// of a (target, source) pair is computed once and applied to every
-// right-hand side with packed FMAs over pairs of right-hand sides.  Used for
-// both the near field (targets = particles of a leaf, PP and PC sources) and
-// the far field (targets = proxies of a cell, CP and CC sources).
-// ---------------------------------------------------------------------------
-template <int KID, int NT, int NR, bool SELF>
-__device__ __forceinline__ void eval_multi(const float4 *__restrict__ sp,
-                                           const ulonglong2 *__restrict__ sw4, int j,
-                                           const float (&tx)[NT], const float (&ty)[NT],
-                                           const float (&tz)[NT], const int (&self)[NT],
-                                           f2x (&acc)[NT][NR / 2]) {
-  const float4 s = sp[j];
-  f2x w2[NR / 2];
-#pragma unroll
-  for (int q = 0; q < NR / 4; ++q) {
-    const ulonglong2 u = sw4[j * (NR / 4) + q];
-    w2[2 * q] = u.x;
-    w2[2 * q + 1] = u.y;
-  }
-#pragma unroll
-  for (int k = 0; k < NT; ++k) {
-    const float rx = tx[k] - s.x, ry = ty[k] - s.y, rz = tz[k] - s.z;
-    const float d2 = fmaf(rz, rz, fmaf(ry, ry, rx * rx));
-    float f = kfactor<KID>(d2);
-    if constexpr (SELF) f = (j == self[k]) ? 0.0f : f;
-    const f2x ff = f2_pack(f, f);
-#pragma unroll
-    for (int q = 0; q < NR / 2; ++q) acc[k][q] = f2_fma(w2[q], ff, acc[k][q]);
-  }
-}
-
-template <int KID, int NT, int NR, bool SELF>
-__device__ __forceinline__ void tile_sum_multi(const float4 *__restrict__ sp,
-                                               const ulonglong2 *__restrict__ sw4, int nj,
-                                               const float (&tx)[NT], const float (&ty)[NT],
-                                               const float (&tz)[NT], const int (&self)[NT],
-                                               f2x (&hi)[NT][NR / 2], f2x (&lo)[NT][NR / 2]) {
-  for (int jc = 0; jc < nj; jc += kChunk) {
-    f2x acc[NT][NR / 2];
-#pragma unroll
-    for (int k = 0; k < NT; ++k)
-#pragma unroll
-      for (int q = 0; q < NR / 2; ++q) acc[k][q] = 0ull;
-    if (jc + kChunk <= nj) {  // full chunk: constant trip count
-#pragma unroll 2
-      for (int jj = 0; jj < kChunk; ++jj)
-        eval_multi<KID, NT, NR, SELF>(sp, sw4, jc + jj, tx, ty, tz, self, acc);
-    } else {
-#pragma unroll 2
-      for (int j = jc; j < nj; ++j) eval_multi<KID, NT, NR, SELF>(sp, sw4, j, tx, ty, tz, self, acc);
-    }
-#pragma unroll
-    for (int k = 0; k < NT; ++k)
-#pragma unroll
-      for (int q = 0; q < NR / 2; ++q) two_sum_fold(hi[k][q], lo[k][q], acc[k][q]);
-  }
-}
-
-// FAR = false: near field of leaf leaves[blockIdx.x] into phi (FP64);
-// FAR = true: far field of cell blockIdx.x into psi (FP64).  NT targets per
-// thread, strided by blockDim; every target keeps FP32 (hi, lo) running totals
-// per right-hand side over the whole list and writes FP64 once.
-// Targets per thread and threads per block of the multi-right-hand-side
-// kernel.  The kernel is bound by shared-memory loads (one coordinate and four
-// weight vectors per source); two targets per thread halve them per target
-// (measured at 16 RHS, N = 1.57M Poisson: near field 20.5 ms with one target,
-// 16.2 ms with two at 128 threads, 17.4 ms with two at 64 threads).
-#ifndef CSFMM_MULTI_NT
-#define CSFMM_MULTI_NT 2
-#endif
-#ifndef CSFMM_MULTI_THREADS
-#define CSFMM_MULTI_THREADS 128
-#endif
-
+// Multi-right-hand-side interactions (multi32.cuh): one block per target
+// leaf (near field) or cell (far field).
 template <int KID, int NR, bool FAR>
 __global__ void __launch_bounds__(CSFMM_MULTI_THREADS) multi32_kernel(
     PlanView v, const int32_t *leaves, const float *wsf, const float *wbar, int ldr, int r0,
     double *phi, double *psi) {
-  constexpr int NT = CSFMM_MULTI_NT;
-  // one partial weight sum per warp; every launch uses at most
-  // CSFMM_MULTI_THREADS threads
-  static_assert(CSFMM_MULTI_THREADS % 32 == 0 && CSFMM_MULTI_THREADS <= 1024, "block size");
-  __shared__ float4 sp[kTile];
-  __shared__ ulonglong2 sw4[(NR / 4) * kTile];
+  __shared__ float4 sp[kMultiTile];
+  __shared__ ulonglong2 sw4[(NR / 4) * kMultiTile];
   const int c = FAR ? (int)blockIdx.x : leaves[blockIdx.x];
-  const int P = v.P, nth = blockDim.x;
-  const int tb = FAR ? 0 : v.cbegin[c];
-  const int te = FAR ? P : v.cend[c];
-  const double cTx = v.ccentre[3 * c], cTy = v.ccentre[3 * c + 1], cTz = v.ccentre[3 * c + 2];
-  const int64_t po = (int64_t)c * 3 * P;
-  float *swf = reinterpret_cast<float *>(sw4);
-  for (int i0 = tb; i0 < te; i0 += nth * NT) {
-    float ox[NT], oy[NT], oz[NT];
-    // running totals over all list entries, FP32 (hi, lo) pairs per pair of
-    // right-hand sides; the log kernel holds sum w (log2 d2 - 1)
-    f2x hi[NT][NR / 2], lo[NT][NR / 2];
-#pragma unroll
-    for (int k = 0; k < NT; ++k) {
-      const int i = i0 + threadIdx.x + k * nth;
-      const int ii = i < te ? i : tb;
-      if (FAR) {
-        ox[k] = v.proxy32[po + ii]; oy[k] = v.proxy32[po + P + ii]; oz[k] = v.proxy32[po + 2 * P + ii];
-      } else {
-        const float4 o = v.off32[ii];
-        ox[k] = o.x; oy[k] = o.y; oz[k] = o.z;
-      }
-#pragma unroll
-      for (int q = 0; q < NR / 2; ++q) hi[k][q] = lo[k][q] = 0ull;
-    }
-    for (int pass = 0; pass < 2; ++pass) {
-      const int type = FAR ? (pass == 0 ? CSFMM_LIST_CP : CSFMM_LIST_CC)
-                           : (pass == 0 ? CSFMM_LIST_PP : CSFMM_LIST_PC);
-      const bool particles = type == CSFMM_LIST_PP || type == CSFMM_LIST_CP;
-      const int e0 = v.loff[type][c], e1 = v.loff[type][c + 1];
-      for (int ee = e0; ee < e1; ++ee) {
-        const int s = v.lsrc[type][ee];
-        const float dcx = (float)(cTx - v.ccentre[3 * s]);
-        const float dcy = (float)(cTy - v.ccentre[3 * s + 1]);
-        const float dcz = (float)(cTz - v.ccentre[3 * s + 2]);
-        float tx[NT], ty[NT], tz[NT];
-#pragma unroll
-        for (int k = 0; k < NT; ++k) {
-          tx[k] = ox[k] + dcx;
-          ty[k] = oy[k] + dcy;
-          tz[k] = oz[k] + dcz;
-        }
-        const int sb = particles ? v.cbegin[s] : 0;
-        const int nsrc = particles ? v.cend[s] - sb : P;
-        const bool self_tile = !FAR && type == CSFMM_LIST_PP && s == c;
-        if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
-          // -(1/4pi) sum w ln(d2/2) = -(ln2/4pi) (sum w log2 d2 - sum w); the
-          // target's own weight is not part of the sum over the self leaf
-#pragma unroll
-          for (int q = 0; q < NR / 2; ++q) {
-            const float2 W0 = weight_total(v, s, r0 + 2 * q, particles ? 0 : 1);
-            const float2 W1 = weight_total(v, s, r0 + 2 * q + 1, particles ? 0 : 1);
-#pragma unroll
-            for (int k = 0; k < NT; ++k) {
-              two_sum_fold(hi[k][q], lo[k][q], f2_pack(-W0.x, -W1.x));
-              lo[k][q] = f2_add(lo[k][q], f2_pack(-W0.y, -W1.y));
-              const int i = i0 + threadIdx.x + k * nth;
-              if (self_tile && i < te)
-                two_sum_fold(hi[k][q], lo[k][q], f2_pack(wsf[(int64_t)(r0 + 2 * q) * v.N + i],
-                                                         wsf[(int64_t)(r0 + 2 * q + 1) * v.N + i]));
-            }
-          }
-        }
-        for (int j0 = 0; j0 < nsrc; j0 += kTile) {
-          const int nj = min(kTile, nsrc - j0);
-          __syncthreads();
-          for (int t = threadIdx.x; t < nj; t += nth) {
-            float wv[NR];
-            if (particles) {
-              const int j = sb + j0 + t;
-              sp[t] = v.off32[j];
-#pragma unroll
-              for (int q = 0; q < NR; ++q) wv[q] = wsf[(int64_t)(r0 + q) * v.N + j];
-            } else {
-              const int64_t so = (int64_t)s * 3 * P;
-              const int k = j0 + t;
-              sp[t] = make_float4(v.proxy32[so + k], v.proxy32[so + P + k], v.proxy32[so + 2 * P + k], 0.f);
-#pragma unroll
-              for (int q = 0; q < NR; ++q) wv[q] = wbar[((int64_t)s * ldr + r0 + q) * P + k];
-            }
-#pragma unroll
-            for (int q = 0; q < NR / 4; ++q)
-              reinterpret_cast<float4 *>(swf)[t * (NR / 4) + q] =
-                  make_float4(wv[4 * q], wv[4 * q + 1], wv[4 * q + 2], wv[4 * q + 3]);
-          }
-          __syncthreads();
-          int self[NT];
-#pragma unroll
-          for (int k = 0; k < NT; ++k) self[k] = (i0 + (int)threadIdx.x + k * nth) - (sb + j0);
-          if (self_tile)
-            tile_sum_multi<KID, NT, NR, true>(sp, sw4, nj, tx, ty, tz, self, hi, lo);
-          else
-            tile_sum_multi<KID, NT, NR, false>(sp, sw4, nj, tx, ty, tz, self, hi, lo);
-        }
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < NT; ++k) {
-      const int i = i0 + threadIdx.x + k * nth;
-      if (i >= te) continue;
-#pragma unroll
-      for (int q = 0; q < NR / 2; ++q)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int qq = 2 * q + h;
-          double val = f2_total(hi[k][q], lo[k][q], h);
-          if constexpr (KID == CSFMM_KERNEL_LAPLACE) val *= -(0.69314718055994530942 * kInv4Pi);
-          if constexpr (KID == CSFMM_KERNEL_BIHARMONIC) val *= kInv4Pi;
-          if (FAR) psi[((int64_t)c * ldr + r0 + qq) * P + i] = val;
-          else phi[(int64_t)(r0 + qq) * v.N + i] = val;
-        }
-    }
-  }
+  multi32_item<KID, NR, FAR>(v, c, wsf, wbar, ldr, r0, phi, psi, sp, sw4, threadIdx.x, blockDim.x,
+                             0);
 }
 
 template <int KID, int NR>

@@ -93,7 +93,12 @@ extern "C" csfmm_status csfmm_evaluate_static(csfmm_plan plan, const double *wei
   const bool sym = pl.precision != CSFMM_FP64 && nrhs == 1 && pl.n_sym_pairs > 0 &&
                    pl.kernel_id != CSFMM_KERNEL_BIOT_SAVART;
   const size_t b_sym = sym ? round256((size_t)pl.sym_part_len * sizeof(float)) : 0;
-  const size_t need = b_ws + b_wbar + b_psi + b_phi + b_wsf + b_wtot + b_sym;
+  // FP32 bulk, scalar kernels: the work and dependency counters of the
+  // persistent launch (several right-hand sides)
+  const size_t b_ctr = pl.precision != CSFMM_FP64 && pl.kernel_id != CSFMM_KERNEL_BIOT_SAVART
+                           ? round256(persistent_counter_ints(pl) * sizeof(int))
+                           : 0;
+  const size_t need = b_ws + b_wbar + b_psi + b_phi + b_wsf + b_wtot + b_sym + b_ctr;
   if (need > (size_t)CSFMM_STATIC_SCRATCH_BYTES) {
     set_error("this evaluation needs %zu bytes of scratch; the static scratch holds %zu bytes "
               "(use csfmm_evaluate, or fewer right-hand sides)",
@@ -104,7 +109,8 @@ extern "C" csfmm_status csfmm_evaluate_static(csfmm_plan plan, const double *wei
   csfmm_status s = scratch_address(device, &base);
   if (s != CSFMM_OK) return s;
   // Every scratch buffer is fully written before it is read (gather, P2M/M2M,
-  // far, the symmetric pass, near), so nothing needs clearing between calls.
+  // far, the symmetric pass, near; the persistent launch clears its counters
+  // itself), so nothing needs clearing between calls.
   // W has no side stream: the passes run in order on `stream`.
   Workspace W;
   W.graphs_ok = false;  // W lives only for this call
@@ -119,5 +125,7 @@ extern "C" csfmm_status csfmm_evaluate_static(csfmm_plan plan, const double *wei
   if (b_wtot) W.wtot = reinterpret_cast<float2 *>(base + b_ws + b_wbar + b_psi + b_phi + b_wsf);
   if (b_sym)
     W.sym_part = reinterpret_cast<float *>(base + b_ws + b_wbar + b_psi + b_phi + b_wsf + b_wtot);
+  if (b_ctr)
+    W.ctr = reinterpret_cast<int *>(base + b_ws + b_wbar + b_psi + b_phi + b_wsf + b_wtot + b_sym);
   return evaluate_impl(pl, W, weights, nrhs, out, (cudaStream_t)stream);
 }
