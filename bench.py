@@ -621,7 +621,9 @@ def run_serving(args, sample=None):
     n_req = sample or args.serve_requests
     ms = (64, 128, 256, 512, 1024)
     grids = S.DeviceGrids(ms, torch.device("cuda", torch.cuda.current_device()))
-    server = Cs.Server(budget_bytes=int(args.serve_budget_gb * (1 << 30)), slots=args.serve_slots)
+    policy = Cs.SERVE_FIFO if args.serve_policy == "fifo" else Cs.SERVE_CHEAPEST_FIRST
+    server = Cs.Server(budget_bytes=int(args.serve_budget_gb * (1 << 30)), slots=args.serve_slots,
+                       policy=policy, age_ms=args.serve_age_ms)
     warm = I.serving_requests(120, rate_hz=1e6, seed=I.MASTER_SEED + 50)
     S.run_stream(server, grids, warm, rate_hz=None)
     burst = I.serving_requests(min(200, n_req), rate_hz=1e6, seed=I.MASTER_SEED + 51)
@@ -635,6 +637,7 @@ def run_serving(args, sample=None):
     summ.update({"arrival_rate_hz": rate, "saturation_requests_per_s": sat["requests_per_s"],
                  "saturation_targets_per_s": sat["targets_per_s"], "slots": args.serve_slots,
                  "budget_gb": args.serve_budget_gb, "plans_built": st["plans_built"],
+                 "policy": args.serve_policy, "age_ms": args.serve_age_ms,
                  "plans_evicted": st["plans_evicted"],
                  "peak_bytes_held_gb": st["peak_bytes_held"] / 2 ** 30,
                  "max_in_flight": st["max_in_flight"]})
@@ -1091,6 +1094,8 @@ def main():
     ap.add_argument("--serve-sample", type=int, default=2000,
                     help="requests of the serving stream measured in the default line (0: none)")
     ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-policy", default="cheapest", choices=["cheapest", "fifo"])
+    ap.add_argument("--serve-age-ms", type=float, default=250.0)
     ap.add_argument("--serve-budget-gb", type=float, default=96.0)
     args = ap.parse_args()
     if args.warmup < 3:

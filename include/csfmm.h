@@ -96,8 +96,24 @@ typedef struct {
                      persistent launch whose blocks draw work from a device counter and wait
                      (bounded in time) only for the downward pass's dependencies; the result
                      equals the per-phase launches bit for bit.  1: per-phase launches */
-  int reserved[2];
+  int schedule;   /* FP32 bulk: OR of CSFMM_SCHED_* bits choosing tile shapes and launch
+                     schedule (0 = the defaults); csfmm_autotune searches them */
+  int reserved[1];
 } csfmm_options;
+
+/* Bits of csfmm_options.schedule (FP32 bulk).  The first three set the tile
+ * shape of the per-phase multi-right-hand-side kernels (nrhs of 8 or more
+ * without the persistent launch); CHUNK_16 changes the order of the FP32
+ * sums and hence the rounding, the others only the work layout. */
+enum {
+  CSFMM_SCHED_NEAR_64_THREADS = 1,  /* near field: 64 threads per leaf instead of 128 */
+  CSFMM_SCHED_ONE_TARGET = 2,       /* one target per thread instead of two */
+  CSFMM_SCHED_CHUNK_16 = 4,         /* tile sums in FP32 chunks of 16 sources instead of 32 */
+  CSFMM_SCHED_NO_SYMMETRIC = 8,     /* one right-hand side: evaluate every PP entry directly
+                                       instead of mirrored leaf pairs once for both directions */
+  CSFMM_SCHED_NO_OVERLAP = 16       /* run every pass in order on the caller's stream instead
+                                       of the upward pass, far field and L2L on a side stream */
+};
 
 typedef struct csfmm_plan_s *csfmm_plan;
 
@@ -273,16 +289,22 @@ csfmm_status csfmm_direct_targets(const double *points, int64_t N, int kernel_id
                                   const double *weights, int nrhs, const int64_t *targets,
                                   int64_t ntargets, double *out, int precision, void *stream);
 
-/* Autotuner (no counterpart in the paper).  Builds plans of the given point
- * set with maximum leaf sizes N0 in {n^2, 2n^2, 3n^2, 4n^2, 6n^2, 8n^2} (at
- * least 8) and, for several right-hand sides in the FP32-bulk form, right-hand-
- * side chunks of 16, 8 and 4; times three evaluations of each with CUDA events
- * and measures the relative l2 error of the first right-hand side against an
- * FP64 direct sum on up to 256 fixed sampled targets.  It returns the fastest
- * candidate whose error is at most err_factor times the error of the paper's
- * default N0 = 4 n^2 (Sec. 10).  With a cache path the choice is read from /
+/* Autotuner (no counterpart in the paper).  Times real evaluations of the
+ * caller's point set (three each after a warm-up, CUDA events) and measures
+ * the relative l2 error of the first right-hand side against an FP64 direct
+ * sum on up to 256 fixed sampled targets.  Stage 1: maximum leaf sizes N0 in
+ * {n^2, 2n^2, 3n^2, 4n^2, 6n^2, 8n^2} (at least 8) with the default schedule.
+ * Stage 2, at the best N0 of stage 1: the launch schedule and tile shapes --
+ * for the FP32-bulk form with 8 or more right-hand sides (scalar kernels) the
+ * persistent launch with right-hand-side chunks of 16 and 8, and the
+ * per-phase launches with chunks of 16, 8 and 4 and every tile shape of
+ * CSFMM_SCHED_NEAR_64_THREADS | CSFMM_SCHED_ONE_TARGET | CSFMM_SCHED_CHUNK_16;
+ * otherwise CSFMM_SCHED_NO_SYMMETRIC (FP32 bulk, one right-hand side) and
+ * CSFMM_SCHED_NO_OVERLAP.  It returns the fastest candidate whose error is
+ * at most err_factor times the error of the default (N0 = 4 n^2, Sec. 10,
+ * and default options).  With a cache path the choice is read from /
  * appended to that text file, keyed by device name, kernel, degree, theta,
- * precision, nrhs and N.
+ * precision, nrhs and N (csfmm_tune_cache_read).
  *   points device [N][3]; weights device [nrhs][N] (1 <= nrhs <= 64)
  * Synchronous.  Errors: INVALID_ARG, OUT_OF_MEMORY, CUDA. */
 typedef struct {
@@ -290,14 +312,29 @@ typedef struct {
   int rhs_chunk;         /* chosen csfmm_options.rhs_chunk */
   double ms_per_eval;    /* its evaluation time */
   double rel_err;        /* its error against the FP64 direct sum on the samples */
-  double default_ms;     /* the same for N0 = 4 n^2, rhs_chunk 0 */
+  double default_ms;     /* the same for N0 = 4 n^2 and default options */
   double default_rel_err;
   int candidates;        /* candidates timed (0 when read from the cache) */
   int from_cache;
+  int no_persistent;     /* chosen csfmm_options.no_persistent */
+  int schedule;          /* chosen csfmm_options.schedule */
 } csfmm_tune_result;
 csfmm_status csfmm_autotune(const double *points, int64_t N, int kernel_id, int degree,
                             double theta, const double *weights, int nrhs, int precision,
                             const char *cache_path, double err_factor, csfmm_tune_result *out);
+
+/* Reads a choice from an autotuner cache file (host only, no device work):
+ * the last valid line for `key`.  A line is
+ *   v2 <key> <max_leaf> <rhs_chunk> <no_persistent> <schedule> <ms_per_eval>
+ *      <rel_err> <default_ms> <default_rel_err>
+ * with key "<device name>|k<kernel>|n<degree>|t<theta>|p<precision>|r<nrhs>|N<N>"
+ * (spaces in the device name replaced by '_').  Lines of another format
+ * (stale caches of earlier versions), with values out of range (leaf < 1,
+ * chunk not 0/4/8/16, flags not 0/1, schedule bits outside 0..31, times or
+ * errors negative or not finite) or cut short are ignored.
+ * Returns OK with *out filled (from_cache = 1), or INVALID_ARG (NULL
+ * argument; no valid line for key, message "not found"). */
+csfmm_status csfmm_tune_cache_read(const char *path, const char *key, csfmm_tune_result *out);
 
 /* Plan statistics (host struct). */
 csfmm_status csfmm_plan_stats(csfmm_plan plan, csfmm_stats *stats);
@@ -346,11 +383,12 @@ csfmm_status csfmm_plan_phase_times(csfmm_plan plan, double *ms, int64_t *calls)
  * A request names a point set by the caller's key (plan_key, e.g. the grid
  * size) plus its method parameters; plans are cached by (plan_key, kernel_id,
  * degree, theta, max_leaf, precision) and built from `points` the first time.
- * Admission is first-come first-served: the head request starts when a slot
- * is free and the memory it needs (its plan if not cached, plus a workspace
- * for up to CSFMM_SERVER_MAX_NRHS right-hand sides if none is idle) fits in
- * hbm_budget_bytes next to what is held; idle cached plans are evicted (least
- * recently used) to make room.  Plans are built with use_graphs = 1.
+ * A request starts when a slot is free and the memory it needs (its plan if
+ * not cached, plus a workspace for up to CSFMM_SERVER_MAX_NRHS right-hand
+ * sides if none is idle) fits in hbm_budget_bytes next to what is held; idle
+ * cached plans are evicted (least recently used) to make room.  Which pending
+ * request starts next is set by csfmm_server_set_policy.  Plans are built
+ * with use_graphs = 1.
  * ------------------------------------------------------------------------ */
 #define CSFMM_SERVER_MAX_NRHS 8
 typedef struct csfmm_server_s *csfmm_server;
@@ -386,6 +424,19 @@ typedef struct {
  * slots (1..64) and a device-memory budget for plans and workspaces.
  * Errors: INVALID_ARG, CUDA. */
 csfmm_status csfmm_server_create(int64_t hbm_budget_bytes, int slots, csfmm_server *out);
+/* Admission order.  CSFMM_SERVE_FIFO: first come first served (the oldest
+ * pending request starts, or nothing does while it does not fit).
+ * CSFMM_SERVE_CHEAPEST_FIRST (the default): the pending request with the
+ * smallest estimated cost N (4 + nrhs) (n+1)^2 starts first, except that a
+ * request pending for more than age_ms milliseconds (default 250) goes
+ * first whatever its cost, and requests of at least 2^20 points occupy at
+ * most half of the slots (at least one); a smaller request runs on a
+ * high-priority stream of its slot with all its passes on that stream (its
+ * plan is built with CSFMM_SCHED_NO_OVERLAP), so its kernels are scheduled
+ * ahead of waiting blocks of large requests.  Results do not depend on the
+ * policy.  Errors: INVALID_ARG (NULL server, unknown policy, age_ms <= 0). */
+enum { CSFMM_SERVE_FIFO = 0, CSFMM_SERVE_CHEAPEST_FIRST = 1 };
+csfmm_status csfmm_server_set_policy(csfmm_server s, int policy, double age_ms);
 /* Queues a request (copied; the buffers it points to must stay valid until
  * it completes) and returns its id.  Never blocks.  Errors: INVALID_ARG;
  * OUT_OF_MEMORY if the request alone can never fit the budget. */

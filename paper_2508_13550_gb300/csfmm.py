@@ -56,14 +56,15 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("max_nrhs", ctypes.c_int),
                 ("use_graphs", ctypes.c_int), ("rhs_chunk", ctypes.c_int),
                 ("shrink", ctypes.c_int), ("no_persistent", ctypes.c_int),
-                ("reserved", ctypes.c_int * 2)]
+                ("schedule", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
 
 
 class TuneResult(ctypes.Structure):
     _fields_ = [("max_leaf", ctypes.c_int), ("rhs_chunk", ctypes.c_int),
                 ("ms_per_eval", ctypes.c_double), ("rel_err", ctypes.c_double),
                 ("default_ms", ctypes.c_double), ("default_rel_err", ctypes.c_double),
-                ("candidates", ctypes.c_int), ("from_cache", ctypes.c_int)]
+                ("candidates", ctypes.c_int), ("from_cache", ctypes.c_int),
+                ("no_persistent", ctypes.c_int), ("schedule", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -114,6 +115,9 @@ class ServerStats(ctypes.Structure):
 
 
 SERVER_MAX_NRHS = 8
+SERVE_FIFO, SERVE_CHEAPEST_FIRST = 0, 1
+SCHED_NEAR_64_THREADS, SCHED_ONE_TARGET, SCHED_CHUNK_16 = 1, 2, 4
+SCHED_NO_SYMMETRIC, SCHED_NO_OVERLAP = 8, 16
 
 _VP, _I64, _I32, _D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
 _SIGS = {
@@ -132,6 +136,7 @@ _SIGS = {
     "csfmm_direct_targets": [_VP, _I64, ctypes.c_int, _VP, ctypes.c_int, _VP, _I64, _VP,
                              ctypes.c_int, _VP],
     "csfmm_plan_stats": [_VP, ctypes.POINTER(Stats)],
+    "csfmm_tune_cache_read": [ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(TuneResult)],
     "csfmm_bve_step": [_VP, _VP, _VP, _I64, _D, _D, ctypes.c_int, _D, ctypes.c_int, ctypes.c_int,
                        _VP, _VP, _VP],
     "csfmm_bve_step_remeshed": [_VP, _VP, _VP, _VP, _VP, _D, _D, ctypes.c_int, _D, ctypes.c_int,
@@ -152,6 +157,7 @@ _SIGS = {
     "csfmm_plan_test_wait": [_VP, ctypes.c_int, ctypes.c_double],
     "csfmm_plan_destroy": [_VP],
     "csfmm_server_create": [_I64, ctypes.c_int, ctypes.POINTER(_VP)],
+    "csfmm_server_set_policy": [_VP, ctypes.c_int, _D],
     "csfmm_server_submit": [_VP, ctypes.POINTER(Request), ctypes.POINTER(_I64)],
     "csfmm_server_poll": [_VP, _I64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(RequestTiming)],
     "csfmm_server_wait": [_VP, _I64, ctypes.POINTER(RequestTiming)],
@@ -234,11 +240,12 @@ class Plan:
 
 def plan_create(points, kernel_id: int, degree: int, theta: float, max_leaf: int,
                 precision: int = FP64, max_nrhs: int = 16, use_graphs: int = 0, rhs_chunk: int = 0,
-                shrink: bool = False, stream=None, no_persistent: bool = False):
+                shrink: bool = False, stream=None, no_persistent: bool = False,
+                schedule: int = 0):
     import torch
     lib = load()
     opt = Options(precision, max_nrhs, use_graphs, rhs_chunk, int(bool(shrink)),
-                  int(bool(no_persistent)))
+                  int(bool(no_persistent)), int(schedule))
     h = ctypes.c_void_p()
     N = points.shape[0]
     rc = lib.csfmm_plan_create(_dev(points, torch.float64), N, kernel_id, degree, theta,
@@ -250,12 +257,12 @@ def plan_create(points, kernel_id: int, degree: int, theta: float, max_leaf: int
 def plan_create_targets(sources, targets, kernel_id: int, degree: int, theta: float,
                         max_leaf: int, precision: int = FP64, max_nrhs: int = 16,
                         use_graphs: int = 0, rhs_chunk: int = 0, shrink: bool = False,
-                        stream=None, no_persistent: bool = False):
+                        stream=None, no_persistent: bool = False, schedule: int = 0):
     """csfmm_plan_create_targets: a plan whose evaluations take weights at the
     sources [nrhs, Ns] and return the sum at separate targets [nrhs, Nt, dim]."""
     import torch
     opt = Options(precision, max_nrhs, use_graphs, rhs_chunk, int(bool(shrink)),
-                  int(bool(no_persistent)))
+                  int(bool(no_persistent)), int(schedule))
     h = ctypes.c_void_p()
     Ns, Nt = sources.shape[0], targets.shape[0]
     _check(load().csfmm_plan_create_targets(_dev(sources, torch.float64), Ns,
@@ -461,8 +468,8 @@ def bve_step_remeshed(g: RemeshGrid, zeta, area, dt: float, omega: float, degree
 
 def autotune(points, kernel_id: int, degree: int, theta: float, weights, precision: int = FP64,
              cache_path: str | None = None, err_factor: float = 2.0) -> dict:
-    """csfmm_autotune: fastest leaf size / right-hand-side chunk within
-    err_factor of the default's error (see include/csfmm.h)."""
+    """csfmm_autotune: fastest leaf size, then launch schedule and tile
+    shapes, within err_factor of the default's error (see include/csfmm.h)."""
     import torch
     w = weights if weights.dim() == 2 else weights.unsqueeze(0)
     res = TuneResult()
@@ -470,6 +477,16 @@ def autotune(points, kernel_id: int, degree: int, theta: float, weights, precisi
                                  theta, _dev(w, torch.float64), w.shape[0], precision,
                                  cache_path.encode() if cache_path else None, err_factor,
                                  ctypes.byref(res)))
+    return res.as_dict()
+
+
+def tune_cache_read(path: str, key: str) -> dict | None:
+    """csfmm_tune_cache_read: the cached choice for key, or None."""
+    res = TuneResult()
+    rc = load().csfmm_tune_cache_read(path.encode(), key.encode(), ctypes.byref(res))
+    if rc == 1 and "not found" in load().csfmm_last_error().decode():
+        return None
+    _check(rc)
     return res.as_dict()
 
 
@@ -554,9 +571,16 @@ class Server:
     """csfmm_server: continuous batching over resident plans (one scheduler
     thread in the library; this class only marshals arguments)."""
 
-    def __init__(self, budget_bytes: int, slots: int):
+    def __init__(self, budget_bytes: int, slots: int, policy: int | None = None,
+                 age_ms: float = 250.0):
         self.handle = ctypes.c_void_p()
         _check(load().csfmm_server_create(int(budget_bytes), int(slots), ctypes.byref(self.handle)))
+        if policy is not None:
+            self.set_policy(policy, age_ms)
+
+    def set_policy(self, policy: int, age_ms: float = 250.0):
+        """csfmm_server_set_policy: SERVE_FIFO or SERVE_CHEAPEST_FIRST."""
+        _check(load().csfmm_server_set_policy(self.handle, int(policy), float(age_ms)))
 
     def submit(self, points, plan_key, kernel_id, degree, theta, max_leaf, precision, weights,
                out):

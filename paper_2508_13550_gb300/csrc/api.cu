@@ -165,6 +165,12 @@ csfmm_status csfmm_plan_create(const double *points, int64_t N, int kernel_id, i
   pl.use_graphs = o.use_graphs;
   pl.shrink = o.shrink != 0;
   pl.no_persistent = o.no_persistent != 0;
+  if (o.schedule < 0 || o.schedule > 31) {
+    set_error("schedule must be an OR of CSFMM_SCHED_* bits (got %d)", o.schedule);
+    delete h;
+    return CSFMM_ERR_INVALID_ARG;
+  }
+  pl.schedule = o.schedule;
   pl.rhs_chunk = o.rhs_chunk == 0 ? 16 : o.rhs_chunk;
   if (pl.rhs_chunk != 16 && pl.rhs_chunk != 8 && pl.rhs_chunk != 4) {
     set_error("rhs_chunk must be 0, 4, 8 or 16 (got %d)", o.rhs_chunk);

@@ -1,13 +1,17 @@
-// autotune.cu -- csfmm_autotune: picks the maximum leaf size N0 and, for the
-// FP32-bulk multi-right-hand-side kernels, the right-hand-side chunk width,
+// autotune.cu -- csfmm_autotune: picks the maximum leaf size N0, then the
+// launch schedule and tile shapes (persistent or per-phase launches,
+// right-hand-side chunk, threads and targets per thread of the multi-right-
+// hand-side kernels, FP32 chunk width, symmetric pass, side-stream overlap),
 // by timing real evaluations of the caller's point set.
 //
-// The leaf size changes the tree and hence the approximation, so a candidate
-// is accepted only if its error against an FP64 direct sum on fixed sampled
-// targets stays within err_factor of the error of the paper's default
-// N0 = 4 n^2; the chunk width changes only the order of FP32 sums.
+// The leaf size changes the tree and hence the approximation, and the FP32
+// chunk width the rounding, so a candidate is accepted only if its error
+// against an FP64 direct sum on fixed sampled targets stays within
+// err_factor of the error of the paper's default N0 = 4 n^2 with default
+// options; the other choices change only the work layout.
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <mutex>
@@ -33,22 +37,46 @@ std::string cache_key(int device, int kid, int degree, double theta, int prec, i
   return buf;
 }
 
+bool finite_nonneg(double x) { return isfinite(x) && x >= 0.0; }
+
+// One cache line of the current format, validated; false for anything else.
+bool parse_line(const char *line, std::string *key, csfmm_tune_result *r) {
+  char tag[8], k[512], extra[8];
+  csfmm_tune_result t{};
+  const int n = sscanf(line, "%7s %511s %d %d %d %d %lf %lf %lf %lf %7s", tag, k, &t.max_leaf,
+                       &t.rhs_chunk, &t.no_persistent, &t.schedule, &t.ms_per_eval, &t.rel_err,
+                       &t.default_ms, &t.default_rel_err, extra);
+  if (n != 10 || strcmp(tag, "v2") != 0) return false;  // stale format, cut short or trailing text
+  if (t.max_leaf < 1 || (t.rhs_chunk != 0 && t.rhs_chunk != 4 && t.rhs_chunk != 8 &&
+                         t.rhs_chunk != 16) ||
+      (t.no_persistent != 0 && t.no_persistent != 1) || t.schedule < 0 || t.schedule > 31 ||
+      !finite_nonneg(t.ms_per_eval) || !finite_nonneg(t.rel_err) ||
+      !finite_nonneg(t.default_ms) || !finite_nonneg(t.default_rel_err))
+    return false;
+  *key = k;
+  *r = t;
+  return true;
+}
+
 bool cache_lookup(const char *path, const std::string &key, csfmm_tune_result *out) {
   std::lock_guard<std::mutex> lk(g_cache_mutex);
   FILE *f = fopen(path, "r");
   if (!f) return false;
-  char line[1024];
+  char *line = nullptr;
+  size_t cap = 0;
+  ssize_t n;
   bool found = false;
-  while (fgets(line, sizeof line, f)) {
-    char k[512];
+  while ((n = getline(&line, &cap, f)) >= 0) {
+    // longer than any valid line, or holding a NUL byte: not a cache line
+    if (n > 1000 || memchr(line, 0, (size_t)n)) continue;
+    std::string k;
     csfmm_tune_result r{};
-    if (sscanf(line, "%511s %d %d %lf %lf %lf %lf", k, &r.max_leaf, &r.rhs_chunk, &r.ms_per_eval,
-               &r.rel_err, &r.default_ms, &r.default_rel_err) == 7 &&
-        key == k && r.max_leaf >= 1) {
-      *out = r;  // the last matching line wins
+    if (parse_line(line, &k, &r) && k == key) {
+      *out = r;  // the last valid matching line wins
       found = true;
     }
   }
+  free(line);
   fclose(f);
   return found;
 }
@@ -57,8 +85,9 @@ void cache_store(const char *path, const std::string &key, const csfmm_tune_resu
   std::lock_guard<std::mutex> lk(g_cache_mutex);
   FILE *f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s %d %d %.6g %.6g %.6g %.6g\n", key.c_str(), r.max_leaf, r.rhs_chunk,
-          r.ms_per_eval, r.rel_err, r.default_ms, r.default_rel_err);
+  fprintf(f, "v2 %s %d %d %d %d %.9g %.9g %.9g %.9g\n", key.c_str(), r.max_leaf, r.rhs_chunk,
+          r.no_persistent, r.schedule, r.ms_per_eval, r.rel_err, r.default_ms,
+          r.default_rel_err);
   fclose(f);
 }
 
@@ -144,57 +173,97 @@ extern "C" csfmm_status csfmm_autotune(const double *points, int64_t N, int kern
   for (double v : href) rnorm += v * v;
   rnorm = sqrt(rnorm);
 
-  const int n2 = degree * degree;
-  const int mult[] = {4, 1, 2, 3, 6, 8};  // the default first
-  std::vector<int> chunks = {0};
-  if (precision == CSFMM_FP32_BULK && nrhs >= 8 && kernel_id != CSFMM_KERNEL_BIOT_SAVART)
-    chunks = {0, 8, 4};
-  struct Cand { int leaf, chunk; double ms, err; };
+  struct Cand {
+    int leaf, chunk, nop, sched;
+    double ms, err;
+  };
   std::vector<Cand> cands;
-  for (int mlt : mult) {
-    const int leaf = mlt * n2 < 8 ? 8 : mlt * n2;
-    bool dup = false;
-    for (const Cand &c : cands) dup |= c.leaf == leaf;
-    if (dup) continue;
+  // times one configuration of an existing plan and records it
+  auto measure = [&](csfmm_plan plan, int leaf, int chunk, int nop, int sched) -> csfmm_status {
+    plan->impl.rhs_chunk = chunk == 0 ? 16 : chunk;
+    plan->impl.no_persistent = nop;
+    plan->impl.schedule = sched;
+    csfmm_status r = csfmm_evaluate(plan, weights, nrhs, outbuf, st);  // warm-up
+    cudaEventRecord(e0, st);
+    for (int k = 0; k < 3 && r == CSFMM_OK; ++k) r = csfmm_evaluate(plan, weights, nrhs, outbuf, st);
+    cudaEventRecord(e1, st);
+    if (r == CSFMM_OK) r = csfmm_plan_sync(plan, st);
+    if (r != CSFMM_OK) return r;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    pick_kernel<<<(ns * dim + 127) / 128, 128, 0, st>>>(outbuf, tg, ns, dim, got);
+    cudaMemcpyAsync(hgot.data(), got, sizeof(double) * hgot.size(), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    double dn = 0.0;
+    for (size_t i = 0; i < hgot.size(); ++i) dn += (hgot[i] - href[i]) * (hgot[i] - href[i]);
+    cands.push_back({leaf, chunk, nop, sched, ms / 3.0, rnorm > 0 ? sqrt(dn) / rnorm : sqrt(dn)});
+    return CSFMM_OK;
+  };
+  auto build = [&](int leaf, csfmm_plan *plan) {
     csfmm_options opt{};
     opt.precision = precision;
     opt.max_nrhs = nrhs;
+    return csfmm_plan_create(points, N, kernel_id, degree, theta, leaf, &opt, st, plan);
+  };
+  auto accepted = [&](const Cand &c) { return c.err <= err_factor * cands[0].err + 1e-300; };
+
+  // stage 1: the leaf size, default options (the paper's N0 = 4 n^2 first)
+  const int n2 = degree * degree;
+  const int mult[] = {4, 1, 2, 3, 6, 8};
+  std::vector<int> leaves;
+  for (int mlt : mult) {
+    const int leaf = mlt * n2 < 8 ? 8 : mlt * n2;
+    bool dup = false;
+    for (int l : leaves) dup |= l == leaf;
+    if (!dup) leaves.push_back(leaf);
+  }
+  for (int leaf : leaves) {
     csfmm_plan plan = nullptr;
-    s = csfmm_plan_create(points, N, kernel_id, degree, theta, leaf, &opt, st, &plan);
+    s = build(leaf, &plan);
+    if (s == CSFMM_OK) s = measure(plan, leaf, 0, 0, 0);
+    if (plan) csfmm_plan_destroy(plan);
     if (s != CSFMM_OK) {
       cleanup();
       return s;
     }
-    for (int ch : chunks) {
-      plan->impl.rhs_chunk = ch == 0 ? 16 : ch;
-      s = csfmm_evaluate(plan, weights, nrhs, outbuf, st);  // warm-up
-      cudaEventRecord(e0, st);
-      for (int k = 0; k < 3 && s == CSFMM_OK; ++k) s = csfmm_evaluate(plan, weights, nrhs, outbuf, st);
-      cudaEventRecord(e1, st);
-      if (s == CSFMM_OK) s = csfmm_plan_sync(plan, st);
-      if (s != CSFMM_OK) {
-        csfmm_plan_destroy(plan);
-        cleanup();
-        return s;
-      }
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      pick_kernel<<<(ns * dim + 127) / 128, 128, 0, st>>>(outbuf, tg, ns, dim, got);
-      cudaMemcpyAsync(hgot.data(), got, sizeof(double) * hgot.size(), cudaMemcpyDeviceToHost, st);
-      cudaStreamSynchronize(st);
-      double dn = 0.0;
-      for (size_t i = 0; i < hgot.size(); ++i) dn += (hgot[i] - href[i]) * (hgot[i] - href[i]);
-      cands.push_back({leaf, ch, ms / 3.0, rnorm > 0 ? sqrt(dn) / rnorm : sqrt(dn)});
+  }
+  const Cand *b1 = &cands[0];
+  for (const Cand &c : cands)
+    if (accepted(c) && c.ms < b1->ms) b1 = &c;
+  const int best_leaf = b1->leaf;
+
+  // stage 2: launch schedule and tile shapes at that leaf size
+  std::vector<Cand> sched;  // (chunk, nop, schedule) to try
+  const bool scalar = kernel_id != CSFMM_KERNEL_BIOT_SAVART;
+  if (precision == CSFMM_FP32_BULK && scalar && nrhs >= 8) {
+    if (nrhs % 8 == 0) sched.push_back({0, 8, 0, 0, 0, 0});        // persistent, chunks of 8
+    for (int ch : {0, 8, 4})
+      for (int shape = 0; shape < 8; ++shape) sched.push_back({0, ch, 1, shape, 0, 0});
+  } else {
+    if (precision == CSFMM_FP32_BULK && scalar && nrhs == 1)
+      sched.push_back({0, 0, 0, CSFMM_SCHED_NO_SYMMETRIC, 0, 0});
+    sched.push_back({0, 0, 0, CSFMM_SCHED_NO_OVERLAP, 0, 0});
+  }
+  {
+    csfmm_plan plan = nullptr;
+    s = build(best_leaf, &plan);
+    for (size_t k = 0; k < sched.size() && s == CSFMM_OK; ++k)
+      s = measure(plan, best_leaf, sched[k].chunk, sched[k].nop, sched[k].sched);
+    if (plan) csfmm_plan_destroy(plan);
+    if (s != CSFMM_OK) {
+      cleanup();
+      return s;
     }
-    csfmm_plan_destroy(plan);
   }
   cleanup();
   const Cand &def = cands[0];
   const Cand *best = &def;
   for (const Cand &c : cands)
-    if (c.err <= err_factor * def.err + 1e-300 && c.ms < best->ms) best = &c;
+    if (accepted(c) && c.ms < best->ms) best = &c;
   out->max_leaf = best->leaf;
   out->rhs_chunk = best->chunk;
+  out->no_persistent = best->nop;
+  out->schedule = best->sched;
   out->ms_per_eval = best->ms;
   out->rel_err = best->err;
   out->default_ms = def.ms;
@@ -202,5 +271,22 @@ extern "C" csfmm_status csfmm_autotune(const double *points, int64_t N, int kern
   out->candidates = (int)cands.size();
   out->from_cache = 0;
   if (cache_path) cache_store(cache_path, key, *out);
+  return CSFMM_OK;
+}
+
+extern "C" csfmm_status csfmm_tune_cache_read(const char *path, const char *key,
+                                              csfmm_tune_result *out) {
+  if (!path || !key || !out) {
+    set_error("path, key and out must be non-NULL");
+    return CSFMM_ERR_INVALID_ARG;
+  }
+  csfmm_tune_result r{};
+  if (!cache_lookup(path, key, &r)) {
+    set_error("not found: no valid line for this key in %s", path);
+    return CSFMM_ERR_INVALID_ARG;
+  }
+  r.from_cache = 1;
+  r.candidates = 0;
+  *out = r;
   return CSFMM_OK;
 }

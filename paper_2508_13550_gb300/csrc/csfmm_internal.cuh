@@ -135,10 +135,13 @@ struct PlanView {
 struct PersistArgs {
   const int32_t *leaves;
   int nleaves, ncells;
-  int nl2l;                 // cells of levels 0 .. nlevels-2 (L2L items, in level order)
+  int nl2l;                 // cells of levels 0 .. nlevels-2 (L2L items)
   int nch, nrhs, ldr;       // nch chunks of NR right-hand sides; rhs stride of wbar / psi
   int far_pair;             // 1: a far item holds two cells, one per half block
-  int nfar, nnear, total;   // items: far, then near, then L2L, then L2P
+  int nfar, nnear, total;   // items: far, then near with the L2L levels inserted, then L2P
+  int nlev;                 // L2L levels (nlevels - 1)
+  int lvl_begin[kLMax + 2]; // cells of level l: [lvl_begin[l], lvl_begin[l+1])
+  int ins[kLMax + 1];       // L2L level l follows near item ins[l] (nondecreasing)
   const float *wsf, *wbar;
   double *phi, *psi, *out;
   int *ctr;                 // [0] queue head, [1] abort flag, then far_done, l2l_done and
@@ -160,6 +163,7 @@ struct Plan {
   int rhs_chunk = 16;   // FP32 bulk, scalar kernels: 16, 8 or 4
   int shrink = 0;       // cell boxes shrunk to their points
   int no_persistent = 0; // 1: several right-hand sides always take the per-phase launches
+  int schedule = 0;      // CSFMM_SCHED_* bits (FP32 bulk tile shapes and launch schedule)
   // dependency waits of the persistent kernel: bound, and a test hook that
   // makes every wait need one completion more than will ever happen
   double wait_limit_ms = 2000.0;
@@ -317,10 +321,11 @@ void launch_cstc(const PlanView &v, bool f32, double theta, int nroots, int nrhs
                  const double *ws, const float *wsf, const double *wbar, const float *wbar32,
                  double *out, cudaStream_t st);
 // FP32-bulk near (far = false) or far (far = true) field for nr = 8 or 16
-// right-hand sides from r0, scalar kernels only (interact32.cu).
+// right-hand sides from r0, scalar kernels only.
+// schedule: the plan's CSFMM_SCHED_* bits (tile shape) (multi32.cu).
 void launch_multi32(const PlanView &v, bool far, int ngrid, const int32_t *leaves,
                     const float *wsf, const float *wbar, int ldr, int r0, int nr, double *phi,
-                    double *psi, cudaStream_t st);
+                    double *psi, int schedule, cudaStream_t st);
 // FP32-bulk far field (interact32.cu): nr <= 4 right-hand sides from r0.
 void launch_far32(const PlanView &v, int ncells, const float *wsf, const float *wbar, int ldr,
                   int r0, int nr, double *psi, cudaStream_t st);

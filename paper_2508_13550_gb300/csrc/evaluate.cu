@@ -752,7 +752,7 @@ csfmm_status run_passes(Plan &pl, Workspace &W, const double *w, int nrhs, doubl
   // pass reads the leaves' weight totals of P2M, so there P2M stays on st
   // before the fork.  Phase timing brackets every phase with its own events
   // on the stream it runs on.
-  const bool overlap = W.side != nullptr;
+  const bool overlap = W.side != nullptr && !(pl.schedule & CSFMM_SCHED_NO_OVERLAP);
   cudaStream_t sf = overlap ? W.side : st;
   const bool p2m_first = !overlap || (sizeof(Real) == 4 && KID == CSFMM_KERNEL_LAPLACE);
 #define CSFMM_BEGIN(ph, s)                           \
@@ -851,7 +851,8 @@ csfmm_status run_passes(Plan &pl, Workspace &W, const double *w, int nrhs, doubl
     const int nr = chunk(r0);
     if constexpr (sizeof(Real) == 4) {
       if (nr > kRB)
-        launch_multi32(v, true, pl.ncells, pl.leaves, W.wsf, wbar, ldr, r0, nr, W.phi, psi, sf);
+        launch_multi32(v, true, pl.ncells, pl.leaves, W.wsf, wbar, ldr, r0, nr, W.phi, psi,
+                       pl.schedule, sf);
       else
         launch_far32(v, pl.ncells, W.wsf, wbar, ldr, r0, nr, psi, sf);
     } else {
@@ -880,7 +881,8 @@ csfmm_status run_passes(Plan &pl, Workspace &W, const double *w, int nrhs, doubl
   // single right-hand side, symmetric scalar kernel: the cross pairs of the PP
   // lists are evaluated once for both directions first
   const bool sym = sizeof(Real) == 4 && nrhs == 1 && KID != CSFMM_KERNEL_BIOT_SAVART &&
-                   pl.n_sym_pairs > 0 && W.sym_part != nullptr;
+                   pl.n_sym_pairs > 0 && W.sym_part != nullptr &&
+                   !(pl.schedule & CSFMM_SCHED_NO_SYMMETRIC);
   CSFMM_BEGIN(CSFMM_PHASE_PPSYM, st);
   if (sym) {
     launch_pp_sym32(v, pl.sym_pairs, pl.sym_off, pl.n_sym_pairs, W.wsf, W.sym_part, st);
@@ -893,7 +895,8 @@ csfmm_status run_passes(Plan &pl, Workspace &W, const double *w, int nrhs, doubl
     const int nr = chunk(r0);
     if constexpr (sizeof(Real) == 4) {
       if (nr > kRB)
-        launch_multi32(v, false, pl.nleaves, pl.leaves, W.wsf, wbar, ldr, r0, nr, W.phi, psi, st);
+        launch_multi32(v, false, pl.nleaves, pl.leaves, W.wsf, wbar, ldr, r0, nr, W.phi, psi,
+                       pl.schedule, st);
       else
         launch_near32(v, pl.leaves, pl.nleaves, W.wsf, N, wbar, ldr, r0, nr, W.phi, st,
                       sym ? W.sym_part : nullptr);

@@ -27,7 +27,6 @@
 
 #include "csfmm_internal.cuh"
 #include "fp32_math.cuh"
-#include "multi32.cuh"
 
 namespace csfmm {
 
@@ -291,19 +290,24 @@ __global__ void __launch_bounds__(kThreads) near32_kernel(PlanView v, const int3
 // Per kernel evaluation the FP32 pipe does 8 lane-ops (3 differences, |r|^2,
 // the row and the column FMA) plus the column reduction, about
 // 2 / (2 kSymQP) lane-ops (one add to fold the packed halves, one in the
-// butterfly, per column and lane), next to one MUFU operation.
+// butterfly, per column and lane), next to one MUFU operation.  Default
+// shape: one warp per leaf pair with eight rows per lane (a 256-point leaf in
+// one pass) and groups of 16 columns, 16 blocks per SM (measured on the
+// N = 6.3M Newtonian workload: 6.98 ms against 7.16 ms for two warps with
+// four rows per lane and 32-column groups; 24 warps per SM with 16-column
+// groups were slower, 7.40-7.45 ms).
 // ---------------------------------------------------------------------------
 #ifndef CSFMM_SYM_WARPS
-#define CSFMM_SYM_WARPS 2
+#define CSFMM_SYM_WARPS 1
 #endif
 #ifndef CSFMM_SYM_QP
-#define CSFMM_SYM_QP 2
+#define CSFMM_SYM_QP 4
 #endif
 #ifndef CSFMM_SYM_GROUP
-#define CSFMM_SYM_GROUP 32
+#define CSFMM_SYM_GROUP 16
 #endif
 #ifndef CSFMM_SYM_MINB
-#define CSFMM_SYM_MINB 8
+#define CSFMM_SYM_MINB 16
 #endif
 constexpr int kSymWarps = CSFMM_SYM_WARPS;
 constexpr int kSymQP = CSFMM_SYM_QP;         // packed row pairs per lane
@@ -794,40 +798,6 @@ void launch_far_kid(const PlanView &v, int ncells, const float *wsf, const float
 }
 
 
-// Multi-right-hand-side interactions (multi32.cuh): one block per target
-// leaf (near field) or cell (far field).
-template <int KID, int NR, bool FAR>
-__global__ void __launch_bounds__(CSFMM_MULTI_THREADS) multi32_kernel(
-    PlanView v, const int32_t *leaves, const float *wsf, const float *wbar, int ldr, int r0,
-    double *phi, double *psi) {
-  __shared__ float4 sp[kMultiTile];
-  __shared__ ulonglong2 sw4[(NR / 4) * kMultiTile];
-  const int c = FAR ? (int)blockIdx.x : leaves[blockIdx.x];
-  multi32_item<KID, NR, FAR>(v, c, wsf, wbar, ldr, r0, phi, psi, sp, sw4, threadIdx.x, blockDim.x,
-                             0);
-}
-
-template <int KID, int NR>
-void launch_multi(const PlanView &v, bool far, int ngrid, const int32_t *leaves, const float *wsf,
-                  const float *wbar, int ldr, int r0, double *phi, double *psi, cudaStream_t st) {
-  if (far) {
-    const int per = 32 * CSFMM_MULTI_NT;  // targets covered by one warp
-    const int nth = std::min(CSFMM_MULTI_THREADS, std::max(32, ((v.P + per - 1) / per) * 32));
-    multi32_kernel<KID, NR, true><<<ngrid, nth, 0, st>>>(v, leaves, wsf, wbar, ldr, r0, phi, psi);
-  } else {
-    multi32_kernel<KID, NR, false><<<ngrid, CSFMM_MULTI_THREADS, 0, st>>>(v, leaves, wsf, wbar,
-                                                                          ldr, r0, phi, psi);
-  }
-}
-
-template <int KID>
-void launch_multi_kid(const PlanView &v, bool far, int ngrid, const int32_t *leaves,
-                      const float *wsf, const float *wbar, int ldr, int r0, int nr, double *phi,
-                      double *psi, cudaStream_t st) {
-  if (nr == 16) launch_multi<KID, 16>(v, far, ngrid, leaves, wsf, wbar, ldr, r0, phi, psi, st);
-  else launch_multi<KID, 8>(v, far, ngrid, leaves, wsf, wbar, ldr, r0, phi, psi, st);
-}
-
 template <int KID, int NR>
 void launch_nr(const PlanView &v, const int32_t *leaves, int nleaves, const float *wsf, int ldw,
                const float *wbar, int ldr, int r0, double *phi, cudaStream_t st,
@@ -852,20 +822,6 @@ void launch_kid(const PlanView &v, const int32_t *leaves, int nleaves, const flo
 }
 
 }  // namespace
-
-// Right-hand sides r0 .. r0+nr-1 with nr = 8 or 16 for the scalar kernels:
-// near field (far = false, one block per leaf) or far field (far = true).
-void launch_multi32(const PlanView &v, bool far, int ngrid, const int32_t *leaves,
-                    const float *wsf, const float *wbar, int ldr, int r0, int nr, double *phi,
-                    double *psi, cudaStream_t st) {
-  switch (v.kernel_id) {
-    case CSFMM_KERNEL_LAPLACE: launch_multi_kid<CSFMM_KERNEL_LAPLACE>(v, far, ngrid, leaves, wsf, wbar, ldr, r0, nr, phi, psi, st); break;
-    case CSFMM_KERNEL_NEWTON: launch_multi_kid<CSFMM_KERNEL_NEWTON>(v, far, ngrid, leaves, wsf, wbar, ldr, r0, nr, phi, psi, st); break;
-    case CSFMM_KERNEL_SAL: launch_multi_kid<CSFMM_KERNEL_SAL>(v, far, ngrid, leaves, wsf, wbar, ldr, r0, nr, phi, psi, st); break;
-    case CSFMM_KERNEL_BIHARMONIC: launch_multi_kid<CSFMM_KERNEL_BIHARMONIC>(v, far, ngrid, leaves, wsf, wbar, ldr, r0, nr, phi, psi, st); break;
-    default: launch_multi_kid<CSFMM_KERNEL_ONE>(v, far, ngrid, leaves, wsf, wbar, ldr, r0, nr, phi, psi, st); break;
-  }
-}
 
 // nr right-hand sides r0 .. r0+nr-1 (nr <= 4); psi [nc][ldr][dim][P] FP64.
 void launch_far32(const PlanView &v, int ncells, const float *wsf, const float *wbar, int ldr,

@@ -62,12 +62,15 @@ __device__ __forceinline__ void eval_multi(const float4 *__restrict__ sp,
   }
 }
 
-template <int KID, int NT, int NR, bool SELF>
+// Sums of one staged tile in FP32 over chunks of CH sources, each chunk
+// folded into the (hi, lo) totals by two-sum.
+template <int KID, int NT, int NR, bool SELF, int CH>
 __device__ __forceinline__ void tile_sum_multi(const float4 *__restrict__ sp,
                                                const ulonglong2 *__restrict__ sw4, int nj,
                                                const float (&tx)[NT], const float (&ty)[NT],
                                                const float (&tz)[NT], const int (&self)[NT],
                                                f2x (&hi)[NT][NR / 2], f2x (&lo)[NT][NR / 2]) {
+  constexpr int kChunk = CH;
   for (int jc = 0; jc < nj; jc += kChunk) {
     f2x acc[NT][NR / 2];
 #pragma unroll
@@ -93,15 +96,14 @@ __device__ __forceinline__ void tile_sum_multi(const float4 *__restrict__ sp,
 // cell c into psi (FP64; a cell without CP/CC entries gets zeros).  nth
 // threads (tid = 0 .. nth-1, synchronised by barrier `bar`) share the item,
 // NT targets per thread strided by nth; every target keeps FP32 (hi, lo)
-// running totals per right-hand side over the whole list and writes FP64
-// once.  sp [kMultiTile] and sw4 [(NR/4) kMultiTile] are this group's shared
-// memory.
-template <int KID, int NR, bool FAR>
+// running totals per right-hand side over the whole list, summing tiles in
+// chunks of CH sources, and writes FP64 once.  sp [kMultiTile] and sw4
+// [(NR/4) kMultiTile] are this group's shared memory.
+template <int KID, int NR, bool FAR, int NT = CSFMM_MULTI_NT, int CH = kChunk>
 __device__ __forceinline__ void multi32_item(const PlanView &v, int c, const float *wsf,
                                              const float *wbar, int ldr, int r0, double *phi,
                                              double *psi, float4 *sp, ulonglong2 *sw4, int tid,
                                              int nth, int bar) {
-  constexpr int NT = CSFMM_MULTI_NT;
   const int P = v.P;
   const int tb = FAR ? 0 : v.cbegin[c];
   const int te = FAR ? P : v.cend[c];
@@ -191,9 +193,9 @@ __device__ __forceinline__ void multi32_item(const PlanView &v, int c, const flo
 #pragma unroll
           for (int k = 0; k < NT; ++k) self[k] = (i0 + tid + k * nth) - (sb + j0);
           if (self_tile)
-            tile_sum_multi<KID, NT, NR, true>(sp, sw4, nj, tx, ty, tz, self, hi, lo);
+            tile_sum_multi<KID, NT, NR, true, CH>(sp, sw4, nj, tx, ty, tz, self, hi, lo);
           else
-            tile_sum_multi<KID, NT, NR, false>(sp, sw4, nj, tx, ty, tz, self, hi, lo);
+            tile_sum_multi<KID, NT, NR, false, CH>(sp, sw4, nj, tx, ty, tz, self, hi, lo);
         }
       }
     }

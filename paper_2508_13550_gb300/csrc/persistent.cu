@@ -8,10 +8,13 @@
 //   far   (cell, chunk): CP and CC proxy potentials (Sec. 5, Eqs. CP, CC);
 //         with P <= 128 one item holds two cells, one per half block
 //   near  (leaf, chunk): PP and PC potentials at the particles (Eqs. PP, PC)
-//   L2L   (cell), cells in level order: proxy potentials passed to the
-//         children (Sec. 8.1, Eq. downward_2), all right-hand sides
+//   L2L   (cell): proxy potentials passed to the children (Sec. 8.1, Eq.
+//         downward_2), all right-hand sides; the cells of level l follow the
+//         first (l + 1)/(2 L) of the near items (L = L2L levels), so that
+//         their parents' items finished long before and the downward chain
+//         runs while other blocks work on the near field
 //   L2P   (leaf): interpolation to the particles plus the near field, output
-//         in input order (Algorithm "CSFMM", downward pass)
+//         in input order (Algorithm "CSFMM", downward pass), after all
 // Every piece of work is independent in the paper's sense (Sec. 11.3: each
 // interaction is its own direct sum); the only dependencies are those of the
 // downward pass, tracked by per-cell counters that an item raises (release)
@@ -89,6 +92,24 @@ __device__ bool wait_at_least(const PersistArgs &a, int *status, const int *flag
   }
 }
 
+// Item of queue position it: (kind, index) with kind 0 far, 1 near, 2 L2L
+// (index = cell), 3 L2P (index into the leaf list).
+__device__ __forceinline__ int2 decode_item(const PersistArgs &a, int it) {
+  if (it < a.nfar) return make_int2(0, it);
+  int pos = it - a.nfar, prev = 0;
+  for (int l = 0; l < a.nlev; ++l) {
+    const int span = a.ins[l] - prev;
+    if (pos < span) return make_int2(1, prev + pos);
+    pos -= span;
+    const int nl = a.lvl_begin[l + 1] - a.lvl_begin[l];
+    if (pos < nl) return make_int2(2, a.lvl_begin[l] + pos);
+    pos -= nl;
+    prev = a.ins[l];
+  }
+  if (pos < a.nnear - prev) return make_int2(1, prev + pos);
+  return make_int2(3, pos - (a.nnear - prev));
+}
+
 // Raises a counter once every thread of the group (barrier bar, nth threads)
 // has written its results.
 __device__ __forceinline__ void signal_done(int *flag, int tid, int bar, int nth) {
@@ -100,7 +121,7 @@ __device__ __forceinline__ void signal_done(int *flag, int tid, int bar, int nth
 }
 
 template <int KID, int NR, int PC>
-__global__ void __launch_bounds__(kPersistThreads) persistent_kernel(PlanView v, PersistArgs a) {
+__global__ void __launch_bounds__(kPersistThreads, 3) persistent_kernel(PlanView v, PersistArgs a) {
   __shared__ __align__(16) unsigned char smem[persist_smem_bytes<NR>()];
   __shared__ int s_item, s_ok;
   int *far_done = a.ctr + 2;
@@ -111,9 +132,10 @@ __global__ void __launch_bounds__(kPersistThreads) persistent_kernel(PlanView v,
     __syncthreads();  // the previous item no longer reads shared memory or s_item
     if (threadIdx.x == 0) s_item = atomicAdd(a.ctr, 1);
     __syncthreads();
-    int it = s_item;
-    if (it >= a.total) return;
-    if (it < a.nfar) {  // far field of one cell (or two) and one chunk
+    if (s_item >= a.total) return;
+    const int2 item = decode_item(a, s_item);
+    const int it = item.y;
+    if (item.x == 0) {  // far field of one cell (or two) and one chunk
       const int r0 = (it % a.nch) * NR;
       const int half = a.far_pair ? (int)(threadIdx.x >> 6) : 0;
       const int c = a.far_pair ? 2 * (it / a.nch) + half : it / a.nch;
@@ -130,8 +152,7 @@ __global__ void __launch_bounds__(kPersistThreads) persistent_kernel(PlanView v,
       }
       continue;
     }
-    it -= a.nfar;
-    if (it < a.nnear) {  // near field of one leaf and one chunk
+    if (item.x == 1) {  // near field of one leaf and one chunk
       const int leaf = a.leaves[it / a.nch], r0 = (it % a.nch) * NR;
       multi32_item<KID, NR, false>(v, leaf, a.wsf, a.wbar, a.ldr, r0, a.phi, a.psi,
                                    reinterpret_cast<float4 *>(smem),
@@ -140,8 +161,7 @@ __global__ void __launch_bounds__(kPersistThreads) persistent_kernel(PlanView v,
       signal_done(near_done + leaf, threadIdx.x, 0, kPersistThreads);
       continue;
     }
-    it -= a.nnear;
-    if (it < a.nl2l) {  // L2L from cell c to its children, all right-hand sides
+    if (item.x == 2) {  // L2L from cell c to its children, all right-hand sides
       const int c = it;
       const int32_t *ch = v.cchild + 4 * c;
       if (ch[0] < 0 && ch[1] < 0 && ch[2] < 0 && ch[3] < 0) continue;  // a leaf
@@ -159,7 +179,6 @@ __global__ void __launch_bounds__(kPersistThreads) persistent_kernel(PlanView v,
       signal_done(l2l_done + c, threadIdx.x, 0, kPersistThreads);
       continue;
     }
-    it -= a.nl2l;
     {  // L2P of one leaf, all right-hand sides
       const int leaf = a.leaves[it];
       if (threadIdx.x == 0) {
@@ -249,6 +268,8 @@ csfmm_status launch_persistent(const PlanView &v, const Plan &pl, Workspace &W, 
   a.nleaves = pl.nleaves;
   a.ncells = pl.ncells;
   a.nl2l = pl.nlevels >= 2 ? pl.level_begin[pl.nlevels - 1] : 0;
+  a.nlev = pl.nlevels >= 2 ? pl.nlevels - 1 : 0;
+  for (int l = 0; l <= a.nlev; ++l) a.lvl_begin[l] = pl.level_begin[l];
   a.nch = nrhs / chunk;
   a.nrhs = nrhs;
   a.ldr = W.max_nrhs;
@@ -256,6 +277,8 @@ csfmm_status launch_persistent(const PlanView &v, const Plan &pl, Workspace &W, 
   a.nfar = (a.far_pair ? (pl.ncells + 1) / 2 : pl.ncells) * a.nch;
   a.nnear = pl.nleaves * a.nch;
   a.total = a.nfar + a.nnear + a.nl2l + pl.nleaves;
+  for (int l = 0; l < a.nlev; ++l)
+    a.ins[l] = (int)((int64_t)a.nnear * (l + 1) / (2 * a.nlev));
   a.wsf = W.wsf;
   a.wbar = W.wbar32;
   a.phi = W.phi;

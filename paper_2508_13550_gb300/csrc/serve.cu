@@ -2,11 +2,22 @@
 // (csfmm_server_* in include/csfmm.h).
 //
 // One scheduler thread owns every plan, workspace and slot.  Callers only
-// append requests to a FIFO under the mutex and wait on a condition variable.
-// The scheduler (1) retires finished slots by polling their CUDA events,
-// (2) admits head-of-queue requests while a slot is free and the device
-// memory the request needs fits in the budget (evicting idle cached plans,
-// least recently used first), and (3) sleeps briefly when nothing changed.
+// append requests to a queue under the mutex and wait on a condition
+// variable.  The scheduler (1) retires finished slots by polling their CUDA
+// events, (2) admits requests while a slot is free and the device memory the
+// request needs fits in the budget (evicting idle cached plans, least
+// recently used first), and (3) sleeps briefly when nothing changed.
+// Admission order (csfmm_server_set_policy): first come first served, or
+// (default) the cheapest pending request first -- cost estimated from its
+// points, right-hand sides and proxies -- with two guards: a request that
+// has waited longer than the aging bound goes first regardless of its cost
+// (and nothing is admitted past it while it does not fit), and large
+// requests (at least 2^20 points) hold at most half of the slots, so that a
+// burst of large requests cannot block small ones behind them.  Under that
+// policy a small request also runs on its slot's high-priority stream with
+// every pass on that stream (its plan is built with CSFMM_SCHED_NO_OVERLAP),
+// so the block scheduler serves its kernels before pending blocks of large
+// requests instead of letting them queue behind those.
 // Each admitted request runs on its slot's stream with its own workspace, so
 // requests of different sizes and kernels overlap on the GPU; a request's
 // result does not depend on what else runs (deterministic kernels, private
@@ -60,7 +71,9 @@ struct Request {
 };
 
 struct Slot {
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;     // default (lowest) priority
+  cudaStream_t stream_hi = nullptr;  // highest priority: small requests under the size-aware policy
+  cudaStream_t cur = nullptr;        // the stream of the request in flight
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   int64_t req = -1;
   PlanKey key{};
@@ -95,9 +108,19 @@ int64_t estimate_plan_bytes(const csfmm_request &r) {
 
 }  // namespace
 
+// Relative cost of a request (points x (right-hand sides + a fixed part) x
+// proxies), used only to order admissions.
+double request_cost(const csfmm_request &r) {
+  const double p = r.degree + 1;
+  return (double)r.N * (4.0 + r.nrhs) * p * p;
+}
+constexpr int64_t kLargeRequestN = 1 << 20;
+
 struct csfmm_server_s {
   int device = 0;
   int64_t budget = 0;
+  int policy = CSFMM_SERVE_CHEAPEST_FIRST;
+  double age_ms = 250.0;
   std::vector<Slot> slots;
   std::mutex mu;
   std::condition_variable cv_sched, cv_done;
@@ -123,6 +146,8 @@ struct csfmm_server_s {
   void run();
   bool retire();
   bool admit(std::unique_lock<std::mutex> &lk);
+  // Index into `pending` of the next request to admit, or -1 to wait.
+  int pick(double now);
   void finish(Slot &s, int status);
 };
 
@@ -159,13 +184,36 @@ bool csfmm_server_s::retire() {
     if (e != cudaSuccess) {
       cudaGetLastError();
       status = CSFMM_ERR_CUDA;
-    } else if (csfmm_plan_sync(plans[s.key].plan, s.stream) != CSFMM_OK) {
+    } else if (csfmm_plan_sync(plans[s.key].plan, s.cur) != CSFMM_OK) {
       status = CSFMM_ERR_DEVICE;
     }
     finish(s, status);
     any = true;
   }
   return any;
+}
+
+int csfmm_server_s::pick(double now) {
+  if (pending.empty()) return -1;
+  if (policy == CSFMM_SERVE_FIFO) return 0;
+  // an aged request goes first (pending is in submission order)
+  if (now - reqs[pending.front()].t.submit_ms > age_ms) return 0;
+  int large = 0;
+  for (const Slot &sl : slots)
+    if (sl.req >= 0 && reqs[sl.req].r.N >= kLargeRequestN) ++large;
+  const int large_cap = (int)slots.size() / 2 > 0 ? (int)slots.size() / 2 : 1;
+  int best = -1;
+  double best_cost = 0.0;
+  for (size_t k = 0; k < pending.size(); ++k) {
+    const csfmm_request &r = reqs[pending[k]].r;
+    if (r.N >= kLargeRequestN && large >= large_cap) continue;
+    const double c = request_cost(r);
+    if (best < 0 || c < best_cost) {
+      best = (int)k;
+      best_cost = c;
+    }
+  }
+  return best;
 }
 
 bool csfmm_server_s::admit(std::unique_lock<std::mutex> &lk) {
@@ -175,7 +223,9 @@ bool csfmm_server_s::admit(std::unique_lock<std::mutex> &lk) {
     for (size_t i = 0; i < slots.size(); ++i)
       if (slots[i].req < 0) { si = (int)i; break; }
     if (si < 0) break;
-    const int64_t id = pending.front();
+    const int pk = pick(now_ms());
+    if (pk < 0) break;
+    const int64_t id = pending[pk];
     Request &q = reqs[id];
     const csfmm_request &r = q.r;
     PlanKey key{r.plan_key, r.kernel_id, r.degree, r.max_leaf, r.precision, r.theta};
@@ -204,7 +254,7 @@ bool csfmm_server_s::admit(std::unique_lock<std::mutex> &lk) {
       it = plans.find(key);
     }
     if (st.bytes_held + need > budget) break;  // wait for running requests to finish
-    pending.pop_front();
+    pending.erase(pending.begin() + pk);
     Slot &s = slots[si];
     s.req = id;
     s.key = key;
@@ -216,6 +266,8 @@ bool csfmm_server_s::admit(std::unique_lock<std::mutex> &lk) {
       opt.precision = r.precision;
       opt.max_nrhs = CSFMM_SERVER_MAX_NRHS;
       opt.use_graphs = 1;
+      if (policy == CSFMM_SERVE_CHEAPEST_FIRST && r.N < kLargeRequestN)
+        opt.schedule = CSFMM_SCHED_NO_OVERLAP;
       csfmm_plan h = nullptr;
       status = csfmm_plan_create(r.points, r.N, r.kernel_id, r.degree, r.theta, r.max_leaf, &opt,
                                  build_stream, &h);
@@ -260,12 +312,14 @@ bool csfmm_server_s::admit(std::unique_lock<std::mutex> &lk) {
         s.acquired = true;
         cp.last_use = ++use_clock;
         q.t.admit_ms = now_ms();
-        cudaEventRecord(s.e0, s.stream);
+        s.cur = (policy == CSFMM_SERVE_CHEAPEST_FIRST && r.N < kLargeRequestN) ? s.stream_hi
+                                                                               : s.stream;
+        cudaEventRecord(s.e0, s.cur);
         if (s.ws)
-          status = csfmm_evaluate_ws(cp.plan, s.ws, r.weights, r.nrhs, r.out, s.stream);
+          status = csfmm_evaluate_ws(cp.plan, s.ws, r.weights, r.nrhs, r.out, s.cur);
         else
-          status = csfmm_evaluate(cp.plan, r.weights, r.nrhs, r.out, s.stream);
-        cudaEventRecord(s.e1, s.stream);
+          status = csfmm_evaluate(cp.plan, r.weights, r.nrhs, r.out, s.cur);
+        cudaEventRecord(s.e1, s.cur);
       }
     }
     lk.lock();
@@ -273,7 +327,7 @@ bool csfmm_server_s::admit(std::unique_lock<std::mutex> &lk) {
     const int inf = in_flight();
     if (inf > st.max_in_flight) st.max_in_flight = inf;
     if (status != CSFMM_OK) {
-      cudaStreamSynchronize(s.stream);
+      cudaStreamSynchronize(s.cur ? s.cur : s.stream);
       finish(s, status);
     }
     any = true;
@@ -313,8 +367,12 @@ csfmm_status csfmm_server_create(int64_t hbm_budget_bytes, int slots, csfmm_serv
   s->st.slots = slots;
   s->slots.resize(slots);
   cudaError_t e = cudaStreamCreateWithFlags(&s->build_stream, cudaStreamNonBlocking);
+  int prio_low = 0, prio_high = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
   for (Slot &sl : s->slots) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+      e = cudaStreamCreateWithPriority(&sl.stream_hi, cudaStreamNonBlocking, prio_high);
     if (e == cudaSuccess) e = cudaEventCreate(&sl.e0);
     if (e == cudaSuccess) e = cudaEventCreate(&sl.e1);
   }
@@ -322,6 +380,7 @@ csfmm_status csfmm_server_create(int64_t hbm_budget_bytes, int slots, csfmm_serv
     csfmm_status st = cuda_status(e, "server stream/event creation");
     for (Slot &sl : s->slots) {
       if (sl.stream) cudaStreamDestroy(sl.stream);
+      if (sl.stream_hi) cudaStreamDestroy(sl.stream_hi);
       if (sl.e0) cudaEventDestroy(sl.e0);
       if (sl.e1) cudaEventDestroy(sl.e1);
     }
@@ -332,6 +391,19 @@ csfmm_status csfmm_server_create(int64_t hbm_budget_bytes, int slots, csfmm_serv
   s->t0 = Clock::now();
   s->th = std::thread([s] { s->run(); });
   *out = s;
+  return CSFMM_OK;
+}
+
+csfmm_status csfmm_server_set_policy(csfmm_server s, int policy, double age_ms) {
+  if (!s || (policy != CSFMM_SERVE_FIFO && policy != CSFMM_SERVE_CHEAPEST_FIRST) ||
+      !(age_ms > 0.0)) {
+    set_error("server must be non-NULL, policy CSFMM_SERVE_FIFO or CSFMM_SERVE_CHEAPEST_FIRST "
+              "and age_ms > 0");
+    return CSFMM_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->policy = policy;
+  s->age_ms = age_ms;
   return CSFMM_OK;
 }
 
@@ -437,6 +509,7 @@ csfmm_status csfmm_server_destroy(csfmm_server s) {
   }
   for (Slot &sl : s->slots) {
     cudaStreamDestroy(sl.stream);
+    cudaStreamDestroy(sl.stream_hi);
     cudaEventDestroy(sl.e0);
     cudaEventDestroy(sl.e1);
   }

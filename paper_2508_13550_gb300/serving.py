@@ -111,8 +111,11 @@ def run_stream(server: C.Server, grids: DeviceGrids, requests, rate_hz=None, the
 
 def summarize(records):
     """p50/p99 latency (ms), aggregate targets/s (sum of N * nrhs over the
-    span from first submission to last completion) and request rate."""
+    span from first submission to last completion) and request rate, and the
+    latency percentiles and median GPU time per grid size m."""
     lat = np.array([r["latency_ms"] for r in records])
+    ms = np.array([r["m"] for r in records])
+    gpu = np.array([r["gpu_ms"] for r in records])
     first = min(r["submit_ms"] for r in records)
     last = max(r["done_ms"] for r in records)
     span_s = (last - first) / 1e3
@@ -128,4 +131,10 @@ def summarize(records):
         "requests_per_s": len(records) / span_s,
         "failed": int(sum(1 for r in records if r["status"] != 0)),
         "plans_built_in_stream": int(sum(r["built_plan"] for r in records)),
+        "by_grid_size": {
+            int(m): {"requests": int((ms == m).sum()),
+                     "p50_ms": float(np.percentile(lat[ms == m], 50)),
+                     "p99_ms": float(np.percentile(lat[ms == m], 99)),
+                     "gpu_ms_p50": float(np.percentile(gpu[ms == m], 50))}
+            for m in sorted(set(ms.tolist()))},
     }

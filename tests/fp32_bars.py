@@ -48,6 +48,7 @@ BARS = {
     "fmm32-poisson-y43-m64-n8": 8e-7,  # measured 1.87e-07
     "fmm32-poisson16-1.5m-n10": 3e-7,  # measured 6.22e-08
     "fmm32-sal-chunk-vs-single": 6e-9,  # measured 1.40e-09
+    "fmm32-schedule-k0-r1": 8e-7,  # provisional: the Poisson m=64 bar (same arithmetic)
     "fmm32-sal-land-m128-n8": 2e-7,  # measured 2.83e-08
     "fmm32-sal-multi-vs-oracle-fmm": 6e-7,  # measured 1.26e-07
     "fmm32-sal-varres-shrink0": 2e-7,  # measured 3.21e-08

@@ -76,3 +76,37 @@ def test_requests_that_can_never_fit_are_refused(env):
     with pytest.raises(C.CsfmmError):
         server.submit(grids.points(64), 64, 0, 8, 0.7, 256, 1, w.repeat(9, 1), out)
     server.close()
+
+
+@pytest.mark.parametrize("policy", ["fifo", "cheapest"])
+def test_admission_order_policy(env, policy):
+    """Three large requests (6 x 512^2 points) then ten small ones (6 x 16^2),
+    all submitted at once, two slots.  First come first served starts the
+    third large request before any small one; cheapest-first lets at most one
+    large request run at a time and starts every small request before the
+    third large one."""
+    torch, C, S = env
+    grids = S.DeviceGrids((16, 512), "cuda")
+    pol = C.SERVE_FIFO if policy == "fifo" else C.SERVE_CHEAPEST_FIRST
+    server = C.Server(budget_bytes=16 << 30, slots=2, policy=pol, age_ms=60000.0)
+    # plans built before the burst, so that admissions are not held up by builds
+    warm = [dict(id=i, arrival=0.0, m=m, kernel=0, nrhs=8, degree=d, seed=i)
+            for i, (m, d) in enumerate(((512, 10), (16, 6)))]
+    S.run_stream(server, grids, warm, rate_hz=None)
+    burst = [(512, 8, 10, 10 + i) for i in range(3)] + [(16, 1, 6, 20 + i) for i in range(10)]
+    bufs = []
+    for m, nrhs, deg, seed in burst:  # every input ready before the first submission
+        w = grids.weights(m, nrhs, seed)
+        bufs.append((w, torch.empty((nrhs, w.shape[1], 1), dtype=torch.float64, device="cuda")))
+    torch.cuda.synchronize()
+    ids = [server.submit(grids.points(m), m, 0, deg, 0.7, S.leaf_size(deg), C.FP32_BULK, w, out)
+           for (m, nrhs, deg, seed), (w, out) in zip(burst, bufs)]
+    t = [server.wait(i) for i in ids]
+    server.close()
+    assert all(rc == 0 for rc, _ in t)
+    admit = [tt["admit_ms"] for _, tt in t]
+    third_large, small = admit[2], admit[3:]
+    if policy == "fifo":
+        assert third_large <= min(small)
+    else:
+        assert max(small) <= third_large
