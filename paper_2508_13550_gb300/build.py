@@ -40,15 +40,25 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+CHECKED_LIB = os.path.join(BUILD, "checked", "libcsfmm.so")
+
+
+def build(force: bool = False, verbose: bool = False, extra_flags=(), checked: bool = False) -> str:
+    """Builds libcsfmm.so; checked=True builds the bounds-checked variant
+    (-DCSFMM_CHECKED: every cell index taken from a list is validated, a bad
+    one sets the plan's status word) into _build/checked/ instead."""
+    build_dir = os.path.join(BUILD, "checked") if checked else BUILD
+    lib_path = CHECKED_LIB if checked else LIB
+    if checked:
+        extra_flags = list(extra_flags) + ["-DCSFMM_CHECKED"]
+    os.makedirs(build_dir, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     headers.append(os.path.join(HERE, "..", "include", "csfmm.h"))
     objs = []
     jobs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(build_dir, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + headers):
             cmd = [nvcc()] + _flags() + list(extra_flags) + ["-c", s, "-o", o]
@@ -65,11 +75,11 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             for out in ex.map(run, jobs):
                 if verbose and out.strip():
                     print(out)
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or jobs or _stale(lib_path, objs):
+        tmp = lib_path + f".tmp{os.getpid()}"
         run([nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -431,6 +431,22 @@ __device__ __forceinline__ void lagrange_dev(int n, const double *s, double u, d
   for (int k = 0; k <= n; ++k) L[k] *= inv;
 }
 
+// Checked builds (compiled with -DCSFMM_CHECKED, the stand-in for a memory
+// checker on this pool): every cell index a kernel takes from a list, a leaf
+// table or a child slot is validated before use; a bad one sets the plan's
+// status word (CSFMM_ERR_DEVICE from csfmm_plan_sync) and the entry is
+// skipped instead of read.  Unchecked builds compile the test away.
+#ifdef CSFMM_CHECKED
+__device__ __forceinline__ bool cell_ok(const PlanView &v, int c) {
+  const bool ok = c >= 0 && c < v.ncells && v.cbegin[c] >= 0 && v.cbegin[c] <= v.cend[c] &&
+                  v.cend[c] <= v.N;
+  if (!ok) atomicOr(v.status, kStatusInternal);
+  return ok;
+}
+#else
+__device__ __forceinline__ bool cell_ok(const PlanView &, int) { return true; }
+#endif
+
 constexpr double kInv4Pi = 0.079577471545947667884;  // 1/(4 pi)
 constexpr double kInv2Pi = 0.15915494309189533577;   // 1/(2 pi)
 

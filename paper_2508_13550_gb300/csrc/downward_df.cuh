@@ -81,7 +81,7 @@ __device__ __forceinline__ void l2l_df_cell(const PlanView &v, int c, int r0, in
       }
       for (int q = 0; q < 4; ++q) {
         const int cc = ch[q];
-        if (cc < 0) continue;
+        if (cc < 0 || !cell_ok(v, cc)) continue;
         int qa = q & 1, qb = q >> 1;
         __syncthreads();
         if (v.mcell32) {  // shrunk boxes: this child's own matrices
@@ -141,6 +141,7 @@ __device__ __forceinline__ void l2p_df_leaf(const PlanView &v, int c, const doub
   float *sph = sm, *spl = sm + kMaxP * kMaxP;
   float *sLa = sm + 2 * kMaxP * kMaxP, *sLal = sLa + kL2PThreads * kMaxP;
   float *sLb = sLal + kL2PThreads * kMaxP, *sLbl = sLb + kL2PThreads * kMaxP;
+  if (!cell_ok(v, c)) return;
   const int b = v.cbegin[c], e = v.cend[c];
   const int p = PC > 0 ? PC : v.p, P = p * p;
   for (int i0 = b; i0 < e; i0 += kL2PThreads) {

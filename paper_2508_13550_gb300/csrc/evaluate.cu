@@ -167,6 +167,7 @@ __global__ void p2m_kernel(PlanView v, const int32_t *leaves, const double *ws, 
   constexpr int CH = 64;
   __shared__ Real sLa[CH * kMaxP], sLb[CH * kMaxP], sw[NR * CH];
   const int c = leaves[blockIdx.x];
+  if (!cell_ok(v, c)) return;
   const int b = v.cbegin[c], e = v.cend[c], p = v.p, P = v.P;
   const Real *La = La_of<Real>(v), *Lb = Lb_of<Real>(v);
   const int k = threadIdx.x;
@@ -537,6 +538,7 @@ __global__ void near_kernel(PlanView v, const int32_t *leaves, const double *ws,
   constexpr int DIM = kdim<KID>();
   __shared__ Real sx[kNearTile], sy[kNearTile], sz[kNearTile], sw[kRB * kNearTile];
   const int c = leaves[blockIdx.x];
+  if (!cell_ok(v, c)) return;
   const int b = v.cbegin[c], e = v.cend[c];
   const int P = v.P;
   const double cTx = v.ccentre[3 * c], cTy = v.ccentre[3 * c + 1], cTz = v.ccentre[3 * c + 2];
@@ -562,6 +564,7 @@ __global__ void near_kernel(PlanView v, const int32_t *leaves, const double *ws,
       const int e0 = v.loff[type][c], e1 = v.loff[type][c + 1];
       for (int ee = e0; ee < e1; ++ee) {
         const int s = v.lsrc[type][ee];
+        if (!cell_ok(v, s)) continue;
         Real rx0, ry0, rz0;
         if constexpr (sizeof(Real) == 4) {
           rx0 = ox + (Real)(cTx - v.ccentre[3 * s]);
@@ -640,6 +643,7 @@ __global__ void __launch_bounds__(kL2PThreads) l2p_kernel(PlanView v, const int3
   __shared__ Real sp[kMaxP * kMaxP];
   __shared__ Real sLa[kL2PThreads * kMaxP], sLb[kL2PThreads * kMaxP];
   const int c = leaves[blockIdx.x];
+  if (!cell_ok(v, c)) return;
   const int b = v.cbegin[c], e = v.cend[c], p = v.p, P = v.P;
   const Real *La = La_of<Real>(v), *Lb = Lb_of<Real>(v);
   for (int i0 = b; i0 < e; i0 += kL2PThreads) {

@@ -157,6 +157,7 @@ __global__ void __launch_bounds__(kThreads) near32_kernel(PlanView v, const int3
   __shared__ float4 sp[kTile];
   __shared__ float sw[NR * kTile];
   const int c = leaves[blockIdx.x];
+  if (!cell_ok(v, c)) return;
   const int b = v.cbegin[c], e = v.cend[c], P = v.P;
   const double cTx = v.ccentre[3 * c], cTy = v.ccentre[3 * c + 1], cTz = v.ccentre[3 * c + 2];
   for (int i0 = b; i0 < e; i0 += kThreads * NT) {
@@ -181,6 +182,7 @@ __global__ void __launch_bounds__(kThreads) near32_kernel(PlanView v, const int3
       const int e0 = v.loff[type][c], e1 = v.loff[type][c + 1];
       for (int ee = e0; ee < e1; ++ee) {
         const int s = v.lsrc[type][ee];
+        if (!cell_ok(v, s)) continue;
         const float dcx = (float)(cTx - v.ccentre[3 * s]);
         const float dcy = (float)(cTy - v.ccentre[3 * s + 1]);
         const float dcz = (float)(cTz - v.ccentre[3 * s + 2]);
@@ -347,6 +349,7 @@ __global__ void __launch_bounds__(kSymThreads, CSFMM_SYM_MINB) pp_sym_kernel(
   __shared__ float colacc[kSymWarps][kSymCols];
   const int2 pr = pairs[blockIdx.x];
   const int T = pr.x, S = pr.y;
+  if (!cell_ok(v, T) || !cell_ok(v, S)) return;
   const int tb = v.cbegin[T], te = v.cend[T], sb = v.cbegin[S], se = v.cend[S];
   const int nT = te - tb, nS = se - sb;
   float *rowpart = part + off[blockIdx.x];
@@ -485,6 +488,7 @@ __global__ void __launch_bounds__(kThreads, CSFMM_NEAR_MINB) near32x2_kernel(Pla
   constexpr int NT = 2 * NP;
   __shared__ ulonglong2 sA[kTile], sB[kTile];
   const int c = leaves[blockIdx.x];
+  if (!cell_ok(v, c)) return;
   const int b = v.cbegin[c], e = v.cend[c], P = v.P;
   const double cTx = v.ccentre[3 * c], cTy = v.ccentre[3 * c + 1], cTz = v.ccentre[3 * c + 2];
   const float *wr = wsf + (int64_t)r0 * v.N;
@@ -507,6 +511,7 @@ __global__ void __launch_bounds__(kThreads, CSFMM_NEAR_MINB) near32x2_kernel(Pla
       const int e0 = v.loff[type][c], e1 = v.loff[type][c + 1];
       for (int ee = e0; ee < e1; ++ee) {
         const int s = v.lsrc[type][ee];
+        if (!cell_ok(v, s)) continue;
         if (part && type == CSFMM_LIST_PP && v.sym_contrib[ee] >= 0) {
           const float *pp = part + v.sym_contrib[ee] - b;
 #pragma unroll
@@ -623,6 +628,7 @@ __global__ void __launch_bounds__(160, 8) far32x2_kernel(PlanView v, const float
     const int e0 = v.loff[type][c], e1 = v.loff[type][c + 1];
     for (int ee = e0; ee < e1; ++ee) {
       const int s = v.lsrc[type][ee];
+      if (!cell_ok(v, s)) continue;
       const float dcx = (float)(cTx - v.ccentre[3 * s]);
       const float dcy = (float)(cTy - v.ccentre[3 * s + 1]);
       const float dcz = (float)(cTz - v.ccentre[3 * s + 2]);
@@ -699,6 +705,7 @@ __global__ void __launch_bounds__(160) far32_kernel(PlanView v, const float *wsf
     const int e0 = v.loff[type][c], e1 = v.loff[type][c + 1];
     for (int ee = e0; ee < e1; ++ee) {
       const int s = v.lsrc[type][ee];
+      if (!cell_ok(v, s)) continue;
       const float dcx = (float)(cTx - v.ccentre[3 * s]);
       const float dcy = (float)(cTy - v.ccentre[3 * s + 1]);
       const float dcz = (float)(cTz - v.ccentre[3 * s + 2]);

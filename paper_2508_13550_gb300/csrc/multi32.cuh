@@ -104,6 +104,7 @@ __device__ __forceinline__ void multi32_item(const PlanView &v, int c, const flo
                                              const float *wbar, int ldr, int r0, double *phi,
                                              double *psi, float4 *sp, ulonglong2 *sw4, int tid,
                                              int nth, int bar) {
+  if (!cell_ok(v, c)) return;
   const int P = v.P;
   const int tb = FAR ? 0 : v.cbegin[c];
   const int te = FAR ? P : v.cend[c];
@@ -135,6 +136,7 @@ __device__ __forceinline__ void multi32_item(const PlanView &v, int c, const flo
       const int e0 = v.loff[type][c], e1 = v.loff[type][c + 1];
       for (int ee = e0; ee < e1; ++ee) {
         const int s = v.lsrc[type][ee];
+        if (!cell_ok(v, s)) continue;
         const float dcx = (float)(cTx - v.ccentre[3 * s]);
         const float dcy = (float)(cTy - v.ccentre[3 * s + 1]);
         const float dcz = (float)(cTz - v.ccentre[3 * s + 2]);
