@@ -262,7 +262,7 @@ def timed_steps(torch, Cs, plan, dw, out, stream, steps):
 
 
 def side_workloads(args, torch, Cs, n_sm, sm_max):
-    """The other BASELINE workloads measured in the same run, each on its
+    """The other benchmark workloads measured in the same run, each on its
     own plan with inputs resident (CUDA events, median of the steps):
     Biot-Savart on 6 x 256^2 points (n = 10, FP64 and FP32 bulk) and the
     16-right-hand-side Poisson workload on 6 x 512^2 points (n = 10, FP32
@@ -589,6 +589,31 @@ def run_ours(args):
         "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms),
                     "n": len(step_ms)},
     }
+    if rank == 0 and world == 1 and nrhs == 1 and prec == Cs.FP32_BULK:
+        # every phase alone on one stream (CSFMM_SCHED_NO_OVERLAP), so that each
+        # interaction kernel's event time is its own, not shared with the side
+        # stream's far field
+        p1 = Cs.plan_create(dpts, wl["kernel"], wl["n"], wl["theta"], wl["N0"], precision=prec,
+                            max_nrhs=1, schedule=Cs.SCHED_NO_OVERLAP)
+        for _ in range(2):
+            Cs.evaluate(p1, dw, out=out)
+        Cs.plan_enable_timing(p1, True)
+        for _ in range(5):
+            Cs.evaluate(p1, dw, out=out)
+        torch.cuda.synchronize(dev)
+        ph1, c1 = Cs.plan_phase_times(p1)
+        Cs.plan_enable_timing(p1, False)
+        Cs.plan_destroy(p1)
+        alone = {}
+        for k, (e, _) in kern.items():
+            phase = {"pp_sym_kernel": "ppsym", "near32x2_kernel": "near",
+                     "far32x2_kernel": "far"}[k]
+            m = ph1[phase] / max(c1, 1)
+            alone[k] = {"ms_per_launch": m, "geval_per_s": e / (m / 1e3) / 1e9,
+                        "frac_of_alu_peak": e / (m / 1e3) / peak_evals}
+        line["kernels_alone"] = alone
+        line["kernels_alone_note"] = ("5 evaluations with every phase on one stream "
+                                      "(CSFMM_SCHED_NO_OVERLAP), CUDA events per phase")
     if rank == 0 and world == 1 and args.side_workloads:
         line["other_workloads"] = side_workloads(args, torch, Cs, n_sm, sm_max)
     if rank == 0 and world == 1 and args.serve_sample > 0:

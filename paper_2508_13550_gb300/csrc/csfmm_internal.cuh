@@ -18,6 +18,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include <string>
@@ -117,6 +118,10 @@ struct PlanView {
   const double *proxy;   // [nc][3][P]
   const float *proxy32;  // [nc][3][P]
   const int32_t *loff[4], *lsrc[4];
+  // FP32 form: centre difference c_T - c_S of every list entry as FP32 (x, y, z, 0),
+  // rounded once from FP64 (stochastically for the far-field types CP, CC of the
+  // 1/|x - y| kernels)
+  const float4 *ldc[4];
   const int32_t *sym_contrib;
   const double *m2m64;   // [2][p][p]: M[q][k][m] = L_k((s_m + 2q - 1)/2)
   const float *m2m32;    // [2][2][p][p]: FP32 rounding of m2m64, then the remainders
@@ -191,6 +196,7 @@ struct Plan {
   float *proxy32 = nullptr;
   int32_t *loff[4] = {nullptr, nullptr, nullptr, nullptr};
   int32_t *lsrc[4] = {nullptr, nullptr, nullptr, nullptr};
+  float4 *ldc[4] = {nullptr, nullptr, nullptr, nullptr};  // FP32 form: per-entry centre differences
   int64_t nlist[4] = {0, 0, 0, 0};
   // target cells that own at least one entry of a list group, for launches
   int32_t *near_targets = nullptr;  // leaves with PP or PC entries
@@ -429,6 +435,33 @@ __device__ __forceinline__ void lagrange_dev(int n, const double *s, double u, d
   }
   double inv = 1.0 / den;
   for (int k = 0; k <= n; ++k) L[k] *= inv;
+}
+
+// Unbiased stochastic rounding of x to FP32: the representable neighbour on
+// the far side of x is chosen with probability |x - RN(x)| / gap, decided by
+// the 24 high bits of the hash h, so the expected value is x.  The FP32
+// Lagrange rows use it with a hash of (point, axis, node) and the FP32 centre
+// differences of far-field list entries with a hash of (target cell, source
+// cell, axis): a uniform grid repeats the same local coordinates in every leaf
+// and the same cell offsets along a face, and round-to-nearest would give them
+// all the same rounding errors, which then add up instead of averaging out.
+__device__ __forceinline__ uint32_t hash32(uint32_t x) {
+  // integer finaliser "lowbias32" (C. Wellons, hash-prospector)
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
+__device__ __forceinline__ float round_stochastic(double x, uint32_t h) {
+  const float r = __double2float_rn(x);
+  const double d = x - (double)r;
+  if (d == 0.0) return r;
+  const float o = nextafterf(r, d > 0.0 ? INFINITY : -INFINITY);
+  const double gap = fabs((double)o - (double)r);
+  const double u = (double)(h >> 8) * (1.0 / 16777216.0);
+  return u * gap < fabs(d) ? o : r;
 }
 
 // Checked builds (compiled with -DCSFMM_CHECKED, the stand-in for a memory

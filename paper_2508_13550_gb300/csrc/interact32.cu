@@ -159,7 +159,6 @@ __global__ void __launch_bounds__(kThreads) near32_kernel(PlanView v, const int3
   const int c = leaves[blockIdx.x];
   if (!cell_ok(v, c)) return;
   const int b = v.cbegin[c], e = v.cend[c], P = v.P;
-  const double cTx = v.ccentre[3 * c], cTy = v.ccentre[3 * c + 1], cTz = v.ccentre[3 * c + 2];
   for (int i0 = b; i0 < e; i0 += kThreads * NT) {
     float ox[NT], oy[NT], oz[NT];
     bool act[NT];
@@ -183,9 +182,8 @@ __global__ void __launch_bounds__(kThreads) near32_kernel(PlanView v, const int3
       for (int ee = e0; ee < e1; ++ee) {
         const int s = v.lsrc[type][ee];
         if (!cell_ok(v, s)) continue;
-        const float dcx = (float)(cTx - v.ccentre[3 * s]);
-        const float dcy = (float)(cTy - v.ccentre[3 * s + 1]);
-        const float dcz = (float)(cTz - v.ccentre[3 * s + 2]);
+        const float4 dcv = v.ldc[type][ee];
+        const float dcx = dcv.x, dcy = dcv.y, dcz = dcv.z;
         float tx[NT], ty[NT], tz[NT];
 #pragma unroll
         for (int k = 0; k < NT; ++k) {
@@ -490,7 +488,6 @@ __global__ void __launch_bounds__(kThreads, CSFMM_NEAR_MINB) near32x2_kernel(Pla
   const int c = leaves[blockIdx.x];
   if (!cell_ok(v, c)) return;
   const int b = v.cbegin[c], e = v.cend[c], P = v.P;
-  const double cTx = v.ccentre[3 * c], cTy = v.ccentre[3 * c + 1], cTz = v.ccentre[3 * c + 2];
   const float *wr = wsf + (int64_t)r0 * v.N;
   for (int i0 = b; i0 < e; i0 += kThreads * NT) {
     float ox[NT], oy[NT], oz[NT];
@@ -521,9 +518,8 @@ __global__ void __launch_bounds__(kThreads, CSFMM_NEAR_MINB) near32x2_kernel(Pla
           }
           continue;
         }
-        const float dcx = (float)(cTx - v.ccentre[3 * s]);
-        const float dcy = (float)(cTy - v.ccentre[3 * s + 1]);
-        const float dcz = (float)(cTz - v.ccentre[3 * s + 2]);
+        const float4 dcv = v.ldc[type][ee];
+        const float dcx = dcv.x, dcy = dcv.y, dcz = dcv.z;
         f2x tx[NP], ty[NP], tz[NP];
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
@@ -602,43 +598,63 @@ __global__ void __launch_bounds__(kThreads, CSFMM_NEAR_MINB) near32x2_kernel(Pla
 // thread.  Same pair-relative FP32 arithmetic as the near field; a target
 // proxy never coincides with a source (the pair is well separated).
 // ---------------------------------------------------------------------------
+// Packed target pairs per thread of the far kernel (two targets per pair).
+#ifndef CSFMM_FAR_NP
+#define CSFMM_FAR_NP 1
+#endif
+#ifndef CSFMM_FAR_MINB
+#define CSFMM_FAR_MINB 8
+#endif
+constexpr int kFarNP = CSFMM_FAR_NP;
+
 template <int KID>
-__global__ void __launch_bounds__(160, 8) far32x2_kernel(PlanView v, const float *wsf,
+__global__ void __launch_bounds__(160, CSFMM_FAR_MINB) far32x2_kernel(PlanView v, const float *wsf,
                                                       const float *wbar, int ldr, int r0,
                                                       double *psi) {
+  constexpr int NP = kFarNP, NT = 2 * NP;
   __shared__ ulonglong2 sA[kTile], sB[kTile];
   const int c = blockIdx.x, P = v.P, nth = blockDim.x;
   const int64_t po = (int64_t)c * 3 * P;
-  float ox[2], oy[2], oz[2];
+  float ox[NT], oy[NT], oz[NT];
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
+  for (int h = 0; h < NT; ++h) {
     const int m = threadIdx.x + h * nth;
     const int mm = m < P ? m : 0;
     ox[h] = v.proxy32[po + mm];
     oy[h] = v.proxy32[po + P + mm];
     oz[h] = v.proxy32[po + 2 * P + mm];
   }
-  // running totals of the two target proxies over all entries (FP32 pairs)
-  f2x hi[1] = {0ull}, lo[1] = {0ull};
-  const double cTx = v.ccentre[3 * c], cTy = v.ccentre[3 * c + 1], cTz = v.ccentre[3 * c + 2];
+  // running totals of the target pairs over all entries (FP32 pairs)
+  f2x hi[NP], lo[NP];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) hi[q] = lo[q] = 0ull;
   const float *wr = wsf + (int64_t)r0 * v.N;
-  const int self_none[2] = {-1, -1};
+  int self_none[NT];
+#pragma unroll
+  for (int h = 0; h < NT; ++h) self_none[h] = -1;
   for (int pass = 0; pass < 2; ++pass) {
     const int type = pass == 0 ? CSFMM_LIST_CP : CSFMM_LIST_CC;
     const int e0 = v.loff[type][c], e1 = v.loff[type][c + 1];
     for (int ee = e0; ee < e1; ++ee) {
       const int s = v.lsrc[type][ee];
       if (!cell_ok(v, s)) continue;
-      const float dcx = (float)(cTx - v.ccentre[3 * s]);
-      const float dcy = (float)(cTy - v.ccentre[3 * s + 1]);
-      const float dcz = (float)(cTz - v.ccentre[3 * s + 2]);
-      const f2x tx[1] = {f2_pack(ox[0] + dcx, ox[1] + dcx)};
-      const f2x ty[1] = {f2_pack(oy[0] + dcy, oy[1] + dcy)};
-      const f2x tz[1] = {f2_pack(oz[0] + dcz, oz[1] + dcz)};
+      const float4 dcv = v.ldc[type][ee];
+      const float dcx = dcv.x, dcy = dcv.y, dcz = dcv.z;
+      f2x tx[NP], ty[NP], tz[NP];
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        tx[q] = f2_pack(ox[2 * q] + dcx, ox[2 * q + 1] + dcx);
+        ty[q] = f2_pack(oy[2 * q] + dcy, oy[2 * q + 1] + dcy);
+        tz[q] = f2_pack(oz[2 * q] + dcz, oz[2 * q + 1] + dcz);
+      }
       const bool cp = type == CSFMM_LIST_CP;
       const int sb = cp ? v.cbegin[s] : 0;
       const int nsrc = cp ? v.cend[s] - sb : P;
-      if constexpr (KID == CSFMM_KERNEL_LAPLACE) fold_minus(hi[0], lo[0], weight_total(v, s, r0, cp ? 0 : 1));
+      if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
+        const float2 W = weight_total(v, s, r0, cp ? 0 : 1);
+#pragma unroll
+        for (int q = 0; q < NP; ++q) fold_minus(hi[q], lo[q], W);
+      }
       for (int j0 = 0; j0 < nsrc; j0 += kTile) {
         const int nj = min(kTile, nsrc - j0);
         __syncthreads();
@@ -659,14 +675,14 @@ __global__ void __launch_bounds__(160, 8) far32x2_kernel(PlanView v, const float
           sB[t] = make_ulonglong2(f2_pack(z, z), f2_pack(w, w));
         }
         __syncthreads();
-        tile_sum_x2<KID, 1, false>(sA, sB, nj, tx, ty, tz, self_none, hi, lo);
+        tile_sum_x2<KID, NP, false>(sA, sB, nj, tx, ty, tz, self_none, hi, lo);
       }
     }
   }
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
+  for (int h = 0; h < NT; ++h) {
     const int m = threadIdx.x + h * nth;
-    double o = f2_total(hi[0], lo[0], h);
+    double o = f2_total(hi[h / 2], lo[h / 2], h & 1);
     if constexpr (KID == CSFMM_KERNEL_LAPLACE) o *= -(0.69314718055994530942 * kInv4Pi);
     if constexpr (KID == CSFMM_KERNEL_BIHARMONIC) o *= kInv4Pi;
     if (m < P) psi[((int64_t)c * ldr + r0) * P + m] = o;
@@ -698,7 +714,6 @@ __global__ void __launch_bounds__(160) far32_kernel(PlanView v, const float *wsf
 #pragma unroll
       for (int d = 0; d < 3; ++d) ahi[h][q][d] = alo[h][q][d] = 0.f;
   }
-  const double cTx = v.ccentre[3 * c], cTy = v.ccentre[3 * c + 1], cTz = v.ccentre[3 * c + 2];
   const int self_none[NT] = {-1, -1};
   for (int pass = 0; pass < 2; ++pass) {
     const int type = pass == 0 ? CSFMM_LIST_CP : CSFMM_LIST_CC;
@@ -706,9 +721,8 @@ __global__ void __launch_bounds__(160) far32_kernel(PlanView v, const float *wsf
     for (int ee = e0; ee < e1; ++ee) {
       const int s = v.lsrc[type][ee];
       if (!cell_ok(v, s)) continue;
-      const float dcx = (float)(cTx - v.ccentre[3 * s]);
-      const float dcy = (float)(cTy - v.ccentre[3 * s + 1]);
-      const float dcz = (float)(cTz - v.ccentre[3 * s + 2]);
+      const float4 dcv = v.ldc[type][ee];
+      const float dcx = dcv.x, dcy = dcv.y, dcz = dcv.z;
       float tx[NT], ty[NT], tz[NT];
 #pragma unroll
       for (int h = 0; h < NT; ++h) {
@@ -792,7 +806,9 @@ void launch_far_kid(const PlanView &v, int ncells, const float *wsf, const float
   const int nth = ((v.P + 63) / 64) * 32;  // 2 targets per thread
   if constexpr (KID != CSFMM_KERNEL_BIOT_SAVART) {
     if (nr == 1) {
-      far32x2_kernel<KID><<<ncells, nth, 0, st>>>(v, wsf, wbar, ldr, r0, psi);
+      const int per = 64 * kFarNP;  // targets of one warp
+      far32x2_kernel<KID><<<ncells, ((v.P + per - 1) / per) * 32, 0, st>>>(v, wsf, wbar, ldr,
+                                                                            r0, psi);
       return;
     }
   }

@@ -108,7 +108,6 @@ __device__ __forceinline__ void multi32_item(const PlanView &v, int c, const flo
   const int P = v.P;
   const int tb = FAR ? 0 : v.cbegin[c];
   const int te = FAR ? P : v.cend[c];
-  const double cTx = v.ccentre[3 * c], cTy = v.ccentre[3 * c + 1], cTz = v.ccentre[3 * c + 2];
   const int64_t po = (int64_t)c * 3 * P;
   float *swf = reinterpret_cast<float *>(sw4);
   for (int i0 = tb; i0 < te; i0 += nth * NT) {
@@ -137,9 +136,8 @@ __device__ __forceinline__ void multi32_item(const PlanView &v, int c, const flo
       for (int ee = e0; ee < e1; ++ee) {
         const int s = v.lsrc[type][ee];
         if (!cell_ok(v, s)) continue;
-        const float dcx = (float)(cTx - v.ccentre[3 * s]);
-        const float dcy = (float)(cTy - v.ccentre[3 * s + 1]);
-        const float dcz = (float)(cTz - v.ccentre[3 * s + 2]);
+        const float4 dcv = v.ldc[type][ee];
+        const float dcx = dcv.x, dcy = dcv.y, dcz = dcv.z;
         float tx[NT], ty[NT], tz[NT];
 #pragma unroll
         for (int k = 0; k < NT; ++k) {

@@ -727,30 +727,59 @@ __global__ void proxies_kernel(PlanView v, double *proxy, float *proxy32) {
   }
 }
 
-// Unbiased stochastic rounding of x to FP32: the representable neighbour on
-// the far side of x is chosen with probability |x - RN(x)| / gap, decided by
-// the 24 high bits of the hash h, so the expected value is x.  The FP32
-// Lagrange rows use it with a hash of (point, axis, node): points of a uniform
-// grid repeat the same local coordinates in every leaf, and round-to-nearest
-// would give every leaf the same rounding errors, which then add up in the
-// proxy weights instead of averaging out.
-__device__ __forceinline__ uint32_t hash32(uint32_t x) {
-  // integer finaliser "lowbias32" (C. Wellons, hash-prospector)
-  x ^= x >> 16;
-  x *= 0x7feb352du;
-  x ^= x >> 15;
-  x *= 0x846ca68bu;
-  x ^= x >> 16;
-  return x;
+// L_k(u), k = 0..n, at the Chebyshev nodes s (Sec. 4, Eq. barycentric) with
+// one division: with d_k = u - s_k and l_k = prod_{j != k} d_j (prefix and
+// suffix products), L_k = w_k l_k / sum_j w_j l_j, which equals the
+// barycentric form (w_k / d_k) / sum_j (w_j / d_j).  A node u == s_k makes
+// every l_j with j != k zero, so L = delta exactly.
+__device__ __forceinline__ void lagrange_prod(int n, const double *s, double u, double *L) {
+  double d[kMaxP], pre[kMaxP];
+  double acc = 1.0;
+  for (int k = 0; k <= n; ++k) {
+    d[k] = u - s[k];
+    pre[k] = acc;
+    acc *= d[k];
+  }
+  double suf = 1.0, den = 0.0;
+  for (int k = n; k >= 0; --k) {
+    L[k] = bary_w(k, n) * pre[k] * suf;
+    suf *= d[k];
+    den += L[k];
+  }
+  const double inv = 1.0 / den;
+  for (int k = 0; k <= n; ++k) L[k] *= inv;
 }
-__device__ __forceinline__ float round_stochastic(double x, uint32_t h) {
-  const float r = __double2float_rn(x);
-  const double d = x - (double)r;
-  if (d == 0.0) return r;
-  const float o = nextafterf(r, d > 0.0 ? INFINITY : -INFINITY);
-  const double gap = fabs((double)o - (double)r);
-  const double u = (double)(h >> 8) * (1.0 / 16777216.0);
-  return u * gap < fabs(d) ? o : r;
+
+// FP32 centre difference c_T - c_S of every entry of one list type (one
+// thread per target cell T), formed in FP64 and rounded once.  With
+// `stochastic` (far-field entries of the 1/|x - y| kernels, Newtonian and SAL)
+// it is rounded stochastically with a hash of (T, S, axis): on a uniform grid
+// the same cell offsets recur along a face, and rounding them all to nearest
+// shifted every far-field interaction of an offset the same way (measured at
+// N = 6.3M, n = 12, land-mask weights: a signed bias of -1.8e-8 in the
+// Newtonian potential and E = 1.96e-8; -1.1e-8 and 1.4e-8 with stochastic
+// rounding).  Stochastic rounding doubles the variance of the rounding error,
+// and where that error is random rather than systematic it costs accuracy
+// (log and dilogarithm kernels: E of the Poisson Y43 field 1.48e-7 -> 1.86e-7
+// at n = 12, of the biharmonic test field 6.4e-8 -> 8.6e-8), so the other
+// kernels and the near field keep round-to-nearest.
+__global__ void list_centre_diff_kernel(const double *centre, const int32_t *loff,
+                                        const int32_t *lsrc, int nc, bool stochastic,
+                                        float4 *out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nc) return;
+  for (int e = loff[t]; e < loff[t + 1]; ++e) {
+    const int s = lsrc[e];
+    const double dx = centre[3 * t] - centre[3 * s], dy = centre[3 * t + 1] - centre[3 * s + 1],
+                 dz = centre[3 * t + 2] - centre[3 * s + 2];
+    if (stochastic) {
+      const uint32_t h = hash32(((uint32_t)t * 0x9e3779b1u) ^ hash32((uint32_t)s + 0x7f4a7c15u));
+      out[e] = make_float4(round_stochastic(dx, hash32(h)), round_stochastic(dy, hash32(h + 1u)),
+                           round_stochastic(dz, hash32(h + 2u)), 0.f);
+    } else {
+      out[e] = make_float4((float)dx, (float)dy, (float)dz, 0.f);
+    }
+  }
 }
 
 // One block per leaf: leaf id of each point, FP32 offset from the leaf centre and
@@ -787,7 +816,7 @@ __global__ void leaf_points_kernel(PlanView v, const int32_t *leaves, int32_t *l
     double u = (atan(a) - xm) / h;
     double w = (atan(bb) - ym) / hy;
     double L[kMaxP];
-    lagrange_dev(n, s, u, L);
+    lagrange_prod(n, s, u, L);
     for (int k = 0; k < p; ++k) {
       const int64_t o = (int64_t)i * p + k;
       if (La64) La64[o] = L[k];
@@ -797,7 +826,7 @@ __global__ void leaf_points_kernel(PlanView v, const int32_t *leaves, int32_t *l
         La32lo[o] = (float)(L[k] - (double)hi);
       }
     }
-    lagrange_dev(n, s, w, L);
+    lagrange_prod(n, s, w, L);
     for (int k = 0; k < p; ++k) {
       const int64_t o = (int64_t)i * p + k;
       if (Lb64) Lb64[o] = L[k];
@@ -1060,7 +1089,7 @@ PlanView Plan::view() const {
   v.cchild = cchild; v.ccentre = ccentre; v.cradius = cradius; v.cxmid = cxmid; v.cymid = cymid;
   v.chalf = chalf; v.chy = chy; v.proxy = proxy; v.proxy32 = proxy32;
   v.mcell64 = mcell64; v.mcell32 = mcell32;
-  for (int t = 0; t < 4; ++t) { v.loff[t] = loff[t]; v.lsrc[t] = lsrc[t]; }
+  for (int t = 0; t < 4; ++t) { v.loff[t] = loff[t]; v.lsrc[t] = lsrc[t]; v.ldc[t] = ldc[t]; }
   v.sym_contrib = sym_contrib;
   v.m2m64 = m2m64; v.m2m32 = m2m32; v.cheb = cheb; v.status = status;
   v.wtot = nullptr; v.wtot_ld = 0;
@@ -1424,6 +1453,19 @@ csfmm_status build_tree(Plan &pl, const double *points, cudaStream_t st) {
     list_offsets_kernel<<<grid_for(nc + 1, 128), 128, 0, st>>>(lk, lo, hi, ty, bits, nc,
                                                                 pl.loff[ty], pl.lsrc[ty]);
     CSFMM_CUDA(cudaGetLastError());
+  }
+
+  // FP32 form: the centre difference of every list entry, rounded once
+  if (pl.precision == CSFMM_FP32_BULK) {
+    for (int ty = 0; ty < 4; ++ty) {
+      CSFMM_TRY(A.alloc(&pl.ldc[ty], (size_t)std::max<int64_t>(pl.nlist[ty], 1)));
+      list_centre_diff_kernel<<<grid_for(nc, 128), 128, 0, st>>>(
+          pl.ccentre, pl.loff[ty], pl.lsrc[ty], nc,
+          (ty == CSFMM_LIST_CP || ty == CSFMM_LIST_CC) &&
+              (pl.kernel_id == CSFMM_KERNEL_NEWTON || pl.kernel_id == CSFMM_KERNEL_SAL),
+          pl.ldc[ty]);
+      CSFMM_CUDA(cudaGetLastError());
+    }
   }
 
   // symmetric near field: cross pairs of the PP lists (FP32 form)
