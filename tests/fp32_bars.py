@@ -31,54 +31,54 @@ BARS = {
     "direct32-k2": 4e-7,  # measured 9.76e-08
     "direct32-k3": 8e-7,  # measured 1.93e-07
     "direct32-sal-land-m128": 8e-8,  # measured 1.78e-08
-    "fmm32-biharmonic-land-m128-n8": 4e-7,  # measured 8.64e-08
-    "fmm32-chunk-vs-single-k0": 2e-7,  # measured 4.58e-08
+    "fmm32-biharmonic-land-m128-n8": 3e-7,  # measured 6.33e-08
+    "fmm32-chunk-vs-single-k0": 2e-7,  # measured 4.57e-08
     "fmm32-chunk-vs-single-k1": 1e-10,  # measured 0.00e+00
     "fmm32-chunk-vs-single-k100": 7e-9,  # measured 1.66e-09
-    "fmm32-chunk-vs-single-k2": 2e-7,  # measured 2.73e-08
-    "fmm32-chunk-vs-single-k3": 2e-7,  # measured 3.89e-08
-    "fmm32-multi-k0-r16": 5e-7,  # measured 1.02e-07
-    "fmm32-multi-k1-r6": 2e-7,  # measured 4.55e-08
+    "fmm32-chunk-vs-single-k2": 1e-7,  # measured 2.47e-08
+    "fmm32-chunk-vs-single-k3": 2e-7,  # measured 3.88e-08
+    "fmm32-multi-k0-r16": 4e-7,  # measured 8.78e-08
+    "fmm32-multi-k1-r6": 2e-7,  # measured 4.29e-08
     "fmm32-multi-k100-r8": 9e-8,  # measured 2.01e-08
-    "fmm32-multi-k2-r9": 3e-7,  # measured 5.54e-08
-    "fmm32-multi-k3-r16": 2e-6,  # measured 2.57e-07
+    "fmm32-multi-k2-r9": 3e-7,  # measured 5.39e-08
+    "fmm32-multi-k3-r16": 2e-6,  # measured 2.98e-07
     "fmm32-newton-land-6m-n12": 6e-8,  # measured 1.39e-08
-    "fmm32-newton-land-m256-n8": 5e-8,  # measured 1.08e-08
-    "fmm32-poisson-y43-m256-n8": 9e-7,  # measured 2.12e-07
-    "fmm32-poisson-y43-m64-n8": 9e-7,  # measured 2.23e-07
-    "fmm32-poisson16-1.5m-n10": 3e-7,  # measured 6.91e-08
-    "fmm32-sal-chunk-vs-single": 2e-8,  # measured 3.30e-09
-    "fmm32-sal-land-m128-n8": 9e-8,  # measured 2.04e-08
+    "fmm32-newton-land-m256-n8": 5e-8,  # measured 1.09e-08
+    "fmm32-poisson-y43-m256-n8": 7e-7,  # measured 1.74e-07
+    "fmm32-poisson-y43-m64-n8": 8e-7,  # measured 1.87e-07
+    "fmm32-poisson16-1.5m-n10": 3e-7,  # measured 6.22e-08
+    "fmm32-sal-chunk-vs-single": 8e-9,  # measured 1.82e-09
+    "fmm32-sal-land-m128-n8": 9e-8,  # measured 2.09e-08
     "fmm32-sal-multi-vs-oracle-fmm": 5e-7,  # measured 1.24e-07
-    "fmm32-sal-varres-shrink0": 1e-7,  # measured 2.31e-08
-    "fmm32-sal-varres-shrink1": 2e-7,  # measured 2.75e-08
-    "fmm32-schedule-k0-r1": 3e-7,  # measured 6.23e-08
-    "fmm32-shrunk-clustered-k0": 2e-7,  # measured 3.46e-08
-    "fmm32-shrunk-clustered-k1": 2e-6,  # measured 3.39e-07
-    "fmm32-shrunk-clustered-k2": 2e-7,  # measured 3.06e-08
-    "fmm32-shrunk-clustered-k3": 6e-7,  # measured 1.39e-07
-    "fmm32-sym-6m-mixed-k0": 3e-7,  # measured 5.88e-08
-    "fmm32-sym-6m-mixed-k2": 2e-7,  # measured 3.00e-08
-    "fmm32-sym-k0-mixed": 9e-7,  # measured 2.01e-07
-    "fmm32-sym-k0-positive": 5e-7,  # measured 1.05e-07
+    "fmm32-sal-varres-shrink0": 1e-7,  # measured 2.30e-08
+    "fmm32-sal-varres-shrink1": 2e-7,  # measured 2.73e-08
+    "fmm32-schedule-k0-r1": 3e-7,  # measured 5.49e-08
+    "fmm32-shrunk-clustered-k0": 2e-7,  # measured 3.76e-08
+    "fmm32-shrunk-clustered-k1": 2e-6,  # measured 3.37e-07
+    "fmm32-shrunk-clustered-k2": 2e-7,  # measured 2.74e-08
+    "fmm32-shrunk-clustered-k3": 6e-7,  # measured 1.41e-07
+    "fmm32-sym-6m-mixed-k0": 2e-7,  # measured 4.44e-08
+    "fmm32-sym-6m-mixed-k2": 2e-7,  # measured 3.01e-08
+    "fmm32-sym-k0-mixed": 8e-7,  # measured 1.93e-07
+    "fmm32-sym-k0-positive": 7e-7,  # measured 1.58e-07
     "fmm32-sym-k100-mixed": 8e-8,  # measured 1.83e-08
     "fmm32-sym-k100-positive": 6e-8,  # measured 1.43e-08
     "fmm32-sym-k2-mixed": 1e-5,  # measured 2.33e-06
-    "fmm32-sym-k2-positive": 2e-7,  # measured 3.12e-08
-    "fmm32-sym-k3-mixed": 1e-6,  # measured 2.38e-07
-    "fmm32-sym-k3-positive": 3e-7,  # measured 7.41e-08
-    "fmm32-sym-vs-2rhs-k0-mixed": 3e-7,  # measured 5.67e-08
+    "fmm32-sym-k2-positive": 2e-7,  # measured 3.11e-08
+    "fmm32-sym-k3-mixed": 9e-7,  # measured 2.21e-07
+    "fmm32-sym-k3-positive": 3e-7,  # measured 5.29e-08
+    "fmm32-sym-vs-2rhs-k0-mixed": 3e-7,  # measured 5.60e-08
     "fmm32-sym-vs-2rhs-k0-positive": 5e-8,  # measured 1.23e-08
     "fmm32-sym-vs-2rhs-k100-mixed": 9e-10,  # measured 2.24e-10
     "fmm32-sym-vs-2rhs-k100-positive": 2e-9,  # measured 2.63e-10
-    "fmm32-sym-vs-2rhs-k2-mixed": 3e-7,  # measured 5.71e-08
-    "fmm32-sym-vs-2rhs-k2-positive": 9e-9,  # measured 2.17e-09
-    "fmm32-sym-vs-2rhs-k3-mixed": 8e-8,  # measured 1.98e-08
-    "fmm32-sym-vs-2rhs-k3-positive": 3e-9,  # measured 6.10e-10
-    "fmm32-targets-k0": 4e-7,  # measured 8.09e-08
+    "fmm32-sym-vs-2rhs-k2-mixed": 2e-7,  # measured 4.31e-08
+    "fmm32-sym-vs-2rhs-k2-positive": 7e-9,  # measured 1.73e-09
+    "fmm32-sym-vs-2rhs-k3-mixed": 8e-8,  # measured 1.94e-08
+    "fmm32-sym-vs-2rhs-k3-positive": 3e-9,  # measured 6.08e-10
+    "fmm32-targets-k0": 3e-7,  # measured 7.45e-08
     "fmm32-targets-k1": 7e-6,  # measured 1.55e-06
-    "fmm32-targets-k2": 4e-7,  # measured 9.30e-08
-    "fmm32-targets-k3": 4e-7,  # measured 7.82e-08
+    "fmm32-targets-k2": 4e-7,  # measured 9.29e-08
+    "fmm32-targets-k3": 4e-7,  # measured 8.19e-08
 }
 
 

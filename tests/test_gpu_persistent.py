@@ -88,6 +88,40 @@ def test_persistent_equals_per_phase_ragged(torch, C, name, mk, n, theta, N0):
     assert np.array_equal(per, phase), name
 
 
+def test_persistent_separate_targets_and_workspaces(torch, C):
+    """Separate target points (outputs at the targets only) and two
+    concurrent evaluations on their own workspaces and streams: the persistent
+    launch equals the per-phase launches bit for bit."""
+    src, tgt = I.random_sphere_points(12000, 76), I.random_sphere_points(3000, 77)
+    W = np.random.default_rng(78).standard_normal((16, len(src))) / len(src)
+    outs = []
+    for nop in (False, True):
+        P = C.plan_create_targets(dev(torch, src), dev(torch, tgt), C.KERNEL_NEWTON, 7, 0.7, 60,
+                                  precision=C.FP32_BULK, max_nrhs=16, no_persistent=nop)
+        outs.append(C.evaluate(P, dev(torch, W)).cpu().numpy())
+        C.plan_sync(P)
+        C.plan_destroy(P)
+    assert outs[0].shape == (16, len(tgt), 1)
+    assert np.array_equal(outs[0], outs[1])
+    pts, A = I.cubed_sphere_grid(40)
+    P = C.plan_create(dev(torch, pts), C.KERNEL_LAPLACE, 7, 0.7, 50, precision=C.FP32_BULK,
+                      max_nrhs=16)
+    W1, W2 = dev(torch, _weights(pts, A, 16, seed=85)), dev(torch, _weights(pts, A, 16, seed=86))
+    ref1 = C.evaluate(P, W1).cpu().numpy()
+    ref2 = C.evaluate(P, W2).cpu().numpy()
+    ws1, ws2 = C.workspace_create(P, 16), C.workspace_create(P, 16)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    with torch.cuda.stream(s1):
+        o1 = C.evaluate_ws(P, ws1, W1, stream=s1.cuda_stream)
+    with torch.cuda.stream(s2):
+        o2 = C.evaluate_ws(P, ws2, W2, stream=s2.cuda_stream)
+    torch.cuda.synchronize()
+    C.plan_sync(P)
+    assert np.array_equal(o1.cpu().numpy(), ref1) and np.array_equal(o2.cpu().numpy(), ref2)
+    C.workspace_destroy(ws1)
+    C.workspace_destroy(ws2)
+
+
 def test_persistent_graph_replay_retargets_output(torch, C):
     pts, A = I.cubed_sphere_grid(40)
     plain = C.plan_create(dev(torch, pts), C.KERNEL_LAPLACE, 7, 0.7, 50, precision=C.FP32_BULK,
