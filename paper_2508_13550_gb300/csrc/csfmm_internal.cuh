@@ -454,14 +454,20 @@ __device__ __forceinline__ uint32_t hash32(uint32_t x) {
   x ^= x >> 16;
   return x;
 }
+// For x in the normal FP32 range the 29 low mantissa bits of the double are
+// the part below the FP32 rounding toward zero, as a fraction of its gap, so
+// the decision is integer work: round away from zero when 29 bits of the hash
+// fall below them.  Other values (zero, FP32 subnormals, overflow) round to
+// nearest.
 __device__ __forceinline__ float round_stochastic(double x, uint32_t h) {
-  const float r = __double2float_rn(x);
-  const double d = x - (double)r;
-  if (d == 0.0) return r;
-  const float o = nextafterf(r, d > 0.0 ? INFINITY : -INFINITY);
-  const double gap = fabs((double)o - (double)r);
-  const double u = (double)(h >> 8) * (1.0 / 16777216.0);
-  return u * gap < fabs(d) ? o : r;
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff) - 1023;  // unbiased binary exponent
+  if (e < -126 || e > 127) return __double2float_rn(x);
+  const uint32_t below = (uint32_t)(b & ((1u << 29) - 1));
+  const float t = __double2float_rz(x);
+  if ((h >> 3) >= below) return t;
+  const uint32_t tb = (uint32_t)__float_as_int(t);
+  return __int_as_float((int)(tb + 1u));  // the next FP32 value away from zero
 }
 
 // Checked builds (compiled with -DCSFMM_CHECKED, the stand-in for a memory
