@@ -60,10 +60,10 @@ def log(*a):
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2508_13550_gb300", "csrc", f)
                   for f in ("interact32.cu", "fp32_math.cuh")]
 TRAFFIC_PER_EVAL = {
-    "source_sha256": "c9ced554527b7479",
-    "pp_sym_kernel": (35.325952e6 + 129.473792e6) / 6083051520,
-    "near32x2_kernel": (233.098240e6 + 12.497920e6) / 3743870976,
-    "far32x2_kernel": 18.471680e6 / 1503908016,
+    "source_sha256": "497ac4cec1048274",
+    "pp_sym_kernel": (35.344896e6 + 129.297920e6) / 6083051520,
+    "near32x2_kernel": (236.997888e6 + 15.994112e6) / 3743870976,
+    "far32x2_kernel": 19.117312e6 / 1503908016,
 }
 
 
