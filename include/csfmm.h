@@ -131,16 +131,20 @@ typedef struct {
   int64_t launches_per_evaluate; /* kernels launched by the last evaluation */
   int64_t sym_pairs;       /* FP32 bulk: PP leaf pairs evaluated once for both directions */
   int64_t sym_evals;       /* kernel evaluations of those pairs (each serves two interactions) */
+  int64_t cc_sym_pairs;    /* FP32 bulk, scalar kernel: mirrored CC cell pairs evaluated once
+                              for both directions (P^2 kernel values each) */
 } csfmm_stats;
 
 /* Evaluation phases timed by csfmm_plan_phase_times.  With the persistent
  * launch (csfmm_options.no_persistent) the NEAR phase covers that whole
- * launch (far field, near field, L2L, L2P) and FAR, PPSYM, L2L, L2P are
- * empty. */
+ * launch (far field, near field, L2L, L2P) and CCSYM, FAR, PPSYM, L2L, L2P
+ * are empty. */
 enum {
   CSFMM_PHASE_GATHER = 0, CSFMM_PHASE_P2M = 1, CSFMM_PHASE_M2M = 2, CSFMM_PHASE_FAR = 3,
   CSFMM_PHASE_PPSYM = 4, /* FP32 bulk, one RHS: mirrored PP pairs (empty otherwise) */
-  CSFMM_PHASE_NEAR = 5, CSFMM_PHASE_L2L = 6, CSFMM_PHASE_L2P = 7, CSFMM_NUM_PHASES = 8
+  CSFMM_PHASE_NEAR = 5, CSFMM_PHASE_L2L = 6, CSFMM_PHASE_L2P = 7,
+  CSFMM_PHASE_CCSYM = 8, /* FP32 bulk, one RHS: mirrored CC pairs, before FAR (empty otherwise) */
+  CSFMM_NUM_PHASES = 9
 };
 
 /* Builds a plan on the current device: sorts the points into cubed-sphere
@@ -252,6 +256,9 @@ csfmm_status csfmm_evaluate_ws(csfmm_plan plan, csfmm_workspace ws, const double
  *   + 4 L (nrhs = 1, kernels other than Biot-Savart; L = floats of the
  *          mirrored-pair partial sums, about 2 N times the PP leaf pairs per
  *          leaf that have a mirror)
+ *   + 8 P C (nrhs = 1, kernels other than Biot-Savart; C = the mirrored CC
+ *          cell pairs, csfmm_stats.cc_sym_pairs)
+ *   + 4 (2 + 3 ncells) (kernels other than Biot-Savart: work counters)
  * with N the points of the plan (sources and targets), P = (n+1)^2.  Larger
  * requests fail with CSFMM_ERR_INVALID_ARG and a message that states the
  * size.  The first call on a device looks up the array's device address

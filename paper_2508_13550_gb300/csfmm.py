@@ -79,7 +79,7 @@ class Stats(ctypes.Structure):
                 ("pairs_covered", ctypes.c_int64), ("mac_margin", ctypes.c_double),
                 ("device_bytes", ctypes.c_int64), ("build_ms", ctypes.c_double),
                 ("launches_per_evaluate", ctypes.c_int64), ("sym_pairs", ctypes.c_int64),
-                ("sym_evals", ctypes.c_int64)]
+                ("sym_evals", ctypes.c_int64), ("cc_sym_pairs", ctypes.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -542,7 +542,7 @@ def plan_export_proxy_weights(plan: Plan, nrhs: int = 1):
     return wb
 
 
-PHASES = ("gather", "p2m", "m2m", "far", "ppsym", "near", "l2l", "l2p")
+PHASES = ("gather", "p2m", "m2m", "far", "ppsym", "near", "l2l", "l2p", "ccsym")
 
 
 def plan_enable_timing(plan: Plan, on: bool = True):

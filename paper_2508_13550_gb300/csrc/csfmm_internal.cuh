@@ -123,6 +123,7 @@ struct PlanView {
   // 1/|x - y| kernels)
   const float4 *ldc[4];
   const int32_t *sym_contrib;
+  const int32_t *cc_contrib;  // [nCC] partial-buffer offset of a mirrored CC entry, or -1
   const double *m2m64;   // [2][p][p]: M[q][k][m] = L_k((s_m + 2q - 1)/2)
   const float *m2m32;    // [2][2][p][p]: FP32 rounding of m2m64, then the remainders
   const double *cheb;    // [p]
@@ -215,6 +216,15 @@ struct Plan {
                                     // PP entry (-1: evaluated directly)
   int n_sym_pairs = 0;
   int64_t sym_part_len = 0;         // floats in one partial buffer
+  // Symmetric far field (FP32 bulk, one right-hand side, K(x,y) = K(y,x)):
+  // every CC entry (T, S), S > T, whose mirror (S, T) is also a CC entry is
+  // one pair whose P x P kernel matrix serves both; its partial sums (T's
+  // proxies, then S's) live at 2 P pair in the workspace's CC partial buffer.
+  int2 *cc_pairs = nullptr;         // [n_cc_pairs] (T, S), T < S
+  int32_t *cc_entry = nullptr;      // [n_cc_pairs] CC entry index of (T, S)
+  int32_t *cc_contrib = nullptr;    // [nCC] offset of the target cell's partials of this entry
+                                    // (-1: evaluated directly)
+  int n_cc_pairs = 0;
   double *m2m64 = nullptr;
   float *m2m32 = nullptr;
   double *cheb = nullptr;
@@ -275,6 +285,7 @@ struct Workspace {
   double *psi = nullptr;    // [nc][max_nrhs][dim][P] proxy potentials (FP64 in both forms)
   double *phi = nullptr;    // [max_nrhs][N][dim] near-field potentials, tree order
   float *sym_part = nullptr;     // [plan.sym_part_len] cross-pair partial sums (FP32 form)
+  float *cc_part = nullptr;      // [2 P plan.n_cc_pairs] mirrored CC pair partial sums (FP32 form)
   float2 *wtot = nullptr;        // [nc][max_nrhs][2] weight totals (FP32 form)
   int *ctr = nullptr;            // [2 + 3 nc] work counter and dependency counters of the
                                  // persistent kernel (FP32 form, scalar kernels)
@@ -333,8 +344,15 @@ void launch_multi32(const PlanView &v, bool far, int ngrid, const int32_t *leave
                     const float *wsf, const float *wbar, int ldr, int r0, int nr, double *phi,
                     double *psi, int schedule, cudaStream_t st);
 // FP32-bulk far field (interact32.cu): nr <= 4 right-hand sides from r0.
+// With cpart != nullptr (one right-hand side) the CC entries that belong to a
+// mirrored pair are read from the pairs' partials instead of being evaluated.
 void launch_far32(const PlanView &v, int ncells, const float *wsf, const float *wbar, int ldr,
-                  int r0, int nr, double *psi, cudaStream_t st);
+                  int r0, int nr, double *psi, cudaStream_t st, const float *cpart = nullptr);
+// Symmetric CC evaluation of the mirrored far-field pairs (interact32.cu), one
+// right-hand side, scalar kernels: proxy weights wbar [nc][ldr][P] in, the
+// pairs' partial sums out.
+void launch_cc_sym32(const PlanView &v, const int2 *pairs, const int32_t *entry, int npairs,
+                     const float *wbar, int ldr, float *part, cudaStream_t st);
 // Symmetric PP evaluation of the cross pairs (interact32.cu), one right-hand
 // side, scalar kernels; writes the pairs' partial sums into part.
 void launch_pp_sym32(const PlanView &v, const int2 *pairs, const int32_t *off, int npairs,

@@ -813,7 +813,8 @@ csfmm_status run_passes(Plan &pl, Workspace &W, const double *w, int nrhs, doubl
         return s0;
       ++pl.launches;
       CSFMM_END(CSFMM_PHASE_NEAR, st);
-      for (int ph : {CSFMM_PHASE_FAR, CSFMM_PHASE_PPSYM, CSFMM_PHASE_L2L, CSFMM_PHASE_L2P}) {
+      for (int ph : {CSFMM_PHASE_CCSYM, CSFMM_PHASE_FAR, CSFMM_PHASE_PPSYM, CSFMM_PHASE_L2L,
+                     CSFMM_PHASE_L2P}) {
         CSFMM_BEGIN(ph, st);  // empty: their work is inside the persistent launch
         CSFMM_END(ph, st);
       }
@@ -850,6 +851,19 @@ csfmm_status run_passes(Plan &pl, Workspace &W, const double *w, int nrhs, doubl
     if (multi && left >= 8 && pl.rhs_chunk >= 8) return 8;
     return min(kRB, left);
   };
+  // single right-hand side, symmetric scalar kernel: the mirrored CC pairs are
+  // evaluated once for both directions, then the far field reads their sums
+  const bool ccsym = sizeof(Real) == 4 && nrhs == 1 && KID != CSFMM_KERNEL_BIOT_SAVART &&
+                     pl.n_cc_pairs > 0 && W.cc_part != nullptr &&
+                     !(pl.schedule & CSFMM_SCHED_NO_SYMMETRIC);
+  CSFMM_BEGIN(CSFMM_PHASE_CCSYM, sf);
+  if constexpr (sizeof(Real) == 4) {
+    if (ccsym) {
+      launch_cc_sym32(v, pl.cc_pairs, pl.cc_entry, pl.n_cc_pairs, wbar, ldr, W.cc_part, sf);
+      ++pl.launches;
+    }
+  }
+  CSFMM_END(CSFMM_PHASE_CCSYM, sf);
   CSFMM_BEGIN(CSFMM_PHASE_FAR, sf);
   for (int r0 = 0; r0 < nrhs; r0 += chunk(r0)) {
     const int nr = chunk(r0);
@@ -858,7 +872,8 @@ csfmm_status run_passes(Plan &pl, Workspace &W, const double *w, int nrhs, doubl
         launch_multi32(v, true, pl.ncells, pl.leaves, W.wsf, wbar, ldr, r0, nr, W.phi, psi,
                        pl.schedule, sf);
       else
-        launch_far32(v, pl.ncells, W.wsf, wbar, ldr, r0, nr, psi, sf);
+        launch_far32(v, pl.ncells, W.wsf, wbar, ldr, r0, nr, psi, sf,
+                     ccsym ? W.cc_part : nullptr);
     } else {
       launch_far<KID, Real>(v, pl, W, nr, r0, tb_prox, wbar, psi, sf);
     }
@@ -1047,6 +1062,9 @@ csfmm_status workspace_alloc(Plan &pl, Workspace &W, int max_nrhs) {
       return s;
     if (pl.n_sym_pairs > 0 && pl.kernel_id != CSFMM_KERNEL_BIOT_SAVART &&
         (s = W.arena.alloc(&W.sym_part, (size_t)pl.sym_part_len)) != CSFMM_OK)
+      return s;
+    if (pl.n_cc_pairs > 0 &&
+        (s = W.arena.alloc(&W.cc_part, (size_t)2 * P * pl.n_cc_pairs)) != CSFMM_OK)
       return s;
   }
   if ((s = W.arena.alloc(&W.psi, nc * R * pl.dim * P)) != CSFMM_OK) return s;

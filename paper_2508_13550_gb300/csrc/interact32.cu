@@ -340,38 +340,60 @@ __device__ __forceinline__ float transpose_reduce(float (&v)[G], int lane) {
   return r;
 }
 
-template <int KID>
-__global__ void __launch_bounds__(kSymThreads, CSFMM_SYM_MINB) pp_sym_kernel(
-    PlanView v, const int2 *pairs, const int32_t *off, const float *wsf, float *part) {
-  constexpr int QP = kSymQP, G = kSymGroup;
+// CC = false: a mirrored PP leaf pair (rows: the points of T, columns: the
+// points of S, particle weights wsrc = wsf, partials at part + off[pair]).
+// CC = true: a mirrored CC cell pair (Sec. 5, Eq. CC: the kernel matrix
+// between the proxies of T and of S serves both entries), rows and columns
+// the P proxies of T and S, proxy weights wsrc = wbar [nc][ldr][P] of the
+// first right-hand side, the centre difference of CC entry entry[pair], and
+// partials at part + 2 P pair (P rows, then P columns).  QP packed row pairs
+// per lane.
+template <int KID, bool CC, int QP>
+__global__ void __launch_bounds__(kSymThreads, CSFMM_SYM_MINB) sym_kernel(
+    PlanView v, const int2 *pairs, const int32_t *off, const int32_t *entry, const float *wsrc,
+    int ldr, float *part) {
+  constexpr int G = kSymGroup;
+  constexpr int kRowsPerWarp = 2 * QP * 32;
+  constexpr int kRows = kRowsPerWarp * kSymWarps;  // rows per pass
   __shared__ ulonglong2 sA[kSymCols], sB[kSymCols];
   __shared__ float colacc[kSymWarps][kSymCols];
   const int2 pr = pairs[blockIdx.x];
   const int T = pr.x, S = pr.y;
   if (!cell_ok(v, T) || !cell_ok(v, S)) return;
-  const int tb = v.cbegin[T], te = v.cend[T], sb = v.cbegin[S], se = v.cend[S];
-  const int nT = te - tb, nS = se - sb;
-  float *rowpart = part + off[blockIdx.x];
+  const int P = v.P;
+  const int tb = CC ? 0 : v.cbegin[T], sb = CC ? 0 : v.cbegin[S];
+  const int nT = CC ? P : v.cend[T] - tb, nS = CC ? P : v.cend[S] - sb;
+  float *rowpart = part + (CC ? (int64_t)2 * P * blockIdx.x : (int64_t)off[blockIdx.x]);
   float *colpart = rowpart + nT;
+  const int64_t pT = (int64_t)T * 3 * P, pS = (int64_t)S * 3 * P;
+  const float *wT = CC ? wsrc + (int64_t)T * ldr * P : wsrc + tb;
+  const float *wS = CC ? wsrc + (int64_t)S * ldr * P : wsrc + sb;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const float dcx = (float)(v.ccentre[3 * T] - v.ccentre[3 * S]);
-  const float dcy = (float)(v.ccentre[3 * T + 1] - v.ccentre[3 * S + 1]);
-  const float dcz = (float)(v.ccentre[3 * T + 2] - v.ccentre[3 * S + 2]);
+  float dcx, dcy, dcz;
+  if constexpr (CC) {
+    const float4 d = v.ldc[CSFMM_LIST_CC][entry[blockIdx.x]];
+    dcx = d.x; dcy = d.y; dcz = d.z;
+  } else {
+    dcx = (float)(v.ccentre[3 * T] - v.ccentre[3 * S]);
+    dcy = (float)(v.ccentre[3 * T + 1] - v.ccentre[3 * S + 1]);
+    dcz = (float)(v.ccentre[3 * T + 2] - v.ccentre[3 * S + 2]);
+  }
   int lse = 0;
   float sg = 1.f;
   if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
     lse = log_scale_exp(v, T, S);
     sg = exp2i(lse);
   }
-  // log kernel: weight totals of T and S for -(ln2/4pi)(sum w log2 d2 - sum w)
+  // log kernel: weight totals of T and S (particles, or proxies for CC) for
+  // -(ln2/4pi)(sum w log2 d2 - sum w)
   double WT = 0.0, WS = 0.0;
   if constexpr (KID == CSFMM_KERNEL_LAPLACE) {
-    const float2 a = weight_total(v, T, 0, 0), b2 = weight_total(v, S, 0, 0);
+    const float2 a = weight_total(v, T, 0, CC ? 1 : 0), b2 = weight_total(v, S, 0, CC ? 1 : 0);
     WT = (double)a.x + (double)a.y;
     WS = (double)b2.x + (double)b2.y;
   }
-  for (int r0 = 0; r0 < nT; r0 += kSymRows) {
-    // rows of this lane: r0 + warp*kSymRowsPerWarp + lane + 32k, k = 0..2QP-1,
+  for (int r0 = 0; r0 < nT; r0 += kRows) {
+    // rows of this lane: r0 + warp*kRowsPerWarp + lane + 32k, k = 0..2QP-1,
     // packed as pairs (2q, 2q+1)
     f2x tx[QP], ty[QP], tz[QP], wr[QP], rhi[QP], rlo[QP];
     bool act[2 * QP];
@@ -381,14 +403,20 @@ __global__ void __launch_bounds__(kSymThreads, CSFMM_SYM_MINB) pp_sym_kernel(
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int k = 2 * q + h;
-        const int i = r0 + warp * kSymRowsPerWarp + lane + 32 * k;
+        const int i = r0 + warp * kRowsPerWarp + lane + 32 * k;
         act[k] = i < nT;
-        const int ii = tb + (act[k] ? i : 0);
-        const float4 o = v.off32[ii];
-        x[h] = (o.x + dcx) * sg;
-        y[h] = (o.y + dcy) * sg;
-        z[h] = (o.z + dcz) * sg;
-        w[h] = act[k] ? wsf[ii] : 0.f;
+        const int ii = act[k] ? i : 0;
+        float ox, oy, oz;
+        if constexpr (CC) {
+          ox = v.proxy32[pT + ii]; oy = v.proxy32[pT + P + ii]; oz = v.proxy32[pT + 2 * P + ii];
+        } else {
+          const float4 o = v.off32[tb + ii];
+          ox = o.x; oy = o.y; oz = o.z;
+        }
+        x[h] = (ox + dcx) * sg;
+        y[h] = (oy + dcy) * sg;
+        z[h] = (oz + dcz) * sg;
+        w[h] = act[k] ? wT[ii] : 0.f;
       }
       tx[q] = f2_pack(x[0], x[1]);
       ty[q] = f2_pack(y[0], y[1]);
@@ -403,9 +431,15 @@ __global__ void __launch_bounds__(kSymThreads, CSFMM_SYM_MINB) pp_sym_kernel(
       for (int t = threadIdx.x; t < kSymCols; t += kSymThreads) {
         float x = 1.0e4f, y = 1.0e4f, z = 1.0e4f, w = 0.f;  // padding: far away, no weight
         if (t < nj) {
-          const float4 o = v.off32[sb + c0 + t];
-          x = o.x * sg; y = o.y * sg; z = o.z * sg;
-          w = wsf[sb + c0 + t];
+          const int j = c0 + t;
+          if constexpr (CC) {
+            x = v.proxy32[pS + j] * sg; y = v.proxy32[pS + P + j] * sg;
+            z = v.proxy32[pS + 2 * P + j] * sg;
+          } else {
+            const float4 o = v.off32[sb + j];
+            x = o.x * sg; y = o.y * sg; z = o.z * sg;
+          }
+          w = wS[j];
         }
         sA[t] = make_ulonglong2(f2_pack(x, x), f2_pack(y, y));
         sB[t] = make_ulonglong2(f2_pack(z, z), f2_pack(w, w));
@@ -460,7 +494,7 @@ __global__ void __launch_bounds__(kSymThreads, CSFMM_SYM_MINB) pp_sym_kernel(
       for (int h = 0; h < 2; ++h) {
         const int k = 2 * q + h;
         if (!act[k]) continue;
-        const int i = r0 + warp * kSymRowsPerWarp + lane + 32 * k;
+        const int i = r0 + warp * kRowsPerWarp + lane + 32 * k;
         double val = f2_total(rhi[q], rlo[q], h);
         if constexpr (KID == CSFMM_KERNEL_LAPLACE) val -= (1 + 2 * lse) * WS;
         rowpart[i] = (float)val;
@@ -614,7 +648,7 @@ constexpr int kFarNP = CSFMM_FAR_NP;
 template <int KID>
 __global__ void __launch_bounds__(160, CSFMM_FAR_MINB) far32x2_kernel(PlanView v, const float *wsf,
                                                       const float *wbar, int ldr, int r0,
-                                                      double *psi) {
+                                                      double *psi, const float *cpart) {
   constexpr int NP = kFarNP, NT = 2 * NP;
   __shared__ ulonglong2 sA[kTile], sB[kTile];
   const int c = blockIdx.x, P = v.P, nth = blockDim.x;
@@ -642,6 +676,16 @@ __global__ void __launch_bounds__(160, CSFMM_FAR_MINB) far32x2_kernel(PlanView v
     for (int ee = e0; ee < e1; ++ee) {
       const int s = v.lsrc[type][ee];
       if (!cell_ok(v, s)) continue;
+      if (cpart && type == CSFMM_LIST_CC && v.cc_contrib[ee] >= 0) {
+        // a mirrored CC pair: this cell's sums come from the pair's partials
+        const float *pp = cpart + v.cc_contrib[ee];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+          const int m0 = threadIdx.x + 2 * q * nth, m1 = m0 + nth;
+          two_sum_fold(hi[q], lo[q], f2_pack(m0 < P ? pp[m0] : 0.f, m1 < P ? pp[m1] : 0.f));
+        }
+        continue;
+      }
       const float4 dcv = v.ldc[type][ee];
       const float dcx = dcv.x, dcy = dcv.y, dcz = dcv.z;
       f2x tx[NP], ty[NP], tz[NP];
@@ -806,13 +850,13 @@ __global__ void __launch_bounds__(160) far32_kernel(PlanView v, const float *wsf
 
 template <int KID>
 void launch_far_kid(const PlanView &v, int ncells, const float *wsf, const float *wbar, int ldr,
-                    int r0, int nr, double *psi, cudaStream_t st) {
+                    int r0, int nr, double *psi, cudaStream_t st, const float *cpart) {
   const int nth = ((v.P + 63) / 64) * 32;  // 2 targets per thread
   if constexpr (KID != CSFMM_KERNEL_BIOT_SAVART) {
     if (nr == 1) {
       const int per = 64 * kFarNP;  // targets of one warp
       far32x2_kernel<KID><<<ncells, ((v.P + per - 1) / per) * 32, 0, st>>>(v, wsf, wbar, ldr,
-                                                                            r0, psi);
+                                                                            r0, psi, cpart);
       return;
     }
   }
@@ -852,14 +896,14 @@ void launch_kid(const PlanView &v, const int32_t *leaves, int nleaves, const flo
 
 // nr right-hand sides r0 .. r0+nr-1 (nr <= 4); psi [nc][ldr][dim][P] FP64.
 void launch_far32(const PlanView &v, int ncells, const float *wsf, const float *wbar, int ldr,
-                  int r0, int nr, double *psi, cudaStream_t st) {
+                  int r0, int nr, double *psi, cudaStream_t st, const float *cpart) {
   switch (v.kernel_id) {
-    case CSFMM_KERNEL_LAPLACE: launch_far_kid<CSFMM_KERNEL_LAPLACE>(v, ncells, wsf, wbar, ldr, r0, nr, psi, st); break;
-    case CSFMM_KERNEL_BIOT_SAVART: launch_far_kid<CSFMM_KERNEL_BIOT_SAVART>(v, ncells, wsf, wbar, ldr, r0, nr, psi, st); break;
-    case CSFMM_KERNEL_NEWTON: launch_far_kid<CSFMM_KERNEL_NEWTON>(v, ncells, wsf, wbar, ldr, r0, nr, psi, st); break;
-    case CSFMM_KERNEL_SAL: launch_far_kid<CSFMM_KERNEL_SAL>(v, ncells, wsf, wbar, ldr, r0, nr, psi, st); break;
-    case CSFMM_KERNEL_BIHARMONIC: launch_far_kid<CSFMM_KERNEL_BIHARMONIC>(v, ncells, wsf, wbar, ldr, r0, nr, psi, st); break;
-    default: launch_far_kid<CSFMM_KERNEL_ONE>(v, ncells, wsf, wbar, ldr, r0, nr, psi, st); break;
+    case CSFMM_KERNEL_LAPLACE: launch_far_kid<CSFMM_KERNEL_LAPLACE>(v, ncells, wsf, wbar, ldr, r0, nr, psi, st, cpart); break;
+    case CSFMM_KERNEL_BIOT_SAVART: launch_far_kid<CSFMM_KERNEL_BIOT_SAVART>(v, ncells, wsf, wbar, ldr, r0, nr, psi, st, nullptr); break;
+    case CSFMM_KERNEL_NEWTON: launch_far_kid<CSFMM_KERNEL_NEWTON>(v, ncells, wsf, wbar, ldr, r0, nr, psi, st, cpart); break;
+    case CSFMM_KERNEL_SAL: launch_far_kid<CSFMM_KERNEL_SAL>(v, ncells, wsf, wbar, ldr, r0, nr, psi, st, cpart); break;
+    case CSFMM_KERNEL_BIHARMONIC: launch_far_kid<CSFMM_KERNEL_BIHARMONIC>(v, ncells, wsf, wbar, ldr, r0, nr, psi, st, cpart); break;
+    default: launch_far_kid<CSFMM_KERNEL_ONE>(v, ncells, wsf, wbar, ldr, r0, nr, psi, st, cpart); break;
   }
 }
 
@@ -880,12 +924,41 @@ void launch_near32(const PlanView &v, const int32_t *leaves, int nleaves, const 
 void launch_pp_sym32(const PlanView &v, const int2 *pairs, const int32_t *off, int npairs,
                      const float *wsf, float *part, cudaStream_t st) {
   if (npairs <= 0) return;
+#define CSFMM_PPSYM(K) \
+  sym_kernel<K, false, kSymQP><<<npairs, kSymThreads, 0, st>>>(v, pairs, off, nullptr, wsf, 0, part)
   switch (v.kernel_id) {
-    case CSFMM_KERNEL_LAPLACE: pp_sym_kernel<CSFMM_KERNEL_LAPLACE><<<npairs, kSymThreads, 0, st>>>(v, pairs, off, wsf, part); break;
-    case CSFMM_KERNEL_NEWTON: pp_sym_kernel<CSFMM_KERNEL_NEWTON><<<npairs, kSymThreads, 0, st>>>(v, pairs, off, wsf, part); break;
-    case CSFMM_KERNEL_SAL: pp_sym_kernel<CSFMM_KERNEL_SAL><<<npairs, kSymThreads, 0, st>>>(v, pairs, off, wsf, part); break;
-    case CSFMM_KERNEL_BIHARMONIC: pp_sym_kernel<CSFMM_KERNEL_BIHARMONIC><<<npairs, kSymThreads, 0, st>>>(v, pairs, off, wsf, part); break;
-    default: pp_sym_kernel<CSFMM_KERNEL_ONE><<<npairs, kSymThreads, 0, st>>>(v, pairs, off, wsf, part); break;
+    case CSFMM_KERNEL_LAPLACE: CSFMM_PPSYM(CSFMM_KERNEL_LAPLACE); break;
+    case CSFMM_KERNEL_NEWTON: CSFMM_PPSYM(CSFMM_KERNEL_NEWTON); break;
+    case CSFMM_KERNEL_SAL: CSFMM_PPSYM(CSFMM_KERNEL_SAL); break;
+    case CSFMM_KERNEL_BIHARMONIC: CSFMM_PPSYM(CSFMM_KERNEL_BIHARMONIC); break;
+    default: CSFMM_PPSYM(CSFMM_KERNEL_ONE); break;
+  }
+#undef CSFMM_PPSYM
+}
+
+namespace {
+template <int KID>
+void launch_cc_sym_kid(const PlanView &v, const int2 *pairs, const int32_t *entry, int npairs,
+                       const float *wbar, int ldr, float *part, cudaStream_t st) {
+  // row pairs per lane: the P rows of a pass with few idle lanes
+  if (v.P <= 128)
+    sym_kernel<KID, true, 2><<<npairs, kSymThreads, 0, st>>>(v, pairs, nullptr, entry, wbar, ldr, part);
+  else if (v.P <= 192)
+    sym_kernel<KID, true, 3><<<npairs, kSymThreads, 0, st>>>(v, pairs, nullptr, entry, wbar, ldr, part);
+  else
+    sym_kernel<KID, true, 4><<<npairs, kSymThreads, 0, st>>>(v, pairs, nullptr, entry, wbar, ldr, part);
+}
+}  // namespace
+
+void launch_cc_sym32(const PlanView &v, const int2 *pairs, const int32_t *entry, int npairs,
+                     const float *wbar, int ldr, float *part, cudaStream_t st) {
+  if (npairs <= 0) return;
+  switch (v.kernel_id) {
+    case CSFMM_KERNEL_LAPLACE: launch_cc_sym_kid<CSFMM_KERNEL_LAPLACE>(v, pairs, entry, npairs, wbar, ldr, part, st); break;
+    case CSFMM_KERNEL_NEWTON: launch_cc_sym_kid<CSFMM_KERNEL_NEWTON>(v, pairs, entry, npairs, wbar, ldr, part, st); break;
+    case CSFMM_KERNEL_SAL: launch_cc_sym_kid<CSFMM_KERNEL_SAL>(v, pairs, entry, npairs, wbar, ldr, part, st); break;
+    case CSFMM_KERNEL_BIHARMONIC: launch_cc_sym_kid<CSFMM_KERNEL_BIHARMONIC>(v, pairs, entry, npairs, wbar, ldr, part, st); break;
+    default: launch_cc_sym_kid<CSFMM_KERNEL_ONE>(v, pairs, entry, npairs, wbar, ldr, part, st); break;
   }
 }
 

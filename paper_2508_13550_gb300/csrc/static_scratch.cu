@@ -88,17 +88,21 @@ extern "C" csfmm_status csfmm_evaluate_static(csfmm_plan plan, const double *wei
   const size_t b_wsf = pl.precision == CSFMM_FP64 ? 0 : round256(R * N * sizeof(float));
   const size_t b_wtot = pl.precision == CSFMM_FP64 ? 0 : round256(nc * R * 2 * sizeof(float2));
   // FP32 bulk, one right-hand side, symmetric kernel: the partial sums of the
-  // mirrored PP leaf pairs, so that the same symmetric pass runs as in
-  // csfmm_evaluate
+  // mirrored PP leaf pairs and CC cell pairs, so that the same symmetric
+  // passes run as in csfmm_evaluate
   const bool sym = pl.precision != CSFMM_FP64 && nrhs == 1 && pl.n_sym_pairs > 0 &&
                    pl.kernel_id != CSFMM_KERNEL_BIOT_SAVART;
   const size_t b_sym = sym ? round256((size_t)pl.sym_part_len * sizeof(float)) : 0;
+  const size_t b_cc =
+      pl.precision != CSFMM_FP64 && nrhs == 1 && pl.n_cc_pairs > 0
+          ? round256((size_t)2 * P * pl.n_cc_pairs * sizeof(float))
+          : 0;
   // FP32 bulk, scalar kernels: the work and dependency counters of the
   // persistent launch (several right-hand sides)
   const size_t b_ctr = pl.precision != CSFMM_FP64 && pl.kernel_id != CSFMM_KERNEL_BIOT_SAVART
                            ? round256(persistent_counter_ints(pl) * sizeof(int))
                            : 0;
-  const size_t need = b_ws + b_wbar + b_psi + b_phi + b_wsf + b_wtot + b_sym + b_ctr;
+  const size_t need = b_ws + b_wbar + b_psi + b_phi + b_wsf + b_wtot + b_sym + b_ctr + b_cc;
   if (need > (size_t)CSFMM_STATIC_SCRATCH_BYTES) {
     set_error("this evaluation needs %zu bytes of scratch; the static scratch holds %zu bytes "
               "(use csfmm_evaluate, or fewer right-hand sides)",
@@ -127,5 +131,8 @@ extern "C" csfmm_status csfmm_evaluate_static(csfmm_plan plan, const double *wei
     W.sym_part = reinterpret_cast<float *>(base + b_ws + b_wbar + b_psi + b_phi + b_wsf + b_wtot);
   if (b_ctr)
     W.ctr = reinterpret_cast<int *>(base + b_ws + b_wbar + b_psi + b_phi + b_wsf + b_wtot + b_sym);
+  if (b_cc)
+    W.cc_part = reinterpret_cast<float *>(base + b_ws + b_wbar + b_psi + b_phi + b_wsf + b_wtot +
+                                          b_sym + b_ctr);
   return evaluate_impl(pl, W, weights, nrhs, out, (cudaStream_t)stream);
 }

@@ -1025,6 +1025,40 @@ __global__ void sym_contrib_kernel(const int32_t *off, const int32_t *src, int n
   }
 }
 
+// Mirrored CC pairs (T, S), T < S: the pair and the index of its CC entry.
+__global__ void cc_pair_emit_kernel(const int32_t *off, const int32_t *src, int ncells,
+                                    const int32_t *flag, const int32_t *pidx, int2 *pairs,
+                                    int32_t *entry) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncells) return;
+  for (int q = off[c]; q < off[c + 1]; ++q) {
+    if (!flag[q]) continue;
+    pairs[pidx[q]] = make_int2(c, src[q]);
+    entry[pidx[q]] = q;
+  }
+}
+
+// contrib[q] for CC entry q = (c, s): where cell c's proxy sums of this entry
+// start in the pair partials (2 P per pair: the rows, i.e. the proxies of
+// the lower cell, then the columns), -1 if the entry has no mirror.
+__global__ void cc_contrib_kernel(const int32_t *off, const int32_t *src, int ncells,
+                                  const int32_t *flag, const int32_t *pidx, int P,
+                                  int32_t *contrib) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncells) return;
+  for (int q = off[c]; q < off[c + 1]; ++q) {
+    const int s = src[q];
+    int val = -1;
+    if (s > c) {
+      if (flag[q]) val = 2 * P * pidx[q];
+    } else {
+      const int m = mirror_entry(off, src, s, c);
+      if (m >= 0 && flag[m]) val = 2 * P * pidx[m] + P;
+    }
+    contrib[q] = val;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Host driver.
 // ---------------------------------------------------------------------------
@@ -1091,6 +1125,7 @@ PlanView Plan::view() const {
   v.mcell64 = mcell64; v.mcell32 = mcell32;
   for (int t = 0; t < 4; ++t) { v.loff[t] = loff[t]; v.lsrc[t] = lsrc[t]; v.ldc[t] = ldc[t]; }
   v.sym_contrib = sym_contrib;
+  v.cc_contrib = cc_contrib;
   v.m2m64 = m2m64; v.m2m32 = m2m32; v.cheb = cheb; v.status = status;
   v.wtot = nullptr; v.wtot_ld = 0;
   return v;
@@ -1508,6 +1543,42 @@ csfmm_status build_tree(Plan &pl, const double *points, cudaStream_t st) {
       CSFMM_CUDA(cudaGetLastError());
       pl.n_sym_pairs = npairs;
       pl.sym_part_len = part_len;
+    }
+  }
+
+  // symmetric far field: mirrored CC pairs (FP32 form, scalar kernels); the
+  // partial offsets are int32, so a plan with 2 P npairs >= 2^31 keeps the
+  // direct evaluation
+  if (pl.precision == CSFMM_FP32_BULK && pl.kernel_id != CSFMM_KERNEL_BIOT_SAVART &&
+      pl.nlist[CSFMM_LIST_CC] > 0) {
+    const int ncc = (int)pl.nlist[CSFMM_LIST_CC];
+    int32_t *flag, *pidx;
+    CSFMM_TRY(tmp.alloc(&flag, ncc));
+    CSFMM_TRY(tmp.alloc(&pidx, ncc));
+    sym_flag_kernel<<<grid_for(nc, 128), 128, 0, st>>>(pl.loff[CSFMM_LIST_CC],
+                                                        pl.lsrc[CSFMM_LIST_CC], nc, flag);
+    CSFMM_CUDA(cudaGetLastError());
+    need = scan_tmp_elems(ncc);
+    if (need > scan_tmp_cap) {
+      CSFMM_TRY(tmp.alloc(&scan_tmp, need));
+      scan_tmp_cap = need;
+    }
+    int32_t npairs = 0;
+    CSFMM_TRY(exclusive_scan_i32(flag, pidx, ncc, &npairs, scan_tmp, st));
+    if (npairs > 0 && (int64_t)2 * pl.P * npairs < ((int64_t)1 << 31)) {
+      CSFMM_TRY(A.alloc(&pl.cc_pairs, npairs));
+      CSFMM_TRY(A.alloc(&pl.cc_entry, npairs));
+      CSFMM_TRY(A.alloc(&pl.cc_contrib, ncc));
+      cc_pair_emit_kernel<<<grid_for(nc, 128), 128, 0, st>>>(pl.loff[CSFMM_LIST_CC],
+                                                              pl.lsrc[CSFMM_LIST_CC], nc, flag,
+                                                              pidx, pl.cc_pairs, pl.cc_entry);
+      CSFMM_CUDA(cudaGetLastError());
+      cc_contrib_kernel<<<grid_for(nc, 128), 128, 0, st>>>(pl.loff[CSFMM_LIST_CC],
+                                                            pl.lsrc[CSFMM_LIST_CC], nc, flag,
+                                                            pidx, pl.P, pl.cc_contrib);
+      CSFMM_CUDA(cudaGetLastError());
+      pl.n_cc_pairs = npairs;
+      pl.stats.cc_sym_pairs = npairs;
     }
   }
 
