@@ -52,18 +52,19 @@ def log(*a):
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the FP32
 # interaction kernels per kernel evaluation, from one ncu capture of the
-# 6 x 512^2 Newtonian case (profiles/pp_sym_newton_1.5m.md and
-# profiles/near32x2_far32x2_newton_1.5m.md), valid only while the kernel
-# sources (interact32.cu, fp32_math.cuh) hash to the given SHA-256 prefix; the bench scales it to a launch by the
-# evaluations the launch performs (the traffic of these kernels grows with the
-# number of leaf pairs and points, as the evaluations do).
+# 6 x 512^2 Newtonian case (summarised under profiles/), valid only while the
+# kernel sources (interact32.cu, fp32_math.cuh) hash to the given SHA-256
+# prefix; the bench scales it to a launch by the evaluations the launch
+# performs (the traffic of these kernels grows with the number of leaf pairs,
+# cell pairs and points, as the evaluations do).
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2508_13550_gb300", "csrc", f)
                   for f in ("interact32.cu", "fp32_math.cuh")]
 TRAFFIC_PER_EVAL = {
-    "source_sha256": "497ac4cec1048274",
-    "pp_sym_kernel": (35.344896e6 + 129.297920e6) / 6083051520,
-    "near32x2_kernel": (236.997888e6 + 15.994112e6) / 3743870976,
-    "far32x2_kernel": 19.117312e6 / 1503908016,
+    "source_sha256": "6623d6568d7547fd",
+    "pp_sym_kernel": (35.288576e6 + 129.246976e6) / 6083051520,
+    "near32x2_kernel": (236.353792e6 + 9.826816e6) / 3743870976,
+    "far32x2_kernel": (40.254464e6 + 0.027648e6) / 615546672,
+    "cc_sym_kernel": 6.238464e6 / 444180672,
 }
 
 
@@ -624,6 +625,7 @@ def run_ours(args):
             alone[k] = {"ms_per_launch": m, "geval_per_s": e / (m / 1e3) / 1e9,
                         "frac_of_alu_peak": e / (m / 1e3) / peak_evals}
         line["kernels_alone"] = alone
+        line["phase_ms_alone"] = {k: v / max(c1, 1) for k, v in ph1.items()}
         line["kernels_alone_note"] = ("5 evaluations with every phase on one stream "
                                       "(CSFMM_SCHED_NO_OVERLAP), CUDA events per phase; "
                                       "plan_build_ms_warm_pool: a rebuild of that plan "

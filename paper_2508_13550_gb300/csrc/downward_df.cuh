@@ -138,7 +138,8 @@ template <int PC>
 __device__ __forceinline__ void l2p_df_leaf(const PlanView &v, int c, const double *psi, int ldr,
                                             int nrhs, int dim, const double *phi, double *out,
                                             float *sm) {
-  float *sph = sm, *spl = sm + kMaxP * kMaxP;
+  // proxy potentials as (hi, lo) pairs: one 8-byte shared load per term
+  float2 *sps = reinterpret_cast<float2 *>(sm);
   float *sLa = sm + 2 * kMaxP * kMaxP, *sLal = sLa + kL2PThreads * kMaxP;
   float *sLb = sLal + kL2PThreads * kMaxP, *sLbl = sLb + kL2PThreads * kMaxP;
   if (!cell_ok(v, c)) return;
@@ -162,8 +163,7 @@ __device__ __forceinline__ void l2p_df_leaf(const PlanView &v, int c, const doub
         for (int u = threadIdx.x; u < P; u += kL2PThreads) {
           const double x = __ldcg(psi + (((int64_t)c * ldr + r) * dim + d) * P + u);
           const float hi = (float)x;
-          sph[u] = hi;
-          spl[u] = (float)(x - (double)hi);
+          sps[u] = make_float2(hi, (float)(x - (double)hi));
         }
         __syncthreads();
         if (t < nj && v.perm[i] >= v.tbase) {
@@ -181,15 +181,19 @@ __device__ __forceinline__ void l2p_df_leaf(const PlanView &v, int c, const doub
             for (int m1 = 0; m1 < PC; ++m1) {
               float sh = 0.f, sl = 0.f;
 #pragma unroll
-              for (int m2 = 0; m2 < PC; ++m2)
-                df_fma(sh, sl, sph[m1 * PC + m2], spl[m1 * PC + m2], bh[m2], bl[m2]);
+              for (int m2 = 0; m2 < PC; ++m2) {
+                const float2 ps = sps[m1 * PC + m2];
+                df_fma(sh, sl, ps.x, ps.y, bh[m2], bl[m2]);
+              }
               df_fma(S, C, lah[m1], lal[m1], sh, sl);
             }
           } else {
             for (int m1 = 0; m1 < p; ++m1) {
               float sh = 0.f, sl = 0.f;
-              for (int m2 = 0; m2 < p; ++m2)
-                df_fma(sh, sl, sph[m1 * p + m2], spl[m1 * p + m2], lbh[m2], lbl[m2]);
+              for (int m2 = 0; m2 < p; ++m2) {
+                const float2 ps = sps[m1 * p + m2];
+                df_fma(sh, sl, ps.x, ps.y, lbh[m2], lbl[m2]);
+              }
               df_fma(S, C, lah[m1], lal[m1], sh, sl);
             }
           }

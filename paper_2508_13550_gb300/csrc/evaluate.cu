@@ -683,7 +683,7 @@ __global__ void __launch_bounds__(kL2PThreads) l2p_df_kernel(PlanView v, const i
                                                              const double *psi, int ldr, int nrhs,
                                                              int dim, const double *phi,
                                                              double *out) {
-  __shared__ float sm[kL2PDfSmemFloats];
+  __shared__ __align__(16) float sm[kL2PDfSmemFloats];
   l2p_df_leaf<PC>(v, leaves[blockIdx.x], psi, ldr, nrhs, dim, phi, out, sm);
 }
 

@@ -74,6 +74,17 @@ __device__ __forceinline__ void eval_x2(const ulonglong2 *__restrict__ sA,
   }
 }
 
+// Columns of a chunk unrolled in the packed tile sums.  The whole 32-column
+// chunk gives the scheduler the most independent kernel evaluations to
+// interleave with the MUFU operations; measured at N = 6.3M, n = 12: near
+// field 3.79 / 3.69 / 3.68 / 3.63 ms and far field 0.94 / 0.89 / 0.87 /
+// 0.80 ms for 4 / 8 / 16 / 32 (the register caps of the launch bounds kept;
+// lifting them measured slower).
+#ifndef CSFMM_X2_UNROLL
+#define CSFMM_X2_UNROLL 32
+#endif
+#define CSFMM_STR(x) #x
+#define CSFMM_UNROLL(n) _Pragma(CSFMM_STR(unroll n))
 template <int KID, int NP, bool SELF>
 __device__ __forceinline__ void tile_sum_x2(const ulonglong2 *__restrict__ sA,
                                             const ulonglong2 *__restrict__ sB, int nj,
@@ -85,7 +96,7 @@ __device__ __forceinline__ void tile_sum_x2(const ulonglong2 *__restrict__ sA,
     f2x acc[NP];
 #pragma unroll
     for (int q = 0; q < NP; ++q) acc[q] = 0ull;
-#pragma unroll 4
+CSFMM_UNROLL(CSFMM_X2_UNROLL)
     for (int jj = 0; jj < kChunk; ++jj) eval_x2<KID, NP, SELF>(sA, sB, jc + jj, tx, ty, tz, self, acc);
 #pragma unroll
     for (int q = 0; q < NP; ++q) two_sum_fold(hi[q], lo[q], acc[q]);
@@ -94,7 +105,7 @@ __device__ __forceinline__ void tile_sum_x2(const ulonglong2 *__restrict__ sA,
     f2x acc[NP];
 #pragma unroll
     for (int q = 0; q < NP; ++q) acc[q] = 0ull;
-#pragma unroll 4
+CSFMM_UNROLL(CSFMM_X2_UNROLL)
     for (int j = jc; j < nj; ++j) eval_x2<KID, NP, SELF>(sA, sB, j, tx, ty, tz, self, acc);
 #pragma unroll
     for (int q = 0; q < NP; ++q) two_sum_fold(hi[q], lo[q], acc[q]);
@@ -286,7 +297,9 @@ __global__ void __launch_bounds__(kThreads) near32_kernel(PlanView v, const int3
 // accumulates its rows' contributions to the group's columns, then a
 // butterfly transpose-reduction over the warp leaves the sum of column
 // g*kSymGroup + (lane mod kSymGroup) in that lane; the warps are combined in
-// a fixed order, so results are deterministic.
+// a fixed order, so results are deterministic.  The row sums are FP32 over
+// 32 columns (two groups), then folded into (hi, lo) pairs by two-sum, the
+// chunk width of the direct kernels.
 //
 // Per kernel evaluation the FP32 pipe does 8 lane-ops (3 differences, |r|^2,
 // the row and the column FMA) plus the column reduction, about
@@ -296,7 +309,13 @@ __global__ void __launch_bounds__(kThreads) near32_kernel(PlanView v, const int3
 // one pass) and groups of 16 columns, 16 blocks per SM (measured on the
 // N = 6.3M Newtonian workload: 6.98 ms against 7.16 ms for two warps with
 // four rows per lane and 32-column groups; 24 warps per SM with 16-column
-// groups were slower, 7.40-7.45 ms).
+// groups were slower, 7.40-7.45 ms; folding the row sums every 32 columns
+// instead of 16: 6.76 against 6.92 ms).  The instruction mix, not occupancy,
+// bounds this kernel: the FMA pipe is busy 76% of the cycles and the MUFU
+// 69% (a synthetic loop of 8 FP32 lane-ops and one MUFU op per value reaches
+// 92% of 16 values per clock per SM at 8 warps per SM); 12, 20 or 24 blocks
+// per SM, 8-column groups and a software-pipelined column loop measured the
+// same or slower.
 // ---------------------------------------------------------------------------
 #ifndef CSFMM_SYM_WARPS
 #define CSFMM_SYM_WARPS 1
@@ -446,10 +465,13 @@ __global__ void __launch_bounds__(kSymThreads, CSFMM_SYM_MINB) sym_kernel(
       }
       __syncthreads();
       const int ng = (nj + G - 1) / G;
+      f2x racc[QP];
       for (int g = 0; g < ng; ++g) {
-        f2x colv[G], racc[QP];
+        f2x colv[G];
+        if ((g & 1) == 0) {
 #pragma unroll
-        for (int q = 0; q < QP; ++q) racc[q] = 0ull;
+          for (int q = 0; q < QP; ++q) racc[q] = 0ull;
+        }
 #pragma unroll
         for (int j = 0; j < G; ++j) {
           const ulonglong2 A = sA[g * G + j], B = sB[g * G + j];
@@ -467,8 +489,10 @@ __global__ void __launch_bounds__(kSymThreads, CSFMM_SYM_MINB) sym_kernel(
             colv[j] = f2_fma(f, wr[q], colv[j]);
           }
         }
+        if ((g & 1) || g + 1 == ng) {
 #pragma unroll
-        for (int q = 0; q < QP; ++q) two_sum_fold(rhi[q], rlo[q], racc[q]);
+          for (int q = 0; q < QP; ++q) two_sum_fold(rhi[q], rlo[q], racc[q]);
+        }
         float cv[G];
 #pragma unroll
         for (int j = 0; j < G; ++j) {

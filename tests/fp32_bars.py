@@ -31,66 +31,66 @@ BARS = {
     "direct32-k2": 4e-7,  # measured 9.76e-08
     "direct32-k3": 8e-7,  # measured 1.93e-07
     "direct32-sal-land-m128": 8e-8,  # measured 1.78e-08
-    "fmm32-biharmonic-land-m128-n8": 3e-7,  # measured 6.33e-08
-    "fmm32-ccsym-k0-n8": 2e-7,  # measured 3.71e-08
-    "fmm32-ccsym-k2-n12": 2e-7,  # measured 3.30e-08
-    "fmm32-ccsym-k4-n8": 6e-7,  # measured 1.49e-07
+    "fmm32-biharmonic-land-m128-n8": 3e-7,  # measured 6.32e-08
+    "fmm32-ccsym-k0-n8": 2e-7,  # measured 4.02e-08
+    "fmm32-ccsym-k2-n12": 2e-7,  # measured 3.55e-08
+    "fmm32-ccsym-k4-n8": 7e-7,  # measured 1.63e-07
     "fmm32-ccsym-k3-n14": 9e-7,  # measured 2.14e-07
-    "fmm32-ccsym-k100-n12": 4e-8,  # measured 7.89e-09
-    "fmm32-ccsym-vs-direct-k0-n8": 2e-7,  # measured 4.30e-08
-    "fmm32-ccsym-vs-direct-k2-n12": 2e-7,  # measured 2.74e-08
-    "fmm32-ccsym-vs-direct-k4-n8": 6e-7,  # measured 1.46e-07
-    "fmm32-ccsym-vs-direct-k3-n14": 9e-8,  # measured 2.14e-08
-    "fmm32-ccsym-vs-direct-k100-n12": 4e-8,  # measured 7.83e-09
+    "fmm32-ccsym-k100-n12": 4e-8,  # measured 8.17e-09
+    "fmm32-ccsym-vs-direct-k0-n8": 2e-7,  # measured 4.03e-08
+    "fmm32-ccsym-vs-direct-k2-n12": 1e-7,  # measured 2.27e-08
+    "fmm32-ccsym-vs-direct-k4-n8": 5e-7,  # measured 1.22e-07
+    "fmm32-ccsym-vs-direct-k3-n14": 8e-8,  # measured 1.77e-08
+    "fmm32-ccsym-vs-direct-k100-n12": 3e-8,  # measured 5.47e-09
     "fmm32-ccsym-unbalanced-k2": 3e-5,  # measured 5.29e-06
-    "fmm32-ccsym-vs-direct-unbalanced-k2": 3e-7,  # measured 5.52e-08
-    "fmm32-chunk-vs-single-k0": 4e-7,  # measured 7.77e-08
+    "fmm32-ccsym-vs-direct-unbalanced-k2": 3e-7,  # measured 5.46e-08
+    "fmm32-chunk-vs-single-k0": 3e-7,  # measured 7.01e-08
     "fmm32-chunk-vs-single-k1": 1e-10,  # measured 0.00e+00
-    "fmm32-chunk-vs-single-k100": 7e-8,  # measured 1.62e-08
-    "fmm32-chunk-vs-single-k2": 2e-7,  # measured 4.33e-08
-    "fmm32-chunk-vs-single-k3": 5e-7,  # measured 1.08e-07
+    "fmm32-chunk-vs-single-k100": 5e-8,  # measured 1.20e-08
+    "fmm32-chunk-vs-single-k2": 2e-7,  # measured 3.33e-08
+    "fmm32-chunk-vs-single-k3": 4e-7,  # measured 9.74e-08
     "fmm32-multi-k0-r16": 4e-7,  # measured 8.92e-08
     "fmm32-multi-k1-r6": 2e-7,  # measured 4.30e-08
     "fmm32-multi-k100-r8": 9e-8,  # measured 2.20e-08
     "fmm32-multi-k2-r9": 3e-7,  # measured 5.31e-08
     "fmm32-multi-k3-r16": 2e-6,  # measured 2.96e-07
-    "fmm32-newton-land-6m-n12": 6e-8,  # measured 1.47e-08
-    "fmm32-newton-land-m256-n8": 5e-8,  # measured 1.14e-08
-    "fmm32-poisson-y43-m256-n8": 6e-7,  # measured 1.43e-07
-    "fmm32-poisson-y43-m64-n8": 6e-7,  # measured 1.50e-07
+    "fmm32-newton-land-6m-n12": 7e-8,  # measured 1.50e-08
+    "fmm32-newton-land-m256-n8": 5e-8,  # measured 1.19e-08
+    "fmm32-poisson-y43-m256-n8": 7e-7,  # measured 1.60e-07
+    "fmm32-poisson-y43-m64-n8": 7e-7,  # measured 1.72e-07
     "fmm32-poisson16-1.5m-n10": 3e-7,  # measured 6.03e-08
-    "fmm32-sal-chunk-vs-single": 6e-8,  # measured 1.36e-08
-    "fmm32-sal-land-m128-n8": 9e-8,  # measured 2.03e-08
+    "fmm32-sal-chunk-vs-single": 5e-8,  # measured 1.10e-08
+    "fmm32-sal-land-m128-n8": 9e-8,  # measured 2.13e-08
     "fmm32-sal-multi-vs-oracle-fmm": 5e-7,  # measured 1.24e-07
-    "fmm32-sal-varres-shrink0": 9e-8,  # measured 2.24e-08
-    "fmm32-sal-varres-shrink1": 1e-7,  # measured 2.27e-08
+    "fmm32-sal-varres-shrink0": 1e-7,  # measured 2.34e-08
+    "fmm32-sal-varres-shrink1": 1e-7,  # measured 2.39e-08
     "fmm32-schedule-k0-r1": 3e-7,  # measured 5.41e-08
-    "fmm32-shrunk-clustered-k0": 2e-7,  # measured 3.45e-08
+    "fmm32-shrunk-clustered-k0": 2e-7,  # measured 3.53e-08
     "fmm32-shrunk-clustered-k1": 2e-6,  # measured 3.37e-07
-    "fmm32-shrunk-clustered-k2": 2e-7,  # measured 2.70e-08
-    "fmm32-shrunk-clustered-k3": 6e-7,  # measured 1.43e-07
-    "fmm32-sym-6m-mixed-k0": 2e-7,  # measured 3.06e-08
-    "fmm32-sym-6m-mixed-k2": 2e-7,  # measured 2.72e-08
-    "fmm32-sym-k0-mixed": 7e-7,  # measured 1.52e-07
-    "fmm32-sym-k0-positive": 6e-7,  # measured 1.43e-07
-    "fmm32-sym-k100-mixed": 5e-8,  # measured 1.04e-08
-    "fmm32-sym-k100-positive": 4e-8,  # measured 8.25e-09
+    "fmm32-shrunk-clustered-k2": 2e-7,  # measured 2.63e-08
+    "fmm32-shrunk-clustered-k3": 6e-7,  # measured 1.44e-07
+    "fmm32-sym-6m-mixed-k0": 2e-7,  # measured 3.18e-08
+    "fmm32-sym-6m-mixed-k2": 2e-7,  # measured 3.04e-08
+    "fmm32-sym-k0-mixed": 7e-7,  # measured 1.62e-07
+    "fmm32-sym-k0-positive": 6e-7,  # measured 1.40e-07
+    "fmm32-sym-k100-mixed": 8e-8,  # measured 1.78e-08
+    "fmm32-sym-k100-positive": 6e-8,  # measured 1.45e-08
     "fmm32-sym-k2-mixed": 1e-5,  # measured 2.33e-06
-    "fmm32-sym-k2-positive": 2e-7,  # measured 3.09e-08
-    "fmm32-sym-k3-mixed": 1e-6,  # measured 2.30e-07
-    "fmm32-sym-k3-positive": 3e-7,  # measured 5.04e-08
-    "fmm32-sym-vs-2rhs-k0-mixed": 6e-7,  # measured 1.32e-07
-    "fmm32-sym-vs-2rhs-k0-positive": 2e-7,  # measured 4.90e-08
-    "fmm32-sym-vs-2rhs-k100-mixed": 2e-7,  # measured 3.24e-08
-    "fmm32-sym-vs-2rhs-k100-positive": 6e-8,  # measured 1.50e-08
-    "fmm32-sym-vs-2rhs-k2-mixed": 3e-7,  # measured 5.51e-08
-    "fmm32-sym-vs-2rhs-k2-positive": 5e-8,  # measured 1.00e-08
-    "fmm32-sym-vs-2rhs-k3-mixed": 4e-7,  # measured 7.87e-08
-    "fmm32-sym-vs-2rhs-k3-positive": 5e-8,  # measured 1.10e-08
+    "fmm32-sym-k2-positive": 2e-7,  # measured 3.14e-08
+    "fmm32-sym-k3-mixed": 1e-6,  # measured 2.34e-07
+    "fmm32-sym-k3-positive": 3e-7,  # measured 5.08e-08
+    "fmm32-sym-vs-2rhs-k0-mixed": 5e-7,  # measured 1.11e-07
+    "fmm32-sym-vs-2rhs-k0-positive": 2e-7,  # measured 4.58e-08
+    "fmm32-sym-vs-2rhs-k100-mixed": 1e-7,  # measured 2.38e-08
+    "fmm32-sym-vs-2rhs-k100-positive": 4e-8,  # measured 9.25e-09
+    "fmm32-sym-vs-2rhs-k2-mixed": 3e-7,  # measured 5.06e-08
+    "fmm32-sym-vs-2rhs-k2-positive": 3e-8,  # measured 7.47e-09
+    "fmm32-sym-vs-2rhs-k3-mixed": 3e-7,  # measured 6.64e-08
+    "fmm32-sym-vs-2rhs-k3-positive": 4e-8,  # measured 8.74e-09
     "fmm32-targets-k0": 3e-7,  # measured 7.45e-08
     "fmm32-targets-k1": 7e-6,  # measured 1.55e-06
-    "fmm32-targets-k2": 4e-7,  # measured 9.30e-08
-    "fmm32-targets-k3": 4e-7,  # measured 8.23e-08
+    "fmm32-targets-k2": 4e-7,  # measured 9.29e-08
+    "fmm32-targets-k3": 4e-7,  # measured 8.24e-08
 }
 
 
