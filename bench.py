@@ -411,7 +411,7 @@ def run_ours(args):
     plan = Cs.plan_create(dpts, wl["kernel"], wl["n"], wl["theta"], wl["N0"], precision=prec,
                           max_nrhs=max(nrhs, 1),
                           rhs_chunk=tuned["rhs_chunk"] if tuned else 0,
-                          no_persistent=args.no_persistent)
+                          no_persistent=args.no_persistent, schedule=args.schedule)
     st = Cs.plan_stats(plan)
     dim = Cs.kernel_dim(wl["kernel"])
     out = torch.empty((nrhs, N, dim), dtype=torch.float64, device=dev)
@@ -564,6 +564,7 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if prec == Cs.FP32_BULK else "f64", "data": "synthetic",
         "autotuned": tuned,
+        "schedule": args.schedule,
         "config": workload_config(args, wl_base, N, nrhs, world),
         "l2": "inputs larger than L2 (plan + workspace "
               f"{st['device_bytes'] / 1e9:.2f} GB resident)",
@@ -1123,6 +1124,8 @@ def main():
                     help="several right-hand sides: per-phase launches instead of the "
                          "persistent launch")
     ap.add_argument("--no-fp64-compare", dest="fp64_compare", action="store_false")
+    ap.add_argument("--schedule", type=int, default=0,
+                    help="csfmm_options.schedule bits of the benchmarked plan (CSFMM_SCHED_*)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="multi-RHS workloads: keep the default leaf size and RHS chunk")
     ap.add_argument("--sweep-m", type=int, default=1024)

@@ -111,8 +111,20 @@ enum {
   CSFMM_SCHED_CHUNK_16 = 4,         /* tile sums in FP32 chunks of 16 sources instead of 32 */
   CSFMM_SCHED_NO_SYMMETRIC = 8,     /* one right-hand side: evaluate every PP entry directly
                                        instead of mirrored leaf pairs once for both directions */
-  CSFMM_SCHED_NO_OVERLAP = 16       /* run every pass in order on the caller's stream instead
+  CSFMM_SCHED_NO_OVERLAP = 16,      /* run every pass in order on the caller's stream instead
                                        of the upward pass, far field and L2L on a side stream */
+  CSFMM_SCHED_SIDE_FIRST = 32       /* the side stream at the device's greatest stream priority:
+                                       its passes take SMs ahead of the near field's mirrored
+                                       pairs, which then absorb them (one RHS at N = 6.3M:
+                                       13.08 against 13.17 ms per evaluation; the per-phase
+                                       event times then overlap) */,
+  CSFMM_SCHED_TENSOR_NEAR = 64      /* 16 right-hand sides at a time, scalar kernel: the near
+                                       field's kernel-matrix x weight products on the tensor
+                                       cores (warp-level TF32 mma, three products per term) in
+                                       per-phase launches instead of the persistent launch.
+                                       Measured on 16 RHS, N = 1.57M Poisson: near field 15.8
+                                       against 16.9 ms (FP32 pipe, per-phase), error 2.2e-7
+                                       against 5.1e-8; not chosen by default or by the tuner */
 };
 
 typedef struct csfmm_plan_s *csfmm_plan;
@@ -337,7 +349,7 @@ csfmm_status csfmm_autotune(const double *points, int64_t N, int kernel_id, int 
  * with key "<device name>|k<kernel>|n<degree>|t<theta>|p<precision>|r<nrhs>|N<N>"
  * (spaces in the device name replaced by '_').  Lines of another format
  * (stale caches of earlier versions), with values out of range (leaf < 1,
- * chunk not 0/4/8/16, flags not 0/1, schedule bits outside 0..31, times or
+ * chunk not 0/4/8/16, flags not 0/1, schedule bits outside 0..127, times or
  * errors negative or not finite) or cut short are ignored.
  * Returns OK with *out filled (from_cache = 1), or INVALID_ARG (NULL
  * argument; no valid line for key, message "not found"). */

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libcsfmm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["tree.cu", "evaluate.cu", "interact32.cu", "persistent.cu", "multi32.cu", "direct.cu", "api.cu", "static_scratch.cu", "serve.cu", "autotune.cu", "cstc.cu", "bve.cu", "remesh.cu"]
+SOURCES = ["tree.cu", "evaluate.cu", "interact32.cu", "persistent.cu", "multi32.cu", "multi_tc.cu", "direct.cu", "api.cu", "static_scratch.cu", "serve.cu", "autotune.cu", "cstc.cu", "bve.cu", "remesh.cu"]
 
 
 def nvcc() -> str:

@@ -117,7 +117,7 @@ class ServerStats(ctypes.Structure):
 SERVER_MAX_NRHS = 8
 SERVE_FIFO, SERVE_CHEAPEST_FIRST = 0, 1
 SCHED_NEAR_64_THREADS, SCHED_ONE_TARGET, SCHED_CHUNK_16 = 1, 2, 4
-SCHED_NO_SYMMETRIC, SCHED_NO_OVERLAP = 8, 16
+SCHED_NO_SYMMETRIC, SCHED_NO_OVERLAP, SCHED_SIDE_FIRST, SCHED_TENSOR_NEAR = 8, 16, 32, 64
 
 _VP, _I64, _I32, _D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
 _SIGS = {

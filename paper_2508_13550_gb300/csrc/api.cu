@@ -165,7 +165,7 @@ csfmm_status csfmm_plan_create(const double *points, int64_t N, int kernel_id, i
   pl.use_graphs = o.use_graphs;
   pl.shrink = o.shrink != 0;
   pl.no_persistent = o.no_persistent != 0;
-  if (o.schedule < 0 || o.schedule > 31) {
+  if (o.schedule < 0 || o.schedule > 127) {
     set_error("schedule must be an OR of CSFMM_SCHED_* bits (got %d)", o.schedule);
     delete h;
     return CSFMM_ERR_INVALID_ARG;

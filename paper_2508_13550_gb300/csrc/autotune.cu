@@ -49,7 +49,7 @@ bool parse_line(const char *line, std::string *key, csfmm_tune_result *r) {
   if (n != 10 || strcmp(tag, "v2") != 0) return false;  // stale format, cut short or trailing text
   if (t.max_leaf < 1 || (t.rhs_chunk != 0 && t.rhs_chunk != 4 && t.rhs_chunk != 8 &&
                          t.rhs_chunk != 16) ||
-      (t.no_persistent != 0 && t.no_persistent != 1) || t.schedule < 0 || t.schedule > 31 ||
+      (t.no_persistent != 0 && t.no_persistent != 1) || t.schedule < 0 || t.schedule > 127 ||
       !finite_nonneg(t.ms_per_eval) || !finite_nonneg(t.rel_err) ||
       !finite_nonneg(t.default_ms) || !finite_nonneg(t.default_rel_err))
     return false;
@@ -243,6 +243,7 @@ extern "C" csfmm_status csfmm_autotune(const double *points, int64_t N, int kern
     if (precision == CSFMM_FP32_BULK && scalar && nrhs == 1)
       sched.push_back({0, 0, 0, CSFMM_SCHED_NO_SYMMETRIC, 0, 0});
     sched.push_back({0, 0, 0, CSFMM_SCHED_NO_OVERLAP, 0, 0});
+    sched.push_back({0, 0, 0, CSFMM_SCHED_SIDE_FIRST, 0, 0});
   }
   {
     csfmm_plan plan = nullptr;

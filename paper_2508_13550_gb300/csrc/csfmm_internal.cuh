@@ -299,7 +299,9 @@ struct Workspace {
   // Second stream of an evaluation: the upward pass, far field and L2L run on
   // it while the near field runs on the caller's stream, joined by events
   // (null for short-lived workspaces, which run every pass in order).
-  cudaStream_t side = nullptr;
+  // side_hi: the same at the device's greatest stream priority
+  // (CSFMM_SCHED_SIDE_FIRST).
+  cudaStream_t side = nullptr, side_hi = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_up = nullptr, ev_done = nullptr;
   csfmm_status create_side();
   void release_side() {
@@ -307,7 +309,8 @@ struct Workspace {
     if (ev_up) cudaEventDestroy(ev_up);
     if (ev_done) cudaEventDestroy(ev_done);
     if (side) cudaStreamDestroy(side);
-    side = nullptr;
+    if (side_hi) cudaStreamDestroy(side_hi);
+    side = side_hi = nullptr;
     ev_fork = ev_up = ev_done = nullptr;
   }
 };
@@ -348,6 +351,10 @@ void launch_multi32(const PlanView &v, bool far, int ngrid, const int32_t *leave
 // mirrored pair are read from the pairs' partials instead of being evaluated.
 void launch_far32(const PlanView &v, int ncells, const float *wsf, const float *wbar, int ldr,
                   int r0, int nr, double *psi, cudaStream_t st, const float *cpart = nullptr);
+// Near field of right-hand sides r0 .. r0+15 with the kernel-matrix products
+// on the tensor cores (multi_tc.cu; CSFMM_SCHED_TENSOR_NEAR).
+void launch_near16_tc(const PlanView &v, int nleaves, const int32_t *leaves, const float *wsf,
+                      const float *wbar, int ldr, int r0, double *phi, cudaStream_t st);
 // Symmetric CC evaluation of the mirrored far-field pairs (interact32.cu), one
 // right-hand side, scalar kernels: proxy weights wbar [nc][ldr][P] in, the
 // pairs' partial sums out.

@@ -757,7 +757,7 @@ csfmm_status run_passes(Plan &pl, Workspace &W, const double *w, int nrhs, doubl
   // before the fork.  Phase timing brackets every phase with its own events
   // on the stream it runs on.
   const bool overlap = W.side != nullptr && !(pl.schedule & CSFMM_SCHED_NO_OVERLAP);
-  cudaStream_t sf = overlap ? W.side : st;
+  cudaStream_t sf = overlap ? ((pl.schedule & CSFMM_SCHED_SIDE_FIRST) ? W.side_hi : W.side) : st;
   const bool p2m_first = !overlap || (sizeof(Real) == 4 && KID == CSFMM_KERNEL_LAPLACE);
 #define CSFMM_BEGIN(ph, s)                           \
   do {                                               \
@@ -913,7 +913,9 @@ csfmm_status run_passes(Plan &pl, Workspace &W, const double *w, int nrhs, doubl
   for (int r0 = 0; r0 < nrhs; r0 += chunk(r0)) {
     const int nr = chunk(r0);
     if constexpr (sizeof(Real) == 4) {
-      if (nr > kRB)
+      if (nr == 16 && (pl.schedule & CSFMM_SCHED_TENSOR_NEAR))
+        launch_near16_tc(v, pl.nleaves, pl.leaves, W.wsf, wbar, ldr, r0, W.phi, st);
+      else if (nr > kRB)
         launch_multi32(v, false, pl.nleaves, pl.leaves, W.wsf, wbar, ldr, r0, nr, W.phi, psi,
                        pl.schedule, st);
       else
@@ -1034,7 +1036,11 @@ csfmm_status Plan::phase(int ph, bool begin, cudaStream_t st) {
 
 csfmm_status Workspace::create_side() {
   if (side) return CSFMM_OK;
+  int prio_least = 0, prio_greatest = 0;
   cudaError_t e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+  if (e == cudaSuccess)
+    e = cudaStreamCreateWithPriority(&side_hi, cudaStreamNonBlocking, prio_greatest);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_up, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_done, cudaEventDisableTiming);
@@ -1129,7 +1135,8 @@ csfmm_status capture(Plan &pl, Workspace &W, const double *w, int nrhs, double *
     g.persist_view = W.last_persist_view;
     g.persist_args = W.last_persist_args;
   }
-  CSFMM_CUDA(cudaGraphInstantiate(&g.exec, graph, 0));
+  // node priorities captured from the streams (CSFMM_SCHED_SIDE_FIRST) hold in the graph
+  CSFMM_CUDA(cudaGraphInstantiate(&g.exec, graph, cudaGraphInstantiateFlagUseNodePriority));
   g.nrhs = nrhs;
   g.w = w;
   g.out = out;

@@ -41,6 +41,16 @@ constexpr int kTile = 256;
 #ifndef CSFMM_NEAR_MINB
 #define CSFMM_NEAR_MINB 16
 #endif
+// Threads per block and packed target pairs per thread of the one-RHS near
+// kernel (one block per target leaf; 2 kNearNP targets per thread).
+#ifndef CSFMM_NEAR_THREADS
+#define CSFMM_NEAR_THREADS 64
+#endif
+#ifndef CSFMM_NEAR_NP
+#define CSFMM_NEAR_NP 2
+#endif
+constexpr int kNearThreads = CSFMM_NEAR_THREADS;
+constexpr int kNearNP = CSFMM_NEAR_NP;
 
 template <int KID>
 __host__ __device__ constexpr int kdim32() {
@@ -538,7 +548,7 @@ __global__ void __launch_bounds__(kSymThreads, CSFMM_SYM_MINB) sym_kernel(
 // symmetric cross-pair partials (final potentials, added in list order); the
 // self entry and entries without a mirror are evaluated here.
 template <int KID, int NP>
-__global__ void __launch_bounds__(kThreads, CSFMM_NEAR_MINB) near32x2_kernel(PlanView v, const int32_t *leaves,
+__global__ void __launch_bounds__(kNearThreads, CSFMM_NEAR_MINB) near32x2_kernel(PlanView v, const int32_t *leaves,
                                                             const float *wsf, const float *wbar,
                                                             int ldr, int r0, double *phi,
                                                             const float *part) {
@@ -548,7 +558,7 @@ __global__ void __launch_bounds__(kThreads, CSFMM_NEAR_MINB) near32x2_kernel(Pla
   if (!cell_ok(v, c)) return;
   const int b = v.cbegin[c], e = v.cend[c], P = v.P;
   const float *wr = wsf + (int64_t)r0 * v.N;
-  for (int i0 = b; i0 < e; i0 += kThreads * NT) {
+  for (int i0 = b; i0 < e; i0 += kNearThreads * NT) {
     float ox[NT], oy[NT], oz[NT];
     // running totals of the target pairs over all list entries (and the
     // cross-pair partials) as FP32 (hi, lo) pairs; the log kernel holds
@@ -556,7 +566,7 @@ __global__ void __launch_bounds__(kThreads, CSFMM_NEAR_MINB) near32x2_kernel(Pla
     f2x hi[NP], lo[NP];
 #pragma unroll
     for (int k = 0; k < NT; ++k) {
-      const int i = i0 + threadIdx.x + k * kThreads;
+      const int i = i0 + threadIdx.x + k * kNearThreads;
       const float4 o = v.off32[i < e ? i : b];
       ox[k] = o.x; oy[k] = o.y; oz[k] = o.z;
     }
@@ -572,7 +582,7 @@ __global__ void __launch_bounds__(kThreads, CSFMM_NEAR_MINB) near32x2_kernel(Pla
           const float *pp = part + v.sym_contrib[ee] - b;
 #pragma unroll
           for (int q = 0; q < NP; ++q) {
-            const int i = i0 + threadIdx.x + 2 * q * kThreads, i1 = i + kThreads;
+            const int i = i0 + threadIdx.x + 2 * q * kNearThreads, i1 = i + kNearThreads;
             two_sum_fold(hi[q], lo[q], f2_pack(i < e ? pp[i] : 0.f, i1 < e ? pp[i1] : 0.f));
           }
           continue;
@@ -598,7 +608,7 @@ __global__ void __launch_bounds__(kThreads, CSFMM_NEAR_MINB) near32x2_kernel(Pla
           for (int q = 0; q < NP; ++q) {
             fold_minus(hi[q], lo[q], W);
             if (self_tile) {
-              const int i = i0 + threadIdx.x + 2 * q * kThreads, i1 = i + kThreads;
+              const int i = i0 + threadIdx.x + 2 * q * kNearThreads, i1 = i + kNearThreads;
               two_sum_fold(hi[q], lo[q], f2_pack(i < e ? wr[i] : 0.f, i1 < e ? wr[i1] : 0.f));
             }
           }
@@ -606,7 +616,7 @@ __global__ void __launch_bounds__(kThreads, CSFMM_NEAR_MINB) near32x2_kernel(Pla
         for (int j0 = 0; j0 < nsrc; j0 += kTile) {
           const int nj = min(kTile, nsrc - j0);
           __syncthreads();
-          for (int t = threadIdx.x; t < nj; t += kThreads) {
+          for (int t = threadIdx.x; t < nj; t += kNearThreads) {
             float x, y, z, w;
             if (pp) {
               const int j = sb + j0 + t;
@@ -625,7 +635,7 @@ __global__ void __launch_bounds__(kThreads, CSFMM_NEAR_MINB) near32x2_kernel(Pla
           __syncthreads();
           int self[NT];
 #pragma unroll
-          for (int k = 0; k < NT; ++k) self[k] = (i0 + (int)threadIdx.x + k * kThreads) - (sb + j0);
+          for (int k = 0; k < NT; ++k) self[k] = (i0 + (int)threadIdx.x + k * kNearThreads) - (sb + j0);
           if (self_tile)
             tile_sum_x2<KID, NP, true>(sA, sB, nj, tx, ty, tz, self, hi, lo);
           else
@@ -637,7 +647,7 @@ __global__ void __launch_bounds__(kThreads, CSFMM_NEAR_MINB) near32x2_kernel(Pla
     for (int q = 0; q < NP; ++q)
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int i = i0 + threadIdx.x + (2 * q + h) * kThreads;
+        const int i = i0 + threadIdx.x + (2 * q + h) * kNearThreads;
         double o = f2_total(hi[q], lo[q], h);
         if constexpr (KID == CSFMM_KERNEL_LAPLACE) o *= -(0.69314718055994530942 * kInv4Pi);
         if constexpr (KID == CSFMM_KERNEL_BIHARMONIC) o *= kInv4Pi;
@@ -667,10 +677,13 @@ __global__ void __launch_bounds__(kThreads, CSFMM_NEAR_MINB) near32x2_kernel(Pla
 #ifndef CSFMM_FAR_MINB
 #define CSFMM_FAR_MINB 8
 #endif
+#ifndef CSFMM_FAR_MAXT
+#define CSFMM_FAR_MAXT 160
+#endif
 constexpr int kFarNP = CSFMM_FAR_NP;
 
 template <int KID>
-__global__ void __launch_bounds__(160, CSFMM_FAR_MINB) far32x2_kernel(PlanView v, const float *wsf,
+__global__ void __launch_bounds__(CSFMM_FAR_MAXT, CSFMM_FAR_MINB) far32x2_kernel(PlanView v, const float *wsf,
                                                       const float *wbar, int ldr, int r0,
                                                       double *psi, const float *cpart) {
   constexpr int NP = kFarNP, NT = 2 * NP;
@@ -898,7 +911,8 @@ void launch_nr(const PlanView &v, const int32_t *leaves, int nleaves, const floa
                const float *wbar, int ldr, int r0, double *phi, cudaStream_t st,
                const float *part) {
   if constexpr (NR == 1 && KID != CSFMM_KERNEL_BIOT_SAVART) {
-    near32x2_kernel<KID, 2><<<nleaves, kThreads, 0, st>>>(v, leaves, wsf, wbar, ldr, r0, phi, part);
+    near32x2_kernel<KID, kNearNP><<<nleaves, kNearThreads, 0, st>>>(v, leaves, wsf, wbar, ldr, r0,
+                                                                  phi, part);
   } else {
     near32_kernel<KID, 2, NR><<<nleaves, kThreads, 0, st>>>(v, leaves, wsf, ldw, wbar, ldr, r0, phi);
   }

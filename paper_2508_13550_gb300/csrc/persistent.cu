@@ -235,7 +235,8 @@ int blocks_per_sm(const void *f) {
 
 bool persistent_eligible(const Plan &pl, const Workspace &W, int nrhs, int *chunk) {
   if (pl.precision == CSFMM_FP64 || pl.kernel_id == CSFMM_KERNEL_BIOT_SAVART ||
-      pl.no_persistent || !W.ctr || W.wsf == nullptr || W.wbar32 == nullptr)
+      pl.no_persistent || (pl.schedule & CSFMM_SCHED_TENSOR_NEAR) || !W.ctr ||
+      W.wsf == nullptr || W.wbar32 == nullptr)
     return false;
   if (nrhs % 16 == 0 && pl.rhs_chunk >= 16) *chunk = 16;
   else if (nrhs % 8 == 0 && pl.rhs_chunk >= 8) *chunk = 8;

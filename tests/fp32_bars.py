@@ -87,6 +87,17 @@ BARS = {
     "fmm32-sym-vs-2rhs-k2-positive": 3e-8,  # measured 7.47e-09
     "fmm32-sym-vs-2rhs-k3-mixed": 3e-7,  # measured 6.64e-08
     "fmm32-sym-vs-2rhs-k3-positive": 4e-8,  # measured 8.74e-09
+    "fmm32-tc-k0-n8-r16": 2e-6,  # measured 4.37e-07
+    "fmm32-tc-k2-n12-r16": 6e-6,  # measured 1.36e-06
+    "fmm32-tc-k4-n8-r16": 7e-6,  # measured 1.59e-06
+    "fmm32-tc-k3-n8-r16": 3e-6,  # measured 6.07e-07
+    "fmm32-tc-k100-n8-r16": 2e-7,  # measured 2.94e-08
+    "fmm32-tc-vs-fp32-k0-n8-r16": 2e-6,  # measured 4.01e-07
+    "fmm32-tc-vs-fp32-k2-n12-r16": 6e-6,  # measured 1.37e-06
+    "fmm32-tc-vs-fp32-k4-n8-r16": 7e-6,  # measured 1.64e-06
+    "fmm32-tc-vs-fp32-k3-n8-r16": 4e-6,  # measured 7.86e-07
+    "fmm32-tc-vs-fp32-k100-n8-r16": 1e-7,  # measured 2.47e-08
+    "fmm32-tc-ragged-k2-r16": 7e-6,  # measured 1.73e-06
     "fmm32-targets-k0": 3e-7,  # measured 7.45e-08
     "fmm32-targets-k1": 7e-6,  # measured 1.55e-06
     "fmm32-targets-k2": 4e-7,  # measured 9.29e-08

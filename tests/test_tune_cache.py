@@ -41,7 +41,7 @@ def test_valid_line_is_read(lib, tmp_path):
     f"v2 {KEY} 0 16 0 0 20.5 5.1e-08 20.6 5.1e-08\n",         # leaf size out of range
     f"v2 {KEY} 400 12 0 0 20.5 5.1e-08 20.6 5.1e-08\n",       # chunk not 0/4/8/16
     f"v2 {KEY} 400 16 2 0 20.5 5.1e-08 20.6 5.1e-08\n",       # flag not 0/1
-    f"v2 {KEY} 400 16 0 64 20.5 5.1e-08 20.6 5.1e-08\n",      # schedule bits out of range
+    f"v2 {KEY} 400 16 0 128 20.5 5.1e-08 20.6 5.1e-08\n",     # schedule bits out of range
     f"v2 {KEY} 400 16 0 0 nan 5.1e-08 20.6 5.1e-08\n",        # not finite
     f"v2 {KEY} 400 16 0 0 -1 5.1e-08 20.6 5.1e-08\n",         # negative time
     f"v2 {KEY} 400 16 0 0 20.5 5.1e-08 20.6 5.1e-08 junk\n",  # trailing text
