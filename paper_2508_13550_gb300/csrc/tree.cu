@@ -711,10 +711,16 @@ __global__ void proxies_kernel(PlanView v, double *proxy, float *proxy32) {
   int c = blockIdx.x;
   const int P = v.P, p = v.p;
   double cx = v.ccentre[3 * c], cy = v.ccentre[3 * c + 1], cz = v.ccentre[3 * c + 2];
+  // the p tangents of each face coordinate, shared by the P = p^2 proxies
+  // (blockDim >= 2 p)
+  __shared__ double ta[kMaxP], tb[kMaxP];
+  if (threadIdx.x < p) ta[threadIdx.x] = tan(v.cxmid[c] + v.chalf[c] * v.cheb[threadIdx.x]);
+  else if (threadIdx.x < 2 * p)
+    tb[threadIdx.x - p] = tan(v.cymid[c] + v.chy[c] * v.cheb[threadIdx.x - p]);
+  __syncthreads();
   for (int k = threadIdx.x; k < P; k += blockDim.x) {
     int k1 = k / p, k2 = k - k1 * p;
-    double a = tan(v.cxmid[c] + v.chalf[c] * v.cheb[k1]);
-    double b = tan(v.cymid[c] + v.chy[c] * v.cheb[k2]);
+    const double a = ta[k1], b = tb[k2];
     double x[3];
     face_point_rn(v.cface[c], a, b, x);
     int64_t o = (int64_t)c * 3 * P;
@@ -782,10 +788,93 @@ __global__ void list_centre_diff_kernel(const double *centre, const int32_t *lof
   }
 }
 
+// ---------------------------------------------------------------------------
+// Double-float arithmetic (value = h + l, |l| <= ulp(h)/2) for the FP32 form's
+// Lagrange rows: Knuth's two-sum and FMA-exact products, about 2^-46 relative
+// per operation, on the FP32 pipe (GB300's FP64 pipe runs 1/64 of its rate).
+// ---------------------------------------------------------------------------
+struct DF {
+  float h, l;
+};
+__device__ __forceinline__ DF df_norm(float s, float e) {  // |s| >= |e|
+  const float h = __fadd_rn(s, e);
+  return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ DF df_of(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ DF df_sub(DF a, DF b) {
+  const float s = __fsub_rn(a.h, b.h);
+  const float bb = __fsub_rn(s, a.h);
+  float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fadd_rn(-b.h, -bb));
+  e = __fadd_rn(e, __fsub_rn(a.l, b.l));
+  return df_norm(s, e);
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) { return df_sub(a, DF{-b.h, -b.l}); }
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, fmaf(a.l, b.h, e));
+  return df_norm(p, e);
+}
+__device__ __forceinline__ DF df_scale(DF a, float w) {  // w a power of two times +-1
+  return {a.h * w, a.l * w};
+}
+// 1 / b: FP32 quotient refined by one Newton step on the double-float residual
+__device__ __forceinline__ DF df_recip(DF b) {
+  const float q = __frcp_rn(b.h);
+  const DF r = df_sub(DF{1.f, 0.f}, df_mul(DF{q, 0.f}, b));  // 1 - q b, small
+  return df_norm(q, __fmul_rn(r.h, q));
+}
+
+// Lagrange rows of the FP32 form in double-float: the product form of
+// lagrange_prod with d_k = u - s_k, prefix and suffix products and one
+// reciprocal (the weights w_k are +-1 and +-1/2, exact scalings).  The
+// FP32 row value is then rounded stochastically from (h, l): away from h
+// toward h + l's side with probability |l| / gap, decided by the hash, so the
+// expected value is h + l; the remainder is (h - chosen) + l.
+__device__ __forceinline__ void lagrange_rows_df(int n, const DF *sd, double u, uint32_t hbase,
+                                                 uint32_t hstep, float *hi_out, float *lo_out) {
+  DF d[kMaxP], pre[kMaxP];
+  const DF ud = df_of(u);
+  DF acc{1.f, 0.f};
+  for (int k = 0; k <= n; ++k) {
+    d[k] = df_sub(ud, sd[k]);
+    pre[k] = acc;
+    acc = df_mul(acc, d[k]);
+  }
+  DF L[kMaxP];
+  DF suf{1.f, 0.f}, den{0.f, 0.f};
+  for (int k = n; k >= 0; --k) {
+    const float w = ((k & 1) ? -1.f : 1.f) * ((k == 0 || k == n) ? 0.5f : 1.f);
+    L[k] = df_scale(df_mul(pre[k], suf), w);
+    suf = df_mul(suf, d[k]);
+    den = df_add(den, L[k]);
+  }
+  const DF inv = df_recip(den);
+  for (int k = 0; k <= n; ++k) {
+    const DF x = df_mul(L[k], inv);
+    float hi = x.h;
+    if (x.l != 0.f) {
+      const uint32_t hb = (uint32_t)__float_as_int(x.h);
+      // the neighbour of h on the side of h + l
+      const bool away = (x.l > 0.f) == (x.h > 0.f);
+      const float nb = __int_as_float((int)(away ? hb + 1u : hb - 1u));
+      const float gap = fabsf(__fsub_rn(nb, x.h));
+      const float prob = __fdiv_rn(fabsf(x.l), gap);
+      const uint32_t hh = hash32(hbase + hstep * (uint32_t)k);
+      if (((float)(hh >> 8) + 0.5f) * 5.9604644775390625e-8f < prob) hi = nb;
+    }
+    hi_out[k] = hi;
+    lo_out[k] = __fadd_rn(__fsub_rn(x.h, hi), x.l);
+  }
+}
+
 // One block per leaf: leaf id of each point, FP32 offset from the leaf centre and
 // the Lagrange values in the leaf's local coordinates (FP64 rows for the FP64
 // form; stochastically rounded FP32 rows plus their FP32 remainders for the
-// FP32 form).
+// FP32 form, formed in double-float).
 __global__ void leaf_points_kernel(PlanView v, const int32_t *leaves, int32_t *leaf_of,
                                    float4 *off32, double *La64, double *Lb64, float *La32,
                                    float *Lb32, float *La32lo, float *Lb32lo) {
@@ -793,7 +882,11 @@ __global__ void leaf_points_kernel(PlanView v, const int32_t *leaves, int32_t *l
   int b = v.cbegin[c], e = v.cend[c];
   const int p = v.p, n = v.n;
   __shared__ double s[kMaxP];
-  if (threadIdx.x < p) s[threadIdx.x] = v.cheb[threadIdx.x];
+  __shared__ DF sd[kMaxP];
+  if (threadIdx.x < p) {
+    s[threadIdx.x] = v.cheb[threadIdx.x];
+    sd[threadIdx.x] = df_of(v.cheb[threadIdx.x]);
+  }
   __syncthreads();
   double cx = v.ccentre[3 * c], cy = v.ccentre[3 * c + 1], cz = v.ccentre[3 * c + 2];
   double xm = v.cxmid[c], ym = v.cymid[c], h = v.chalf[c], hy = v.chy[c];
@@ -815,26 +908,18 @@ __global__ void leaf_points_kernel(PlanView v, const int32_t *leaves, int32_t *l
     }
     double u = (atan(a) - xm) / h;
     double w = (atan(bb) - ym) / hy;
-    double L[kMaxP];
-    lagrange_prod(n, s, u, L);
-    for (int k = 0; k < p; ++k) {
-      const int64_t o = (int64_t)i * p + k;
-      if (La64) La64[o] = L[k];
-      if (La32) {
-        const float hi = round_stochastic(L[k], hash32((uint32_t)(2 * o)));
-        La32[o] = hi;
-        La32lo[o] = (float)(L[k] - (double)hi);
-      }
+    if (La64) {
+      double L[kMaxP];
+      lagrange_prod(n, s, u, L);
+      for (int k = 0; k < p; ++k) La64[(int64_t)i * p + k] = L[k];
+      lagrange_prod(n, s, w, L);
+      for (int k = 0; k < p; ++k) Lb64[(int64_t)i * p + k] = L[k];
     }
-    lagrange_prod(n, s, w, L);
-    for (int k = 0; k < p; ++k) {
-      const int64_t o = (int64_t)i * p + k;
-      if (Lb64) Lb64[o] = L[k];
-      if (Lb32) {
-        const float hi = round_stochastic(L[k], hash32((uint32_t)(2 * o + 1)));
-        Lb32[o] = hi;
-        Lb32lo[o] = (float)(L[k] - (double)hi);
-      }
+    if (La32) {
+      // hashes of (point, axis, node): 2 o and 2 o + 1 for row entry o = i p + k
+      const int64_t o0 = (int64_t)i * p;
+      lagrange_rows_df(n, sd, u, (uint32_t)(2 * o0), 2u, La32 + o0, La32lo + o0);
+      lagrange_rows_df(n, sd, w, (uint32_t)(2 * o0 + 1), 2u, Lb32 + o0, Lb32lo + o0);
     }
   }
 }
