@@ -60,11 +60,11 @@ def log(*a):
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2508_13550_gb300", "csrc", f)
                   for f in ("interact32.cu", "fp32_math.cuh")]
 TRAFFIC_PER_EVAL = {
-    "source_sha256": "6623d6568d7547fd",
-    "pp_sym_kernel": (35.288576e6 + 129.246976e6) / 6083051520,
-    "near32x2_kernel": (236.353792e6 + 9.826816e6) / 3743870976,
-    "far32x2_kernel": (40.254464e6 + 0.027648e6) / 615546672,
-    "cc_sym_kernel": 6.238464e6 / 444180672,
+    "source_sha256": "a15ccee5df2fcfeb",
+    "pp_sym_kernel": (35.367424e6 + 128.747264e6) / 6083051520,
+    "near32x2_kernel": (236.443648e6 + 9.799936e6) / 3743870976,
+    "far32x2_kernel": (40.254208e6 + 0.066048e6) / 615546672,
+    "cc_sym_kernel": 6.239744e6 / 444180672,
 }
 
 
