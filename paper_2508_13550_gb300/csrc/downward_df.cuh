@@ -132,16 +132,23 @@ __device__ __forceinline__ void l2l_df_cell(const PlanView &v, int c, int r0, in
 // constant (0: runtime p) keeps each point's rows in registers and unrolls
 // the contractions.
 constexpr int kL2PThreads = 128;
-constexpr int kL2PDfSmemFloats = 2 * kMaxP * kMaxP + 4 * kL2PThreads * kMaxP;
+// Shared floats of l2p_df_leaf<PC>: the proxy potentials' (hi, lo) pairs and the
+// staged rows, with stride PC (kMaxP for a runtime p).
+template <int PC>
+constexpr int l2p_df_smem_floats() {
+  return 2 * (PC > 0 ? PC : kMaxP) * (PC > 0 ? PC : kMaxP) + 4 * kL2PThreads * (PC > 0 ? PC : kMaxP);
+}
+constexpr int kL2PDfSmemFloats = l2p_df_smem_floats<0>();
 
 template <int PC>
 __device__ __forceinline__ void l2p_df_leaf(const PlanView &v, int c, const double *psi, int ldr,
                                             int nrhs, int dim, const double *phi, double *out,
                                             float *sm) {
   // proxy potentials as (hi, lo) pairs: one 8-byte shared load per term
+  constexpr int PS = PC > 0 ? PC : kMaxP;
   float2 *sps = reinterpret_cast<float2 *>(sm);
-  float *sLa = sm + 2 * kMaxP * kMaxP, *sLal = sLa + kL2PThreads * kMaxP;
-  float *sLb = sLal + kL2PThreads * kMaxP, *sLbl = sLb + kL2PThreads * kMaxP;
+  float *sLa = sm + 2 * PS * PS, *sLal = sLa + kL2PThreads * PS;
+  float *sLb = sLal + kL2PThreads * PS, *sLbl = sLb + kL2PThreads * PS;
   if (!cell_ok(v, c)) return;
   const int b = v.cbegin[c], e = v.cend[c];
   const int p = PC > 0 ? PC : v.p, P = p * p;

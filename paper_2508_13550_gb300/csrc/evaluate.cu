@@ -677,13 +677,18 @@ __global__ void __launch_bounds__(kL2PThreads) l2p_kernel(PlanView v, const int3
 }
 
 // L2P + finalize of the FP32-bulk form (downward_df.cuh), one block of
-// kL2PThreads per leaf.
+// kL2PThreads per leaf; shared memory sized for the compile-time degree and
+// 7 resident blocks per SM requested (72 registers): at N = 6.3M, n = 12,
+// 0.562 ms against 0.589 ms with kMaxP-sized shared memory (6 blocks) and
+// 0.582 / 0.692 ms with 6 / 1 requested.
+#ifndef CSFMM_L2P_MINB
+#define CSFMM_L2P_MINB 7
+#endif
 template <int PC>
-__global__ void __launch_bounds__(kL2PThreads) l2p_df_kernel(PlanView v, const int32_t *leaves,
-                                                             const double *psi, int ldr, int nrhs,
-                                                             int dim, const double *phi,
-                                                             double *out) {
-  __shared__ __align__(16) float sm[kL2PDfSmemFloats];
+__global__ void __launch_bounds__(kL2PThreads, CSFMM_L2P_MINB) l2p_df_kernel(
+    PlanView v, const int32_t *leaves, const double *psi, int ldr, int nrhs, int dim,
+    const double *phi, double *out) {
+  __shared__ __align__(16) float sm[l2p_df_smem_floats<PC>()];
   l2p_df_leaf<PC>(v, leaves[blockIdx.x], psi, ldr, nrhs, dim, phi, out, sm);
 }
 

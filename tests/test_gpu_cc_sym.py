@@ -96,3 +96,26 @@ def test_no_cc_pairs_where_the_symmetric_pass_does_not_run():
     assert st64["cc_sym_pairs"] == 0
     st_bs, _ = _run(torch, C, pts, O.KERNEL_BIOT_SAVART, w, 8, 64, 0)
     assert st_bs["cc_sym_pairs"] == 0
+
+
+def _mirrored_pairs(t, s):
+    """Pairs (T, S), T < S, with both (T, S) and (S, T) in one list."""
+    es = set(zip(t.tolist(), s.tolist()))
+    return sum(1 for a, b in es if a < b and (b, a) in es)
+
+
+@pytest.mark.parametrize("name,mk,n,N0", [
+    ("cubed m=48, n=8", lambda: I.cubed_sphere_grid(48)[0], 8, 64),
+    ("random 20,000 points, n=6", lambda: I.random_sphere_points(20000, 63), 6, 60),
+])
+def test_pair_counts_equal_the_oracle_lists(name, mk, n, N0):
+    """The plan's mirrored PP and CC pairs are exactly the pairs of mirrored
+    entries in the oracle's lists (integer work: bit-exact)."""
+    torch = cuda_or_skip()
+    from paper_2508_13550_gb300 import csfmm as C
+    pts = mk()
+    f = O.FMM(pts, n, 0.7, N0)
+    L = f.lists()
+    st, _ = _run(torch, C, pts, O.KERNEL_NEWTON, np.ones(len(pts)) / len(pts), n, N0, 0)
+    assert st["sym_pairs"] == _mirrored_pairs(*L[O.PP]), name
+    assert st["cc_sym_pairs"] == _mirrored_pairs(*L[O.CC]), name
