@@ -887,10 +887,13 @@ csfmm_status run_passes(Plan &pl, Workspace &W, const double *w, int nrhs, doubl
   CSFMM_END(CSFMM_PHASE_FAR, sf);
   auto l2l = [&](cudaStream_t s) -> csfmm_status {
     CSFMM_BEGIN(CSFMM_PHASE_L2L, s);
+    // double-float L2L: one thread per child proxy (P = 169: 192 threads, 0.200
+    // against 0.229 ms with 128 at N = 6.3M, n = 12)
+    const int tb_l2l = std::max(64, ((pl.P + 31) / 32) * 32);
     for (int l = 0; l + 1 < pl.nlevels; ++l) {
       int c0 = pl.level_begin[l], nlev = pl.level_begin[l + 1] - c0;
       if constexpr (sizeof(Real) == 4)
-        l2l_df_kernel<<<nlev, 128, 0, s>>>(v, c0, 0, nrhs, dim, psi, ldr);
+        l2l_df_kernel<<<nlev, tb_l2l, 0, s>>>(v, c0, 0, nrhs, dim, psi, ldr);
       else
         l2l_kernel<double><<<nlev, 128, 0, s>>>(v, c0, 0, nrhs, dim, psi, ldr);
       ++pl.launches;
