@@ -295,11 +295,13 @@ __global__ void m2m_kernel(PlanView v, int cell0, int r0, int nr, Real *wbar, in
 // same pattern from cell to cell, so rounding the contraction to FP32 biases
 // all proxy weights alike (measured: a relative bias of up to 8e-8 in the
 // potentials at degree 8); in double-float that bias is gone.
-__global__ void m2m_df_kernel(PlanView v, int cell0, int r0, int nr, float *wbar, int ldr,
-                              float2 *wtot) {
-  // per right-hand side and warp (launched with 128 threads): partial totals
-  // of the cell's proxy weights
-  __shared__ double red[kMaxNrhs][4];
+constexpr int kM2MThreads = 192;  // one thread per parent proxy at P <= 192
+constexpr int kM2MWarps = kM2MThreads / 32;
+__global__ void __launch_bounds__(kM2MThreads) m2m_df_kernel(PlanView v, int cell0, int r0, int nr,
+                                                             float *wbar, int ldr, float2 *wtot) {
+  // per right-hand side and warp (launched with kM2MThreads threads): partial
+  // totals of the cell's proxy weights
+  __shared__ double red[kMaxNrhs][kM2MWarps];
   __shared__ float sMh[2 * kMaxP * kMaxP], sMl[2 * kMaxP * kMaxP];
   __shared__ float sw[kMaxP * kMaxP], sth[kMaxP * kMaxP], stl[kMaxP * kMaxP];
   const int c = cell0 + blockIdx.x;
@@ -311,7 +313,7 @@ __global__ void m2m_df_kernel(PlanView v, int cell0, int r0, int nr, float *wbar
     sMl[t] = v.m2m32[2 * p * p + t];
   }
   for (int r = r0; r < r0 + nr; ++r) {
-    constexpr int kPer = (kMaxP * kMaxP + 127) / 128;
+    constexpr int kPer = (kMaxP * kMaxP + kM2MThreads - 1) / kM2MThreads;
     float ah[kPer], al[kPer];
     for (int u = 0; u < kPer; ++u) ah[u] = al[u] = 0.f;
     for (int q = 0; q < 4; ++q) {
@@ -362,9 +364,11 @@ __global__ void m2m_df_kernel(PlanView v, int cell0, int r0, int nr, float *wbar
   }
   if (wtot) {  // totals of the cell's FP32 proxy weights, fixed summation order
     __syncthreads();
-    for (int r = threadIdx.x; r < nr; r += blockDim.x)
-      wtot[((int64_t)c * ldr + r0 + r) * 2 + 1] =
-          split_f32(red[r][0] + red[r][1] + red[r][2] + red[r][3]);
+    for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+      double s = 0.0;
+      for (int w = 0; w < kM2MWarps; ++w) s += red[r][w];
+      wtot[((int64_t)c * ldr + r0 + r) * 2 + 1] = split_f32(s);
+    }
   }
 }
 
@@ -808,7 +812,7 @@ csfmm_status run_passes(Plan &pl, Workspace &W, const double *w, int nrhs, doubl
       CSFMM_BEGIN(CSFMM_PHASE_M2M, st);
       for (int l = pl.nlevels - 2; l >= 0; --l) {
         const int c0 = pl.level_begin[l], nlev = pl.level_begin[l + 1] - c0;
-        m2m_df_kernel<<<nlev, 128, 0, st>>>(v, c0, 0, nrhs, wbar, ldr, wtot);
+        m2m_df_kernel<<<nlev, kM2MThreads, 0, st>>>(v, c0, 0, nrhs, wbar, ldr, wtot);
         ++pl.launches;
       }
       CSFMM_END(CSFMM_PHASE_M2M, st);
@@ -840,7 +844,7 @@ csfmm_status run_passes(Plan &pl, Workspace &W, const double *w, int nrhs, doubl
   for (int l = pl.nlevels - 2; l >= 0; --l) {
     int c0 = pl.level_begin[l], nlev = pl.level_begin[l + 1] - c0;
     if constexpr (sizeof(Real) == 4)
-      m2m_df_kernel<<<nlev, 128, 0, sf>>>(v, c0, 0, nrhs, wbar, ldr, wtot);
+      m2m_df_kernel<<<nlev, kM2MThreads, 0, sf>>>(v, c0, 0, nrhs, wbar, ldr, wtot);
     else
       m2m_kernel<Real><<<nlev, 128, 0, sf>>>(v, c0, 0, nrhs, wbar, ldr);
     ++pl.launches;
@@ -980,7 +984,7 @@ csfmm_status run_cstc(Plan &pl, Workspace &W, const double *w, int nrhs, double 
   for (int l = pl.nlevels - 2; l >= 0; --l) {
     const int c0 = pl.level_begin[l], nlev = pl.level_begin[l + 1] - c0;
     if constexpr (sizeof(Real) == 4)
-      m2m_df_kernel<<<nlev, 128, 0, st>>>(v, c0, 0, nrhs, wbar, ldr, wtot);
+      m2m_df_kernel<<<nlev, kM2MThreads, 0, st>>>(v, c0, 0, nrhs, wbar, ldr, wtot);
     else
       m2m_kernel<Real><<<nlev, 128, 0, st>>>(v, c0, 0, nrhs, wbar, ldr);
   }
