@@ -165,7 +165,8 @@ template <typename Real, int NR>
 __global__ void p2m_kernel(PlanView v, const int32_t *leaves, const double *ws, int ldw, int r0,
                            Real *wbar, int ldr, float2 *wtot) {
   constexpr int CH = 64;
-  __shared__ Real sLa[CH * kMaxP], sLb[CH * kMaxP], sw[NR * CH];
+  __shared__ Real sLa[CH * kMaxP], sLb[CH * kMaxP];
+  __shared__ __align__(16) Real sw[CH * NR];  // [point][rhs]: one vector load per point
   const int c = leaves[blockIdx.x];
   if (!cell_ok(v, c)) return;
   const int b = v.cbegin[c], e = v.cend[c], p = v.p, P = v.P;
@@ -184,7 +185,7 @@ __global__ void p2m_kernel(PlanView v, const int32_t *leaves, const double *ws, 
     }
     for (int t = threadIdx.x; t < NR * CH; t += blockDim.x) {
       const int q = t / CH, j = t - q * CH;
-      sw[t] = j < nj ? (Real)ws[(int64_t)(r0 + q) * ldw + j0 + j] : (Real)0;
+      sw[j * NR + q] = j < nj ? (Real)ws[(int64_t)(r0 + q) * ldw + j0 + j] : (Real)0;
     }
     __syncthreads();
     if (k < P) {
@@ -194,7 +195,7 @@ __global__ void p2m_kernel(PlanView v, const int32_t *leaves, const double *ws, 
       for (int j = 0; j < nj; ++j) {
         const Real l = sLa[j * p + k1] * sLb[j * p + k2];
 #pragma unroll
-        for (int q = 0; q < NR; ++q) ch[q] += l * sw[q * CH + j];
+        for (int q = 0; q < NR; ++q) ch[q] += l * sw[j * NR + q];
       }
 #pragma unroll
       for (int q = 0; q < NR; ++q) acc[q] += (double)ch[q];
@@ -787,9 +788,11 @@ csfmm_status run_passes(Plan &pl, Workspace &W, const double *w, int nrhs, doubl
   const int tb_p2m = tb_prox < 64 ? 64 : tb_prox;
   auto p2m = [&](cudaStream_t s) -> csfmm_status {
     CSFMM_BEGIN(CSFMM_PHASE_P2M, s);
-    for (int r0 = 0; r0 < nrhs; r0 += kRB) {
+    for (int r0 = 0; r0 < nrhs; r0 += (sizeof(Real) == 4 && nrhs - r0 >= 8) ? 8 : kRB) {
       int nr = min(kRB, nrhs - r0);
+      if (sizeof(Real) == 4 && nrhs - r0 >= 8) nr = 8;  // FP32 form: 8 RHS per pass over the rows
       switch (nr) {
+        case 8: p2m_kernel<Real, 8><<<pl.nleaves, tb_p2m, 0, s>>>(v, pl.leaves, W.ws, N, r0, wbar, ldr, wtot); break;
         case 1: p2m_kernel<Real, 1><<<pl.nleaves, tb_p2m, 0, s>>>(v, pl.leaves, W.ws, N, r0, wbar, ldr, wtot); break;
         case 2: p2m_kernel<Real, 2><<<pl.nleaves, tb_p2m, 0, s>>>(v, pl.leaves, W.ws, N, r0, wbar, ldr, wtot); break;
         case 3: p2m_kernel<Real, 3><<<pl.nleaves, tb_p2m, 0, s>>>(v, pl.leaves, W.ws, N, r0, wbar, ldr, wtot); break;
